@@ -1,0 +1,208 @@
+"""Seeded synthetic inputs shared by the tests, the oracle runs and the benchmark.
+
+This module only builds problem statements: lattices of PD nodes, finite-element
+meshes, pre-crack cuts, traction loads, material constants and random initial
+fields. It holds none of the method's arithmetic (no bond force, no time step,
+no coupling), so the oracle and the CUDA library can both take their inputs
+from it without sharing any computation.
+
+Workloads follow the benchmark plates of arXiv 2403.03605 (Sec. 3.3, Sec. 4.1):
+regular lattices with nodes at cell centres, horizon 3.015 dx, glass-like
+material (E = 72 GPa, nu = 1/3, rho = 2440 kg/m^3, G0 = 3.8 J/m^2), tractions
+applied as a body force over a layer of width delta (Sec. 3.3) and straight
+pre-cracks whose crossing bonds start broken. The paper uses no dataset; these
+synthetic plates stand in for its examples.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+HORIZON_FACTOR = 3.015
+
+
+@dataclass
+class Material:
+    E: float = 72e9
+    nu: float = 1.0 / 3.0
+    rho: float = 2440.0
+    G0: float = 3.8
+    thickness: float = 1e-3  # plane-stress thickness h of the 2D plates [m]
+
+
+def pmb_constants(dim: int, mat: Material, delta: float):
+    """Micromodulus constant c and critical stretch s0 of the benchmark plates.
+
+    2D plane stress: c = 9E / (pi h delta^3), s0 = sqrt(4 pi G0 / (9 E delta)).
+    3D: c = 12E / (pi delta^4), s0 = sqrt(5 G0 / (9 E delta)).
+    These are the problem statement's constants, inputs to both sides.
+    """
+    if dim == 2:
+        c = 9.0 * mat.E / (math.pi * mat.thickness * delta ** 3)
+        s0 = math.sqrt(4.0 * math.pi * mat.G0 / (9.0 * mat.E * delta))
+    else:
+        c = 12.0 * mat.E / (math.pi * delta ** 4)
+        s0 = math.sqrt(5.0 * mat.G0 / (9.0 * mat.E * delta))
+    return c, s0
+
+
+@dataclass
+class Lattice:
+    """Regular lattice of PD nodes at cell centres, x fastest.
+
+    shape: nodes per axis; dx: spacing; origin: corner of the lattice box.
+    Node (ix, iy[, iz]) has index ix + nx * (iy + ny * iz) and position
+    origin + (idx + 1/2) dx. `P` holds the same position in integer half-dx
+    units relative to origin (2 idx + 1), used for exact pre-crack tests.
+    """
+    shape: tuple
+    dx: float
+    origin: tuple
+
+    @property
+    def dim(self):
+        return len(self.shape)
+
+    @property
+    def n(self):
+        return int(np.prod(self.shape))
+
+    def index_grid(self):
+        axes = [np.arange(s, dtype=np.int64) for s in self.shape]
+        grids = np.meshgrid(*axes, indexing="ij")  # grids[d][ix, iy, ...]
+        # flatten with x fastest: transpose so that axis 0 (x) varies fastest
+        return np.stack([g.transpose(*reversed(range(self.dim))).reshape(-1) for g in grids])
+
+    @property
+    def idx(self):
+        return self.index_grid()
+
+    @property
+    def X(self):
+        idx = self.index_grid().astype(np.float64)
+        org = np.asarray(self.origin, dtype=np.float64).reshape(-1, 1)
+        return org + (idx + 0.5) * self.dx
+
+    @property
+    def P(self):
+        return 2 * self.index_grid() + 1
+
+    def half_units(self, value: float, axis: int) -> int:
+        """A coordinate on the half-dx grid, as an exact integer (asserts it is on it)."""
+        q = (value - self.origin[axis]) / (0.5 * self.dx)
+        k = int(round(q))
+        assert abs(q - k) < 1e-6, (value, axis, q)
+        return k
+
+
+@dataclass
+class Cut:
+    """Axis-aligned straight pre-crack: plane x[normal] = level, lo <= x[along] < hi [m]."""
+    normal: int
+    level: float
+    along: int
+    lo: float
+    hi: float
+
+    def as_array(self):
+        return np.array([self.normal, self.level, self.along, self.lo, self.hi], dtype=np.float64)
+
+    def in_half_units(self, lat: Lattice):
+        return (self.normal, lat.half_units(self.level, self.normal), self.along,
+                lat.half_units(self.lo, self.along), lat.half_units(self.hi, self.along))
+
+
+def edge_traction_body_force(lat: Lattice, traction: float, delta: float, axis: int = 1):
+    """Traction on the two faces normal to `axis` as a body force (Sec. 3.3, Sec. 4.1).
+
+    Nodes whose cell-centre distance to a face is at most delta form a layer of
+    `k` rows; each gets b = +-T / (k dx) along `axis` (outward), so the layer
+    carries exactly T per unit face area.
+    """
+    idx = lat.idx
+    ncount = lat.shape[axis]
+    k = 0
+    while k < ncount and (k + 0.5) * lat.dx <= delta:
+        k += 1
+    b = np.zeros((lat.dim, lat.n))
+    mag = traction / (k * lat.dx)
+    b[axis, idx[axis] < k] = -mag
+    b[axis, idx[axis] >= ncount - k] = +mag
+    return b
+
+
+@dataclass
+class PDProblem:
+    """A pure PD problem statement (inputs only)."""
+    name: str
+    lat: Lattice
+    mat: Material
+    delta: float
+    c: float
+    s0: float
+    dt: float
+    nsteps: int
+    cuts: list
+    b: np.ndarray
+    vol: float
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def dim(self):
+        return self.lat.dim
+
+    @property
+    def n(self):
+        return self.lat.n
+
+
+def plate2d(nx: int, ny: int, dx: float, *, cuts_mm=(), traction=12e6, dt=25e-9, nsteps=500,
+            mat: Material | None = None, name="plate2d") -> PDProblem:
+    mat = mat or Material()
+    lat = Lattice((nx, ny), dx, (0.0, 0.0))
+    delta = HORIZON_FACTOR * dx
+    c, s0 = pmb_constants(2, mat, delta)
+    cuts = [Cut(*cm) for cm in cuts_mm]
+    b = edge_traction_body_force(lat, traction, delta, axis=1) if traction else np.zeros((2, lat.n))
+    return PDProblem(name, lat, mat, delta, c, s0, dt, nsteps, cuts, b, mat.thickness * dx * dx)
+
+
+def plate3d(nx: int, ny: int, nz: int, dx: float, *, cuts_mm=(), traction=12e6, dt=20e-9, nsteps=300,
+            mat: Material | None = None, name="plate3d") -> PDProblem:
+    mat = mat or Material(nu=0.25)
+    lat = Lattice((nx, ny, nz), dx, (0.0, 0.0, 0.0))
+    delta = HORIZON_FACTOR * dx
+    c, s0 = pmb_constants(3, mat, delta)
+    cuts = [Cut(*cm) for cm in cuts_mm]
+    b = edge_traction_body_force(lat, traction, delta, axis=1) if traction else np.zeros((3, lat.n))
+    return PDProblem(name, lat, mat, delta, c, s0, dt, nsteps, cuts, b, dx ** 3)
+
+
+def config0() -> PDProblem:
+    """Pure FP64 2D plate: 0.05 x 0.05 m, dx 0.5 mm (100 x 100 nodes), centred 10 mm
+    pre-crack at mid-height, 12 MPa on top/bottom edges, dt 25 ns, 500 steps."""
+    return plate2d(100, 100, 0.5e-3, cuts_mm=[(1, 0.025, 0, 0.020, 0.030)], traction=12e6,
+                   dt=25e-9, nsteps=500, name="plate2d_100x100_dx0.5mm_centre_crack")
+
+
+def small_plate(nx=40, ny=24, dx=0.5e-3, nsteps=200, crack=True, dt=25e-9) -> PDProblem:
+    """A small plate the oracle finishes in well under a second (tests)."""
+    cuts = [(1, ny * dx / 2, 0, 0.0, nx * dx * 0.4)] if crack else []
+    return plate2d(nx, ny, dx, cuts_mm=cuts, traction=12e6, dt=dt, nsteps=nsteps,
+                   name=f"plate2d_{nx}x{ny}")
+
+
+def strip_lattice_pd(nx: int, ny: int, dx: float, crack_len: float, traction=12e6, dt=5e-9, nsteps=100,
+                     name="strip") -> PDProblem:
+    """The PD strip of the coupled plates used as a standalone PD lattice
+    (edge pre-crack along the mid line, traction layer on the strip's faces)."""
+    return plate2d(nx, ny, dx, cuts_mm=[(1, ny * dx / 2, 0, 0.0, crack_len)], traction=traction,
+                   dt=dt, nsteps=nsteps, name=name)
+
+
+def random_field(shape, scale, seed):
+    """Seeded smooth-ish random field (used for initial displacements in tests)."""
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal(shape) * scale
