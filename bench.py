@@ -1,0 +1,308 @@
+"""Benchmark of the PD hot path (bond updates/s, fraction of the HBM roofline).
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+A step is one coarse step's PD cycle: m = 20 velocity-Verlet substeps (bond
+gather, stretch, irreversible breaking, force sum, update) of the 2000 x 400
+(800,000-node, 22.3M directed-bond) PD lattice of the fine coupled plate,
+FP32-bulk arithmetic, replayed as one captured CUDA graph. Inputs are seeded
+synthetic data resident in HBM before the timed region; L2 is flushed between
+timed steps. One JSON line is printed by rank 0.
+
+--impl reference times the FP64 CPU oracle (the reference of this build) on
+the host cores, on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD = dict(name="pd_strip_2000x400_dx0.05mm_m20_fp32bulk", nx=2000, ny=400, dx=0.05e-3, crack=0.05,
+                traction=12e6, dt=5e-9, m=20)
+METRIC = "PD bond updates/s"
+UNIT = "bond updates/s"
+
+
+def make_problem():
+    from paper_2403_03605_gb300 import workloads as W
+    w = WORKLOAD
+    return W.strip_lattice_pd(w["nx"], w["ny"], w["dx"], w["crack"], traction=w["traction"], dt=w["dt"],
+                              name=w["name"])
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4) if s[5 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def algorithmic_bytes(info, pb, with_body=True):
+    """Bytes one FP32-bulk 2D substep must move with this layout: per directed
+    bond a 4-byte family word and one status bit; per node u (16 in, 16 out),
+    v (16 in, 16 out), a (8 in, 8 out), 1/m (4), the weighted body force (8)."""
+    nb, n = info["n_bonds"], info["n"]
+    per_node = 16 + 16 + 16 + 16 + 8 + 8 + 4 + (8 if with_body else 0)
+    return 4 * nb + nb / 8.0 + per_node * n, per_node
+
+
+def oracle_sample(pb, nsub, setup=None):
+    """Time `nsub` oracle substeps on this workload (FP64, plain C, one core)."""
+    import oracle
+    if setup is None:
+        rp, col = oracle.family(pb.lat.X, pb.delta)
+        mu, _ = oracle.precrack(pb.lat.P, rp, col, [c.in_half_units(pb.lat) for c in pb.cuts])
+        opd = oracle.PD(pb.lat.X, pb.vol, pb.delta, pb.c, pb.s0, pb.mat.rho, pb.dt)
+        u = np.zeros((2, pb.n)); v = np.zeros_like(u); a = np.zeros_like(u)
+        oracle.pd_run(opd, rp, col, mu, u, v, a, 0, b=pb.b, init=True)
+        setup = (rp, col, mu, opd, u, v, a)
+    rp, col, mu, opd, u, v, a = setup
+    t0 = time.perf_counter()
+    oracle.pd_run(opd, rp, col, mu, u, v, a, nsub, b=pb.b)
+    dt = time.perf_counter() - t0
+    return len(col) * nsub / dt, dt, setup
+
+
+def run_reference(args, rank, world):
+    pb = make_problem()
+    if rank != 0:
+        return
+    nsub = 2
+    setup = None
+    for _ in range(args.warmup):
+        _, _, setup = oracle_sample(pb, nsub, setup)
+    total_t, total_u = 0.0, 0
+    for _ in range(args.steps):
+        rate, dt, setup = oracle_sample(pb, nsub, setup)
+        total_t += dt
+        total_u += len(setup[1]) * nsub
+    value = total_u / total_t
+    sample = f"{nsub} FP64 oracle substeps of the {pb.n}-node lattice per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD["name"], "nodes": pb.n,
+                                            "bonds": len(setup[1]), "m": WORKLOAD["m"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    from paper_2403_03605_gb300 import build as B
+    from paper_2403_03605_gb300 import pdmts as P
+
+    B.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    pb = make_problem()
+    m = WORKLOAD["m"]
+    stream = torch.cuda.current_stream(dev)
+    ctx = P.pdmts_ctx_create(local_rank, stream.cuda_stream)
+    pd = P.pd_create(ctx, pb.lat.X, horizon=pb.delta, c=pb.c, s0=pb.s0, rho=pb.mat.rho, vol_uniform=pb.vol,
+                     precision=P.PDMTS_FP32_BULK)
+    P.pd_set_precrack(pd, [c.as_array() for c in pb.cuts])
+    P.pd_set_body_force(pd, pb.b)
+    P.mts_set_time(ctx, pb.dt, m)
+    info = P.pd_info(pd)
+    flush = torch.empty(int(256e6) // 4, dtype=torch.float32, device=dev)  # > L2 (129 MiB)
+
+    for _ in range(args.warmup):
+        P.mts_advance(ctx, 1)
+    torch.cuda.synchronize(dev)
+
+    # ---- device-timed region: K steps, L2 flushed between steps ----------
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stops = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    st0 = P.pdmts_get_stats(ctx)
+    P.pdmts_get_timing(ctx)
+    P.pdmts_set_timing(ctx, True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local_rank) as clk:
+        time.sleep(0.3)
+        for k in range(args.steps):
+            flush.zero_()
+            starts[k].record(stream)
+            P.mts_advance(ctx, 1)
+            stops[k].record(stream)
+        torch.cuda.synchronize(dev)
+    P.pdmts_set_timing(ctx, False)
+    if world > 1:
+        dist.barrier()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, stops)]
+    total_ms = float(sum(step_ms))
+    chain_ms, chain_sub = P.pdmts_get_timing(ctx)
+    st1 = P.pdmts_get_stats(ctx)
+    launches = st1["kernel_launches"] - st0["kernel_launches"]
+    units = info["n_bonds"] * m * args.steps
+    t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    value = units * world / (total_ms * 1e-3)
+
+    # ---- roofline of the dominant kernel (the FP32-bulk substep) ----------
+    abytes, per_node = algorithmic_bytes(info, pb)
+    launch_ms = chain_ms / max(chain_sub, 1)
+    achieved = abytes / (launch_ms * 1e-3) / 1e9
+    peak, peak_kind = peaks()
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "pd_step_f32_strip2000x400_traffic.json")
+    if os.path.exists(tfile):
+        try:
+            with open(tfile) as f:
+                tj = json.load(f)
+            if tj.get("kernel_version") == kernel_version():
+                traffic = tj["dram_bytes_per_launch"]
+        except Exception:
+            traffic = None
+
+    # ---- end to end through the C ABI with host buffers ------------------
+    b_host = torch.from_numpy(np.ascontiguousarray(pb.b)).pin_memory()
+    u_host = torch.empty((pb.dim, pb.n), dtype=torch.float64).pin_memory()
+    e2e_steps = max(3, min(args.steps, 10))
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        P.pd_set_body_force(pd, b_host)
+        P.mts_advance(ctx, 1)
+        P.pd_read_displacement(pd, u_host.numpy())
+    torch.cuda.synchronize(dev)
+    e2e_s = time.perf_counter() - t0
+    e2e_value = info["n_bonds"] * m * e2e_steps * world / e2e_s
+    u_final = u_host.numpy()
+    assert np.isfinite(u_final).all()
+
+    # ---- CPU baseline: the FP64 oracle on a bounded sample ----------------
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        nsub = 20
+        rate, dt, _ = oracle_sample(pb, nsub)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{nsub} FP64 oracle substeps of the same {pb.n}-node lattice ({dt:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD["name"], "nodes": pb.n, "bonds": info["n_bonds"], "m": m,
+                       "substeps_per_step": m, "graph": "one captured graph per step",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "l2": "flushed between timed steps (256 MB write); working set 166 MB"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                         "kernel": "k_pd_step_f32<2>", "algorithmic_bytes_per_launch": abytes,
+                         "launch_us": launch_ms * 1e3},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(b_host.numel() * 8),
+                    "d2h_bytes_per_step": int(u_host.numel() * 8)},
+            "gpu_launches": int(launches),
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    P.pdmts_ctx_destroy(ctx)
+
+
+def kernel_version():
+    """Hash of the hot-path kernel source: a stored DRAM-traffic figure is only
+    reported while the kernel it was measured on is unchanged."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_2403_03605_gb300", "csrc", "pd_kernels.cu")
+    with open(src, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

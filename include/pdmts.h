@@ -1,0 +1,198 @@
+/*
+ * pdmts.h -- C ABI of the GB300 library for multi-time-step (MTS) coupling of
+ * bond-based peridynamics (PD) and classical continuum mechanics (CCM)
+ * following arXiv 2403.03605 ("Multi-time-step coupling of peridynamics and
+ * classical continuum mechanics for dynamic brittle fracture").
+ *
+ * Conventions (apply to every call below):
+ *  - Every call returns int: PDMTS_OK (0) on success, a negative PDMTS_ERR_*
+ *    code otherwise. pdmts_last_error() returns a message for the calling
+ *    thread's most recent failure.
+ *  - Handles are opaque and owned by the library; each *_destroy frees one.
+ *  - Input arrays are caller-owned and are copied in during the call; nothing
+ *    is retained after the call returns. A pointer may address host memory
+ *    (pageable or pinned) or device memory of the context's device (UVA).
+ *  - Output arrays are caller-owned buffers of the stated size, host or device.
+ *  - Vector fields are structure-of-arrays: component d of node i is at
+ *    [d * n + i]. Units are SI. Indices are int32 within one subdomain.
+ *  - All device work is ordered after work already queued on the stream given
+ *    to pdmts_ctx_create, and work queued on that stream afterwards is ordered
+ *    after it. Read-back calls block until their data is on the caller side.
+ *  - Failure: arguments are validated before any device work; a failed call
+ *    leaves the handle's state unchanged unless stated otherwise.
+ */
+#ifndef PDMTS_H
+#define PDMTS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define PDMTS_OK 0
+#define PDMTS_ERR_ARG (-1)         /* null pointer, size mismatch, NaN, out-of-range value   */
+#define PDMTS_ERR_MASS (-2)        /* a PD node with (1 - alpha_i) rho <= 0                 */
+#define PDMTS_ERR_STABILITY (-3)   /* dt above the explicit stability bound of the PD model */
+#define PDMTS_ERR_CUDA (-4)        /* a CUDA runtime call or kernel failed                  */
+#define PDMTS_ERR_TIMEOUT (-5)     /* a bounded device-side wait gave up                    */
+#define PDMTS_ERR_STATE (-6)       /* call out of order (e.g. advance before set-up)        */
+#define PDMTS_ERR_NOMEM (-7)       /* host or device allocation failed                      */
+#define PDMTS_ERR_UNSUPPORTED (-8) /* valid request this build does not implement            */
+
+/* ---- enumerations -------------------------------------------------------- */
+#define PDMTS_FP64 0      /* all PD arithmetic in IEEE FP64, fixed summation order, no FMA  */
+#define PDMTS_FP32_BULK 1 /* bond stretch/force in FP32 from displacement differences;
+                             u, v carried as compensated FP32 pairs (needs lattice nodes) */
+
+#define PDMTS_MICRO_POWER 0 /* c(|xi|) = c / |xi|^3  (linearised PMB constant)           */
+#define PDMTS_MICRO_EXP 1   /* c(|xi|) = c exp(-|xi| / l)                                 */
+
+#define PDMTS_FORCE_LINEAR 0 /* f = c(|xi|) (xi (x) xi) eta                     (Eq. 2)  */
+#define PDMTS_FORCE_PMB 1    /* f = c(|xi|) |xi|^3 s (xi + eta) / |xi + eta|   (variant) */
+
+#define PDMTS_WEIGHT_CONSTANT 0 /* alpha = 1/2 in the overlap                     (Sec. 3.2) */
+#define PDMTS_WEIGHT_LINEAR 1   /* alpha = l1 / l_O                                (Sec. 3.2) */
+#define PDMTS_WEIGHT_CUBIC 2    /* alpha = (l1 / l_O)^3                            (Sec. 3.2) */
+
+typedef struct pdmts_ctx pdmts_ctx;
+typedef struct pdmts_pd pdmts_pd;
+typedef struct pdmts_fem pdmts_fem;
+typedef struct pdmts_arl pdmts_arl;
+
+/* ---- context ------------------------------------------------------------- */
+
+/* Create a context on CUDA device `device`. `cuda_stream` is a cudaStream_t
+ * (e.g. torch.cuda.current_stream().cuda_stream) or NULL for the legacy
+ * default stream; the library orders its own stream against it. */
+int pdmts_ctx_create(pdmts_ctx **ctx, int device, void *cuda_stream);
+int pdmts_ctx_destroy(pdmts_ctx *ctx);
+
+/* Message for the calling thread's last failed call ("" if none). The
+ * pointer stays valid until the next failing call on the same thread. */
+const char *pdmts_last_error(void);
+
+/* Optional device allocator (e.g. PyTorch's caching allocator). alloc must
+ * return device memory of the context's device, aligned to 256 bytes, or NULL.
+ * Must be set before any subdomain is created. NULL restores cudaMalloc. */
+typedef void *(*pdmts_alloc_fn)(size_t bytes, void *user);
+typedef void (*pdmts_free_fn)(void *ptr, void *user);
+int pdmts_set_allocator(pdmts_ctx *ctx, pdmts_alloc_fn alloc, pdmts_free_fn free_fn, void *user);
+
+/* Block the host until all work queued by the library has finished. */
+int pdmts_ctx_synchronize(pdmts_ctx *ctx);
+
+/* ---- PD subdomain (Sec. 2.1: Eq. 1-5; Sec. 2.3: Eq. 34 weights) ---------- */
+
+/* Create the PD subdomain of `ctx` (one per context).
+ *   dim            2 (plane stress, per-unit-thickness volumes) or 3
+ *   n              number of PD nodes (material points), 0 < n < 2^31
+ *   X              reference positions, dim * n doubles (SoA)
+ *   vol            nodal volumes V_i (n doubles) or NULL to use vol_uniform
+ *   horizon        delta > 0; the family is H_delta(x) = {x' : |x' - x| <= delta}
+ *   micro_kind     PDMTS_MICRO_POWER or PDMTS_MICRO_EXP; c, l its constants (Eq. 2,
+ *                  Sec. 3.2 / Sec. 3.3 exponential form)
+ *   s0             critical stretch s_crit of Eq. 4 (> 0)
+ *   rho            mass density (> 0)
+ *   precision      PDMTS_FP64 or PDMTS_FP32_BULK
+ * The family (CSR, each row ascending) is built here. FP32_BULK requires the
+ * nodes to lie on a regular lattice x = x0 + k h (k integer, |k| < 32768);
+ * otherwise PDMTS_ERR_UNSUPPORTED. Initial state: u = v = 0, all bonds intact,
+ * no body force, breaking enabled, force law PDMTS_FORCE_LINEAR. */
+int pd_create(pdmts_ctx *ctx, int dim, int64_t n, const double *X, const double *vol,
+              double vol_uniform, double horizon, int micro_kind, double c, double l,
+              double s0, double rho, int precision, pdmts_pd **pd);
+int pd_destroy(pdmts_pd *pd);
+
+/* Pre-crack: each cut is 5 doubles {normal axis, level, along axis, lo, hi}:
+ * the plane x[normal] = level, restricted to lo <= x[along] < hi (in 3D the
+ * third axis is unrestricted). A bond is broken (mu = 0, Eq. 4) when its end
+ * points lie strictly on opposite sides of the plane and its crossing point
+ * is inside [lo, hi). On a lattice the test is exact (half-spacing units). */
+int pd_set_precrack(pdmts_pd *pd, int n_cuts, const double *cuts);
+
+/* External body force density b (Eq. 1), dim * n doubles [N/m^3]; NULL clears. */
+int pd_set_body_force(pdmts_pd *pd, const double *b);
+
+/* Displacement u and velocity v (dim * n doubles each; NULL means zero). The
+ * acceleration is recomputed from u (Eq. 1) at the start of the next advance. */
+int pd_set_state(pdmts_pd *pd, const double *u, const double *v);
+
+/* Arlequin weights alpha_i of the PD nodes (Eq. 17-18, Eq. 34), n doubles in
+ * [0, 1) or NULL (all zero). The PD node mass becomes (1 - alpha_i) rho V_i,
+ * its body force (1 - alpha_i) b_i, and bond (i, j) is weighted by
+ * 1 - (alpha_i + alpha_j) / 2. PDMTS_ERR_MASS if some 1 - alpha_i <= 0.
+ * arlequin_bind sets these from the overlap geometry. */
+int pd_set_weights(pdmts_pd *pd, const double *alpha);
+
+/* Enable (1) or freeze (0) bond breaking (Eq. 4). */
+int pd_set_breaking(pdmts_pd *pd, int enabled);
+
+/* PDMTS_FORCE_LINEAR (Eq. 2, default) or PDMTS_FORCE_PMB. */
+int pd_set_force_law(pdmts_pd *pd, int kind);
+
+typedef struct {
+    int32_t dim;
+    int32_t precision;
+    int64_t n;             /* nodes                                        */
+    int64_t n_bonds;       /* directed bonds (CSR entries)                 */
+    int64_t n_slots;       /* stored slots of the sliced-ELL layout        */
+    int32_t max_degree;    /* largest family                               */
+    int32_t on_lattice;    /* 1 if the nodes lie on a regular lattice      */
+    double lattice_h;      /* lattice spacing (0 if not on a lattice)      */
+    int64_t steps_done;    /* PD substeps advanced since creation          */
+    int64_t device_bytes;  /* device memory held by this subdomain         */
+} pdmts_pd_info;
+int pd_info(const pdmts_pd *pd, pdmts_pd_info *info);
+
+/* Read-back (blocking). u, v, a: dim * n doubles at the current time. */
+int pd_read_displacement(pdmts_pd *pd, double *u);
+int pd_read_velocity(pdmts_pd *pd, double *v);
+int pd_read_acceleration(pdmts_pd *pd, double *a);
+/* Damage phi_i (Eq. 5), n doubles. */
+int pd_read_damage(pdmts_pd *pd, double *phi);
+/* Bond status mu (Eq. 4) in CSR order (n_bonds bytes, 1 = intact); n_intact
+ * may be NULL. */
+int pd_read_bond_status(pdmts_pd *pd, uint8_t *mu, int64_t *n_intact);
+/* The family in CSR form: row_ptr (n + 1 int64), col (n_bonds int32). */
+int pd_read_family(pdmts_pd *pd, int64_t *row_ptr, int32_t *col);
+
+/* ---- time integration (Sec. 2.4 Eq. 38; Sec. 2.5 Eq. 39-49, Alg. 1) ------- */
+
+/* dt_pd: PD time step; m_ratio: dt_fe = m dt_pd (Sec. 2.5); (gamma_fe, beta_fe):
+ * Newmark parameters of the FE subdomain. The PD subdomain always uses
+ * velocity Verlet (gamma, beta) = (1/2, 0). With check_stability != 0 a dt_pd
+ * above the PD stability bound returns PDMTS_ERR_STABILITY. */
+int mts_set_time(pdmts_ctx *ctx, double dt_pd, int m_ratio, double gamma_fe, double beta_fe,
+                 int check_stability);
+
+/* Advance n_coarse coarse steps. Without an Arlequin coupling bound, a coarse
+ * step is m_ratio plain PD velocity-Verlet steps (pure PD). With a coupling,
+ * each coarse step is Alg. 1 (FE free step, m PD free substeps with the
+ * interpolated multiplier, multiplier solve, correction). */
+int mts_advance(pdmts_ctx *ctx, int64_t n_coarse);
+
+/* Kernel timing. While enabled, every chain of PD substeps is bracketed by
+ * CUDA events on the library's own stream (the stream the substep kernels run
+ * on). pdmts_get_timing blocks, returns the summed chain time in milliseconds
+ * and the number of substeps inside those chains, and resets both. */
+int pdmts_set_timing(pdmts_ctx *ctx, int enabled);
+int pdmts_get_timing(pdmts_ctx *ctx, double *substep_ms, int64_t *substeps);
+
+/* Counters since context creation. */
+typedef struct {
+    int64_t pd_substeps;      /* PD substeps (free + link)                */
+    int64_t bond_updates;     /* directed-bond evaluations                */
+    int64_t coarse_steps;     /* coarse steps completed                   */
+    int64_t bonds_broken;     /* bonds broken by the dynamics             */
+    int64_t kernel_launches;  /* kernels launched by the library          */
+    int64_t graph_launches;   /* CUDA graph launches                      */
+} pdmts_stats;
+int pdmts_get_stats(pdmts_ctx *ctx, pdmts_stats *stats);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PDMTS_H */

@@ -1,0 +1,1311 @@
+// api.cpp -- C ABI of the pdmts library: context, PD subdomain set-up and
+// read-back, pure-PD time stepping. The hot path itself is in pd_kernels.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <map>
+#include <new>
+#include <tuple>
+
+#include "pd.h"
+
+namespace pdmts {
+
+static thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+void clear_error() { g_err.clear(); }
+
+static bool finite_all(const double *p, int64_t n)
+{
+    for (int64_t i = 0; i < n; ++i)
+        if (!std::isfinite(p[i]))
+            return false;
+    return true;
+}
+
+// Copy `count` elements from a host or device pointer into a host vector.
+template <typename T>
+static int fetch(std::vector<T> &out, const T *src, int64_t count)
+{
+    out.resize((size_t)count);
+    if (count == 0)
+        return PDMTS_OK;
+    PDMTS_CUDA_TRY(cudaMemcpy(out.data(), src, sizeof(T) * (size_t)count, cudaMemcpyDefault));
+    return PDMTS_OK;
+}
+
+}  // namespace pdmts
+
+using namespace pdmts;
+
+// ------------------------------------------------------------- context ------
+void *pdmts_ctx::dalloc(size_t bytes)
+{
+    if (bytes == 0)
+        bytes = 256;
+    void *p = nullptr;
+    if (alloc) {
+        p = alloc(bytes, alloc_user);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p)
+        device_bytes += (int64_t)bytes;
+    return p;
+}
+
+void pdmts_ctx::dfree(void *p)
+{
+    if (!p)
+        return;
+    if (free_fn)
+        free_fn(p, alloc_user);
+    else
+        cudaFree(p);
+}
+
+int pdmts_ctx::begin()
+{
+    PDMTS_CUDA_TRY(cudaSetDevice(device));
+    PDMTS_CUDA_TRY(cudaEventRecord(ev_in, user_stream));
+    PDMTS_CUDA_TRY(cudaStreamWaitEvent(stream, ev_in, 0));
+    return PDMTS_OK;
+}
+
+int pdmts_ctx::end()
+{
+    PDMTS_CUDA_TRY(cudaGetLastError());
+    PDMTS_CUDA_TRY(cudaEventRecord(ev_out, stream));
+    PDMTS_CUDA_TRY(cudaStreamWaitEvent(user_stream, ev_out, 0));
+    return PDMTS_OK;
+}
+
+int pdmts_ctx::time_begin(cudaEvent_t *start)
+{
+    *start = nullptr;
+    if (!timing)
+        return PDMTS_OK;
+    if (ev_pool.size() < 2) {
+        for (int k = 0; k < 64; ++k) {
+            cudaEvent_t e;
+            PDMTS_CUDA_TRY(cudaEventCreate(&e));
+            ev_pool.push_back(e);
+        }
+    }
+    *start = ev_pool.back();
+    ev_pool.pop_back();
+    PDMTS_CUDA_TRY(cudaEventRecord(*start, stream));
+    return PDMTS_OK;
+}
+
+int pdmts_ctx::time_end(cudaEvent_t start, int64_t substeps)
+{
+    if (!start)
+        return PDMTS_OK;
+    cudaEvent_t stop = ev_pool.back();
+    ev_pool.pop_back();
+    PDMTS_CUDA_TRY(cudaEventRecord(stop, stream));
+    ev_marks.push_back({start, stop});
+    ev_counts.push_back(substeps);
+    return PDMTS_OK;
+}
+
+extern "C" int pdmts_set_timing(pdmts_ctx *ctx, int enabled)
+{
+    clear_error();
+    if (!ctx)
+        return fail(PDMTS_ERR_ARG, "pdmts_set_timing: ctx is NULL");
+    ctx->timing = enabled != 0;
+    return PDMTS_OK;
+}
+
+extern "C" int pdmts_get_timing(pdmts_ctx *ctx, double *substep_ms, int64_t *substeps)
+{
+    clear_error();
+    if (!ctx || !substep_ms || !substeps)
+        return fail(PDMTS_ERR_ARG, "pdmts_get_timing: NULL argument");
+    PDMTS_CUDA_TRY(cudaSetDevice(ctx->device));
+    PDMTS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    double ms = 0.0;
+    int64_t cnt = 0;
+    for (size_t k = 0; k < ctx->ev_marks.size(); ++k) {
+        float t = 0.f;
+        PDMTS_CUDA_TRY(cudaEventElapsedTime(&t, ctx->ev_marks[k].first, ctx->ev_marks[k].second));
+        ms += t;
+        cnt += ctx->ev_counts[k];
+        ctx->ev_pool.push_back(ctx->ev_marks[k].first);
+        ctx->ev_pool.push_back(ctx->ev_marks[k].second);
+    }
+    ctx->ev_marks.clear();
+    ctx->ev_counts.clear();
+    *substep_ms = ms;
+    *substeps = cnt;
+    return PDMTS_OK;
+}
+
+extern "C" const char *pdmts_last_error(void) { return g_err.c_str(); }
+
+extern "C" int pdmts_ctx_create(pdmts_ctx **ctx, int device, void *cuda_stream)
+{
+    clear_error();
+    if (!ctx)
+        return fail(PDMTS_ERR_ARG, "pdmts_ctx_create: ctx is NULL");
+    *ctx = nullptr;
+    int ndev = 0;
+    PDMTS_CUDA_TRY(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev)
+        return fail(PDMTS_ERR_ARG, "pdmts_ctx_create: device %d out of range (%d devices)", device, ndev);
+    PDMTS_CUDA_TRY(cudaSetDevice(device));
+    auto *c = new (std::nothrow) pdmts_ctx();
+    if (!c)
+        return fail(PDMTS_ERR_NOMEM, "pdmts_ctx_create: out of host memory");
+    c->device = device;
+    c->user_stream = (cudaStream_t)cuda_stream;
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming) != cudaSuccess ||
+        cudaMalloc(&c->d_counter, 64) != cudaSuccess) {
+        cudaGetLastError();
+        pdmts_ctx_destroy(c);
+        return fail(PDMTS_ERR_CUDA, "pdmts_ctx_create: stream/event/counter creation failed");
+    }
+    if (cudaMemset(c->d_counter, 0, 64) != cudaSuccess) {
+        pdmts_ctx_destroy(c);
+        return fail(PDMTS_ERR_CUDA, "pdmts_ctx_create: memset failed");
+    }
+    *ctx = c;
+    return PDMTS_OK;
+}
+
+extern "C" int mts_destroy_coupling(pdmts_ctx *ctx);  // mts.cu
+
+extern "C" int pdmts_ctx_destroy(pdmts_ctx *ctx)
+{
+    clear_error();
+    if (!ctx)
+        return PDMTS_OK;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream)
+        cudaStreamSynchronize(ctx->stream);
+    mts_destroy_coupling(ctx);
+    if (ctx->pd)
+        pd_destroy(ctx->pd);
+    if (ctx->d_counter)
+        cudaFree(ctx->d_counter);
+    for (auto &m : ctx->ev_marks) {
+        ctx->ev_pool.push_back(m.first);
+        ctx->ev_pool.push_back(m.second);
+    }
+    for (cudaEvent_t e : ctx->ev_pool)
+        cudaEventDestroy(e);
+    if (ctx->ev_in)
+        cudaEventDestroy(ctx->ev_in);
+    if (ctx->ev_out)
+        cudaEventDestroy(ctx->ev_out);
+    if (ctx->stream)
+        cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return PDMTS_OK;
+}
+
+extern "C" int pdmts_set_allocator(pdmts_ctx *ctx, pdmts_alloc_fn alloc, pdmts_free_fn free_fn, void *user)
+{
+    clear_error();
+    if (!ctx)
+        return fail(PDMTS_ERR_ARG, "pdmts_set_allocator: ctx is NULL");
+    if ((alloc == nullptr) != (free_fn == nullptr))
+        return fail(PDMTS_ERR_ARG, "pdmts_set_allocator: give both alloc and free, or neither");
+    if (ctx->pd || ctx->fem)
+        return fail(PDMTS_ERR_STATE, "pdmts_set_allocator: subdomains already created");
+    ctx->alloc = alloc;
+    ctx->free_fn = free_fn;
+    ctx->alloc_user = user;
+    return PDMTS_OK;
+}
+
+extern "C" int pdmts_ctx_synchronize(pdmts_ctx *ctx)
+{
+    clear_error();
+    if (!ctx)
+        return fail(PDMTS_ERR_ARG, "pdmts_ctx_synchronize: ctx is NULL");
+    PDMTS_CUDA_TRY(cudaSetDevice(ctx->device));
+    PDMTS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    return PDMTS_OK;
+}
+
+extern "C" int pdmts_get_stats(pdmts_ctx *ctx, pdmts_stats *stats)
+{
+    clear_error();
+    if (!ctx || !stats)
+        return fail(PDMTS_ERR_ARG, "pdmts_get_stats: NULL argument");
+    PDMTS_CUDA_TRY(cudaSetDevice(ctx->device));
+    PDMTS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    unsigned long long broken = 0;
+    PDMTS_CUDA_TRY(cudaMemcpy(&broken, ctx->d_counter, sizeof(broken), cudaMemcpyDeviceToHost));
+    ctx->stats.bonds_broken = (int64_t)broken;
+    *stats = ctx->stats;
+    return PDMTS_OK;
+}
+
+// ------------------------------------------------------- PD handle helpers -
+template <typename T>
+int pdmts_pd::alloc(DevArr<T> &a, int64_t count)
+{
+    release(a);
+    a.p = (T *)ctx->dalloc(sizeof(T) * (size_t)std::max<int64_t>(count, 1));
+    if (!a.p)
+        return fail(PDMTS_ERR_NOMEM, "device allocation of %lld bytes failed",
+                    (long long)(sizeof(T) * count));
+    a.count = count;
+    device_bytes += (int64_t)(sizeof(T) * std::max<int64_t>(count, 1));
+    return PDMTS_OK;
+}
+
+template <typename T>
+void pdmts_pd::release(DevArr<T> &a)
+{
+    if (a.p) {
+        ctx->dfree(a.p);
+        device_bytes -= (int64_t)(sizeof(T) * std::max<int64_t>(a.count, 1));
+    }
+    a.p = nullptr;
+    a.count = 0;
+}
+
+extern int pd_invalidate_graphs(pdmts_pd *pd);  // pd_kernels.cu
+
+void pdmts_pd::release_all()
+{
+    pd_invalidate_graphs(this);
+    release(d_tile_ptr); release(d_mask_ptr); release(d_tile_k); release(d_col); release(d_deg);
+    release(d_mask); release(d_V); release(d_out); release(d_b);
+    release(d_X); release(d_cb); release(d_alpha); release(d_mass); release(d_wb); release(d_g);
+    release(d_v); release(d_a); release(d_u[0]); release(d_u[1]);
+    release(d_stencil); release(f_alpha); release(f_invm); release(f_wb); release(f_g);
+    release(f_v4); release(f_v2); release(f_a);
+    release(f_u4[0]); release(f_u4[1]); release(f_u2[0]); release(f_u2[1]);
+}
+
+template <typename T>
+static int upload(DevArr<T> &a, const T *src, int64_t count, cudaStream_t s)
+{
+    if (count == 0)
+        return PDMTS_OK;
+    PDMTS_CUDA_TRY(cudaMemcpyAsync(a.p, src, sizeof(T) * (size_t)count, cudaMemcpyHostToDevice, s));
+    return PDMTS_OK;
+}
+
+// Family H_delta of every node (Sec. 2.1): all j != i with |x_j - x_i|^2 <=
+// delta^2 (closed ball), rows ascending. Nodes are bucketed by a counting
+// sort over a grid of cell size delta; each node scans the 3^dim cells
+// around its own.
+static int build_family(pdmts_pd *pd)
+{
+    const int dim = pd->dim;
+    const int64_t n = pd->n;
+    const double delta = pd->horizon;
+    double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    int64_t nc[3] = {1, 1, 1};
+    for (int d = 0; d < dim; ++d) {
+        const double *x = &pd->X[(size_t)d * n];
+        lo[d] = *std::min_element(x, x + n);
+        hi[d] = *std::max_element(x, x + n);
+        nc[d] = (int64_t)std::floor((hi[d] - lo[d]) / delta) + 1;
+    }
+    const int64_t ncell = nc[0] * nc[1] * nc[2];
+    if (ncell > (int64_t)4 * n + 1024)  // very sparse clouds: coarsen is not needed for lattices
+        return fail(PDMTS_ERR_UNSUPPORTED, "pd_create: node cloud too sparse for the cell grid");
+    std::vector<int64_t> cell_of((size_t)n), start((size_t)ncell + 1, 0), order((size_t)n);
+    std::vector<std::array<int64_t, 3>> cidx((size_t)n);
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t id = 0;
+        for (int d = 2; d >= 0; --d) {
+            int64_t k = 0;
+            if (d < dim) {
+                k = (int64_t)std::floor((pd->X[(size_t)d * n + i] - lo[d]) / delta);
+                k = std::min(std::max<int64_t>(k, 0), nc[d] - 1);
+            }
+            cidx[(size_t)i][(size_t)d] = k;
+            id = id * nc[d] + k;
+        }
+        cell_of[(size_t)i] = id;
+        start[(size_t)id + 1]++;
+    }
+    for (int64_t c = 0; c < ncell; ++c)
+        start[(size_t)c + 1] += start[(size_t)c];
+    {
+        std::vector<int64_t> fill(start.begin(), start.end() - 1);
+        for (int64_t i = 0; i < n; ++i)
+            order[(size_t)fill[(size_t)cell_of[(size_t)i]]++] = i;
+    }
+    const double d2max = delta * delta;
+    pd->row_ptr.assign((size_t)n + 1, 0);
+    pd->col.clear();
+    pd->col.reserve((size_t)n * (dim == 2 ? 29 : 123));
+    std::vector<int32_t> row;
+    for (int64_t i = 0; i < n; ++i) {
+        row.clear();
+        const auto &ci = cidx[(size_t)i];
+        int64_t r0 = dim > 0 ? 1 : 0, r1 = dim > 1 ? 1 : 0, r2 = dim > 2 ? 1 : 0;
+        for (int64_t o2 = -r2; o2 <= r2; ++o2)
+            for (int64_t o1 = -r1; o1 <= r1; ++o1)
+                for (int64_t o0 = -r0; o0 <= r0; ++o0) {
+                    int64_t k0 = ci[0] + o0, k1 = ci[1] + o1, k2 = ci[2] + o2;
+                    if (k0 < 0 || k0 >= nc[0] || k1 < 0 || k1 >= nc[1] || k2 < 0 || k2 >= nc[2])
+                        continue;
+                    int64_t id = (k2 * nc[1] + k1) * nc[0] + k0;
+                    for (int64_t q = start[(size_t)id]; q < start[(size_t)id + 1]; ++q) {
+                        int64_t j = order[(size_t)q];
+                        if (j == i)
+                            continue;
+                        double r2s = 0.0;
+                        for (int d = 0; d < dim; ++d) {
+                            double e = pd->X[(size_t)d * n + j] - pd->X[(size_t)d * n + i];
+                            r2s += e * e;
+                        }
+                        if (r2s <= d2max)
+                            row.push_back((int32_t)j);
+                    }
+                }
+        std::sort(row.begin(), row.end());
+        pd->col.insert(pd->col.end(), row.begin(), row.end());
+        pd->row_ptr[(size_t)i + 1] = (int64_t)pd->col.size();
+    }
+    return PDMTS_OK;
+}
+
+// Detect x = x0 + k h with integer k (|k| < 32768) for all nodes.
+static void detect_lattice(pdmts_pd *pd)
+{
+    pd->on_lattice = false;
+    const int dim = pd->dim;
+    const int64_t n = pd->n;
+    double hmin2 = INFINITY;
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t k = pd->row_ptr[(size_t)i]; k < pd->row_ptr[(size_t)i + 1]; ++k) {
+            int64_t j = pd->col[(size_t)k];
+            double r2 = 0;
+            for (int d = 0; d < dim; ++d) {
+                double e = pd->X[(size_t)d * n + j] - pd->X[(size_t)d * n + i];
+                r2 += e * e;
+            }
+            hmin2 = std::min(hmin2, r2);
+        }
+    if (!std::isfinite(hmin2) || hmin2 <= 0)
+        return;
+    const double h = std::sqrt(hmin2);
+    std::vector<int32_t> lk((size_t)dim * n);
+    for (int d = 0; d < dim; ++d) {
+        const double *x = &pd->X[(size_t)d * n];
+        double x0 = *std::min_element(x, x + n);
+        for (int64_t i = 0; i < n; ++i) {
+            double q = (x[i] - x0) / h;
+            double k = std::nearbyint(q);
+            if (std::fabs(q - k) > 1e-6 || k > 32767.0)
+                return;
+            lk[(size_t)d * n + i] = (int32_t)k;
+        }
+        pd->x0[(size_t)d] = x0;
+    }
+    pd->h = h;
+    pd->lk.swap(lk);
+    pd->on_lattice = true;
+}
+
+static void build_sell(pdmts_pd *pd)
+{
+    const int64_t n = pd->n;
+    pd->ntiles = (n + 31) / 32;
+    pd->tile_ptr.assign((size_t)pd->ntiles + 1, 0);
+    pd->mask_ptr.assign((size_t)pd->ntiles + 1, 0);
+    pd->tile_k.assign((size_t)pd->ntiles, 0);
+    pd->deg.assign((size_t)n, 0);
+    pd->max_deg = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        int32_t dg = (int32_t)(pd->row_ptr[(size_t)i + 1] - pd->row_ptr[(size_t)i]);
+        pd->deg[(size_t)i] = dg;
+        pd->max_deg = std::max(pd->max_deg, dg);
+        int64_t t = i / 32;
+        pd->tile_k[(size_t)t] = std::max(pd->tile_k[(size_t)t], dg);
+    }
+    for (int64_t t = 0; t < pd->ntiles; ++t) {
+        int64_t K = pd->tile_k[(size_t)t];
+        pd->tile_ptr[(size_t)t + 1] = pd->tile_ptr[(size_t)t] + 32 * K;
+        pd->mask_ptr[(size_t)t + 1] = pd->mask_ptr[(size_t)t] + 32 * ((K + 31) / 32);
+    }
+    pd->n_slots = pd->tile_ptr[(size_t)pd->ntiles];
+    pd->n_mask_words = pd->mask_ptr[(size_t)pd->ntiles];
+    // all existing bonds intact, padding slots 0
+    pd->mask_host.assign((size_t)std::max<int64_t>(pd->n_mask_words, 1), 0u);
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t t = i / 32, lane = i % 32;
+        for (int32_t k = 0; k < pd->deg[(size_t)i]; ++k)
+            pd->mask_host[(size_t)(pd->mask_ptr[(size_t)t] + 32 * (k / 32) + lane)] |= 1u << (k % 32);
+    }
+}
+
+static double micromodulus_host(const pdmts_pd *pd, double xi2)
+{
+    double r = std::sqrt(xi2);
+    if (pd->micro_kind == PDMTS_MICRO_EXP)
+        return pd->c * std::exp(-r / pd->l);
+    return pd->c / (xi2 * r);
+}
+
+// Device arrays of the family and the state.
+static int upload_family_and_state(pdmts_pd *pd)
+{
+    cudaStream_t s = pd->ctx->stream;
+    const int dim = pd->dim;
+    const int64_t n = pd->n;
+    PDMTS_TRY(pd->alloc(pd->d_tile_ptr, pd->ntiles + 1));
+    PDMTS_TRY(pd->alloc(pd->d_mask_ptr, pd->ntiles + 1));
+    PDMTS_TRY(pd->alloc(pd->d_tile_k, pd->ntiles));
+    PDMTS_TRY(pd->alloc(pd->d_col, pd->n_slots));
+    PDMTS_TRY(pd->alloc(pd->d_deg, n));
+    PDMTS_TRY(pd->alloc(pd->d_mask, std::max<int64_t>(pd->n_mask_words, 1)));
+    PDMTS_TRY(pd->alloc(pd->d_V, n));
+    PDMTS_TRY(pd->alloc(pd->d_out, (int64_t)dim * n));
+    PDMTS_TRY(upload(pd->d_tile_ptr, pd->tile_ptr.data(), pd->ntiles + 1, s));
+    PDMTS_TRY(upload(pd->d_mask_ptr, pd->mask_ptr.data(), pd->ntiles + 1, s));
+    PDMTS_TRY(upload(pd->d_tile_k, pd->tile_k.data(), pd->ntiles, s));
+    PDMTS_TRY(upload(pd->d_deg, pd->deg.data(), n, s));
+    PDMTS_TRY(upload(pd->d_mask, pd->mask_host.data(), std::max<int64_t>(pd->n_mask_words, 1), s));
+    PDMTS_TRY(upload(pd->d_V, pd->V.data(), n, s));
+
+    std::vector<int32_t> colS((size_t)std::max<int64_t>(pd->n_slots, 1), 0);
+    if (pd->precision == PDMTS_FP64) {
+        std::vector<double> cb((size_t)std::max<int64_t>(pd->n_slots, 1), 0.0);
+        for (int64_t i = 0; i < n; ++i) {
+            int64_t t = i / 32, lane = i % 32;
+            for (int32_t k = 0; k < pd->tile_k[(size_t)t]; ++k) {
+                int64_t slot = pd->tile_ptr[(size_t)t] + 32 * (int64_t)k + lane;
+                if (k < pd->deg[(size_t)i]) {
+                    int64_t j = pd->col[(size_t)(pd->row_ptr[(size_t)i] + k)];
+                    colS[(size_t)slot] = (int32_t)j;
+                    double xi2 = 0.0;
+                    for (int d = 0; d < dim; ++d) {
+                        double e = pd->X[(size_t)d * n + j] - pd->X[(size_t)d * n + i];
+                        xi2 += e * e;
+                    }
+                    cb[(size_t)slot] = micromodulus_host(pd, xi2);
+                } else {
+                    colS[(size_t)slot] = (int32_t)i;  // padding: self, bit 0
+                }
+            }
+        }
+        // padding of the last tile's missing lanes
+        for (int64_t i = n; i < pd->ntiles * 32; ++i) {
+            int64_t t = i / 32, lane = i % 32;
+            for (int32_t k = 0; k < pd->tile_k[(size_t)t]; ++k)
+                colS[(size_t)(pd->tile_ptr[(size_t)t] + 32 * (int64_t)k + lane)] = 0;
+        }
+        PDMTS_TRY(pd->alloc(pd->d_cb, pd->n_slots));
+        PDMTS_TRY(upload(pd->d_cb, cb.data(), pd->n_slots, s));
+        PDMTS_TRY(upload(pd->d_col, colS.data(), pd->n_slots, s));
+        PDMTS_TRY(pd->alloc(pd->d_X, (int64_t)dim * n));
+        PDMTS_TRY(upload(pd->d_X, pd->X.data(), (int64_t)dim * n, s));
+        for (int b = 0; b < 2; ++b)
+            PDMTS_TRY(pd->alloc(pd->d_u[b], (int64_t)dim * n));
+        PDMTS_TRY(pd->alloc(pd->d_v, (int64_t)dim * n));
+        PDMTS_TRY(pd->alloc(pd->d_a, (int64_t)dim * n));
+        PDMTS_CUDA_TRY(cudaMemsetAsync(pd->d_u[0].p, 0, sizeof(double) * dim * n, s));
+        PDMTS_CUDA_TRY(cudaMemsetAsync(pd->d_u[1].p, 0, sizeof(double) * dim * n, s));
+        PDMTS_CUDA_TRY(cudaMemsetAsync(pd->d_v.p, 0, sizeof(double) * dim * n, s));
+        PDMTS_CUDA_TRY(cudaMemsetAsync(pd->d_a.p, 0, sizeof(double) * dim * n, s));
+    } else {
+        // stencil table over the distinct lattice offsets
+        std::map<std::array<int32_t, 3>, int> ids;
+        std::vector<StencilEntry> table;
+        const double h = pd->h;
+        const double V = pd->V[0];
+        for (int64_t i = 0; i < n; ++i) {
+            int64_t t = i / 32, lane = i % 32;
+            for (int32_t k = 0; k < pd->tile_k[(size_t)t]; ++k) {
+                int64_t slot = pd->tile_ptr[(size_t)t] + 32 * (int64_t)k + lane;
+                if (k >= pd->deg[(size_t)i]) {
+                    colS[(size_t)slot] = (int32_t)((uint32_t)i << 8);
+                    continue;
+                }
+                int64_t j = pd->col[(size_t)(pd->row_ptr[(size_t)i] + k)];
+                std::array<int32_t, 3> off{0, 0, 0};
+                for (int d = 0; d < dim; ++d)
+                    off[(size_t)d] = pd->lk[(size_t)d * n + j] - pd->lk[(size_t)d * n + i];
+                auto it = ids.find(off);
+                int id;
+                if (it == ids.end()) {
+                    id = (int)table.size();
+                    if (id >= kMaxStencil)
+                        return fail(PDMTS_ERR_UNSUPPORTED, "pd_create: more than %d lattice offsets", kMaxStencil);
+                    ids[off] = id;
+                    double r2 = 0.0;
+                    for (int d = 0; d < dim; ++d)
+                        r2 += (double)off[(size_t)d] * off[(size_t)d];
+                    StencilEntry e{};
+                    for (int d = 0; d < 3; ++d)
+                        e.d[d] = (float)off[(size_t)d];
+                    double xi2 = r2 * h * h;
+                    e.coef = (float)(micromodulus_host(pd, xi2) * h * h * V);
+                    e.thr = (float)(pd->s0 * (2.0 + pd->s0) * r2);
+                    e.rd = (float)std::sqrt(r2);
+                    table.push_back(e);
+                } else {
+                    id = it->second;
+                }
+                colS[(size_t)slot] = (int32_t)(((uint32_t)j << 8) | (uint32_t)id);
+            }
+        }
+        for (int64_t i = n; i < pd->ntiles * 32; ++i) {
+            int64_t t = i / 32, lane = i % 32;
+            for (int32_t k = 0; k < pd->tile_k[(size_t)t]; ++k)
+                colS[(size_t)(pd->tile_ptr[(size_t)t] + 32 * (int64_t)k + lane)] = 0;
+        }
+        pd->n_stencil = (int)table.size();
+        PDMTS_TRY(pd->alloc(pd->d_stencil, std::max<int64_t>(pd->n_stencil, 1)));
+        PDMTS_TRY(upload(pd->d_stencil, table.data(), pd->n_stencil, s));
+        PDMTS_TRY(upload(pd->d_col, colS.data(), pd->n_slots, s));
+        const int adim = dim == 2 ? 2 : 4;
+        for (int b = 0; b < 2; ++b) {
+            PDMTS_TRY(pd->alloc(pd->f_u4[b], n));
+            PDMTS_CUDA_TRY(cudaMemsetAsync(pd->f_u4[b].p, 0, sizeof(float4) * n, s));
+            if (dim == 3) {
+                PDMTS_TRY(pd->alloc(pd->f_u2[b], n));
+                PDMTS_CUDA_TRY(cudaMemsetAsync(pd->f_u2[b].p, 0, sizeof(float2) * n, s));
+            }
+        }
+        PDMTS_TRY(pd->alloc(pd->f_v4, n));
+        PDMTS_CUDA_TRY(cudaMemsetAsync(pd->f_v4.p, 0, sizeof(float4) * n, s));
+        if (dim == 3) {
+            PDMTS_TRY(pd->alloc(pd->f_v2, n));
+            PDMTS_CUDA_TRY(cudaMemsetAsync(pd->f_v2.p, 0, sizeof(float2) * n, s));
+        }
+        PDMTS_TRY(pd->alloc(pd->f_a, (int64_t)adim * n));
+        PDMTS_CUDA_TRY(cudaMemsetAsync(pd->f_a.p, 0, sizeof(float) * adim * n, s));
+    }
+    return PDMTS_OK;
+}
+
+// (Re)build the per-node weight and load arrays: mass (1 - alpha) rho,
+// (1 - alpha) b, and the interface force density g (Eq. 33-34).
+int pdmts_pd::upload_weights_and_loads()
+{
+    pd_invalidate_graphs(this);
+    cudaStream_t s = ctx->stream;
+    const bool has_alpha = !alpha.empty();
+    for (int64_t i = 0; i < n; ++i) {
+        double ai = has_alpha ? alpha[(size_t)i] : 0.0;
+        if (!((1.0 - ai) * rho > 0.0))
+            return fail(PDMTS_ERR_MASS, "PD node %lld has non-positive weighted mass (alpha = %g)",
+                        (long long)i, ai);
+    }
+    if (precision == PDMTS_FP64) {
+        std::vector<double> mass((size_t)n);
+        for (int64_t i = 0; i < n; ++i)
+            mass[(size_t)i] = (1.0 - (has_alpha ? alpha[(size_t)i] : 0.0)) * rho;
+        PDMTS_TRY(alloc(d_mass, n));
+        PDMTS_TRY(upload(d_mass, mass.data(), n, s));
+        if (has_alpha) {
+            PDMTS_TRY(alloc(d_alpha, n));
+            PDMTS_TRY(upload(d_alpha, alpha.data(), n, s));
+        } else {
+            release(d_alpha);
+        }
+        if (has_b) {
+            if (!d_wb.p)
+                PDMTS_TRY(alloc(d_wb, (int64_t)dim * n));
+            cudaError_t e = launch_weighted_load(dim, n, d_b.p, d_alpha.p, nullptr, 0.0, d_wb.p, nullptr,
+                                                 nullptr, s);
+            if (e != cudaSuccess)
+                return fail(PDMTS_ERR_CUDA, "weighted load kernel: %s", cudaGetErrorString(e));
+        } else {
+            release(d_wb);
+        }
+    } else {
+        std::vector<float> invm((size_t)n);
+        for (int64_t i = 0; i < n; ++i)
+            invm[(size_t)i] = (float)(1.0 / ((1.0 - (has_alpha ? alpha[(size_t)i] : 0.0)) * rho));
+        PDMTS_TRY(alloc(f_invm, n));
+        PDMTS_TRY(upload(f_invm, invm.data(), n, s));
+        if (has_alpha) {
+            std::vector<float> af(alpha.begin(), alpha.end());
+            PDMTS_TRY(alloc(f_alpha, n));
+            PDMTS_TRY(upload(f_alpha, af.data(), n, s));
+        } else {
+            release(f_alpha);
+        }
+        if (has_b) {
+            if (!f_wb.p)
+                PDMTS_TRY(alloc(f_wb, (int64_t)dim * n));
+            cudaError_t e = launch_weighted_load(dim, n, d_b.p, nullptr, f_alpha.p, 1.0 / h, nullptr, f_wb.p,
+                                                 nullptr, s);
+            if (e != cudaSuccess)
+                return fail(PDMTS_ERR_CUDA, "weighted load kernel: %s", cudaGetErrorString(e));
+        } else {
+            release(f_wb);
+        }
+    }
+    PDMTS_CUDA_TRY(cudaStreamSynchronize(s));  // host vectors above are temporaries
+    return PDMTS_OK;
+}
+
+// One substep on the current state: forces at u[cur] (with breaking), a, v,
+// and the predicted displacement into u[1 - cur]; then the buffers swap.
+// With init, a is computed from u[cur] and u[1 - cur] = u + dt v + dt^2/2 a,
+// and the buffers do not swap (u[cur] stays the current displacement).
+int pdmts_pd::step(bool init, double theta, cudaStream_t s)
+{
+    const double dt = ctx->dt_pd;
+    cudaError_t e;
+    SellView fam{d_tile_ptr.p, d_tile_k.p, d_mask_ptr.p, d_col.p, d_mask.p, d_deg.p, n, ntiles};
+    if (precision == PDMTS_FP64) {
+        F64StepArgs A{};
+        A.fam = fam;
+        A.X = d_X.p;
+        A.V = d_V.p;
+        A.cb = d_cb.p;
+        A.alpha = d_alpha.p;
+        A.mass = d_mass.p;
+        A.wb = d_wb.p;
+        A.g = d_g.p;
+        A.u_in = d_u[cur].p;
+        A.u_out = d_u[1 - cur].p;
+        A.v = d_v.p;
+        A.a = d_a.p;
+        A.s0p2 = (1.0 + s0) * (1.0 + s0);
+        A.dt = dt;
+        A.hdt = 0.5 * dt;
+        A.hdt2 = 0.5 * dt * dt;
+        A.theta = theta;
+        A.breaking = breaking ? 1 : 0;
+        A.pmb = force_kind == PDMTS_FORCE_PMB;
+        A.broken = ctx->d_counter;
+        e = launch_pd_step_f64(dim, A, init, s);
+    } else {
+        F32StepArgs A{};
+        A.fam = fam;
+        A.stencil = d_stencil.p;
+        A.n_stencil = n_stencil;
+        A.alpha = f_alpha.p;
+        A.inv_m = f_invm.p;
+        A.wb = f_wb.p;
+        A.g = f_g.p;
+        A.u4_in = f_u4[cur].p;
+        A.u2_in = f_u2[cur].p;
+        A.u4_out = f_u4[1 - cur].p;
+        A.u2_out = f_u2[1 - cur].p;
+        A.v4 = f_v4.p;
+        A.v2 = f_v2.p;
+        A.a = f_a.p;
+        A.dt = (float)dt;
+        A.hdt = (float)(0.5 * dt);
+        A.hdt2 = (float)(0.5 * dt * dt);
+        A.theta = (float)theta;
+        A.s0 = (float)s0;
+        A.breaking = breaking ? 1 : 0;
+        A.pmb = force_kind == PDMTS_FORCE_PMB;
+        A.broken = ctx->d_counter;
+        e = launch_pd_step_f32(dim, A, init, s);
+    }
+    if (e != cudaSuccess)
+        return fail(PDMTS_ERR_CUDA, "PD substep launch failed: %s", cudaGetErrorString(e));
+    ctx->stats.kernel_launches++;
+    if (!init) {
+        cur = 1 - cur;
+        steps_done++;
+        ctx->stats.pd_substeps++;
+        ctx->stats.bond_updates += (int64_t)row_ptr[(size_t)n];
+    }
+    return PDMTS_OK;
+}
+
+int pdmts_pd::ensure_init(cudaStream_t s)
+{
+    if (!need_init)
+        return PDMTS_OK;
+    PDMTS_TRY(step(true, 0.0, s));
+    need_init = false;
+    return PDMTS_OK;
+}
+
+// ------------------------------------------------------------ PD ABI ------
+extern "C" int pd_create(pdmts_ctx *ctx, int dim, int64_t n, const double *X, const double *vol,
+                         double vol_uniform, double horizon, int micro_kind, double c, double l,
+                         double s0, double rho, int precision, pdmts_pd **out)
+{
+    clear_error();
+    if (!ctx || !X || !out)
+        return fail(PDMTS_ERR_ARG, "pd_create: NULL argument");
+    *out = nullptr;
+    if (ctx->pd)
+        return fail(PDMTS_ERR_STATE, "pd_create: context already has a PD subdomain");
+    if (dim != 2 && dim != 3)
+        return fail(PDMTS_ERR_ARG, "pd_create: dim must be 2 or 3 (got %d)", dim);
+    if (n <= 0 || n >= ((int64_t)1 << 31))
+        return fail(PDMTS_ERR_ARG, "pd_create: n out of range (%lld)", (long long)n);
+    if (!(horizon > 0) || !std::isfinite(horizon))
+        return fail(PDMTS_ERR_ARG, "pd_create: horizon must be > 0");
+    if (!(s0 > 0) || !std::isfinite(s0))
+        return fail(PDMTS_ERR_ARG, "pd_create: s0 must be > 0");
+    if (!(rho > 0) || !std::isfinite(rho))
+        return fail(PDMTS_ERR_ARG, "pd_create: rho must be > 0");
+    if (!(c > 0) || !std::isfinite(c))
+        return fail(PDMTS_ERR_ARG, "pd_create: micromodulus constant must be > 0");
+    if (micro_kind != PDMTS_MICRO_POWER && micro_kind != PDMTS_MICRO_EXP)
+        return fail(PDMTS_ERR_ARG, "pd_create: unknown micromodulus kind %d", micro_kind);
+    if (micro_kind == PDMTS_MICRO_EXP && !(l > 0))
+        return fail(PDMTS_ERR_ARG, "pd_create: exponential micromodulus needs l > 0");
+    if (precision != PDMTS_FP64 && precision != PDMTS_FP32_BULK)
+        return fail(PDMTS_ERR_ARG, "pd_create: unknown precision %d", precision);
+    if (!vol && !(vol_uniform > 0))
+        return fail(PDMTS_ERR_ARG, "pd_create: vol_uniform must be > 0 when vol is NULL");
+    PDMTS_CUDA_TRY(cudaSetDevice(ctx->device));
+
+    auto *pd = new (std::nothrow) pdmts_pd();
+    if (!pd)
+        return fail(PDMTS_ERR_NOMEM, "pd_create: out of host memory");
+    pd->ctx = ctx;
+    pd->dim = dim;
+    pd->n = n;
+    pd->precision = precision;
+    pd->horizon = horizon;
+    pd->c = c;
+    pd->l = l;
+    pd->s0 = s0;
+    pd->rho = rho;
+    pd->micro_kind = micro_kind;
+    int r = fetch(pd->X, X, (int64_t)dim * n);
+    if (r == PDMTS_OK && !finite_all(pd->X.data(), (int64_t)dim * n))
+        r = fail(PDMTS_ERR_ARG, "pd_create: X contains NaN/Inf");
+    if (r == PDMTS_OK) {
+        if (vol) {
+            r = fetch(pd->V, vol, n);
+            pd->uniform_vol = false;
+            for (int64_t i = 0; r == PDMTS_OK && i < n; ++i)
+                if (!(pd->V[(size_t)i] > 0) || !std::isfinite(pd->V[(size_t)i]))
+                    r = fail(PDMTS_ERR_ARG, "pd_create: vol[%lld] must be finite and > 0", (long long)i);
+        } else {
+            pd->V.assign((size_t)n, vol_uniform);
+        }
+    }
+    if (r == PDMTS_OK)
+        r = build_family(pd);
+    if (r == PDMTS_OK) {
+        detect_lattice(pd);
+        if (precision == PDMTS_FP32_BULK) {
+            if (!pd->on_lattice)
+                r = fail(PDMTS_ERR_UNSUPPORTED, "pd_create: FP32_BULK needs nodes on a regular lattice");
+            else if (vol)
+                r = fail(PDMTS_ERR_UNSUPPORTED, "pd_create: FP32_BULK needs a uniform nodal volume");
+            else if (n >= ((int64_t)1 << 24))
+                r = fail(PDMTS_ERR_UNSUPPORTED, "pd_create: FP32_BULK supports n < 2^24 nodes");
+        }
+    }
+    if (r == PDMTS_OK) {
+        build_sell(pd);
+        r = upload_family_and_state(pd);
+    }
+    if (r == PDMTS_OK)
+        r = pd->upload_weights_and_loads();
+    if (r == PDMTS_OK) {
+        cudaError_t e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess)
+            r = fail(PDMTS_ERR_CUDA, "pd_create: %s", cudaGetErrorString(e));
+    }
+    if (r != PDMTS_OK) {
+        std::string msg = pdmts_last_error();
+        pd->release_all();
+        delete pd;
+        return fail(r, "%s", msg.c_str());
+    }
+    ctx->pd = pd;
+    *out = pd;
+    return PDMTS_OK;
+}
+
+extern "C" int pd_destroy(pdmts_pd *pd)
+{
+    clear_error();
+    if (!pd)
+        return PDMTS_OK;
+    cudaSetDevice(pd->ctx->device);
+    cudaStreamSynchronize(pd->ctx->stream);
+    if (pd->ctx->pd == pd)
+        pd->ctx->pd = nullptr;
+    pd->release_all();
+    delete pd;
+    return PDMTS_OK;
+}
+
+// Exact pre-crack test in half-spacing units (lattice) or FP64 (otherwise).
+extern "C" int pd_set_precrack(pdmts_pd *pd, int n_cuts, const double *cuts)
+{
+    clear_error();
+    if (!pd || (n_cuts > 0 && !cuts) || n_cuts < 0)
+        return fail(PDMTS_ERR_ARG, "pd_set_precrack: bad arguments");
+    std::vector<double> cv;
+    PDMTS_TRY(fetch(cv, cuts, (int64_t)5 * n_cuts));
+    const int dim = pd->dim;
+    const int64_t n = pd->n;
+    struct CutI {
+        int na, pa;
+        int64_t level, lo, hi;
+        double lv, lod, hid;
+        bool exact;
+    };
+    std::vector<CutI> cl;
+    for (int c = 0; c < n_cuts; ++c) {
+        const double *q = &cv[(size_t)5 * c];
+        CutI k{};
+        k.na = (int)q[0];
+        k.pa = (int)q[2];
+        if (k.na < 0 || k.na >= dim || k.pa < 0 || k.pa >= dim || k.na == k.pa || (double)k.na != q[0] ||
+            (double)k.pa != q[2] || !std::isfinite(q[1]) || !std::isfinite(q[3]) || !std::isfinite(q[4]))
+            return fail(PDMTS_ERR_ARG, "pd_set_precrack: cut %d is malformed", c);
+        k.lv = q[1];
+        k.lod = q[3];
+        k.hid = q[4];
+        k.exact = false;
+        if (pd->on_lattice) {
+            // half-spacing units relative to the lattice box corner x0 - h/2
+            auto hu = [&](double v, int ax, int64_t &outv) {
+                double t = (v - (pd->x0[(size_t)ax] - 0.5 * pd->h)) / (0.5 * pd->h);
+                double r = std::nearbyint(t);
+                if (std::fabs(t - r) > 1e-6 || std::fabs(r) > 4e9)
+                    return false;
+                outv = (int64_t)r;
+                return true;
+            };
+            k.exact = hu(q[1], k.na, k.level) && hu(q[3], k.pa, k.lo) && hu(q[4], k.pa, k.hi);
+        }
+        cl.push_back(k);
+    }
+    // current bond status from the device
+    PDMTS_CUDA_TRY(cudaSetDevice(pd->ctx->device));
+    PDMTS_TRY(pd->ctx->begin());
+    PDMTS_CUDA_TRY(cudaMemcpyAsync(pd->mask_host.data(), pd->d_mask.p, sizeof(uint32_t) * pd->n_mask_words,
+                                   cudaMemcpyDeviceToHost, pd->ctx->stream));
+    PDMTS_CUDA_TRY(cudaStreamSynchronize(pd->ctx->stream));
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t t = i / 32, lane = i % 32;
+        for (int32_t k = 0; k < pd->deg[(size_t)i]; ++k) {
+            int64_t j = pd->col[(size_t)(pd->row_ptr[(size_t)i] + k)];
+            bool cut = false;
+            for (const CutI &q : cl) {
+                if (q.exact) {
+                    int64_t ni = 2 * (int64_t)pd->lk[(size_t)q.na * n + i] + 1;
+                    int64_t nj = 2 * (int64_t)pd->lk[(size_t)q.na * n + j] + 1;
+                    int64_t ai = 2 * (int64_t)pd->lk[(size_t)q.pa * n + i] + 1;
+                    int64_t aj = 2 * (int64_t)pd->lk[(size_t)q.pa * n + j] + 1;
+                    if (!((ni < q.level && q.level < nj) || (nj < q.level && q.level < ni)))
+                        continue;
+                    // crossing point along pa: ai + (level - ni)(aj - ai)/(nj - ni) in [lo, hi)
+                    int64_t den = nj - ni;
+                    int64_t num = ai * den + (q.level - ni) * (aj - ai);
+                    if (den < 0) {
+                        den = -den;
+                        num = -num;
+                    }
+                    if (num >= q.lo * den && num < q.hi * den)
+                        cut = true;
+                } else {
+                    double ni = pd->X[(size_t)q.na * n + i], nj = pd->X[(size_t)q.na * n + j];
+                    if (!((ni < q.lv && q.lv < nj) || (nj < q.lv && q.lv < ni)))
+                        continue;
+                    double ai = pd->X[(size_t)q.pa * n + i], aj = pd->X[(size_t)q.pa * n + j];
+                    double xc = ai + (q.lv - ni) * (aj - ai) / (nj - ni);
+                    if (xc >= q.lod && xc < q.hid)
+                        cut = true;
+                }
+                if (cut)
+                    break;
+            }
+            if (cut)
+                pd->mask_host[(size_t)(pd->mask_ptr[(size_t)t] + 32 * (k / 32) + lane)] &= ~(1u << (k % 32));
+        }
+    }
+    PDMTS_CUDA_TRY(cudaMemcpyAsync(pd->d_mask.p, pd->mask_host.data(), sizeof(uint32_t) * pd->n_mask_words,
+                                   cudaMemcpyHostToDevice, pd->ctx->stream));
+    PDMTS_CUDA_TRY(cudaStreamSynchronize(pd->ctx->stream));
+    pd->need_init = true;
+    return pd->ctx->end();
+}
+
+extern "C" int pd_set_body_force(pdmts_pd *pd, const double *b)
+{
+    clear_error();
+    if (!pd)
+        return fail(PDMTS_ERR_ARG, "pd_set_body_force: pd is NULL");
+    PDMTS_CUDA_TRY(cudaSetDevice(pd->ctx->device));
+    PDMTS_TRY(pd->ctx->begin());
+    cudaStream_t s = pd->ctx->stream;
+    const int64_t m = (int64_t)pd->dim * pd->n;
+    if (!b) {
+        pd->has_b = false;
+        pd->release(pd->d_b);
+        PDMTS_TRY(pd->upload_weights_and_loads());
+        pd->need_init = true;
+        return pd->ctx->end();
+    }
+    // stage, validate on the device, then commit (the state is untouched on failure)
+    unsigned long long *flag = pd->ctx->d_counter + 1;
+    PDMTS_CUDA_TRY(cudaMemcpyAsync(pd->d_out.p, b, sizeof(double) * m, cudaMemcpyDefault, s));
+    PDMTS_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(unsigned long long), s));
+    cudaError_t e = launch_weighted_load(pd->dim, pd->n, pd->d_out.p, nullptr, nullptr, 0.0, nullptr, nullptr,
+                                         flag, s);
+    if (e != cudaSuccess)
+        return fail(PDMTS_ERR_CUDA, "body force check: %s", cudaGetErrorString(e));
+    unsigned long long bad = 0;
+    PDMTS_CUDA_TRY(cudaMemcpyAsync(&bad, flag, sizeof(bad), cudaMemcpyDeviceToHost, s));
+    PDMTS_CUDA_TRY(cudaStreamSynchronize(s));
+    if (bad)
+        return fail(PDMTS_ERR_ARG, "pd_set_body_force: NaN/Inf in b");
+    const bool fresh_arrays = !pd->has_b;
+    if (!pd->d_b.p)
+        PDMTS_TRY(pd->alloc(pd->d_b, m));
+    PDMTS_CUDA_TRY(cudaMemcpyAsync(pd->d_b.p, pd->d_out.p, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+    pd->has_b = true;
+    if (fresh_arrays) {
+        PDMTS_TRY(pd->upload_weights_and_loads());  // allocates the weighted-load arrays once
+    } else {
+        // same arrays, new values: captured substep graphs stay valid
+        e = pd->precision == PDMTS_FP64
+                ? launch_weighted_load(pd->dim, pd->n, pd->d_b.p, pd->d_alpha.p, nullptr, 0.0, pd->d_wb.p,
+                                       nullptr, nullptr, s)
+                : launch_weighted_load(pd->dim, pd->n, pd->d_b.p, nullptr, pd->f_alpha.p, 1.0 / pd->h, nullptr,
+                                       pd->f_wb.p, nullptr, s);
+        if (e != cudaSuccess)
+            return fail(PDMTS_ERR_CUDA, "weighted load kernel: %s", cudaGetErrorString(e));
+        pd->ctx->stats.kernel_launches++;
+    }
+    return pd->ctx->end();
+}
+
+extern "C" int pd_set_weights(pdmts_pd *pd, const double *alpha)
+{
+    clear_error();
+    if (!pd)
+        return fail(PDMTS_ERR_ARG, "pd_set_weights: pd is NULL");
+    std::vector<double> na;
+    if (alpha) {
+        PDMTS_TRY(fetch(na, alpha, pd->n));
+        for (int64_t i = 0; i < pd->n; ++i)
+            if (!std::isfinite(na[(size_t)i]) || na[(size_t)i] < 0.0)
+                return fail(PDMTS_ERR_ARG, "pd_set_weights: alpha[%lld] must be finite and >= 0", (long long)i);
+    }
+    PDMTS_CUDA_TRY(cudaSetDevice(pd->ctx->device));
+    PDMTS_TRY(pd->ctx->begin());
+    std::vector<double> old;
+    old.swap(pd->alpha);
+    pd->alpha.swap(na);
+    int r = pd->upload_weights_and_loads();
+    if (r != PDMTS_OK) {
+        std::string msg = pdmts_last_error();
+        pd->alpha.swap(old);
+        pd->upload_weights_and_loads();
+        return fail(r, "%s", msg.c_str());
+    }
+    pd->need_init = true;
+    return pd->ctx->end();
+}
+
+extern "C" int pd_set_state(pdmts_pd *pd, const double *u, const double *v)
+{
+    clear_error();
+    if (!pd)
+        return fail(PDMTS_ERR_ARG, "pd_set_state: pd is NULL");
+    const int64_t m = (int64_t)pd->dim * pd->n;
+    std::vector<double> hu, hv;
+    if (u) {
+        PDMTS_TRY(fetch(hu, u, m));
+        if (!finite_all(hu.data(), m))
+            return fail(PDMTS_ERR_ARG, "pd_set_state: NaN/Inf in u");
+    }
+    if (v) {
+        PDMTS_TRY(fetch(hv, v, m));
+        if (!finite_all(hv.data(), m))
+            return fail(PDMTS_ERR_ARG, "pd_set_state: NaN/Inf in v");
+    }
+    PDMTS_CUDA_TRY(cudaSetDevice(pd->ctx->device));
+    PDMTS_TRY(pd->ctx->begin());
+    cudaStream_t s = pd->ctx->stream;
+    if (pd->precision == PDMTS_FP64) {
+        if (u)
+            PDMTS_CUDA_TRY(cudaMemcpyAsync(pd->d_u[pd->cur].p, hu.data(), sizeof(double) * m, cudaMemcpyHostToDevice, s));
+        else
+            PDMTS_CUDA_TRY(cudaMemsetAsync(pd->d_u[pd->cur].p, 0, sizeof(double) * m, s));
+        if (v)
+            PDMTS_CUDA_TRY(cudaMemcpyAsync(pd->d_v.p, hv.data(), sizeof(double) * m, cudaMemcpyHostToDevice, s));
+        else
+            PDMTS_CUDA_TRY(cudaMemsetAsync(pd->d_v.p, 0, sizeof(double) * m, s));
+    } else {
+        // compensated pairs in lattice units, packed per node
+        const int dim = pd->dim;
+        const int64_t n = pd->n;
+        const double inv_h = 1.0 / pd->h;
+        std::vector<float4> p4((size_t)n);
+        std::vector<float2> p2((size_t)n);
+        auto pack = [&](const std::vector<double> &src, float4 *d4, float2 *d2) -> int {
+            float hv[3] = {0, 0, 0}, lv[3] = {0, 0, 0};
+            for (int64_t i = 0; i < n; ++i) {
+                for (int d = 0; d < dim; ++d) {
+                    double x = src.empty() ? 0.0 : src[(size_t)d * n + i] * inv_h;
+                    hv[d] = (float)x;
+                    lv[d] = (float)(x - (double)hv[d]);
+                }
+                if (dim == 2) {
+                    p4[(size_t)i] = make_float4(hv[0], hv[1], lv[0], lv[1]);
+                } else {
+                    p4[(size_t)i] = make_float4(hv[0], hv[1], hv[2], lv[0]);
+                    p2[(size_t)i] = make_float2(lv[1], lv[2]);
+                }
+            }
+            PDMTS_CUDA_TRY(cudaMemcpyAsync(d4, p4.data(), sizeof(float4) * n, cudaMemcpyHostToDevice, s));
+            if (dim == 3)
+                PDMTS_CUDA_TRY(cudaMemcpyAsync(d2, p2.data(), sizeof(float2) * n, cudaMemcpyHostToDevice, s));
+            PDMTS_CUDA_TRY(cudaStreamSynchronize(s));
+            return PDMTS_OK;
+        };
+        PDMTS_TRY(pack(hu, pd->f_u4[pd->cur].p, pd->f_u2[pd->cur].p));
+        PDMTS_TRY(pack(hv, pd->f_v4.p, pd->f_v2.p));
+    }
+    PDMTS_CUDA_TRY(cudaStreamSynchronize(s));
+    pd->need_init = true;
+    return pd->ctx->end();
+}
+
+extern "C" int pd_set_breaking(pdmts_pd *pd, int enabled)
+{
+    clear_error();
+    if (!pd)
+        return fail(PDMTS_ERR_ARG, "pd_set_breaking: pd is NULL");
+    pd->breaking = enabled != 0;
+    pd_invalidate_graphs(pd);
+    return PDMTS_OK;
+}
+
+extern "C" int pd_set_force_law(pdmts_pd *pd, int kind)
+{
+    clear_error();
+    if (!pd)
+        return fail(PDMTS_ERR_ARG, "pd_set_force_law: pd is NULL");
+    if (kind != PDMTS_FORCE_LINEAR && kind != PDMTS_FORCE_PMB)
+        return fail(PDMTS_ERR_ARG, "pd_set_force_law: unknown kind %d", kind);
+    pd->force_kind = kind;
+    pd->need_init = true;
+    pd_invalidate_graphs(pd);
+    return PDMTS_OK;
+}
+
+extern "C" int pd_info(const pdmts_pd *pd, pdmts_pd_info *info)
+{
+    clear_error();
+    if (!pd || !info)
+        return fail(PDMTS_ERR_ARG, "pd_info: NULL argument");
+    info->dim = pd->dim;
+    info->precision = pd->precision;
+    info->n = pd->n;
+    info->n_bonds = pd->row_ptr.empty() ? 0 : pd->row_ptr[(size_t)pd->n];
+    info->n_slots = pd->n_slots;
+    info->max_degree = pd->max_deg;
+    info->on_lattice = pd->on_lattice ? 1 : 0;
+    info->lattice_h = pd->on_lattice ? pd->h : 0.0;
+    info->steps_done = pd->steps_done;
+    info->device_bytes = pd->device_bytes;
+    return PDMTS_OK;
+}
+
+// Copy a dim * n field at the current time into `out` (host or device).
+static int read_field(pdmts_pd *pd, int which, double *out)
+{
+    if (!pd || !out)
+        return fail(PDMTS_ERR_ARG, "pd_read: NULL argument");
+    PDMTS_CUDA_TRY(cudaSetDevice(pd->ctx->device));
+    PDMTS_TRY(pd->ctx->begin());
+    cudaStream_t s = pd->ctx->stream;
+    const int64_t m = (int64_t)pd->dim * pd->n;
+    if (which == 2)
+        PDMTS_TRY(pd->ensure_init(s));
+    const double *src = nullptr;
+    if (pd->precision == PDMTS_FP64) {
+        src = which == 0 ? pd->d_u[pd->cur].p : which == 1 ? pd->d_v.p : pd->d_a.p;
+    } else {
+        const float4 *p4 = which == 0 ? pd->f_u4[pd->cur].p : which == 1 ? pd->f_v4.p : (const float4 *)pd->f_a.p;
+        const float2 *p2 = which == 0 ? pd->f_u2[pd->cur].p : which == 1 ? pd->f_v2.p : nullptr;
+        cudaError_t e = launch_unpack_f32(pd->dim, pd->n, p4, p2, which == 2, pd->h, pd->d_out.p, s);
+        if (e != cudaSuccess)
+            return fail(PDMTS_ERR_CUDA, "read-back conversion failed: %s", cudaGetErrorString(e));
+        src = pd->d_out.p;
+    }
+    PDMTS_CUDA_TRY(cudaMemcpyAsync(out, src, sizeof(double) * m, cudaMemcpyDefault, s));
+    PDMTS_CUDA_TRY(cudaStreamSynchronize(s));
+    return pd->ctx->end();
+}
+
+extern "C" int pd_read_displacement(pdmts_pd *pd, double *u)
+{
+    clear_error();
+    return read_field(pd, 0, u);
+}
+extern "C" int pd_read_velocity(pdmts_pd *pd, double *v)
+{
+    clear_error();
+    return read_field(pd, 1, v);
+}
+extern "C" int pd_read_acceleration(pdmts_pd *pd, double *a)
+{
+    clear_error();
+    return read_field(pd, 2, a);
+}
+
+extern "C" int pd_read_damage(pdmts_pd *pd, double *phi)
+{
+    clear_error();
+    if (!pd || !phi)
+        return fail(PDMTS_ERR_ARG, "pd_read_damage: NULL argument");
+    PDMTS_CUDA_TRY(cudaSetDevice(pd->ctx->device));
+    PDMTS_TRY(pd->ctx->begin());
+    cudaStream_t s = pd->ctx->stream;
+    SellView fam{pd->d_tile_ptr.p, pd->d_tile_k.p, pd->d_mask_ptr.p, pd->d_col.p, pd->d_mask.p, pd->d_deg.p,
+                 pd->n, pd->ntiles};
+    cudaError_t e = launch_damage(fam, pd->precision == PDMTS_FP32_BULK, pd->d_V.p, pd->d_out.p, s);
+    if (e != cudaSuccess)
+        return fail(PDMTS_ERR_CUDA, "damage kernel failed: %s", cudaGetErrorString(e));
+    pd->ctx->stats.kernel_launches++;
+    PDMTS_CUDA_TRY(cudaMemcpyAsync(phi, pd->d_out.p, sizeof(double) * pd->n, cudaMemcpyDefault, s));
+    PDMTS_CUDA_TRY(cudaStreamSynchronize(s));
+    return pd->ctx->end();
+}
+
+extern "C" int pd_read_bond_status(pdmts_pd *pd, uint8_t *mu, int64_t *n_intact)
+{
+    clear_error();
+    if (!pd || !mu)
+        return fail(PDMTS_ERR_ARG, "pd_read_bond_status: NULL argument");
+    PDMTS_CUDA_TRY(cudaSetDevice(pd->ctx->device));
+    PDMTS_TRY(pd->ctx->begin());
+    cudaStream_t s = pd->ctx->stream;
+    PDMTS_CUDA_TRY(cudaMemcpyAsync(pd->mask_host.data(), pd->d_mask.p, sizeof(uint32_t) * pd->n_mask_words,
+                                   cudaMemcpyDeviceToHost, s));
+    PDMTS_CUDA_TRY(cudaStreamSynchronize(s));
+    std::vector<uint8_t> st((size_t)pd->row_ptr[(size_t)pd->n]);
+    int64_t intact = 0;
+    for (int64_t i = 0; i < pd->n; ++i) {
+        int64_t t = i / 32, lane = i % 32;
+        for (int32_t k = 0; k < pd->deg[(size_t)i]; ++k) {
+            uint32_t w = pd->mask_host[(size_t)(pd->mask_ptr[(size_t)t] + 32 * (k / 32) + lane)];
+            uint8_t bit = (uint8_t)((w >> (k % 32)) & 1u);
+            st[(size_t)(pd->row_ptr[(size_t)i] + k)] = bit;
+            intact += bit;
+        }
+    }
+    PDMTS_CUDA_TRY(cudaMemcpy(mu, st.data(), st.size(), cudaMemcpyDefault));
+    if (n_intact)
+        *n_intact = intact;
+    return pd->ctx->end();
+}
+
+extern "C" int pd_read_family(pdmts_pd *pd, int64_t *row_ptr, int32_t *col)
+{
+    clear_error();
+    if (!pd || !row_ptr || !col)
+        return fail(PDMTS_ERR_ARG, "pd_read_family: NULL argument");
+    PDMTS_CUDA_TRY(cudaMemcpy(row_ptr, pd->row_ptr.data(), sizeof(int64_t) * (pd->n + 1), cudaMemcpyDefault));
+    PDMTS_CUDA_TRY(cudaMemcpy(col, pd->col.data(), sizeof(int32_t) * pd->col.size(), cudaMemcpyDefault));
+    return PDMTS_OK;
+}
+
+// ------------------------------------------------------ time integration --
+// Velocity-Verlet critical time step of the PD model (Silling-Askari bound
+// for the linearised bond model): dt <= sqrt(2 rho_i / sum_j V_j C_ij) with
+// the bond stiffness C_ij = c(|xi|) |xi|^2 (Eq. 2 projected on the bond).
+static double pd_dt_crit(const pdmts_pd *pd)
+{
+    double worst = INFINITY;
+    const int64_t n = pd->n;
+    for (int64_t i = 0; i < n; ++i) {
+        double sum = 0.0;
+        for (int64_t k = pd->row_ptr[(size_t)i]; k < pd->row_ptr[(size_t)i + 1]; ++k) {
+            int64_t j = pd->col[(size_t)k];
+            double xi2 = 0.0;
+            for (int d = 0; d < pd->dim; ++d) {
+                double e = pd->X[(size_t)d * n + j] - pd->X[(size_t)d * n + i];
+                xi2 += e * e;
+            }
+            sum += pd->V[(size_t)j] * micromodulus_host(pd, xi2) * xi2;
+        }
+        if (sum > 0)
+            worst = std::min(worst, std::sqrt(2.0 * pd->rho / sum));
+    }
+    return worst;
+}
+
+int mts_time_changed(pdmts_ctx *ctx);                          // mts.cu
+int pd_run_steps_graph(pdmts_pd *pd, int64_t nsteps, int chunk, cudaStream_t s);  // pd_kernels.cu
+
+extern "C" int mts_set_time(pdmts_ctx *ctx, double dt_pd, int m_ratio, double gamma_fe, double beta_fe,
+                            int check_stability)
+{
+    clear_error();
+    if (!ctx)
+        return fail(PDMTS_ERR_ARG, "mts_set_time: ctx is NULL");
+    if (!(dt_pd > 0) || !std::isfinite(dt_pd) || m_ratio < 1)
+        return fail(PDMTS_ERR_ARG, "mts_set_time: need dt_pd > 0 and m_ratio >= 1");
+    if (!(gamma_fe >= 0.5) || !(beta_fe >= 0.0))
+        return fail(PDMTS_ERR_ARG, "mts_set_time: Newmark parameters need gamma >= 1/2, beta >= 0");
+    if (check_stability && ctx->pd) {
+        double dc = pd_dt_crit(ctx->pd);
+        if (dt_pd > dc)
+            return fail(PDMTS_ERR_STABILITY, "mts_set_time: dt_pd = %g exceeds the PD bound %g", dt_pd, dc);
+    }
+    if (ctx->pd && ctx->dt_pd != dt_pd) {
+        ctx->pd->need_init = true;  // the prediction u + dt v + dt^2/2 a depends on dt
+        pd_invalidate_graphs(ctx->pd);
+    }
+    ctx->dt_pd = dt_pd;
+    ctx->m_ratio = m_ratio;
+    ctx->gamma_fe = gamma_fe;
+    ctx->beta_fe = beta_fe;
+    ctx->time_set = true;
+    return mts_time_changed(ctx);
+}
+
+extern int mts_advance_coupled(pdmts_ctx *ctx, int64_t n_coarse);  // mts.cu
+
+extern "C" int mts_advance(pdmts_ctx *ctx, int64_t n_coarse)
+{
+    clear_error();
+    if (!ctx)
+        return fail(PDMTS_ERR_ARG, "mts_advance: ctx is NULL");
+    if (n_coarse < 0)
+        return fail(PDMTS_ERR_ARG, "mts_advance: n_coarse < 0");
+    if (!ctx->pd)
+        return fail(PDMTS_ERR_STATE, "mts_advance: no PD subdomain");
+    if (!ctx->time_set)
+        return fail(PDMTS_ERR_STATE, "mts_advance: call mts_set_time first");
+    if (ctx->arl)
+        return mts_advance_coupled(ctx, n_coarse);
+    PDMTS_CUDA_TRY(cudaSetDevice(ctx->device));
+    PDMTS_TRY(ctx->begin());
+    pdmts_pd *pd = ctx->pd;
+    cudaStream_t s = ctx->stream;
+    PDMTS_TRY(pd->ensure_init(s));
+    const int64_t nsteps = n_coarse * ctx->m_ratio;
+    // one coarse step of m substeps is one captured chain (m = 1: chains of 16)
+    const int chunk = ctx->m_ratio >= 2 ? ctx->m_ratio : 16;
+    PDMTS_TRY(pd_run_steps_graph(pd, nsteps, chunk, s));
+    ctx->stats.coarse_steps += n_coarse;
+    return ctx->end();
+}

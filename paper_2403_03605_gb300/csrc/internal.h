@@ -1,0 +1,158 @@
+// internal.h -- shared internal declarations of the pdmts library (host + device).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "pdmts.h"
+
+namespace pdmts {
+
+// ---------------------------------------------------------------- errors ---
+int fail(int code, const char *fmt, ...);  // records a thread-local message, returns code
+void clear_error();
+
+#define PDMTS_CUDA_TRY(call)                                                              \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return ::pdmts::fail(PDMTS_ERR_CUDA, "%s failed: %s (%s:%d)", #call,          \
+                                 cudaGetErrorString(e_), __FILE__, __LINE__);             \
+    } while (0)
+
+#define PDMTS_TRY(expr)         \
+    do {                        \
+        int r_ = (expr);        \
+        if (r_ != PDMTS_OK)     \
+            return r_;          \
+    } while (0)
+
+// --------------------------------------------------------- kernel views ---
+// Sliced-ELL family with slice height 32 (one warp = one tile of 32 nodes).
+// Node i = 32 t + lane of tile t owns slots k = 0..deg_i-1 at
+// col[tile_ptr[t] + 32 k + lane] in ascending neighbour order; slots
+// deg_i..tile_k[t]-1 are padding (bit 0 in the mask). Bond status bit k of
+// node i is bit (k % 32) of mask[mask_ptr[t] + 32 (k / 32) + lane].
+struct SellView {
+    const int64_t *tile_ptr;  // [ntiles + 1]
+    const int32_t *tile_k;    // [ntiles]
+    const int64_t *mask_ptr;  // [ntiles]
+    const int32_t *col;       // FP64 path: neighbour index; FP32 path: (j << 8) | stencil id
+    uint32_t *mask;
+    const int32_t *deg;       // [n]
+    int64_t n;
+    int64_t ntiles;
+};
+
+struct F64StepArgs {
+    SellView fam;
+    const double *X;      // dim * n
+    const double *V;      // n
+    const double *cb;     // per slot: c(|xi|)
+    const double *alpha;  // n (null when no weights)
+    const double *mass;   // n: (1 - alpha) rho
+    const double *wb;     // dim * n: (1 - alpha) b (null when no body force)
+    const double *g;      // dim * n: interface force per volume (null when none)
+    const double *u_in;   // dim * n: displacement at the evaluated time
+    double *u_out;        // dim * n: predicted displacement for the next step
+    double *v;            // dim * n, in place
+    double *a;            // dim * n, in place
+    double s0p2;          // (1 + s0)^2
+    double dt, hdt, hdt2; // dt, dt/2, dt^2/2
+    double theta;         // interface-force factor of this substep
+    int breaking;
+    int pmb;              // PMB force law instead of the linearised one
+    unsigned long long *broken;  // running count of broken bonds (may be null)
+};
+
+// Stencil entry of the lattice (FP32) path: offset d = (x_j - x_i) / h in
+// lattice units, coef = c(|xi|) h^2 V, thr = s0 (2 + s0) |d|^2, rd = |d|,
+// r2 = |d|^2.
+struct StencilEntry {
+    float d[3];
+    float coef;
+    float thr;
+    float rd;
+    float r2;
+    float pad;
+};
+constexpr int kMaxStencil = 256;
+
+struct F32StepArgs {
+    SellView fam;               // col = (j << 8) | stencil id
+    const StencilEntry *stencil;// [n_stencil]
+    int n_stencil;
+    const float *alpha;         // n (null when no weights)
+    const float *inv_m;         // n: 1 / ((1 - alpha) rho)
+    const float *wb;            // dim * n: (1 - alpha) b / h (null when none)
+    const float *g;             // dim * n: interface force per volume / h (null when none)
+    // state in lattice units (u / h) as compensated pairs hi + lo, packed per
+    // node: 2D u4 = {hx, hy, lx, ly}; 3D u4 = {hx, hy, hz, lx}, u2 = {ly, lz}
+    const float4 *u4_in;
+    const float2 *u2_in;
+    float4 *u4_out;
+    float2 *u2_out;
+    float4 *v4;                 // in place, same packing
+    float2 *v2;
+    float *a;                   // 2D: float2 {ax, ay}; 3D: float4 {ax, ay, az, 0}; in place
+    float dt, hdt, hdt2, theta;
+    float s0;                   // critical stretch (PMB law)
+    int breaking;
+    int pmb;
+    unsigned long long *broken;
+};
+
+// Launchers (pd_kernels.cu). `init` computes a_0 from u_0 and predicts u_1
+// without touching v.
+cudaError_t launch_pd_step_f64(int dim, const F64StepArgs &A, bool init, cudaStream_t s);
+cudaError_t launch_pd_step_f32(int dim, const F32StepArgs &A, bool init, cudaStream_t s);
+cudaError_t launch_damage(const SellView &fam, int packed, const double *V, double *phi, cudaStream_t s);
+// Unpack a packed FP32 state field (u4/u2 or v4/v2 pairs, or a with u2 ==
+// null and `accel`) into dim * n doubles scaled by h.
+cudaError_t launch_unpack_f32(int dim, int64_t n, const float4 *p4, const float2 *p2, int accel,
+                              double h, double *out, cudaStream_t s);
+// Weighted body force from a staged dim * n FP64 field b on the device:
+// FP64: wb64 = (1 - alpha) b ; FP32: wb32 = (1 - alpha) b / h. Sets
+// flag[0] = 1 if b holds a non-finite value.
+cudaError_t launch_weighted_load(int dim, int64_t n, const double *b, const double *alpha64,
+                                 const float *alpha32, double inv_h, double *wb64, float *wb32,
+                                 unsigned long long *flag, cudaStream_t s);
+
+}  // namespace pdmts
+
+// --------------------------------------------------------------- handles ---
+struct pdmts_ctx {
+    int device = 0;
+    cudaStream_t user_stream = nullptr;  // caller's stream (may be legacy default)
+    cudaStream_t stream = nullptr;       // library's own non-blocking stream
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    pdmts_alloc_fn alloc = nullptr;
+    pdmts_free_fn free_fn = nullptr;
+    void *alloc_user = nullptr;
+    pdmts_pd *pd = nullptr;
+    pdmts_fem *fem = nullptr;
+    pdmts_arl *arl = nullptr;
+    double dt_pd = 0.0;
+    int m_ratio = 1;
+    double gamma_fe = 0.5, beta_fe = 0.25;
+    bool time_set = false;
+    pdmts_stats stats{};
+    unsigned long long *d_counter = nullptr;  // [0] broken bonds, [1] non-finite input flag
+    int64_t device_bytes = 0;
+    // substep-chain timing
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_marks;
+    std::vector<int64_t> ev_counts;
+    int time_begin(cudaEvent_t *start);                    // record a start mark (if timing)
+    int time_end(cudaEvent_t start, int64_t substeps);     // record the matching stop mark
+
+    void *dalloc(size_t bytes);
+    void dfree(void *p);
+    int begin();  // order own stream after the user stream
+    int end();    // order the user stream after own stream
+};

@@ -1,0 +1,91 @@
+// pd.h -- the PD subdomain handle (host mirror + device arrays).
+#pragma once
+
+#include <array>
+#include <vector>
+
+#include "internal.h"
+
+template <typename T>
+struct DevArr {
+    T *p = nullptr;
+    int64_t count = 0;
+};
+
+struct pdmts_pd {
+    pdmts_ctx *ctx = nullptr;
+    int dim = 2;
+    int64_t n = 0;
+    int precision = PDMTS_FP64;
+    double horizon = 0, c = 0, l = 0, s0 = 0, rho = 0;
+    int micro_kind = PDMTS_MICRO_POWER;
+    int force_kind = PDMTS_FORCE_LINEAR;
+    bool breaking = true;
+
+    // host mirror of the problem statement
+    std::vector<double> X;  // dim * n
+    std::vector<double> V;  // n
+    bool uniform_vol = true;
+    std::vector<int64_t> row_ptr;
+    std::vector<int32_t> col;
+
+    // lattice description (x = x0 + k h)
+    bool on_lattice = false;
+    double h = 0.0;
+    std::array<double, 3> x0{0, 0, 0};
+    std::vector<int32_t> lk;  // dim * n integer lattice coordinates
+
+    // sliced-ELL layout
+    int64_t ntiles = 0, n_slots = 0, n_mask_words = 0;
+    int32_t max_deg = 0;
+    std::vector<int64_t> tile_ptr, mask_ptr;
+    std::vector<int32_t> tile_k, deg;
+    std::vector<uint32_t> mask_host;  // initial / staged mask
+
+    // loads and weights
+    std::vector<double> alpha;  // n (empty: all zero)
+    bool has_b = false;         // body force set (raw field kept on the device in d_b)
+    std::vector<double> g;      // dim * n interface force density (empty: none)
+
+    // device arrays common to both precisions
+    DevArr<int64_t> d_tile_ptr, d_mask_ptr;
+    DevArr<int32_t> d_tile_k, d_col, d_deg;
+    DevArr<uint32_t> d_mask;
+    DevArr<double> d_V, d_out;  // d_out: dim * n staging for read-back and uploads
+    DevArr<double> d_b;         // raw body force b, dim * n
+    // FP64
+    DevArr<double> d_X, d_cb, d_alpha, d_mass, d_wb, d_g, d_v, d_a;
+    DevArr<double> d_u[2];
+    // FP32 bulk
+    DevArr<pdmts::StencilEntry> d_stencil;
+    int n_stencil = 0;
+    DevArr<float> f_alpha, f_invm, f_wb, f_g;
+    // state in lattice units, compensated pairs, per-node packed:
+    // 2D: u4 = {hx, hy, lx, ly}; 3D: u4 = {hx, hy, hz, lx}, u2 = {ly, lz}
+    DevArr<float4> f_u4[2], f_v4;
+    DevArr<float2> f_u2[2], f_v2;
+    DevArr<float> f_a;   // 2D: {ax, ay} per node; 3D: {ax, ay, az, 0} per node (lattice units)
+
+    // captured substep chains, keyed by (starting buffer parity, length, theta schedule id)
+    struct GraphEntry {
+        int parity, len, sched;
+        cudaGraphExec_t exec;
+    };
+    std::vector<GraphEntry> graphs;
+    bool use_graphs = true;
+
+    int cur = 0;            // buffer holding u at the current time
+    bool need_init = true;  // a must be recomputed from u before the next step
+    int64_t steps_done = 0;
+    int64_t device_bytes = 0;
+
+    template <typename T>
+    int alloc(DevArr<T> &a, int64_t count);
+    template <typename T>
+    void release(DevArr<T> &a);
+    void release_all();
+
+    int upload_weights_and_loads();  // (re)build mass, wb, g device arrays
+    int step(bool init, double theta, cudaStream_t s);  // one substep on the current state
+    int ensure_init(cudaStream_t s);
+};

@@ -1,0 +1,540 @@
+// pd_kernels.cu -- the PD substep (hot path) for sm_103a.
+//
+// One thread per PD node, one warp per tile of 32 consecutive nodes. The
+// family is a sliced-ELL layout with slice height 32: slot k of the 32 nodes
+// of a tile is one coalesced 128-byte row, and on a lattice the 32 neighbours
+// read in one slot are 32 consecutive nodes, so the neighbour gather is
+// coalesced as well. Each node accumulates its own force in registers in
+// ascending neighbour order: no atomics, no reductions, a fixed summation
+// order. The broken-bond state is one bit per slot (uint32 words, 32 slots per
+// word per node), cleared irreversibly and written back only when it changes.
+//
+// Per substep (arXiv 2403.03605, Eq. 1-4, Eq. 33-34, Eq. 38 with gamma = 1/2,
+// beta = 0, and the free-problem interface term of Eq. 48a):
+//   for each intact bond: xi, eta, breaking test s >= s0, force sum
+//   a = (f + (1 - alpha) b + theta g) / ((1 - alpha) rho)
+//   v += dt/2 (a_old + a);   u_next = u + dt v + dt^2/2 a   (next substep's u)
+//
+// Two precisions:
+//  * FP64: the parity build. Every operation is IEEE FP64 with explicit
+//    round-to-nearest intrinsics (no FMA contraction) in exactly the order of
+//    the CPU oracle, so results and broken-bond sets are bit-identical.
+//  * FP32 bulk: bond kinematics and forces in FP32 from displacement
+//    differences in lattice units; u and v are compensated (hi + lo) FP32
+//    pairs so differences keep ~48 bits; the per-bond family word packs the
+//    neighbour index and a stencil id whose offset, micromodulus and
+//    threshold sit in shared memory. No FP64 instruction in the bond loop.
+#include <algorithm>
+
+#include "pd.h"
+
+namespace pdmts {
+
+// ------------------------------------------------------------------ FP64 --
+__device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double ddiv(double a, double b) { return __ddiv_rn(a, b); }
+
+template <int DIM>
+__global__ void __launch_bounds__(256) k_pd_step_f64(const F64StepArgs A, const int init)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t tile = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (tile >= A.fam.ntiles)
+        return;
+    const int64_t n = A.fam.n;
+    const int64_t i = tile * 32 + lane;
+    const bool valid = i < n;
+    const int64_t ii = valid ? i : n - 1;
+    const int K = A.fam.tile_k[tile];
+    const int64_t base = A.fam.tile_ptr[tile];
+    const int64_t mbase = A.fam.mask_ptr[tile];
+
+    double xi_i[DIM], ui[DIM], f[DIM];
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+        xi_i[d] = A.X[d * n + ii];
+        ui[d] = A.u_in[d * n + ii];
+        f[d] = 0.0;
+    }
+    const double ai = A.alpha ? A.alpha[ii] : 0.0;
+    unsigned nbroken = 0;
+
+    for (int w = 0; 32 * w < K; ++w) {
+        const uint32_t m0 = valid ? A.fam.mask[mbase + 32 * w + lane] : 0u;
+        uint32_t m = m0;
+        const int kend = min(32, K - 32 * w);
+        for (int kk = 0; kk < kend; ++kk) {
+            if (!((m0 >> kk) & 1u))
+                continue;
+            const int64_t slot = base + (int64_t)(32 * w + kk) * 32 + lane;
+            const int64_t j = A.fam.col[slot];
+            double xi[DIM], eta[DIM];
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) {
+                xi[d] = dsub(A.X[d * n + j], xi_i[d]);
+                eta[d] = dsub(A.u_in[d * n + j], ui[d]);
+            }
+            double xi2 = 0.0, y2 = 0.0;
+#pragma unroll
+            for (int d = 0; d < DIM; ++d)
+                xi2 = dadd(xi2, dmul(xi[d], xi[d]));
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) {
+                const double y = dadd(xi[d], eta[d]);
+                y2 = dadd(y2, dmul(y, y));
+            }
+            if (A.breaking && y2 >= dmul(A.s0p2, xi2)) {  // s >= s0 (Eq. 3-4)
+                m &= ~(1u << kk);
+                continue;
+            }
+            double wc = A.cb[slot];
+            if (A.alpha) {
+                const double w_ij = dsub(1.0, dmul(0.5, dadd(ai, A.alpha[j])));
+                wc = dmul(w_ij, wc);
+            }
+            if (A.pmb) {
+                const double r = __dsqrt_rn(xi2), ry = __dsqrt_rn(y2);
+                const double s = ddiv(dsub(ry, r), r);
+                const double cp = dmul(dmul(A.cb[slot], xi2), r);
+                double wcp = cp;
+                if (A.alpha)
+                    wcp = dmul(dsub(1.0, dmul(0.5, dadd(ai, A.alpha[j]))), cp);
+                const double sc = dmul(ddiv(dmul(wcp, s), ry), A.V[j]);
+#pragma unroll
+                for (int d = 0; d < DIM; ++d)
+                    f[d] = dadd(f[d], dmul(sc, dadd(xi[d], eta[d])));
+            } else {
+                double dot = 0.0;
+#pragma unroll
+                for (int d = 0; d < DIM; ++d)
+                    dot = dadd(dot, dmul(xi[d], eta[d]));
+                const double sc = dmul(dmul(wc, dot), A.V[j]);
+#pragma unroll
+                for (int d = 0; d < DIM; ++d)
+                    f[d] = dadd(f[d], dmul(sc, xi[d]));
+            }
+        }
+        if (m != m0) {
+            A.fam.mask[mbase + 32 * w + lane] = m;
+            nbroken += __popc(m0 ^ m);
+        }
+    }
+    if (A.broken) {
+        const unsigned tot = __reduce_add_sync(0xffffffffu, nbroken);
+        if (lane == 0 && tot)
+            atomicAdd(A.broken, (unsigned long long)tot);
+    }
+    if (!valid)
+        return;
+    const double mi = A.mass[i];
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+        double t = f[d];
+        if (A.wb)
+            t = dadd(t, A.wb[d * n + i]);
+        if (A.g)
+            t = dadd(t, dmul(A.theta, A.g[d * n + i]));
+        const double an = ddiv(t, mi);
+        double v = A.v[d * n + i];
+        if (!init) {
+            v = dadd(v, dmul(A.hdt, dadd(A.a[d * n + i], an)));
+            A.v[d * n + i] = v;
+        }
+        A.a[d * n + i] = an;
+        A.u_out[d * n + i] = dadd(dadd(ui[d], dmul(A.dt, v)), dmul(A.hdt2, an));
+    }
+}
+
+// ------------------------------------------------------------- FP32 bulk --
+// Compensated addition (hi, lo) += x: Knuth's two-sum followed by a
+// renormalisation, all in FP32 without products (nothing to contract).
+__device__ __forceinline__ void df_add(float &hi, float &lo, float x)
+{
+    const float s = hi + x;
+    const float bp = s - hi;
+    float e = (hi - (s - bp)) + (x - bp);
+    e += lo;
+    const float h2 = s + e;
+    lo = e - (h2 - s);
+    hi = h2;
+}
+
+template <int DIM>
+__device__ __forceinline__ void load_pair(const float4 *p4, const float2 *p2, int64_t i, float (&h)[DIM],
+                                          float (&l)[DIM])
+{
+    const float4 q = p4[i];
+    if constexpr (DIM == 2) {
+        h[0] = q.x; h[1] = q.y; l[0] = q.z; l[1] = q.w;
+    } else {
+        const float2 r = p2[i];
+        h[0] = q.x; h[1] = q.y; h[2] = q.z; l[0] = q.w; l[1] = r.x; l[2] = r.y;
+    }
+}
+
+template <int DIM>
+__device__ __forceinline__ void store_pair(float4 *p4, float2 *p2, int64_t i, const float (&h)[DIM],
+                                           const float (&l)[DIM])
+{
+    if constexpr (DIM == 2) {
+        p4[i] = make_float4(h[0], h[1], l[0], l[1]);
+    } else {
+        p4[i] = make_float4(h[0], h[1], h[2], l[0]);
+        p2[i] = make_float2(l[1], l[2]);
+    }
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(256) k_pd_step_f32(const F32StepArgs A, const int init)
+{
+    __shared__ float4 s_d[kMaxStencil];  // {d0, d1, d2, coef}
+    __shared__ float4 s_t[kMaxStencil];  // {thr, rd, r2, 0}
+    for (int q = threadIdx.x; q < A.n_stencil; q += blockDim.x) {
+        const StencilEntry e = A.stencil[q];
+        s_d[q] = make_float4(e.d[0], e.d[1], e.d[2], e.coef);
+        s_t[q] = make_float4(e.thr, e.rd, e.r2, 0.f);
+    }
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31;
+    const int64_t tile = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (tile >= A.fam.ntiles)
+        return;
+    const int64_t n = A.fam.n;
+    const int64_t i = tile * 32 + lane;
+    const bool valid = i < n;
+    const int64_t ii = valid ? i : n - 1;
+    const int K = A.fam.tile_k[tile];
+    const int64_t base = A.fam.tile_ptr[tile];
+    const int64_t mbase = A.fam.mask_ptr[tile];
+    const uint32_t *col = reinterpret_cast<const uint32_t *>(A.fam.col);
+
+    float uh[DIM], ul[DIM], f[DIM];
+    load_pair<DIM>(A.u4_in, A.u2_in, ii, uh, ul);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d)
+        f[d] = 0.f;
+    const float ai = A.alpha ? A.alpha[ii] : 0.f;
+    unsigned nbroken = 0;
+
+    for (int w = 0; 32 * w < K; ++w) {
+        const uint32_t m0 = valid ? A.fam.mask[mbase + 32 * w + lane] : 0u;
+        uint32_t m = m0;
+        const int kend = min(32, K - 32 * w);
+        const uint32_t *cp = col + base + (int64_t)(32 * w) * 32 + lane;
+#pragma unroll 4
+        for (int kk = 0; kk < kend; ++kk) {
+            const uint32_t cw = __ldg(cp + 32 * kk);
+            if (!((m0 >> kk) & 1u))
+                continue;
+            const uint32_t j = cw >> 8;
+            const uint32_t sid = cw & 255u;
+            const float4 sd = s_d[sid];
+            const float4 st = s_t[sid];
+            float jh[DIM], jl[DIM], eta[DIM];
+            load_pair<DIM>(A.u4_in, A.u2_in, j, jh, jl);
+#pragma unroll
+            for (int d = 0; d < DIM; ++d)
+                eta[d] = (jh[d] - uh[d]) + (jl[d] - ul[d]);
+            const float dd[3] = {sd.x, sd.y, sd.z};
+            float dot = dd[0] * eta[0];
+            float e2 = eta[0] * eta[0];
+#pragma unroll
+            for (int d = 1; d < DIM; ++d) {
+                dot = fmaf(dd[d], eta[d], dot);
+                e2 = fmaf(eta[d], eta[d], e2);
+            }
+            // |xi + eta|^2 - |xi|^2 = h^2 (2 d.eta + |eta|^2) >= ((1+s0)^2 - 1)|xi|^2
+            const float lhs = fmaf(2.f, dot, e2);
+            if (A.breaking && lhs >= st.x) {
+                m &= ~(1u << kk);
+                continue;
+            }
+            float coef = sd.w;
+            if (A.alpha)
+                coef *= 1.f - 0.5f * (ai + A.alpha[j]);
+            if (A.pmb) {
+                // s = (|d + eta| - |d|)/|d| = lhs / ((ry + rd) rd), force along d + eta
+                const float ry = sqrtf(st.z + lhs);
+                const float sc = coef * st.z * lhs / ((ry + st.y) * ry);
+#pragma unroll
+                for (int d = 0; d < DIM; ++d)
+                    f[d] = fmaf(sc, dd[d] + eta[d], f[d]);
+            } else {
+                const float s = coef * dot;
+#pragma unroll
+                for (int d = 0; d < DIM; ++d)
+                    f[d] = fmaf(s, dd[d], f[d]);
+            }
+        }
+        if (m != m0) {
+            A.fam.mask[mbase + 32 * w + lane] = m;
+            nbroken += __popc(m0 ^ m);
+        }
+    }
+    if (A.broken) {
+        const unsigned tot = __reduce_add_sync(0xffffffffu, nbroken);
+        if (lane == 0 && tot)
+            atomicAdd(A.broken, (unsigned long long)tot);
+    }
+    if (!valid)
+        return;
+    const float im = A.inv_m[i];
+    float an[DIM], ao[DIM];
+    if constexpr (DIM == 2) {
+        const float2 q = reinterpret_cast<const float2 *>(A.a)[i];
+        ao[0] = q.x; ao[1] = q.y;
+    } else {
+        const float4 q = reinterpret_cast<const float4 *>(A.a)[i];
+        ao[0] = q.x; ao[1] = q.y; ao[2] = q.z;
+    }
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+        float t = f[d];
+        if (A.wb)
+            t += A.wb[d * n + i];
+        if (A.g)
+            t = fmaf(A.theta, A.g[d * n + i], t);
+        an[d] = t * im;
+    }
+    float vh[DIM], vl[DIM];
+    load_pair<DIM>(A.v4, A.v2, i, vh, vl);
+    if (!init) {
+#pragma unroll
+        for (int d = 0; d < DIM; ++d)
+            df_add(vh[d], vl[d], A.hdt * (ao[d] + an[d]));
+        store_pair<DIM>(A.v4, A.v2, i, vh, vl);
+    }
+    if constexpr (DIM == 2)
+        reinterpret_cast<float2 *>(A.a)[i] = make_float2(an[0], an[1]);
+    else
+        reinterpret_cast<float4 *>(A.a)[i] = make_float4(an[0], an[1], an[2], 0.f);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d)
+        df_add(uh[d], ul[d], fmaf(A.dt, vh[d], fmaf(A.dt, vl[d], A.hdt2 * an[d])));
+    store_pair<DIM>(A.u4_out, A.u2_out, i, uh, ul);
+}
+
+// ----------------------------------------------------------- damage (Eq. 5)
+__global__ void k_damage(const SellView fam, const int packed, const double *__restrict__ V,
+                         double *__restrict__ phi)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= fam.n)
+        return;
+    const int64_t t = i >> 5, lane = i & 31;
+    const int dg = fam.deg[i];
+    const int64_t base = fam.tile_ptr[t], mbase = fam.mask_ptr[t];
+    double num = 0.0, den = 0.0;
+    for (int k = 0; k < dg; ++k) {
+        uint32_t cw = (uint32_t)fam.col[base + (int64_t)k * 32 + lane];
+        int64_t j = packed ? (int64_t)(cw >> 8) : (int64_t)cw;
+        const uint32_t w = fam.mask[mbase + 32 * (k >> 5) + lane];
+        den = __dadd_rn(den, V[j]);
+        if ((w >> (k & 31)) & 1u)
+            num = __dadd_rn(num, V[j]);
+    }
+    phi[i] = den > 0.0 ? __dsub_rn(1.0, __ddiv_rn(num, den)) : 0.0;
+}
+
+__global__ void k_unpack(const int dim, const int64_t n, const float4 *__restrict__ p4,
+                         const float2 *__restrict__ p2, const int accel, const double h,
+                         double *__restrict__ out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n)
+        return;
+    if (accel) {
+        if (dim == 2) {
+            const float2 q = reinterpret_cast<const float2 *>(p4)[i];
+            out[i] = (double)q.x * h;
+            out[n + i] = (double)q.y * h;
+        } else {
+            const float4 q = p4[i];
+            out[i] = (double)q.x * h;
+            out[n + i] = (double)q.y * h;
+            out[2 * n + i] = (double)q.z * h;
+        }
+        return;
+    }
+    const float4 q = p4[i];
+    if (dim == 2) {
+        out[i] = ((double)q.x + (double)q.z) * h;
+        out[n + i] = ((double)q.y + (double)q.w) * h;
+    } else {
+        const float2 r = p2[i];
+        out[i] = ((double)q.x + (double)q.w) * h;
+        out[n + i] = ((double)q.y + (double)r.x) * h;
+        out[2 * n + i] = ((double)q.z + (double)r.y) * h;
+    }
+}
+
+// (1 - alpha) b for the FP64 path, (1 - alpha) b / h for the FP32 path, or
+// only a finiteness check of b (flag set to 1 on NaN/Inf).
+__global__ void k_weighted_load(const int dim, const int64_t n, const double *__restrict__ b,
+                                const double *__restrict__ alpha64, const float *__restrict__ alpha32,
+                                const double inv_h, double *__restrict__ wb64, float *__restrict__ wb32,
+                                unsigned long long *flag)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n)
+        return;
+    for (int d = 0; d < dim; ++d) {
+        const double x = b[d * n + i];
+        if (flag) {
+            if (!isfinite(x))
+                atomicExch(flag, 1ull);
+            continue;
+        }
+        if (wb64)
+            wb64[d * n + i] = alpha64 ? __dmul_rn(__dsub_rn(1.0, alpha64[i]), x) : x;
+        if (wb32) {
+            const double w = alpha32 ? 1.0 - (double)alpha32[i] : 1.0;
+            wb32[d * n + i] = (float)(w * x * inv_h);
+        }
+    }
+}
+
+// ------------------------------------------------------------- launchers --
+static inline unsigned grid_for_tiles(int64_t ntiles) { return (unsigned)((ntiles + 7) / 8); }
+
+cudaError_t launch_pd_step_f64(int dim, const F64StepArgs &A, bool init, cudaStream_t s)
+{
+    if (A.fam.ntiles == 0)
+        return cudaSuccess;
+    const unsigned grid = grid_for_tiles(A.fam.ntiles);
+    if (dim == 2)
+        k_pd_step_f64<2><<<grid, 256, 0, s>>>(A, init ? 1 : 0);
+    else
+        k_pd_step_f64<3><<<grid, 256, 0, s>>>(A, init ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pd_step_f32(int dim, const F32StepArgs &A, bool init, cudaStream_t s)
+{
+    if (A.fam.ntiles == 0)
+        return cudaSuccess;
+    const unsigned grid = grid_for_tiles(A.fam.ntiles);
+    if (dim == 2)
+        k_pd_step_f32<2><<<grid, 256, 0, s>>>(A, init ? 1 : 0);
+    else
+        k_pd_step_f32<3><<<grid, 256, 0, s>>>(A, init ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_damage(const SellView &fam, int packed, const double *V, double *phi, cudaStream_t s)
+{
+    if (fam.n == 0)
+        return cudaSuccess;
+    k_damage<<<(unsigned)((fam.n + 255) / 256), 256, 0, s>>>(fam, packed, V, phi);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_weighted_load(int dim, int64_t n, const double *b, const double *alpha64, const float *alpha32,
+                                 double inv_h, double *wb64, float *wb32, unsigned long long *flag, cudaStream_t s)
+{
+    if (n == 0)
+        return cudaSuccess;
+    k_weighted_load<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(dim, n, b, alpha64, alpha32, inv_h, wb64, wb32,
+                                                                 flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack_f32(int dim, int64_t n, const float4 *p4, const float2 *p2, int accel, double h,
+                              double *out, cudaStream_t s)
+{
+    if (n == 0)
+        return cudaSuccess;
+    k_unpack<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(dim, n, p4, p2, accel, h, out);
+    return cudaGetLastError();
+}
+
+}  // namespace pdmts
+
+// -------------------------------------------------- substep chains / graphs
+// A chain of substeps alternates the two displacement buffers, so a captured
+// graph of `len` substeps is keyed by the buffer parity it starts from (and by
+// the interface-force schedule `sched` it bakes in). Graphs are dropped
+// whenever a kernel argument or array changes.
+using namespace pdmts;
+
+int pd_invalidate_graphs(pdmts_pd *pd)
+{
+    for (auto &g : pd->graphs)
+        if (g.exec)
+            cudaGraphExecDestroy(g.exec);
+    pd->graphs.clear();
+    return PDMTS_OK;
+}
+
+// Launch one chain of `len` substeps with interface factors theta(k), either
+// directly or by replaying its captured graph. Host bookkeeping (buffer
+// parity, counters) is applied once per chain.
+int pd_run_chain(pdmts_pd *pd, int len, int sched, const double *theta, cudaStream_t s)
+{
+    pdmts_ctx *ctx = pd->ctx;
+    cudaEvent_t t0 = nullptr;
+    PDMTS_TRY(ctx->time_begin(&t0));
+    if (!pd->use_graphs || len < 2) {
+        for (int k = 0; k < len; ++k)
+            PDMTS_TRY(pd->step(false, theta ? theta[k] : 0.0, s));
+        return ctx->time_end(t0, len);
+    }
+    const int p = pd->cur;
+    cudaGraphExec_t exec = nullptr;
+    for (auto &g : pd->graphs)
+        if (g.parity == p && g.len == len && g.sched == sched)
+            exec = g.exec;
+    if (!exec) {
+        const int cur0 = pd->cur;
+        const int64_t steps0 = pd->steps_done;
+        const pdmts_stats st0 = ctx->stats;
+        cudaGraph_t g = nullptr;
+        PDMTS_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        int r = PDMTS_OK;
+        for (int k = 0; k < len && r == PDMTS_OK; ++k)
+            r = pd->step(false, theta ? theta[k] : 0.0, s);
+        cudaError_t e = cudaStreamEndCapture(s, &g);
+        pd->cur = cur0;
+        pd->steps_done = steps0;
+        ctx->stats = st0;
+        if (r != PDMTS_OK) {
+            if (g)
+                cudaGraphDestroy(g);
+            return r;
+        }
+        if (e != cudaSuccess)
+            return fail(PDMTS_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess)
+            return fail(PDMTS_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+        pd->graphs.push_back({p, len, sched, exec});
+    }
+    PDMTS_CUDA_TRY(cudaGraphLaunch(exec, s));
+    ctx->stats.graph_launches++;
+    ctx->stats.kernel_launches += len;
+    ctx->stats.pd_substeps += len;
+    ctx->stats.bond_updates += (int64_t)len * pd->row_ptr[(size_t)pd->n];
+    pd->steps_done += len;
+    if (len & 1)
+        pd->cur = 1 - pd->cur;
+    return ctx->time_end(t0, len);
+}
+
+// nsteps plain substeps (theta = 0) in chains of `chunk`.
+int pd_run_steps_graph(pdmts_pd *pd, int64_t nsteps, int chunk, cudaStream_t s)
+{
+    if (chunk < 1)
+        chunk = 1;
+    int64_t done = 0;
+    while (nsteps - done >= chunk) {
+        PDMTS_TRY(pd_run_chain(pd, chunk, 0, nullptr, s));
+        done += chunk;
+    }
+    if (done < nsteps)
+        PDMTS_TRY(pd_run_chain(pd, (int)(nsteps - done), 0, nullptr, s));
+    return PDMTS_OK;
+}

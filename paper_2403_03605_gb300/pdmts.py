@@ -1,0 +1,301 @@
+"""Thin ctypes binding of the pdmts C ABI (include/pdmts.h).
+
+Function names match the C entry points; this module only marshals arguments
+(numpy arrays or torch tensors in, numpy arrays out) and turns negative status
+codes into exceptions. Every step of the computation runs in libpdmts.so. If
+the library has not been built, load() raises instead of falling back to
+anything else. PyTorch provides the CUDA stream and, through
+pdmts_set_allocator, the device memory (its caching allocator).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libpdmts.so")
+
+PDMTS_OK = 0
+ERRORS = {-1: "PDMTS_ERR_ARG", -2: "PDMTS_ERR_MASS", -3: "PDMTS_ERR_STABILITY", -4: "PDMTS_ERR_CUDA",
+          -5: "PDMTS_ERR_TIMEOUT", -6: "PDMTS_ERR_STATE", -7: "PDMTS_ERR_NOMEM", -8: "PDMTS_ERR_UNSUPPORTED"}
+PDMTS_FP64, PDMTS_FP32_BULK = 0, 1
+PDMTS_MICRO_POWER, PDMTS_MICRO_EXP = 0, 1
+PDMTS_FORCE_LINEAR, PDMTS_FORCE_PMB = 0, 1
+PDMTS_WEIGHT_CONSTANT, PDMTS_WEIGHT_LINEAR, PDMTS_WEIGHT_CUBIC = 0, 1, 2
+
+
+class PdmtsError(RuntimeError):
+    def __init__(self, code, where, msg):
+        super().__init__(f"{where}: {ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class PDInfo(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("precision", C.c_int32), ("n", C.c_int64), ("n_bonds", C.c_int64),
+                ("n_slots", C.c_int64), ("max_degree", C.c_int32), ("on_lattice", C.c_int32),
+                ("lattice_h", C.c_double), ("steps_done", C.c_int64), ("device_bytes", C.c_int64)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("pd_substeps", C.c_int64), ("bond_updates", C.c_int64), ("coarse_steps", C.c_int64),
+                ("bonds_broken", C.c_int64), ("kernel_launches", C.c_int64), ("graph_launches", C.c_int64)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+_lib = None
+_lock = threading.Lock()
+_V, _I, _I64, _D = C.c_void_p, C.c_int, C.c_int64, C.c_double
+
+# (name, restype, argtypes) for every function declared in include/pdmts.h
+SIGNATURES = [
+    ("pdmts_ctx_create", _I, [C.POINTER(_V), _I, _V]),
+    ("pdmts_ctx_destroy", _I, [_V]),
+    ("pdmts_last_error", C.c_char_p, []),
+    ("pdmts_set_allocator", _I, [_V, ALLOC_FN, FREE_FN, _V]),
+    ("pdmts_ctx_synchronize", _I, [_V]),
+    ("pd_create", _I, [_V, _I, _I64, _V, _V, _D, _D, _I, _D, _D, _D, _D, _I, C.POINTER(_V)]),
+    ("pd_destroy", _I, [_V]),
+    ("pd_set_precrack", _I, [_V, _I, _V]),
+    ("pd_set_body_force", _I, [_V, _V]),
+    ("pd_set_state", _I, [_V, _V, _V]),
+    ("pd_set_weights", _I, [_V, _V]),
+    ("pd_set_breaking", _I, [_V, _I]),
+    ("pd_set_force_law", _I, [_V, _I]),
+    ("pd_info", _I, [_V, C.POINTER(PDInfo)]),
+    ("pd_read_displacement", _I, [_V, _V]),
+    ("pd_read_velocity", _I, [_V, _V]),
+    ("pd_read_acceleration", _I, [_V, _V]),
+    ("pd_read_damage", _I, [_V, _V]),
+    ("pd_read_bond_status", _I, [_V, _V, C.POINTER(_I64)]),
+    ("pd_read_family", _I, [_V, _V, _V]),
+    ("mts_set_time", _I, [_V, _D, _I, _D, _D, _I]),
+    ("mts_advance", _I, [_V, _I64]),
+    ("pdmts_set_timing", _I, [_V, _I]),
+    ("pdmts_get_timing", _I, [_V, C.POINTER(_D), C.POINTER(_I64)]),
+    ("pdmts_get_stats", _I, [_V, C.POINTER(Stats)]),
+]
+
+
+def load():
+    """Load libpdmts.so (built by paper_2403_03605_gb300.build). No fallback."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2403_03605_gb300.build.build()")
+            lib = C.CDLL(LIB_PATH)
+            for name, res, args in SIGNATURES:
+                fn = getattr(lib, name, None)
+                if fn is None:
+                    continue
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+        return _lib
+
+
+def _check(code, where):
+    if code != PDMTS_OK:
+        msg = load().pdmts_last_error()
+        raise PdmtsError(code, where, msg.decode() if msg else "")
+
+
+def _ptr(a):
+    """Address of a numpy array or torch tensor (host or device), or None."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        assert a.is_contiguous()
+        return a.data_ptr()
+    assert a.flags.c_contiguous
+    return a.ctypes.data
+
+
+def _f64(a):
+    if a is None or hasattr(a, "data_ptr"):
+        return a
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# ------------------------------------------------------------------ context
+class _TorchAllocator:
+    """PyTorch's caching allocator exposed through pdmts_set_allocator."""
+
+    def __init__(self, device, stream):
+        import torch
+        self.torch = torch
+        self.device = device
+        self.stream = stream
+        self.alloc = ALLOC_FN(self._alloc)
+        self.free = FREE_FN(self._free)
+
+    def _alloc(self, size, user):
+        try:
+            return self.torch.cuda.caching_allocator_alloc(int(size), self.device, self.stream)
+        except Exception:
+            return None
+
+    def _free(self, ptr, user):
+        self.torch.cuda.caching_allocator_delete(ptr)
+
+
+_allocators = {}
+
+
+def pdmts_ctx_create(device=0, stream=None, torch_allocator=True):
+    """Create a context. `stream` is a cudaStream_t integer (default: torch's
+    current stream on `device`); with torch_allocator the library draws its
+    device memory from PyTorch's caching allocator."""
+    L = load()
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream(device).cuda_stream
+    h = _V()
+    _check(L.pdmts_ctx_create(C.byref(h), int(device), _V(stream) if stream else None), "pdmts_ctx_create")
+    if torch_allocator:
+        al = _TorchAllocator(device, stream)
+        _check(L.pdmts_set_allocator(h, al.alloc, al.free, None), "pdmts_set_allocator")
+        _allocators[h.value] = al
+    return h.value
+
+
+def pdmts_ctx_destroy(ctx):
+    _check(load().pdmts_ctx_destroy(ctx), "pdmts_ctx_destroy")
+    _allocators.pop(ctx, None)
+
+
+def pdmts_last_error():
+    m = load().pdmts_last_error()
+    return m.decode() if m else ""
+
+
+def pdmts_ctx_synchronize(ctx):
+    _check(load().pdmts_ctx_synchronize(ctx), "pdmts_ctx_synchronize")
+
+
+def pdmts_get_stats(ctx):
+    s = Stats()
+    _check(load().pdmts_get_stats(ctx, C.byref(s)), "pdmts_get_stats")
+    return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+
+def pdmts_set_timing(ctx, enabled):
+    _check(load().pdmts_set_timing(ctx, int(bool(enabled))), "pdmts_set_timing")
+
+
+def pdmts_get_timing(ctx):
+    """(summed substep-chain milliseconds, substeps timed) since the last call."""
+    ms, cnt = _D(), _I64()
+    _check(load().pdmts_get_timing(ctx, C.byref(ms), C.byref(cnt)), "pdmts_get_timing")
+    return ms.value, cnt.value
+
+
+# ------------------------------------------------------------------------ PD
+def pd_create(ctx, X, *, horizon, c, s0, rho, vol=None, vol_uniform=0.0, micro_kind=PDMTS_MICRO_POWER, l=0.0,
+              precision=PDMTS_FP64):
+    """X: (dim, n) reference positions. Returns the PD handle."""
+    X = _f64(X)
+    dim, n = X.shape
+    vol = _f64(vol)
+    h = _V()
+    _check(load().pd_create(ctx, int(dim), int(n), _ptr(X), _ptr(vol), float(vol_uniform), float(horizon),
+                            int(micro_kind), float(c), float(l), float(s0), float(rho), int(precision),
+                            C.byref(h)), "pd_create")
+    return h.value
+
+
+def pd_destroy(pd):
+    _check(load().pd_destroy(pd), "pd_destroy")
+
+
+def pd_set_precrack(pd, cuts):
+    """cuts: iterable of (normal axis, level, along axis, lo, hi) in metres."""
+    arr = np.ascontiguousarray(np.asarray(list(cuts), dtype=np.float64).reshape(-1, 5))
+    _check(load().pd_set_precrack(pd, len(arr), _ptr(arr) if len(arr) else None), "pd_set_precrack")
+
+
+def pd_set_body_force(pd, b):
+    b = _f64(b)
+    _check(load().pd_set_body_force(pd, _ptr(b)), "pd_set_body_force")
+
+
+def pd_set_state(pd, u=None, v=None):
+    u, v = _f64(u), _f64(v)
+    _check(load().pd_set_state(pd, _ptr(u), _ptr(v)), "pd_set_state")
+
+
+def pd_set_weights(pd, alpha):
+    alpha = _f64(alpha)
+    _check(load().pd_set_weights(pd, _ptr(alpha)), "pd_set_weights")
+
+
+def pd_set_breaking(pd, enabled):
+    _check(load().pd_set_breaking(pd, int(bool(enabled))), "pd_set_breaking")
+
+
+def pd_set_force_law(pd, kind):
+    _check(load().pd_set_force_law(pd, int(kind)), "pd_set_force_law")
+
+
+def pd_info(pd):
+    s = PDInfo()
+    _check(load().pd_info(pd, C.byref(s)), "pd_info")
+    return {k: getattr(s, k) for k, _ in PDInfo._fields_}
+
+
+def _read(fn, pd, shape, out=None, dtype=np.float64):
+    if out is None:
+        out = np.empty(shape, dtype=dtype)
+    _check(getattr(load(), fn)(pd, _ptr(out)), fn)
+    return out
+
+
+def pd_read_displacement(pd, out=None):
+    i = pd_info(pd)
+    return _read("pd_read_displacement", pd, (i["dim"], i["n"]), out)
+
+
+def pd_read_velocity(pd, out=None):
+    i = pd_info(pd)
+    return _read("pd_read_velocity", pd, (i["dim"], i["n"]), out)
+
+
+def pd_read_acceleration(pd, out=None):
+    i = pd_info(pd)
+    return _read("pd_read_acceleration", pd, (i["dim"], i["n"]), out)
+
+
+def pd_read_damage(pd, out=None):
+    i = pd_info(pd)
+    return _read("pd_read_damage", pd, (i["n"],), out)
+
+
+def pd_read_bond_status(pd):
+    i = pd_info(pd)
+    mu = np.empty(i["n_bonds"], dtype=np.uint8)
+    cnt = _I64()
+    _check(load().pd_read_bond_status(pd, _ptr(mu), C.byref(cnt)), "pd_read_bond_status")
+    return mu, cnt.value
+
+
+def pd_read_family(pd):
+    i = pd_info(pd)
+    rp = np.empty(i["n"] + 1, dtype=np.int64)
+    col = np.empty(max(i["n_bonds"], 1), dtype=np.int32)
+    _check(load().pd_read_family(pd, _ptr(rp), _ptr(col)), "pd_read_family")
+    return rp, col[: i["n_bonds"]]
+
+
+# ------------------------------------------------------------------- time
+def mts_set_time(ctx, dt_pd, m_ratio=1, gamma_fe=0.5, beta_fe=0.25, check_stability=True):
+    _check(load().mts_set_time(ctx, float(dt_pd), int(m_ratio), float(gamma_fe), float(beta_fe),
+                               int(bool(check_stability))), "mts_set_time")
+
+
+def mts_advance(ctx, n_coarse):
+    _check(load().mts_advance(ctx, int(n_coarse)), "mts_advance")
