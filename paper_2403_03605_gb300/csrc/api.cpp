@@ -661,15 +661,19 @@ int pdmts_pd::upload_weights_and_loads()
     return PDMTS_OK;
 }
 
-// One substep on the current state: forces at u[cur] (with breaking), a, v,
-// and the predicted displacement into u[1 - cur]; then the buffers swap.
-// With init, a is computed from u[cur] and u[1 - cur] = u + dt v + dt^2/2 a,
-// and the buffers do not swap (u[cur] stays the current displacement).
+// One substep. u[cur] holds the displacement at the current time and
+// u[1 - cur] its velocity-Verlet prediction for the next time. A substep
+// evaluates forces (with breaking) at the prediction u[1 - cur], updates a and
+// v, writes the following prediction over the old u[cur], and swaps, so that
+// cur again names the current time. With init, a is computed from u[cur] and
+// the first prediction u + dt v + dt^2/2 a is written to u[1 - cur]; no swap.
 int pdmts_pd::step(bool init, double theta, cudaStream_t s)
 {
     const double dt = ctx->dt_pd;
     cudaError_t e;
     SellView fam{d_tile_ptr.p, d_tile_k.p, d_mask_ptr.p, d_col.p, d_mask.p, d_deg.p, n, ntiles};
+    const int src = init ? cur : 1 - cur;  // buffer the forces are evaluated at
+    const int dst = 1 - src;               // buffer receiving the next prediction
     if (precision == PDMTS_FP64) {
         F64StepArgs A{};
         A.fam = fam;
@@ -680,8 +684,8 @@ int pdmts_pd::step(bool init, double theta, cudaStream_t s)
         A.mass = d_mass.p;
         A.wb = d_wb.p;
         A.g = d_g.p;
-        A.u_in = d_u[cur].p;
-        A.u_out = d_u[1 - cur].p;
+        A.u_in = d_u[src].p;
+        A.u_out = d_u[dst].p;
         A.v = d_v.p;
         A.a = d_a.p;
         A.s0p2 = (1.0 + s0) * (1.0 + s0);
@@ -702,10 +706,10 @@ int pdmts_pd::step(bool init, double theta, cudaStream_t s)
         A.inv_m = f_invm.p;
         A.wb = f_wb.p;
         A.g = f_g.p;
-        A.u4_in = f_u4[cur].p;
-        A.u2_in = f_u2[cur].p;
-        A.u4_out = f_u4[1 - cur].p;
-        A.u2_out = f_u2[1 - cur].p;
+        A.u4_in = f_u4[src].p;
+        A.u2_in = f_u2[src].p;
+        A.u4_out = f_u4[dst].p;
+        A.u2_out = f_u2[dst].p;
         A.v4 = f_v4.p;
         A.v2 = f_v2.p;
         A.a = f_a.p;
