@@ -98,11 +98,16 @@ class ClockSampler:
 
 
 def algorithmic_bytes(info, pb, with_body=True):
-    """Bytes one FP32-bulk 2D substep must move with this layout: per directed
-    bond a 4-byte family word and one status bit; per node u (16 in, 16 out),
-    v (16 in, 16 out), a (8 in, 8 out), 1/m (4), the weighted body force (8)."""
+    """Bytes one FP32-bulk 2D substep must move with the family layout in use.
+
+    Per node: u (16 in, 16 out), v (16 in, 16 out), a (8 in, 8 out), 1/m (4),
+    weighted body force (8). Lattice layout: the family is implicit and the
+    node's 32-bit bond word (one bit per bond) is read once. Sliced-ELL
+    layout: per directed bond a 4-byte family word and one status bit."""
     nb, n = info["n_bonds"], info["n"]
     per_node = 16 + 16 + 16 + 16 + 8 + 8 + 4 + (8 if with_body else 0)
+    if info["layout"] == 1:
+        return (per_node + 4) * n, per_node + 4
     return 4 * nb + nb / 8.0 + per_node * n, per_node
 
 
@@ -251,12 +256,14 @@ def run_ours(args, rank, world, local_rank):
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD["name"], "nodes": pb.n, "bonds": info["n_bonds"], "m": m,
+                       "family_layout": "lattice bond words" if info["layout"] == 1 else "sliced ELL",
                        "substeps_per_step": m, "graph": "one captured graph per step",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                       "l2": "flushed between timed steps (256 MB write); working set 166 MB"},
+                       "l2": "flushed between timed steps (256 MB write)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                         "kernel": "k_pd_step_f32<2>", "algorithmic_bytes_per_launch": abytes,
+                         "kernel": "k_pd_step_lattice2d<false>" if info["layout"] == 1 else "k_pd_step_f32<2>",
+                         "algorithmic_bytes_per_launch": abytes,
                          "launch_us": launch_ms * 1e3},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(b_host.numel() * 8),

@@ -45,7 +45,11 @@ extern "C" {
 /* ---- enumerations -------------------------------------------------------- */
 #define PDMTS_FP64 0      /* all PD arithmetic in IEEE FP64, fixed summation order, no FMA  */
 #define PDMTS_FP32_BULK 1 /* bond stretch/force in FP32 from displacement differences;
-                             u, v carried as compensated FP32 pairs (needs lattice nodes) */
+                             u, v carried as compensated FP32 pairs (needs lattice nodes).
+                             On a full 2D rectangle with 3 h <= delta < sqrt(10) h the
+                             family is stored as one 28-bit word per node (lattice kernel);
+                             otherwise as a sliced-ELL neighbour list                      */
+#define PDMTS_FP32_BULK_SELL 2 /* FP32 bulk arithmetic, always on the sliced-ELL list     */
 
 #define PDMTS_MICRO_POWER 0 /* c(|xi|) = c / |xi|^3  (linearised PMB constant)           */
 #define PDMTS_MICRO_EXP 1   /* c(|xi|) = c exp(-|xi| / l)                                 */
@@ -141,6 +145,10 @@ typedef struct {
     int64_t n_slots;       /* stored slots of the sliced-ELL layout        */
     int32_t max_degree;    /* largest family                               */
     int32_t on_lattice;    /* 1 if the nodes lie on a regular lattice      */
+    int32_t layout;        /* 0: sliced-ELL list; 1: 2D lattice bond words */
+    int32_t lattice_nx;    /* lattice layout: nodes along x                */
+    int32_t lattice_ny;    /* lattice layout: nodes along y                */
+    int32_t reserved;
     double lattice_h;      /* lattice spacing (0 if not on a lattice)      */
     int64_t steps_done;    /* PD substeps advanced since creation          */
     int64_t device_bytes;  /* device memory held by this subdomain         */

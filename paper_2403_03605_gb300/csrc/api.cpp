@@ -291,7 +291,7 @@ void pdmts_pd::release_all()
 {
     pd_invalidate_graphs(this);
     release(d_tile_ptr); release(d_mask_ptr); release(d_tile_k); release(d_col); release(d_deg);
-    release(d_mask); release(d_V); release(d_out); release(d_b);
+    release(d_mask); release(d_V); release(d_out); release(d_b); release(d_exists);
     release(d_X); release(d_cb); release(d_alpha); release(d_mass); release(d_wb); release(d_g);
     release(d_v); release(d_a); release(d_u[0]); release(d_u[1]);
     release(d_stencil); release(f_alpha); release(f_invm); release(f_wb); release(f_g);
@@ -457,6 +457,75 @@ static void build_sell(pdmts_pd *pd)
     }
 }
 
+// Word and bit of the k-th CSR bond of node i in the device bond-status array.
+static inline void bond_bit(const pdmts_pd *pd, int64_t i, int32_t k, int64_t &word, int &bit)
+{
+    if (pd->layout == pdmts_pd::LAYOUT_LATTICE2D) {
+        word = i;
+        bit = pd->slot_of_csr[(size_t)(pd->row_ptr[(size_t)i] + k)];
+    } else {
+        word = pd->mask_ptr[(size_t)(i / 32)] + 32 * (k / 32) + (i % 32);
+        bit = k % 32;
+    }
+}
+
+// The 2D lattice layout applies when the nodes are exactly the nx * ny
+// rectangle numbered x + nx y and every family is the 28-offset stencil
+// clipped to the rectangle. Builds the per-node bond words on success.
+static bool try_lattice2d(pdmts_pd *pd)
+{
+    if (pd->dim != 2 || !pd->on_lattice)
+        return false;
+    const int64_t n = pd->n;
+    int32_t nx = 0, ny = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        nx = std::max(nx, pd->lk[(size_t)i] + 1);
+        ny = std::max(ny, pd->lk[(size_t)n + i] + 1);
+    }
+    if ((int64_t)nx * ny != n)
+        return false;
+    for (int64_t i = 0; i < n; ++i)
+        if (pd->lk[(size_t)i] + (int64_t)nx * pd->lk[(size_t)n + i] != i)
+            return false;
+    // stencil slot of every offset, then every family must be stencil ∩ rectangle
+    int slot_of[7][7];
+    for (auto &r : slot_of)
+        for (int &v : r)
+            v = -1;
+    for (int k = 0; k < lat2d::NS; ++k)
+        slot_of[lat2d::DY(k) + 3][lat2d::DX(k) + 3] = k;
+    std::vector<int8_t> slot((size_t)pd->row_ptr[(size_t)n]);
+    std::vector<uint32_t> words((size_t)n, 0u);
+    for (int64_t i = 0; i < n; ++i) {
+        const int xi = pd->lk[(size_t)i], yi = pd->lk[(size_t)n + i];
+        for (int64_t k = pd->row_ptr[(size_t)i]; k < pd->row_ptr[(size_t)i + 1]; ++k) {
+            const int64_t j = pd->col[(size_t)k];
+            const int ox = pd->lk[(size_t)j] - xi, oy = pd->lk[(size_t)n + j] - yi;
+            if (ox < -3 || ox > 3 || oy < -3 || oy > 3 || slot_of[oy + 3][ox + 3] < 0)
+                return false;
+            slot[(size_t)k] = (int8_t)slot_of[oy + 3][ox + 3];
+            words[(size_t)i] |= 1u << slot_of[oy + 3][ox + 3];
+        }
+        int expect = 0;
+        for (int k = 0; k < lat2d::NS; ++k) {
+            const int x = xi + lat2d::DX(k), y = yi + lat2d::DY(k);
+            expect += (x >= 0 && x < nx && y >= 0 && y < ny);
+        }
+        if (expect != pd->row_ptr[(size_t)i + 1] - pd->row_ptr[(size_t)i])
+            return false;
+    }
+    pd->layout = pdmts_pd::LAYOUT_LATTICE2D;
+    pd->lat_dims[0] = nx;
+    pd->lat_dims[1] = ny;
+    pd->slot_of_csr.swap(slot);
+    pd->mask_host.swap(words);
+    pd->n_mask_words = n;
+    pd->max_deg = 0;
+    for (int64_t i = 0; i < n; ++i)
+        pd->max_deg = std::max<int32_t>(pd->max_deg, (int32_t)(pd->row_ptr[(size_t)i + 1] - pd->row_ptr[(size_t)i]));
+    return true;
+}
+
 static double micromodulus_host(const pdmts_pd *pd, double xi2)
 {
     double r = std::sqrt(xi2);
@@ -466,11 +535,23 @@ static double micromodulus_host(const pdmts_pd *pd, double xi2)
 }
 
 // Device arrays of the family and the state.
+static int alloc_f32_state(pdmts_pd *pd);
+
 static int upload_family_and_state(pdmts_pd *pd)
 {
     cudaStream_t s = pd->ctx->stream;
     const int dim = pd->dim;
     const int64_t n = pd->n;
+    if (pd->layout == pdmts_pd::LAYOUT_LATTICE2D) {
+        PDMTS_TRY(pd->alloc(pd->d_mask, n));
+        PDMTS_TRY(pd->alloc(pd->d_exists, n));
+        PDMTS_TRY(pd->alloc(pd->d_V, n));
+        PDMTS_TRY(pd->alloc(pd->d_out, (int64_t)dim * n));
+        PDMTS_TRY(upload(pd->d_mask, pd->mask_host.data(), n, s));
+        PDMTS_TRY(upload(pd->d_exists, pd->mask_host.data(), n, s));
+        PDMTS_TRY(upload(pd->d_V, pd->V.data(), n, s));
+        return alloc_f32_state(pd);
+    }
     PDMTS_TRY(pd->alloc(pd->d_tile_ptr, pd->ntiles + 1));
     PDMTS_TRY(pd->alloc(pd->d_mask_ptr, pd->ntiles + 1));
     PDMTS_TRY(pd->alloc(pd->d_tile_k, pd->ntiles));
@@ -577,24 +658,33 @@ static int upload_family_and_state(pdmts_pd *pd)
         PDMTS_TRY(pd->alloc(pd->d_stencil, std::max<int64_t>(pd->n_stencil, 1)));
         PDMTS_TRY(upload(pd->d_stencil, table.data(), pd->n_stencil, s));
         PDMTS_TRY(upload(pd->d_col, colS.data(), pd->n_slots, s));
-        const int adim = dim == 2 ? 2 : 4;
-        for (int b = 0; b < 2; ++b) {
-            PDMTS_TRY(pd->alloc(pd->f_u4[b], n));
-            PDMTS_CUDA_TRY(cudaMemsetAsync(pd->f_u4[b].p, 0, sizeof(float4) * n, s));
-            if (dim == 3) {
-                PDMTS_TRY(pd->alloc(pd->f_u2[b], n));
-                PDMTS_CUDA_TRY(cudaMemsetAsync(pd->f_u2[b].p, 0, sizeof(float2) * n, s));
-            }
-        }
-        PDMTS_TRY(pd->alloc(pd->f_v4, n));
-        PDMTS_CUDA_TRY(cudaMemsetAsync(pd->f_v4.p, 0, sizeof(float4) * n, s));
-        if (dim == 3) {
-            PDMTS_TRY(pd->alloc(pd->f_v2, n));
-            PDMTS_CUDA_TRY(cudaMemsetAsync(pd->f_v2.p, 0, sizeof(float2) * n, s));
-        }
-        PDMTS_TRY(pd->alloc(pd->f_a, (int64_t)adim * n));
-        PDMTS_CUDA_TRY(cudaMemsetAsync(pd->f_a.p, 0, sizeof(float) * adim * n, s));
+        PDMTS_TRY(alloc_f32_state(pd));
     }
+    return PDMTS_OK;
+}
+
+static int alloc_f32_state(pdmts_pd *pd)
+{
+    cudaStream_t s = pd->ctx->stream;
+    const int dim = pd->dim;
+    const int64_t n = pd->n;
+    const int adim = dim == 2 ? 2 : 4;
+    for (int b = 0; b < 2; ++b) {
+        PDMTS_TRY(pd->alloc(pd->f_u4[b], n));
+        PDMTS_CUDA_TRY(cudaMemsetAsync(pd->f_u4[b].p, 0, sizeof(float4) * n, s));
+        if (dim == 3) {
+            PDMTS_TRY(pd->alloc(pd->f_u2[b], n));
+            PDMTS_CUDA_TRY(cudaMemsetAsync(pd->f_u2[b].p, 0, sizeof(float2) * n, s));
+        }
+    }
+    PDMTS_TRY(pd->alloc(pd->f_v4, n));
+    PDMTS_CUDA_TRY(cudaMemsetAsync(pd->f_v4.p, 0, sizeof(float4) * n, s));
+    if (dim == 3) {
+        PDMTS_TRY(pd->alloc(pd->f_v2, n));
+        PDMTS_CUDA_TRY(cudaMemsetAsync(pd->f_v2.p, 0, sizeof(float2) * n, s));
+    }
+    PDMTS_TRY(pd->alloc(pd->f_a, (int64_t)adim * n));
+    PDMTS_CUDA_TRY(cudaMemsetAsync(pd->f_a.p, 0, sizeof(float) * adim * n, s));
     return PDMTS_OK;
 }
 
@@ -698,30 +788,46 @@ int pdmts_pd::step(bool init, double theta, cudaStream_t s)
         A.broken = ctx->d_counter;
         e = launch_pd_step_f64(dim, A, init, s);
     } else {
-        F32StepArgs A{};
-        A.fam = fam;
-        A.stencil = d_stencil.p;
-        A.n_stencil = n_stencil;
-        A.alpha = f_alpha.p;
-        A.inv_m = f_invm.p;
-        A.wb = f_wb.p;
-        A.g = f_g.p;
-        A.u4_in = f_u4[src].p;
-        A.u2_in = f_u2[src].p;
-        A.u4_out = f_u4[dst].p;
-        A.u2_out = f_u2[dst].p;
-        A.v4 = f_v4.p;
-        A.v2 = f_v2.p;
-        A.a = f_a.p;
-        A.dt = (float)dt;
-        A.hdt = (float)(0.5 * dt);
-        A.hdt2 = (float)(0.5 * dt * dt);
-        A.theta = (float)theta;
-        A.s0 = (float)s0;
-        A.breaking = breaking ? 1 : 0;
-        A.pmb = force_kind == PDMTS_FORCE_PMB;
-        A.broken = ctx->d_counter;
-        e = launch_pd_step_f32(dim, A, init, s);
+        F32NodeArgs N{};
+        N.n = n;
+        N.inv_m = f_invm.p;
+        N.wb = f_wb.p;
+        N.g = f_g.p;
+        N.u4_in = f_u4[src].p;
+        N.u2_in = f_u2[src].p;
+        N.u4_out = f_u4[dst].p;
+        N.u2_out = f_u2[dst].p;
+        N.v4 = f_v4.p;
+        N.v2 = f_v2.p;
+        N.a = f_a.p;
+        N.dt = (float)dt;
+        N.hdt = (float)(0.5 * dt);
+        N.hdt2 = (float)(0.5 * dt * dt);
+        N.theta = (float)theta;
+        N.breaking = breaking ? 1 : 0;
+        N.pmb = force_kind == PDMTS_FORCE_PMB;
+        N.broken = ctx->d_counter;
+        if (layout == LAYOUT_LATTICE2D) {
+            Lat2DArgs A{};
+            A.nx = lat_dims[0];
+            A.ny = lat_dims[1];
+            A.mask = d_mask.p;
+            A.alpha = f_alpha.p;
+            for (int r2 = 0; r2 < 10; ++r2) {
+                A.coef[r2] = r2 > 0 ? (float)(micromodulus_host(this, r2 * h * h) * h * h * V[0]) : 0.f;
+                A.thr[r2] = (float)(s0 * (2.0 + s0) * r2);
+            }
+            A.nd = N;
+            e = launch_pd_step_lattice2d(A, init, s);
+        } else {
+            F32StepArgs A{};
+            A.fam = fam;
+            A.stencil = d_stencil.p;
+            A.n_stencil = n_stencil;
+            A.alpha = f_alpha.p;
+            A.nd = N;
+            e = launch_pd_step_f32(dim, A, init, s);
+        }
     }
     if (e != cudaSuccess)
         return fail(PDMTS_ERR_CUDA, "PD substep launch failed: %s", cudaGetErrorString(e));
@@ -771,8 +877,11 @@ extern "C" int pd_create(pdmts_ctx *ctx, int dim, int64_t n, const double *X, co
         return fail(PDMTS_ERR_ARG, "pd_create: unknown micromodulus kind %d", micro_kind);
     if (micro_kind == PDMTS_MICRO_EXP && !(l > 0))
         return fail(PDMTS_ERR_ARG, "pd_create: exponential micromodulus needs l > 0");
-    if (precision != PDMTS_FP64 && precision != PDMTS_FP32_BULK)
+    if (precision != PDMTS_FP64 && precision != PDMTS_FP32_BULK && precision != PDMTS_FP32_BULK_SELL)
         return fail(PDMTS_ERR_ARG, "pd_create: unknown precision %d", precision);
+    const bool force_sell = precision == PDMTS_FP32_BULK_SELL;
+    if (force_sell)
+        precision = PDMTS_FP32_BULK;
     if (!vol && !(vol_uniform > 0))
         return fail(PDMTS_ERR_ARG, "pd_create: vol_uniform must be > 0 when vol is NULL");
     PDMTS_CUDA_TRY(cudaSetDevice(ctx->device));
@@ -818,7 +927,8 @@ extern "C" int pd_create(pdmts_ctx *ctx, int dim, int64_t n, const double *X, co
         }
     }
     if (r == PDMTS_OK) {
-        build_sell(pd);
+        if (precision == PDMTS_FP64 || force_sell || !try_lattice2d(pd))
+            build_sell(pd);
         r = upload_family_and_state(pd);
     }
     if (r == PDMTS_OK)
@@ -903,8 +1013,8 @@ extern "C" int pd_set_precrack(pdmts_pd *pd, int n_cuts, const double *cuts)
                                    cudaMemcpyDeviceToHost, pd->ctx->stream));
     PDMTS_CUDA_TRY(cudaStreamSynchronize(pd->ctx->stream));
     for (int64_t i = 0; i < n; ++i) {
-        int64_t t = i / 32, lane = i % 32;
-        for (int32_t k = 0; k < pd->deg[(size_t)i]; ++k) {
+        const int32_t deg_i = (int32_t)(pd->row_ptr[(size_t)i + 1] - pd->row_ptr[(size_t)i]);
+        for (int32_t k = 0; k < deg_i; ++k) {
             int64_t j = pd->col[(size_t)(pd->row_ptr[(size_t)i] + k)];
             bool cut = false;
             for (const CutI &q : cl) {
@@ -936,8 +1046,12 @@ extern "C" int pd_set_precrack(pdmts_pd *pd, int n_cuts, const double *cuts)
                 if (cut)
                     break;
             }
-            if (cut)
-                pd->mask_host[(size_t)(pd->mask_ptr[(size_t)t] + 32 * (k / 32) + lane)] &= ~(1u << (k % 32));
+            if (cut) {
+                int64_t word;
+                int bit;
+                bond_bit(pd, i, k, word, bit);
+                pd->mask_host[(size_t)word] &= ~(1u << bit);
+            }
         }
     }
     PDMTS_CUDA_TRY(cudaMemcpyAsync(pd->d_mask.p, pd->mask_host.data(), sizeof(uint32_t) * pd->n_mask_words,
@@ -1125,6 +1239,10 @@ extern "C" int pd_info(const pdmts_pd *pd, pdmts_pd_info *info)
     info->n_slots = pd->n_slots;
     info->max_degree = pd->max_deg;
     info->on_lattice = pd->on_lattice ? 1 : 0;
+    info->layout = pd->layout;
+    info->lattice_nx = pd->lat_dims[0];
+    info->lattice_ny = pd->lat_dims[1];
+    info->reserved = 0;
     info->lattice_h = pd->on_lattice ? pd->h : 0.0;
     info->steps_done = pd->steps_done;
     info->device_bytes = pd->device_bytes;
@@ -1184,7 +1302,9 @@ extern "C" int pd_read_damage(pdmts_pd *pd, double *phi)
     cudaStream_t s = pd->ctx->stream;
     SellView fam{pd->d_tile_ptr.p, pd->d_tile_k.p, pd->d_mask_ptr.p, pd->d_col.p, pd->d_mask.p, pd->d_deg.p,
                  pd->n, pd->ntiles};
-    cudaError_t e = launch_damage(fam, pd->precision == PDMTS_FP32_BULK, pd->d_V.p, pd->d_out.p, s);
+    cudaError_t e = pd->layout == pdmts_pd::LAYOUT_LATTICE2D
+                        ? launch_damage_lattice(pd->n, pd->d_mask.p, pd->d_exists.p, 1, pd->d_out.p, s)
+                        : launch_damage(fam, pd->precision == PDMTS_FP32_BULK, pd->d_V.p, pd->d_out.p, s);
     if (e != cudaSuccess)
         return fail(PDMTS_ERR_CUDA, "damage kernel failed: %s", cudaGetErrorString(e));
     pd->ctx->stats.kernel_launches++;
@@ -1207,10 +1327,12 @@ extern "C" int pd_read_bond_status(pdmts_pd *pd, uint8_t *mu, int64_t *n_intact)
     std::vector<uint8_t> st((size_t)pd->row_ptr[(size_t)pd->n]);
     int64_t intact = 0;
     for (int64_t i = 0; i < pd->n; ++i) {
-        int64_t t = i / 32, lane = i % 32;
-        for (int32_t k = 0; k < pd->deg[(size_t)i]; ++k) {
-            uint32_t w = pd->mask_host[(size_t)(pd->mask_ptr[(size_t)t] + 32 * (k / 32) + lane)];
-            uint8_t bit = (uint8_t)((w >> (k % 32)) & 1u);
+        const int32_t deg_i = (int32_t)(pd->row_ptr[(size_t)i + 1] - pd->row_ptr[(size_t)i]);
+        for (int32_t k = 0; k < deg_i; ++k) {
+            int64_t word;
+            int b;
+            bond_bit(pd, i, k, word, b);
+            uint8_t bit = (uint8_t)((pd->mask_host[(size_t)word] >> b) & 1u);
             st[(size_t)(pd->row_ptr[(size_t)i] + k)] = bit;
             intact += bit;
         }

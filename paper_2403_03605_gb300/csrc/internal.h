@@ -82,11 +82,10 @@ struct StencilEntry {
 };
 constexpr int kMaxStencil = 256;
 
-struct F32StepArgs {
-    SellView fam;               // col = (j << 8) | stencil id
-    const StencilEntry *stencil;// [n_stencil]
-    int n_stencil;
-    const float *alpha;         // n (null when no weights)
+// Per-node arrays and constants of the FP32-bulk update (shared by the
+// sliced-ELL and the lattice kernels).
+struct F32NodeArgs {
+    int64_t n;
     const float *inv_m;         // n: 1 / ((1 - alpha) rho)
     const float *wb;            // dim * n: (1 - alpha) b / h (null when none)
     const float *g;             // dim * n: interface force per volume / h (null when none)
@@ -100,16 +99,57 @@ struct F32StepArgs {
     float2 *v2;
     float *a;                   // 2D: float2 {ax, ay}; 3D: float4 {ax, ay, az, 0}; in place
     float dt, hdt, hdt2, theta;
-    float s0;                   // critical stretch (PMB law)
     int breaking;
     int pmb;
     unsigned long long *broken;
+};
+
+struct F32StepArgs {
+    SellView fam;               // col = (j << 8) | stencil id
+    const StencilEntry *stencil;// [n_stencil]
+    int n_stencil;
+    const float *alpha;         // n (null when no weights)
+    F32NodeArgs nd;
+};
+
+// The 28-offset family of a 2D lattice with 3 h <= delta < sqrt(10) h, in
+// ascending neighbour-index order for row-major (x fastest) numbering, i.e.
+// sorted by (dy, dx). Bit k of a node's bond word is offset k.
+namespace lat2d {
+constexpr int NS = 28;
+constexpr int R = 3;
+__host__ __device__ constexpr int DX(int k)
+{
+    constexpr int t[NS] = {0, -2, -1, 0, 1, 2, -2, -1, 0, 1, 2, -3, -2, -1, 1, 2, 3, -2, -1, 0, 1, 2, -2, -1, 0, 1, 2, 0};
+    return t[k];
+}
+__host__ __device__ constexpr int DY(int k)
+{
+    constexpr int t[NS] = {-3, -2, -2, -2, -2, -2, -1, -1, -1, -1, -1, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 2, 2, 2, 2, 2, 3};
+    return t[k];
+}
+}  // namespace lat2d
+
+// Lattice kernel: nodes form a full nx * ny rectangle numbered i = x + nx y;
+// the bond word mask[i] has bit k set while the bond to (x + DX[k], y + DY[k])
+// exists and is intact. coef / thr are indexed by |d|^2 (0..9).
+struct Lat2DArgs {
+    int nx, ny;
+    uint32_t *mask;
+    const float *alpha;         // n (null when no weights)
+    float coef[10];             // c(|xi|) h^2 V by |d|^2
+    float thr[10];              // s0 (2 + s0) |d|^2
+    F32NodeArgs nd;
 };
 
 // Launchers (pd_kernels.cu). `init` computes a_0 from u_0 and predicts u_1
 // without touching v.
 cudaError_t launch_pd_step_f64(int dim, const F64StepArgs &A, bool init, cudaStream_t s);
 cudaError_t launch_pd_step_f32(int dim, const F32StepArgs &A, bool init, cudaStream_t s);
+cudaError_t launch_pd_step_lattice2d(const Lat2DArgs &A, bool init, cudaStream_t s);
+// Damage of the lattice layout (uniform volume): 1 - popc(intact) / popc(exists).
+cudaError_t launch_damage_lattice(int64_t n, const uint32_t *mask, const uint32_t *exists, int words,
+                                  double *phi, cudaStream_t s);
 cudaError_t launch_damage(const SellView &fam, int packed, const double *V, double *phi, cudaStream_t s);
 // Unpack a packed FP32 state field (u4/u2 or v4/v2 pairs, or a with u2 ==
 // null and `accel`) into dim * n doubles scaled by h.

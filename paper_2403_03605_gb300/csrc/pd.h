@@ -35,6 +35,13 @@ struct pdmts_pd {
     std::array<double, 3> x0{0, 0, 0};
     std::vector<int32_t> lk;  // dim * n integer lattice coordinates
 
+    // family layout: sliced ELL (general) or the 2D lattice stencil
+    enum { LAYOUT_SELL = 0, LAYOUT_LATTICE2D = 1 };
+    int layout = LAYOUT_SELL;
+    int32_t lat_dims[3] = {0, 0, 0};      // nodes per axis (lattice layout)
+    std::vector<int8_t> slot_of_csr;      // lattice layout: stencil slot of each CSR bond
+    DevArr<uint32_t> d_exists;            // lattice layout: existing-bond bits per node
+
     // sliced-ELL layout
     int64_t ntiles = 0, n_slots = 0, n_mask_words = 0;
     int32_t max_deg = 0;

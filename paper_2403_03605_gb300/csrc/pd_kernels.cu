@@ -186,6 +186,82 @@ __device__ __forceinline__ void store_pair(float4 *p4, float2 *p2, int64_t i, co
     }
 }
 
+// Per-node part of an FP32-bulk substep: a = (f + wb + theta g) / m,
+// v += dt/2 (a_old + a), next prediction u + dt v + dt^2/2 a (lattice units).
+template <int DIM>
+__device__ __forceinline__ void finish_node_f32(const F32NodeArgs &N, const int64_t i, const float (&f)[DIM],
+                                                float (&uh)[DIM], float (&ul)[DIM], const int init)
+{
+    const int64_t n = N.n;
+    const float im = N.inv_m[i];
+    float an[DIM], ao[DIM];
+    if constexpr (DIM == 2) {
+        const float2 q = reinterpret_cast<const float2 *>(N.a)[i];
+        ao[0] = q.x; ao[1] = q.y;
+    } else {
+        const float4 q = reinterpret_cast<const float4 *>(N.a)[i];
+        ao[0] = q.x; ao[1] = q.y; ao[2] = q.z;
+    }
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+        float t = f[d];
+        if (N.wb)
+            t += N.wb[d * n + i];
+        if (N.g)
+            t = fmaf(N.theta, N.g[d * n + i], t);
+        an[d] = t * im;
+    }
+    float vh[DIM], vl[DIM];
+    load_pair<DIM>(N.v4, N.v2, i, vh, vl);
+    if (!init) {
+#pragma unroll
+        for (int d = 0; d < DIM; ++d)
+            df_add(vh[d], vl[d], N.hdt * (ao[d] + an[d]));
+        store_pair<DIM>(N.v4, N.v2, i, vh, vl);
+    }
+    if constexpr (DIM == 2)
+        reinterpret_cast<float2 *>(N.a)[i] = make_float2(an[0], an[1]);
+    else
+        reinterpret_cast<float4 *>(N.a)[i] = make_float4(an[0], an[1], an[2], 0.f);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d)
+        df_add(uh[d], ul[d], fmaf(N.dt, vh[d], fmaf(N.dt, vl[d], N.hdt2 * an[d])));
+    store_pair<DIM>(N.u4_out, N.u2_out, i, uh, ul);
+}
+
+__device__ __forceinline__ void count_broken(unsigned long long *counter, unsigned nbroken)
+{
+    if (counter) {
+        const unsigned tot = __reduce_add_sync(0xffffffffu, nbroken);
+        if ((threadIdx.x & 31) == 0 && tot)
+            atomicAdd(counter, (unsigned long long)tot);
+    }
+}
+
+// Bond kinematics of the FP32 path in lattice units: offset d, relative
+// displacement eta. dot = d.eta is formed as fma(d_last, eta_last, ...) from
+// the first component up, the same expression at both ends of a bond, so
+// the breaking decision of (i, j) and (j, i) is identical.
+template <int DIM>
+__device__ __forceinline__ float bond_dot(const float (&d)[3], const float (&eta)[DIM])
+{
+    float dot = d[0] * eta[0];
+#pragma unroll
+    for (int k = 1; k < DIM; ++k)
+        dot = fmaf(d[k], eta[k], dot);
+    return dot;
+}
+
+template <int DIM>
+__device__ __forceinline__ float eta_sq(const float (&eta)[DIM])
+{
+    float e2 = eta[0] * eta[0];
+#pragma unroll
+    for (int k = 1; k < DIM; ++k)
+        e2 = fmaf(eta[k], eta[k], e2);
+    return e2;
+}
+
 template <int DIM>
 __global__ void __launch_bounds__(256) k_pd_step_f32(const F32StepArgs A, const int init)
 {
@@ -198,6 +274,7 @@ __global__ void __launch_bounds__(256) k_pd_step_f32(const F32StepArgs A, const 
     }
     __syncthreads();
 
+    const F32NodeArgs &N = A.nd;
     const int lane = threadIdx.x & 31;
     const int64_t tile = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (tile >= A.fam.ntiles)
@@ -212,7 +289,7 @@ __global__ void __launch_bounds__(256) k_pd_step_f32(const F32StepArgs A, const 
     const uint32_t *col = reinterpret_cast<const uint32_t *>(A.fam.col);
 
     float uh[DIM], ul[DIM], f[DIM];
-    load_pair<DIM>(A.u4_in, A.u2_in, ii, uh, ul);
+    load_pair<DIM>(N.u4_in, N.u2_in, ii, uh, ul);
 #pragma unroll
     for (int d = 0; d < DIM; ++d)
         f[d] = 0.f;
@@ -234,28 +311,22 @@ __global__ void __launch_bounds__(256) k_pd_step_f32(const F32StepArgs A, const 
             const float4 sd = s_d[sid];
             const float4 st = s_t[sid];
             float jh[DIM], jl[DIM], eta[DIM];
-            load_pair<DIM>(A.u4_in, A.u2_in, j, jh, jl);
+            load_pair<DIM>(N.u4_in, N.u2_in, j, jh, jl);
 #pragma unroll
             for (int d = 0; d < DIM; ++d)
                 eta[d] = (jh[d] - uh[d]) + (jl[d] - ul[d]);
             const float dd[3] = {sd.x, sd.y, sd.z};
-            float dot = dd[0] * eta[0];
-            float e2 = eta[0] * eta[0];
-#pragma unroll
-            for (int d = 1; d < DIM; ++d) {
-                dot = fmaf(dd[d], eta[d], dot);
-                e2 = fmaf(eta[d], eta[d], e2);
-            }
+            const float dot = bond_dot<DIM>(dd, eta);
             // |xi + eta|^2 - |xi|^2 = h^2 (2 d.eta + |eta|^2) >= ((1+s0)^2 - 1)|xi|^2
-            const float lhs = fmaf(2.f, dot, e2);
-            if (A.breaking && lhs >= st.x) {
+            const float lhs = fmaf(2.f, dot, eta_sq<DIM>(eta));
+            if (N.breaking && lhs >= st.x) {
                 m &= ~(1u << kk);
                 continue;
             }
             float coef = sd.w;
             if (A.alpha)
                 coef *= 1.f - 0.5f * (ai + A.alpha[j]);
-            if (A.pmb) {
+            if (N.pmb) {
                 // s = (|d + eta| - |d|)/|d| = lhs / ((ry + rd) rd), force along d + eta
                 const float ry = sqrtf(st.z + lhs);
                 const float sc = coef * st.z * lhs / ((ry + st.y) * ry);
@@ -263,10 +334,10 @@ __global__ void __launch_bounds__(256) k_pd_step_f32(const F32StepArgs A, const 
                 for (int d = 0; d < DIM; ++d)
                     f[d] = fmaf(sc, dd[d] + eta[d], f[d]);
             } else {
-                const float s = coef * dot;
+                const float sc = coef * dot;
 #pragma unroll
                 for (int d = 0; d < DIM; ++d)
-                    f[d] = fmaf(s, dd[d], f[d]);
+                    f[d] = fmaf(sc, dd[d], f[d]);
             }
         }
         if (m != m0) {
@@ -274,47 +345,92 @@ __global__ void __launch_bounds__(256) k_pd_step_f32(const F32StepArgs A, const 
             nbroken += __popc(m0 ^ m);
         }
     }
-    if (A.broken) {
-        const unsigned tot = __reduce_add_sync(0xffffffffu, nbroken);
-        if (lane == 0 && tot)
-            atomicAdd(A.broken, (unsigned long long)tot);
-    }
+    count_broken(N.broken, nbroken);
     if (!valid)
         return;
-    const float im = A.inv_m[i];
-    float an[DIM], ao[DIM];
-    if constexpr (DIM == 2) {
-        const float2 q = reinterpret_cast<const float2 *>(A.a)[i];
-        ao[0] = q.x; ao[1] = q.y;
-    } else {
-        const float4 q = reinterpret_cast<const float4 *>(A.a)[i];
-        ao[0] = q.x; ao[1] = q.y; ao[2] = q.z;
+    finish_node_f32<DIM>(N, i, f, uh, ul, init);
+}
+
+// ---------------------------------------------------------- 2D lattice ----
+// A CTA owns a 32 x 8 node tile of the nx * ny lattice. Its displacement halo
+// (38 x 14 nodes, 8.5 KB) is loaded once into shared memory; every bond then
+// reads its neighbour from shared memory at a compile-time offset. The family
+// is implicit (offset k of the 28-offset stencil), so per bond only one bit of
+// the node's bond word is read from HBM.
+namespace lat2d {
+constexpr int TX = 32, TY = 8, HX = TX + 2 * R, HY = TY + 2 * R;
+}
+
+template <bool HAS_ALPHA>
+__global__ void __launch_bounds__(256) k_pd_step_lattice2d(const Lat2DArgs A, const int init)
+{
+    using namespace lat2d;
+    __shared__ float4 su[HY][HX];
+    __shared__ float salpha[HAS_ALPHA ? HY : 1][HAS_ALPHA ? HX : 1];
+    const F32NodeArgs &N = A.nd;
+    const int nx = A.nx, ny = A.ny;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    for (int q = threadIdx.x; q < HX * HY; q += blockDim.x) {
+        const int hy = q / HX, hx = q - hy * HX;
+        const int gx = x0 + hx - R, gy = y0 + hy - R;
+        const bool in = gx >= 0 && gx < nx && gy >= 0 && gy < ny;
+        const int64_t gi = (int64_t)gy * nx + gx;
+        su[hy][hx] = in ? N.u4_in[gi] : make_float4(0.f, 0.f, 0.f, 0.f);
+        if constexpr (HAS_ALPHA)
+            salpha[hy][hx] = in ? A.alpha[gi] : 0.f;
     }
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int x = x0 + tx, y = y0 + ty;
+    const bool valid = x < nx && y < ny;
+    const int64_t i = (int64_t)y * nx + x;
+    const uint32_t m0 = valid ? A.mask[i] : 0u;
+    __syncthreads();
+
+    const float4 ui = su[ty + R][tx + R];
+    const float ai = HAS_ALPHA ? salpha[ty + R][tx + R] : 0.f;
+    float f[2] = {0.f, 0.f};
+    uint32_t m = m0;
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-        float t = f[d];
-        if (A.wb)
-            t += A.wb[d * n + i];
-        if (A.g)
-            t = fmaf(A.theta, A.g[d * n + i], t);
-        an[d] = t * im;
+    for (int k = 0; k < NS; ++k) {
+        if (m0 & (1u << k)) {
+            const float4 uj = su[ty + R + DY(k)][tx + R + DX(k)];
+            float eta[2];
+            eta[0] = (uj.x - ui.x) + (uj.z - ui.z);
+            eta[1] = (uj.y - ui.y) + (uj.w - ui.w);
+            const float dd[3] = {(float)DX(k), (float)DY(k), 0.f};
+            const int r2 = DX(k) * DX(k) + DY(k) * DY(k);
+            const float dot = bond_dot<2>(dd, eta);
+            const float lhs = fmaf(2.f, dot, eta_sq<2>(eta));
+            if (N.breaking && lhs >= A.thr[r2]) {
+                m &= ~(1u << k);
+            } else {
+                float coef = A.coef[r2];
+                if constexpr (HAS_ALPHA)
+                    coef *= 1.f - 0.5f * (ai + salpha[ty + R + DY(k)][tx + R + DX(k)]);
+                if (N.pmb) {
+                    const float r2f = (float)r2;
+                    const float ry = sqrtf(r2f + lhs);
+                    const float sc = coef * r2f * lhs / ((ry + sqrtf(r2f)) * ry);
+                    f[0] = fmaf(sc, dd[0] + eta[0], f[0]);
+                    f[1] = fmaf(sc, dd[1] + eta[1], f[1]);
+                } else {
+                    const float sc = coef * dot;
+                    f[0] = fmaf(sc, dd[0], f[0]);
+                    f[1] = fmaf(sc, dd[1], f[1]);
+                }
+            }
+        }
     }
-    float vh[DIM], vl[DIM];
-    load_pair<DIM>(A.v4, A.v2, i, vh, vl);
-    if (!init) {
-#pragma unroll
-        for (int d = 0; d < DIM; ++d)
-            df_add(vh[d], vl[d], A.hdt * (ao[d] + an[d]));
-        store_pair<DIM>(A.v4, A.v2, i, vh, vl);
+    unsigned nbroken = 0;
+    if (m != m0) {
+        A.mask[i] = m;
+        nbroken = __popc(m0 ^ m);
     }
-    if constexpr (DIM == 2)
-        reinterpret_cast<float2 *>(A.a)[i] = make_float2(an[0], an[1]);
-    else
-        reinterpret_cast<float4 *>(A.a)[i] = make_float4(an[0], an[1], an[2], 0.f);
-#pragma unroll
-    for (int d = 0; d < DIM; ++d)
-        df_add(uh[d], ul[d], fmaf(A.dt, vh[d], fmaf(A.dt, vl[d], A.hdt2 * an[d])));
-    store_pair<DIM>(A.u4_out, A.u2_out, i, uh, ul);
+    count_broken(N.broken, nbroken);
+    if (!valid)
+        return;
+    float uh[2] = {ui.x, ui.y}, ul[2] = {ui.z, ui.w};
+    finish_node_f32<2>(N, i, f, uh, ul, init);
 }
 
 // ----------------------------------------------------------- damage (Eq. 5)
@@ -337,6 +453,20 @@ __global__ void k_damage(const SellView fam, const int packed, const double *__r
             num = __dadd_rn(num, V[j]);
     }
     phi[i] = den > 0.0 ? __dsub_rn(1.0, __ddiv_rn(num, den)) : 0.0;
+}
+
+__global__ void k_damage_lattice(const int64_t n, const uint32_t *__restrict__ mask,
+                                 const uint32_t *__restrict__ exists, const int words, double *__restrict__ phi)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n)
+        return;
+    int intact = 0, total = 0;
+    for (int w = 0; w < words; ++w) {
+        intact += __popc(mask[(int64_t)w * n + i]);
+        total += __popc(exists[(int64_t)w * n + i]);
+    }
+    phi[i] = total > 0 ? 1.0 - (double)intact / (double)total : 0.0;
 }
 
 __global__ void k_unpack(const int dim, const int64_t n, const float4 *__restrict__ p4,
@@ -421,6 +551,27 @@ cudaError_t launch_pd_step_f32(int dim, const F32StepArgs &A, bool init, cudaStr
         k_pd_step_f32<2><<<grid, 256, 0, s>>>(A, init ? 1 : 0);
     else
         k_pd_step_f32<3><<<grid, 256, 0, s>>>(A, init ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pd_step_lattice2d(const Lat2DArgs &A, bool init, cudaStream_t s)
+{
+    if (A.nx <= 0 || A.ny <= 0)
+        return cudaSuccess;
+    const dim3 grid((unsigned)((A.nx + lat2d::TX - 1) / lat2d::TX), (unsigned)((A.ny + lat2d::TY - 1) / lat2d::TY));
+    if (A.alpha)
+        k_pd_step_lattice2d<true><<<grid, 256, 0, s>>>(A, init ? 1 : 0);
+    else
+        k_pd_step_lattice2d<false><<<grid, 256, 0, s>>>(A, init ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_damage_lattice(int64_t n, const uint32_t *mask, const uint32_t *exists, int words, double *phi,
+                                  cudaStream_t s)
+{
+    if (n == 0)
+        return cudaSuccess;
+    k_damage_lattice<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, mask, exists, words, phi);
     return cudaGetLastError();
 }
 

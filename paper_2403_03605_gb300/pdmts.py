@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_PKG, "libpdmts.so")
 PDMTS_OK = 0
 ERRORS = {-1: "PDMTS_ERR_ARG", -2: "PDMTS_ERR_MASS", -3: "PDMTS_ERR_STABILITY", -4: "PDMTS_ERR_CUDA",
           -5: "PDMTS_ERR_TIMEOUT", -6: "PDMTS_ERR_STATE", -7: "PDMTS_ERR_NOMEM", -8: "PDMTS_ERR_UNSUPPORTED"}
-PDMTS_FP64, PDMTS_FP32_BULK = 0, 1
+PDMTS_FP64, PDMTS_FP32_BULK, PDMTS_FP32_BULK_SELL = 0, 1, 2
 PDMTS_MICRO_POWER, PDMTS_MICRO_EXP = 0, 1
 PDMTS_FORCE_LINEAR, PDMTS_FORCE_PMB = 0, 1
 PDMTS_WEIGHT_CONSTANT, PDMTS_WEIGHT_LINEAR, PDMTS_WEIGHT_CUBIC = 0, 1, 2
@@ -36,7 +36,8 @@ class PdmtsError(RuntimeError):
 class PDInfo(C.Structure):
     _fields_ = [("dim", C.c_int32), ("precision", C.c_int32), ("n", C.c_int64), ("n_bonds", C.c_int64),
                 ("n_slots", C.c_int64), ("max_degree", C.c_int32), ("on_lattice", C.c_int32),
-                ("lattice_h", C.c_double), ("steps_done", C.c_int64), ("device_bytes", C.c_int64)]
+                ("layout", C.c_int32), ("lattice_nx", C.c_int32), ("lattice_ny", C.c_int32),
+                ("reserved", C.c_int32), ("lattice_h", C.c_double), ("steps_done", C.c_int64), ("device_bytes", C.c_int64)]
 
 
 class Stats(C.Structure):
