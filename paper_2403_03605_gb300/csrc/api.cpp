@@ -642,6 +642,7 @@ static int upload_family_and_state(pdmts_pd *pd)
                     e.coef = (float)(micromodulus_host(pd, xi2) * h * h * V);
                     e.thr = (float)(pd->s0 * (2.0 + pd->s0) * r2);
                     e.rd = (float)std::sqrt(r2);
+                    e.r2 = (float)r2;
                     table.push_back(e);
                 } else {
                     id = it->second;
@@ -816,6 +817,7 @@ int pdmts_pd::step(bool init, double theta, cudaStream_t s)
             for (int r2 = 0; r2 < 10; ++r2) {
                 A.coef[r2] = r2 > 0 ? (float)(micromodulus_host(this, r2 * h * h) * h * h * V[0]) : 0.f;
                 A.thr[r2] = (float)(s0 * (2.0 + s0) * r2);
+                A.rd[r2] = (float)std::sqrt((double)r2);
             }
             A.nd = N;
             e = launch_pd_step_lattice2d(A, init, s);

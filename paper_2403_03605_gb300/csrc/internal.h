@@ -139,6 +139,7 @@ struct Lat2DArgs {
     const float *alpha;         // n (null when no weights)
     float coef[10];             // c(|xi|) h^2 V by |d|^2
     float thr[10];              // s0 (2 + s0) |d|^2
+    float rd[10];               // |d|
     F32NodeArgs nd;
 };
 

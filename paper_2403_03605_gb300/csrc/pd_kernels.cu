@@ -149,15 +149,17 @@ __global__ void __launch_bounds__(256) k_pd_step_f64(const F64StepArgs A, const 
 
 // ------------------------------------------------------------- FP32 bulk --
 // Compensated addition (hi, lo) += x: Knuth's two-sum followed by a
-// renormalisation, all in FP32 without products (nothing to contract).
+// renormalisation. Explicit round-to-nearest intrinsics keep the compiler
+// from fusing the caller's product into the first sum, which would break the
+// error term.
 __device__ __forceinline__ void df_add(float &hi, float &lo, float x)
 {
-    const float s = hi + x;
-    const float bp = s - hi;
-    float e = (hi - (s - bp)) + (x - bp);
-    e += lo;
-    const float h2 = s + e;
-    lo = e - (h2 - s);
+    const float s = __fadd_rn(hi, x);
+    const float bp = __fsub_rn(s, hi);
+    float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
+    e = __fadd_rn(e, lo);
+    const float h2 = __fadd_rn(s, e);
+    lo = __fsub_rn(e, __fsub_rn(h2, s));
     hi = h2;
 }
 
@@ -206,17 +208,17 @@ __device__ __forceinline__ void finish_node_f32(const F32NodeArgs &N, const int6
     for (int d = 0; d < DIM; ++d) {
         float t = f[d];
         if (N.wb)
-            t += N.wb[d * n + i];
+            t = __fadd_rn(t, N.wb[d * n + i]);
         if (N.g)
-            t = fmaf(N.theta, N.g[d * n + i], t);
-        an[d] = t * im;
+            t = __fmaf_rn(N.theta, N.g[d * n + i], t);
+        an[d] = __fmul_rn(t, im);
     }
     float vh[DIM], vl[DIM];
     load_pair<DIM>(N.v4, N.v2, i, vh, vl);
     if (!init) {
 #pragma unroll
         for (int d = 0; d < DIM; ++d)
-            df_add(vh[d], vl[d], N.hdt * (ao[d] + an[d]));
+            df_add(vh[d], vl[d], __fmul_rn(N.hdt, __fadd_rn(ao[d], an[d])));
         store_pair<DIM>(N.v4, N.v2, i, vh, vl);
     }
     if constexpr (DIM == 2)
@@ -225,7 +227,7 @@ __device__ __forceinline__ void finish_node_f32(const F32NodeArgs &N, const int6
         reinterpret_cast<float4 *>(N.a)[i] = make_float4(an[0], an[1], an[2], 0.f);
 #pragma unroll
     for (int d = 0; d < DIM; ++d)
-        df_add(uh[d], ul[d], fmaf(N.dt, vh[d], fmaf(N.dt, vl[d], N.hdt2 * an[d])));
+        df_add(uh[d], ul[d], __fmaf_rn(N.dt, vh[d], __fmaf_rn(N.dt, vl[d], __fmul_rn(N.hdt2, an[d]))));
     store_pair<DIM>(N.u4_out, N.u2_out, i, uh, ul);
 }
 
@@ -238,27 +240,67 @@ __device__ __forceinline__ void count_broken(unsigned long long *counter, unsign
     }
 }
 
-// Bond kinematics of the FP32 path in lattice units: offset d, relative
-// displacement eta. dot = d.eta is formed as fma(d_last, eta_last, ...) from
-// the first component up, the same expression at both ends of a bond, so
-// the breaking decision of (i, j) and (j, i) is identical.
+// One bond of the FP32 path, in lattice units (offset d, relative
+// displacement eta = u_j - u_i). Written once for both FP32 kernels with
+// explicit round-to-nearest intrinsics, so the two produce identical bits:
+//   lhs = 2 d.eta + |eta|^2  (= (|xi + eta|^2 - |xi|^2) / h^2, no cancellation)
+//   breaks when lhs >= thr = s0 (2 + s0) |d|^2        (s >= s0, Eq. 3-4)
+//   linear force  coef (d.eta) d ; PMB  coef |d|^2 lhs / ((|d+eta| + |d|)|d+eta|) (d + eta)
+// Every expression is invariant under (d, eta) -> (-d, -eta), so bond (i, j)
+// and (j, i) reach the same decision. `on` is the bond's intact bit; the
+// evaluation is branch-free (a broken or absent bond contributes 0).
+struct Bond2 {
+    float2 nuh, nul;  // -u_i (hi, lo)
+};
+
+__device__ __forceinline__ void bond_2d(const float4 uj, const Bond2 &B, const float d0, const float d1,
+                                        const float coef, const float thr, const float r2, const float rd,
+                                        const bool on, const int breaking, const int pmb, const uint32_t bit,
+                                        uint32_t &m, float2 &f)
+{
+    const float2 eh = __fadd2_rn(make_float2(uj.x, uj.y), B.nuh);
+    const float2 el = __fadd2_rn(make_float2(uj.z, uj.w), B.nul);
+    const float2 eta = __fadd2_rn(eh, el);
+    const float dot = __fmaf_rn(d1, eta.y, __fmul_rn(d0, eta.x));
+    const float e2 = __fmaf_rn(eta.y, eta.y, __fmul_rn(eta.x, eta.x));
+    const float lhs = __fmaf_rn(2.f, dot, e2);
+    const bool brk = on && breaking && lhs >= thr;
+    m = brk ? (m & ~bit) : m;
+    const float w = (on && !brk) ? coef : 0.f;
+    if (!pmb) {
+        const float sc = __fmul_rn(w, dot);
+        f = __ffma2_rn(make_float2(sc, sc), make_float2(d0, d1), f);
+    } else {
+        const float ry = __fsqrt_rn(__fadd_rn(r2, fmaxf(lhs, -r2)));
+        const float den = __fmul_rn(__fadd_rn(ry, rd), ry);
+        const float sc = w != 0.f ? __fdiv_rn(__fmul_rn(__fmul_rn(w, r2), lhs), den) : 0.f;
+        f = __ffma2_rn(make_float2(sc, sc), __fadd2_rn(make_float2(d0, d1), eta), f);
+    }
+}
+
+// Weight of bond (i, j) in the Arlequin overlap: 1 - (alpha_i + alpha_j) / 2.
+__device__ __forceinline__ float bond_weight(const float ai, const float aj)
+{
+    return __fmaf_rn(-0.5f, __fadd_rn(ai, aj), 1.f);
+}
+
 template <int DIM>
 __device__ __forceinline__ float bond_dot(const float (&d)[3], const float (&eta)[DIM])
 {
-    float dot = d[0] * eta[0];
+    float dot = __fmul_rn(d[0], eta[0]);
 #pragma unroll
     for (int k = 1; k < DIM; ++k)
-        dot = fmaf(d[k], eta[k], dot);
+        dot = __fmaf_rn(d[k], eta[k], dot);
     return dot;
 }
 
 template <int DIM>
 __device__ __forceinline__ float eta_sq(const float (&eta)[DIM])
 {
-    float e2 = eta[0] * eta[0];
+    float e2 = __fmul_rn(eta[0], eta[0]);
 #pragma unroll
     for (int k = 1; k < DIM; ++k)
-        e2 = fmaf(eta[k], eta[k], e2);
+        e2 = __fmaf_rn(eta[k], eta[k], e2);
     return e2;
 }
 
@@ -294,6 +336,12 @@ __global__ void __launch_bounds__(256) k_pd_step_f32(const F32StepArgs A, const 
     for (int d = 0; d < DIM; ++d)
         f[d] = 0.f;
     const float ai = A.alpha ? A.alpha[ii] : 0.f;
+    Bond2 B;
+    if constexpr (DIM == 2) {
+        B.nuh = make_float2(-uh[0], -uh[1]);
+        B.nul = make_float2(-ul[0], -ul[1]);
+    }
+    float2 f2 = make_float2(0.f, 0.f);
     unsigned nbroken = 0;
 
     for (int w = 0; 32 * w < K; ++w) {
@@ -304,46 +352,54 @@ __global__ void __launch_bounds__(256) k_pd_step_f32(const F32StepArgs A, const 
 #pragma unroll 4
         for (int kk = 0; kk < kend; ++kk) {
             const uint32_t cw = __ldg(cp + 32 * kk);
-            if (!((m0 >> kk) & 1u))
+            const uint32_t bit = 1u << kk;
+            if (!(m0 & bit))
                 continue;
             const uint32_t j = cw >> 8;
             const uint32_t sid = cw & 255u;
             const float4 sd = s_d[sid];
             const float4 st = s_t[sid];
-            float jh[DIM], jl[DIM], eta[DIM];
-            load_pair<DIM>(N.u4_in, N.u2_in, j, jh, jl);
-#pragma unroll
-            for (int d = 0; d < DIM; ++d)
-                eta[d] = (jh[d] - uh[d]) + (jl[d] - ul[d]);
-            const float dd[3] = {sd.x, sd.y, sd.z};
-            const float dot = bond_dot<DIM>(dd, eta);
-            // |xi + eta|^2 - |xi|^2 = h^2 (2 d.eta + |eta|^2) >= ((1+s0)^2 - 1)|xi|^2
-            const float lhs = fmaf(2.f, dot, eta_sq<DIM>(eta));
-            if (N.breaking && lhs >= st.x) {
-                m &= ~(1u << kk);
-                continue;
-            }
             float coef = sd.w;
             if (A.alpha)
-                coef *= 1.f - 0.5f * (ai + A.alpha[j]);
-            if (N.pmb) {
-                // s = (|d + eta| - |d|)/|d| = lhs / ((ry + rd) rd), force along d + eta
-                const float ry = sqrtf(st.z + lhs);
-                const float sc = coef * st.z * lhs / ((ry + st.y) * ry);
-#pragma unroll
-                for (int d = 0; d < DIM; ++d)
-                    f[d] = fmaf(sc, dd[d] + eta[d], f[d]);
+                coef = __fmul_rn(coef, bond_weight(ai, A.alpha[j]));
+            if constexpr (DIM == 2) {
+                bond_2d(N.u4_in[j], B, sd.x, sd.y, coef, st.x, st.z, st.y, true, N.breaking, N.pmb, bit, m, f2);
             } else {
-                const float sc = coef * dot;
+                float jh[DIM], jl[DIM], eta[DIM];
+                load_pair<DIM>(N.u4_in, N.u2_in, j, jh, jl);
 #pragma unroll
                 for (int d = 0; d < DIM; ++d)
-                    f[d] = fmaf(sc, dd[d], f[d]);
+                    eta[d] = __fadd_rn(__fsub_rn(jh[d], uh[d]), __fsub_rn(jl[d], ul[d]));
+                const float dd[3] = {sd.x, sd.y, sd.z};
+                const float dot = bond_dot<DIM>(dd, eta);
+                const float lhs = __fmaf_rn(2.f, dot, eta_sq<DIM>(eta));
+                if (N.breaking && lhs >= st.x) {
+                    m &= ~bit;
+                    continue;
+                }
+                if (N.pmb) {
+                    const float ry = __fsqrt_rn(__fadd_rn(st.z, fmaxf(lhs, -st.z)));
+                    const float sc = __fdiv_rn(__fmul_rn(__fmul_rn(coef, st.z), lhs),
+                                               __fmul_rn(__fadd_rn(ry, st.y), ry));
+#pragma unroll
+                    for (int d = 0; d < DIM; ++d)
+                        f[d] = __fmaf_rn(sc, __fadd_rn(dd[d], eta[d]), f[d]);
+                } else {
+                    const float sc = __fmul_rn(coef, dot);
+#pragma unroll
+                    for (int d = 0; d < DIM; ++d)
+                        f[d] = __fmaf_rn(sc, dd[d], f[d]);
+                }
             }
         }
         if (m != m0) {
             A.fam.mask[mbase + 32 * w + lane] = m;
             nbroken += __popc(m0 ^ m);
         }
+    }
+    if constexpr (DIM == 2) {
+        f[0] = f2.x;
+        f[1] = f2.y;
     }
     count_broken(N.broken, nbroken);
     if (!valid)
@@ -388,38 +444,19 @@ __global__ void __launch_bounds__(256) k_pd_step_lattice2d(const Lat2DArgs A, co
 
     const float4 ui = su[ty + R][tx + R];
     const float ai = HAS_ALPHA ? salpha[ty + R][tx + R] : 0.f;
-    float f[2] = {0.f, 0.f};
+    Bond2 B;
+    B.nuh = make_float2(-ui.x, -ui.y);
+    B.nul = make_float2(-ui.z, -ui.w);
+    float2 f2 = make_float2(0.f, 0.f);
     uint32_t m = m0;
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
-        if (m0 & (1u << k)) {
-            const float4 uj = su[ty + R + DY(k)][tx + R + DX(k)];
-            float eta[2];
-            eta[0] = (uj.x - ui.x) + (uj.z - ui.z);
-            eta[1] = (uj.y - ui.y) + (uj.w - ui.w);
-            const float dd[3] = {(float)DX(k), (float)DY(k), 0.f};
-            const int r2 = DX(k) * DX(k) + DY(k) * DY(k);
-            const float dot = bond_dot<2>(dd, eta);
-            const float lhs = fmaf(2.f, dot, eta_sq<2>(eta));
-            if (N.breaking && lhs >= A.thr[r2]) {
-                m &= ~(1u << k);
-            } else {
-                float coef = A.coef[r2];
-                if constexpr (HAS_ALPHA)
-                    coef *= 1.f - 0.5f * (ai + salpha[ty + R + DY(k)][tx + R + DX(k)]);
-                if (N.pmb) {
-                    const float r2f = (float)r2;
-                    const float ry = sqrtf(r2f + lhs);
-                    const float sc = coef * r2f * lhs / ((ry + sqrtf(r2f)) * ry);
-                    f[0] = fmaf(sc, dd[0] + eta[0], f[0]);
-                    f[1] = fmaf(sc, dd[1] + eta[1], f[1]);
-                } else {
-                    const float sc = coef * dot;
-                    f[0] = fmaf(sc, dd[0], f[0]);
-                    f[1] = fmaf(sc, dd[1], f[1]);
-                }
-            }
-        }
+        const int r2 = DX(k) * DX(k) + DY(k) * DY(k);
+        float coef = A.coef[r2];
+        if constexpr (HAS_ALPHA)
+            coef = __fmul_rn(coef, bond_weight(ai, salpha[ty + R + DY(k)][tx + R + DX(k)]));
+        bond_2d(su[ty + R + DY(k)][tx + R + DX(k)], B, (float)DX(k), (float)DY(k), coef, A.thr[r2], (float)r2,
+                A.rd[r2], (m0 >> k) & 1u, N.breaking, N.pmb, 1u << k, m, f2);
     }
     unsigned nbroken = 0;
     if (m != m0) {
@@ -429,6 +466,7 @@ __global__ void __launch_bounds__(256) k_pd_step_lattice2d(const Lat2DArgs A, co
     count_broken(N.broken, nbroken);
     if (!valid)
         return;
+    const float f[2] = {f2.x, f2.y};
     float uh[2] = {ui.x, ui.y}, ul[2] = {ui.z, ui.w};
     finish_node_f32<2>(N, i, f, uh, ul, init);
 }
