@@ -417,12 +417,94 @@ namespace lat2d {
 constexpr int TX = 32, TY = 8, HX = TX + 2 * R, HY = TY + 2 * R;
 }
 
-template <bool HAS_ALPHA>
+// Bond slot k of a lattice node: the same branch-free expression as bond_2d
+// with compile-time offset, |d|^2 and |d|.
+template <int K, bool PMB>
+__device__ __forceinline__ void lattice_bond(const float4 uj, const Bond2 &B, const float coef, const float thr,
+                                             bool &new_break, float2 &f)
+{
+    constexpr int dx = lat2d::DX(K), dy = lat2d::DY(K), r2 = dx * dx + dy * dy;
+    const float2 eh = __fadd2_rn(make_float2(uj.x, uj.y), B.nuh);
+    const float2 el = __fadd2_rn(make_float2(uj.z, uj.w), B.nul);
+    const float2 eta = __fadd2_rn(eh, el);
+    const float dot = __fmaf_rn((float)dy, eta.y, __fmul_rn((float)dx, eta.x));
+    const float e2 = __fmaf_rn(eta.y, eta.y, __fmul_rn(eta.x, eta.x));
+    const float lhs = __fmaf_rn(2.f, dot, e2);
+    new_break |= lhs >= thr;
+    if constexpr (!PMB) {
+        const float sc = __fmul_rn(coef, dot);
+        f = __ffma2_rn(make_float2(sc, sc), make_float2((float)dx, (float)dy), f);
+    } else {
+        constexpr float rd = (r2 == 1 ? 1.f : r2 == 2 ? 1.41421354f : r2 == 4 ? 2.f : r2 == 5 ? 2.23606801f
+                              : r2 == 8 ? 2.82842708f : 3.f);
+        const float ry = __fsqrt_rn(__fadd_rn((float)r2, fmaxf(lhs, -(float)r2)));
+        const float den = __fmul_rn(__fadd_rn(ry, rd), ry);
+        const float sc = __fdiv_rn(__fmul_rn(__fmul_rn(coef, (float)r2), lhs), den);
+        f = __ffma2_rn(make_float2(sc, sc), __fadd2_rn(make_float2((float)dx, (float)dy), eta), f);
+    }
+}
+
+template <int K, bool HAS_ALPHA, bool PMB>
+struct LatticeSlots {
+    // all 28 slots unconditionally (warp fast path: every bond intact)
+    __device__ static __forceinline__ void all(const float4 (*su)[lat2d::HX], const int ty, const int tx,
+                                               const Lat2DArgs &A, const Bond2 &B, const float ai,
+                                               const float (*sal)[lat2d::HX], bool &nb, float2 &f)
+    {
+        using namespace lat2d;
+        constexpr int dx = DX(K), dy = DY(K), r2 = dx * dx + dy * dy;
+        float coef = A.coef[r2];
+        if constexpr (HAS_ALPHA)
+            coef = __fmul_rn(coef, bond_weight(ai, sal[ty + R + dy][tx + R + dx]));
+        lattice_bond<K, PMB>(su[ty + R + dy][tx + R + dx], B, coef, A.thr[r2], nb, f);
+        LatticeSlots<K + 1, HAS_ALPHA, PMB>::all(su, ty, tx, A, B, ai, sal, nb, f);
+    }
+    // slot by slot with the bond bits: exact breaking, absent bonds skipped
+    __device__ static __forceinline__ void masked(const float4 (*su)[lat2d::HX], const int ty, const int tx,
+                                                  const Lat2DArgs &A, const Bond2 &B, const float ai,
+                                                  const float (*sal)[lat2d::HX], const uint32_t m0,
+                                                  const int breaking, uint32_t &m, float2 &f)
+    {
+        using namespace lat2d;
+        constexpr int dx = DX(K), dy = DY(K), r2 = dx * dx + dy * dy;
+        if (m0 & (1u << K)) {
+            float coef = A.coef[r2];
+            if constexpr (HAS_ALPHA)
+                coef = __fmul_rn(coef, bond_weight(ai, sal[ty + R + dy][tx + R + dx]));
+            bool brk = false;
+            float2 g = f;
+            lattice_bond<K, PMB>(su[ty + R + dy][tx + R + dx], B, coef, A.thr[r2], brk, g);
+            if (breaking && brk)
+                m &= ~(1u << K);
+            else
+                f = g;
+        }
+        LatticeSlots<K + 1, HAS_ALPHA, PMB>::masked(su, ty, tx, A, B, ai, sal, m0, breaking, m, f);
+    }
+};
+
+template <bool HAS_ALPHA, bool PMB>
+struct LatticeSlots<lat2d::NS, HAS_ALPHA, PMB> {
+    __device__ static __forceinline__ void all(const float4 (*)[lat2d::HX], int, int, const Lat2DArgs &,
+                                               const Bond2 &, float, const float (*)[lat2d::HX], bool &, float2 &)
+    {
+    }
+    __device__ static __forceinline__ void masked(const float4 (*)[lat2d::HX], int, int, const Lat2DArgs &,
+                                                  const Bond2 &, float, const float (*)[lat2d::HX], uint32_t,
+                                                  int, uint32_t &, float2 &)
+    {
+    }
+};
+
+// Bond word of a node with all 28 bonds present and intact.
+constexpr uint32_t kFullWord = (1u << lat2d::NS) - 1u;
+
+template <bool HAS_ALPHA, bool PMB>
 __global__ void __launch_bounds__(256) k_pd_step_lattice2d(const Lat2DArgs A, const int init)
 {
     using namespace lat2d;
     __shared__ float4 su[HY][HX];
-    __shared__ float salpha[HAS_ALPHA ? HY : 1][HAS_ALPHA ? HX : 1];
+    __shared__ float salpha[HAS_ALPHA ? HY : 1][HX];
     const F32NodeArgs &N = A.nd;
     const int nx = A.nx, ny = A.ny;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
@@ -449,14 +531,19 @@ __global__ void __launch_bounds__(256) k_pd_step_lattice2d(const Lat2DArgs A, co
     B.nul = make_float2(-ui.z, -ui.w);
     float2 f2 = make_float2(0.f, 0.f);
     uint32_t m = m0;
-#pragma unroll
-    for (int k = 0; k < NS; ++k) {
-        const int r2 = DX(k) * DX(k) + DY(k) * DY(k);
-        float coef = A.coef[r2];
-        if constexpr (HAS_ALPHA)
-            coef = __fmul_rn(coef, bond_weight(ai, salpha[ty + R + DY(k)][tx + R + DX(k)]));
-        bond_2d(su[ty + R + DY(k)][tx + R + DX(k)], B, (float)DX(k), (float)DY(k), coef, A.thr[r2], (float)r2,
-                A.rd[r2], (m0 >> k) & 1u, N.breaking, N.pmb, 1u << k, m, f2);
+    // Fast path: every node of the warp has all bonds intact; evaluate all
+    // slots without per-bond control flow and only note whether some bond
+    // reached the critical stretch. If one did (rare), redo the warp exactly.
+    bool fast = __all_sync(0xffffffffu, m0 == kFullWord || !valid);
+    if (fast) {
+        bool nb = false;
+        LatticeSlots<0, HAS_ALPHA, PMB>::all(su, ty, tx, A, B, ai, salpha, nb, f2);
+        if (N.breaking && __any_sync(0xffffffffu, nb))
+            fast = false;
+    }
+    if (!fast) {
+        f2 = make_float2(0.f, 0.f);
+        LatticeSlots<0, HAS_ALPHA, PMB>::masked(su, ty, tx, A, B, ai, salpha, m0, N.breaking, m, f2);
     }
     unsigned nbroken = 0;
     if (m != m0) {
@@ -597,10 +684,18 @@ cudaError_t launch_pd_step_lattice2d(const Lat2DArgs &A, bool init, cudaStream_t
     if (A.nx <= 0 || A.ny <= 0)
         return cudaSuccess;
     const dim3 grid((unsigned)((A.nx + lat2d::TX - 1) / lat2d::TX), (unsigned)((A.ny + lat2d::TY - 1) / lat2d::TY));
-    if (A.alpha)
-        k_pd_step_lattice2d<true><<<grid, 256, 0, s>>>(A, init ? 1 : 0);
-    else
-        k_pd_step_lattice2d<false><<<grid, 256, 0, s>>>(A, init ? 1 : 0);
+    const int it = init ? 1 : 0;
+    if (A.alpha) {
+        if (A.nd.pmb)
+            k_pd_step_lattice2d<true, true><<<grid, 256, 0, s>>>(A, it);
+        else
+            k_pd_step_lattice2d<true, false><<<grid, 256, 0, s>>>(A, it);
+    } else {
+        if (A.nd.pmb)
+            k_pd_step_lattice2d<false, true><<<grid, 256, 0, s>>>(A, it);
+        else
+            k_pd_step_lattice2d<false, false><<<grid, 256, 0, s>>>(A, it);
+    }
     return cudaGetLastError();
 }
 
