@@ -207,3 +207,124 @@ def random_field(shape, scale, seed):
     """Seeded smooth-ish random field (used for initial displacements in tests)."""
     rng = np.random.default_rng(seed)
     return rng.standard_normal(shape) * scale
+
+
+# --------------------------------------------------------------------------
+# Coupled PD / finite-element plates (Sec. 2.2-2.5, Sec. 3.3, Sec. 4.1)
+# --------------------------------------------------------------------------
+@dataclass
+class Band:
+    """Overlap band lo <= x[axis] <= hi; the finite-element-only region lies on
+    `fe_side` (-1: below lo, +1: above hi)."""
+    axis: int
+    lo: float
+    hi: float
+    fe_side: int
+
+    def as_array(self):
+        return np.array([self.axis, self.lo, self.hi, self.fe_side, 0.0], dtype=np.float64)
+
+
+@dataclass
+class FEMesh:
+    """Structured Q4 mesh: nodes (2, n) and counter-clockwise connectivity (ne, 4)."""
+    X: np.ndarray
+    conn: np.ndarray
+    h: float  # element size
+
+    @property
+    def n(self):
+        return self.X.shape[1]
+
+    @property
+    def ne(self):
+        return self.conn.shape[0]
+
+
+def q4_block(x0, y0, nex, ney, h, node_offset=0):
+    xs = x0 + h * np.arange(nex + 1)
+    ys = y0 + h * np.arange(ney + 1)
+    X = np.stack(np.meshgrid(xs, ys, indexing="xy")).reshape(2, -1)  # x fastest
+    conn = []
+    for j in range(ney):
+        for i in range(nex):
+            a = j * (nex + 1) + i
+            conn.append([a, a + 1, a + nex + 2, a + nex + 1])
+    return X, np.asarray(conn, dtype=np.int32) + node_offset
+
+
+@dataclass
+class CoupledProblem:
+    """A coupled PD / FE problem statement (inputs only)."""
+    name: str
+    pd: PDProblem          # PD strip (its own body force is zero)
+    fe: FEMesh
+    faces: np.ndarray      # (nf, 2) FE edge node pairs carrying traction
+    face_traction: np.ndarray  # (nf, 2) traction vector per face [Pa]
+    bands: list
+    weight_kind: int       # 0 constant, 1 linear, 2 cubic (Sec. 3.2)
+    m: int                 # time-step ratio dt_FE / dt_PD
+    n_coarse: int
+    gamma_fe: float = 0.5
+    beta_fe: float = 0.25
+
+    @property
+    def dt_pd(self):
+        return self.pd.dt
+
+
+def coupled_plate(Lx, Ly, strip, dx, h_fe, overlap, *, crack=None, traction=12e6, dt=20e-9, m=10, n_coarse=200,
+                  weight_kind=1, mat: Material | None = None, name="coupled_plate") -> CoupledProblem:
+    """Plate [0, Lx] x [0, Ly]; PD strip strip = (y0, y1) at spacing dx; Q4
+    elements of size h_fe on [0, y0 + overlap] and [y1 - overlap, Ly]; the
+    overlap bands are [y0, y0 + overlap] and [y1 - overlap, y1]. Traction on
+    the bottom and top edges (mode I). crack = (y_level, x_lo, x_hi)."""
+    mat = mat or Material()
+    y0, y1 = strip
+    nx = int(round(Lx / dx))
+    ny = int(round((y1 - y0) / dx))
+    lat = Lattice((nx, ny), dx, (0.0, y0))
+    delta = HORIZON_FACTOR * dx
+    c, s0 = pmb_constants(2, mat, delta)
+    cuts = [Cut(1, crack[0], 0, crack[1], crack[2])] if crack else []
+    pd = PDProblem(name + "_pd", lat, mat, delta, c, s0, dt, m * n_coarse, cuts, np.zeros((2, lat.n)),
+                   mat.thickness * dx * dx)
+    nex = int(round(Lx / h_fe))
+    neb = int(round((y0 + overlap) / h_fe))
+    net = int(round((Ly - (y1 - overlap)) / h_fe))
+    Xb, cb = q4_block(0.0, 0.0, nex, neb, h_fe)
+    Xt, ct = q4_block(0.0, y1 - overlap, nex, net, h_fe, node_offset=Xb.shape[1])
+    fe = FEMesh(np.concatenate([Xb, Xt], axis=1), np.concatenate([cb, ct]), h_fe)
+    nb = Xb.shape[1]
+    bot = [(i, i + 1) for i in range(nex)]
+    top_row = nb + net * (nex + 1)
+    top = [(top_row + i + 1, top_row + i) for i in range(nex)]
+    faces = np.asarray(bot + top, dtype=np.int32)
+    tr = np.zeros((len(faces), 2))
+    tr[:nex, 1] = -traction
+    tr[nex:, 1] = +traction
+    bands = [Band(1, y0, y0 + overlap, -1), Band(1, y1 - overlap, y1, +1)]
+    return CoupledProblem(name, pd, fe, faces, tr, bands, weight_kind, m, n_coarse)
+
+
+def config1() -> CoupledProblem:
+    """Coupled 2D plate 0.1 x 0.04 m, 50 mm edge pre-crack at mid-height; PD strip
+    16 mm (400 x 64 nodes at 0.25 mm), Q4 elements of 1 mm elsewhere, 2 mm overlap
+    bands with linear weights; 12 MPa; dt_PD 20 ns, m = 10, 200 coarse steps."""
+    return coupled_plate(0.1, 0.04, (0.012, 0.028), 0.25e-3, 1e-3, 2e-3, crack=(0.020, 0.0, 0.050),
+                         dt=20e-9, m=10, n_coarse=200, name="coupled_plate_100x40mm_pd400x64")
+
+
+def config2() -> CoupledProblem:
+    """Fine coupled plate: PD strip 20 mm at 0.05 mm (2000 x 400 = 800k nodes), Q4
+    0.5 mm, 2 mm overlap, 50 mm edge crack at mid-height; dt_PD 5 ns, m = 20, 500 coarse."""
+    return coupled_plate(0.1, 0.04, (0.010, 0.030), 0.05e-3, 0.5e-3, 2e-3, crack=(0.020, 0.0, 0.050),
+                         dt=5e-9, m=20, n_coarse=500, name="coupled_plate_100x40mm_pd2000x400")
+
+
+def small_coupled(m=4, n_coarse=20, weight_kind=1, crack=True, traction=12e6, dx=0.25e-3) -> CoupledProblem:
+    """A small coupled plate the oracle finishes in seconds (tests): 20 x 10 mm,
+    PD strip y in [3, 7] mm, Q4 1 mm, 1 mm overlap bands."""
+    return coupled_plate(0.02, 0.01, (0.003, 0.007), dx, 1e-3, 1e-3,
+                         crack=(0.005, 0.0, 0.008) if crack else None, traction=traction, dt=20e-9, m=m,
+                         n_coarse=n_coarse, weight_kind=weight_kind, name="coupled_small")
