@@ -189,6 +189,58 @@ int mts_advance(pdmts_ctx *ctx, int64_t n_coarse);
 int pdmts_set_timing(pdmts_ctx *ctx, int enabled);
 int pdmts_get_timing(pdmts_ctx *ctx, double *substep_ms, int64_t *substeps);
 
+/* ---- CCM subdomain and Arlequin coupling (Sec. 2.2-2.5, Eq. 33-49, Alg. 1) -- */
+
+/* Finite-element subdomain of `ctx` (one per context): linear elastic,
+ * isotropic (Eq. 8-9), plane stress with thickness `thickness`. This build
+ * takes dim = 2 with bilinear quadrilaterals (nodes_per_elem = 4, counter-
+ * clockwise, axis-aligned rectangles). Xn: dim * n_nodes (SoA); conn:
+ * n_elems * 4 int32 node ids. PDMTS_ERR_UNSUPPORTED for other element kinds. */
+int fem_create(pdmts_ctx *ctx, int dim, int64_t n_nodes, const double *Xn, int64_t n_elems,
+               int nodes_per_elem, const int32_t *conn, double E, double nu, double rho,
+               double thickness, pdmts_fem **fe);
+/* Uniform traction on boundary edges: face_nodes n_faces * 2 node ids,
+ * traction n_faces * dim [Pa]; consistent nodal loads (Eq. 8). Call before
+ * arlequin_bind. */
+int fem_set_traction(pdmts_fem *fe, int64_t n_faces, const int32_t *face_nodes, const double *traction);
+int fem_destroy(pdmts_fem *fe);
+/* Initial FE displacement and velocity (dim * n_nodes each, NULL = zero); the
+ * acceleration follows from M a = P - K u. Call after arlequin_bind. */
+int fem_set_state(pdmts_fem *fe, const double *u, const double *v);
+/* FE displacement, velocity, acceleration (dim * n_nodes doubles, SoA). */
+int fem_read_displacement(pdmts_fem *fe, double *u);
+int fem_read_velocity(pdmts_fem *fe, double *v);
+int fem_read_acceleration(pdmts_fem *fe, double *a);
+
+/* Couple the PD and FE subdomains over overlap bands (Eq. 17-23, Eq. 33).
+ * bands: n_bands * 5 doubles {axis, lo, hi, fe_side, 0}: the overlap is
+ * lo <= x[axis] <= hi; the FE-only region lies below lo (fe_side = -1) or
+ * above hi (+1). weight_kind: PDMTS_WEIGHT_CONSTANT | LINEAR | CUBIC (Sec. 3.2),
+ * alpha = 1 on the FE-only side, 0 on the PD-only side. This sets the PD
+ * weights (pd_set_weights), assembles the alpha-weighted FE stiffness, lumped
+ * mass and loads (Eq. 34), and builds the constraint operators: the
+ * multiplier lives on the FE nodes of the overlap, G_FE = int_O N_k N_I dV,
+ * G_PD = N_k(x_p) V_p. Afterwards mts_advance runs Algorithm 1. */
+int arlequin_bind(pdmts_ctx *ctx, pdmts_pd *pd, pdmts_fem *fe, int weight_kind, int n_bands,
+                  const double *bands, pdmts_arl **arl);
+int arlequin_destroy(pdmts_arl *arl);
+/* The multiplier lambda of the last completed coarse step (n_lambda doubles,
+ * component-major over the multiplier nodes). */
+int arlequin_read_lambda(pdmts_arl *arl, double *lambda, int64_t *n_lambda);
+/* |G_FE v_FE - G_PD v_PD| (Eq. 41) at the current time and |G_FE v_FE|. */
+int arlequin_constraint_residual(pdmts_arl *arl, double *residual, double *reference);
+
+typedef struct {
+    int64_t n_lambda;        /* multiplier components                     */
+    int64_t n_overlap_pd;    /* PD nodes inside overlap elements          */
+    int64_t fe_dofs;         /* finite-element degrees of freedom         */
+    int64_t colors;          /* link runs per interface-operator build    */
+    int64_t rebuilds;        /* interface-operator builds so far          */
+    int64_t cheb_iterations; /* Chebyshev iterations per FE solve         */
+    int64_t device_bytes;    /* device memory of the coupling and FE      */
+} pdmts_arl_info;
+int arlequin_info(pdmts_arl *arl, pdmts_arl_info *info);
+
 /* Counters since context creation. */
 typedef struct {
     int64_t pd_substeps;      /* PD substeps (free + link)                */

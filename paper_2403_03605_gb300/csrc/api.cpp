@@ -297,6 +297,73 @@ void pdmts_pd::release_all()
     release(d_stencil); release(f_alpha); release(f_invm); release(f_wb); release(f_g);
     release(f_v4); release(f_v2); release(f_a);
     release(f_u4[0]); release(f_u4[1]); release(f_u2[0]); release(f_u2[1]);
+    release(lk_u[0]); release(lk_u[1]); release(lk_v); release(lk_a); release(lk_g);
+    release(lk_u4[0]); release(lk_u4[1]); release(lk_v4); release(lk_u2[0]); release(lk_u2[1]); release(lk_v2);
+    release(lk_af); release(lk_gf); release(d_mask_link);
+}
+
+int pdmts_pd::alloc_link_state()
+{
+    if (has_link)
+        return PDMTS_OK;
+    const int64_t m = (int64_t)dim * n;
+    if (precision == PDMTS_FP64) {
+        PDMTS_TRY(alloc(lk_u[0], m));
+        PDMTS_TRY(alloc(lk_u[1], m));
+        PDMTS_TRY(alloc(lk_v, m));
+        PDMTS_TRY(alloc(lk_a, m));
+        PDMTS_TRY(alloc(lk_g, m));
+        if (!d_g.p)
+            PDMTS_TRY(alloc(d_g, m));
+    } else {
+        for (int b = 0; b < 2; ++b) {
+            PDMTS_TRY(alloc(lk_u4[b], n));
+            if (dim == 3)
+                PDMTS_TRY(alloc(lk_u2[b], n));
+        }
+        PDMTS_TRY(alloc(lk_v4, n));
+        if (dim == 3)
+            PDMTS_TRY(alloc(lk_v2, n));
+        PDMTS_TRY(alloc(lk_af, (int64_t)(dim == 2 ? 2 : 4) * n));
+        PDMTS_TRY(alloc(lk_gf, m));
+        if (!f_g.p)
+            PDMTS_TRY(alloc(f_g, m));
+    }
+    PDMTS_TRY(alloc(d_mask_link, std::max<int64_t>(n_mask_words, 1)));
+    cudaStream_t s = ctx->stream;
+    PDMTS_CUDA_TRY(cudaMemcpyAsync(d_mask_link.p, d_mask.p, sizeof(uint32_t) * std::max<int64_t>(n_mask_words, 1),
+                                   cudaMemcpyDeviceToDevice, s));
+    if (precision == PDMTS_FP64)
+        PDMTS_CUDA_TRY(cudaMemsetAsync(d_g.p, 0, sizeof(double) * m, s));
+    else
+        PDMTS_CUDA_TRY(cudaMemsetAsync(f_g.p, 0, sizeof(float) * m, s));
+    has_link = true;
+    has_g = true;
+    pd_invalidate_graphs(this);
+    return PDMTS_OK;
+}
+
+int pdmts_pd::zero_link_state(cudaStream_t s)
+{
+    const int64_t m = (int64_t)dim * n;
+    if (precision == PDMTS_FP64) {
+        for (int b = 0; b < 2; ++b)
+            PDMTS_CUDA_TRY(cudaMemsetAsync(lk_u[b].p, 0, sizeof(double) * m, s));
+        PDMTS_CUDA_TRY(cudaMemsetAsync(lk_v.p, 0, sizeof(double) * m, s));
+        PDMTS_CUDA_TRY(cudaMemsetAsync(lk_a.p, 0, sizeof(double) * m, s));
+    } else {
+        for (int b = 0; b < 2; ++b) {
+            PDMTS_CUDA_TRY(cudaMemsetAsync(lk_u4[b].p, 0, sizeof(float4) * n, s));
+            if (dim == 3)
+                PDMTS_CUDA_TRY(cudaMemsetAsync(lk_u2[b].p, 0, sizeof(float2) * n, s));
+        }
+        PDMTS_CUDA_TRY(cudaMemsetAsync(lk_v4.p, 0, sizeof(float4) * n, s));
+        if (dim == 3)
+            PDMTS_CUDA_TRY(cudaMemsetAsync(lk_v2.p, 0, sizeof(float2) * n, s));
+        PDMTS_CUDA_TRY(cudaMemsetAsync(lk_af.p, 0, sizeof(float) * (dim == 2 ? 2 : 4) * n, s));
+    }
+    lk_cur = 0;  // W_0 = 0: current and predicted displacement both zero, a_0 = 0
+    return PDMTS_OK;
 }
 
 template <typename T>
@@ -758,13 +825,16 @@ int pdmts_pd::upload_weights_and_loads()
 // v, writes the following prediction over the old u[cur], and swaps, so that
 // cur again names the current time. With init, a is computed from u[cur] and
 // the first prediction u + dt v + dt^2/2 a is written to u[1 - cur]; no swap.
-int pdmts_pd::step(bool init, double theta, cudaStream_t s)
+int pdmts_pd::step(bool init, double theta, cudaStream_t s, bool link)
 {
     const double dt = ctx->dt_pd;
     cudaError_t e;
     SellView fam{d_tile_ptr.p, d_tile_k.p, d_mask_ptr.p, d_col.p, d_mask.p, d_deg.p, n, ntiles};
-    const int src = init ? cur : 1 - cur;  // buffer the forces are evaluated at
-    const int dst = 1 - src;               // buffer receiving the next prediction
+    int &c = link ? lk_cur : cur;
+    const int src = init ? c : 1 - c;  // buffer the forces are evaluated at
+    const int dst = 1 - src;           // buffer receiving the next prediction
+    uint32_t *mask = link ? d_mask_link.p : d_mask.p;
+    fam.mask = mask;
     if (precision == PDMTS_FP64) {
         F64StepArgs A{};
         A.fam = fam;
@@ -773,18 +843,18 @@ int pdmts_pd::step(bool init, double theta, cudaStream_t s)
         A.cb = d_cb.p;
         A.alpha = d_alpha.p;
         A.mass = d_mass.p;
-        A.wb = d_wb.p;
-        A.g = d_g.p;
-        A.u_in = d_u[src].p;
-        A.u_out = d_u[dst].p;
-        A.v = d_v.p;
-        A.a = d_a.p;
+        A.wb = link ? nullptr : d_wb.p;
+        A.g = link ? lk_g.p : (has_g ? d_g.p : nullptr);
+        A.u_in = link ? lk_u[src].p : d_u[src].p;
+        A.u_out = link ? lk_u[dst].p : d_u[dst].p;
+        A.v = link ? lk_v.p : d_v.p;
+        A.a = link ? lk_a.p : d_a.p;
         A.s0p2 = (1.0 + s0) * (1.0 + s0);
         A.dt = dt;
         A.hdt = 0.5 * dt;
         A.hdt2 = 0.5 * dt * dt;
         A.theta = theta;
-        A.breaking = breaking ? 1 : 0;
+        A.breaking = (breaking && !link) ? 1 : 0;
         A.pmb = force_kind == PDMTS_FORCE_PMB;
         A.broken = ctx->d_counter;
         e = launch_pd_step_f64(dim, A, init, s);
@@ -792,27 +862,27 @@ int pdmts_pd::step(bool init, double theta, cudaStream_t s)
         F32NodeArgs N{};
         N.n = n;
         N.inv_m = f_invm.p;
-        N.wb = f_wb.p;
-        N.g = f_g.p;
-        N.u4_in = f_u4[src].p;
-        N.u2_in = f_u2[src].p;
-        N.u4_out = f_u4[dst].p;
-        N.u2_out = f_u2[dst].p;
-        N.v4 = f_v4.p;
-        N.v2 = f_v2.p;
-        N.a = f_a.p;
+        N.wb = link ? nullptr : f_wb.p;
+        N.g = link ? lk_gf.p : (has_g ? f_g.p : nullptr);
+        N.u4_in = link ? lk_u4[src].p : f_u4[src].p;
+        N.u2_in = link ? lk_u2[src].p : f_u2[src].p;
+        N.u4_out = link ? lk_u4[dst].p : f_u4[dst].p;
+        N.u2_out = link ? lk_u2[dst].p : f_u2[dst].p;
+        N.v4 = link ? lk_v4.p : f_v4.p;
+        N.v2 = link ? lk_v2.p : f_v2.p;
+        N.a = link ? lk_af.p : f_a.p;
         N.dt = (float)dt;
         N.hdt = (float)(0.5 * dt);
         N.hdt2 = (float)(0.5 * dt * dt);
         N.theta = (float)theta;
-        N.breaking = breaking ? 1 : 0;
+        N.breaking = (breaking && !link) ? 1 : 0;
         N.pmb = force_kind == PDMTS_FORCE_PMB;
         N.broken = ctx->d_counter;
         if (layout == LAYOUT_LATTICE2D) {
             Lat2DArgs A{};
             A.nx = lat_dims[0];
             A.ny = lat_dims[1];
-            A.mask = d_mask.p;
+            A.mask = mask;
             A.alpha = f_alpha.p;
             for (int r2 = 0; r2 < 10; ++r2) {
                 A.coef[r2] = r2 > 0 ? (float)(micromodulus_host(this, r2 * h * h) * h * h * V[0]) : 0.f;
@@ -835,8 +905,9 @@ int pdmts_pd::step(bool init, double theta, cudaStream_t s)
         return fail(PDMTS_ERR_CUDA, "PD substep launch failed: %s", cudaGetErrorString(e));
     ctx->stats.kernel_launches++;
     if (!init) {
-        cur = 1 - cur;
-        steps_done++;
+        c = 1 - c;
+        if (!link)
+            steps_done++;
         ctx->stats.pd_substeps++;
         ctx->stats.bond_updates += (int64_t)row_ptr[(size_t)n];
     }

@@ -163,6 +163,46 @@ cudaError_t launch_weighted_load(int dim, int64_t n, const double *b, const doub
                                  const float *alpha32, double inv_h, double *wb64, float *wb32,
                                  unsigned long long *flag, cudaStream_t s);
 
+// ---- MTS coupling helpers (pd_kernels.cu) ----
+// Interface force density of the PD overlap nodes, g_p = sum_a N_a(x_p)
+// lambda[k_a] per component (= (G_PD^T lambda)_p / V_p); nodes outside the
+// overlap are not written. g64 (FP64, dim * n) or g32 (FP32 lattice units,
+// scaled by inv_h); lam is dim * nl (component-major).
+cudaError_t launch_interface_force(int dim, int64_t n, int64_t n_ov, const int32_t *ov_node, const int32_t *ov_k,
+                                   const double *ov_N, int corners, const double *lam, int64_t nl, double inv_h,
+                                   double *g64, float *g32, cudaStream_t s);
+// y[c * nl + k] = sign * sum_p G_PD[k, p] v_p[c] over CSR rows (row k, per
+// component) plus, if gfe_col != null, sum_I G_FE[k, I] vfe[c * nfe + I]
+// (ELL rows of width gfe_w). v is the PD velocity (FP64 v64, or the FP32
+// packed pairs v4/v2 scaled by h).
+cudaError_t launch_constraint(int dim, int64_t nl, const int64_t *gpd_ptr, const int32_t *gpd_col,
+                              const double *gpd_val, int64_t npd, const double *v64, const float4 *v4,
+                              const float2 *v2, double h, const int32_t *gfe_col, const double *gfe_val, int gfe_w,
+                              int64_t nfe, const double *vfe, double sign_pd, double sign_fe, double *y,
+                              cudaStream_t s);
+// U_PD += W (u, v, a of the link state), then the prediction for the next
+// substep u + dt v + dt^2/2 a.
+struct PDAddLink {
+    int dim;
+    int64_t n;
+    double dt, hdt2;
+    // FP64
+    double *u, *u_pred, *v, *a;
+    const double *wu, *wv, *wa;
+    // FP32 (lattice units)
+    float4 *u4, *u4_pred, *v4;
+    float2 *u2, *u2_pred, *v2;
+    float *af;
+    const float4 *wu4, *wv4;
+    const float2 *wu2, *wv2;
+    const float *waf;
+};
+cudaError_t launch_pd_add_link(const PDAddLink &A, cudaStream_t s);
+// Count bond words of `flag`ged nodes that differ between two mask arrays
+// (lattice layout: words indexed by node; sliced ELL: per tile).
+cudaError_t launch_count_changed(int64_t nwords, const uint32_t *a, const uint32_t *b, const uint8_t *word_flag,
+                                 unsigned long long *count, cudaStream_t s);
+
 }  // namespace pdmts
 
 // --------------------------------------------------------------- handles ---

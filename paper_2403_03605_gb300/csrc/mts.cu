@@ -1,13 +1,1379 @@
-// mts.cu -- multi-time-step Arlequin coupling (Sec. 2.5, Alg. 1).
+// mts.cu -- multi-time-step Arlequin coupling of PD and finite elements
+// (arXiv 2403.03605, Sec. 2.2-2.5, Eq. 33-49, Algorithm 1).
+//
+// Per coarse step t_0 -> t_m = t_0 + m dt_PD:
+//   stream B: finite-element free step (Eq. 47a with Newmark, Eq. 39): predictor,
+//             K_eff a = P - K u~ by Chebyshev iteration (no reductions), update;
+//   stream A: interface force G_PD^T lambda_0 / V on the PD overlap nodes, then
+//             the m PD free substeps (Eq. 48a) with factor (1 - j/m), one graph;
+//   join;     y = G_FE v_FE - G_PD v_PD, lambda_m = (-H)^-1 y (Eq. 49);
+//             FE correction a += -X lambda_m with X = K_eff^-1 G_FE^T (unit
+//             responses, Eq. unit); PD correction U += W from the link problem
+//             (Eq. 48b, zero start, factor j/m, bond words of the step start,
+//             no breaking); rebuild flag if a bond near an overlap band broke.
+// Conventions follow Eq. 33: FE carries +G_FE^T lambda, PD -G_PD^T lambda and
+// the constraint is G_FE v_FE - G_PD v_PD = 0. All coupling arithmetic is FP64.
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <new>
+
 #include "pd.h"
 
 using namespace pdmts;
 
-int mts_time_changed(pdmts_ctx *) { return PDMTS_OK; }
+// ------------------------------------------------------------ FE handle --
+struct pdmts_fem {
+    pdmts_ctx *ctx = nullptr;
+    int dim = 2, npe = 4;
+    int64_t n = 0, ne = 0;
+    std::vector<double> X;      // dim * n
+    std::vector<int32_t> conn;  // ne * npe
+    double E = 0, nu = 0, rho = 0, thick = 1;
+    std::vector<int32_t> faces;       // nf * 2
+    std::vector<double> face_tr;      // nf * dim
+    // assembled operators (host copies of the alpha-weighted matrices)
+    int W = 18;                       // ELL width (2D Q4: 9 nodes x 2 components)
+    std::vector<int32_t> col;         // ndof * W
+    std::vector<double> kval;         // ndof * W, stiffness K
+    std::vector<double> mass;         // ndof, lumped mass
+    std::vector<double> load;         // ndof, loads P
+    double gersh = 0;                 // Gershgorin bound of M^-1 K
+    // device
+    DevArr<int32_t> d_col;
+    DevArr<double> d_K, d_Keff, d_Minv, d_P;
+    DevArr<double> d_u, d_v, d_a, d_ut, d_vt, d_b, d_r, d_d[2];
+    int64_t device_bytes = 0;
+    // Chebyshev schedule for K_eff (depends on dt_FE)
+    double keff_dt = -1, cheb_theta = 0, cheb_delta = 0;
+    std::vector<double> cheb_c1, cheb_c2;
+    bool assembled = false;
+    int64_t ndof() const { return (int64_t)dim * n; }
 
-extern "C" int mts_destroy_coupling(pdmts_ctx *) { return PDMTS_OK; }
+    template <typename T>
+    int alloc(DevArr<T> &a, int64_t count)
+    {
+        release(a);
+        a.p = (T *)ctx->dalloc(sizeof(T) * (size_t)std::max<int64_t>(count, 1));
+        if (!a.p)
+            return fail(PDMTS_ERR_NOMEM, "FE: device allocation of %lld bytes failed", (long long)(sizeof(T) * count));
+        a.count = count;
+        device_bytes += (int64_t)(sizeof(T) * std::max<int64_t>(count, 1));
+        return PDMTS_OK;
+    }
+    template <typename T>
+    void release(DevArr<T> &a)
+    {
+        if (a.p)
+            ctx->dfree(a.p);
+        a.p = nullptr;
+        a.count = 0;
+    }
+    void release_all()
+    {
+        release(d_col); release(d_K); release(d_Keff); release(d_Minv); release(d_P);
+        release(d_u); release(d_v); release(d_a); release(d_ut); release(d_vt); release(d_b); release(d_r);
+        release(d_d[0]); release(d_d[1]);
+    }
+};
 
-int mts_advance_coupled(pdmts_ctx *, int64_t)
+struct BandDesc {
+    int axis;
+    double lo, hi;
+    int fe_side;
+};
+
+// Arlequin weight (Sec. 3.2) at a point: t = normalised distance to the FE
+// boundary of the band; linear t, cubic t^3, constant 1/2; `outside` elsewhere.
+static double arlequin_alpha(const std::vector<BandDesc> &bands, int kind, const double *x, double outside)
 {
-    return fail(PDMTS_ERR_UNSUPPORTED, "mts_advance: coupled stepping not available");
+    for (const BandDesc &b : bands) {
+        const double c = x[b.axis];
+        if (c >= b.lo && c <= b.hi) {
+            const double t = b.fe_side < 0 ? (b.hi - c) / (b.hi - b.lo) : (c - b.lo) / (b.hi - b.lo);
+            if (kind == PDMTS_WEIGHT_CONSTANT)
+                return 0.5;
+            if (kind == PDMTS_WEIGHT_CUBIC)
+                return t * t * t;
+            return t;
+        }
+    }
+    return outside;
+}
+
+// ------------------------------------------------------- arlequin handle --
+struct pdmts_arl {
+    pdmts_ctx *ctx = nullptr;
+    pdmts_pd *pd = nullptr;
+    pdmts_fem *fe = nullptr;
+    int kind = PDMTS_WEIGHT_LINEAR;
+    std::vector<BandDesc> bands;
+    int64_t nl = 0, nlam = 0;        // multiplier nodes, multiplier components (dim * nl)
+    std::vector<int32_t> lam_node;   // FE node of each multiplier node
+    // G_FE rows (ELL, width 9 in 2D) per multiplier node; G_PD rows (CSR)
+    int gfe_w = 9;
+    std::vector<int32_t> gfe_col;
+    std::vector<double> gfe_val;
+    std::vector<int64_t> gpd_ptr;
+    std::vector<int32_t> gpd_col;
+    std::vector<double> gpd_val;
+    // PD overlap nodes: element corners (multiplier ids) and shape values
+    std::vector<int32_t> ov_node, ov_k;
+    std::vector<double> ov_N;
+    int64_t n_ov = 0;
+    // device
+    DevArr<int32_t> d_gfe_col, d_gpd_col, d_ov_node, d_ov_k, d_owner;
+    DevArr<double> d_gfe_val, d_gpd_val, d_ov_N, d_X, d_Hneg_inv, d_colbuf, d_lam0, d_lam, d_y, d_unit;
+    DevArr<double> d_B[4];          // block Chebyshev work (x, r, d0, d1)
+    DevArr<int64_t> d_gpd_ptr;
+    DevArr<uint8_t> d_near;         // bond words of nodes within (m + 1) delta of a band
+    DevArr<unsigned long long> d_changed;
+    unsigned long long *h_changed = nullptr;  // pinned
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_flag = nullptr;
+    cudaStream_t fe_stream = nullptr;
+    bool H_valid = false, X_valid = false, flag_pending = false;
+    int64_t rebuilds = 0, colors = 0;
+    int built_m = 0;
+    std::vector<double> theta_free, theta_link;
+    int64_t device_bytes = 0;
+
+    template <typename T>
+    int alloc(DevArr<T> &a, int64_t count)
+    {
+        release(a);
+        a.p = (T *)ctx->dalloc(sizeof(T) * (size_t)std::max<int64_t>(count, 1));
+        if (!a.p)
+            return fail(PDMTS_ERR_NOMEM, "coupling: device allocation of %lld bytes failed",
+                        (long long)(sizeof(T) * count));
+        a.count = count;
+        device_bytes += (int64_t)(sizeof(T) * std::max<int64_t>(count, 1));
+        return PDMTS_OK;
+    }
+    template <typename T>
+    void release(DevArr<T> &a)
+    {
+        if (a.p)
+            ctx->dfree(a.p);
+        a.p = nullptr;
+        a.count = 0;
+    }
+    void release_all()
+    {
+        release(d_gfe_col); release(d_gpd_col); release(d_ov_node); release(d_ov_k); release(d_owner);
+        release(d_gfe_val); release(d_gpd_val); release(d_ov_N); release(d_X); release(d_Hneg_inv);
+        release(d_colbuf); release(d_lam0); release(d_lam); release(d_y); release(d_unit);
+        for (auto &b : d_B)
+            release(b);
+        release(d_gpd_ptr); release(d_near); release(d_changed);
+    }
+};
+
+template <typename T>
+static int h2d(T *dst, const std::vector<T> &src, cudaStream_t s)
+{
+    if (src.empty())
+        return PDMTS_OK;
+    PDMTS_CUDA_TRY(cudaMemcpyAsync(dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice, s));
+    return PDMTS_OK;
+}
+
+// ------------------------------------------------------------ FE kernels --
+// Newmark predictor (Eq. 38 / Eq. 39): u~ = u + dt v + (1/2 - beta) dt^2 a,
+// v~ = v + (1 - gamma) dt a, and b = P - K u~ needs the full u~ (second kernel).
+__global__ void k_fe_predict(const int64_t ndof, const double *__restrict__ u, const double *__restrict__ v,
+                             const double *__restrict__ a, const double dt, const double beta, const double gamma,
+                             double *__restrict__ ut, double *__restrict__ vt)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ndof)
+        return;
+    ut[i] = u[i] + dt * v[i] + (0.5 - beta) * dt * dt * a[i];
+    vt[i] = v[i] + (1.0 - gamma) * dt * a[i];
+}
+
+// y = b - A x (ELL rows), optionally d = y / (theta M)
+__global__ void k_fe_residual(const int64_t ndof, const int W, const int32_t *__restrict__ col,
+                              const double *__restrict__ val, const double *__restrict__ x,
+                              const double *__restrict__ b, double *__restrict__ r, const double *__restrict__ Minv,
+                              const double inv_theta, double *__restrict__ d)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ndof)
+        return;
+    double ax = 0.0;
+    for (int e = 0; e < W; ++e)
+        ax += val[i * W + e] * x[col[i * W + e]];
+    const double ri = (b ? b[i] : 0.0) - ax;
+    r[i] = ri;
+    if (d)
+        d[i] = inv_theta * Minv[i] * ri;
+}
+
+// One Chebyshev iteration for K_eff x = b preconditioned by the lumped mass,
+// on nrhs column-major vectors: x += d; r -= K_eff d; d' = c1 d + c2 M^-1 r.
+__global__ void k_cheb_iter(const int64_t ndof, const int nrhs, const int W, const int32_t *__restrict__ col,
+                            const double *__restrict__ val, const double *__restrict__ Minv, double *__restrict__ x,
+                            double *__restrict__ r, const double *__restrict__ d, double *__restrict__ dn,
+                            const double c1, const double c2)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ndof * nrhs)
+        return;
+    const int64_t c = t / ndof, i = t - c * ndof;
+    const double *dc = d + c * ndof;
+    double ad = 0.0;
+    for (int e = 0; e < W; ++e)
+        ad += val[i * W + e] * dc[col[i * W + e]];
+    x[t] += d[t];
+    const double rn = r[t] - ad;
+    r[t] = rn;
+    if (dn)
+        dn[t] = c1 * d[t] + c2 * Minv[i] * rn;
+}
+
+// Newmark corrector: u = u~ + beta dt^2 a, v = v~ + gamma dt a.
+__global__ void k_fe_correct_state(const int64_t ndof, const double *__restrict__ ut, const double *__restrict__ vt,
+                                   const double *__restrict__ a, const double dt, const double beta,
+                                   const double gamma, double *__restrict__ u, double *__restrict__ v)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ndof)
+        return;
+    u[i] = ut[i] + beta * dt * dt * a[i];
+    v[i] = vt[i] + gamma * dt * a[i];
+}
+
+// FE link response added to the state: a_W = -X lambda (X column-major), u +=
+// beta dt^2 a_W, v += gamma dt a_W, a += a_W.
+__global__ void k_fe_link_add(const int64_t ndof, const int64_t nlam, const double *__restrict__ X,
+                              const double *__restrict__ lam, const double dt, const double beta, const double gamma,
+                              double *__restrict__ u, double *__restrict__ v, double *__restrict__ a)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ndof)
+        return;
+    double s = 0.0;
+    for (int64_t q = 0; q < nlam; ++q)
+        s += X[i + q * ndof] * lam[q];
+    const double aw = -s;
+    u[i] += beta * dt * dt * aw;
+    v[i] += gamma * dt * aw;
+    a[i] += aw;
+}
+
+// Right-hand sides G_FE^T e_q for a batch of multiplier columns q0..q0+nb-1.
+__global__ void k_gfe_rhs(const int64_t nfe, const int dim, const int64_t nl, const int gfe_w,
+                          const int32_t *__restrict__ gcol, const double *__restrict__ gval, const int64_t q0,
+                          const int nb, double *__restrict__ B)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)nb)
+        return;
+    const int64_t q = q0 + t;
+    const int c = (int)(q / nl);
+    const int64_t k = q - (int64_t)c * nl;
+    const int64_t ndof = (int64_t)dim * nfe;
+    for (int e = 0; e < gfe_w; ++e) {
+        const double g = gval[k * gfe_w + e];
+        if (g != 0.0)
+            B[t * ndof + (int64_t)c * nfe + gcol[k * gfe_w + e]] += g;
+    }
+}
+
+// H_FE[r, q] = -gamma dt (G_FE X)[r, q] for all rows r, columns q (row-major H).
+__global__ void k_hfe(const int64_t nfe, const int dim, const int64_t nl, const int gfe_w,
+                      const int32_t *__restrict__ gcol, const double *__restrict__ gval, const double *__restrict__ X,
+                      const double scale, double *__restrict__ H)
+{
+    const int64_t nlam = (int64_t)dim * nl;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nlam * nlam)
+        return;
+    const int64_t r = t / nlam, q = t - r * nlam;
+    const int c = (int)(r / nl);
+    const int64_t k = r - (int64_t)c * nl;
+    const int64_t ndof = (int64_t)dim * nfe;
+    double s = 0.0;
+    for (int e = 0; e < gfe_w; ++e)
+        s += gval[k * gfe_w + e] * X[q * ndof + (int64_t)c * nfe + gcol[k * gfe_w + e]];
+    H[t] = scale * s;
+}
+
+// H[r, owner[r]] += sign * y[r] for the rows a colored link run measures.
+__global__ void k_scatter_color(const int64_t nlam, const int32_t *__restrict__ owner, const double *__restrict__ y,
+                                const double sign, double *__restrict__ H)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nlam)
+        return;
+    const int32_t q = owner[r];
+    if (q >= 0)
+        H[r * nlam + q] += sign * y[r];
+}
+
+__global__ void k_negate(const int64_t n, double *__restrict__ A)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n)
+        A[i] = -A[i];
+}
+
+// In-place Gauss-Jordan inversion of a symmetric positive definite matrix,
+// one pivot per launch triple (no pivoting needed for SPD).
+__global__ void k_gj_save_col(const int64_t n, const double *__restrict__ A, const int64_t p, double *__restrict__ cb)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n)
+        cb[i] = A[i * n + p];
+}
+__global__ void k_gj_scale_row(const int64_t n, double *__restrict__ A, const int64_t p,
+                               const double *__restrict__ cb)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n)
+        return;
+    const double piv = cb[p];
+    A[p * n + j] = (j == p) ? 1.0 / piv : A[p * n + j] / piv;
+}
+__global__ void k_gj_update(const int64_t n, double *__restrict__ A, const int64_t p, const double *__restrict__ cb)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * n)
+        return;
+    const int64_t i = t / n, j = t - i * n;
+    if (i == p)
+        return;
+    const double f = cb[i];
+    if (j == p)
+        A[t] = -f * A[p * n + p];
+    else
+        A[t] -= f * A[p * n + j];
+}
+
+// y = A x for a row-major n x n matrix, one warp per row.
+__global__ void k_gemv_rows(const int64_t n, const double *__restrict__ A, const double *__restrict__ x,
+                            const double scale, double *__restrict__ y)
+{
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= n)
+        return;
+    double s = 0.0;
+    for (int64_t j = lane; j < n; j += 32)
+        s += A[row * n + j] * x[j];
+    for (int o = 16; o > 0; o >>= 1)
+        s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0)
+        y[row] = scale * s;
+}
+
+static inline unsigned blocks(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+// ------------------------------------------------------- FE assembly ------
+// alpha-weighted Q4 plane-stress element stiffness and lumped mass with 2 x 2
+// Gauss points (Eq. 24 ff., Eq. 34).
+static void q4_element(const pdmts_fem *fe, const std::vector<BandDesc> &bands, int kind, int64_t e, double ke[8][8],
+                       double me[4])
+{
+    const double g = 1.0 / std::sqrt(3.0);
+    const double nat[4][2] = {{-1, -1}, {1, -1}, {1, 1}, {-1, 1}};
+    const double c = fe->E / (1.0 - fe->nu * fe->nu);
+    const double D[3][3] = {{c, c * fe->nu, 0}, {c * fe->nu, c, 0}, {0, 0, c * (1.0 - fe->nu) / 2.0}};
+    double xe[4][2];
+    for (int a = 0; a < 4; ++a)
+        for (int d = 0; d < 2; ++d)
+            xe[a][d] = fe->X[(size_t)d * fe->n + fe->conn[(size_t)e * 4 + a]];
+    for (int a = 0; a < 8; ++a)
+        for (int b = 0; b < 8; ++b)
+            ke[a][b] = 0.0;
+    for (int a = 0; a < 4; ++a)
+        me[a] = 0.0;
+    for (int gi = 0; gi < 2; ++gi)
+        for (int gj = 0; gj < 2; ++gj) {
+            const double xi = gi ? g : -g, et = gj ? g : -g;
+            double N[4], dxi[4], det_[4];
+            for (int a = 0; a < 4; ++a) {
+                N[a] = 0.25 * (1 + nat[a][0] * xi) * (1 + nat[a][1] * et);
+                dxi[a] = 0.25 * nat[a][0] * (1 + nat[a][1] * et);
+                det_[a] = 0.25 * nat[a][1] * (1 + nat[a][0] * xi);
+            }
+            double J[2][2] = {{0, 0}, {0, 0}}, xg[2] = {0, 0};
+            for (int a = 0; a < 4; ++a) {
+                J[0][0] += dxi[a] * xe[a][0];
+                J[0][1] += dxi[a] * xe[a][1];
+                J[1][0] += det_[a] * xe[a][0];
+                J[1][1] += det_[a] * xe[a][1];
+                xg[0] += N[a] * xe[a][0];
+                xg[1] += N[a] * xe[a][1];
+            }
+            const double detJ = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+            double dNx[4], dNy[4];
+            for (int a = 0; a < 4; ++a) {
+                dNx[a] = (J[1][1] * dxi[a] - J[0][1] * det_[a]) / detJ;
+                dNy[a] = (-J[1][0] * dxi[a] + J[0][0] * det_[a]) / detJ;
+            }
+            double B[3][8];
+            for (int a = 0; a < 4; ++a) {
+                B[0][2 * a] = dNx[a]; B[0][2 * a + 1] = 0;
+                B[1][2 * a] = 0;      B[1][2 * a + 1] = dNy[a];
+                B[2][2 * a] = dNy[a]; B[2][2 * a + 1] = dNx[a];
+            }
+            const double al = arlequin_alpha(bands, kind, xg, 1.0);
+            const double w = al * detJ * fe->thick;
+            for (int a = 0; a < 8; ++a)
+                for (int b = 0; b < 8; ++b) {
+                    double s = 0.0;
+                    for (int p = 0; p < 3; ++p)
+                        for (int q = 0; q < 3; ++q)
+                            s += B[p][a] * D[p][q] * B[q][b];
+                    ke[a][b] += w * s;
+                }
+            for (int a = 0; a < 4; ++a)
+                me[a] += al * fe->rho * N[a] * detJ * fe->thick;
+        }
+}
+
+static int fe_assemble(pdmts_fem *fe, const std::vector<BandDesc> &bands, int kind)
+{
+    const int64_t n = fe->n, ndof = fe->ndof();
+    std::vector<std::map<int32_t, double>> rows((size_t)ndof);
+    fe->mass.assign((size_t)ndof, 0.0);
+    for (int64_t e = 0; e < fe->ne; ++e) {
+        double ke[8][8], me[4];
+        q4_element(fe, bands, kind, e, ke, me);
+        int64_t dof[8];
+        for (int a = 0; a < 4; ++a) {
+            const int64_t node = fe->conn[(size_t)e * 4 + a];
+            dof[2 * a] = node;
+            dof[2 * a + 1] = n + node;
+            fe->mass[(size_t)node] += me[a];
+            fe->mass[(size_t)(n + node)] += me[a];
+        }
+        for (int a = 0; a < 8; ++a)
+            for (int b = 0; b < 8; ++b)
+                rows[(size_t)dof[a]][(int32_t)dof[b]] += ke[a][b];
+    }
+    int W = 0;
+    for (auto &r : rows)
+        W = std::max<int>(W, (int)r.size());
+    fe->W = std::max(W, 1);
+    fe->col.assign((size_t)ndof * fe->W, 0);
+    fe->kval.assign((size_t)ndof * fe->W, 0.0);
+    double gersh = 0.0;
+    for (int64_t i = 0; i < ndof; ++i) {
+        if (!(fe->mass[(size_t)i] > 0))
+            return fail(PDMTS_ERR_MASS, "FE dof %lld has no mass (alpha vanishes on its support)", (long long)i);
+        int e = 0;
+        double rs = 0.0;
+        for (auto &kv : rows[(size_t)i]) {
+            fe->col[(size_t)i * fe->W + e] = kv.first;
+            fe->kval[(size_t)i * fe->W + e] = kv.second;
+            rs += std::fabs(kv.second);
+            ++e;
+        }
+        for (; e < fe->W; ++e)
+            fe->col[(size_t)i * fe->W + e] = (int32_t)i;
+        gersh = std::max(gersh, rs / fe->mass[(size_t)i]);
+    }
+    fe->gersh = gersh;
+    // consistent traction loads, weighted by alpha at the face midpoint (Eq. 34)
+    fe->load.assign((size_t)ndof, 0.0);
+    const int64_t nf = (int64_t)fe->faces.size() / 2;
+    for (int64_t f = 0; f < nf; ++f) {
+        const int64_t i = fe->faces[(size_t)2 * f], j = fe->faces[(size_t)2 * f + 1];
+        const double dx = fe->X[(size_t)j] - fe->X[(size_t)i], dy = fe->X[(size_t)n + j] - fe->X[(size_t)n + i];
+        const double L = std::sqrt(dx * dx + dy * dy);
+        const double xm[2] = {0.5 * (fe->X[(size_t)i] + fe->X[(size_t)j]),
+                              0.5 * (fe->X[(size_t)n + i] + fe->X[(size_t)n + j])};
+        const double al = arlequin_alpha(bands, kind, xm, 1.0);
+        for (int64_t node : {i, j})
+            for (int d = 0; d < 2; ++d)
+                fe->load[(size_t)(d * n + node)] += al * fe->face_tr[(size_t)f * 2 + d] * L * fe->thick / 2.0;
+    }
+    cudaStream_t s = fe->ctx->stream;
+    PDMTS_TRY(fe->alloc(fe->d_col, ndof * fe->W));
+    PDMTS_TRY(fe->alloc(fe->d_K, ndof * fe->W));
+    PDMTS_TRY(fe->alloc(fe->d_Keff, ndof * fe->W));
+    PDMTS_TRY(fe->alloc(fe->d_Minv, ndof));
+    PDMTS_TRY(fe->alloc(fe->d_P, ndof));
+    std::vector<double> minv((size_t)ndof);
+    for (int64_t i = 0; i < ndof; ++i)
+        minv[(size_t)i] = 1.0 / fe->mass[(size_t)i];
+    PDMTS_TRY(h2d(fe->d_col.p, fe->col, s));
+    PDMTS_TRY(h2d(fe->d_K.p, fe->kval, s));
+    PDMTS_TRY(h2d(fe->d_Minv.p, minv, s));
+    PDMTS_TRY(h2d(fe->d_P.p, fe->load, s));
+    for (DevArr<double> *a : {&fe->d_u, &fe->d_v, &fe->d_a, &fe->d_ut, &fe->d_vt, &fe->d_b, &fe->d_r, &fe->d_d[0],
+                              &fe->d_d[1]}) {
+        PDMTS_TRY(fe->alloc(*a, ndof));
+        PDMTS_CUDA_TRY(cudaMemsetAsync(a->p, 0, sizeof(double) * ndof, s));
+    }
+    // initial acceleration from the equation of motion with u = 0, lambda_0 = 0
+    std::vector<double> a0((size_t)ndof);
+    for (int64_t i = 0; i < ndof; ++i)
+        a0[(size_t)i] = fe->load[(size_t)i] / fe->mass[(size_t)i];
+    PDMTS_TRY(h2d(fe->d_a.p, a0, s));
+    PDMTS_CUDA_TRY(cudaStreamSynchronize(s));
+    fe->assembled = true;
+    fe->keff_dt = -1;
+    return PDMTS_OK;
+}
+
+// K_eff = M + beta dt^2 K and its Chebyshev schedule. The spectrum of
+// M^-1 K_eff lies in [1, 1 + beta dt^2 rho(M^-1 K)] with the Gershgorin bound
+// for rho; the iteration count gives a relative error below 1e-15.
+static int fe_prepare_keff(pdmts_fem *fe, double dt, double beta)
+{
+    if (fe->keff_dt == dt)
+        return PDMTS_OK;
+    const int64_t ndof = fe->ndof();
+    std::vector<double> keff(fe->kval);
+    for (int64_t i = 0; i < ndof; ++i) {
+        keff[(size_t)i * fe->W + 0] *= 1.0;
+        for (int e = 0; e < fe->W; ++e)
+            keff[(size_t)i * fe->W + e] *= beta * dt * dt;
+        bool found = false;
+        for (int e = 0; e < fe->W; ++e)
+            if (fe->col[(size_t)i * fe->W + e] == (int32_t)i && !found) {
+                keff[(size_t)i * fe->W + e] += fe->mass[(size_t)i];
+                found = true;
+            }
+        if (!found)
+            return fail(PDMTS_ERR_STATE, "FE matrix row %lld lacks a diagonal entry", (long long)i);
+    }
+    PDMTS_TRY(h2d(fe->d_Keff.p, keff, fe->ctx->stream));
+    const double lmin = 1.0, lmax = 1.0 + beta * dt * dt * fe->gersh;
+    fe->cheb_theta = 0.5 * (lmax + lmin);
+    fe->cheb_delta = 0.5 * (lmax - lmin);
+    const double kappa = lmax / lmin;
+    const double q = (std::sqrt(kappa) - 1.0) / (std::sqrt(kappa) + 1.0);
+    int it = q > 0 ? (int)std::ceil(std::log(2.0 / 1e-16) / std::log(1.0 / q)) + 2 : 1;
+    it = std::max(it, 1);
+    fe->cheb_c1.assign((size_t)it, 0.0);
+    fe->cheb_c2.assign((size_t)it, 0.0);
+    const double sigma = fe->cheb_theta / std::max(fe->cheb_delta, 1e-300);
+    double rho = 1.0 / sigma;
+    for (int k = 0; k < it; ++k) {
+        const double rn = 1.0 / (2.0 * sigma - rho);
+        fe->cheb_c1[(size_t)k] = rn * rho;
+        fe->cheb_c2[(size_t)k] = 2.0 * rn / std::max(fe->cheb_delta, 1e-300);
+        rho = rn;
+    }
+    fe->keff_dt = dt;
+    PDMTS_CUDA_TRY(cudaStreamSynchronize(fe->ctx->stream));
+    return PDMTS_OK;
+}
+
+// x <- K_eff^-1 b on nrhs column-major vectors (x holds the initial guess).
+// Work arrays r, d0, d1 have the same shape.
+static int fe_cheb_solve(pdmts_fem *fe, int nrhs, double *x, const double *b, double *r, double *d0, double *d1,
+                         cudaStream_t s, int64_t *launches)
+{
+    const int64_t ndof = fe->ndof();
+    const int64_t tot = ndof * nrhs;
+    for (int c = 0; c < nrhs; ++c) {
+        k_fe_residual<<<blocks(ndof), 256, 0, s>>>(ndof, fe->W, fe->d_col.p, fe->d_Keff.p, x + c * ndof,
+                                                  b + c * ndof, r + c * ndof, fe->d_Minv.p, 1.0 / fe->cheb_theta,
+                                                  d0 + c * ndof);
+        ++*launches;
+    }
+    double *d = d0, *dn = d1;
+    const int it = (int)fe->cheb_c1.size();
+    for (int k = 0; k < it; ++k) {
+        const bool last = k == it - 1;
+        k_cheb_iter<<<blocks(tot), 256, 0, s>>>(ndof, nrhs, fe->W, fe->d_col.p, fe->d_Keff.p, fe->d_Minv.p, x, r, d,
+                                                last ? nullptr : dn, fe->cheb_c1[(size_t)k], fe->cheb_c2[(size_t)k]);
+        ++*launches;
+        std::swap(d, dn);
+    }
+    PDMTS_CUDA_TRY(cudaGetLastError());
+    return PDMTS_OK;
+}
+
+// Free FE step (Eq. 47a + Eq. 39): predictor, K_eff a = P - K u~, corrector.
+static int fe_free_step(pdmts_fem *fe, double dt, double beta, double gamma, cudaStream_t s, int64_t *launches)
+{
+    const int64_t ndof = fe->ndof();
+    k_fe_predict<<<blocks(ndof), 256, 0, s>>>(ndof, fe->d_u.p, fe->d_v.p, fe->d_a.p, dt, beta, gamma, fe->d_ut.p,
+                                              fe->d_vt.p);
+    k_fe_residual<<<blocks(ndof), 256, 0, s>>>(ndof, fe->W, fe->d_col.p, fe->d_K.p, fe->d_ut.p, fe->d_P.p, fe->d_b.p,
+                                               nullptr, 0.0, nullptr);
+    *launches += 2;
+    // warm start from the previous acceleration (kept in d_a)
+    PDMTS_TRY(fe_cheb_solve(fe, 1, fe->d_a.p, fe->d_b.p, fe->d_r.p, fe->d_d[0].p, fe->d_d[1].p, s, launches));
+    k_fe_correct_state<<<blocks(ndof), 256, 0, s>>>(ndof, fe->d_ut.p, fe->d_vt.p, fe->d_a.p, dt, beta, gamma,
+                                                    fe->d_u.p, fe->d_v.p);
+    ++*launches;
+    PDMTS_CUDA_TRY(cudaGetLastError());
+    return PDMTS_OK;
+}
+
+// ------------------------------------------------------------ FE ABI -----
+extern "C" int fem_create(pdmts_ctx *ctx, int dim, int64_t n_nodes, const double *Xn, int64_t n_elems,
+                          int nodes_per_elem, const int32_t *conn, double E, double nu, double rho, double thickness,
+                          pdmts_fem **out)
+{
+    clear_error();
+    if (!ctx || !Xn || !conn || !out)
+        return fail(PDMTS_ERR_ARG, "fem_create: NULL argument");
+    *out = nullptr;
+    if (ctx->fem)
+        return fail(PDMTS_ERR_STATE, "fem_create: context already has a finite-element subdomain");
+    if (dim != 2 || nodes_per_elem != 4)
+        return fail(PDMTS_ERR_UNSUPPORTED, "fem_create: this build supports 2D Q4 elements (dim 2, 4 nodes)");
+    if (n_nodes <= 0 || n_elems <= 0 || n_nodes >= ((int64_t)1 << 30))
+        return fail(PDMTS_ERR_ARG, "fem_create: bad sizes");
+    if (!(E > 0) || !(rho > 0) || !(thickness > 0) || !(nu > -1.0 && nu < 0.5))
+        return fail(PDMTS_ERR_ARG, "fem_create: bad material (E, rho, thickness > 0; -1 < nu < 1/2)");
+    auto *fe = new (std::nothrow) pdmts_fem();
+    if (!fe)
+        return fail(PDMTS_ERR_NOMEM, "fem_create: out of host memory");
+    fe->ctx = ctx;
+    fe->dim = dim;
+    fe->n = n_nodes;
+    fe->ne = n_elems;
+    fe->npe = nodes_per_elem;
+    fe->E = E;
+    fe->nu = nu;
+    fe->rho = rho;
+    fe->thick = thickness;
+    fe->X.resize((size_t)dim * n_nodes);
+    fe->conn.resize((size_t)n_elems * nodes_per_elem);
+    if (cudaMemcpy(fe->X.data(), Xn, sizeof(double) * fe->X.size(), cudaMemcpyDefault) != cudaSuccess ||
+        cudaMemcpy(fe->conn.data(), conn, sizeof(int32_t) * fe->conn.size(), cudaMemcpyDefault) != cudaSuccess) {
+        delete fe;
+        return fail(PDMTS_ERR_CUDA, "fem_create: copying inputs failed");
+    }
+    for (int32_t c : fe->conn)
+        if (c < 0 || c >= n_nodes) {
+            delete fe;
+            return fail(PDMTS_ERR_ARG, "fem_create: connectivity index out of range");
+        }
+    for (double x : fe->X)
+        if (!std::isfinite(x)) {
+            delete fe;
+            return fail(PDMTS_ERR_ARG, "fem_create: non-finite node coordinate");
+        }
+    ctx->fem = fe;
+    *out = fe;
+    return PDMTS_OK;
+}
+
+extern "C" int fem_set_traction(pdmts_fem *fe, int64_t n_faces, const int32_t *face_nodes, const double *traction)
+{
+    clear_error();
+    if (!fe || n_faces < 0 || (n_faces > 0 && (!face_nodes || !traction)))
+        return fail(PDMTS_ERR_ARG, "fem_set_traction: bad arguments");
+    std::vector<int32_t> f((size_t)2 * n_faces);
+    std::vector<double> t((size_t)2 * n_faces);
+    if (n_faces > 0 &&
+        (cudaMemcpy(f.data(), face_nodes, sizeof(int32_t) * f.size(), cudaMemcpyDefault) != cudaSuccess ||
+         cudaMemcpy(t.data(), traction, sizeof(double) * t.size(), cudaMemcpyDefault) != cudaSuccess))
+        return fail(PDMTS_ERR_CUDA, "fem_set_traction: copying inputs failed");
+    for (int32_t c : f)
+        if (c < 0 || c >= fe->n)
+            return fail(PDMTS_ERR_ARG, "fem_set_traction: face node out of range");
+    for (double x : t)
+        if (!std::isfinite(x))
+            return fail(PDMTS_ERR_ARG, "fem_set_traction: non-finite traction");
+    if (fe->assembled)
+        return fail(PDMTS_ERR_STATE, "fem_set_traction: set tractions before arlequin_bind");
+    fe->faces.swap(f);
+    fe->face_tr.swap(t);
+    return PDMTS_OK;
+}
+
+extern "C" int fem_destroy(pdmts_fem *fe)
+{
+    clear_error();
+    if (!fe)
+        return PDMTS_OK;
+    cudaSetDevice(fe->ctx->device);
+    cudaStreamSynchronize(fe->ctx->stream);
+    if (fe->ctx->fem == fe)
+        fe->ctx->fem = nullptr;
+    fe->release_all();
+    delete fe;
+    return PDMTS_OK;
+}
+
+static int fem_read(pdmts_fem *fe, int which, double *out)
+{
+    if (!fe || !out)
+        return fail(PDMTS_ERR_ARG, "fem_read: NULL argument");
+    if (!fe->assembled)
+        return fail(PDMTS_ERR_STATE, "fem_read: the FE subdomain is not bound to a coupling yet");
+    PDMTS_CUDA_TRY(cudaSetDevice(fe->ctx->device));
+    PDMTS_TRY(fe->ctx->begin());
+    const double *src = which == 0 ? fe->d_u.p : which == 1 ? fe->d_v.p : fe->d_a.p;
+    PDMTS_CUDA_TRY(cudaMemcpyAsync(out, src, sizeof(double) * fe->ndof(), cudaMemcpyDefault, fe->ctx->stream));
+    PDMTS_CUDA_TRY(cudaStreamSynchronize(fe->ctx->stream));
+    return fe->ctx->end();
+}
+extern "C" int fem_set_state(pdmts_fem *fe, const double *u, const double *v)
+{
+    clear_error();
+    if (!fe)
+        return fail(PDMTS_ERR_ARG, "fem_set_state: fe is NULL");
+    if (!fe->assembled)
+        return fail(PDMTS_ERR_STATE, "fem_set_state: bind the FE subdomain to a coupling first");
+    const int64_t nd = fe->ndof();
+    std::vector<double> hu((size_t)nd, 0.0), hv((size_t)nd, 0.0);
+    if (u)
+        PDMTS_CUDA_TRY(cudaMemcpy(hu.data(), u, sizeof(double) * nd, cudaMemcpyDefault));
+    if (v)
+        PDMTS_CUDA_TRY(cudaMemcpy(hv.data(), v, sizeof(double) * nd, cudaMemcpyDefault));
+    for (int64_t i = 0; i < nd; ++i)
+        if (!std::isfinite(hu[(size_t)i]) || !std::isfinite(hv[(size_t)i]))
+            return fail(PDMTS_ERR_ARG, "fem_set_state: non-finite value");
+    // acceleration from the equation of motion M a = P - K u (lambda = 0)
+    std::vector<double> a((size_t)nd);
+    for (int64_t i = 0; i < nd; ++i) {
+        double ku = 0.0;
+        for (int e = 0; e < fe->W; ++e)
+            ku += fe->kval[(size_t)i * fe->W + e] * hu[(size_t)fe->col[(size_t)i * fe->W + e]];
+        a[(size_t)i] = (fe->load[(size_t)i] - ku) / fe->mass[(size_t)i];
+    }
+    PDMTS_CUDA_TRY(cudaSetDevice(fe->ctx->device));
+    PDMTS_TRY(fe->ctx->begin());
+    cudaStream_t s = fe->ctx->stream;
+    PDMTS_TRY(h2d(fe->d_u.p, hu, s));
+    PDMTS_TRY(h2d(fe->d_v.p, hv, s));
+    PDMTS_TRY(h2d(fe->d_a.p, a, s));
+    PDMTS_CUDA_TRY(cudaStreamSynchronize(s));
+    return fe->ctx->end();
+}
+
+extern "C" int fem_read_displacement(pdmts_fem *fe, double *u) { clear_error(); return fem_read(fe, 0, u); }
+extern "C" int fem_read_velocity(pdmts_fem *fe, double *v) { clear_error(); return fem_read(fe, 1, v); }
+extern "C" int fem_read_acceleration(pdmts_fem *fe, double *a) { clear_error(); return fem_read(fe, 2, a); }
+
+// ------------------------------------------------------- coupling set-up --
+// Multiplier nodes, G_FE, G_PD and the PD overlap interpolation (Eq. 33, Eq. 41).
+static int build_constraint(pdmts_arl *A)
+{
+    pdmts_fem *fe = A->fe;
+    pdmts_pd *pd = A->pd;
+    const int64_t nfe = fe->n, npd = pd->n;
+    // overlap elements: centroid strictly inside a band
+    std::vector<int64_t> ov_el;
+    std::vector<char> is_lam((size_t)nfe, 0);
+    for (int64_t e = 0; e < fe->ne; ++e) {
+        double c[2] = {0, 0};
+        for (int a = 0; a < 4; ++a)
+            for (int d = 0; d < 2; ++d)
+                c[d] += 0.25 * fe->X[(size_t)d * nfe + fe->conn[(size_t)e * 4 + a]];
+        for (const BandDesc &b : A->bands)
+            if (c[b.axis] > b.lo && c[b.axis] < b.hi) {
+                ov_el.push_back(e);
+                for (int a = 0; a < 4; ++a)
+                    is_lam[(size_t)fe->conn[(size_t)e * 4 + a]] = 1;
+                break;
+            }
+    }
+    if (ov_el.empty())
+        return fail(PDMTS_ERR_ARG, "arlequin_bind: no finite element lies inside an overlap band");
+    std::vector<int32_t> pos((size_t)nfe, -1);
+    A->lam_node.clear();
+    for (int64_t i = 0; i < nfe; ++i)
+        if (is_lam[(size_t)i]) {
+            pos[(size_t)i] = (int32_t)A->lam_node.size();
+            A->lam_node.push_back((int32_t)i);
+        }
+    A->nl = (int64_t)A->lam_node.size();
+    A->nlam = 2 * A->nl;
+    // G_FE[k, I] = int_O N_k N_I dV (2 x 2 Gauss), rows of width 9
+    std::vector<std::map<int32_t, double>> grow((size_t)A->nl);
+    const double g = 1.0 / std::sqrt(3.0);
+    const double nat[4][2] = {{-1, -1}, {1, -1}, {1, 1}, {-1, 1}};
+    for (int64_t e : ov_el) {
+        double xe[4][2];
+        for (int a = 0; a < 4; ++a)
+            for (int d = 0; d < 2; ++d)
+                xe[a][d] = fe->X[(size_t)d * nfe + fe->conn[(size_t)e * 4 + a]];
+        for (int gi = 0; gi < 2; ++gi)
+            for (int gj = 0; gj < 2; ++gj) {
+                const double xi = gi ? g : -g, et = gj ? g : -g;
+                double N[4], dxi[4], det_[4];
+                for (int a = 0; a < 4; ++a) {
+                    N[a] = 0.25 * (1 + nat[a][0] * xi) * (1 + nat[a][1] * et);
+                    dxi[a] = 0.25 * nat[a][0] * (1 + nat[a][1] * et);
+                    det_[a] = 0.25 * nat[a][1] * (1 + nat[a][0] * xi);
+                }
+                double J00 = 0, J01 = 0, J10 = 0, J11 = 0;
+                for (int a = 0; a < 4; ++a) {
+                    J00 += dxi[a] * xe[a][0]; J01 += dxi[a] * xe[a][1];
+                    J10 += det_[a] * xe[a][0]; J11 += det_[a] * xe[a][1];
+                }
+                const double w = (J00 * J11 - J01 * J10) * fe->thick;
+                for (int a = 0; a < 4; ++a)
+                    for (int b = 0; b < 4; ++b)
+                        grow[(size_t)pos[(size_t)fe->conn[(size_t)e * 4 + a]]][fe->conn[(size_t)e * 4 + b]] +=
+                            N[a] * N[b] * w;
+            }
+    }
+    A->gfe_w = 0;
+    for (auto &r : grow)
+        A->gfe_w = std::max<int>(A->gfe_w, (int)r.size());
+    A->gfe_col.assign((size_t)A->nl * A->gfe_w, 0);
+    A->gfe_val.assign((size_t)A->nl * A->gfe_w, 0.0);
+    for (int64_t k = 0; k < A->nl; ++k) {
+        int e = 0;
+        for (auto &kv : grow[(size_t)k]) {
+            A->gfe_col[(size_t)k * A->gfe_w + e] = kv.first;
+            A->gfe_val[(size_t)k * A->gfe_w + e] = kv.second;
+            ++e;
+        }
+    }
+    // PD nodes inside overlap elements: G_PD[k, p] = N_k(x_p) V_p
+    std::vector<std::vector<std::pair<int32_t, double>>> prow((size_t)A->nl);
+    A->ov_node.clear(); A->ov_k.clear(); A->ov_N.clear();
+    for (int64_t e : ov_el) {
+        double lo[2] = {INFINITY, INFINITY}, hi[2] = {-INFINITY, -INFINITY};
+        int32_t cn[4];
+        for (int a = 0; a < 4; ++a) {
+            cn[a] = fe->conn[(size_t)e * 4 + a];
+            for (int d = 0; d < 2; ++d) {
+                lo[d] = std::min(lo[d], fe->X[(size_t)d * nfe + cn[a]]);
+                hi[d] = std::max(hi[d], fe->X[(size_t)d * nfe + cn[a]]);
+            }
+        }
+        // axis-aligned rectangle: node a at (lo|hi)
+        for (int64_t p = 0; p < npd; ++p) {
+            const double x = pd->X[(size_t)p], y = pd->X[(size_t)npd + p];
+            if (!(x > lo[0] && x < hi[0] && y > lo[1] && y < hi[1]))
+                continue;
+            const double xi = 2.0 * (x - lo[0]) / (hi[0] - lo[0]) - 1.0;
+            const double et = 2.0 * (y - lo[1]) / (hi[1] - lo[1]) - 1.0;
+            A->ov_node.push_back((int32_t)p);
+            for (int a = 0; a < 4; ++a) {
+                // natural coordinates of the corner from its position
+                const double ax = fe->X[(size_t)cn[a]] > 0.5 * (lo[0] + hi[0]) ? 1.0 : -1.0;
+                const double ay = fe->X[(size_t)nfe + cn[a]] > 0.5 * (lo[1] + hi[1]) ? 1.0 : -1.0;
+                const double Na = 0.25 * (1 + ax * xi) * (1 + ay * et);
+                const int32_t k = pos[(size_t)cn[a]];
+                A->ov_k.push_back(k);
+                A->ov_N.push_back(Na);
+                prow[(size_t)k].push_back({(int32_t)p, Na * pd->V[(size_t)p]});
+            }
+        }
+    }
+    A->n_ov = (int64_t)A->ov_node.size();
+    A->gpd_ptr.assign((size_t)A->nl + 1, 0);
+    A->gpd_col.clear();
+    A->gpd_val.clear();
+    for (int64_t k = 0; k < A->nl; ++k) {
+        auto &r = prow[(size_t)k];
+        std::sort(r.begin(), r.end());
+        for (auto &pv : r) {
+            A->gpd_col.push_back(pv.first);
+            A->gpd_val.push_back(pv.second);
+        }
+        A->gpd_ptr[(size_t)k + 1] = (int64_t)A->gpd_col.size();
+    }
+    cudaStream_t s = A->ctx->stream;
+    PDMTS_TRY(A->alloc(A->d_gfe_col, (int64_t)A->gfe_col.size()));
+    PDMTS_TRY(A->alloc(A->d_gfe_val, (int64_t)A->gfe_val.size()));
+    PDMTS_TRY(A->alloc(A->d_gpd_ptr, (int64_t)A->gpd_ptr.size()));
+    PDMTS_TRY(A->alloc(A->d_gpd_col, std::max<int64_t>((int64_t)A->gpd_col.size(), 1)));
+    PDMTS_TRY(A->alloc(A->d_gpd_val, std::max<int64_t>((int64_t)A->gpd_val.size(), 1)));
+    PDMTS_TRY(A->alloc(A->d_ov_node, std::max<int64_t>(A->n_ov, 1)));
+    PDMTS_TRY(A->alloc(A->d_ov_k, std::max<int64_t>(4 * A->n_ov, 1)));
+    PDMTS_TRY(A->alloc(A->d_ov_N, std::max<int64_t>(4 * A->n_ov, 1)));
+    PDMTS_TRY(h2d(A->d_gfe_col.p, A->gfe_col, s));
+    PDMTS_TRY(h2d(A->d_gfe_val.p, A->gfe_val, s));
+    PDMTS_TRY(h2d(A->d_gpd_ptr.p, A->gpd_ptr, s));
+    PDMTS_TRY(h2d(A->d_gpd_col.p, A->gpd_col, s));
+    PDMTS_TRY(h2d(A->d_gpd_val.p, A->gpd_val, s));
+    PDMTS_TRY(h2d(A->d_ov_node.p, A->ov_node, s));
+    PDMTS_TRY(h2d(A->d_ov_k.p, A->ov_k, s));
+    PDMTS_TRY(h2d(A->d_ov_N.p, A->ov_N, s));
+    for (DevArr<double> *a : {&A->d_lam0, &A->d_lam, &A->d_y, &A->d_unit, &A->d_colbuf}) {
+        PDMTS_TRY(A->alloc(*a, A->nlam));
+        PDMTS_CUDA_TRY(cudaMemsetAsync(a->p, 0, sizeof(double) * A->nlam, s));
+    }
+    PDMTS_TRY(A->alloc(A->d_owner, A->nlam));
+    PDMTS_TRY(A->alloc(A->d_Hneg_inv, A->nlam * A->nlam));
+    PDMTS_TRY(A->alloc(A->d_changed, 1));
+    // bond words of PD nodes within (m + 1) delta of a band (rebuild rule)
+    PDMTS_CUDA_TRY(cudaStreamSynchronize(s));
+    return PDMTS_OK;
+}
+
+static int update_near_flags(pdmts_arl *A, int m)
+{
+    pdmts_pd *pd = A->pd;
+    const int64_t npd = pd->n;
+    const double reach = (m + 1) * pd->horizon;
+    std::vector<uint8_t> near_node((size_t)npd, 0);
+    for (int64_t p = 0; p < npd; ++p)
+        for (const BandDesc &b : A->bands) {
+            const double c = pd->X[(size_t)b.axis * npd + p];
+            if (c >= b.lo - reach && c <= b.hi + reach)
+                near_node[(size_t)p] = 1;
+        }
+    std::vector<uint8_t> wflag((size_t)std::max<int64_t>(pd->n_mask_words, 1), 0);
+    if (pd->layout == pdmts_pd::LAYOUT_LATTICE2D) {
+        for (int64_t p = 0; p < npd; ++p)
+            wflag[(size_t)p] = near_node[(size_t)p];
+    } else {
+        for (int64_t p = 0; p < npd; ++p) {
+            const int64_t t = p / 32, lane = p % 32;
+            const int words = (pd->tile_k[(size_t)t] + 31) / 32;
+            for (int w = 0; w < words; ++w)
+                wflag[(size_t)(pd->mask_ptr[(size_t)t] + 32 * w + lane)] = near_node[(size_t)p];
+        }
+    }
+    PDMTS_TRY(A->alloc(A->d_near, (int64_t)wflag.size()));
+    PDMTS_TRY(h2d(A->d_near.p, wflag, A->ctx->stream));
+    PDMTS_CUDA_TRY(cudaStreamSynchronize(A->ctx->stream));
+    return PDMTS_OK;
+}
+
+// Unit responses of the FE subdomain: X = K_eff^-1 G_FE^T (column-major), by
+// block Chebyshev in batches of columns.
+static int build_X(pdmts_arl *A, int64_t *launches)
+{
+    pdmts_fem *fe = A->fe;
+    const int64_t ndof = fe->ndof();
+    const int64_t nlam = A->nlam;
+    cudaStream_t s = A->ctx->stream;
+    PDMTS_TRY(A->alloc(A->d_X, ndof * nlam));
+    const int batch = (int)std::min<int64_t>(nlam, 512);
+    for (int b = 0; b < 4; ++b)
+        PDMTS_TRY(A->alloc(A->d_B[b], ndof * batch));
+    for (int64_t q0 = 0; q0 < nlam; q0 += batch) {
+        const int nb = (int)std::min<int64_t>(batch, nlam - q0);
+        PDMTS_CUDA_TRY(cudaMemsetAsync(A->d_B[0].p, 0, sizeof(double) * ndof * nb, s));
+        k_gfe_rhs<<<blocks(nb), 256, 0, s>>>(fe->n, 2, A->nl, A->gfe_w, A->d_gfe_col.p, A->d_gfe_val.p, q0, nb,
+                                             A->d_B[0].p);
+        double *x = A->d_X.p + q0 * ndof;
+        PDMTS_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * ndof * nb, s));
+        PDMTS_TRY(fe_cheb_solve(fe, nb, x, A->d_B[0].p, A->d_B[1].p, A->d_B[2].p, A->d_B[3].p, s, launches));
+    }
+    for (int b = 0; b < 4; ++b)
+        A->release(A->d_B[b]);
+    A->X_valid = true;
+    PDMTS_CUDA_TRY(cudaGetLastError());
+    return PDMTS_OK;
+}
+
+int pd_run_chain(pdmts_pd *pd, int len, int sched, const double *theta, cudaStream_t s, bool link);
+int pd_invalidate_graphs(pdmts_pd *pd);
+
+// The PD link run (Eq. 48b) for the multiplier in dev_lam: W_0 = 0, m
+// substeps with factor j/m, bond words of the step start, no breaking.
+static int pd_link_run(pdmts_arl *A, const double *dev_lam, int m, cudaStream_t s)
+{
+    pdmts_pd *pd = A->pd;
+    const bool f64 = pd->precision == PDMTS_FP64;
+    cudaError_t e = launch_interface_force(pd->dim, pd->n, A->n_ov, A->d_ov_node.p, A->d_ov_k.p, A->d_ov_N.p, 4,
+                                           dev_lam, A->nl, f64 ? 0.0 : 1.0 / pd->h, f64 ? pd->lk_g.p : nullptr,
+                                           f64 ? nullptr : pd->lk_gf.p, s);
+    if (e != cudaSuccess)
+        return fail(PDMTS_ERR_CUDA, "interface force: %s", cudaGetErrorString(e));
+    PDMTS_TRY(pd->zero_link_state(s));
+    PDMTS_TRY(pd_run_chain(pd, m, 2, A->theta_link.data(), s, true));
+    pd->ctx->stats.kernel_launches += 1;
+    return PDMTS_OK;
+}
+
+// Interface operator H = G_FE Ydot_FE - G_PD Ydot_PD (Eq. 49) and its inverse.
+// Columns of H_PD come from link runs of several unit multipliers at once:
+// columns whose supports are more than 2R apart (R = 2 h_FE + m delta, the
+// reach of a link response over m substeps plus the shape-function supports)
+// cannot be seen by the same constraint row, so each row is attributed to the
+// one column of the run within R of it.
+static int build_H(pdmts_arl *A, int m)
+{
+    pdmts_fem *fe = A->fe;
+    pdmts_pd *pd = A->pd;
+    pdmts_ctx *ctx = A->ctx;
+    cudaStream_t s = ctx->stream;
+    const int64_t nlam = A->nlam, nl = A->nl;
+    int64_t launches = 0;
+    if (!A->X_valid)
+        PDMTS_TRY(build_X(A, &launches));
+    const double gamma = ctx->gamma_fe, dtf = m * ctx->dt_pd;
+    double *H = A->d_Hneg_inv.p;  // holds H while building, then (-H)^-1
+    k_hfe<<<blocks(nlam * nlam), 256, 0, s>>>(fe->n, 2, nl, A->gfe_w, A->d_gfe_col.p, A->d_gfe_val.p, A->d_X.p,
+                                             -gamma * dtf, H);
+    ++launches;
+    // colouring of the multiplier columns
+    double hmax = 0.0;
+    for (int64_t e = 0; e < fe->ne; ++e) {
+        const int32_t a = fe->conn[(size_t)e * 4], c = fe->conn[(size_t)e * 4 + 2];
+        hmax = std::max({hmax, std::fabs(fe->X[(size_t)c] - fe->X[(size_t)a]),
+                         std::fabs(fe->X[(size_t)fe->n + c] - fe->X[(size_t)fe->n + a])});
+    }
+    const double R = 2.0 * hmax + m * pd->horizon;
+    auto xk = [&](int64_t q, int d) { return fe->X[(size_t)d * fe->n + A->lam_node[(size_t)(q % nl)]]; };
+    std::vector<std::vector<int64_t>> colors;
+    for (int64_t q = 0; q < nlam; ++q) {
+        bool placed = false;
+        for (auto &cl : colors) {
+            bool ok = true;
+            for (int64_t o : cl) {
+                const double dist = std::max(std::fabs(xk(q, 0) - xk(o, 0)), std::fabs(xk(q, 1) - xk(o, 1)));
+                if (dist <= 2.0 * R) {
+                    ok = false;
+                    break;
+                }
+            }
+            if (ok) {
+                cl.push_back(q);
+                placed = true;
+                break;
+            }
+        }
+        if (!placed)
+            colors.push_back({q});
+    }
+    A->colors = (int64_t)colors.size();
+    std::vector<double> unit((size_t)nlam);
+    std::vector<int32_t> owner((size_t)nlam);
+    const bool f64 = pd->precision == PDMTS_FP64;
+    for (auto &cl : colors) {
+        std::fill(unit.begin(), unit.end(), 0.0);
+        std::fill(owner.begin(), owner.end(), -1);
+        for (int64_t q : cl)
+            unit[(size_t)q] = 1.0;
+        for (int64_t r = 0; r < nlam; ++r)
+            for (int64_t q : cl) {
+                const double dist = std::max(std::fabs(xk(q, 0) - xk(r, 0)), std::fabs(xk(q, 1) - xk(r, 1)));
+                if (dist <= R) {
+                    owner[(size_t)r] = (int32_t)q;
+                    break;
+                }
+            }
+        PDMTS_TRY(h2d(A->d_unit.p, unit, s));
+        PDMTS_TRY(h2d(A->d_owner.p, owner, s));
+        PDMTS_TRY(pd_link_run(A, A->d_unit.p, m, s));
+        // y = G_PD v_link
+        cudaError_t e = launch_constraint(2, nl, A->d_gpd_ptr.p, A->d_gpd_col.p, A->d_gpd_val.p, pd->n,
+                                          f64 ? pd->lk_v.p : nullptr, f64 ? nullptr : pd->lk_v4.p,
+                                          f64 ? nullptr : pd->lk_v2.p, pd->h, nullptr, nullptr, 0, 0, nullptr, 1.0,
+                                          0.0, A->d_y.p, s);
+        if (e != cudaSuccess)
+            return fail(PDMTS_ERR_CUDA, "constraint rows: %s", cudaGetErrorString(e));
+        k_scatter_color<<<blocks(nlam), 256, 0, s>>>(nlam, A->d_owner.p, A->d_y.p, -1.0, H);
+        launches += 2;
+        // the host vectors are reused for the next colour
+        PDMTS_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    // (-H)^-1 by Gauss-Jordan (-H is symmetric positive definite)
+    const int64_t n2 = nlam * nlam;
+    k_negate<<<blocks(n2), 256, 0, s>>>(n2, H);
+    for (int64_t p = 0; p < nlam; ++p) {
+        k_gj_save_col<<<blocks(nlam), 256, 0, s>>>(nlam, H, p, A->d_colbuf.p);
+        k_gj_scale_row<<<blocks(nlam), 256, 0, s>>>(nlam, H, p, A->d_colbuf.p);
+        k_gj_update<<<blocks(n2), 256, 0, s>>>(nlam, H, p, A->d_colbuf.p);
+        launches += 3;
+    }
+    PDMTS_CUDA_TRY(cudaGetLastError());
+    PDMTS_CUDA_TRY(cudaStreamSynchronize(s));
+    ctx->stats.kernel_launches += launches;
+    A->H_valid = true;
+    A->built_m = m;
+    A->rebuilds++;
+    return PDMTS_OK;
+}
+
+// ------------------------------------------------------------ ABI ---------
+extern "C" int arlequin_bind(pdmts_ctx *ctx, pdmts_pd *pd, pdmts_fem *fe, int weight_kind, int n_bands,
+                             const double *bands, pdmts_arl **out)
+{
+    clear_error();
+    if (!ctx || !pd || !fe || !out || n_bands <= 0 || !bands)
+        return fail(PDMTS_ERR_ARG, "arlequin_bind: bad arguments");
+    *out = nullptr;
+    if (ctx->arl)
+        return fail(PDMTS_ERR_STATE, "arlequin_bind: context already has a coupling");
+    if (pd->ctx != ctx || fe->ctx != ctx)
+        return fail(PDMTS_ERR_ARG, "arlequin_bind: subdomains belong to another context");
+    if (pd->dim != 2 || fe->dim != 2)
+        return fail(PDMTS_ERR_UNSUPPORTED, "arlequin_bind: this build couples 2D subdomains");
+    if (weight_kind < PDMTS_WEIGHT_CONSTANT || weight_kind > PDMTS_WEIGHT_CUBIC)
+        return fail(PDMTS_ERR_ARG, "arlequin_bind: unknown weight kind %d", weight_kind);
+    std::vector<double> bv((size_t)5 * n_bands);
+    PDMTS_CUDA_TRY(cudaMemcpy(bv.data(), bands, sizeof(double) * bv.size(), cudaMemcpyDefault));
+    std::vector<BandDesc> bl;
+    for (int k = 0; k < n_bands; ++k) {
+        BandDesc b{(int)bv[(size_t)5 * k], bv[(size_t)5 * k + 1], bv[(size_t)5 * k + 2], (int)bv[(size_t)5 * k + 3]};
+        if ((b.axis != 0 && b.axis != 1) || !(b.hi > b.lo) || (b.fe_side != -1 && b.fe_side != 1))
+            return fail(PDMTS_ERR_ARG, "arlequin_bind: band %d is malformed", k);
+        bl.push_back(b);
+    }
+    PDMTS_CUDA_TRY(cudaSetDevice(ctx->device));
+    auto *A = new (std::nothrow) pdmts_arl();
+    if (!A)
+        return fail(PDMTS_ERR_NOMEM, "arlequin_bind: out of host memory");
+    A->ctx = ctx;
+    A->pd = pd;
+    A->fe = fe;
+    A->kind = weight_kind;
+    A->bands = bl;
+    int r = PDMTS_OK;
+    // PD weights alpha_i (0 outside the bands)
+    std::vector<double> alpha((size_t)pd->n);
+    for (int64_t p = 0; p < pd->n; ++p) {
+        const double x[2] = {pd->X[(size_t)p], pd->X[(size_t)pd->n + p]};
+        alpha[(size_t)p] = arlequin_alpha(bl, weight_kind, x, 0.0);
+    }
+    r = pd_set_weights(pd, alpha.data());
+    if (r == PDMTS_OK)
+        r = pd->alloc_link_state();
+    if (r == PDMTS_OK)
+        r = fe_assemble(fe, bl, weight_kind);
+    if (r == PDMTS_OK)
+        r = build_constraint(A);
+    if (r == PDMTS_OK) {
+        if (cudaStreamCreateWithFlags(&A->fe_stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&A->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&A->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&A->ev_flag, cudaEventDisableTiming) != cudaSuccess ||
+            cudaMallocHost(&A->h_changed, sizeof(unsigned long long)) != cudaSuccess)
+            r = fail(PDMTS_ERR_CUDA, "arlequin_bind: stream/event creation failed");
+    }
+    if (r != PDMTS_OK) {
+        std::string msg = pdmts_last_error();
+        A->release_all();
+        if (A->fe_stream) cudaStreamDestroy(A->fe_stream);
+        if (A->ev_fork) cudaEventDestroy(A->ev_fork);
+        if (A->ev_join) cudaEventDestroy(A->ev_join);
+        if (A->ev_flag) cudaEventDestroy(A->ev_flag);
+        if (A->h_changed) cudaFreeHost(A->h_changed);
+        delete A;
+        return fail(r, "%s", msg.c_str());
+    }
+    *A->h_changed = 0;
+    ctx->arl = A;
+    *out = A;
+    return PDMTS_OK;
+}
+
+extern "C" int arlequin_destroy(pdmts_arl *A)
+{
+    clear_error();
+    if (!A)
+        return PDMTS_OK;
+    cudaSetDevice(A->ctx->device);
+    cudaStreamSynchronize(A->ctx->stream);
+    if (A->fe_stream) {
+        cudaStreamSynchronize(A->fe_stream);
+        cudaStreamDestroy(A->fe_stream);
+    }
+    if (A->ev_fork) cudaEventDestroy(A->ev_fork);
+    if (A->ev_join) cudaEventDestroy(A->ev_join);
+    if (A->ev_flag) cudaEventDestroy(A->ev_flag);
+    if (A->h_changed) cudaFreeHost(A->h_changed);
+    if (A->ctx->arl == A)
+        A->ctx->arl = nullptr;
+    A->release_all();
+    delete A;
+    return PDMTS_OK;
+}
+
+extern "C" int mts_destroy_coupling(pdmts_ctx *ctx)
+{
+    if (ctx && ctx->arl)
+        arlequin_destroy(ctx->arl);
+    if (ctx && ctx->fem)
+        fem_destroy(ctx->fem);
+    return PDMTS_OK;
+}
+
+int mts_time_changed(pdmts_ctx *ctx)
+{
+    if (ctx->arl) {
+        ctx->arl->H_valid = false;
+        ctx->arl->X_valid = false;
+    }
+    return PDMTS_OK;
+}
+
+// One coarse step of Algorithm 1.
+static int coarse_step(pdmts_arl *A)
+{
+    pdmts_ctx *ctx = A->ctx;
+    pdmts_pd *pd = A->pd;
+    pdmts_fem *fe = A->fe;
+    cudaStream_t s = ctx->stream;
+    const int m = ctx->m_ratio;
+    const double dtf = m * ctx->dt_pd, beta = ctx->beta_fe, gamma = ctx->gamma_fe;
+    const bool f64 = pd->precision == PDMTS_FP64;
+    int64_t launches = 0;
+    // rebuild flag of the previous step (a bond near an overlap band broke)
+    if (A->flag_pending) {
+        PDMTS_CUDA_TRY(cudaEventSynchronize(A->ev_flag));
+        if (*A->h_changed)
+            A->H_valid = false;
+        A->flag_pending = false;
+    }
+    if (A->built_m != m || (int)A->theta_free.size() != m) {
+        A->theta_free.resize((size_t)m);
+        A->theta_link.resize((size_t)m);
+        for (int j = 1; j <= m; ++j) {
+            A->theta_free[(size_t)j - 1] = 1.0 - (double)j / m;  // S_j = (1 - j/m) lambda_0
+            A->theta_link[(size_t)j - 1] = (double)j / m;        // (j/m) lambda_m
+        }
+        PDMTS_TRY(update_near_flags(A, m));
+        A->H_valid = false;
+        pd_invalidate_graphs(pd);
+        // the link problem starts from the current bond state
+        PDMTS_CUDA_TRY(cudaMemcpyAsync(pd->d_mask_link.p, pd->d_mask.p, sizeof(uint32_t) * pd->n_mask_words,
+                                       cudaMemcpyDeviceToDevice, s));
+    }
+    PDMTS_TRY(fe_prepare_keff(fe, dtf, beta));
+    PDMTS_TRY(pd->ensure_init(s));
+    if (!A->H_valid)
+        PDMTS_TRY(build_H(A, m));
+    // ---- FE free step on the second stream (Eq. 47a) ----
+    PDMTS_CUDA_TRY(cudaEventRecord(A->ev_fork, s));
+    PDMTS_CUDA_TRY(cudaStreamWaitEvent(A->fe_stream, A->ev_fork, 0));
+    PDMTS_TRY(fe_free_step(fe, dtf, beta, gamma, A->fe_stream, &launches));
+    PDMTS_CUDA_TRY(cudaEventRecord(A->ev_join, A->fe_stream));
+    // ---- PD free substeps with (1 - j/m) lambda_0 (Eq. 48a) ----
+    cudaError_t e = launch_interface_force(pd->dim, pd->n, A->n_ov, A->d_ov_node.p, A->d_ov_k.p, A->d_ov_N.p, 4,
+                                           A->d_lam0.p, A->nl, f64 ? 0.0 : 1.0 / pd->h, f64 ? pd->d_g.p : nullptr,
+                                           f64 ? nullptr : pd->f_g.p, s);
+    if (e != cudaSuccess)
+        return fail(PDMTS_ERR_CUDA, "interface force: %s", cudaGetErrorString(e));
+    ++launches;
+    PDMTS_TRY(pd_run_chain(pd, m, 1, A->theta_free.data(), s, false));
+    PDMTS_CUDA_TRY(cudaStreamWaitEvent(s, A->ev_join, 0));
+    // ---- interface problem (Eq. 49): lambda_m = (-H)^-1 (G_FE v_FE - G_PD v_PD) ----
+    const float4 *v4 = f64 ? nullptr : pd->f_v4.p;
+    const float2 *v2 = f64 ? nullptr : pd->f_v2.p;
+    e = launch_constraint(2, A->nl, A->d_gpd_ptr.p, A->d_gpd_col.p, A->d_gpd_val.p, pd->n, f64 ? pd->d_v.p : nullptr,
+                          v4, v2, pd->h, A->d_gfe_col.p, A->d_gfe_val.p, A->gfe_w, fe->n, fe->d_v.p, -1.0, 1.0,
+                          A->d_y.p, s);
+    if (e != cudaSuccess)
+        return fail(PDMTS_ERR_CUDA, "interface residual: %s", cudaGetErrorString(e));
+    k_gemv_rows<<<blocks(A->nlam * 32), 256, 0, s>>>(A->nlam, A->d_Hneg_inv.p, A->d_y.p, 1.0, A->d_lam.p);
+    // ---- corrections U = V + Y lambda_m ----
+    k_fe_link_add<<<blocks(fe->ndof()), 256, 0, s>>>(fe->ndof(), A->nlam, A->d_X.p, A->d_lam.p, dtf, beta, gamma,
+                                                    fe->d_u.p, fe->d_v.p, fe->d_a.p);
+    launches += 3;
+    PDMTS_TRY(pd_link_run(A, A->d_lam.p, m, s));
+    PDAddLink L{};
+    L.dim = pd->dim;
+    L.n = pd->n;
+    L.dt = ctx->dt_pd;
+    L.hdt2 = 0.5 * ctx->dt_pd * ctx->dt_pd;
+    if (f64) {
+        L.u = pd->d_u[pd->cur].p;
+        L.u_pred = pd->d_u[1 - pd->cur].p;
+        L.v = pd->d_v.p;
+        L.a = pd->d_a.p;
+        L.wu = pd->lk_u[pd->lk_cur].p;
+        L.wv = pd->lk_v.p;
+        L.wa = pd->lk_a.p;
+    } else {
+        L.u4 = pd->f_u4[pd->cur].p;
+        L.u2 = pd->f_u2[pd->cur].p;
+        L.u4_pred = pd->f_u4[1 - pd->cur].p;
+        L.u2_pred = pd->f_u2[1 - pd->cur].p;
+        L.v4 = pd->f_v4.p;
+        L.v2 = pd->f_v2.p;
+        L.af = pd->f_a.p;
+        L.wu4 = pd->lk_u4[pd->lk_cur].p;
+        L.wu2 = pd->lk_u2[pd->lk_cur].p;
+        L.wv4 = pd->lk_v4.p;
+        L.wv2 = pd->lk_v2.p;
+        L.waf = pd->lk_af.p;
+    }
+    e = launch_pd_add_link(L, s);
+    if (e != cudaSuccess)
+        return fail(PDMTS_ERR_CUDA, "PD correction: %s", cudaGetErrorString(e));
+    // ---- rebuild flag: bonds near a band broken this step; new start mask ----
+    PDMTS_CUDA_TRY(cudaMemsetAsync(A->d_changed.p, 0, sizeof(unsigned long long), s));
+    e = launch_count_changed(pd->n_mask_words, pd->d_mask.p, pd->d_mask_link.p, A->d_near.p, A->d_changed.p, s);
+    if (e != cudaSuccess)
+        return fail(PDMTS_ERR_CUDA, "rebuild flag: %s", cudaGetErrorString(e));
+    PDMTS_CUDA_TRY(cudaMemcpyAsync(A->h_changed, A->d_changed.p, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    PDMTS_CUDA_TRY(cudaEventRecord(A->ev_flag, s));
+    A->flag_pending = true;
+    PDMTS_CUDA_TRY(cudaMemcpyAsync(pd->d_mask_link.p, pd->d_mask.p, sizeof(uint32_t) * pd->n_mask_words,
+                                   cudaMemcpyDeviceToDevice, s));
+    PDMTS_CUDA_TRY(cudaMemcpyAsync(A->d_lam0.p, A->d_lam.p, sizeof(double) * A->nlam, cudaMemcpyDeviceToDevice, s));
+    launches += 3;
+    ctx->stats.kernel_launches += launches;
+    ctx->stats.coarse_steps += 1;
+    PDMTS_CUDA_TRY(cudaGetLastError());
+    return PDMTS_OK;
+}
+
+int mts_advance_coupled(pdmts_ctx *ctx, int64_t n_coarse)
+{
+    PDMTS_CUDA_TRY(cudaSetDevice(ctx->device));
+    PDMTS_TRY(ctx->begin());
+    for (int64_t k = 0; k < n_coarse; ++k)
+        PDMTS_TRY(coarse_step(ctx->arl));
+    return ctx->end();
+}
+
+extern "C" int arlequin_read_lambda(pdmts_arl *A, double *lam, int64_t *n_lambda)
+{
+    clear_error();
+    if (!A || !lam)
+        return fail(PDMTS_ERR_ARG, "arlequin_read_lambda: NULL argument");
+    PDMTS_CUDA_TRY(cudaSetDevice(A->ctx->device));
+    PDMTS_TRY(A->ctx->begin());
+    PDMTS_CUDA_TRY(cudaMemcpyAsync(lam, A->d_lam0.p, sizeof(double) * A->nlam, cudaMemcpyDefault, A->ctx->stream));
+    PDMTS_CUDA_TRY(cudaStreamSynchronize(A->ctx->stream));
+    if (n_lambda)
+        *n_lambda = A->nlam;
+    return A->ctx->end();
+}
+
+extern "C" int arlequin_constraint_residual(pdmts_arl *A, double *residual, double *reference)
+{
+    clear_error();
+    if (!A || !residual)
+        return fail(PDMTS_ERR_ARG, "arlequin_constraint_residual: NULL argument");
+    pdmts_pd *pd = A->pd;
+    pdmts_fem *fe = A->fe;
+    if (!fe->assembled)
+        return fail(PDMTS_ERR_STATE, "arlequin_constraint_residual: not assembled");
+    PDMTS_CUDA_TRY(cudaSetDevice(A->ctx->device));
+    PDMTS_TRY(A->ctx->begin());
+    cudaStream_t s = A->ctx->stream;
+    const bool f64 = pd->precision == PDMTS_FP64;
+    std::vector<double> y((size_t)A->nlam), yf((size_t)A->nlam);
+    for (int pass = 0; pass < 2; ++pass) {
+        cudaError_t e = launch_constraint(2, A->nl, A->d_gpd_ptr.p, A->d_gpd_col.p, A->d_gpd_val.p, pd->n,
+                                          f64 ? pd->d_v.p : nullptr, f64 ? nullptr : pd->f_v4.p,
+                                          f64 ? nullptr : pd->f_v2.p, pd->h, A->d_gfe_col.p, A->d_gfe_val.p,
+                                          A->gfe_w, fe->n, fe->d_v.p, pass == 0 ? -1.0 : 0.0, 1.0, A->d_y.p, s);
+        if (e != cudaSuccess)
+            return fail(PDMTS_ERR_CUDA, "constraint: %s", cudaGetErrorString(e));
+        PDMTS_CUDA_TRY(cudaMemcpyAsync(pass == 0 ? y.data() : yf.data(), A->d_y.p, sizeof(double) * A->nlam,
+                                       cudaMemcpyDeviceToHost, s));
+    }
+    PDMTS_CUDA_TRY(cudaStreamSynchronize(s));
+    double r2 = 0, f2 = 0;
+    for (int64_t k = 0; k < A->nlam; ++k) {
+        r2 += y[(size_t)k] * y[(size_t)k];
+        f2 += yf[(size_t)k] * yf[(size_t)k];
+    }
+    *residual = std::sqrt(r2);
+    if (reference)
+        *reference = std::sqrt(f2);
+    return A->ctx->end();
+}
+
+extern "C" int arlequin_info(pdmts_arl *A, pdmts_arl_info *info)
+{
+    clear_error();
+    if (!A || !info)
+        return fail(PDMTS_ERR_ARG, "arlequin_info: NULL argument");
+    info->n_lambda = A->nlam;
+    info->n_overlap_pd = A->n_ov;
+    info->fe_dofs = A->fe->ndof();
+    info->colors = A->colors;
+    info->rebuilds = A->rebuilds;
+    info->cheb_iterations = (int64_t)A->fe->cheb_c1.size();
+    info->device_bytes = A->device_bytes + A->fe->device_bytes;
+    return PDMTS_OK;
 }

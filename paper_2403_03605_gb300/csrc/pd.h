@@ -73,6 +73,19 @@ struct pdmts_pd {
     DevArr<float2> f_u2[2], f_v2;
     DevArr<float> f_a;   // 2D: {ax, ay} per node; 3D: {ax, ay, az, 0} per node (lattice units)
 
+    // Link problem of the MTS coupling (Eq. 48b): a second velocity-Verlet
+    // state driven only by the interpolated multiplier, with its own bond
+    // words (the state at the start of the coarse step) and no breaking.
+    bool has_link = false;
+    DevArr<double> lk_u[2], lk_v, lk_a, lk_g;       // FP64
+    DevArr<float4> lk_u4[2], lk_v4;                 // FP32 bulk
+    DevArr<float2> lk_u2[2], lk_v2;
+    DevArr<float> lk_af, lk_gf;
+    DevArr<uint32_t> d_mask_link;
+    int lk_cur = 0;
+    // interface force density of the free problem (G_PD^T lambda_0 / V): FP64 d_g or FP32 f_g
+    bool has_g = false;
+
     // captured substep chains, keyed by (starting buffer parity, length, theta schedule id)
     struct GraphEntry {
         int parity, len, sched;
@@ -93,6 +106,8 @@ struct pdmts_pd {
     void release_all();
 
     int upload_weights_and_loads();  // (re)build mass, wb, g device arrays
-    int step(bool init, double theta, cudaStream_t s);  // one substep on the current state
+    int step(bool init, double theta, cudaStream_t s, bool link = false);  // one substep
+    int alloc_link_state();                  // link-problem arrays (MTS coupling)
+    int zero_link_state(cudaStream_t s);     // W_0 = 0 before a link run
     int ensure_init(cudaStream_t s);
 };

@@ -652,6 +652,140 @@ __global__ void k_weighted_load(const int dim, const int64_t n, const double *__
     }
 }
 
+// ------------------------------------------------------- MTS helpers ------
+__global__ void k_interface_force(const int dim, const int64_t n, const int64_t n_ov, const int32_t *__restrict__ ov_node,
+                                  const int32_t *__restrict__ ov_k, const double *__restrict__ ov_N, const int corners,
+                                  const double *__restrict__ lam, const int64_t nl, const double inv_h,
+                                  double *__restrict__ g64, float *__restrict__ g32)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n_ov)
+        return;
+    const int64_t p = ov_node[q];
+    for (int d = 0; d < dim; ++d) {
+        double g = 0.0;
+        for (int a = 0; a < corners; ++a)
+            g += ov_N[q * corners + a] * lam[d * nl + ov_k[q * corners + a]];
+        if (g64)
+            g64[d * n + p] = g;
+        if (g32)
+            g32[d * n + p] = (float)(g * inv_h);
+    }
+}
+
+__global__ void k_constraint(const int dim, const int64_t nl, const int64_t *__restrict__ gpd_ptr,
+                             const int32_t *__restrict__ gpd_col, const double *__restrict__ gpd_val, const int64_t npd,
+                             const double *__restrict__ v64, const float4 *__restrict__ v4,
+                             const float2 *__restrict__ v2, const double h, const int32_t *__restrict__ gfe_col,
+                             const double *__restrict__ gfe_val, const int gfe_w, const int64_t nfe,
+                             const double *__restrict__ vfe, const double sign_pd, const double sign_fe,
+                             double *__restrict__ y)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= (int64_t)dim * nl)
+        return;
+    const int c = (int)(r / nl);
+    const int64_t k = r - (int64_t)c * nl;
+    double sp = 0.0;
+    for (int64_t e = gpd_ptr[k]; e < gpd_ptr[k + 1]; ++e) {
+        const int64_t p = gpd_col[e];
+        double vp;
+        if (v64) {
+            vp = v64[(int64_t)c * npd + p];
+        } else {
+            const float4 q = v4[p];
+            if (dim == 2)
+                vp = c == 0 ? (double)q.x + (double)q.z : (double)q.y + (double)q.w;
+            else
+                vp = c == 0 ? (double)q.x + (double)q.w
+                            : (c == 1 ? (double)q.y + (double)v2[p].x : (double)q.z + (double)v2[p].y);
+            vp *= h;
+        }
+        sp += gpd_val[e] * vp;
+    }
+    double sf = 0.0;
+    if (gfe_col)
+        for (int e = 0; e < gfe_w; ++e)
+            sf += gfe_val[k * gfe_w + e] * vfe[(int64_t)c * nfe + gfe_col[k * gfe_w + e]];
+    y[r] = sign_pd * sp + sign_fe * sf;
+}
+
+__global__ void k_pd_add_link(const PDAddLink A)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= A.n)
+        return;
+    const int64_t n = A.n;
+    if (A.u) {
+        for (int d = 0; d < A.dim; ++d) {
+            const int64_t q = d * n + i;
+            const double u = A.u[q] + A.wu[q], v = A.v[q] + A.wv[q], a = A.a[q] + A.wa[q];
+            A.u[q] = u;
+            A.v[q] = v;
+            A.a[q] = a;
+            A.u_pred[q] = u + A.dt * v + A.hdt2 * a;
+        }
+        return;
+    }
+    float uh[3], ul[3], vh[3], vl[3], wuh[3], wul[3], wvh[3], wvl[3], a[3];
+    if (A.dim == 2) {
+        load_pair<2>(A.u4, A.u2, i, reinterpret_cast<float(&)[2]>(uh), reinterpret_cast<float(&)[2]>(ul));
+        load_pair<2>(A.v4, A.v2, i, reinterpret_cast<float(&)[2]>(vh), reinterpret_cast<float(&)[2]>(vl));
+        load_pair<2>(A.wu4, A.wu2, i, reinterpret_cast<float(&)[2]>(wuh), reinterpret_cast<float(&)[2]>(wul));
+        load_pair<2>(A.wv4, A.wv2, i, reinterpret_cast<float(&)[2]>(wvh), reinterpret_cast<float(&)[2]>(wvl));
+        const float2 aa = reinterpret_cast<const float2 *>(A.af)[i];
+        const float2 wa = reinterpret_cast<const float2 *>(A.waf)[i];
+        a[0] = __fadd_rn(aa.x, wa.x);
+        a[1] = __fadd_rn(aa.y, wa.y);
+    } else {
+        load_pair<3>(A.u4, A.u2, i, uh, ul);
+        load_pair<3>(A.v4, A.v2, i, vh, vl);
+        load_pair<3>(A.wu4, A.wu2, i, wuh, wul);
+        load_pair<3>(A.wv4, A.wv2, i, wvh, wvl);
+        const float4 aa = reinterpret_cast<const float4 *>(A.af)[i];
+        const float4 wa = reinterpret_cast<const float4 *>(A.waf)[i];
+        a[0] = __fadd_rn(aa.x, wa.x);
+        a[1] = __fadd_rn(aa.y, wa.y);
+        a[2] = __fadd_rn(aa.z, wa.z);
+    }
+    const float dtf = (float)A.dt, hdt2f = (float)A.hdt2;
+    for (int d = 0; d < A.dim; ++d) {
+        df_add(uh[d], ul[d], wuh[d]);
+        df_add(uh[d], ul[d], wul[d]);
+        df_add(vh[d], vl[d], wvh[d]);
+        df_add(vh[d], vl[d], wvl[d]);
+    }
+    float ph[3], pl[3];
+    for (int d = 0; d < A.dim; ++d) {
+        ph[d] = uh[d];
+        pl[d] = ul[d];
+        df_add(ph[d], pl[d], __fmaf_rn(dtf, vh[d], __fmaf_rn(dtf, vl[d], __fmul_rn(hdt2f, a[d]))));
+    }
+    if (A.dim == 2) {
+        store_pair<2>(A.u4, A.u2, i, reinterpret_cast<float(&)[2]>(uh), reinterpret_cast<float(&)[2]>(ul));
+        store_pair<2>(A.v4, A.v2, i, reinterpret_cast<float(&)[2]>(vh), reinterpret_cast<float(&)[2]>(vl));
+        store_pair<2>(A.u4_pred, A.u2_pred, i, reinterpret_cast<float(&)[2]>(ph), reinterpret_cast<float(&)[2]>(pl));
+        reinterpret_cast<float2 *>(A.af)[i] = make_float2(a[0], a[1]);
+    } else {
+        store_pair<3>(A.u4, A.u2, i, uh, ul);
+        store_pair<3>(A.v4, A.v2, i, vh, vl);
+        store_pair<3>(A.u4_pred, A.u2_pred, i, ph, pl);
+        reinterpret_cast<float4 *>(A.af)[i] = make_float4(a[0], a[1], a[2], 0.f);
+    }
+}
+
+__global__ void k_count_changed(const int64_t nwords, const uint32_t *__restrict__ a, const uint32_t *__restrict__ b,
+                                const uint8_t *__restrict__ flag, unsigned long long *count)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned c = 0;
+    if (i < nwords && flag[i] && a[i] != b[i])
+        c = __popc(a[i] ^ b[i]);
+    c = __reduce_add_sync(0xffffffffu, c);
+    if ((threadIdx.x & 31) == 0 && c)
+        atomicAdd(count, (unsigned long long)c);
+}
+
 // ------------------------------------------------------------- launchers --
 static inline unsigned grid_for_tiles(int64_t ntiles) { return (unsigned)((ntiles + 7) / 8); }
 
@@ -726,6 +860,49 @@ cudaError_t launch_weighted_load(int dim, int64_t n, const double *b, const doub
     return cudaGetLastError();
 }
 
+cudaError_t launch_interface_force(int dim, int64_t n, int64_t n_ov, const int32_t *ov_node, const int32_t *ov_k,
+                                   const double *ov_N, int corners, const double *lam, int64_t nl, double inv_h,
+                                   double *g64, float *g32, cudaStream_t s)
+{
+    if (n_ov == 0)
+        return cudaSuccess;
+    k_interface_force<<<(unsigned)((n_ov + 255) / 256), 256, 0, s>>>(dim, n, n_ov, ov_node, ov_k, ov_N, corners, lam,
+                                                                      nl, inv_h, g64, g32);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_constraint(int dim, int64_t nl, const int64_t *gpd_ptr, const int32_t *gpd_col,
+                              const double *gpd_val, int64_t npd, const double *v64, const float4 *v4,
+                              const float2 *v2, double h, const int32_t *gfe_col, const double *gfe_val, int gfe_w,
+                              int64_t nfe, const double *vfe, double sign_pd, double sign_fe, double *y,
+                              cudaStream_t s)
+{
+    const int64_t rows = (int64_t)dim * nl;
+    if (rows == 0)
+        return cudaSuccess;
+    k_constraint<<<(unsigned)((rows + 127) / 128), 128, 0, s>>>(dim, nl, gpd_ptr, gpd_col, gpd_val, npd, v64, v4, v2,
+                                                                 h, gfe_col, gfe_val, gfe_w, nfe, vfe, sign_pd,
+                                                                 sign_fe, y);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pd_add_link(const PDAddLink &A, cudaStream_t s)
+{
+    if (A.n == 0)
+        return cudaSuccess;
+    k_pd_add_link<<<(unsigned)((A.n + 255) / 256), 256, 0, s>>>(A);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count_changed(int64_t nwords, const uint32_t *a, const uint32_t *b, const uint8_t *word_flag,
+                                 unsigned long long *count, cudaStream_t s)
+{
+    if (nwords == 0)
+        return cudaSuccess;
+    k_count_changed<<<(unsigned)((nwords + 255) / 256), 256, 0, s>>>(nwords, a, b, word_flag, count);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_unpack_f32(int dim, int64_t n, const float4 *p4, const float2 *p2, int accel, double h,
                               double *out, cudaStream_t s)
 {
@@ -756,32 +933,34 @@ int pd_invalidate_graphs(pdmts_pd *pd)
 // Launch one chain of `len` substeps with interface factors theta(k), either
 // directly or by replaying its captured graph. Host bookkeeping (buffer
 // parity, counters) is applied once per chain.
-int pd_run_chain(pdmts_pd *pd, int len, int sched, const double *theta, cudaStream_t s)
+int pd_run_chain(pdmts_pd *pd, int len, int sched, const double *theta, cudaStream_t s, bool link)
 {
     pdmts_ctx *ctx = pd->ctx;
     cudaEvent_t t0 = nullptr;
-    PDMTS_TRY(ctx->time_begin(&t0));
+    if (!link)
+        PDMTS_TRY(ctx->time_begin(&t0));
+    int &cur = link ? pd->lk_cur : pd->cur;
     if (!pd->use_graphs || len < 2) {
         for (int k = 0; k < len; ++k)
-            PDMTS_TRY(pd->step(false, theta ? theta[k] : 0.0, s));
-        return ctx->time_end(t0, len);
+            PDMTS_TRY(pd->step(false, theta ? theta[k] : 0.0, s, link));
+        return link ? PDMTS_OK : ctx->time_end(t0, len);
     }
-    const int p = pd->cur;
+    const int p = cur + (link ? 2 : 0);
     cudaGraphExec_t exec = nullptr;
     for (auto &g : pd->graphs)
         if (g.parity == p && g.len == len && g.sched == sched)
             exec = g.exec;
     if (!exec) {
-        const int cur0 = pd->cur;
+        const int cur0 = cur;
         const int64_t steps0 = pd->steps_done;
         const pdmts_stats st0 = ctx->stats;
         cudaGraph_t g = nullptr;
         PDMTS_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
         int r = PDMTS_OK;
         for (int k = 0; k < len && r == PDMTS_OK; ++k)
-            r = pd->step(false, theta ? theta[k] : 0.0, s);
+            r = pd->step(false, theta ? theta[k] : 0.0, s, link);
         cudaError_t e = cudaStreamEndCapture(s, &g);
-        pd->cur = cur0;
+        cur = cur0;
         pd->steps_done = steps0;
         ctx->stats = st0;
         if (r != PDMTS_OK) {
@@ -802,10 +981,11 @@ int pd_run_chain(pdmts_pd *pd, int len, int sched, const double *theta, cudaStre
     ctx->stats.kernel_launches += len;
     ctx->stats.pd_substeps += len;
     ctx->stats.bond_updates += (int64_t)len * pd->row_ptr[(size_t)pd->n];
-    pd->steps_done += len;
+    if (!link)
+        pd->steps_done += len;
     if (len & 1)
-        pd->cur = 1 - pd->cur;
-    return ctx->time_end(t0, len);
+        cur = 1 - cur;
+    return link ? PDMTS_OK : ctx->time_end(t0, len);
 }
 
 // nsteps plain substeps (theta = 0) in chains of `chunk`.
@@ -815,10 +995,10 @@ int pd_run_steps_graph(pdmts_pd *pd, int64_t nsteps, int chunk, cudaStream_t s)
         chunk = 1;
     int64_t done = 0;
     while (nsteps - done >= chunk) {
-        PDMTS_TRY(pd_run_chain(pd, chunk, 0, nullptr, s));
+        PDMTS_TRY(pd_run_chain(pd, chunk, 0, nullptr, s, false));
         done += chunk;
     }
     if (done < nsteps)
-        PDMTS_TRY(pd_run_chain(pd, (int)(nsteps - done), 0, nullptr, s));
+        PDMTS_TRY(pd_run_chain(pd, (int)(nsteps - done), 0, nullptr, s, false));
     return PDMTS_OK;
 }

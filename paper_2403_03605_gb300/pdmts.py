@@ -76,6 +76,18 @@ SIGNATURES = [
     ("pd_read_family", _I, [_V, _V, _V]),
     ("mts_set_time", _I, [_V, _D, _I, _D, _D, _I]),
     ("mts_advance", _I, [_V, _I64]),
+    ("fem_create", _I, [_V, _I, _I64, _V, _I64, _I, _V, _D, _D, _D, _D, C.POINTER(_V)]),
+    ("fem_set_traction", _I, [_V, _I64, _V, _V]),
+    ("fem_set_state", _I, [_V, _V, _V]),
+    ("fem_destroy", _I, [_V]),
+    ("fem_read_displacement", _I, [_V, _V]),
+    ("fem_read_velocity", _I, [_V, _V]),
+    ("fem_read_acceleration", _I, [_V, _V]),
+    ("arlequin_bind", _I, [_V, _V, _V, _I, _I, _V, C.POINTER(_V)]),
+    ("arlequin_destroy", _I, [_V]),
+    ("arlequin_read_lambda", _I, [_V, _V, C.POINTER(_I64)]),
+    ("arlequin_constraint_residual", _I, [_V, C.POINTER(_D), C.POINTER(_D)]),
+    ("arlequin_info", _I, [_V, _V]),
     ("pdmts_set_timing", _I, [_V, _I]),
     ("pdmts_get_timing", _I, [_V, C.POINTER(_D), C.POINTER(_I64)]),
     ("pdmts_get_stats", _I, [_V, C.POINTER(Stats)]),
@@ -300,3 +312,87 @@ def mts_set_time(ctx, dt_pd, m_ratio=1, gamma_fe=0.5, beta_fe=0.25, check_stabil
 
 def mts_advance(ctx, n_coarse):
     _check(load().mts_advance(ctx, int(n_coarse)), "mts_advance")
+
+
+# --------------------------------------------------------- FE and coupling
+class ArlInfo(C.Structure):
+    _fields_ = [("n_lambda", C.c_int64), ("n_overlap_pd", C.c_int64), ("fe_dofs", C.c_int64),
+                ("colors", C.c_int64), ("rebuilds", C.c_int64), ("cheb_iterations", C.c_int64),
+                ("device_bytes", C.c_int64)]
+
+
+def fem_create(ctx, X, conn, *, E, nu, rho, thickness):
+    """X: (2, n) node positions; conn: (ne, 4) int32 Q4 connectivity."""
+    X = _f64(X)
+    conn = np.ascontiguousarray(conn, dtype=np.int32)
+    h = _V()
+    _check(load().fem_create(ctx, int(X.shape[0]), int(X.shape[1]), _ptr(X), int(conn.shape[0]),
+                             int(conn.shape[1]), _ptr(conn), float(E), float(nu), float(rho), float(thickness),
+                             C.byref(h)), "fem_create")
+    return h.value
+
+
+def fem_set_traction(fe, faces, traction):
+    faces = np.ascontiguousarray(faces, dtype=np.int32)
+    traction = _f64(traction)
+    _check(load().fem_set_traction(fe, int(faces.shape[0]), _ptr(faces), _ptr(traction)), "fem_set_traction")
+
+
+def fem_set_state(fe, u=None, v=None):
+    u, v = _f64(u), _f64(v)
+    _check(load().fem_set_state(fe, _ptr(u), _ptr(v)), "fem_set_state")
+
+
+def fem_destroy(fe):
+    _check(load().fem_destroy(fe), "fem_destroy")
+
+
+def _fe_read(fn, fe, ndof, out=None):
+    if out is None:
+        out = np.empty(ndof, dtype=np.float64)
+    _check(getattr(load(), fn)(fe, _ptr(out)), fn)
+    return out
+
+
+def fem_read_displacement(fe, ndof, out=None):
+    return _fe_read("fem_read_displacement", fe, ndof, out)
+
+
+def fem_read_velocity(fe, ndof, out=None):
+    return _fe_read("fem_read_velocity", fe, ndof, out)
+
+
+def fem_read_acceleration(fe, ndof, out=None):
+    return _fe_read("fem_read_acceleration", fe, ndof, out)
+
+
+def arlequin_bind(ctx, pd, fe, weight_kind, bands):
+    """bands: iterable of (axis, lo, hi, fe_side, 0)."""
+    b = np.ascontiguousarray(np.asarray(list(bands), dtype=np.float64).reshape(-1, 5))
+    h = _V()
+    _check(load().arlequin_bind(ctx, pd, fe, int(weight_kind), len(b), _ptr(b), C.byref(h)), "arlequin_bind")
+    return h.value
+
+
+def arlequin_destroy(arl):
+    _check(load().arlequin_destroy(arl), "arlequin_destroy")
+
+
+def arlequin_info(arl):
+    s = ArlInfo()
+    _check(load().arlequin_info(arl, C.byref(s)), "arlequin_info")
+    return {k: getattr(s, k) for k, _ in ArlInfo._fields_}
+
+
+def arlequin_read_lambda(arl):
+    n = arlequin_info(arl)["n_lambda"]
+    lam = np.empty(n, dtype=np.float64)
+    cnt = _I64()
+    _check(load().arlequin_read_lambda(arl, _ptr(lam), C.byref(cnt)), "arlequin_read_lambda")
+    return lam
+
+
+def arlequin_constraint_residual(arl):
+    r, f = _D(), _D()
+    _check(load().arlequin_constraint_residual(arl, C.byref(r), C.byref(f)), "arlequin_constraint_residual")
+    return r.value, f.value

@@ -85,3 +85,51 @@ class GpuRun:
 
     def damage(self):
         return P.pd_read_damage(self.pd)
+
+
+class GpuMTS:
+    """A coupled problem advanced by libpdmts.so (Algorithm 1) through the C ABI."""
+
+    def __init__(self, ctx, cp, precision, v0=None):
+        self.ctx, self.cp = ctx, cp
+        pb = cp.pd
+        mat = pb.mat
+        self.pd = P.pd_create(ctx, pb.lat.X, horizon=pb.delta, c=pb.c, s0=pb.s0, rho=mat.rho, vol_uniform=pb.vol,
+                              precision=precision)
+        if pb.cuts:
+            P.pd_set_precrack(self.pd, [c.as_array() for c in pb.cuts])
+        self.fe = P.fem_create(ctx, cp.fe.X, cp.fe.conn, E=mat.E, nu=mat.nu, rho=mat.rho, thickness=mat.thickness)
+        P.fem_set_traction(self.fe, cp.faces, cp.face_traction)
+        self.arl = P.arlequin_bind(ctx, self.pd, self.fe, cp.weight_kind, [b.as_array() for b in cp.bands])
+        if v0 is not None:
+            v0 = np.asarray(v0, dtype=np.float64)
+            P.pd_set_state(self.pd, None, np.repeat(v0.reshape(2, 1), pb.n, axis=1))
+            P.fem_set_state(self.fe, None, np.repeat(v0, cp.fe.n))
+        P.mts_set_time(ctx, cp.dt_pd, cp.m, cp.gamma_fe, cp.beta_fe)
+        self.ndof = 2 * cp.fe.n
+
+    def run(self, n):
+        P.mts_advance(self.ctx, n)
+        return self
+
+    def u(self):
+        return P.pd_read_displacement(self.pd)
+
+    def v(self):
+        return P.pd_read_velocity(self.pd)
+
+    def mu(self):
+        return P.pd_read_bond_status(self.pd)[0]
+
+    def uf(self):
+        return P.fem_read_displacement(self.fe, self.ndof)
+
+    def vf(self):
+        return P.fem_read_velocity(self.fe, self.ndof)
+
+    def lam(self):
+        return P.arlequin_read_lambda(self.arl)
+
+    def residual(self):
+        r, f = P.arlequin_constraint_residual(self.arl)
+        return r / f if f > 0 else r

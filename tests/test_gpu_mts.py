@@ -1,0 +1,98 @@
+"""GPU parity of the MTS Arlequin coupling (Algorithm 1) against the FP64 oracle."""
+import numpy as np
+import pytest
+
+from gpu_common import GpuMTS, rel_l2
+from oracle.mts import MTSOracle
+from paper_2403_03605_gb300 import pdmts as P
+from paper_2403_03605_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-10
+
+
+@pytest.fixture
+def fresh():
+    from paper_2403_03605_gb300 import build
+    build.build()
+    made = []
+
+    def mk():
+        c = P.pdmts_ctx_create(0)
+        made.append(c)
+        return c
+    yield mk
+    for c in made:
+        P.pdmts_ctx_destroy(c)
+
+
+def _compare(g, o, tol, lam_tol, mu_exact=True):
+    assert rel_l2(g.u(), o.u) <= tol
+    assert rel_l2(g.v(), o.v) <= tol
+    assert rel_l2(g.uf(), o.uf) <= tol
+    assert rel_l2(g.vf(), o.vf) <= tol
+    assert rel_l2(g.lam(), o.lam) <= lam_tol
+    if mu_exact:
+        assert np.array_equal(g.mu(), o.mu)
+
+
+CASES = [
+    dict(name="linear_m4", cp=lambda: W.small_coupled(m=4, n_coarse=20)),
+    dict(name="m1", cp=lambda: W.small_coupled(m=1, n_coarse=25)),
+    dict(name="cubic_m5", cp=lambda: W.small_coupled(m=5, n_coarse=12, weight_kind=2)),
+    dict(name="constant_m3", cp=lambda: W.small_coupled(m=3, n_coarse=12, weight_kind=0)),
+    dict(name="breaking_rebuild", cp=lambda: W.small_coupled(m=4, n_coarse=16, traction=30e6)),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c["name"] for c in CASES])
+def test_mts_fp64_matches_oracle(fresh, case):
+    cp = case["cp"]()
+    o = MTSOracle(cp).advance(cp.n_coarse)
+    g = GpuMTS(fresh(), cp, P.PDMTS_FP64).run(cp.n_coarse)
+    _compare(g, o, FP64_TOL, 1e-8)
+    info = P.arlequin_info(g.arl)
+    assert info["rebuilds"] == o.n_rebuilds
+    assert g.residual() <= 1e-12
+    if case["name"] == "breaking_rebuild":
+        assert o.n_rebuilds > 1 and (o.mu == 0).sum() > 100
+
+
+def test_mts_fp32_bulk_within_tolerance(fresh):
+    cp = W.small_coupled(m=4, n_coarse=20)
+    o = MTSOracle(cp).advance(cp.n_coarse)
+    g = GpuMTS(fresh(), cp, P.PDMTS_FP32_BULK).run(cp.n_coarse)
+    err = rel_l2(g.u(), o.u)
+    mm = np.count_nonzero(g.mu() != o.mu) / len(o.mu)
+    print(f"MTS fp32-bulk: rel-L2 u_pd {err:.2e}, u_fe {rel_l2(g.uf(), o.uf):.2e}, mismatch {mm:.2e}")
+    assert err <= 1e-4
+    assert rel_l2(g.uf(), o.uf) <= 1e-4
+    assert mm <= 1e-3
+    assert g.residual() <= 1e-5
+
+
+def test_mts_uniform_velocity_patch(fresh):
+    cp = W.small_coupled(m=5, n_coarse=4, crack=False, traction=0.0)
+    v0 = np.array([3.0, -1.5])
+    g = GpuMTS(fresh(), cp, P.PDMTS_FP64, v0=v0).run(4)
+    assert np.abs(g.v() - v0.reshape(2, 1)).max() <= 1e-12 * 3.0
+    assert np.abs(g.vf() - np.repeat(v0, cp.fe.n)).max() <= 1e-12 * 3.0
+    force_scale = cp.pd.mat.rho * 3.0 / (cp.m * cp.dt_pd)
+    assert np.abs(g.lam()).max() <= 1e-9 * force_scale
+
+
+@pytest.mark.parametrize("prec", [P.PDMTS_FP64, P.PDMTS_FP32_BULK])
+def test_config1_full_size_properties(fresh, prec):
+    """The 100 x 40 mm coupled plate (25,600 PD nodes, 3,030 FE nodes): the
+    velocity constraint holds after every coarse step and the state stays finite."""
+    cp = W.config1()
+    g = GpuMTS(fresh(), cp, prec)
+    for _ in range(3):
+        g.run(5)
+        res = g.residual()
+        assert res <= (1e-11 if prec == P.PDMTS_FP64 else 1e-5), res
+    assert np.isfinite(g.u()).all() and np.isfinite(g.uf()).all()
+    info = P.arlequin_info(g.arl)
+    print("config1 coupling:", info)
+    assert info["n_lambda"] == 2 * 606
