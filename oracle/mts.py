@@ -289,7 +289,7 @@ class MTSOracle:
         near_break = bool(np.any(broke & (self.near[i_of] | self.near[self.col])))
         self.mu_link = self.mu.copy()
         if self.rebuild_mode == "always" or (self.rebuild_mode == "auto" and near_break):
-            self.build_H()
+            self.H = None  # rebuilt at the start of the next coarse step
         return lam
 
     def advance(self, n):

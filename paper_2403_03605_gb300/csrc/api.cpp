@@ -333,10 +333,15 @@ int pdmts_pd::alloc_link_state()
     cudaStream_t s = ctx->stream;
     PDMTS_CUDA_TRY(cudaMemcpyAsync(d_mask_link.p, d_mask.p, sizeof(uint32_t) * std::max<int64_t>(n_mask_words, 1),
                                    cudaMemcpyDeviceToDevice, s));
-    if (precision == PDMTS_FP64)
+    // interface forces are written only at overlap nodes: every other entry must be zero
+    // (device memory may come recycled from the allocator)
+    if (precision == PDMTS_FP64) {
         PDMTS_CUDA_TRY(cudaMemsetAsync(d_g.p, 0, sizeof(double) * m, s));
-    else
+        PDMTS_CUDA_TRY(cudaMemsetAsync(lk_g.p, 0, sizeof(double) * m, s));
+    } else {
         PDMTS_CUDA_TRY(cudaMemsetAsync(f_g.p, 0, sizeof(float) * m, s));
+        PDMTS_CUDA_TRY(cudaMemsetAsync(lk_gf.p, 0, sizeof(float) * m, s));
+    }
     has_link = true;
     has_g = true;
     pd_invalidate_graphs(this);
