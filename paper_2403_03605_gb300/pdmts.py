@@ -72,6 +72,7 @@ SIGNATURES = [
     ("pd_read_velocity", _I, [_V, _V]),
     ("pd_read_acceleration", _I, [_V, _V]),
     ("pd_read_damage", _I, [_V, _V]),
+    ("pd_read_damage_static", _I, [_V, _V]),
     ("pd_read_bond_status", _I, [_V, _V, C.POINTER(_I64)]),
     ("pd_read_family", _I, [_V, _V, _V]),
     ("mts_set_time", _I, [_V, _D, _I, _D, _D, _I]),
@@ -286,6 +287,12 @@ def pd_read_acceleration(pd, out=None):
 def pd_read_damage(pd, out=None):
     i = pd_info(pd)
     return _read("pd_read_damage", pd, (i["n"],), out)
+
+
+def pd_read_damage_static(pd, out=None):
+    """Damage through the non-allocating entry point (static device scratch)."""
+    i = pd_info(pd)
+    return _read("pd_read_damage_static", pd, (i["n"],), out)
 
 
 def pd_read_bond_status(pd):
