@@ -1,16 +1,23 @@
-"""Benchmark of the PD hot path (bond updates/s, fraction of the HBM roofline).
+"""Benchmark of the MTS-coupled PD hot path (bond updates/s, HBM roofline).
 
-python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload coupled|pd]
 
-A step is one coarse step's PD cycle: m = 20 velocity-Verlet substeps (bond
-gather, stretch, irreversible breaking, force sum, update) of the 2000 x 400
-(800,000-node, 22.3M directed-bond) PD lattice of the fine coupled plate,
-FP32-bulk arithmetic, replayed as one captured CUDA graph. Inputs are seeded
-synthetic data resident in HBM before the timed region; L2 is flushed between
-timed steps. One JSON line is printed by rank 0.
+Default workload (coupled): the fine coupled plate, 0.1 x 0.04 m with a 50 mm
+edge pre-crack, a 20 mm PD strip at 0.05 mm (2000 x 400 = 800,000 PD nodes,
+22.3M directed bonds), Q4 elements of 0.5 mm elsewhere, 2 mm overlap bands,
+12 MPa, FP32-bulk PD with FP64 coupling, m = 20. A step is one coarse step of
+Algorithm 1: the FE free step (concurrent stream), 20 PD free substeps (one
+CUDA graph), the FP64 interface solve, the FE correction and 20 PD link
+substeps. `value` counts every PD bond update (free and link substeps) per
+second of device time; coarse steps/s is reported beside it.
 
---impl reference times the FP64 CPU oracle (the reference of this build) on
-the host cores, on bounded samples of the same workload.
+--workload pd: the same 800,000-node lattice as a pure PD plate (traction as a
+body force on its faces), 20 substeps per step.
+
+Inputs are seeded synthetic data resident in HBM before the timed region; L2
+is flushed between timed steps. --impl reference times the FP64 CPU oracle
+(the reference of this build) on the host cores, on bounded samples of the
+same lattice. One JSON line is printed by rank 0.
 """
 from __future__ import annotations
 
@@ -29,6 +36,7 @@ import numpy as np  # noqa: E402
 
 WORKLOAD = dict(name="pd_strip_2000x400_dx0.05mm_m20_fp32bulk", nx=2000, ny=400, dx=0.05e-3, crack=0.05,
                 traction=12e6, dt=5e-9, m=20)
+COUPLED_NAME = "coupled_plate_100x40mm_pd2000x400_fe0.5mm_m20_fp32bulk"
 METRIC = "PD bond updates/s"
 UNIT = "bond updates/s"
 
@@ -97,15 +105,17 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
-def algorithmic_bytes(info, pb, with_body=True):
+def algorithmic_bytes(info, pb, with_body=True, coupled=False):
     """Bytes one FP32-bulk 2D substep must move with the family layout in use.
 
     Per node: u (16 in, 16 out), v (16 in, 16 out), a (8 in, 8 out), 1/m (4),
-    weighted body force (8). Lattice layout: the family is implicit and the
-    node's 32-bit bond word (one bit per bond) is read once. Sliced-ELL
-    layout: per directed bond a 4-byte family word and one status bit."""
+    plus the weighted body force (8) in the pure-PD plate, or the Arlequin
+    weight (4) and the interface force (8) in the coupled plate. Lattice
+    layout: the family is implicit and the node's 32-bit bond word (one bit
+    per bond) is read once. Sliced-ELL layout: per directed bond a 4-byte
+    family word and one status bit."""
     nb, n = info["n_bonds"], info["n"]
-    per_node = 16 + 16 + 16 + 16 + 8 + 8 + 4 + (8 if with_body else 0)
+    per_node = 16 + 16 + 16 + 16 + 8 + 8 + 4 + (8 if with_body else 0) + (12 if coupled else 0)
     if info["layout"] == 1:
         return (per_node + 4) * n, per_node + 4
     return 4 * nb + nb / 8.0 + per_node * n, per_node
@@ -153,6 +163,31 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def setup_ours(P, ctx, workload):
+    """Create the workload through the C ABI; returns (pd, fe, arl, info, pb, m, cp)."""
+    from paper_2403_03605_gb300 import workloads as W
+    if workload == "pd":
+        pb = make_problem()
+        m = WORKLOAD["m"]
+        pd = P.pd_create(ctx, pb.lat.X, horizon=pb.delta, c=pb.c, s0=pb.s0, rho=pb.mat.rho, vol_uniform=pb.vol,
+                         precision=P.PDMTS_FP32_BULK)
+        P.pd_set_precrack(pd, [c.as_array() for c in pb.cuts])
+        P.pd_set_body_force(pd, pb.b)
+        P.mts_set_time(ctx, pb.dt, m)
+        return pd, None, None, P.pd_info(pd), pb, m, None
+    cp = W.config2()
+    pb = cp.pd
+    mat = pb.mat
+    pd = P.pd_create(ctx, pb.lat.X, horizon=pb.delta, c=pb.c, s0=pb.s0, rho=mat.rho, vol_uniform=pb.vol,
+                     precision=P.PDMTS_FP32_BULK)
+    P.pd_set_precrack(pd, [c.as_array() for c in pb.cuts])
+    fe = P.fem_create(ctx, cp.fe.X, cp.fe.conn, E=mat.E, nu=mat.nu, rho=mat.rho, thickness=mat.thickness)
+    P.fem_set_traction(fe, cp.faces, cp.face_traction)
+    arl = P.arlequin_bind(ctx, pd, fe, cp.weight_kind, [b.as_array() for b in cp.bands])
+    P.mts_set_time(ctx, cp.dt_pd, cp.m, cp.gamma_fe, cp.beta_fe)
+    return pd, fe, arl, P.pd_info(pd), pb, cp.m, cp
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -162,21 +197,17 @@ def run_ours(args, rank, world, local_rank):
     B.build()
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    pb = make_problem()
-    m = WORKLOAD["m"]
+    coupled = args.workload == "coupled"
     stream = torch.cuda.current_stream(dev)
     ctx = P.pdmts_ctx_create(local_rank, stream.cuda_stream)
-    pd = P.pd_create(ctx, pb.lat.X, horizon=pb.delta, c=pb.c, s0=pb.s0, rho=pb.mat.rho, vol_uniform=pb.vol,
-                     precision=P.PDMTS_FP32_BULK)
-    P.pd_set_precrack(pd, [c.as_array() for c in pb.cuts])
-    P.pd_set_body_force(pd, pb.b)
-    P.mts_set_time(ctx, pb.dt, m)
-    info = P.pd_info(pd)
+    t_setup = time.perf_counter()
+    pd, fe, arl, info, pb, m, cp = setup_ours(P, ctx, args.workload)
     flush = torch.empty(int(256e6) // 4, dtype=torch.float32, device=dev)  # > L2 (129 MiB)
 
-    for _ in range(args.warmup):
+    for _ in range(args.warmup):  # the first coarse step also builds the interface operator
         P.mts_advance(ctx, 1)
     torch.cuda.synchronize(dev)
+    t_setup = time.perf_counter() - t_setup
 
     # ---- device-timed region: K steps, L2 flushed between steps ----------
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -203,71 +234,90 @@ def run_ours(args, rank, world, local_rank):
     chain_ms, chain_sub = P.pdmts_get_timing(ctx)
     st1 = P.pdmts_get_stats(ctx)
     launches = st1["kernel_launches"] - st0["kernel_launches"]
-    units = info["n_bonds"] * m * args.steps
+    substeps = st1["pd_substeps"] - st0["pd_substeps"]
+    units = st1["bond_updates"] - st0["bond_updates"]  # link substeps count only the rows they evaluate
     t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     total_ms = float(t.item())
     value = units * world / (total_ms * 1e-3)
+    coarse_per_s = args.steps * world / (total_ms * 1e-3)
 
     # ---- roofline of the dominant kernel (the FP32-bulk substep) ----------
-    abytes, per_node = algorithmic_bytes(info, pb)
+    abytes, per_node = algorithmic_bytes(info, pb, with_body=not coupled, coupled=coupled)
     launch_ms = chain_ms / max(chain_sub, 1)
     achieved = abytes / (launch_ms * 1e-3) / 1e9
     peak, peak_kind = peaks()
+    kname = ("k_pd_step_lattice2d<%s,false>" % ("true" if coupled else "false")) if info["layout"] == 1 \
+        else "k_pd_step_f32<2>"
     traffic = None
-    tfile = os.path.join(ROOT, "profiles", "pd_step_f32_strip2000x400_traffic.json")
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tfile):
         try:
             with open(tfile) as f:
                 tj = json.load(f)
-            if tj.get("kernel_version") == kernel_version():
-                traffic = tj["dram_bytes_per_launch"]
+            ent = tj.get(args.workload, {})
+            if ent.get("kernel_version") == kernel_version():
+                traffic = ent["dram_bytes_per_launch"]
         except Exception:
             traffic = None
 
     # ---- end to end through the C ABI with host buffers ------------------
-    b_host = torch.from_numpy(np.ascontiguousarray(pb.b)).pin_memory()
+    # each step: upload a PD body-force field from pinned host memory, advance
+    # one coarse step, read the PD (and FE) displacement back into pinned memory
+    b_np = np.zeros((pb.dim, pb.n)) if coupled else np.ascontiguousarray(pb.b)
+    b_host = torch.from_numpy(b_np).pin_memory()
     u_host = torch.empty((pb.dim, pb.n), dtype=torch.float64).pin_memory()
+    nfe_dof = 2 * cp.fe.n if coupled else 0
+    uf_host = torch.empty(max(nfe_dof, 1), dtype=torch.float64).pin_memory()
+    P.pd_set_body_force(pd, b_host)  # first upload allocates the load arrays (outside the timing)
     e2e_steps = max(3, min(args.steps, 10))
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
+    st2 = P.pdmts_get_stats(ctx)
     for _ in range(e2e_steps):
         P.pd_set_body_force(pd, b_host)
         P.mts_advance(ctx, 1)
         P.pd_read_displacement(pd, u_host.numpy())
+        if coupled:
+            P.fem_read_displacement(fe, nfe_dof, uf_host.numpy())
     torch.cuda.synchronize(dev)
     e2e_s = time.perf_counter() - t0
-    e2e_value = info["n_bonds"] * m * e2e_steps * world / e2e_s
-    u_final = u_host.numpy()
-    assert np.isfinite(u_final).all()
+    e2e_units = P.pdmts_get_stats(ctx)["bond_updates"] - st2["bond_updates"]
+    e2e_value = e2e_units * world / e2e_s
+    assert np.isfinite(u_host.numpy()).all()
 
     # ---- CPU baseline: the FP64 oracle on a bounded sample ----------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         nsub = 20
-        rate, dt, _ = oracle_sample(pb, nsub)
+        rate, dt, _ = oracle_sample(make_problem(), nsub)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{nsub} FP64 oracle substeps of the same {pb.n}-node lattice ({dt:.1f} s)"}
+               "sample": f"{nsub} FP64 oracle PD substeps of the same 800,000-node lattice ({dt:.1f} s)"}
 
     if rank == 0:
+        cfg = {"workload": COUPLED_NAME if coupled else WORKLOAD["name"], "pd_nodes": pb.n,
+               "directed_bonds": info["n_bonds"], "m": m,
+               "family_layout": "lattice bond words" if info["layout"] == 1 else "sliced ELL",
+               "graph": "one captured graph per PD substep chain",
+               "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+               "l2": "flushed between timed steps (256 MB write)"}
+        if coupled:
+            ai = P.arlequin_info(arl)
+            cfg.update({"fe_dofs": ai["fe_dofs"], "n_lambda": ai["n_lambda"],
+                        "pd_substeps_per_step": substeps // args.steps, "setup_s": round(t_setup, 2),
+                        "interface_builds": ai["rebuilds"]})
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD["name"], "nodes": pb.n, "bonds": info["n_bonds"], "m": m,
-                       "family_layout": "lattice bond words" if info["layout"] == 1 else "sliced ELL",
-                       "substeps_per_step": m, "graph": "one captured graph per step",
-                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                       "l2": "flushed between timed steps (256 MB write)"},
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
+            "coarse_steps_per_s": coarse_per_s if coupled else None,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                         "kernel": "k_pd_step_lattice2d<false>" if info["layout"] == 1 else "k_pd_step_f32<2>",
-                         "algorithmic_bytes_per_launch": abytes,
-                         "launch_us": launch_ms * 1e3},
+                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind, "kernel": kname,
+                         "algorithmic_bytes_per_launch": abytes, "launch_us": launch_ms * 1e3},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(b_host.numel() * 8),
-                    "d2h_bytes_per_step": int(u_host.numel() * 8)},
+                    "d2h_bytes_per_step": int(u_host.numel() * 8 + nfe_dof * 8)},
             "gpu_launches": int(launches),
             "clocks": clk.summary(),
         }
@@ -291,6 +341,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["coupled", "pd"], default="coupled")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

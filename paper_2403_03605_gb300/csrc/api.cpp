@@ -895,6 +895,10 @@ int pdmts_pd::step(bool init, double theta, cudaStream_t s, bool link)
                 A.rd[r2] = (float)std::sqrt((double)r2);
             }
             A.nd = N;
+            for (int w = 0; w < 2; ++w) {
+                A.win_lo[w] = link ? link_win_lo[w] : 0;
+                A.win_n[w] = link ? link_win_n[w] : 0;
+            }
             e = launch_pd_step_lattice2d(A, init, s);
         } else {
             F32StepArgs A{};
@@ -914,7 +918,7 @@ int pdmts_pd::step(bool init, double theta, cudaStream_t s, bool link)
         if (!link)
             steps_done++;
         ctx->stats.pd_substeps++;
-        ctx->stats.bond_updates += (int64_t)row_ptr[(size_t)n];
+        ctx->stats.bond_updates += (link && link_bonds >= 0) ? link_bonds : (int64_t)row_ptr[(size_t)n];
     }
     return PDMTS_OK;
 }

@@ -118,6 +118,7 @@ struct F32StepArgs {
 namespace lat2d {
 constexpr int NS = 28;
 constexpr int R = 3;
+constexpr int TX = 32, TY = 8;  // CTA node tile of the lattice kernel
 __host__ __device__ constexpr int DX(int k)
 {
     constexpr int t[NS] = {0, -2, -1, 0, 1, 2, -2, -1, 0, 1, 2, -3, -2, -1, 1, 2, 3, -2, -1, 0, 1, 2, -2, -1, 0, 1, 2, 0};
@@ -140,6 +141,7 @@ struct Lat2DArgs {
     float coef[10];             // c(|xi|) h^2 V by |d|^2
     float thr[10];              // s0 (2 + s0) |d|^2
     float rd[10];               // |d|
+    int win_lo[2], win_n[2];    // optional tile-row windows (win_n[0] == 0: whole lattice)
     F32NodeArgs nd;
 };
 

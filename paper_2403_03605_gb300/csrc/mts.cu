@@ -243,22 +243,40 @@ __global__ void k_fe_correct_state(const int64_t ndof, const double *__restrict_
     v[i] = vt[i] + gamma * dt * a[i];
 }
 
-// FE link response added to the state: a_W = -X lambda (X column-major), u +=
-// beta dt^2 a_W, v += gamma dt a_W, a += a_W.
+// FE link response added to the state: a_W = -X lambda with X row-major
+// (ndof x nlam, one warp per FE dof), u += beta dt^2 a_W, v += gamma dt a_W,
+// a += a_W.
 __global__ void k_fe_link_add(const int64_t ndof, const int64_t nlam, const double *__restrict__ X,
                               const double *__restrict__ lam, const double dt, const double beta, const double gamma,
                               double *__restrict__ u, double *__restrict__ v, double *__restrict__ a)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (i >= ndof)
         return;
     double s = 0.0;
-    for (int64_t q = 0; q < nlam; ++q)
-        s += X[i + q * ndof] * lam[q];
-    const double aw = -s;
-    u[i] += beta * dt * dt * aw;
-    v[i] += gamma * dt * aw;
-    a[i] += aw;
+    for (int64_t q = lane; q < nlam; q += 32)
+        s += X[i * nlam + q] * lam[q];
+    for (int o = 16; o > 0; o >>= 1)
+        s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+        const double aw = -s;
+        u[i] += beta * dt * dt * aw;
+        v[i] += gamma * dt * aw;
+        a[i] += aw;
+    }
+}
+
+// Transpose a batch of nb solved columns (column-major, ndof rows) into the
+// row-major unit-response matrix X (ndof x nlam) at columns q0..q0+nb-1.
+__global__ void k_store_rows(const int64_t ndof, const int64_t nlam, const int64_t q0, const int nb,
+                             const double *__restrict__ cols, double *__restrict__ X)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ndof * nb)
+        return;
+    const int64_t i = t / nb, c = t - i * nb;
+    X[i * nlam + q0 + c] = cols[c * ndof + i];
 }
 
 // Right-hand sides G_FE^T e_q for a batch of multiplier columns q0..q0+nb-1.
@@ -292,10 +310,9 @@ __global__ void k_hfe(const int64_t nfe, const int dim, const int64_t nl, const 
     const int64_t r = t / nlam, q = t - r * nlam;
     const int c = (int)(r / nl);
     const int64_t k = r - (int64_t)c * nl;
-    const int64_t ndof = (int64_t)dim * nfe;
     double s = 0.0;
     for (int e = 0; e < gfe_w; ++e)
-        s += gval[k * gfe_w + e] * X[q * ndof + (int64_t)c * nfe + gcol[k * gfe_w + e]];
+        s += gval[k * gfe_w + e] * X[((int64_t)c * nfe + gcol[k * gfe_w + e]) * nlam + q];
     H[t] = scale * s;
 }
 
@@ -926,6 +943,48 @@ static int update_near_flags(pdmts_arl *A, int m)
     }
     PDMTS_TRY(A->alloc(A->d_near, (int64_t)wflag.size()));
     PDMTS_TRY(h2d(A->d_near.p, wflag, A->ctx->stream));
+    // Tile rows of the lattice kernel that the link problem can reach: its
+    // response stays within m delta of the loaded overlap nodes, so tile rows
+    // holding no node within (m + 1) delta of a band stay exactly zero.
+    pd->link_win_n[0] = pd->link_win_n[1] = 0;
+    pd->link_bonds = -1;
+    if (pd->layout == pdmts_pd::LAYOUT_LATTICE2D && A->bands.size() <= 2) {
+        const int ny = pd->lat_dims[1], nx = pd->lat_dims[0];
+        const int ntr = (ny + lat2d::TY - 1) / lat2d::TY;
+        std::vector<char> need((size_t)ntr, 0);
+        for (int y = 0; y < ny; ++y)
+            if (near_node[(size_t)y * nx])  // a lattice row is near iff its nodes are (bands span x)
+                need[(size_t)(y / lat2d::TY)] = 1;
+        bool all_x = true;
+        for (const BandDesc &b : A->bands)
+            all_x = all_x && b.axis == 1;
+        int lo[2] = {0, 0}, cnt[2] = {0, 0}, nw = 0;
+        bool ok = all_x;
+        for (int t = 0; t < ntr && ok; ++t) {
+            if (!need[(size_t)t])
+                continue;
+            if (nw > 0 && lo[nw - 1] + cnt[nw - 1] == t) {
+                cnt[nw - 1]++;
+            } else if (nw < 2) {
+                lo[nw] = t;
+                cnt[nw] = 1;
+                ++nw;
+            } else {
+                ok = false;
+            }
+        }
+        if (ok && nw > 0 && cnt[0] + cnt[1] < ntr) {
+            int64_t bonds = 0;
+            for (int w = 0; w < 2; ++w) {
+                pd->link_win_lo[w] = lo[w];
+                pd->link_win_n[w] = cnt[w];
+                const int64_t r0 = std::min<int64_t>((int64_t)lo[w] * lat2d::TY, ny);
+                const int64_t r1 = std::min<int64_t>((int64_t)(lo[w] + cnt[w]) * lat2d::TY, ny);
+                bonds += pd->row_ptr[(size_t)(r1 * nx)] - pd->row_ptr[(size_t)(r0 * nx)];
+            }
+            pd->link_bonds = bonds;
+        }
+    }
     PDMTS_CUDA_TRY(cudaStreamSynchronize(A->ctx->stream));
     return PDMTS_OK;
 }
@@ -940,6 +999,8 @@ static int build_X(pdmts_arl *A, int64_t *launches)
     cudaStream_t s = A->ctx->stream;
     PDMTS_TRY(A->alloc(A->d_X, ndof * nlam));
     const int batch = (int)std::min<int64_t>(nlam, 512);
+    DevArr<double> xb;
+    PDMTS_TRY(A->alloc(xb, ndof * batch));
     for (int b = 0; b < 4; ++b)
         PDMTS_TRY(A->alloc(A->d_B[b], ndof * batch));
     for (int64_t q0 = 0; q0 < nlam; q0 += batch) {
@@ -947,10 +1008,13 @@ static int build_X(pdmts_arl *A, int64_t *launches)
         PDMTS_CUDA_TRY(cudaMemsetAsync(A->d_B[0].p, 0, sizeof(double) * ndof * nb, s));
         k_gfe_rhs<<<blocks(nb), 256, 0, s>>>(fe->n, 2, A->nl, A->gfe_w, A->d_gfe_col.p, A->d_gfe_val.p, q0, nb,
                                              A->d_B[0].p);
-        double *x = A->d_X.p + q0 * ndof;
-        PDMTS_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * ndof * nb, s));
-        PDMTS_TRY(fe_cheb_solve(fe, nb, x, A->d_B[0].p, A->d_B[1].p, A->d_B[2].p, A->d_B[3].p, s, launches));
+        PDMTS_CUDA_TRY(cudaMemsetAsync(xb.p, 0, sizeof(double) * ndof * nb, s));
+        PDMTS_TRY(fe_cheb_solve(fe, nb, xb.p, A->d_B[0].p, A->d_B[1].p, A->d_B[2].p, A->d_B[3].p, s, launches));
+        k_store_rows<<<blocks(ndof * nb), 256, 0, s>>>(ndof, nlam, q0, nb, xb.p, A->d_X.p);
+        ++*launches;
     }
+    PDMTS_CUDA_TRY(cudaStreamSynchronize(s));
+    A->release(xb);
     for (int b = 0; b < 4; ++b)
         A->release(A->d_B[b]);
     A->X_valid = true;
@@ -1251,9 +1315,12 @@ static int coarse_step(pdmts_arl *A)
     if (e != cudaSuccess)
         return fail(PDMTS_ERR_CUDA, "interface residual: %s", cudaGetErrorString(e));
     k_gemv_rows<<<blocks(A->nlam * 32), 256, 0, s>>>(A->nlam, A->d_Hneg_inv.p, A->d_y.p, 1.0, A->d_lam.p);
-    // ---- corrections U = V + Y lambda_m ----
-    k_fe_link_add<<<blocks(fe->ndof()), 256, 0, s>>>(fe->ndof(), A->nlam, A->d_X.p, A->d_lam.p, dtf, beta, gamma,
-                                                    fe->d_u.p, fe->d_v.p, fe->d_a.p);
+    // ---- corrections U = V + Y lambda_m: FE on its stream, PD link run here ----
+    PDMTS_CUDA_TRY(cudaEventRecord(A->ev_fork, s));
+    PDMTS_CUDA_TRY(cudaStreamWaitEvent(A->fe_stream, A->ev_fork, 0));
+    k_fe_link_add<<<blocks(fe->ndof() * 32), 256, 0, A->fe_stream>>>(fe->ndof(), A->nlam, A->d_X.p, A->d_lam.p, dtf,
+                                                                    beta, gamma, fe->d_u.p, fe->d_v.p, fe->d_a.p);
+    PDMTS_CUDA_TRY(cudaEventRecord(A->ev_join, A->fe_stream));
     launches += 3;
     PDMTS_TRY(pd_link_run(A, A->d_lam.p, m, s));
     PDAddLink L{};
@@ -1297,6 +1364,8 @@ static int coarse_step(pdmts_arl *A)
     PDMTS_CUDA_TRY(cudaMemcpyAsync(pd->d_mask_link.p, pd->d_mask.p, sizeof(uint32_t) * pd->n_mask_words,
                                    cudaMemcpyDeviceToDevice, s));
     PDMTS_CUDA_TRY(cudaMemcpyAsync(A->d_lam0.p, A->d_lam.p, sizeof(double) * A->nlam, cudaMemcpyDeviceToDevice, s));
+    // the step ends when the FE correction has also finished
+    PDMTS_CUDA_TRY(cudaStreamWaitEvent(s, A->ev_join, 0));
     launches += 3;
     ctx->stats.kernel_launches += launches;
     ctx->stats.coarse_steps += 1;

@@ -83,6 +83,8 @@ struct pdmts_pd {
     DevArr<float> lk_af, lk_gf;
     DevArr<uint32_t> d_mask_link;
     int lk_cur = 0;
+    int link_win_lo[2] = {0, 0}, link_win_n[2] = {0, 0};  // tile rows the link problem can reach
+    int64_t link_bonds = -1;  // directed bonds evaluated per link substep (-1: all)
     // interface force density of the free problem (G_PD^T lambda_0 / V): FP64 d_g or FP32 f_g
     bool has_g = false;
 

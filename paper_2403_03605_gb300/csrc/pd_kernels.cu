@@ -414,7 +414,7 @@ __global__ void __launch_bounds__(256) k_pd_step_f32(const F32StepArgs A, const 
 // is implicit (offset k of the 28-offset stencil), so per bond only one bit of
 // the node's bond word is read from HBM.
 namespace lat2d {
-constexpr int TX = 32, TY = 8, HX = TX + 2 * R, HY = TY + 2 * R;
+constexpr int HX = TX + 2 * R, HY = TY + 2 * R;
 }
 
 // Bond slot k of a lattice node: the same branch-free expression as bond_2d
@@ -507,7 +507,12 @@ __global__ void __launch_bounds__(256) k_pd_step_lattice2d(const Lat2DArgs A, co
     __shared__ float salpha[HAS_ALPHA ? HY : 1][HX];
     const F32NodeArgs &N = A.nd;
     const int nx = A.nx, ny = A.ny;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    // tile row: all tile rows, or the rows of up to two windows [win_lo, win_lo + win_n)
+    const int trow = A.win_n[0] > 0
+                         ? ((int)blockIdx.y < A.win_n[0] ? A.win_lo[0] + (int)blockIdx.y
+                                                          : A.win_lo[1] + (int)blockIdx.y - A.win_n[0])
+                         : (int)blockIdx.y;
+    const int x0 = blockIdx.x * TX, y0 = trow * TY;
     for (int q = threadIdx.x; q < HX * HY; q += blockDim.x) {
         const int hy = q / HX, hx = q - hy * HX;
         const int gx = x0 + hx - R, gy = y0 + hy - R;
@@ -681,13 +686,15 @@ __global__ void k_constraint(const int dim, const int64_t nl, const int64_t *__r
                              const double *__restrict__ vfe, const double sign_pd, const double sign_fe,
                              double *__restrict__ y)
 {
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // one warp per constraint row (multiplier node k, component c)
+    const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (r >= (int64_t)dim * nl)
         return;
     const int c = (int)(r / nl);
     const int64_t k = r - (int64_t)c * nl;
     double sp = 0.0;
-    for (int64_t e = gpd_ptr[k]; e < gpd_ptr[k + 1]; ++e) {
+    for (int64_t e = gpd_ptr[k] + lane; e < gpd_ptr[k + 1]; e += 32) {
         const int64_t p = gpd_col[e];
         double vp;
         if (v64) {
@@ -704,10 +711,13 @@ __global__ void k_constraint(const int dim, const int64_t nl, const int64_t *__r
         sp += gpd_val[e] * vp;
     }
     double sf = 0.0;
-    if (gfe_col)
-        for (int e = 0; e < gfe_w; ++e)
-            sf += gfe_val[k * gfe_w + e] * vfe[(int64_t)c * nfe + gfe_col[k * gfe_w + e]];
-    y[r] = sign_pd * sp + sign_fe * sf;
+    if (gfe_col && lane < gfe_w)
+        sf = gfe_val[k * gfe_w + lane] * vfe[(int64_t)c * nfe + gfe_col[k * gfe_w + lane]];
+    double t = sign_pd * sp + sign_fe * sf;
+    for (int o = 16; o > 0; o >>= 1)
+        t += __shfl_down_sync(0xffffffffu, t, o);
+    if (lane == 0)
+        y[r] = t;
 }
 
 __global__ void k_pd_add_link(const PDAddLink A)
@@ -817,7 +827,9 @@ cudaError_t launch_pd_step_lattice2d(const Lat2DArgs &A, bool init, cudaStream_t
 {
     if (A.nx <= 0 || A.ny <= 0)
         return cudaSuccess;
-    const dim3 grid((unsigned)((A.nx + lat2d::TX - 1) / lat2d::TX), (unsigned)((A.ny + lat2d::TY - 1) / lat2d::TY));
+    const unsigned rows = A.win_n[0] > 0 ? (unsigned)(A.win_n[0] + A.win_n[1])
+                                         : (unsigned)((A.ny + lat2d::TY - 1) / lat2d::TY);
+    const dim3 grid((unsigned)((A.nx + lat2d::TX - 1) / lat2d::TX), rows);
     const int it = init ? 1 : 0;
     if (A.alpha) {
         if (A.nd.pmb)
@@ -880,9 +892,11 @@ cudaError_t launch_constraint(int dim, int64_t nl, const int64_t *gpd_ptr, const
     const int64_t rows = (int64_t)dim * nl;
     if (rows == 0)
         return cudaSuccess;
-    k_constraint<<<(unsigned)((rows + 127) / 128), 128, 0, s>>>(dim, nl, gpd_ptr, gpd_col, gpd_val, npd, v64, v4, v2,
-                                                                 h, gfe_col, gfe_val, gfe_w, nfe, vfe, sign_pd,
-                                                                 sign_fe, y);
+    if (gfe_w > 32)
+        return cudaErrorInvalidValue;
+    k_constraint<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, s>>>(dim, nl, gpd_ptr, gpd_col, gpd_val, npd, v64, v4,
+                                                                      v2, h, gfe_col, gfe_val, gfe_w, nfe, vfe,
+                                                                      sign_pd, sign_fe, y);
     return cudaGetLastError();
 }
 
@@ -980,7 +994,8 @@ int pd_run_chain(pdmts_pd *pd, int len, int sched, const double *theta, cudaStre
     ctx->stats.graph_launches++;
     ctx->stats.kernel_launches += len;
     ctx->stats.pd_substeps += len;
-    ctx->stats.bond_updates += (int64_t)len * pd->row_ptr[(size_t)pd->n];
+    ctx->stats.bond_updates +=
+        (int64_t)len * ((link && pd->link_bonds >= 0) ? pd->link_bonds : pd->row_ptr[(size_t)pd->n]);
     if (!link)
         pd->steps_done += len;
     if (len & 1)
