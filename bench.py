@@ -163,6 +163,20 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def reduce_job(total_ms, units, world, device=None):
+    """Whole-job figures of N replicas (weak scaling): the slowest rank's time
+    and the units all ranks processed, divided. Returns (max_ms, units_sum, rate)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    tmax, usum = float(t.item()), float(u.item())
+    return tmax, usum, usum / (tmax * 1e-3)
+
+
 def setup_ours(P, ctx, workload):
     """Create the workload through the C ABI; returns (pd, fe, arl, info, pb, m, cp)."""
     from paper_2403_03605_gb300 import workloads as W
@@ -236,11 +250,7 @@ def run_ours(args, rank, world, local_rank):
     launches = st1["kernel_launches"] - st0["kernel_launches"]
     substeps = st1["pd_substeps"] - st0["pd_substeps"]
     units = st1["bond_updates"] - st0["bond_updates"]  # link substeps count only the rows they evaluate
-    t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
-    value = units * world / (total_ms * 1e-3)
+    total_ms, _, value = reduce_job(total_ms, units, world, device=dev)
     coarse_per_s = args.steps * world / (total_ms * 1e-3)
 
     # ---- roofline of the dominant kernel (the FP32-bulk substep) ----------

@@ -1,0 +1,52 @@
+"""The multi-rank (replica) path of bench.py on CPU ranks with gloo (world size 2)."""
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out):
+    import sys
+    import torch.distributed as dist
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, root)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    # each replica reports its own time and units; the job takes the slowest rank
+    tmax, usum, rate = bench.reduce_job(10.0 + 5.0 * rank, 1000 * (rank + 1), world)
+    dist.barrier()
+    dist.destroy_process_group()
+    out[rank] = (tmax, usum, rate)
+
+
+def test_replicas_take_max_time_and_sum_units():
+    world = 2
+    port = _free_port()
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    mp.start_processes(_rank_main, args=(world, port, out), nprocs=world, join=True, start_method="spawn")
+    for r in range(world):
+        tmax, usum, rate = out[r]
+        assert tmax == pytest.approx(15.0)
+        assert usum == pytest.approx(3000.0)
+        assert rate == pytest.approx(3000.0 / 15e-3)
+
+
+def test_reference_arm_other_ranks_do_no_work(monkeypatch):
+    import bench
+    called = []
+    monkeypatch.setattr(bench, "oracle_sample", lambda *a, **k: called.append(1))
+    monkeypatch.setattr(bench, "make_problem", lambda: None)
+
+    class A:
+        steps, warmup, gpus = 2, 1, 2
+    bench.run_reference(A(), rank=1, world=2)
+    assert not called
