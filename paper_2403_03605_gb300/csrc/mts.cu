@@ -7,20 +7,84 @@
 //   stream A: interface force G_PD^T lambda_0 / V on the PD overlap nodes, then
 //             the m PD free substeps (Eq. 48a) with factor (1 - j/m), one graph;
 //   join;     y = G_FE v_FE - G_PD v_PD, lambda_m = (-H)^-1 y (Eq. 49);
-//             FE correction a += -X lambda_m with X = K_eff^-1 G_FE^T (unit
-//             responses, Eq. unit); PD correction U += W from the link problem
-//             (Eq. 48b, zero start, factor j/m, bond words of the step start,
-//             no breaking); rebuild flag if a bond near an overlap band broke.
+//             stream B: FE correction a += a_W with K_eff a_W = -G_FE^T lambda_m
+//             (Eq. 47b, the same Chebyshev solve as the free step); stream A:
+//             PD correction U += W from the link problem (Eq. 48b, zero start,
+//             factor j/m, bond words of the step start, no breaking); rebuild
+//             flag if a bond near an overlap band broke.
+// Stream B has the higher priority: its short kernels take SMs as soon as a
+// PD kernel's blocks retire, so the FE work hides under the PD chains. Both FE
+// sequences run as CUDA graphs captured once per schedule.
 // Conventions follow Eq. 33: FE carries +G_FE^T lambda, PD -G_PD^T lambda and
 // the constraint is G_FE v_FE - G_PD v_PD = 0. All coupling arithmetic is FP64.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <map>
 #include <new>
 
 #include "pd.h"
 
 using namespace pdmts;
+
+// A captured launch sequence, replayed while the launch arguments it was
+// captured with (pointers and scalars, packed into key) are unchanged.
+struct GraphSlot {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<uint64_t> key;
+    int64_t launches = 0;
+    void reset()
+    {
+        if (exec)
+            cudaGraphExecDestroy(exec);
+        exec = nullptr;
+        key.clear();
+        launches = 0;
+    }
+};
+
+static uint64_t key_bits(double x)
+{
+    uint64_t b;
+    std::memcpy(&b, &x, sizeof b);
+    return b;
+}
+static uint64_t key_bits(const void *p) { return (uint64_t)(uintptr_t)p; }
+
+// Replay g on s, capturing enqueue(&launches) first if g is empty or was
+// captured under another key.
+template <class F>
+static int run_graph(pdmts_ctx *ctx, GraphSlot &g, const std::vector<uint64_t> &key, cudaStream_t s, F &&enqueue,
+                     int64_t *launches)
+{
+    if (!g.exec || g.key != key) {
+        g.reset();
+        cudaGraph_t graph = nullptr;
+        PDMTS_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        int64_t n = 0;
+        const int r = enqueue(&n);
+        const cudaError_t ce = cudaStreamEndCapture(s, &graph);
+        if (r != PDMTS_OK) {
+            if (graph)
+                cudaGraphDestroy(graph);
+            return r;
+        }
+        if (ce != cudaSuccess)
+            return fail(PDMTS_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ce));
+        const cudaError_t ie = cudaGraphInstantiate(&g.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ie != cudaSuccess) {
+            g.exec = nullptr;
+            return fail(PDMTS_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(ie));
+        }
+        g.key = key;
+        g.launches = n;
+    }
+    PDMTS_CUDA_TRY(cudaGraphLaunch(g.exec, s));
+    *launches += g.launches;
+    ctx->stats.graph_launches += 1;
+    return PDMTS_OK;
+}
 
 // ------------------------------------------------------------ FE handle --
 struct pdmts_fem {
@@ -39,14 +103,18 @@ struct pdmts_fem {
     std::vector<double> mass;         // ndof, lumped mass
     std::vector<double> load;         // ndof, loads P
     double gersh = 0;                 // Gershgorin bound of M^-1 K
-    // device
+    // device; the ELL arrays are stored transposed (entry e of row i at
+    // e * ndof + i) so that a warp's 32 rows read consecutive words
     DevArr<int32_t> d_col;
     DevArr<double> d_K, d_Keff, d_Minv, d_P;
     DevArr<double> d_u, d_v, d_a, d_ut, d_vt, d_b, d_r, d_d[2];
+    DevArr<double> d_aw, d_bw;        // link correction: a_W and -G_FE^T lambda
     int64_t device_bytes = 0;
-    // Chebyshev schedule for K_eff (depends on dt_FE)
+    // Chebyshev schedule for K_eff (depends on dt_FE); version counts changes
     double keff_dt = -1, cheb_theta = 0, cheb_delta = 0;
     std::vector<double> cheb_c1, cheb_c2;
+    int64_t keff_version = 0;
+    GraphSlot g_free, g_link;         // captured free step and link correction
     bool assembled = false;
     int64_t ndof() const { return (int64_t)dim * n; }
 
@@ -71,9 +139,11 @@ struct pdmts_fem {
     }
     void release_all()
     {
+        g_free.reset();
+        g_link.reset();
         release(d_col); release(d_K); release(d_Keff); release(d_Minv); release(d_P);
         release(d_u); release(d_v); release(d_a); release(d_ut); release(d_vt); release(d_b); release(d_r);
-        release(d_d[0]); release(d_d[1]);
+        release(d_d[0]); release(d_d[1]); release(d_aw); release(d_bw);
     }
 };
 
@@ -122,8 +192,14 @@ struct pdmts_arl {
     std::vector<double> ov_N;
     int64_t n_ov = 0;
     // device
-    DevArr<int32_t> d_gfe_col, d_gpd_col, d_ov_node, d_ov_k, d_owner;
-    DevArr<double> d_gfe_val, d_gpd_val, d_ov_N, d_X, d_Hneg_inv, d_colbuf, d_lam0, d_lam, d_y, d_unit;
+    // G_FE^T by FE node (CSR): multiplier node and weight of each entry
+    std::vector<int64_t> gfeT_ptr;
+    std::vector<int32_t> gfeT_k;
+    std::vector<double> gfeT_val;
+    DevArr<int32_t> d_gfe_col, d_gpd_col, d_ov_node, d_ov_k, d_owner, d_gfeT_k;
+    DevArr<int64_t> d_gfeT_ptr;
+    DevArr<double> d_gfe_val, d_gpd_val, d_ov_N, d_gfeT_val, d_Hfe, d_Hneg_inv, d_colbuf, d_lam0, d_lam, d_y,
+        d_unit;
     DevArr<double> d_B[4];          // block Chebyshev work (x, r, d0, d1)
     DevArr<int64_t> d_gpd_ptr;
     DevArr<uint8_t> d_near;         // bond words of nodes within (m + 1) delta of a band
@@ -131,7 +207,7 @@ struct pdmts_arl {
     unsigned long long *h_changed = nullptr;  // pinned
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_flag = nullptr;
     cudaStream_t fe_stream = nullptr;
-    bool H_valid = false, X_valid = false, flag_pending = false;
+    bool H_valid = false, Hfe_valid = false, flag_pending = false;
     int64_t rebuilds = 0, colors = 0;
     int built_m = 0;
     std::vector<double> theta_free, theta_link;
@@ -160,7 +236,8 @@ struct pdmts_arl {
     void release_all()
     {
         release(d_gfe_col); release(d_gpd_col); release(d_ov_node); release(d_ov_k); release(d_owner);
-        release(d_gfe_val); release(d_gpd_val); release(d_ov_N); release(d_X); release(d_Hneg_inv);
+        release(d_gfeT_k); release(d_gfeT_ptr); release(d_gfeT_val); release(d_Hfe);
+        release(d_gfe_val); release(d_gpd_val); release(d_ov_N); release(d_Hneg_inv);
         release(d_colbuf); release(d_lam0); release(d_lam); release(d_y); release(d_unit);
         for (auto &b : d_B)
             release(b);
@@ -174,6 +251,20 @@ static int h2d(T *dst, const std::vector<T> &src, cudaStream_t s)
     if (src.empty())
         return PDMTS_OK;
     PDMTS_CUDA_TRY(cudaMemcpyAsync(dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice, s));
+    return PDMTS_OK;
+}
+
+// Row-major ELL (rows x W) to the transposed device layout (W x rows). The
+// copy is synchronous: the host vector is a temporary.
+template <typename T>
+static int h2d_ell_t(T *dst, const std::vector<T> &src, int64_t rows, int W, cudaStream_t s)
+{
+    std::vector<T> t(src.size());
+    for (int64_t i = 0; i < rows; ++i)
+        for (int e = 0; e < W; ++e)
+            t[(size_t)e * rows + i] = src[(size_t)i * W + e];
+    PDMTS_TRY(h2d(dst, t, s));
+    PDMTS_CUDA_TRY(cudaStreamSynchronize(s));
     return PDMTS_OK;
 }
 
@@ -202,7 +293,7 @@ __global__ void k_fe_residual(const int64_t ndof, const int W, const int32_t *__
         return;
     double ax = 0.0;
     for (int e = 0; e < W; ++e)
-        ax += val[i * W + e] * x[col[i * W + e]];
+        ax += val[e * ndof + i] * x[col[e * ndof + i]];
     const double ri = (b ? b[i] : 0.0) - ax;
     r[i] = ri;
     if (d)
@@ -223,7 +314,7 @@ __global__ void k_cheb_iter(const int64_t ndof, const int nrhs, const int W, con
     const double *dc = d + c * ndof;
     double ad = 0.0;
     for (int e = 0; e < W; ++e)
-        ad += val[i * W + e] * dc[col[i * W + e]];
+        ad += val[e * ndof + i] * dc[col[e * ndof + i]];
     x[t] += d[t];
     const double rn = r[t] - ad;
     r[t] = rn;
@@ -243,40 +334,36 @@ __global__ void k_fe_correct_state(const int64_t ndof, const double *__restrict_
     v[i] = vt[i] + gamma * dt * a[i];
 }
 
-// FE link response added to the state: a_W = -X lambda with X row-major
-// (ndof x nlam, one warp per FE dof), u += beta dt^2 a_W, v += gamma dt a_W,
-// a += a_W.
-__global__ void k_fe_link_add(const int64_t ndof, const int64_t nlam, const double *__restrict__ X,
-                              const double *__restrict__ lam, const double dt, const double beta, const double gamma,
-                              double *__restrict__ u, double *__restrict__ v, double *__restrict__ a)
+// b = -G_FE^T lambda on the FE dofs (gather over the transpose, so the sum
+// order is fixed and the result reproducible).
+__global__ void k_gfe_lam(const int64_t nfe, const int dim, const int64_t nl, const int64_t *__restrict__ ptr,
+                          const int32_t *__restrict__ kk, const double *__restrict__ val,
+                          const double *__restrict__ lam, double *__restrict__ b)
 {
-    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (i >= ndof)
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)dim * nfe)
         return;
+    const int c = (int)(i / nfe);
+    const int64_t node = i - (int64_t)c * nfe;
     double s = 0.0;
-    for (int64_t q = lane; q < nlam; q += 32)
-        s += X[i * nlam + q] * lam[q];
-    for (int o = 16; o > 0; o >>= 1)
-        s += __shfl_down_sync(0xffffffffu, s, o);
-    if (lane == 0) {
-        const double aw = -s;
-        u[i] += beta * dt * dt * aw;
-        v[i] += gamma * dt * aw;
-        a[i] += aw;
-    }
+    for (int64_t j = ptr[node]; j < ptr[node + 1]; ++j)
+        s += val[j] * lam[(int64_t)c * nl + kk[j]];
+    b[i] = -s;
 }
 
-// Transpose a batch of nb solved columns (column-major, ndof rows) into the
-// row-major unit-response matrix X (ndof x nlam) at columns q0..q0+nb-1.
-__global__ void k_store_rows(const int64_t ndof, const int64_t nlam, const int64_t q0, const int nb,
-                             const double *__restrict__ cols, double *__restrict__ X)
+// FE link correction (Eq. 47b with Newmark): u += beta dt^2 a_W,
+// v += gamma dt a_W, a += a_W.
+__global__ void k_fe_apply_link(const int64_t ndof, const double *__restrict__ aw, const double dt, const double beta,
+                                const double gamma, double *__restrict__ u, double *__restrict__ v,
+                                double *__restrict__ a)
 {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= ndof * nb)
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ndof)
         return;
-    const int64_t i = t / nb, c = t - i * nb;
-    X[i * nlam + q0 + c] = cols[c * ndof + i];
+    const double w = aw[i];
+    u[i] += beta * dt * dt * w;
+    v[i] += gamma * dt * w;
+    a[i] += w;
 }
 
 // Right-hand sides G_FE^T e_q for a batch of multiplier columns q0..q0+nb-1.
@@ -298,22 +385,25 @@ __global__ void k_gfe_rhs(const int64_t nfe, const int dim, const int64_t nl, co
     }
 }
 
-// H_FE[r, q] = -gamma dt (G_FE X)[r, q] for all rows r, columns q (row-major H).
-__global__ void k_hfe(const int64_t nfe, const int dim, const int64_t nl, const int gfe_w,
-                      const int32_t *__restrict__ gcol, const double *__restrict__ gval, const double *__restrict__ X,
-                      const double scale, double *__restrict__ H)
+// Columns q0..q0+nb-1 of H_FE = -gamma dt G_FE K_eff^-1 G_FE^T from the solved
+// batch cols (column-major, ndof rows): H[r, q0 + c] for every row r.
+__global__ void k_hfe_cols(const int64_t nfe, const int dim, const int64_t nl, const int gfe_w,
+                           const int32_t *__restrict__ gcol, const double *__restrict__ gval, const int64_t q0,
+                           const int nb, const double *__restrict__ cols, const double scale, double *__restrict__ H)
 {
-    const int64_t nlam = (int64_t)dim * nl;
+    const int64_t nlam = (int64_t)dim * nl, ndof = (int64_t)dim * nfe;
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nlam * nlam)
+    if (t >= nlam * nb)
         return;
-    const int64_t r = t / nlam, q = t - r * nlam;
-    const int c = (int)(r / nl);
-    const int64_t k = r - (int64_t)c * nl;
+    const int64_t r = t / nb;
+    const int c = (int)(t - r * nb);
+    const int cd = (int)(r / nl);
+    const int64_t k = r - (int64_t)cd * nl;
+    const double *x = cols + (int64_t)c * ndof + (int64_t)cd * nfe;
     double s = 0.0;
     for (int e = 0; e < gfe_w; ++e)
-        s += gval[k * gfe_w + e] * X[((int64_t)c * nfe + gcol[k * gfe_w + e]) * nlam + q];
-    H[t] = scale * s;
+        s += gval[k * gfe_w + e] * x[gcol[k * gfe_w + e]];
+    H[r * nlam + q0 + c] = scale * s;
 }
 
 // H[r, owner[r]] += sign * y[r] for the rows a colored link run measures.
@@ -516,12 +606,12 @@ static int fe_assemble(pdmts_fem *fe, const std::vector<BandDesc> &bands, int ki
     std::vector<double> minv((size_t)ndof);
     for (int64_t i = 0; i < ndof; ++i)
         minv[(size_t)i] = 1.0 / fe->mass[(size_t)i];
-    PDMTS_TRY(h2d(fe->d_col.p, fe->col, s));
-    PDMTS_TRY(h2d(fe->d_K.p, fe->kval, s));
+    PDMTS_TRY(h2d_ell_t(fe->d_col.p, fe->col, ndof, fe->W, s));
+    PDMTS_TRY(h2d_ell_t(fe->d_K.p, fe->kval, ndof, fe->W, s));
     PDMTS_TRY(h2d(fe->d_Minv.p, minv, s));
     PDMTS_TRY(h2d(fe->d_P.p, fe->load, s));
     for (DevArr<double> *a : {&fe->d_u, &fe->d_v, &fe->d_a, &fe->d_ut, &fe->d_vt, &fe->d_b, &fe->d_r, &fe->d_d[0],
-                              &fe->d_d[1]}) {
+                              &fe->d_d[1], &fe->d_aw, &fe->d_bw}) {
         PDMTS_TRY(fe->alloc(*a, ndof));
         PDMTS_CUDA_TRY(cudaMemsetAsync(a->p, 0, sizeof(double) * ndof, s));
     }
@@ -533,6 +623,8 @@ static int fe_assemble(pdmts_fem *fe, const std::vector<BandDesc> &bands, int ki
     PDMTS_CUDA_TRY(cudaStreamSynchronize(s));
     fe->assembled = true;
     fe->keff_dt = -1;
+    fe->g_free.reset();
+    fe->g_link.reset();
     return PDMTS_OK;
 }
 
@@ -546,7 +638,6 @@ static int fe_prepare_keff(pdmts_fem *fe, double dt, double beta)
     const int64_t ndof = fe->ndof();
     std::vector<double> keff(fe->kval);
     for (int64_t i = 0; i < ndof; ++i) {
-        keff[(size_t)i * fe->W + 0] *= 1.0;
         for (int e = 0; e < fe->W; ++e)
             keff[(size_t)i * fe->W + e] *= beta * dt * dt;
         bool found = false;
@@ -558,7 +649,7 @@ static int fe_prepare_keff(pdmts_fem *fe, double dt, double beta)
         if (!found)
             return fail(PDMTS_ERR_STATE, "FE matrix row %lld lacks a diagonal entry", (long long)i);
     }
-    PDMTS_TRY(h2d(fe->d_Keff.p, keff, fe->ctx->stream));
+    PDMTS_TRY(h2d_ell_t(fe->d_Keff.p, keff, ndof, fe->W, fe->ctx->stream));
     const double lmin = 1.0, lmax = 1.0 + beta * dt * dt * fe->gersh;
     fe->cheb_theta = 0.5 * (lmax + lmin);
     fe->cheb_delta = 0.5 * (lmax - lmin);
@@ -577,6 +668,7 @@ static int fe_prepare_keff(pdmts_fem *fe, double dt, double beta)
         rho = rn;
     }
     fe->keff_dt = dt;
+    fe->keff_version += 1;
     PDMTS_CUDA_TRY(cudaStreamSynchronize(fe->ctx->stream));
     return PDMTS_OK;
 }
@@ -608,7 +700,7 @@ static int fe_cheb_solve(pdmts_fem *fe, int nrhs, double *x, const double *b, do
 }
 
 // Free FE step (Eq. 47a + Eq. 39): predictor, K_eff a = P - K u~, corrector.
-static int fe_free_step(pdmts_fem *fe, double dt, double beta, double gamma, cudaStream_t s, int64_t *launches)
+static int fe_free_enqueue(pdmts_fem *fe, double dt, double beta, double gamma, cudaStream_t s, int64_t *launches)
 {
     const int64_t ndof = fe->ndof();
     k_fe_predict<<<blocks(ndof), 256, 0, s>>>(ndof, fe->d_u.p, fe->d_v.p, fe->d_a.p, dt, beta, gamma, fe->d_ut.p,
@@ -623,6 +715,28 @@ static int fe_free_step(pdmts_fem *fe, double dt, double beta, double gamma, cud
     ++*launches;
     PDMTS_CUDA_TRY(cudaGetLastError());
     return PDMTS_OK;
+}
+
+// Launch arguments an FE graph depends on: step scalars, the K_eff schedule
+// version and every FE array pointer.
+static std::vector<uint64_t> fe_graph_key(const pdmts_fem *fe, double dt, double beta, double gamma)
+{
+    std::vector<uint64_t> k{key_bits(dt), key_bits(beta), key_bits(gamma), (uint64_t)fe->keff_version};
+    for (const void *p : {(const void *)fe->d_col.p, (const void *)fe->d_K.p, (const void *)fe->d_Keff.p,
+                          (const void *)fe->d_Minv.p, (const void *)fe->d_P.p, (const void *)fe->d_u.p,
+                          (const void *)fe->d_v.p, (const void *)fe->d_a.p, (const void *)fe->d_ut.p,
+                          (const void *)fe->d_vt.p, (const void *)fe->d_b.p, (const void *)fe->d_r.p,
+                          (const void *)fe->d_d[0].p, (const void *)fe->d_d[1].p, (const void *)fe->d_aw.p,
+                          (const void *)fe->d_bw.p})
+        k.push_back(key_bits(p));
+    return k;
+}
+
+static int fe_free_step(pdmts_fem *fe, double dt, double beta, double gamma, cudaStream_t s, int64_t *launches)
+{
+    return run_graph(
+        fe->ctx, fe->g_free, fe_graph_key(fe, dt, beta, gamma), s,
+        [&](int64_t *n) { return fe_free_enqueue(fe, dt, beta, gamma, s, n); }, launches);
 }
 
 // ------------------------------------------------------------ FE ABI -----
@@ -842,6 +956,24 @@ static int build_constraint(pdmts_arl *A)
             ++e;
         }
     }
+    // the transpose by FE node, for the FE link correction
+    A->gfeT_ptr.assign((size_t)nfe + 1, 0);
+    for (int64_t k = 0; k < A->nl; ++k)
+        for (auto &kv : grow[(size_t)k])
+            A->gfeT_ptr[(size_t)kv.first + 1] += 1;
+    for (int64_t i = 0; i < nfe; ++i)
+        A->gfeT_ptr[(size_t)i + 1] += A->gfeT_ptr[(size_t)i];
+    A->gfeT_k.assign((size_t)A->gfeT_ptr[(size_t)nfe], 0);
+    A->gfeT_val.assign((size_t)A->gfeT_ptr[(size_t)nfe], 0.0);
+    {
+        std::vector<int64_t> fill(A->gfeT_ptr.begin(), A->gfeT_ptr.end() - 1);
+        for (int64_t k = 0; k < A->nl; ++k)
+            for (auto &kv : grow[(size_t)k]) {
+                const int64_t j = fill[(size_t)kv.first]++;
+                A->gfeT_k[(size_t)j] = (int32_t)k;
+                A->gfeT_val[(size_t)j] = kv.second;
+            }
+    }
     // PD nodes inside overlap elements: G_PD[k, p] = N_k(x_p) V_p
     std::vector<std::vector<std::pair<int32_t, double>>> prow((size_t)A->nl);
     A->ov_node.clear(); A->ov_k.clear(); A->ov_N.clear();
@@ -897,8 +1029,14 @@ static int build_constraint(pdmts_arl *A)
     PDMTS_TRY(A->alloc(A->d_ov_node, std::max<int64_t>(A->n_ov, 1)));
     PDMTS_TRY(A->alloc(A->d_ov_k, std::max<int64_t>(4 * A->n_ov, 1)));
     PDMTS_TRY(A->alloc(A->d_ov_N, std::max<int64_t>(4 * A->n_ov, 1)));
+    PDMTS_TRY(A->alloc(A->d_gfeT_ptr, (int64_t)A->gfeT_ptr.size()));
+    PDMTS_TRY(A->alloc(A->d_gfeT_k, std::max<int64_t>((int64_t)A->gfeT_k.size(), 1)));
+    PDMTS_TRY(A->alloc(A->d_gfeT_val, std::max<int64_t>((int64_t)A->gfeT_val.size(), 1)));
     PDMTS_TRY(h2d(A->d_gfe_col.p, A->gfe_col, s));
     PDMTS_TRY(h2d(A->d_gfe_val.p, A->gfe_val, s));
+    PDMTS_TRY(h2d(A->d_gfeT_ptr.p, A->gfeT_ptr, s));
+    PDMTS_TRY(h2d(A->d_gfeT_k.p, A->gfeT_k, s));
+    PDMTS_TRY(h2d(A->d_gfeT_val.p, A->gfeT_val, s));
     PDMTS_TRY(h2d(A->d_gpd_ptr.p, A->gpd_ptr, s));
     PDMTS_TRY(h2d(A->d_gpd_col.p, A->gpd_col, s));
     PDMTS_TRY(h2d(A->d_gpd_val.p, A->gpd_val, s));
@@ -989,15 +1127,17 @@ static int update_near_flags(pdmts_arl *A, int m)
     return PDMTS_OK;
 }
 
-// Unit responses of the FE subdomain: X = K_eff^-1 G_FE^T (column-major), by
-// block Chebyshev in batches of columns.
-static int build_X(pdmts_arl *A, int64_t *launches)
+// FE part of the interface operator, H_FE = -gamma dt_FE G_FE K_eff^-1 G_FE^T
+// (Eq. 49 with the Newmark velocity response of a unit multiplier), by block
+// Chebyshev over batches of unit columns. It does not depend on the PD bond
+// state, so it is kept until dt_FE changes.
+static int build_Hfe(pdmts_arl *A, double dtf, int64_t *launches)
 {
     pdmts_fem *fe = A->fe;
     const int64_t ndof = fe->ndof();
     const int64_t nlam = A->nlam;
     cudaStream_t s = A->ctx->stream;
-    PDMTS_TRY(A->alloc(A->d_X, ndof * nlam));
+    PDMTS_TRY(A->alloc(A->d_Hfe, nlam * nlam));
     const int batch = (int)std::min<int64_t>(nlam, 512);
     DevArr<double> xb;
     PDMTS_TRY(A->alloc(xb, ndof * batch));
@@ -1010,16 +1150,47 @@ static int build_X(pdmts_arl *A, int64_t *launches)
                                              A->d_B[0].p);
         PDMTS_CUDA_TRY(cudaMemsetAsync(xb.p, 0, sizeof(double) * ndof * nb, s));
         PDMTS_TRY(fe_cheb_solve(fe, nb, xb.p, A->d_B[0].p, A->d_B[1].p, A->d_B[2].p, A->d_B[3].p, s, launches));
-        k_store_rows<<<blocks(ndof * nb), 256, 0, s>>>(ndof, nlam, q0, nb, xb.p, A->d_X.p);
-        ++*launches;
+        k_hfe_cols<<<blocks(nlam * nb), 256, 0, s>>>(fe->n, 2, A->nl, A->gfe_w, A->d_gfe_col.p, A->d_gfe_val.p, q0,
+                                                     nb, xb.p, -A->ctx->gamma_fe * dtf, A->d_Hfe.p);
+        *launches += 2;
     }
     PDMTS_CUDA_TRY(cudaStreamSynchronize(s));
     A->release(xb);
     for (int b = 0; b < 4; ++b)
         A->release(A->d_B[b]);
-    A->X_valid = true;
+    A->Hfe_valid = true;
     PDMTS_CUDA_TRY(cudaGetLastError());
     return PDMTS_OK;
+}
+
+// FE link correction (Eq. 47b): K_eff a_W = -G_FE^T lambda_m from a zero
+// start with the free step's Chebyshev schedule, then the Newmark update.
+static int fe_link_enqueue(pdmts_arl *A, double dt, double beta, double gamma, cudaStream_t s, int64_t *launches)
+{
+    pdmts_fem *fe = A->fe;
+    const int64_t ndof = fe->ndof();
+    k_gfe_lam<<<blocks(ndof), 256, 0, s>>>(fe->n, 2, A->nl, A->d_gfeT_ptr.p, A->d_gfeT_k.p, A->d_gfeT_val.p,
+                                           A->d_lam.p, fe->d_bw.p);
+    PDMTS_CUDA_TRY(cudaMemsetAsync(fe->d_aw.p, 0, sizeof(double) * ndof, s));
+    ++*launches;
+    PDMTS_TRY(fe_cheb_solve(fe, 1, fe->d_aw.p, fe->d_bw.p, fe->d_r.p, fe->d_d[0].p, fe->d_d[1].p, s, launches));
+    k_fe_apply_link<<<blocks(ndof), 256, 0, s>>>(ndof, fe->d_aw.p, dt, beta, gamma, fe->d_u.p, fe->d_v.p,
+                                                 fe->d_a.p);
+    ++*launches;
+    PDMTS_CUDA_TRY(cudaGetLastError());
+    return PDMTS_OK;
+}
+
+static int fe_link_step(pdmts_arl *A, double dt, double beta, double gamma, cudaStream_t s, int64_t *launches)
+{
+    std::vector<uint64_t> key = fe_graph_key(A->fe, dt, beta, gamma);
+    for (const void *p : {(const void *)A->d_gfeT_ptr.p, (const void *)A->d_gfeT_k.p,
+                          (const void *)A->d_gfeT_val.p, (const void *)A->d_lam.p})
+        key.push_back(key_bits(p));
+    key.push_back((uint64_t)A->nl);
+    return run_graph(
+        A->ctx, A->fe->g_link, key, s, [&](int64_t *n) { return fe_link_enqueue(A, dt, beta, gamma, s, n); },
+        launches);
 }
 
 int pd_run_chain(pdmts_pd *pd, int len, int sched, const double *theta, cudaStream_t s, bool link);
@@ -1056,13 +1227,11 @@ static int build_H(pdmts_arl *A, int m)
     cudaStream_t s = ctx->stream;
     const int64_t nlam = A->nlam, nl = A->nl;
     int64_t launches = 0;
-    if (!A->X_valid)
-        PDMTS_TRY(build_X(A, &launches));
-    const double gamma = ctx->gamma_fe, dtf = m * ctx->dt_pd;
+    const double dtf = m * ctx->dt_pd;
+    if (!A->Hfe_valid)
+        PDMTS_TRY(build_Hfe(A, dtf, &launches));
     double *H = A->d_Hneg_inv.p;  // holds H while building, then (-H)^-1
-    k_hfe<<<blocks(nlam * nlam), 256, 0, s>>>(fe->n, 2, nl, A->gfe_w, A->d_gfe_col.p, A->d_gfe_val.p, A->d_X.p,
-                                             -gamma * dtf, H);
-    ++launches;
+    PDMTS_CUDA_TRY(cudaMemcpyAsync(H, A->d_Hfe.p, sizeof(double) * nlam * nlam, cudaMemcpyDeviceToDevice, s));
     // colouring of the multiplier columns
     double hmax = 0.0;
     for (int64_t e = 0; e < fe->ne; ++e) {
@@ -1192,7 +1361,9 @@ extern "C" int arlequin_bind(pdmts_ctx *ctx, pdmts_pd *pd, pdmts_fem *fe, int we
     if (r == PDMTS_OK)
         r = build_constraint(A);
     if (r == PDMTS_OK) {
-        if (cudaStreamCreateWithFlags(&A->fe_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        int lo_prio = 0, hi_prio = 0;
+        if (cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&A->fe_stream, cudaStreamNonBlocking, hi_prio) != cudaSuccess ||
             cudaEventCreateWithFlags(&A->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&A->ev_join, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&A->ev_flag, cudaEventDisableTiming) != cudaSuccess ||
@@ -1251,7 +1422,7 @@ int mts_time_changed(pdmts_ctx *ctx)
 {
     if (ctx->arl) {
         ctx->arl->H_valid = false;
-        ctx->arl->X_valid = false;
+        ctx->arl->Hfe_valid = false;
     }
     return PDMTS_OK;
 }
@@ -1292,11 +1463,9 @@ static int coarse_step(pdmts_arl *A)
     PDMTS_TRY(pd->ensure_init(s));
     if (!A->H_valid)
         PDMTS_TRY(build_H(A, m));
-    // ---- FE free step on the second stream (Eq. 47a) ----
+    // The FE free step may start once the previous step has ended; the PD
+    // chain is enqueued first so that it starts without waiting for the host.
     PDMTS_CUDA_TRY(cudaEventRecord(A->ev_fork, s));
-    PDMTS_CUDA_TRY(cudaStreamWaitEvent(A->fe_stream, A->ev_fork, 0));
-    PDMTS_TRY(fe_free_step(fe, dtf, beta, gamma, A->fe_stream, &launches));
-    PDMTS_CUDA_TRY(cudaEventRecord(A->ev_join, A->fe_stream));
     // ---- PD free substeps with (1 - j/m) lambda_0 (Eq. 48a) ----
     cudaError_t e = launch_interface_force(pd->dim, pd->n, A->n_ov, A->d_ov_node.p, A->d_ov_k.p, A->d_ov_N.p, 4,
                                            A->d_lam0.p, A->nl, f64 ? 0.0 : 1.0 / pd->h, f64 ? pd->d_g.p : nullptr,
@@ -1305,6 +1474,10 @@ static int coarse_step(pdmts_arl *A)
         return fail(PDMTS_ERR_CUDA, "interface force: %s", cudaGetErrorString(e));
     ++launches;
     PDMTS_TRY(pd_run_chain(pd, m, 1, A->theta_free.data(), s, false));
+    // ---- FE free step on the second stream (Eq. 47a) ----
+    PDMTS_CUDA_TRY(cudaStreamWaitEvent(A->fe_stream, A->ev_fork, 0));
+    PDMTS_TRY(fe_free_step(fe, dtf, beta, gamma, A->fe_stream, &launches));
+    PDMTS_CUDA_TRY(cudaEventRecord(A->ev_join, A->fe_stream));
     PDMTS_CUDA_TRY(cudaStreamWaitEvent(s, A->ev_join, 0));
     // ---- interface problem (Eq. 49): lambda_m = (-H)^-1 (G_FE v_FE - G_PD v_PD) ----
     const float4 *v4 = f64 ? nullptr : pd->f_v4.p;
@@ -1318,10 +1491,9 @@ static int coarse_step(pdmts_arl *A)
     // ---- corrections U = V + Y lambda_m: FE on its stream, PD link run here ----
     PDMTS_CUDA_TRY(cudaEventRecord(A->ev_fork, s));
     PDMTS_CUDA_TRY(cudaStreamWaitEvent(A->fe_stream, A->ev_fork, 0));
-    k_fe_link_add<<<blocks(fe->ndof() * 32), 256, 0, A->fe_stream>>>(fe->ndof(), A->nlam, A->d_X.p, A->d_lam.p, dtf,
-                                                                    beta, gamma, fe->d_u.p, fe->d_v.p, fe->d_a.p);
+    PDMTS_TRY(fe_link_step(A, dtf, beta, gamma, A->fe_stream, &launches));
     PDMTS_CUDA_TRY(cudaEventRecord(A->ev_join, A->fe_stream));
-    launches += 3;
+    launches += 2;
     PDMTS_TRY(pd_link_run(A, A->d_lam.p, m, s));
     PDAddLink L{};
     L.dim = pd->dim;
