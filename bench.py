@@ -216,6 +216,7 @@ def run_ours(args, rank, world, local_rank):
     ctx = P.pdmts_ctx_create(local_rank, stream.cuda_stream)
     t_setup = time.perf_counter()
     pd, fe, arl, info, pb, m, cp = setup_ours(P, ctx, args.workload)
+    P.pd_set_lattice_tile(pd, args.lattice_tile)
     flush = torch.empty(int(256e6) // 4, dtype=torch.float32, device=dev)  # > L2 (129 MiB)
 
     for _ in range(args.warmup):  # the first coarse step also builds the interface operator
@@ -260,8 +261,11 @@ def run_ours(args, rank, world, local_rank):
     launch_ms = chain_ms / max(chain_sub, 1)
     achieved = abytes / (launch_ms * 1e-3) / 1e9
     peak, peak_kind = peaks()
-    kname = ("k_pd_step_lattice2d<%s,false>" % ("true" if coupled else "false")) if info["layout"] == 1 \
-        else "k_pd_step_f32<2>"
+    tile = P.pd_info(pd)["lattice_tile"]
+    # lattice kernel of each tile configuration, as listed at pd_set_lattice_tile
+    lat_kernels = ["k_pd_step_lattice2d<false,2,3>", "k_pd_step_lattice2d<false,2,4>",
+                   "k_pd_step_lattice2d_pipe<false,2,2>", "k_pd_step_lattice2d_pipe<false,1,4>"]
+    kname = lat_kernels[tile] if info["layout"] == 1 and tile >= 0 else "k_pd_step_f32<2>"
     traffic = None
     tfile = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tfile):
@@ -311,6 +315,7 @@ def run_ours(args, rank, world, local_rank):
         cfg = {"workload": COUPLED_NAME if coupled else WORKLOAD["name"], "pd_nodes": pb.n,
                "directed_bonds": info["n_bonds"], "m": m,
                "family_layout": "lattice bond words" if info["layout"] == 1 else "sliced ELL",
+               "lattice_tile": tile,
                "graph": "one captured graph per PD substep chain",
                "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                "l2": "flushed between timed steps (256 MB write)"}
@@ -341,9 +346,11 @@ def kernel_version():
     """Hash of the hot-path kernel source: a stored DRAM-traffic figure is only
     reported while the kernel it was measured on is unchanged."""
     import hashlib
-    src = os.path.join(ROOT, "paper_2403_03605_gb300", "csrc", "pd_kernels.cu")
-    with open(src, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for name in ("lattice2d.cuh", "f32_device.cuh", "pd_kernels.cu"):
+        with open(os.path.join(ROOT, "paper_2403_03605_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def main():
@@ -354,6 +361,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=["coupled", "pd"], default="coupled")
+    ap.add_argument("--lattice-tile", type=int, default=-1,
+                    help="fix the lattice kernel tile configuration (default: autotune)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

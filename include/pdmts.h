@@ -137,6 +137,21 @@ int pd_set_breaking(pdmts_pd *pd, int enabled);
 /* PDMTS_FORCE_LINEAR (Eq. 2, default) or PDMTS_FORCE_PMB. */
 int pd_set_force_law(pdmts_pd *pd, int kind);
 
+/* Tile configuration of the FP32-bulk 2D lattice kernel (a performance
+ * setting; results do not depend on it: every configuration evaluates each
+ * node's bonds in the same order). 0 .. PDMTS_LATTICE_TILES - 1 fixes one;
+ * PDMTS_LATTICE_TILE_AUTO (the default) times every configuration once, on
+ * scratch copies of the state, before the next substep chain and keeps the
+ * fastest. Configurations: 0: one CTA per 32 x 16 tile, strips of 2 nodes
+ * per thread, registers for 3 CTAs per SM; 1: the same for 4 CTAs per SM;
+ * 2: a persistent grid that stages each CTA's next tile while it computes
+ * the current one, 2 nodes per thread; 3: the same with 1 node per thread.
+ * Other layouts and precisions ignore the setting. PDMTS_ERR_ARG if out of
+ * range. */
+#define PDMTS_LATTICE_TILES 4
+#define PDMTS_LATTICE_TILE_AUTO (-1)
+int pd_set_lattice_tile(pdmts_pd *pd, int tile);
+
 typedef struct {
     int32_t dim;
     int32_t precision;
@@ -148,7 +163,8 @@ typedef struct {
     int32_t layout;        /* 0: sliced-ELL list; 1: 2D lattice bond words */
     int32_t lattice_nx;    /* lattice layout: nodes along x                */
     int32_t lattice_ny;    /* lattice layout: nodes along y                */
-    int32_t reserved;
+    int32_t lattice_tile;  /* lattice kernel tile configuration in use,
+                              PDMTS_LATTICE_TILE_AUTO until it is tuned    */
     double lattice_h;      /* lattice spacing (0 if not on a lattice)      */
     int64_t steps_done;    /* PD substeps advanced since creation          */
     int64_t device_bytes;  /* device memory held by this subdomain         */

@@ -173,6 +173,8 @@ extern "C" int pdmts_ctx_create(pdmts_ctx **ctx, int device, void *cuda_stream)
     if (!c)
         return fail(PDMTS_ERR_NOMEM, "pdmts_ctx_create: out of host memory");
     c->device = device;
+    if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || c->num_sms < 1)
+        c->num_sms = 1;
     c->user_stream = (cudaStream_t)cuda_stream;
     if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming) != cudaSuccess ||
@@ -830,6 +832,111 @@ int pdmts_pd::upload_weights_and_loads()
 // v, writes the following prediction over the old u[cur], and swaps, so that
 // cur again names the current time. With init, a is computed from u[cur] and
 // the first prediction u + dt v + dt^2/2 a is written to u[1 - cur]; no swap.
+// Arguments of the lattice kernel around the per-node arguments N.
+pdmts::Lat2DArgs pdmts_pd::lattice_args(const pdmts::F32NodeArgs &N, uint32_t *mask, bool link) const
+{
+    Lat2DArgs A{};
+    A.nx = lat_dims[0];
+    A.ny = lat_dims[1];
+    A.mask = mask;
+    A.alpha = f_alpha.p;
+    for (int r2 = 0; r2 < 10; ++r2) {
+        const double coef = r2 > 0 ? micromodulus_host(this, r2 * h * h) * h * h * V[0] : 0.0;
+        A.clin[r2] = (float)(coef * r2 / 2.0);
+        A.cpmb[r2] = (float)(coef * r2 * r2);
+    }
+    A.qthr = (float)(s0 * (2.0 + s0));
+    A.tile = lattice_tile >= 0 ? lattice_tile : 0;
+    A.num_sms = ctx->num_sms;
+    A.nd = N;
+    for (int w = 0; w < 2; ++w) {
+        A.win_lo[w] = link ? link_win_lo[w] : 0;
+        A.win_n[w] = link ? link_win_n[w] : 0;
+    }
+    return A;
+}
+
+// Lattice tile autotuner: times every tile configuration on scratch copies of
+// the FP32 state (the simulation state and counters are not touched) and keeps
+// the fastest. Runs once, before the first substep chain is captured.
+int pdmts_pd::tune_lattice(cudaStream_t s)
+{
+    if (lattice_tile >= 0 || layout != LAYOUT_LATTICE2D || precision == PDMTS_FP64)
+        return PDMTS_OK;
+    DevArr<float4> su[2], sv;
+    DevArr<float> sa;
+    DevArr<uint32_t> sm;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int best = 0;
+    float best_ms = 0.f;
+    int r = PDMTS_OK;
+    auto release_all = [&]() {
+        release(su[0]); release(su[1]); release(sv); release(sa); release(sm);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    };
+    if ((r = alloc(su[0], n)) != PDMTS_OK || (r = alloc(su[1], n)) != PDMTS_OK || (r = alloc(sv, n)) != PDMTS_OK ||
+        (r = alloc(sa, 2 * n)) != PDMTS_OK || (r = alloc(sm, n_mask_words)) != PDMTS_OK) {
+        release_all();
+        return r;
+    }
+    cudaError_t e = cudaMemcpyAsync(su[0].p, f_u4[cur].p, sizeof(float4) * n, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(sv.p, f_v4.p, sizeof(float4) * n, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(sa.p, f_a.p, sizeof(float) * 2 * n, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(sm.p, d_mask.p, sizeof(uint32_t) * n_mask_words, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaEventCreate(&e0);
+    if (e == cudaSuccess)
+        e = cudaEventCreate(&e1);
+    F32NodeArgs N{};
+    N.n = n;
+    N.inv_m = f_invm.p;
+    N.wb = f_wb.p;
+    N.g = has_g ? f_g.p : nullptr;
+    N.v4 = sv.p;
+    N.a = sa.p;
+    N.dt = (float)ctx->dt_pd;
+    N.hdt = (float)(0.5 * ctx->dt_pd);
+    N.hdt2 = (float)(0.5 * ctx->dt_pd * ctx->dt_pd);
+    N.breaking = breaking ? 1 : 0;
+    N.pmb = force_kind == PDMTS_FORCE_PMB;
+    N.broken = nullptr;
+    for (int t = 0; t < kLatTiles && e == cudaSuccess; ++t) {
+        Lat2DArgs A = lattice_args(N, sm.p, false);
+        A.tile = t;
+        int c = 0;
+        for (int k = 0; k < 12 && e == cudaSuccess; ++k) {
+            if (k == 2)
+                e = cudaEventRecord(e0, s);
+            A.nd.u4_in = su[c].p;
+            A.nd.u4_out = su[1 - c].p;
+            if (e == cudaSuccess)
+                e = launch_pd_step_lattice2d(A, false, s);
+            c = 1 - c;
+        }
+        if (e == cudaSuccess)
+            e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess)
+            e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess)
+            e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && (t == 0 || ms < best_ms)) {
+            best = t;
+            best_ms = ms;
+        }
+    }
+    release_all();
+    if (e != cudaSuccess)
+        return fail(PDMTS_ERR_CUDA, "lattice autotune: %s", cudaGetErrorString(e));
+    lattice_tile = best;
+    pd_invalidate_graphs(this);
+    return PDMTS_OK;
+}
+
 int pdmts_pd::step(bool init, double theta, cudaStream_t s, bool link)
 {
     const double dt = ctx->dt_pd;
@@ -884,21 +991,7 @@ int pdmts_pd::step(bool init, double theta, cudaStream_t s, bool link)
         N.pmb = force_kind == PDMTS_FORCE_PMB;
         N.broken = ctx->d_counter;
         if (layout == LAYOUT_LATTICE2D) {
-            Lat2DArgs A{};
-            A.nx = lat_dims[0];
-            A.ny = lat_dims[1];
-            A.mask = mask;
-            A.alpha = f_alpha.p;
-            for (int r2 = 0; r2 < 10; ++r2) {
-                A.coef[r2] = r2 > 0 ? (float)(micromodulus_host(this, r2 * h * h) * h * h * V[0]) : 0.f;
-                A.thr[r2] = (float)(s0 * (2.0 + s0) * r2);
-                A.rd[r2] = (float)std::sqrt((double)r2);
-            }
-            A.nd = N;
-            for (int w = 0; w < 2; ++w) {
-                A.win_lo[w] = link ? link_win_lo[w] : 0;
-                A.win_n[w] = link ? link_win_n[w] : 0;
-            }
+            Lat2DArgs A = lattice_args(N, mask, link);
             e = launch_pd_step_lattice2d(A, init, s);
         } else {
             F32StepArgs A{};
@@ -1309,6 +1402,19 @@ extern "C" int pd_set_force_law(pdmts_pd *pd, int kind)
     return PDMTS_OK;
 }
 
+extern "C" int pd_set_lattice_tile(pdmts_pd *pd, int tile)
+{
+    clear_error();
+    if (!pd)
+        return fail(PDMTS_ERR_ARG, "pd_set_lattice_tile: pd is NULL");
+    if (tile != PDMTS_LATTICE_TILE_AUTO && (tile < 0 || tile >= kLatTiles))
+        return fail(PDMTS_ERR_ARG, "pd_set_lattice_tile: tile %d outside [0, %d) and not AUTO", tile, kLatTiles);
+    static_assert(kLatTiles == PDMTS_LATTICE_TILES, "tile table and ABI disagree");
+    pd->lattice_tile = tile;
+    pd_invalidate_graphs(pd);
+    return PDMTS_OK;
+}
+
 extern "C" int pd_info(const pdmts_pd *pd, pdmts_pd_info *info)
 {
     clear_error();
@@ -1324,7 +1430,7 @@ extern "C" int pd_info(const pdmts_pd *pd, pdmts_pd_info *info)
     info->layout = pd->layout;
     info->lattice_nx = pd->lat_dims[0];
     info->lattice_ny = pd->lat_dims[1];
-    info->reserved = 0;
+    info->lattice_tile = pd->lattice_tile;
     info->lattice_h = pd->on_lattice ? pd->h : 0.0;
     info->steps_done = pd->steps_done;
     info->device_bytes = pd->device_bytes;
@@ -1509,6 +1615,7 @@ extern "C" int mts_advance(pdmts_ctx *ctx, int64_t n_coarse)
     PDMTS_TRY(ctx->begin());
     pdmts_pd *pd = ctx->pd;
     cudaStream_t s = ctx->stream;
+    PDMTS_TRY(pd->tune_lattice(s));
     PDMTS_TRY(pd->ensure_init(s));
     const int64_t nsteps = n_coarse * ctx->m_ratio;
     // one coarse step of m substeps is one captured chain (m = 1: chains of 16)

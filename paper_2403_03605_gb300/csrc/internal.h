@@ -133,15 +133,17 @@ __host__ __device__ constexpr int DY(int k)
 
 // Lattice kernel: nodes form a full nx * ny rectangle numbered i = x + nx y;
 // the bond word mask[i] has bit k set while the bond to (x + DX[k], y + DY[k])
-// exists and is intact. coef / thr are indexed by |d|^2 (0..9).
+// exists and is intact. Coefficients are indexed by |d|^2 (0..9).
 struct Lat2DArgs {
     int nx, ny;
     uint32_t *mask;
     const float *alpha;         // n (null when no weights)
-    float coef[10];             // c(|xi|) h^2 V by |d|^2
-    float thr[10];              // s0 (2 + s0) |d|^2
-    float rd[10];               // |d|
-    int win_lo[2], win_n[2];    // optional tile-row windows (win_n[0] == 0: whole lattice)
+    float clin[10];             // linear law: c(|xi|) h^2 V |d|^2 / 2
+    float cpmb[10];             // PMB: c(|xi|) h^2 V |d|^4
+    float qthr;                 // s0 (2 + s0)
+    int tile;                   // tile configuration, 0 .. kLatTiles - 1
+    int num_sms;                // SMs of the device (persistent grids)
+    int win_lo[2], win_n[2];    // optional windows in units of TY node rows (win_n[0] == 0: whole lattice)
     F32NodeArgs nd;
 };
 
@@ -150,6 +152,19 @@ struct Lat2DArgs {
 cudaError_t launch_pd_step_f64(int dim, const F64StepArgs &A, bool init, cudaStream_t s);
 cudaError_t launch_pd_step_f32(int dim, const F32StepArgs &A, bool init, cudaStream_t s);
 cudaError_t launch_pd_step_lattice2d(const Lat2DArgs &A, bool init, cudaStream_t s);
+// Lattice tile configurations: strip height KR (nodes per thread, CTA tile
+// 32 x 8 KR), the resident CTAs per SM the registers are limited for, and
+// whether the persistent pipelined kernel (asynchronous staging of the next
+// tiles) is used.
+struct LatTile {
+    int kr, min_blocks, pipelined;
+};
+constexpr int kLatTiles = 4;
+constexpr LatTile kLatTile[kLatTiles] = {{2, 3, 0}, {2, 4, 0}, {2, 2, 1}, {1, 4, 1}};
+cudaError_t launch_lattice2d_t0(const Lat2DArgs &A, bool init, cudaStream_t s);
+cudaError_t launch_lattice2d_t1(const Lat2DArgs &A, bool init, cudaStream_t s);
+cudaError_t launch_lattice2d_t2(const Lat2DArgs &A, bool init, cudaStream_t s);
+cudaError_t launch_lattice2d_t3(const Lat2DArgs &A, bool init, cudaStream_t s);
 // Damage of the lattice layout (uniform volume): 1 - popc(intact) / popc(exists).
 cudaError_t launch_damage_lattice(int64_t n, const uint32_t *mask, const uint32_t *exists, int words,
                                   double *phi, cudaStream_t s);
@@ -210,6 +225,7 @@ cudaError_t launch_count_changed(int64_t nwords, const uint32_t *a, const uint32
 // --------------------------------------------------------------- handles ---
 struct pdmts_ctx {
     int device = 0;
+    int num_sms = 1;                                       // SMs of the device
     cudaStream_t user_stream = nullptr;  // caller's stream (may be legacy default)
     cudaStream_t stream = nullptr;       // library's own non-blocking stream
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;

@@ -1460,6 +1460,7 @@ static int coarse_step(pdmts_arl *A)
                                        cudaMemcpyDeviceToDevice, s));
     }
     PDMTS_TRY(fe_prepare_keff(fe, dtf, beta));
+    PDMTS_TRY(pd->tune_lattice(s));
     PDMTS_TRY(pd->ensure_init(s));
     if (!A->H_valid)
         PDMTS_TRY(build_H(A, m));

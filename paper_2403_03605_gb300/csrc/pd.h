@@ -83,7 +83,8 @@ struct pdmts_pd {
     DevArr<float> lk_af, lk_gf;
     DevArr<uint32_t> d_mask_link;
     int lk_cur = 0;
-    int link_win_lo[2] = {0, 0}, link_win_n[2] = {0, 0};  // tile rows the link problem can reach
+    int link_win_lo[2] = {0, 0}, link_win_n[2] = {0, 0};  // TY-row units the link problem can reach
+    int lattice_tile = -1;                                // lattice tile configuration (-1: tune)
     int64_t link_bonds = -1;  // directed bonds evaluated per link substep (-1: all)
     // interface force density of the free problem (G_PD^T lambda_0 / V): FP64 d_g or FP32 f_g
     bool has_g = false;
@@ -109,6 +110,8 @@ struct pdmts_pd {
 
     int upload_weights_and_loads();  // (re)build mass, wb, g device arrays
     int step(bool init, double theta, cudaStream_t s, bool link = false);  // one substep
+    pdmts::Lat2DArgs lattice_args(const pdmts::F32NodeArgs &N, uint32_t *mask, bool link) const;
+    int tune_lattice(cudaStream_t s);        // pick the lattice tile configuration (once)
     int alloc_link_state();                  // link-problem arrays (MTS coupling)
     int zero_link_state(cudaStream_t s);     // W_0 = 0 before a link run
     int ensure_init(cudaStream_t s);

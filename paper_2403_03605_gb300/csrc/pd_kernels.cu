@@ -25,8 +25,7 @@
 //    neighbour index and a stencil id whose offset, micromodulus and
 //    threshold sit in shared memory. No FP64 instruction in the bond loop.
 #include <algorithm>
-
-#include "pd.h"
+#include "f32_device.cuh"
 
 namespace pdmts {
 
@@ -147,99 +146,6 @@ __global__ void __launch_bounds__(256) k_pd_step_f64(const F64StepArgs A, const 
     }
 }
 
-// ------------------------------------------------------------- FP32 bulk --
-// Compensated addition (hi, lo) += x: Knuth's two-sum followed by a
-// renormalisation. Explicit round-to-nearest intrinsics keep the compiler
-// from fusing the caller's product into the first sum, which would break the
-// error term.
-__device__ __forceinline__ void df_add(float &hi, float &lo, float x)
-{
-    const float s = __fadd_rn(hi, x);
-    const float bp = __fsub_rn(s, hi);
-    float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
-    e = __fadd_rn(e, lo);
-    const float h2 = __fadd_rn(s, e);
-    lo = __fsub_rn(e, __fsub_rn(h2, s));
-    hi = h2;
-}
-
-template <int DIM>
-__device__ __forceinline__ void load_pair(const float4 *p4, const float2 *p2, int64_t i, float (&h)[DIM],
-                                          float (&l)[DIM])
-{
-    const float4 q = p4[i];
-    if constexpr (DIM == 2) {
-        h[0] = q.x; h[1] = q.y; l[0] = q.z; l[1] = q.w;
-    } else {
-        const float2 r = p2[i];
-        h[0] = q.x; h[1] = q.y; h[2] = q.z; l[0] = q.w; l[1] = r.x; l[2] = r.y;
-    }
-}
-
-template <int DIM>
-__device__ __forceinline__ void store_pair(float4 *p4, float2 *p2, int64_t i, const float (&h)[DIM],
-                                           const float (&l)[DIM])
-{
-    if constexpr (DIM == 2) {
-        p4[i] = make_float4(h[0], h[1], l[0], l[1]);
-    } else {
-        p4[i] = make_float4(h[0], h[1], h[2], l[0]);
-        p2[i] = make_float2(l[1], l[2]);
-    }
-}
-
-// Per-node part of an FP32-bulk substep: a = (f + wb + theta g) / m,
-// v += dt/2 (a_old + a), next prediction u + dt v + dt^2/2 a (lattice units).
-template <int DIM>
-__device__ __forceinline__ void finish_node_f32(const F32NodeArgs &N, const int64_t i, const float (&f)[DIM],
-                                                float (&uh)[DIM], float (&ul)[DIM], const int init)
-{
-    const int64_t n = N.n;
-    const float im = N.inv_m[i];
-    float an[DIM], ao[DIM];
-    if constexpr (DIM == 2) {
-        const float2 q = reinterpret_cast<const float2 *>(N.a)[i];
-        ao[0] = q.x; ao[1] = q.y;
-    } else {
-        const float4 q = reinterpret_cast<const float4 *>(N.a)[i];
-        ao[0] = q.x; ao[1] = q.y; ao[2] = q.z;
-    }
-#pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-        float t = f[d];
-        if (N.wb)
-            t = __fadd_rn(t, N.wb[d * n + i]);
-        if (N.g)
-            t = __fmaf_rn(N.theta, N.g[d * n + i], t);
-        an[d] = __fmul_rn(t, im);
-    }
-    float vh[DIM], vl[DIM];
-    load_pair<DIM>(N.v4, N.v2, i, vh, vl);
-    if (!init) {
-#pragma unroll
-        for (int d = 0; d < DIM; ++d)
-            df_add(vh[d], vl[d], __fmul_rn(N.hdt, __fadd_rn(ao[d], an[d])));
-        store_pair<DIM>(N.v4, N.v2, i, vh, vl);
-    }
-    if constexpr (DIM == 2)
-        reinterpret_cast<float2 *>(N.a)[i] = make_float2(an[0], an[1]);
-    else
-        reinterpret_cast<float4 *>(N.a)[i] = make_float4(an[0], an[1], an[2], 0.f);
-#pragma unroll
-    for (int d = 0; d < DIM; ++d)
-        df_add(uh[d], ul[d], __fmaf_rn(N.dt, vh[d], __fmaf_rn(N.dt, vl[d], __fmul_rn(N.hdt2, an[d]))));
-    store_pair<DIM>(N.u4_out, N.u2_out, i, uh, ul);
-}
-
-__device__ __forceinline__ void count_broken(unsigned long long *counter, unsigned nbroken)
-{
-    if (counter) {
-        const unsigned tot = __reduce_add_sync(0xffffffffu, nbroken);
-        if ((threadIdx.x & 31) == 0 && tot)
-            atomicAdd(counter, (unsigned long long)tot);
-    }
-}
-
 // One bond of the FP32 path, in lattice units (offset d, relative
 // displacement eta = u_j - u_i). Written once for both FP32 kernels with
 // explicit round-to-nearest intrinsics, so the two produce identical bits:
@@ -276,12 +182,6 @@ __device__ __forceinline__ void bond_2d(const float4 uj, const Bond2 &B, const f
         const float sc = w != 0.f ? __fdiv_rn(__fmul_rn(__fmul_rn(w, r2), lhs), den) : 0.f;
         f = __ffma2_rn(make_float2(sc, sc), __fadd2_rn(make_float2(d0, d1), eta), f);
     }
-}
-
-// Weight of bond (i, j) in the Arlequin overlap: 1 - (alpha_i + alpha_j) / 2.
-__device__ __forceinline__ float bond_weight(const float ai, const float aj)
-{
-    return __fmaf_rn(-0.5f, __fadd_rn(ai, aj), 1.f);
 }
 
 template <int DIM>
@@ -405,162 +305,6 @@ __global__ void __launch_bounds__(256) k_pd_step_f32(const F32StepArgs A, const 
     if (!valid)
         return;
     finish_node_f32<DIM>(N, i, f, uh, ul, init);
-}
-
-// ---------------------------------------------------------- 2D lattice ----
-// A CTA owns a 32 x 8 node tile of the nx * ny lattice. Its displacement halo
-// (38 x 14 nodes, 8.5 KB) is loaded once into shared memory; every bond then
-// reads its neighbour from shared memory at a compile-time offset. The family
-// is implicit (offset k of the 28-offset stencil), so per bond only one bit of
-// the node's bond word is read from HBM.
-namespace lat2d {
-constexpr int HX = TX + 2 * R, HY = TY + 2 * R;
-}
-
-// Bond slot k of a lattice node: the same branch-free expression as bond_2d
-// with compile-time offset, |d|^2 and |d|.
-template <int K, bool PMB>
-__device__ __forceinline__ void lattice_bond(const float4 uj, const Bond2 &B, const float coef, const float thr,
-                                             bool &new_break, float2 &f)
-{
-    constexpr int dx = lat2d::DX(K), dy = lat2d::DY(K), r2 = dx * dx + dy * dy;
-    const float2 eh = __fadd2_rn(make_float2(uj.x, uj.y), B.nuh);
-    const float2 el = __fadd2_rn(make_float2(uj.z, uj.w), B.nul);
-    const float2 eta = __fadd2_rn(eh, el);
-    const float dot = __fmaf_rn((float)dy, eta.y, __fmul_rn((float)dx, eta.x));
-    const float e2 = __fmaf_rn(eta.y, eta.y, __fmul_rn(eta.x, eta.x));
-    const float lhs = __fmaf_rn(2.f, dot, e2);
-    new_break |= lhs >= thr;
-    if constexpr (!PMB) {
-        const float sc = __fmul_rn(coef, dot);
-        f = __ffma2_rn(make_float2(sc, sc), make_float2((float)dx, (float)dy), f);
-    } else {
-        constexpr float rd = (r2 == 1 ? 1.f : r2 == 2 ? 1.41421354f : r2 == 4 ? 2.f : r2 == 5 ? 2.23606801f
-                              : r2 == 8 ? 2.82842708f : 3.f);
-        const float ry = __fsqrt_rn(__fadd_rn((float)r2, fmaxf(lhs, -(float)r2)));
-        const float den = __fmul_rn(__fadd_rn(ry, rd), ry);
-        const float sc = __fdiv_rn(__fmul_rn(__fmul_rn(coef, (float)r2), lhs), den);
-        f = __ffma2_rn(make_float2(sc, sc), __fadd2_rn(make_float2((float)dx, (float)dy), eta), f);
-    }
-}
-
-template <int K, bool HAS_ALPHA, bool PMB>
-struct LatticeSlots {
-    // all 28 slots unconditionally (warp fast path: every bond intact)
-    __device__ static __forceinline__ void all(const float4 (*su)[lat2d::HX], const int ty, const int tx,
-                                               const Lat2DArgs &A, const Bond2 &B, const float ai,
-                                               const float (*sal)[lat2d::HX], bool &nb, float2 &f)
-    {
-        using namespace lat2d;
-        constexpr int dx = DX(K), dy = DY(K), r2 = dx * dx + dy * dy;
-        float coef = A.coef[r2];
-        if constexpr (HAS_ALPHA)
-            coef = __fmul_rn(coef, bond_weight(ai, sal[ty + R + dy][tx + R + dx]));
-        lattice_bond<K, PMB>(su[ty + R + dy][tx + R + dx], B, coef, A.thr[r2], nb, f);
-        LatticeSlots<K + 1, HAS_ALPHA, PMB>::all(su, ty, tx, A, B, ai, sal, nb, f);
-    }
-    // slot by slot with the bond bits: exact breaking, absent bonds skipped
-    __device__ static __forceinline__ void masked(const float4 (*su)[lat2d::HX], const int ty, const int tx,
-                                                  const Lat2DArgs &A, const Bond2 &B, const float ai,
-                                                  const float (*sal)[lat2d::HX], const uint32_t m0,
-                                                  const int breaking, uint32_t &m, float2 &f)
-    {
-        using namespace lat2d;
-        constexpr int dx = DX(K), dy = DY(K), r2 = dx * dx + dy * dy;
-        if (m0 & (1u << K)) {
-            float coef = A.coef[r2];
-            if constexpr (HAS_ALPHA)
-                coef = __fmul_rn(coef, bond_weight(ai, sal[ty + R + dy][tx + R + dx]));
-            bool brk = false;
-            float2 g = f;
-            lattice_bond<K, PMB>(su[ty + R + dy][tx + R + dx], B, coef, A.thr[r2], brk, g);
-            if (breaking && brk)
-                m &= ~(1u << K);
-            else
-                f = g;
-        }
-        LatticeSlots<K + 1, HAS_ALPHA, PMB>::masked(su, ty, tx, A, B, ai, sal, m0, breaking, m, f);
-    }
-};
-
-template <bool HAS_ALPHA, bool PMB>
-struct LatticeSlots<lat2d::NS, HAS_ALPHA, PMB> {
-    __device__ static __forceinline__ void all(const float4 (*)[lat2d::HX], int, int, const Lat2DArgs &,
-                                               const Bond2 &, float, const float (*)[lat2d::HX], bool &, float2 &)
-    {
-    }
-    __device__ static __forceinline__ void masked(const float4 (*)[lat2d::HX], int, int, const Lat2DArgs &,
-                                                  const Bond2 &, float, const float (*)[lat2d::HX], uint32_t,
-                                                  int, uint32_t &, float2 &)
-    {
-    }
-};
-
-// Bond word of a node with all 28 bonds present and intact.
-constexpr uint32_t kFullWord = (1u << lat2d::NS) - 1u;
-
-template <bool HAS_ALPHA, bool PMB>
-__global__ void __launch_bounds__(256) k_pd_step_lattice2d(const Lat2DArgs A, const int init)
-{
-    using namespace lat2d;
-    __shared__ float4 su[HY][HX];
-    __shared__ float salpha[HAS_ALPHA ? HY : 1][HX];
-    const F32NodeArgs &N = A.nd;
-    const int nx = A.nx, ny = A.ny;
-    // tile row: all tile rows, or the rows of up to two windows [win_lo, win_lo + win_n)
-    const int trow = A.win_n[0] > 0
-                         ? ((int)blockIdx.y < A.win_n[0] ? A.win_lo[0] + (int)blockIdx.y
-                                                          : A.win_lo[1] + (int)blockIdx.y - A.win_n[0])
-                         : (int)blockIdx.y;
-    const int x0 = blockIdx.x * TX, y0 = trow * TY;
-    for (int q = threadIdx.x; q < HX * HY; q += blockDim.x) {
-        const int hy = q / HX, hx = q - hy * HX;
-        const int gx = x0 + hx - R, gy = y0 + hy - R;
-        const bool in = gx >= 0 && gx < nx && gy >= 0 && gy < ny;
-        const int64_t gi = (int64_t)gy * nx + gx;
-        su[hy][hx] = in ? N.u4_in[gi] : make_float4(0.f, 0.f, 0.f, 0.f);
-        if constexpr (HAS_ALPHA)
-            salpha[hy][hx] = in ? A.alpha[gi] : 0.f;
-    }
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const int x = x0 + tx, y = y0 + ty;
-    const bool valid = x < nx && y < ny;
-    const int64_t i = (int64_t)y * nx + x;
-    const uint32_t m0 = valid ? A.mask[i] : 0u;
-    __syncthreads();
-
-    const float4 ui = su[ty + R][tx + R];
-    const float ai = HAS_ALPHA ? salpha[ty + R][tx + R] : 0.f;
-    Bond2 B;
-    B.nuh = make_float2(-ui.x, -ui.y);
-    B.nul = make_float2(-ui.z, -ui.w);
-    float2 f2 = make_float2(0.f, 0.f);
-    uint32_t m = m0;
-    // Fast path: every node of the warp has all bonds intact; evaluate all
-    // slots without per-bond control flow and only note whether some bond
-    // reached the critical stretch. If one did (rare), redo the warp exactly.
-    bool fast = __all_sync(0xffffffffu, m0 == kFullWord || !valid);
-    if (fast) {
-        bool nb = false;
-        LatticeSlots<0, HAS_ALPHA, PMB>::all(su, ty, tx, A, B, ai, salpha, nb, f2);
-        if (N.breaking && __any_sync(0xffffffffu, nb))
-            fast = false;
-    }
-    if (!fast) {
-        f2 = make_float2(0.f, 0.f);
-        LatticeSlots<0, HAS_ALPHA, PMB>::masked(su, ty, tx, A, B, ai, salpha, m0, N.breaking, m, f2);
-    }
-    unsigned nbroken = 0;
-    if (m != m0) {
-        A.mask[i] = m;
-        nbroken = __popc(m0 ^ m);
-    }
-    count_broken(N.broken, nbroken);
-    if (!valid)
-        return;
-    const float f[2] = {f2.x, f2.y};
-    float uh[2] = {ui.x, ui.y}, ul[2] = {ui.z, ui.w};
-    finish_node_f32<2>(N, i, f, uh, ul, init);
 }
 
 // ----------------------------------------------------------- damage (Eq. 5)
@@ -827,22 +571,13 @@ cudaError_t launch_pd_step_lattice2d(const Lat2DArgs &A, bool init, cudaStream_t
 {
     if (A.nx <= 0 || A.ny <= 0)
         return cudaSuccess;
-    const unsigned rows = A.win_n[0] > 0 ? (unsigned)(A.win_n[0] + A.win_n[1])
-                                         : (unsigned)((A.ny + lat2d::TY - 1) / lat2d::TY);
-    const dim3 grid((unsigned)((A.nx + lat2d::TX - 1) / lat2d::TX), rows);
-    const int it = init ? 1 : 0;
-    if (A.alpha) {
-        if (A.nd.pmb)
-            k_pd_step_lattice2d<true, true><<<grid, 256, 0, s>>>(A, it);
-        else
-            k_pd_step_lattice2d<true, false><<<grid, 256, 0, s>>>(A, it);
-    } else {
-        if (A.nd.pmb)
-            k_pd_step_lattice2d<false, true><<<grid, 256, 0, s>>>(A, it);
-        else
-            k_pd_step_lattice2d<false, false><<<grid, 256, 0, s>>>(A, it);
+    switch (A.tile) {
+    case 0: return launch_lattice2d_t0(A, init, s);
+    case 1: return launch_lattice2d_t1(A, init, s);
+    case 2: return launch_lattice2d_t2(A, init, s);
+    case 3: return launch_lattice2d_t3(A, init, s);
+    default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 cudaError_t launch_damage_lattice(int64_t n, const uint32_t *mask, const uint32_t *exists, int words, double *phi,

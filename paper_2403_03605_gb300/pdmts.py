@@ -25,6 +25,7 @@ PDMTS_FP64, PDMTS_FP32_BULK, PDMTS_FP32_BULK_SELL = 0, 1, 2
 PDMTS_MICRO_POWER, PDMTS_MICRO_EXP = 0, 1
 PDMTS_FORCE_LINEAR, PDMTS_FORCE_PMB = 0, 1
 PDMTS_WEIGHT_CONSTANT, PDMTS_WEIGHT_LINEAR, PDMTS_WEIGHT_CUBIC = 0, 1, 2
+PDMTS_LATTICE_TILES, PDMTS_LATTICE_TILE_AUTO = 4, -1
 
 
 class PdmtsError(RuntimeError):
@@ -37,7 +38,7 @@ class PDInfo(C.Structure):
     _fields_ = [("dim", C.c_int32), ("precision", C.c_int32), ("n", C.c_int64), ("n_bonds", C.c_int64),
                 ("n_slots", C.c_int64), ("max_degree", C.c_int32), ("on_lattice", C.c_int32),
                 ("layout", C.c_int32), ("lattice_nx", C.c_int32), ("lattice_ny", C.c_int32),
-                ("reserved", C.c_int32), ("lattice_h", C.c_double), ("steps_done", C.c_int64), ("device_bytes", C.c_int64)]
+                ("lattice_tile", C.c_int32), ("lattice_h", C.c_double), ("steps_done", C.c_int64), ("device_bytes", C.c_int64)]
 
 
 class Stats(C.Structure):
@@ -67,6 +68,7 @@ SIGNATURES = [
     ("pd_set_weights", _I, [_V, _V]),
     ("pd_set_breaking", _I, [_V, _I]),
     ("pd_set_force_law", _I, [_V, _I]),
+    ("pd_set_lattice_tile", _I, [_V, _I]),
     ("pd_info", _I, [_V, C.POINTER(PDInfo)]),
     ("pd_read_displacement", _I, [_V, _V]),
     ("pd_read_velocity", _I, [_V, _V]),
@@ -254,6 +256,10 @@ def pd_set_breaking(pd, enabled):
 
 def pd_set_force_law(pd, kind):
     _check(load().pd_set_force_law(pd, int(kind)), "pd_set_force_law")
+
+
+def pd_set_lattice_tile(pd, tile):
+    _check(load().pd_set_lattice_tile(pd, int(tile)), "pd_set_lattice_tile")
 
 
 def pd_info(pd):

@@ -96,3 +96,22 @@ def test_config1_full_size_properties(fresh, prec):
     info = P.arlequin_info(g.arl)
     print("config1 coupling:", info)
     assert info["n_lambda"] == 2 * 606
+
+
+def test_coupled_lattice_tiles_bit_identical(fresh):
+    """Coupled FP32-bulk steps on the 100 x 40 mm plate with every lattice tile
+    configuration (the link substeps run on windows of tile rows converted per
+    tile height): identical PD, FE and multiplier states."""
+    cp = W.config1()
+    ref = None
+    for tile in range(P.PDMTS_LATTICE_TILES):
+        g = GpuMTS(fresh(), cp, P.PDMTS_FP32_BULK)
+        P.pd_set_lattice_tile(g.pd, tile)
+        g.run(4)
+        assert P.pd_info(g.pd)["lattice_tile"] == tile
+        got = (g.u(), g.v(), g.uf(), g.lam(), g.mu())
+        if ref is None:
+            ref = got
+            continue
+        for a, b in zip(got, ref):
+            assert np.array_equal(a, b)

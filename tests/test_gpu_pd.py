@@ -132,23 +132,52 @@ LATTICE_CASES = [
 ]
 
 
-@pytest.mark.parametrize("case", LATTICE_CASES, ids=[c["name"] for c in LATTICE_CASES])
-def test_fp32_lattice_kernel_equals_sliced_ell_kernel(fresh, case):
-    """The 2D lattice kernel (bond words + shared-memory halo) and the sliced-ELL
-    kernel evaluate the same expressions in the same order: identical results."""
+def _lattice_pair(fresh, case):
     pb = case["pb"]()
     rng = np.random.default_rng(21)
     alpha = rng.uniform(0.0, 0.7, pb.n) if case.get("alpha") else None
     force = P.PDMTS_FORCE_PMB if case.get("force") else P.PDMTS_FORCE_LINEAR
     u0 = rng.standard_normal((2, pb.n)) * pb.s0 * pb.lat.dx * 0.2
+    return pb, alpha, force, u0
+
+
+@pytest.mark.parametrize("case", LATTICE_CASES, ids=[c["name"] for c in LATTICE_CASES])
+def test_fp32_lattice_kernel_agrees_with_sliced_ell_kernel(fresh, case):
+    """The 2D lattice kernel (bond words, shared-memory halo, strips of nodes per
+    thread) and the sliced-ELL kernel evaluate the same bond law, the lattice
+    kernel in its scaled form (q = lhs / |d|^2) and in stencil-column order:
+    they agree to FP32 rounding, with the FP32 bar on the broken set."""
+    pb, alpha, force, u0 = _lattice_pair(fresh, case)
     gl = GpuRun(fresh(), pb, P.PDMTS_FP32_BULK, alpha=alpha, force=force, u0=u0)
     gs = GpuRun(fresh(), pb, P.PDMTS_FP32_BULK_SELL, alpha=alpha, force=force, u0=u0)
     assert P.pd_info(gl.pd)["layout"] == 1 and P.pd_info(gs.pd)["layout"] == 0
     gl.run(case["steps"])
     gs.run(case["steps"])
-    assert np.array_equal(gl.u(), gs.u()) and np.array_equal(gl.v(), gs.v())
-    assert np.array_equal(gl.mu(), gs.mu())
-    np.testing.assert_allclose(gl.damage(), gs.damage(), rtol=0, atol=1e-15)
+    eu, ev = rel_l2(gl.u(), gs.u()), rel_l2(gl.v(), gs.v())
+    mm = _mismatch(gl.mu(), gs.mu())
+    print(f"lattice vs sliced-ELL {case['name']}: rel-L2 u {eu:.2e} v {ev:.2e}, broken mismatch {mm:.2e}")
+    assert eu <= FP32_TOL and ev <= FP32_TOL, (eu, ev)
+    assert mm <= FP32_MISMATCH, mm
+
+
+@pytest.mark.parametrize("case", LATTICE_CASES, ids=[c["name"] for c in LATTICE_CASES])
+def test_lattice_tile_configurations_bit_identical(fresh, case):
+    """Every tile configuration of the lattice kernel (strip height, CTAs per SM)
+    gives each node its bonds in the same order, and a warp that falls back to
+    the bond-by-bond path without a break reproduces the fast path: identical
+    bits, and the autotuner's choice cannot change results."""
+    pb, alpha, force, u0 = _lattice_pair(fresh, case)
+    runs = []
+    for tile in [*range(P.PDMTS_LATTICE_TILES), P.PDMTS_LATTICE_TILE_AUTO]:
+        g = GpuRun(fresh(), pb, P.PDMTS_FP32_BULK, alpha=alpha, force=force, u0=u0)
+        P.pd_set_lattice_tile(g.pd, tile)
+        g.run(case["steps"])
+        got = P.pd_info(g.pd)["lattice_tile"]
+        assert got == tile if tile >= 0 else 0 <= got < P.PDMTS_LATTICE_TILES
+        runs.append((g.u(), g.v(), g.mu()))
+    for u, v, mu in runs[1:]:
+        assert np.array_equal(u, runs[0][0]) and np.array_equal(v, runs[0][1])
+        assert np.array_equal(mu, runs[0][2])
 
 
 def _mismatch(mu_a, mu_b):
