@@ -249,6 +249,7 @@ def run_ours(args, rank, world, local_rank):
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, stops)]
     total_ms = float(sum(step_ms))
     chain_ms, chain_sub = P.pdmts_get_timing(ctx)
+    phases, nph = P.mts_get_phase_timing(ctx) if coupled else ({}, 0)
     st1 = P.pdmts_get_stats(ctx)
     launches = st1["kernel_launches"] - st0["kernel_launches"]
     substeps = st1["pd_substeps"] - st0["pd_substeps"]
@@ -321,6 +322,7 @@ def run_ours(args, rank, world, local_rank):
                "l2": "flushed between timed steps (256 MB write)"}
         if coupled:
             ai = P.arlequin_info(arl)
+            cfg.update({"phase_us_per_step": {k: round(v * 1e3 / max(nph, 1), 1) for k, v in phases.items()}})
             cfg.update({"fe_dofs": ai["fe_dofs"], "n_lambda": ai["n_lambda"],
                         "pd_substeps_per_step": substeps // args.steps, "setup_s": round(t_setup, 2),
                         "interface_builds": ai["rebuilds"]})

@@ -217,6 +217,14 @@ int mts_advance(pdmts_ctx *ctx, int64_t n_coarse);
  * and the number of substeps inside those chains, and resets both. */
 int pdmts_set_timing(pdmts_ctx *ctx, int enabled);
 int pdmts_get_timing(pdmts_ctx *ctx, double *substep_ms, int64_t *substeps);
+/* Phase times of the coupled coarse steps run while timing was enabled,
+ * summed in milliseconds since the last call (blocks): phase_ms[0] PD free
+ * substeps with the FE free step alongside, up to their join; [1] interface
+ * problem (constraint residual and lambda_m, Eq. 49); [2] PD link run (Eq.
+ * 48b) with the FE correction alongside; [3] PD correction and the rebuild
+ * flag, up to the end of the FE correction; [4] whole steps. n_steps receives
+ * the number of steps timed. phase_ms holds 5 doubles. */
+int mts_get_phase_timing(pdmts_ctx *ctx, double *phase_ms, int64_t *n_steps);
 
 /* ---- CCM subdomain and Arlequin coupling (Sec. 2.2-2.5, Eq. 33-49, Alg. 1) -- */
 

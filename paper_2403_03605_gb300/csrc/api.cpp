@@ -93,30 +93,41 @@ int pdmts_ctx::end()
     return PDMTS_OK;
 }
 
-int pdmts_ctx::time_begin(cudaEvent_t *start)
+int pdmts_ctx::pool_event(cudaEvent_t *e)
 {
-    *start = nullptr;
-    if (!timing)
-        return PDMTS_OK;
-    if (ev_pool.size() < 2) {
+    if (ev_pool.empty()) {
         for (int k = 0; k < 64; ++k) {
-            cudaEvent_t e;
-            PDMTS_CUDA_TRY(cudaEventCreate(&e));
-            ev_pool.push_back(e);
+            cudaEvent_t ev;
+            PDMTS_CUDA_TRY(cudaEventCreate(&ev));
+            ev_pool.push_back(ev);
         }
     }
-    *start = ev_pool.back();
+    *e = ev_pool.back();
     ev_pool.pop_back();
-    PDMTS_CUDA_TRY(cudaEventRecord(*start, stream));
     return PDMTS_OK;
+}
+
+int pdmts_ctx::mark(cudaEvent_t *e)
+{
+    *e = nullptr;
+    if (!timing)
+        return PDMTS_OK;
+    PDMTS_TRY(pool_event(e));
+    PDMTS_CUDA_TRY(cudaEventRecord(*e, stream));
+    return PDMTS_OK;
+}
+
+int pdmts_ctx::time_begin(cudaEvent_t *start)
+{
+    return mark(start);
 }
 
 int pdmts_ctx::time_end(cudaEvent_t start, int64_t substeps)
 {
     if (!start)
         return PDMTS_OK;
-    cudaEvent_t stop = ev_pool.back();
-    ev_pool.pop_back();
+    cudaEvent_t stop = nullptr;
+    PDMTS_TRY(pool_event(&stop));
     PDMTS_CUDA_TRY(cudaEventRecord(stop, stream));
     ev_marks.push_back({start, stop});
     ev_counts.push_back(substeps);
@@ -153,6 +164,31 @@ extern "C" int pdmts_get_timing(pdmts_ctx *ctx, double *substep_ms, int64_t *sub
     ctx->ev_counts.clear();
     *substep_ms = ms;
     *substeps = cnt;
+    return PDMTS_OK;
+}
+
+extern "C" int mts_get_phase_timing(pdmts_ctx *ctx, double *phase_ms, int64_t *n_steps)
+{
+    clear_error();
+    if (!ctx || !phase_ms || !n_steps)
+        return fail(PDMTS_ERR_ARG, "mts_get_phase_timing: NULL argument");
+    PDMTS_CUDA_TRY(cudaSetDevice(ctx->device));
+    PDMTS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    for (int k = 0; k < 5; ++k)
+        phase_ms[k] = 0.0;
+    for (auto &m : ctx->phase_marks) {
+        float t = 0.f;
+        for (int k = 0; k < 4; ++k) {
+            PDMTS_CUDA_TRY(cudaEventElapsedTime(&t, m[(size_t)k], m[(size_t)k + 1]));
+            phase_ms[k] += t;
+        }
+        PDMTS_CUDA_TRY(cudaEventElapsedTime(&t, m[0], m[4]));
+        phase_ms[4] += t;
+        for (cudaEvent_t e : m)
+            ctx->ev_pool.push_back(e);
+    }
+    *n_steps = (int64_t)ctx->phase_marks.size();
+    ctx->phase_marks.clear();
     return PDMTS_OK;
 }
 
@@ -346,28 +382,41 @@ int pdmts_pd::alloc_link_state()
     }
     has_link = true;
     has_g = true;
+    link_seg_lo[0] = link_seg_lo[1] = 0;
+    link_seg_n[0] = n;
+    link_seg_n[1] = 0;
+    PDMTS_TRY(zero_link_state(s, true));
     pd_invalidate_graphs(this);
     return PDMTS_OK;
 }
 
-int pdmts_pd::zero_link_state(cudaStream_t s)
+int pdmts_pd::zero_link_state(cudaStream_t s, bool all)
 {
-    const int64_t m = (int64_t)dim * n;
-    if (precision == PDMTS_FP64) {
-        for (int b = 0; b < 2; ++b)
-            PDMTS_CUDA_TRY(cudaMemsetAsync(lk_u[b].p, 0, sizeof(double) * m, s));
-        PDMTS_CUDA_TRY(cudaMemsetAsync(lk_v.p, 0, sizeof(double) * m, s));
-        PDMTS_CUDA_TRY(cudaMemsetAsync(lk_a.p, 0, sizeof(double) * m, s));
-    } else {
-        for (int b = 0; b < 2; ++b) {
-            PDMTS_CUDA_TRY(cudaMemsetAsync(lk_u4[b].p, 0, sizeof(float4) * n, s));
+    // only the node ranges a link run writes (the link state is zero
+    // elsewhere), or everything
+    for (int w = 0; w < 2; ++w) {
+        const int64_t lo = all ? 0 : link_seg_lo[w], cnt = all ? (w == 0 ? n : 0) : link_seg_n[w];
+        if (cnt <= 0)
+            continue;
+        if (precision == PDMTS_FP64) {
+            for (int d = 0; d < dim; ++d) {
+                for (int b = 0; b < 2; ++b)
+                    PDMTS_CUDA_TRY(cudaMemsetAsync(lk_u[b].p + (int64_t)d * n + lo, 0, sizeof(double) * cnt, s));
+                PDMTS_CUDA_TRY(cudaMemsetAsync(lk_v.p + (int64_t)d * n + lo, 0, sizeof(double) * cnt, s));
+                PDMTS_CUDA_TRY(cudaMemsetAsync(lk_a.p + (int64_t)d * n + lo, 0, sizeof(double) * cnt, s));
+            }
+        } else {
+            for (int b = 0; b < 2; ++b) {
+                PDMTS_CUDA_TRY(cudaMemsetAsync(lk_u4[b].p + lo, 0, sizeof(float4) * cnt, s));
+                if (dim == 3)
+                    PDMTS_CUDA_TRY(cudaMemsetAsync(lk_u2[b].p + lo, 0, sizeof(float2) * cnt, s));
+            }
+            PDMTS_CUDA_TRY(cudaMemsetAsync(lk_v4.p + lo, 0, sizeof(float4) * cnt, s));
             if (dim == 3)
-                PDMTS_CUDA_TRY(cudaMemsetAsync(lk_u2[b].p, 0, sizeof(float2) * n, s));
+                PDMTS_CUDA_TRY(cudaMemsetAsync(lk_v2.p + lo, 0, sizeof(float2) * cnt, s));
+            const int per = dim == 2 ? 2 : 4;
+            PDMTS_CUDA_TRY(cudaMemsetAsync(lk_af.p + (int64_t)per * lo, 0, sizeof(float) * per * cnt, s));
         }
-        PDMTS_CUDA_TRY(cudaMemsetAsync(lk_v4.p, 0, sizeof(float4) * n, s));
-        if (dim == 3)
-            PDMTS_CUDA_TRY(cudaMemsetAsync(lk_v2.p, 0, sizeof(float2) * n, s));
-        PDMTS_CUDA_TRY(cudaMemsetAsync(lk_af.p, 0, sizeof(float) * (dim == 2 ? 2 : 4) * n, s));
     }
     lk_cur = 0;  // W_0 = 0: current and predicted displacement both zero, a_0 = 0
     return PDMTS_OK;

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <array>
 #include <cstdint>
 #include <cstdio>
 #include <string>
@@ -196,12 +197,13 @@ cudaError_t launch_constraint(int dim, int64_t nl, const int64_t *gpd_ptr, const
                               const double *gpd_val, int64_t npd, const double *v64, const float4 *v4,
                               const float2 *v2, double h, const int32_t *gfe_col, const double *gfe_val, int gfe_w,
                               int64_t nfe, const double *vfe, double sign_pd, double sign_fe, double *y,
-                              cudaStream_t s);
+                              cudaStream_t s, float *y32 = nullptr);
 // U_PD += W (u, v, a of the link state), then the prediction for the next
 // substep u + dt v + dt^2/2 a.
 struct PDAddLink {
     int dim;
     int64_t n;
+    int64_t seg_lo[2], seg_n[2];  // node ranges to correct (the link state is zero elsewhere)
     double dt, hdt2;
     // FP64
     double *u, *u_pred, *v, *a;
@@ -249,6 +251,11 @@ struct pdmts_ctx {
     std::vector<int64_t> ev_counts;
     int time_begin(cudaEvent_t *start);                    // record a start mark (if timing)
     int time_end(cudaEvent_t start, int64_t substeps);     // record the matching stop mark
+    // coupled coarse steps while timing: start, free phase joined, lambda
+    // solved, link run done, end
+    std::vector<std::array<cudaEvent_t, 5>> phase_marks;
+    int pool_event(cudaEvent_t *e);                        // an event from the pool
+    int mark(cudaEvent_t *e);                              // record one on `stream` if timing
 
     void *dalloc(size_t bytes);
     void dfree(void *p);

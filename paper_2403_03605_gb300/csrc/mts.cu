@@ -18,6 +18,7 @@
 // Conventions follow Eq. 33: FE carries +G_FE^T lambda, PD -G_PD^T lambda and
 // the constraint is G_FE v_FE - G_PD v_PD = 0. All coupling arithmetic is FP64.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -102,7 +103,7 @@ struct pdmts_fem {
     std::vector<double> kval;         // ndof * W, stiffness K
     std::vector<double> mass;         // ndof, lumped mass
     std::vector<double> load;         // ndof, loads P
-    double gersh = 0;                 // Gershgorin bound of M^-1 K
+    double gersh = 0;                 // upper bound on the spectrum of M^-1 K
     // device; the ELL arrays are stored transposed (entry e of row i at
     // e * ndof + i) so that a warp's 32 rows read consecutive words
     DevArr<int32_t> d_col;
@@ -200,6 +201,10 @@ struct pdmts_arl {
     DevArr<int64_t> d_gfeT_ptr;
     DevArr<double> d_gfe_val, d_gpd_val, d_ov_N, d_gfeT_val, d_Hfe, d_Hneg_inv, d_colbuf, d_lam0, d_lam, d_y,
         d_unit;
+    // FP32-bulk subdomains: (-H)^-1 rounded to FP32, rows padded to a pitch
+    // that is a multiple of 4 (zeros beyond nlam), for the per-step product
+    DevArr<float> d_Hinv32, d_y32;   // and the constraint residual rounded to FP32
+    int64_t pitch32 = 0;
     DevArr<double> d_B[4];          // block Chebyshev work (x, r, d0, d1)
     DevArr<int64_t> d_gpd_ptr;
     DevArr<uint8_t> d_near;         // bond words of nodes within (m + 1) delta of a band
@@ -237,7 +242,7 @@ struct pdmts_arl {
     {
         release(d_gfe_col); release(d_gpd_col); release(d_ov_node); release(d_ov_k); release(d_owner);
         release(d_gfeT_k); release(d_gfeT_ptr); release(d_gfeT_val); release(d_Hfe);
-        release(d_gfe_val); release(d_gpd_val); release(d_ov_N); release(d_Hneg_inv);
+        release(d_gfe_val); release(d_gpd_val); release(d_ov_N); release(d_Hneg_inv); release(d_Hinv32); release(d_y32);
         release(d_colbuf); release(d_lam0); release(d_lam); release(d_y); release(d_unit);
         for (auto &b : d_B)
             release(b);
@@ -474,6 +479,48 @@ __global__ void k_gemv_rows(const int64_t n, const double *__restrict__ A, const
         y[row] = scale * s;
 }
 
+// y = A x for a row-major n x n FP32 matrix with row pitch `pitch` (a
+// multiple of 4; A and x are zero beyond column n), in FP32 (four running
+// sums per lane, combined across the warp in FP64): the FP32-bulk path's
+// interface product, which FP64 arithmetic would bound on this GPU. One warp
+// per row, 16-byte loads.
+__global__ void k_gemv_rows_f32(const int64_t n, const int64_t pitch, const float *__restrict__ A,
+                                const float *__restrict__ x, double *__restrict__ y)
+{
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= n)
+        return;
+    const float4 *a4 = reinterpret_cast<const float4 *>(A + row * pitch);
+    const float4 *x4 = reinterpret_cast<const float4 *>(x);
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+    const int m = (int)(pitch / 4);
+#pragma unroll 4
+    for (int j = lane; j < m; j += 32) {
+        const float4 a = a4[j], b = x4[j];
+        s0 = __fmaf_rn(a.x, b.x, s0);
+        s1 = __fmaf_rn(a.y, b.y, s1);
+        s2 = __fmaf_rn(a.z, b.z, s2);
+        s3 = __fmaf_rn(a.w, b.w, s3);
+    }
+    double t = ((double)s0 + (double)s1) + ((double)s2 + (double)s3);
+    for (int o = 16; o > 0; o >>= 1)
+        t += __shfl_down_sync(0xffffffffu, t, o);
+    if (lane == 0)
+        y[row] = t;
+}
+
+// dst (n rows of `pitch` floats) = src (n x n doubles) rounded, zero padded.
+__global__ void k_to_f32_pitched(const int64_t n, const int64_t pitch, const double *__restrict__ src,
+                                 float *__restrict__ dst)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * pitch)
+        return;
+    const int64_t r = t / pitch, c = t - r * pitch;
+    dst[t] = c < n ? (float)src[r * n + c] : 0.f;
+}
+
 static inline unsigned blocks(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
 // ------------------------------------------------------- FE assembly ------
@@ -540,14 +587,63 @@ static void q4_element(const pdmts_fem *fe, const std::vector<BandDesc> &bands, 
         }
 }
 
+// Largest eigenvalue of the symmetric 8 x 8 matrix a (cyclic Jacobi rotations;
+// a is overwritten).
+static double sym8_max_eig(double a[8][8])
+{
+    for (int sweep = 0; sweep < 64; ++sweep) {
+        double off = 0.0, diag = 0.0;
+        for (int i = 0; i < 8; ++i) {
+            diag += a[i][i] * a[i][i];
+            for (int j = i + 1; j < 8; ++j)
+                off += a[i][j] * a[i][j];
+        }
+        if (off <= 1e-30 * diag)
+            break;
+        for (int p = 0; p < 8; ++p)
+            for (int q = p + 1; q < 8; ++q) {
+                if (a[p][q] == 0.0)
+                    continue;
+                const double th = 0.5 * (a[q][q] - a[p][p]) / a[p][q];
+                const double t = (th >= 0 ? 1.0 : -1.0) / (std::fabs(th) + std::sqrt(th * th + 1.0));
+                const double c = 1.0 / std::sqrt(t * t + 1.0), sn = t * c;
+                for (int k = 0; k < 8; ++k) {  // columns p, q
+                    const double akp = a[k][p], akq = a[k][q];
+                    a[k][p] = c * akp - sn * akq;
+                    a[k][q] = sn * akp + c * akq;
+                }
+                for (int k = 0; k < 8; ++k) {  // rows p, q
+                    const double apk = a[p][k], aqk = a[q][k];
+                    a[p][k] = c * apk - sn * aqk;
+                    a[q][k] = sn * apk + c * aqk;
+                }
+            }
+    }
+    double mx = a[0][0];
+    for (int i = 1; i < 8; ++i)
+        mx = std::max(mx, a[i][i]);
+    return mx;
+}
+
 static int fe_assemble(pdmts_fem *fe, const std::vector<BandDesc> &bands, int kind)
 {
     const int64_t n = fe->n, ndof = fe->ndof();
     std::vector<std::map<int32_t, double>> rows((size_t)ndof);
     fe->mass.assign((size_t)ndof, 0.0);
+    // element bound on the spectrum of M^-1 K: with K = sum K_e and the lumped
+    // M = sum M_e, x'Kx / x'Mx <= max_e of the largest eigenvalue of
+    // M_e^-1/2 K_e M_e^-1/2 (every term is a ratio of non-negative sums)
+    double elem_bound = 0.0;
     for (int64_t e = 0; e < fe->ne; ++e) {
         double ke[8][8], me[4];
         q4_element(fe, bands, kind, e, ke, me);
+        if (me[0] > 0 && me[1] > 0 && me[2] > 0 && me[3] > 0) {
+            double sk[8][8];
+            for (int a = 0; a < 8; ++a)
+                for (int b = 0; b < 8; ++b)
+                    sk[a][b] = ke[a][b] / std::sqrt(me[a / 2] * me[b / 2]);
+            elem_bound = std::max(elem_bound, sym8_max_eig(sk));
+        }
         int64_t dof[8];
         for (int a = 0; a < 4; ++a) {
             const int64_t node = fe->conn[(size_t)e * 4 + a];
@@ -582,7 +678,9 @@ static int fe_assemble(pdmts_fem *fe, const std::vector<BandDesc> &bands, int ki
             fe->col[(size_t)i * fe->W + e] = (int32_t)i;
         gersh = std::max(gersh, rs / fe->mass[(size_t)i]);
     }
-    fe->gersh = gersh;
+    // both are upper bounds; the element bound is the tighter on Q4 meshes
+    // (a relative margin covers the rounding of the rotations)
+    fe->gersh = elem_bound > 0 ? std::min(gersh, elem_bound * (1.0 + 1e-9)) : gersh;
     // consistent traction loads, weighted by alpha at the face midpoint (Eq. 34)
     fe->load.assign((size_t)ndof, 0.0);
     const int64_t nf = (int64_t)fe->faces.size() / 2;
@@ -1043,9 +1141,12 @@ static int build_constraint(pdmts_arl *A)
     PDMTS_TRY(h2d(A->d_ov_node.p, A->ov_node, s));
     PDMTS_TRY(h2d(A->d_ov_k.p, A->ov_k, s));
     PDMTS_TRY(h2d(A->d_ov_N.p, A->ov_N, s));
+    A->pitch32 = (A->nlam + 3) / 4 * 4;
+    PDMTS_TRY(A->alloc(A->d_y32, A->pitch32));
+    PDMTS_CUDA_TRY(cudaMemsetAsync(A->d_y32.p, 0, sizeof(float) * A->pitch32, s));
     for (DevArr<double> *a : {&A->d_lam0, &A->d_lam, &A->d_y, &A->d_unit, &A->d_colbuf}) {
-        PDMTS_TRY(A->alloc(*a, A->nlam));
-        PDMTS_CUDA_TRY(cudaMemsetAsync(a->p, 0, sizeof(double) * A->nlam, s));
+        PDMTS_TRY(A->alloc(*a, A->pitch32));  // zero padding up to the FP32 pitch
+        PDMTS_CUDA_TRY(cudaMemsetAsync(a->p, 0, sizeof(double) * A->pitch32, s));
     }
     PDMTS_TRY(A->alloc(A->d_owner, A->nlam));
     PDMTS_TRY(A->alloc(A->d_Hneg_inv, A->nlam * A->nlam));
@@ -1123,6 +1224,34 @@ static int update_near_flags(pdmts_arl *A, int m)
             pd->link_bonds = bonds;
         }
     }
+    // node ranges a link run may write: the windows widened to 32 rows
+    pd->link_seg_lo[0] = pd->link_seg_lo[1] = 0;
+    pd->link_seg_n[0] = pd->n;
+    pd->link_seg_n[1] = 0;
+    if (pd->link_win_n[0] > 0) {
+        const int64_t nx = pd->lat_dims[0], ny = pd->lat_dims[1];
+        int64_t lo[2] = {0, 0}, hi[2] = {0, 0};
+        int nw = 0;
+        for (int w = 0; w < 2; ++w) {
+            if (pd->link_win_n[w] <= 0)
+                continue;
+            const int64_t r0 = (int64_t)pd->link_win_lo[w] * lat2d::TY / 32 * 32;
+            const int64_t r1 = std::min<int64_t>(ny, ((int64_t)(pd->link_win_lo[w] + pd->link_win_n[w]) * lat2d::TY + 31) / 32 * 32);
+            if (nw > 0 && r0 <= hi[nw - 1]) {
+                hi[nw - 1] = std::max(hi[nw - 1], r1);
+            } else {
+                lo[nw] = r0;
+                hi[nw] = r1;
+                ++nw;
+            }
+        }
+        for (int w = 0; w < 2; ++w) {
+            pd->link_seg_lo[w] = w < nw ? lo[w] * nx : 0;
+            pd->link_seg_n[w] = w < nw ? (hi[w] - lo[w]) * nx : 0;
+        }
+    }
+    // the previous windows may have left link state outside the new ones
+    PDMTS_TRY(pd->zero_link_state(A->ctx->stream, true));
     PDMTS_CUDA_TRY(cudaStreamSynchronize(A->ctx->stream));
     return PDMTS_OK;
 }
@@ -1303,6 +1432,11 @@ static int build_H(pdmts_arl *A, int m)
         k_gj_update<<<blocks(n2), 256, 0, s>>>(nlam, H, p, A->d_colbuf.p);
         launches += 3;
     }
+    if (!f64) {
+        PDMTS_TRY(A->alloc(A->d_Hinv32, nlam * A->pitch32));
+        k_to_f32_pitched<<<blocks(nlam * A->pitch32), 256, 0, s>>>(nlam, A->pitch32, H, A->d_Hinv32.p);
+        ++launches;
+    }
     PDMTS_CUDA_TRY(cudaGetLastError());
     PDMTS_CUDA_TRY(cudaStreamSynchronize(s));
     ctx->stats.kernel_launches += launches;
@@ -1466,6 +1600,8 @@ static int coarse_step(pdmts_arl *A)
         PDMTS_TRY(build_H(A, m));
     // The FE free step may start once the previous step has ended; the PD
     // chain is enqueued first so that it starts without waiting for the host.
+    std::array<cudaEvent_t, 5> ph{};
+    PDMTS_TRY(ctx->mark(&ph[0]));
     PDMTS_CUDA_TRY(cudaEventRecord(A->ev_fork, s));
     // ---- PD free substeps with (1 - j/m) lambda_0 (Eq. 48a) ----
     cudaError_t e = launch_interface_force(pd->dim, pd->n, A->n_ov, A->d_ov_node.p, A->d_ov_k.p, A->d_ov_N.p, 4,
@@ -1480,15 +1616,21 @@ static int coarse_step(pdmts_arl *A)
     PDMTS_TRY(fe_free_step(fe, dtf, beta, gamma, A->fe_stream, &launches));
     PDMTS_CUDA_TRY(cudaEventRecord(A->ev_join, A->fe_stream));
     PDMTS_CUDA_TRY(cudaStreamWaitEvent(s, A->ev_join, 0));
+    PDMTS_TRY(ctx->mark(&ph[1]));
     // ---- interface problem (Eq. 49): lambda_m = (-H)^-1 (G_FE v_FE - G_PD v_PD) ----
     const float4 *v4 = f64 ? nullptr : pd->f_v4.p;
     const float2 *v2 = f64 ? nullptr : pd->f_v2.p;
     e = launch_constraint(2, A->nl, A->d_gpd_ptr.p, A->d_gpd_col.p, A->d_gpd_val.p, pd->n, f64 ? pd->d_v.p : nullptr,
                           v4, v2, pd->h, A->d_gfe_col.p, A->d_gfe_val.p, A->gfe_w, fe->n, fe->d_v.p, -1.0, 1.0,
-                          A->d_y.p, s);
+                          A->d_y.p, s, f64 ? nullptr : A->d_y32.p);
     if (e != cudaSuccess)
         return fail(PDMTS_ERR_CUDA, "interface residual: %s", cudaGetErrorString(e));
-    k_gemv_rows<<<blocks(A->nlam * 32), 256, 0, s>>>(A->nlam, A->d_Hneg_inv.p, A->d_y.p, 1.0, A->d_lam.p);
+    if (f64)
+        k_gemv_rows<<<blocks(A->nlam * 32), 256, 0, s>>>(A->nlam, A->d_Hneg_inv.p, A->d_y.p, 1.0, A->d_lam.p);
+    else
+        k_gemv_rows_f32<<<blocks(A->nlam * 32), 256, 0, s>>>(A->nlam, A->pitch32, A->d_Hinv32.p, A->d_y32.p,
+                                                            A->d_lam.p);
+    PDMTS_TRY(ctx->mark(&ph[2]));
     // ---- corrections U = V + Y lambda_m: FE on its stream, PD link run here ----
     PDMTS_CUDA_TRY(cudaEventRecord(A->ev_fork, s));
     PDMTS_CUDA_TRY(cudaStreamWaitEvent(A->fe_stream, A->ev_fork, 0));
@@ -1496,9 +1638,14 @@ static int coarse_step(pdmts_arl *A)
     PDMTS_CUDA_TRY(cudaEventRecord(A->ev_join, A->fe_stream));
     launches += 2;
     PDMTS_TRY(pd_link_run(A, A->d_lam.p, m, s));
+    PDMTS_TRY(ctx->mark(&ph[3]));
     PDAddLink L{};
     L.dim = pd->dim;
     L.n = pd->n;
+    for (int w = 0; w < 2; ++w) {
+        L.seg_lo[w] = pd->link_seg_lo[w];
+        L.seg_n[w] = pd->link_seg_n[w];
+    }
     L.dt = ctx->dt_pd;
     L.hdt2 = 0.5 * ctx->dt_pd * ctx->dt_pd;
     if (f64) {
@@ -1539,6 +1686,9 @@ static int coarse_step(pdmts_arl *A)
     PDMTS_CUDA_TRY(cudaMemcpyAsync(A->d_lam0.p, A->d_lam.p, sizeof(double) * A->nlam, cudaMemcpyDeviceToDevice, s));
     // the step ends when the FE correction has also finished
     PDMTS_CUDA_TRY(cudaStreamWaitEvent(s, A->ev_join, 0));
+    PDMTS_TRY(ctx->mark(&ph[4]));
+    if (ph[0])
+        ctx->phase_marks.push_back(ph);
     launches += 3;
     ctx->stats.kernel_launches += launches;
     ctx->stats.coarse_steps += 1;

@@ -84,6 +84,9 @@ struct pdmts_pd {
     DevArr<uint32_t> d_mask_link;
     int lk_cur = 0;
     int link_win_lo[2] = {0, 0}, link_win_n[2] = {0, 0};  // TY-row units the link problem can reach
+    // node ranges holding every node a link run may write (the windows widened
+    // to 32 rows, a multiple of every lattice tile height); {0, n} without windows
+    int64_t link_seg_lo[2] = {0, 0}, link_seg_n[2] = {0, 0};
     int lattice_tile = -1;                                // lattice tile configuration (-1: tune)
     int64_t link_bonds = -1;  // directed bonds evaluated per link substep (-1: all)
     // interface force density of the free problem (G_PD^T lambda_0 / V): FP64 d_g or FP32 f_g
@@ -113,6 +116,6 @@ struct pdmts_pd {
     pdmts::Lat2DArgs lattice_args(const pdmts::F32NodeArgs &N, uint32_t *mask, bool link) const;
     int tune_lattice(cudaStream_t s);        // pick the lattice tile configuration (once)
     int alloc_link_state();                  // link-problem arrays (MTS coupling)
-    int zero_link_state(cudaStream_t s);     // W_0 = 0 before a link run
+    int zero_link_state(cudaStream_t s, bool all = false);  // W_0 = 0 before a link run
     int ensure_init(cudaStream_t s);
 };

@@ -428,47 +428,60 @@ __global__ void k_constraint(const int dim, const int64_t nl, const int64_t *__r
                              const float2 *__restrict__ v2, const double h, const int32_t *__restrict__ gfe_col,
                              const double *__restrict__ gfe_val, const int gfe_w, const int64_t nfe,
                              const double *__restrict__ vfe, const double sign_pd, const double sign_fe,
-                             double *__restrict__ y)
+                             double *__restrict__ y, float *__restrict__ y32)
 {
-    // one warp per constraint row (multiplier node k, component c)
-    const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    // one warp per multiplier node k, all components (rows c nl + k): the PD
+    // velocities of the node's support are gathered once for every component
+    const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (r >= (int64_t)dim * nl)
+    if (k >= nl)
         return;
-    const int c = (int)(r / nl);
-    const int64_t k = r - (int64_t)c * nl;
-    double sp = 0.0;
-    for (int64_t e = gpd_ptr[k] + lane; e < gpd_ptr[k + 1]; e += 32) {
+    double sp[3] = {0.0, 0.0, 0.0};
+    const int64_t e1 = gpd_ptr[k + 1];
+#pragma unroll 4
+    for (int64_t e = gpd_ptr[k] + lane; e < e1; e += 32) {
         const int64_t p = gpd_col[e];
-        double vp;
+        const double g = gpd_val[e];
+        double vp[3];
         if (v64) {
-            vp = v64[(int64_t)c * npd + p];
+            for (int c = 0; c < dim; ++c)
+                vp[c] = v64[(int64_t)c * npd + p];
         } else {
             const float4 q = v4[p];
-            if (dim == 2)
-                vp = c == 0 ? (double)q.x + (double)q.z : (double)q.y + (double)q.w;
-            else
-                vp = c == 0 ? (double)q.x + (double)q.w
-                            : (c == 1 ? (double)q.y + (double)v2[p].x : (double)q.z + (double)v2[p].y);
-            vp *= h;
+            if (dim == 2) {
+                vp[0] = ((double)q.x + (double)q.z) * h;
+                vp[1] = ((double)q.y + (double)q.w) * h;
+            } else {
+                const float2 q2 = v2[p];
+                vp[0] = ((double)q.x + (double)q.w) * h;
+                vp[1] = ((double)q.y + (double)q2.x) * h;
+                vp[2] = ((double)q.z + (double)q2.y) * h;
+            }
         }
-        sp += gpd_val[e] * vp;
+        for (int c = 0; c < dim; ++c)
+            sp[c] += g * vp[c];
     }
-    double sf = 0.0;
-    if (gfe_col && lane < gfe_w)
-        sf = gfe_val[k * gfe_w + lane] * vfe[(int64_t)c * nfe + gfe_col[k * gfe_w + lane]];
-    double t = sign_pd * sp + sign_fe * sf;
-    for (int o = 16; o > 0; o >>= 1)
-        t += __shfl_down_sync(0xffffffffu, t, o);
-    if (lane == 0)
-        y[r] = t;
+    for (int c = 0; c < dim; ++c) {
+        double sf = 0.0;
+        if (gfe_col && lane < gfe_w)
+            sf = gfe_val[k * gfe_w + lane] * vfe[(int64_t)c * nfe + gfe_col[k * gfe_w + lane]];
+        double t = sign_pd * sp[c] + sign_fe * sf;
+        for (int o = 16; o > 0; o >>= 1)
+            t += __shfl_down_sync(0xffffffffu, t, o);
+        if (lane == 0) {
+            y[(int64_t)c * nl + k] = t;
+            if (y32)
+                y32[(int64_t)c * nl + k] = (float)t;
+        }
+    }
 }
 
 __global__ void k_pd_add_link(const PDAddLink A)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= A.n)
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= A.seg_n[0] + A.seg_n[1])
         return;
+    const int64_t i = t < A.seg_n[0] ? A.seg_lo[0] + t : A.seg_lo[1] + (t - A.seg_n[0]);
     const int64_t n = A.n;
     if (A.u) {
         for (int d = 0; d < A.dim; ++d) {
@@ -622,24 +635,25 @@ cudaError_t launch_constraint(int dim, int64_t nl, const int64_t *gpd_ptr, const
                               const double *gpd_val, int64_t npd, const double *v64, const float4 *v4,
                               const float2 *v2, double h, const int32_t *gfe_col, const double *gfe_val, int gfe_w,
                               int64_t nfe, const double *vfe, double sign_pd, double sign_fe, double *y,
-                              cudaStream_t s)
+                              cudaStream_t s, float *y32)
 {
     const int64_t rows = (int64_t)dim * nl;
     if (rows == 0)
         return cudaSuccess;
     if (gfe_w > 32)
         return cudaErrorInvalidValue;
-    k_constraint<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, s>>>(dim, nl, gpd_ptr, gpd_col, gpd_val, npd, v64, v4,
+    k_constraint<<<(unsigned)((nl * 32 + 255) / 256), 256, 0, s>>>(dim, nl, gpd_ptr, gpd_col, gpd_val, npd, v64, v4,
                                                                       v2, h, gfe_col, gfe_val, gfe_w, nfe, vfe,
-                                                                      sign_pd, sign_fe, y);
+                                                                      sign_pd, sign_fe, y, y32);
     return cudaGetLastError();
 }
 
 cudaError_t launch_pd_add_link(const PDAddLink &A, cudaStream_t s)
 {
-    if (A.n == 0)
+    const int64_t cnt = A.seg_n[0] + A.seg_n[1];
+    if (cnt == 0)
         return cudaSuccess;
-    k_pd_add_link<<<(unsigned)((A.n + 255) / 256), 256, 0, s>>>(A);
+    k_pd_add_link<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(A);
     return cudaGetLastError();
 }
 

@@ -93,6 +93,7 @@ SIGNATURES = [
     ("arlequin_info", _I, [_V, _V]),
     ("pdmts_set_timing", _I, [_V, _I]),
     ("pdmts_get_timing", _I, [_V, C.POINTER(_D), C.POINTER(_I64)]),
+    ("mts_get_phase_timing", _I, [_V, C.POINTER(_D), C.POINTER(_I64)]),
     ("pdmts_get_stats", _I, [_V, C.POINTER(Stats)]),
 ]
 
@@ -209,6 +210,17 @@ def pdmts_get_timing(ctx):
     ms, cnt = _D(), _I64()
     _check(load().pdmts_get_timing(ctx, C.byref(ms), C.byref(cnt)), "pdmts_get_timing")
     return ms.value, cnt.value
+
+
+MTS_PHASES = ("free", "interface", "link", "correction", "step")
+
+
+def mts_get_phase_timing(ctx):
+    """({phase: summed milliseconds}, coarse steps timed) since the last call."""
+    ms = (_D * 5)()
+    cnt = _I64()
+    _check(load().mts_get_phase_timing(ctx, ms, C.byref(cnt)), "mts_get_phase_timing")
+    return dict(zip(MTS_PHASES, list(ms))), cnt.value
 
 
 # ------------------------------------------------------------------------ PD
