@@ -197,7 +197,7 @@ cudaError_t launch_constraint(int dim, int64_t nl, const int64_t *gpd_ptr, const
                               const double *gpd_val, int64_t npd, const double *v64, const float4 *v4,
                               const float2 *v2, double h, const int32_t *gfe_col, const double *gfe_val, int gfe_w,
                               int64_t nfe, const double *vfe, double sign_pd, double sign_fe, double *y,
-                              cudaStream_t s, float *y32 = nullptr);
+                              cudaStream_t s);
 // U_PD += W (u, v, a of the link state), then the prediction for the next
 // substep u + dt v + dt^2/2 a.
 struct PDAddLink {

@@ -115,6 +115,7 @@ struct pdmts_fem {
     double keff_dt = -1, cheb_theta = 0, cheb_delta = 0;
     std::vector<double> cheb_c1, cheb_c2;
     int64_t keff_version = 0;
+    bool paired_rows = false;         // x and y rows of every node share one column list
     GraphSlot g_free, g_link;         // captured free step and link correction
     bool assembled = false;
     int64_t ndof() const { return (int64_t)dim * n; }
@@ -201,10 +202,6 @@ struct pdmts_arl {
     DevArr<int64_t> d_gfeT_ptr;
     DevArr<double> d_gfe_val, d_gpd_val, d_ov_N, d_gfeT_val, d_Hfe, d_Hneg_inv, d_colbuf, d_lam0, d_lam, d_y,
         d_unit;
-    // FP32-bulk subdomains: (-H)^-1 rounded to FP32, rows padded to a pitch
-    // that is a multiple of 4 (zeros beyond nlam), for the per-step product
-    DevArr<float> d_Hinv32, d_y32;   // and the constraint residual rounded to FP32
-    int64_t pitch32 = 0;
     DevArr<double> d_B[4];          // block Chebyshev work (x, r, d0, d1)
     DevArr<int64_t> d_gpd_ptr;
     DevArr<uint8_t> d_near;         // bond words of nodes within (m + 1) delta of a band
@@ -242,7 +239,7 @@ struct pdmts_arl {
     {
         release(d_gfe_col); release(d_gpd_col); release(d_ov_node); release(d_ov_k); release(d_owner);
         release(d_gfeT_k); release(d_gfeT_ptr); release(d_gfeT_val); release(d_Hfe);
-        release(d_gfe_val); release(d_gpd_val); release(d_ov_N); release(d_Hneg_inv); release(d_Hinv32); release(d_y32);
+        release(d_gfe_val); release(d_gpd_val); release(d_ov_N); release(d_Hneg_inv);
         release(d_colbuf); release(d_lam0); release(d_lam); release(d_y); release(d_unit);
         for (auto &b : d_B)
             release(b);
@@ -479,46 +476,37 @@ __global__ void k_gemv_rows(const int64_t n, const double *__restrict__ A, const
         y[row] = scale * s;
 }
 
-// y = A x for a row-major n x n FP32 matrix with row pitch `pitch` (a
-// multiple of 4; A and x are zero beyond column n), in FP32 (four running
-// sums per lane, combined across the warp in FP64): the FP32-bulk path's
-// interface product, which FP64 arithmetic would bound on this GPU. One warp
-// per row, 16-byte loads.
-__global__ void k_gemv_rows_f32(const int64_t n, const int64_t pitch, const float *__restrict__ A,
-                                const float *__restrict__ x, double *__restrict__ y)
-{
-    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (row >= n)
-        return;
-    const float4 *a4 = reinterpret_cast<const float4 *>(A + row * pitch);
-    const float4 *x4 = reinterpret_cast<const float4 *>(x);
-    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-    const int m = (int)(pitch / 4);
-#pragma unroll 4
-    for (int j = lane; j < m; j += 32) {
-        const float4 a = a4[j], b = x4[j];
-        s0 = __fmaf_rn(a.x, b.x, s0);
-        s1 = __fmaf_rn(a.y, b.y, s1);
-        s2 = __fmaf_rn(a.z, b.z, s2);
-        s3 = __fmaf_rn(a.w, b.w, s3);
-    }
-    double t = ((double)s0 + (double)s1) + ((double)s2 + (double)s3);
-    for (int o = 16; o > 0; o >>= 1)
-        t += __shfl_down_sync(0xffffffffu, t, o);
-    if (lane == 0)
-        y[row] = t;
-}
-
-// dst (n rows of `pitch` floats) = src (n x n doubles) rounded, zero padded.
-__global__ void k_to_f32_pitched(const int64_t n, const int64_t pitch, const double *__restrict__ src,
-                                 float *__restrict__ dst)
+// k_cheb_iter with one thread per FE node and right-hand side: the node's x
+// and y rows (dofs i and nfe + i) have the same column list, so every value of
+// d a row needs is read once for both rows. Per row the same operations in the
+// same order as k_cheb_iter.
+__global__ void k_cheb_iter_node(const int64_t nfe, const int nrhs, const int W, const int32_t *__restrict__ col,
+                                 const double *__restrict__ val, const double *__restrict__ Minv,
+                                 double *__restrict__ x, double *__restrict__ r, const double *__restrict__ d,
+                                 double *__restrict__ dn, const double c1, const double c2)
 {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n * pitch)
+    if (t >= nfe * nrhs)
         return;
-    const int64_t r = t / pitch, c = t - r * pitch;
-    dst[t] = c < n ? (float)src[r * n + c] : 0.f;
+    const int64_t ndof = 2 * nfe;
+    const int64_t c = t / nfe, ix = t - c * nfe, iy = nfe + ix;
+    const double *dc = d + c * ndof;
+    double adx = 0.0, ady = 0.0;
+    for (int e = 0; e < W; ++e) {
+        const double dv = dc[col[e * ndof + ix]];
+        adx += val[e * ndof + ix] * dv;
+        ady += val[e * ndof + iy] * dv;
+    }
+    const int64_t qx = c * ndof + ix, qy = c * ndof + iy;
+    x[qx] += d[qx];
+    x[qy] += d[qy];
+    const double rx = r[qx] - adx, ry = r[qy] - ady;
+    r[qx] = rx;
+    r[qy] = ry;
+    if (dn) {
+        dn[qx] = c1 * d[qx] + c2 * Minv[ix] * rx;
+        dn[qy] = c1 * d[qy] + c2 * Minv[iy] * ry;
+    }
 }
 
 static inline unsigned blocks(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
@@ -678,6 +666,13 @@ static int fe_assemble(pdmts_fem *fe, const std::vector<BandDesc> &bands, int ki
             fe->col[(size_t)i * fe->W + e] = (int32_t)i;
         gersh = std::max(gersh, rs / fe->mass[(size_t)i]);
     }
+    fe->paired_rows = true;
+    for (int64_t i = 0; i < n && fe->paired_rows; ++i)
+        for (int e = 0; e < fe->W; ++e)
+            if (fe->col[(size_t)i * fe->W + e] != fe->col[(size_t)(n + i) * fe->W + e]) {
+                fe->paired_rows = false;
+                break;
+            }
     // both are upper bounds; the element bound is the tighter on Q4 meshes
     // (a relative margin covers the rounding of the rotations)
     fe->gersh = elem_bound > 0 ? std::min(gersh, elem_bound * (1.0 + 1e-9)) : gersh;
@@ -727,8 +722,8 @@ static int fe_assemble(pdmts_fem *fe, const std::vector<BandDesc> &bands, int ki
 }
 
 // K_eff = M + beta dt^2 K and its Chebyshev schedule. The spectrum of
-// M^-1 K_eff lies in [1, 1 + beta dt^2 rho(M^-1 K)] with the Gershgorin bound
-// for rho; the iteration count gives a relative error below 1e-15.
+// M^-1 K_eff lies in [1, 1 + beta dt^2 rho(M^-1 K)] with an upper bound for
+// rho; the iteration count bounds the error by 1e-14 of the initial error.
 static int fe_prepare_keff(pdmts_fem *fe, double dt, double beta)
 {
     if (fe->keff_dt == dt)
@@ -753,7 +748,7 @@ static int fe_prepare_keff(pdmts_fem *fe, double dt, double beta)
     fe->cheb_delta = 0.5 * (lmax - lmin);
     const double kappa = lmax / lmin;
     const double q = (std::sqrt(kappa) - 1.0) / (std::sqrt(kappa) + 1.0);
-    int it = q > 0 ? (int)std::ceil(std::log(2.0 / 1e-16) / std::log(1.0 / q)) + 2 : 1;
+    int it = q > 0 ? (int)std::ceil(std::log(2.0 / 1e-14) / std::log(1.0 / q)) + 2 : 1;
     it = std::max(it, 1);
     fe->cheb_c1.assign((size_t)it, 0.0);
     fe->cheb_c2.assign((size_t)it, 0.0);
@@ -788,8 +783,14 @@ static int fe_cheb_solve(pdmts_fem *fe, int nrhs, double *x, const double *b, do
     const int it = (int)fe->cheb_c1.size();
     for (int k = 0; k < it; ++k) {
         const bool last = k == it - 1;
-        k_cheb_iter<<<blocks(tot), 256, 0, s>>>(ndof, nrhs, fe->W, fe->d_col.p, fe->d_Keff.p, fe->d_Minv.p, x, r, d,
-                                                last ? nullptr : dn, fe->cheb_c1[(size_t)k], fe->cheb_c2[(size_t)k]);
+        if (fe->paired_rows)
+            k_cheb_iter_node<<<blocks(fe->n * nrhs), 256, 0, s>>>(fe->n, nrhs, fe->W, fe->d_col.p, fe->d_Keff.p,
+                                                                  fe->d_Minv.p, x, r, d, last ? nullptr : dn,
+                                                                  fe->cheb_c1[(size_t)k], fe->cheb_c2[(size_t)k]);
+        else
+            k_cheb_iter<<<blocks(tot), 256, 0, s>>>(ndof, nrhs, fe->W, fe->d_col.p, fe->d_Keff.p, fe->d_Minv.p, x, r,
+                                                    d, last ? nullptr : dn, fe->cheb_c1[(size_t)k],
+                                                    fe->cheb_c2[(size_t)k]);
         ++*launches;
         std::swap(d, dn);
     }
@@ -1141,12 +1142,9 @@ static int build_constraint(pdmts_arl *A)
     PDMTS_TRY(h2d(A->d_ov_node.p, A->ov_node, s));
     PDMTS_TRY(h2d(A->d_ov_k.p, A->ov_k, s));
     PDMTS_TRY(h2d(A->d_ov_N.p, A->ov_N, s));
-    A->pitch32 = (A->nlam + 3) / 4 * 4;
-    PDMTS_TRY(A->alloc(A->d_y32, A->pitch32));
-    PDMTS_CUDA_TRY(cudaMemsetAsync(A->d_y32.p, 0, sizeof(float) * A->pitch32, s));
     for (DevArr<double> *a : {&A->d_lam0, &A->d_lam, &A->d_y, &A->d_unit, &A->d_colbuf}) {
-        PDMTS_TRY(A->alloc(*a, A->pitch32));  // zero padding up to the FP32 pitch
-        PDMTS_CUDA_TRY(cudaMemsetAsync(a->p, 0, sizeof(double) * A->pitch32, s));
+        PDMTS_TRY(A->alloc(*a, A->nlam));
+        PDMTS_CUDA_TRY(cudaMemsetAsync(a->p, 0, sizeof(double) * A->nlam, s));
     }
     PDMTS_TRY(A->alloc(A->d_owner, A->nlam));
     PDMTS_TRY(A->alloc(A->d_Hneg_inv, A->nlam * A->nlam));
@@ -1432,11 +1430,6 @@ static int build_H(pdmts_arl *A, int m)
         k_gj_update<<<blocks(n2), 256, 0, s>>>(nlam, H, p, A->d_colbuf.p);
         launches += 3;
     }
-    if (!f64) {
-        PDMTS_TRY(A->alloc(A->d_Hinv32, nlam * A->pitch32));
-        k_to_f32_pitched<<<blocks(nlam * A->pitch32), 256, 0, s>>>(nlam, A->pitch32, H, A->d_Hinv32.p);
-        ++launches;
-    }
     PDMTS_CUDA_TRY(cudaGetLastError());
     PDMTS_CUDA_TRY(cudaStreamSynchronize(s));
     ctx->stats.kernel_launches += launches;
@@ -1622,14 +1615,11 @@ static int coarse_step(pdmts_arl *A)
     const float2 *v2 = f64 ? nullptr : pd->f_v2.p;
     e = launch_constraint(2, A->nl, A->d_gpd_ptr.p, A->d_gpd_col.p, A->d_gpd_val.p, pd->n, f64 ? pd->d_v.p : nullptr,
                           v4, v2, pd->h, A->d_gfe_col.p, A->d_gfe_val.p, A->gfe_w, fe->n, fe->d_v.p, -1.0, 1.0,
-                          A->d_y.p, s, f64 ? nullptr : A->d_y32.p);
+                          A->d_y.p, s);
     if (e != cudaSuccess)
         return fail(PDMTS_ERR_CUDA, "interface residual: %s", cudaGetErrorString(e));
-    if (f64)
-        k_gemv_rows<<<blocks(A->nlam * 32), 256, 0, s>>>(A->nlam, A->d_Hneg_inv.p, A->d_y.p, 1.0, A->d_lam.p);
-    else
-        k_gemv_rows_f32<<<blocks(A->nlam * 32), 256, 0, s>>>(A->nlam, A->pitch32, A->d_Hinv32.p, A->d_y32.p,
-                                                            A->d_lam.p);
+    // the multiplier solve stays FP64 in every precision
+    k_gemv_rows<<<blocks(A->nlam * 32), 256, 0, s>>>(A->nlam, A->d_Hneg_inv.p, A->d_y.p, 1.0, A->d_lam.p);
     PDMTS_TRY(ctx->mark(&ph[2]));
     // ---- corrections U = V + Y lambda_m: FE on its stream, PD link run here ----
     PDMTS_CUDA_TRY(cudaEventRecord(A->ev_fork, s));

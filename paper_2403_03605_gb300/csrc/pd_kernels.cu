@@ -428,7 +428,7 @@ __global__ void k_constraint(const int dim, const int64_t nl, const int64_t *__r
                              const float2 *__restrict__ v2, const double h, const int32_t *__restrict__ gfe_col,
                              const double *__restrict__ gfe_val, const int gfe_w, const int64_t nfe,
                              const double *__restrict__ vfe, const double sign_pd, const double sign_fe,
-                             double *__restrict__ y, float *__restrict__ y32)
+                             double *__restrict__ y)
 {
     // one warp per multiplier node k, all components (rows c nl + k): the PD
     // velocities of the node's support are gathered once for every component
@@ -468,11 +468,8 @@ __global__ void k_constraint(const int dim, const int64_t nl, const int64_t *__r
         double t = sign_pd * sp[c] + sign_fe * sf;
         for (int o = 16; o > 0; o >>= 1)
             t += __shfl_down_sync(0xffffffffu, t, o);
-        if (lane == 0) {
+        if (lane == 0)
             y[(int64_t)c * nl + k] = t;
-            if (y32)
-                y32[(int64_t)c * nl + k] = (float)t;
-        }
     }
 }
 
@@ -635,7 +632,7 @@ cudaError_t launch_constraint(int dim, int64_t nl, const int64_t *gpd_ptr, const
                               const double *gpd_val, int64_t npd, const double *v64, const float4 *v4,
                               const float2 *v2, double h, const int32_t *gfe_col, const double *gfe_val, int gfe_w,
                               int64_t nfe, const double *vfe, double sign_pd, double sign_fe, double *y,
-                              cudaStream_t s, float *y32)
+                              cudaStream_t s)
 {
     const int64_t rows = (int64_t)dim * nl;
     if (rows == 0)
@@ -644,7 +641,7 @@ cudaError_t launch_constraint(int dim, int64_t nl, const int64_t *gpd_ptr, const
         return cudaErrorInvalidValue;
     k_constraint<<<(unsigned)((nl * 32 + 255) / 256), 256, 0, s>>>(dim, nl, gpd_ptr, gpd_col, gpd_val, npd, v64, v4,
                                                                       v2, h, gfe_col, gfe_val, gfe_w, nfe, vfe,
-                                                                      sign_pd, sign_fe, y, y32);
+                                                                      sign_pd, sign_fe, y);
     return cudaGetLastError();
 }
 
