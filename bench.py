@@ -190,6 +190,12 @@ def setup_ours(P, ctx, workload):
         P.mts_set_time(ctx, pb.dt, m)
         return pd, None, None, P.pd_info(pd), pb, m, None
     cp = W.config2()
+    pd, fe, arl = make_coupled(P, ctx, cp)
+    return pd, fe, arl, P.pd_info(pd), cp.pd, cp.m, cp
+
+
+def make_coupled(P, ctx, cp):
+    """Bind one coupled plate (FP32-bulk PD, Q4 FE, Arlequin bands) in ctx."""
     pb = cp.pd
     mat = pb.mat
     pd = P.pd_create(ctx, pb.lat.X, horizon=pb.delta, c=pb.c, s0=pb.s0, rho=mat.rho, vol_uniform=pb.vol,
@@ -199,7 +205,121 @@ def setup_ours(P, ctx, workload):
     P.fem_set_traction(fe, cp.faces, cp.face_traction)
     arl = P.arlequin_bind(ctx, pd, fe, cp.weight_kind, [b.as_array() for b in cp.bands])
     P.mts_set_time(ctx, cp.dt_pd, cp.m, cp.gamma_fe, cp.beta_fe)
-    return pd, fe, arl, P.pd_info(pd), pb, cp.m, cp
+    return pd, fe, arl
+
+
+BATCH_NAME = "batch_{n}_coupled_plates_seed3605_pd20k-400k_m5-10-20_fp32bulk"
+
+
+def run_batch(args, rank, world, local_rank):
+    """Batched workload: independent coupled plates of uneven size, crack, load
+    and m (seeded), advanced one round (one coarse step of each) at a time by
+    mts_batch_advance; the per-instance loop over the same rounds is timed
+    beside it."""
+    import torch
+    from paper_2403_03605_gb300 import build as B
+    from paper_2403_03605_gb300 import pdmts as P
+    from paper_2403_03605_gb300 import workloads as W
+
+    B.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    t_setup = time.perf_counter()
+    cps = W.config4(n=args.batch_members)
+    ctxs, handles = [], []
+    for cp in cps:
+        ctx = P.pdmts_ctx_create(local_rank, stream.cuda_stream)
+        ctxs.append(ctx)
+        handles.append(make_coupled(P, ctx, cp))
+    batch = P.mts_batch_create(ctxs)
+    flush = torch.empty(int(256e6) // 4, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        P.mts_batch_advance(batch, 1)
+    torch.cuda.synchronize(dev)
+    t_setup = time.perf_counter() - t_setup
+
+    def stats_sum():
+        sts = [P.pdmts_get_stats(c) for c in ctxs]
+        return {k: sum(st[k] for st in sts) for k in sts[0]}
+
+    def timed(advance):
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        stops = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        s0 = stats_sum()
+        torch.cuda.synchronize(dev)
+        for k in range(args.steps):
+            flush.zero_()
+            starts[k].record(stream)
+            advance()
+            stops[k].record(stream)
+        torch.cuda.synchronize(dev)
+        s1 = stats_sum()
+        ms = float(sum(a.elapsed_time(b) for a, b in zip(starts, stops)))
+        return ms, {k: s1[k] - s0[k] for k in s1}
+
+    i0 = P.mts_batch_info(batch)
+    with ClockSampler(local_rank) as clk:
+        time.sleep(0.3)
+        torch.cuda.nvtx.range_push("timed_steps")
+        batch_ms, d = timed(lambda: P.mts_batch_advance(batch, 1))
+        torch.cuda.nvtx.range_pop()
+    i1 = P.mts_batch_info(batch)
+    value = d["bond_updates"] / (batch_ms * 1e-3)
+    launches = (d["kernel_launches"] - d["pd_substeps"]) + (i1["batched_launches"] - i0["batched_launches"])
+    solo_ms, ds = timed(lambda: [P.mts_advance(c, 1) for c in ctxs])
+    solo_value = ds["bond_updates"] / (solo_ms * 1e-3)
+
+    # end to end: every round also reads every member's PD and FE displacement back to pinned host memory
+    outs = [(torch.empty((2, cp.pd.n), dtype=torch.float64).pin_memory(),
+             torch.empty(2 * cp.fe.n, dtype=torch.float64).pin_memory()) for cp in cps]
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    s0 = stats_sum()
+    e2e_rounds = max(3, min(args.steps, 10))
+    for _ in range(e2e_rounds):
+        P.mts_batch_advance(batch, 1)
+        for (pd, fe, arl), (u, uf) in zip(handles, outs):
+            P.pd_read_displacement(pd, u.numpy())
+            P.fem_read_displacement(fe, uf.shape[0], uf.numpy())
+    torch.cuda.synchronize(dev)
+    e2e_s = time.perf_counter() - t0
+    e2e_value = (stats_sum()["bond_updates"] - s0["bond_updates"]) / e2e_s
+    d2h = sum(u.numel() * 8 + uf.numel() * 8 for u, uf in outs)
+    info = P.mts_batch_info(batch)
+    P.mts_batch_destroy(batch)
+    for c in ctxs:
+        P.pdmts_ctx_destroy(c)
+    if rank != 0:
+        return
+    nodes = sum(cp.pd.n for cp in cps)
+    ms_mix = sorted({cp.m for cp in cps})
+    # algorithmic bytes of the PD substeps of the timed rounds (100 B per node and substep,
+    # FP32-bulk coupled), over the whole round time: a lower bound on the substeps' own rate
+    sub_bytes = 100.0 * sum(2 * cp.m * cp.pd.n for cp in cps) * args.steps
+    achieved = sub_bytes / (batch_ms * 1e-3) / 1e9
+    peak, peak_kind = peaks()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": batch_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": BATCH_NAME.format(n=len(cps)), "members": len(cps), "pd_nodes_total": nodes,
+                   "m_values": ms_mix, "step": "one round = one coarse step of every member",
+                   "lattice_tile": info["lattice_tile"], "batched_launches_per_round":
+                   (i1["batched_launches"] - i0["batched_launches"]) // max(args.steps, 1),
+                   "work_items_per_round": (i1["work_items"] - i0["work_items"]) // max(args.steps, 1),
+                   "setup_s": round(t_setup, 2), "l2": "flushed between timed rounds (256 MB write)",
+                   "per_instance_loop_value": solo_value, "batch_over_loop": value / solo_value},
+        "coarse_steps_per_s": d["coarse_steps"] / (batch_ms * 1e-3),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "peak_kind": peak_kind, "kernel": "k_pd_step_lattice2d_batch (whole round)",
+                     "algorithmic_bytes_per_step": sub_bytes / args.steps},
+        "cpu_baseline": None,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
 
 
 def run_ours(args, rank, world, local_rank):
@@ -362,7 +482,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["coupled", "pd"], default="coupled")
+    ap.add_argument("--workload", choices=["coupled", "pd", "batch"], default="coupled")
+    ap.add_argument("--batch-members", type=int, default=64, help="members of the batched workload")
     ap.add_argument("--lattice-tile", type=int, default=-1,
                     help="fix the lattice kernel tile configuration (default: autotune)")
     args = ap.parse_args()
@@ -378,7 +499,10 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
     try:
-        run_ours(args, rank, world, local_rank)
+        if args.workload == "batch":
+            run_batch(args, rank, world, local_rank)
+        else:
+            run_ours(args, rank, world, local_rank)
     finally:
         if world > 1:
             import torch.distributed as dist

@@ -65,6 +65,7 @@ typedef struct pdmts_ctx pdmts_ctx;
 typedef struct pdmts_pd pdmts_pd;
 typedef struct pdmts_fem pdmts_fem;
 typedef struct pdmts_arl pdmts_arl;
+typedef struct pdmts_batch pdmts_batch;
 
 /* ---- context ------------------------------------------------------------- */
 
@@ -277,6 +278,34 @@ typedef struct {
     int64_t device_bytes;    /* device memory of the coupling and FE      */
 } pdmts_arl_info;
 int arlequin_info(pdmts_arl *arl, pdmts_arl_info *info);
+
+/* ---- batches of coupled problems (many specimens, one launch per substep) ---- */
+
+/* A batch of n_members coupled problems advanced together. Every member is a
+ * context with a PD subdomain in PDMTS_FP32_BULK on a 2D lattice, an FE
+ * subdomain, an Arlequin coupling and mts_set_time called; all on one device
+ * and with one force law; no context twice. The members keep their own sizes,
+ * loads, cracks and ratios m. The batch does not own them: destroy the batch
+ * before its members. PDMTS_ERR_STATE / _UNSUPPORTED / _ARG otherwise. */
+int mts_batch_create(int n_members, pdmts_ctx *const *members, pdmts_batch **batch);
+/* Advance every member by n_rounds of its own coarse steps (Algorithm 1,
+ * m_i PD substeps each in the free and in the link problem). The PD substeps
+ * of all members in the same substep slot run as one launch over a work list
+ * of (member, tile) of the batch's lattice tile configuration (tuned at the
+ * first call among the one-CTA-per-tile configurations). Each member's state
+ * afterwards equals, bit for bit, what n_rounds calls of mts_advance(member, 1)
+ * would give with the same tile configuration. Work for each member is
+ * ordered after its user stream and before it afterwards. */
+int mts_batch_advance(pdmts_batch *batch, int64_t n_rounds);
+typedef struct {
+    int32_t n_members;
+    int32_t lattice_tile;      /* tile configuration of the batched substeps */
+    int64_t rounds;            /* rounds advanced                            */
+    int64_t work_items;        /* (member, tile) items launched              */
+    int64_t batched_launches;  /* batched substep launches                   */
+} pdmts_batch_info;
+int mts_batch_info(const pdmts_batch *batch, pdmts_batch_info *info);
+int mts_batch_destroy(pdmts_batch *batch);
 
 /* Counters since context creation. */
 typedef struct {

@@ -986,12 +986,55 @@ int pdmts_pd::tune_lattice(cudaStream_t s)
     return PDMTS_OK;
 }
 
+// Per-node arguments of one FP32-bulk substep at the current buffer parity.
+F32NodeArgs pdmts_pd::f32_node_args(bool init, double theta, bool link) const
+{
+    const double dt = ctx->dt_pd;
+    const int c = link ? lk_cur : cur;
+    const int src = init ? c : 1 - c;  // buffer the forces are evaluated at
+    const int dst = 1 - src;           // buffer receiving the next prediction
+    F32NodeArgs N{};
+    N.n = n;
+    N.inv_m = f_invm.p;
+    N.wb = link ? nullptr : f_wb.p;
+    N.g = link ? lk_gf.p : (has_g ? f_g.p : nullptr);
+    N.u4_in = link ? lk_u4[src].p : f_u4[src].p;
+    N.u2_in = link ? lk_u2[src].p : f_u2[src].p;
+    N.u4_out = link ? lk_u4[dst].p : f_u4[dst].p;
+    N.u2_out = link ? lk_u2[dst].p : f_u2[dst].p;
+    N.v4 = link ? lk_v4.p : f_v4.p;
+    N.v2 = link ? lk_v2.p : f_v2.p;
+    N.a = link ? lk_af.p : f_a.p;
+    N.dt = (float)dt;
+    N.hdt = (float)(0.5 * dt);
+    N.hdt2 = (float)(0.5 * dt * dt);
+    N.theta = (float)theta;
+    N.breaking = (breaking && !link) ? 1 : 0;
+    N.pmb = force_kind == PDMTS_FORCE_PMB;
+    N.broken = ctx->d_counter;
+    return N;
+}
+
+// Bookkeeping after a substep was enqueued: buffer parity and counters.
+void pdmts_pd::substep_done(bool init, bool link)
+{
+    ctx->stats.kernel_launches++;
+    if (init)
+        return;
+    int &c = link ? lk_cur : cur;
+    c = 1 - c;
+    if (!link)
+        steps_done++;
+    ctx->stats.pd_substeps++;
+    ctx->stats.bond_updates += (link && link_bonds >= 0) ? link_bonds : (int64_t)row_ptr[(size_t)n];
+}
+
 int pdmts_pd::step(bool init, double theta, cudaStream_t s, bool link)
 {
     const double dt = ctx->dt_pd;
     cudaError_t e;
     SellView fam{d_tile_ptr.p, d_tile_k.p, d_mask_ptr.p, d_col.p, d_mask.p, d_deg.p, n, ntiles};
-    int &c = link ? lk_cur : cur;
+    const int c = link ? lk_cur : cur;
     const int src = init ? c : 1 - c;  // buffer the forces are evaluated at
     const int dst = 1 - src;           // buffer receiving the next prediction
     uint32_t *mask = link ? d_mask_link.p : d_mask.p;
@@ -1020,25 +1063,7 @@ int pdmts_pd::step(bool init, double theta, cudaStream_t s, bool link)
         A.broken = ctx->d_counter;
         e = launch_pd_step_f64(dim, A, init, s);
     } else {
-        F32NodeArgs N{};
-        N.n = n;
-        N.inv_m = f_invm.p;
-        N.wb = link ? nullptr : f_wb.p;
-        N.g = link ? lk_gf.p : (has_g ? f_g.p : nullptr);
-        N.u4_in = link ? lk_u4[src].p : f_u4[src].p;
-        N.u2_in = link ? lk_u2[src].p : f_u2[src].p;
-        N.u4_out = link ? lk_u4[dst].p : f_u4[dst].p;
-        N.u2_out = link ? lk_u2[dst].p : f_u2[dst].p;
-        N.v4 = link ? lk_v4.p : f_v4.p;
-        N.v2 = link ? lk_v2.p : f_v2.p;
-        N.a = link ? lk_af.p : f_a.p;
-        N.dt = (float)dt;
-        N.hdt = (float)(0.5 * dt);
-        N.hdt2 = (float)(0.5 * dt * dt);
-        N.theta = (float)theta;
-        N.breaking = (breaking && !link) ? 1 : 0;
-        N.pmb = force_kind == PDMTS_FORCE_PMB;
-        N.broken = ctx->d_counter;
+        const F32NodeArgs N = f32_node_args(init, theta, link);
         if (layout == LAYOUT_LATTICE2D) {
             Lat2DArgs A = lattice_args(N, mask, link);
             e = launch_pd_step_lattice2d(A, init, s);
@@ -1054,14 +1079,7 @@ int pdmts_pd::step(bool init, double theta, cudaStream_t s, bool link)
     }
     if (e != cudaSuccess)
         return fail(PDMTS_ERR_CUDA, "PD substep launch failed: %s", cudaGetErrorString(e));
-    ctx->stats.kernel_launches++;
-    if (!init) {
-        c = 1 - c;
-        if (!link)
-            steps_done++;
-        ctx->stats.pd_substeps++;
-        ctx->stats.bond_updates += (link && link_bonds >= 0) ? link_bonds : (int64_t)row_ptr[(size_t)n];
-    }
+    substep_done(init, link);
     return PDMTS_OK;
 }
 

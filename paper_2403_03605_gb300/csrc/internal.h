@@ -166,6 +166,14 @@ cudaError_t launch_lattice2d_t0(const Lat2DArgs &A, bool init, cudaStream_t s);
 cudaError_t launch_lattice2d_t1(const Lat2DArgs &A, bool init, cudaStream_t s);
 cudaError_t launch_lattice2d_t2(const Lat2DArgs &A, bool init, cudaStream_t s);
 cudaError_t launch_lattice2d_t3(const Lat2DArgs &A, bool init, cudaStream_t s);
+// Batched substeps (tile configurations 0 and 1): lattice2d_batch_prepare
+// converts A's windows to the configuration's tile rows and returns the
+// instance's tile count (-1 for another configuration); the launch runs one
+// CTA per work item {instance index into d_args, tile}.
+constexpr int kLatBatchTiles = 2;
+int lattice2d_batch_prepare(Lat2DArgs &A, int tile);
+cudaError_t launch_lattice2d_batch(const Lat2DArgs *d_args, const int2 *d_work, int nwork, int tile, bool pmb,
+                                   cudaStream_t s);
 // Damage of the lattice layout (uniform volume): 1 - popc(intact) / popc(exists).
 cudaError_t launch_damage_lattice(int64_t n, const uint32_t *mask, const uint32_t *exists, int words,
                                   double *phi, cudaStream_t s);

@@ -455,6 +455,37 @@ __global__ void __launch_bounds__(256, MINB) k_pd_step_lattice2d_pipe(const Lat2
     count_broken(A.nd.broken, nbroken);
 }
 
+// Batched substep over several lattices: one CTA per work item (instance,
+// tile in that instance's tile list); the CTA copies its instance's arguments
+// to shared memory once. The per-tile code is the single-lattice one, so a
+// batched substep gives every instance the bits of its own substep.
+template <bool PMB, int KR, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_pd_step_lattice2d_batch(const Lat2DArgs *__restrict__ args,
+                                                                        const int2 *__restrict__ work,
+                                                                        const int init)
+{
+    __shared__ __align__(16) Lat2DArgs sA;
+    extern __shared__ __align__(16) unsigned char lat_smem[];
+    LatStage<KR> &S = *reinterpret_cast<LatStage<KR> *>(lat_smem);
+    const int2 w = work[blockIdx.x];
+    static_assert(sizeof(Lat2DArgs) % 4 == 0, "argument block copied as words");
+    const int *src = reinterpret_cast<const int *>(args + w.x);
+    int *dst = reinterpret_cast<int *>(&sA);
+    for (int q = threadIdx.x; q < (int)(sizeof(Lat2DArgs) / 4); q += blockDim.x)
+        dst[q] = src[q];
+    __syncthreads();
+    const Lat2DArgs &A = sA;
+    const int ntx = (A.nx + lat2d::TX - 1) / lat2d::TX;
+    const int x0 = (w.y % ntx) * lat2d::TX, y0 = lattice_trow(A, w.y / ntx) * LatStage<KR>::TYK;
+    lattice_issue_a<KR>(S, A, x0, y0);
+    cp_async_commit();
+    lattice_issue_b<KR>(S, A, x0, y0);
+    cp_async_commit();
+    cp_async_wait<1>();
+    const unsigned nbroken = lattice_tile<PMB, KR, 0>(S, A, x0, y0, init);
+    count_broken(A.nd.broken, nbroken);
+}
+
 // Tile rows of the launch (all, or the windows converted to this tile height).
 template <int TYK>
 __host__ int lattice_tile_rows(Lat2DArgs &A, const Lat2DArgs &A0)
@@ -537,6 +568,29 @@ cudaError_t launch_lattice_kr(const Lat2DArgs &A0, bool init, cudaStream_t s)
     const unsigned rows = (unsigned)lattice_tile_rows<LatStage<KR>::TYK>(A, A0);
     const dim3 grid((unsigned)((A.nx + lat2d::TX - 1) / lat2d::TX), rows);
     kern<<<grid, 256, smem, s>>>(A, init ? 1 : 0);
+    return cudaGetLastError();
+}
+
+template <int KR, int MINB>
+int lattice_batch_prepare(Lat2DArgs &A)
+{
+    const Lat2DArgs A0 = A;
+    const int rows = lattice_tile_rows<LatStage<KR>::TYK>(A, A0);
+    return ((A.nx + lat2d::TX - 1) / lat2d::TX) * rows;
+}
+
+template <int KR, int MINB>
+cudaError_t launch_lattice_batch(const Lat2DArgs *d_args, const int2 *d_work, int nwork, bool pmb, cudaStream_t s)
+{
+    if (nwork <= 0)
+        return cudaSuccess;
+    constexpr size_t smem = sizeof(LatStage<KR>);
+    static int ctas[2] = {0, 0};
+    const auto kern = pmb ? k_pd_step_lattice2d_batch<true, KR, MINB> : k_pd_step_lattice2d_batch<false, KR, MINB>;
+    cudaError_t e = lattice_prepare(kern, smem, ctas[pmb ? 1 : 0]);
+    if (e != cudaSuccess)
+        return e;
+    kern<<<nwork, 256, smem, s>>>(d_args, d_work, 0);
     return cudaGetLastError();
 }
 

@@ -1554,17 +1554,23 @@ int mts_time_changed(pdmts_ctx *ctx)
     return PDMTS_OK;
 }
 
-// One coarse step of Algorithm 1.
-static int coarse_step(pdmts_arl *A)
+// ------------------------------------------------- coarse step phases -----
+// One coarse step of Algorithm 1 is enqueued in phases so that a batch of
+// coupled problems can interleave them around batched PD substeps:
+//   step_prepare     host: rebuild flag of the previous step, schedules, H;
+//   step_free_begin  s: fork mark, interface force of lambda_0 (Eq. 48a);
+//   (m free PD substeps with factor 1 - j/m)
+//   step_fe_free     fs: FE free step (Eq. 47a);
+//   step_interface   s: join, lambda_m = (-H)^-1 (G_FE v_FE - G_PD v_PD) (Eq. 49),
+//                    then the FE correction on fs (Eq. 47b);
+//   step_link_begin  s: interface force of lambda_m, W_0 = 0 (Eq. 48b);
+//   (m link PD substeps with factor j/m)
+//   step_finish      s: U += W, rebuild flag, lambda_0 <- lambda_m, join fs.
+static int step_prepare(pdmts_arl *A, cudaStream_t s)
 {
     pdmts_ctx *ctx = A->ctx;
     pdmts_pd *pd = A->pd;
-    pdmts_fem *fe = A->fe;
-    cudaStream_t s = ctx->stream;
     const int m = ctx->m_ratio;
-    const double dtf = m * ctx->dt_pd, beta = ctx->beta_fe, gamma = ctx->gamma_fe;
-    const bool f64 = pd->precision == PDMTS_FP64;
-    int64_t launches = 0;
     // rebuild flag of the previous step (a bond near an overlap band broke)
     if (A->flag_pending) {
         PDMTS_CUDA_TRY(cudaEventSynchronize(A->ev_flag));
@@ -1586,49 +1592,92 @@ static int coarse_step(pdmts_arl *A)
         PDMTS_CUDA_TRY(cudaMemcpyAsync(pd->d_mask_link.p, pd->d_mask.p, sizeof(uint32_t) * pd->n_mask_words,
                                        cudaMemcpyDeviceToDevice, s));
     }
-    PDMTS_TRY(fe_prepare_keff(fe, dtf, beta));
+    PDMTS_TRY(fe_prepare_keff(A->fe, m * ctx->dt_pd, ctx->beta_fe));
     PDMTS_TRY(pd->tune_lattice(s));
     PDMTS_TRY(pd->ensure_init(s));
     if (!A->H_valid)
         PDMTS_TRY(build_H(A, m));
-    // The FE free step may start once the previous step has ended; the PD
-    // chain is enqueued first so that it starts without waiting for the host.
-    std::array<cudaEvent_t, 5> ph{};
-    PDMTS_TRY(ctx->mark(&ph[0]));
+    return PDMTS_OK;
+}
+
+static int step_free_begin(pdmts_arl *A, cudaStream_t s, int64_t *launches)
+{
+    pdmts_pd *pd = A->pd;
+    const bool f64 = pd->precision == PDMTS_FP64;
+    // the FE free step may start once the previous step has ended
     PDMTS_CUDA_TRY(cudaEventRecord(A->ev_fork, s));
-    // ---- PD free substeps with (1 - j/m) lambda_0 (Eq. 48a) ----
     cudaError_t e = launch_interface_force(pd->dim, pd->n, A->n_ov, A->d_ov_node.p, A->d_ov_k.p, A->d_ov_N.p, 4,
                                            A->d_lam0.p, A->nl, f64 ? 0.0 : 1.0 / pd->h, f64 ? pd->d_g.p : nullptr,
                                            f64 ? nullptr : pd->f_g.p, s);
     if (e != cudaSuccess)
         return fail(PDMTS_ERR_CUDA, "interface force: %s", cudaGetErrorString(e));
-    ++launches;
-    PDMTS_TRY(pd_run_chain(pd, m, 1, A->theta_free.data(), s, false));
-    // ---- FE free step on the second stream (Eq. 47a) ----
-    PDMTS_CUDA_TRY(cudaStreamWaitEvent(A->fe_stream, A->ev_fork, 0));
-    PDMTS_TRY(fe_free_step(fe, dtf, beta, gamma, A->fe_stream, &launches));
-    PDMTS_CUDA_TRY(cudaEventRecord(A->ev_join, A->fe_stream));
+    ++*launches;
+    return PDMTS_OK;
+}
+
+// graphs: replay the FE sequences as captured graphs (not while the caller
+// captures the step itself)
+static int step_fe_free(pdmts_arl *A, cudaStream_t fs, bool graphs, int64_t *launches)
+{
+    pdmts_ctx *ctx = A->ctx;
+    const double dtf = ctx->m_ratio * ctx->dt_pd;
+    PDMTS_CUDA_TRY(cudaStreamWaitEvent(fs, A->ev_fork, 0));
+    if (graphs)
+        PDMTS_TRY(fe_free_step(A->fe, dtf, ctx->beta_fe, ctx->gamma_fe, fs, launches));
+    else
+        PDMTS_TRY(fe_free_enqueue(A->fe, dtf, ctx->beta_fe, ctx->gamma_fe, fs, launches));
+    PDMTS_CUDA_TRY(cudaEventRecord(A->ev_join, fs));
+    return PDMTS_OK;
+}
+
+static int step_interface(pdmts_arl *A, cudaStream_t s, cudaStream_t fs, bool graphs, int64_t *launches)
+{
+    pdmts_ctx *ctx = A->ctx;
+    pdmts_pd *pd = A->pd;
+    pdmts_fem *fe = A->fe;
+    const bool f64 = pd->precision == PDMTS_FP64;
+    const double dtf = ctx->m_ratio * ctx->dt_pd;
     PDMTS_CUDA_TRY(cudaStreamWaitEvent(s, A->ev_join, 0));
-    PDMTS_TRY(ctx->mark(&ph[1]));
-    // ---- interface problem (Eq. 49): lambda_m = (-H)^-1 (G_FE v_FE - G_PD v_PD) ----
     const float4 *v4 = f64 ? nullptr : pd->f_v4.p;
     const float2 *v2 = f64 ? nullptr : pd->f_v2.p;
-    e = launch_constraint(2, A->nl, A->d_gpd_ptr.p, A->d_gpd_col.p, A->d_gpd_val.p, pd->n, f64 ? pd->d_v.p : nullptr,
-                          v4, v2, pd->h, A->d_gfe_col.p, A->d_gfe_val.p, A->gfe_w, fe->n, fe->d_v.p, -1.0, 1.0,
-                          A->d_y.p, s);
+    cudaError_t e = launch_constraint(2, A->nl, A->d_gpd_ptr.p, A->d_gpd_col.p, A->d_gpd_val.p, pd->n,
+                                      f64 ? pd->d_v.p : nullptr, v4, v2, pd->h, A->d_gfe_col.p, A->d_gfe_val.p,
+                                      A->gfe_w, fe->n, fe->d_v.p, -1.0, 1.0, A->d_y.p, s);
     if (e != cudaSuccess)
         return fail(PDMTS_ERR_CUDA, "interface residual: %s", cudaGetErrorString(e));
     // the multiplier solve stays FP64 in every precision
     k_gemv_rows<<<blocks(A->nlam * 32), 256, 0, s>>>(A->nlam, A->d_Hneg_inv.p, A->d_y.p, 1.0, A->d_lam.p);
-    PDMTS_TRY(ctx->mark(&ph[2]));
-    // ---- corrections U = V + Y lambda_m: FE on its stream, PD link run here ----
+    *launches += 2;
+    // FE correction U = V + Y lambda_m on the FE stream
     PDMTS_CUDA_TRY(cudaEventRecord(A->ev_fork, s));
-    PDMTS_CUDA_TRY(cudaStreamWaitEvent(A->fe_stream, A->ev_fork, 0));
-    PDMTS_TRY(fe_link_step(A, dtf, beta, gamma, A->fe_stream, &launches));
-    PDMTS_CUDA_TRY(cudaEventRecord(A->ev_join, A->fe_stream));
-    launches += 2;
-    PDMTS_TRY(pd_link_run(A, A->d_lam.p, m, s));
-    PDMTS_TRY(ctx->mark(&ph[3]));
+    PDMTS_CUDA_TRY(cudaStreamWaitEvent(fs, A->ev_fork, 0));
+    if (graphs)
+        PDMTS_TRY(fe_link_step(A, dtf, ctx->beta_fe, ctx->gamma_fe, fs, launches));
+    else
+        PDMTS_TRY(fe_link_enqueue(A, dtf, ctx->beta_fe, ctx->gamma_fe, fs, launches));
+    PDMTS_CUDA_TRY(cudaEventRecord(A->ev_join, fs));
+    return PDMTS_OK;
+}
+
+static int step_link_begin(pdmts_arl *A, const double *dev_lam, cudaStream_t s, int64_t *launches)
+{
+    pdmts_pd *pd = A->pd;
+    const bool f64 = pd->precision == PDMTS_FP64;
+    cudaError_t e = launch_interface_force(pd->dim, pd->n, A->n_ov, A->d_ov_node.p, A->d_ov_k.p, A->d_ov_N.p, 4,
+                                           dev_lam, A->nl, f64 ? 0.0 : 1.0 / pd->h, f64 ? pd->lk_g.p : nullptr,
+                                           f64 ? nullptr : pd->lk_gf.p, s);
+    if (e != cudaSuccess)
+        return fail(PDMTS_ERR_CUDA, "interface force: %s", cudaGetErrorString(e));
+    ++*launches;
+    PDMTS_TRY(pd->zero_link_state(s));
+    return PDMTS_OK;
+}
+
+static int step_finish(pdmts_arl *A, cudaStream_t s, int64_t *launches)
+{
+    pdmts_ctx *ctx = A->ctx;
+    pdmts_pd *pd = A->pd;
+    const bool f64 = pd->precision == PDMTS_FP64;
     PDAddLink L{};
     L.dim = pd->dim;
     L.n = pd->n;
@@ -1660,7 +1709,7 @@ static int coarse_step(pdmts_arl *A)
         L.wv2 = pd->lk_v2.p;
         L.waf = pd->lk_af.p;
     }
-    e = launch_pd_add_link(L, s);
+    cudaError_t e = launch_pd_add_link(L, s);
     if (e != cudaSuccess)
         return fail(PDMTS_ERR_CUDA, "PD correction: %s", cudaGetErrorString(e));
     // ---- rebuild flag: bonds near a band broken this step; new start mask ----
@@ -1676,12 +1725,38 @@ static int coarse_step(pdmts_arl *A)
     PDMTS_CUDA_TRY(cudaMemcpyAsync(A->d_lam0.p, A->d_lam.p, sizeof(double) * A->nlam, cudaMemcpyDeviceToDevice, s));
     // the step ends when the FE correction has also finished
     PDMTS_CUDA_TRY(cudaStreamWaitEvent(s, A->ev_join, 0));
+    *launches += 2;
+    ctx->stats.coarse_steps += 1;
+    return PDMTS_OK;
+}
+
+// One coarse step of Algorithm 1.
+static int coarse_step(pdmts_arl *A)
+{
+    pdmts_ctx *ctx = A->ctx;
+    pdmts_pd *pd = A->pd;
+    cudaStream_t s = ctx->stream;
+    const int m = ctx->m_ratio;
+    int64_t launches = 0;
+    PDMTS_TRY(step_prepare(A, s));
+    std::array<cudaEvent_t, 5> ph{};
+    PDMTS_TRY(ctx->mark(&ph[0]));
+    // the PD chain is enqueued before the FE step so that it starts without waiting for the host
+    PDMTS_TRY(step_free_begin(A, s, &launches));
+    PDMTS_TRY(pd_run_chain(pd, m, 1, A->theta_free.data(), s, false));
+    PDMTS_TRY(step_fe_free(A, A->fe_stream, true, &launches));
+    PDMTS_CUDA_TRY(cudaStreamWaitEvent(s, A->ev_join, 0));
+    PDMTS_TRY(ctx->mark(&ph[1]));
+    PDMTS_TRY(step_interface(A, s, A->fe_stream, true, &launches));
+    PDMTS_TRY(ctx->mark(&ph[2]));
+    PDMTS_TRY(step_link_begin(A, A->d_lam.p, s, &launches));
+    PDMTS_TRY(pd_run_chain(pd, m, 2, A->theta_link.data(), s, true));
+    PDMTS_TRY(ctx->mark(&ph[3]));
+    PDMTS_TRY(step_finish(A, s, &launches));
     PDMTS_TRY(ctx->mark(&ph[4]));
     if (ph[0])
         ctx->phase_marks.push_back(ph);
-    launches += 3;
     ctx->stats.kernel_launches += launches;
-    ctx->stats.coarse_steps += 1;
     PDMTS_CUDA_TRY(cudaGetLastError());
     return PDMTS_OK;
 }
@@ -1693,6 +1768,323 @@ int mts_advance_coupled(pdmts_ctx *ctx, int64_t n_coarse)
     for (int64_t k = 0; k < n_coarse; ++k)
         PDMTS_TRY(coarse_step(ctx->arl));
     return ctx->end();
+}
+
+// ------------------------------------------------------------- batches ----
+// Several independent coupled problems (members, one context each, on one
+// device) advanced together: every round takes each member through one of
+// its own coarse steps, and the PD substeps of all members that are in the
+// same substep slot run as one batched launch over a work list of (member,
+// tile). Per member the kernels and their arguments are those of its own
+// coarse step, so the batch reproduces each member's solo run bit for bit.
+struct pdmts_batch {
+    int device = 0;
+    std::vector<pdmts_ctx *> members;
+    cudaStream_t s = nullptr;               // batched substeps and per-member interface work
+    std::vector<cudaStream_t> fe_streams;   // FE steps, members round-robin
+    cudaEvent_t ev_in = nullptr, ev_end = nullptr;
+    int tile = -1;                          // batched lattice tile configuration (-1: tune)
+    // argument blocks and work lists of one phase's slots: host staging (pinned) and device copies
+    Lat2DArgs *h_args = nullptr;
+    int2 *h_work = nullptr;
+    Lat2DArgs *d_args = nullptr;
+    int2 *d_work = nullptr;
+    int64_t cap_args = 0, cap_work = 0;
+    int64_t rounds = 0, work_items = 0, batched_launches = 0;
+    bool pending = false;                   // a round is in flight (staging in use)
+};
+
+static void batch_free_buffers(pdmts_batch *b)
+{
+    if (b->h_args) cudaFreeHost(b->h_args);
+    if (b->h_work) cudaFreeHost(b->h_work);
+    if (b->d_args) cudaFree(b->d_args);
+    if (b->d_work) cudaFree(b->d_work);
+    b->h_args = nullptr; b->h_work = nullptr; b->d_args = nullptr; b->d_work = nullptr;
+    b->cap_args = b->cap_work = 0;
+}
+
+static int batch_reserve(pdmts_batch *b, int64_t nargs, int64_t nwork)
+{
+    if (nargs <= b->cap_args && nwork <= b->cap_work)
+        return PDMTS_OK;
+    batch_free_buffers(b);
+    const int64_t na = std::max<int64_t>(nargs, 1), nw = std::max<int64_t>(nwork, 1);
+    if (cudaMallocHost(&b->h_args, sizeof(Lat2DArgs) * na) != cudaSuccess ||
+        cudaMallocHost(&b->h_work, sizeof(int2) * nw) != cudaSuccess ||
+        cudaMalloc(&b->d_args, sizeof(Lat2DArgs) * na) != cudaSuccess ||
+        cudaMalloc(&b->d_work, sizeof(int2) * nw) != cudaSuccess) {
+        batch_free_buffers(b);
+        return fail(PDMTS_ERR_NOMEM, "batch: staging of %lld argument blocks and %lld work items failed",
+                    (long long)na, (long long)nw);
+    }
+    b->cap_args = na;
+    b->cap_work = nw;
+    return PDMTS_OK;
+}
+
+// Build the argument blocks and work lists of the slots of one phase (free or
+// link) of the current round, advancing each member's buffer parity as its
+// substeps are planned; upload them and launch the slots on b->s.
+static int batch_phase(pdmts_batch *b, bool link)
+{
+    const int nm = (int)b->members.size();
+    int M = 0;
+    for (pdmts_ctx *c : b->members)
+        M = std::max(M, c->m_ratio);
+    // count first: one argument block per (slot, active member), its tiles
+    std::vector<int64_t> arg_off((size_t)M + 1, 0), work_off((size_t)M + 1, 0);
+    std::vector<Lat2DArgs> args;
+    std::vector<int2> work;
+    for (int j = 0; j < M; ++j) {
+        for (int i = 0; i < nm; ++i) {
+            pdmts_ctx *c = b->members[(size_t)i];
+            if (j >= c->m_ratio)
+                continue;
+            pdmts_arl *A = c->arl;
+            pdmts_pd *pd = A->pd;
+            const double theta = link ? A->theta_link[(size_t)j] : A->theta_free[(size_t)j];
+            const F32NodeArgs N = pd->f32_node_args(false, theta, link);
+            Lat2DArgs L = pd->lattice_args(N, link ? pd->d_mask_link.p : pd->d_mask.p, link);
+            L.tile = b->tile;
+            const int ntiles = lattice2d_batch_prepare(L, b->tile);
+            if (ntiles < 0)
+                return fail(PDMTS_ERR_UNSUPPORTED, "batch: tile configuration %d cannot be batched", b->tile);
+            const int slot_index = (int)(args.size() - (size_t)arg_off[(size_t)j]);
+            for (int t = 0; t < ntiles; ++t)
+                work.push_back(make_int2(slot_index, t));
+            args.push_back(L);
+            pd->substep_done(false, link);
+        }
+        arg_off[(size_t)j + 1] = (int64_t)args.size();
+        work_off[(size_t)j + 1] = (int64_t)work.size();
+    }
+    PDMTS_TRY(batch_reserve(b, (int64_t)args.size(), (int64_t)work.size()));
+    std::memcpy(b->h_args, args.data(), sizeof(Lat2DArgs) * args.size());
+    std::memcpy(b->h_work, work.data(), sizeof(int2) * work.size());
+    PDMTS_CUDA_TRY(cudaMemcpyAsync(b->d_args, b->h_args, sizeof(Lat2DArgs) * args.size(), cudaMemcpyHostToDevice, b->s));
+    PDMTS_CUDA_TRY(cudaMemcpyAsync(b->d_work, b->h_work, sizeof(int2) * work.size(), cudaMemcpyHostToDevice, b->s));
+    const bool pmb = b->members[0]->pd->force_kind == PDMTS_FORCE_PMB;
+    for (int j = 0; j < M; ++j) {
+        const int nwork = (int)(work_off[(size_t)j + 1] - work_off[(size_t)j]);
+        cudaError_t e = launch_lattice2d_batch(b->d_args + arg_off[(size_t)j], b->d_work + work_off[(size_t)j], nwork,
+                                               b->tile, pmb, b->s);
+        if (e != cudaSuccess)
+            return fail(PDMTS_ERR_CUDA, "batched substep: %s", cudaGetErrorString(e));
+        b->batched_launches += 1;
+        b->work_items += nwork;
+    }
+    return PDMTS_OK;
+}
+
+// Batch tile autotuner: one batched link-mode substep (no breaking, whole
+// lattices) per configuration on the members' link-state buffers, which are
+// scratch between link runs (cleared afterwards); keeps the fastest.
+static int batch_tune(pdmts_batch *b)
+{
+    if (b->tile >= 0)
+        return PDMTS_OK;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    PDMTS_CUDA_TRY(cudaEventCreate(&e0));
+    PDMTS_CUDA_TRY(cudaEventCreate(&e1));
+    int best = 0;
+    float best_ms = 0.f;
+    int r = PDMTS_OK;
+    for (int t = 0; t < kLatBatchTiles && r == PDMTS_OK; ++t) {
+        std::vector<Lat2DArgs> args;
+        std::vector<int2> work;
+        for (size_t i = 0; i < b->members.size(); ++i) {
+            pdmts_pd *pd = b->members[i]->arl->pd;
+            F32NodeArgs N = pd->f32_node_args(false, 0.0, true);
+            N.broken = nullptr;
+            Lat2DArgs L = pd->lattice_args(N, pd->d_mask_link.p, false);  // whole lattice
+            const int ntiles = lattice2d_batch_prepare(L, t);
+            for (int k = 0; k < ntiles; ++k)
+                work.push_back(make_int2((int)args.size(), k));
+            args.push_back(L);
+        }
+        if ((r = batch_reserve(b, (int64_t)args.size(), (int64_t)work.size())) != PDMTS_OK)
+            break;
+        std::memcpy(b->h_args, args.data(), sizeof(Lat2DArgs) * args.size());
+        std::memcpy(b->h_work, work.data(), sizeof(int2) * work.size());
+        cudaError_t e = cudaMemcpyAsync(b->d_args, b->h_args, sizeof(Lat2DArgs) * args.size(), cudaMemcpyHostToDevice, b->s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(b->d_work, b->h_work, sizeof(int2) * work.size(), cudaMemcpyHostToDevice, b->s);
+        const bool pmb = b->members[0]->pd->force_kind == PDMTS_FORCE_PMB;
+        for (int k = 0; k < 4 && e == cudaSuccess; ++k) {
+            if (k == 1)
+                e = cudaEventRecord(e0, b->s);
+            if (e == cudaSuccess)
+                e = launch_lattice2d_batch(b->d_args, b->d_work, (int)work.size(), t, pmb, b->s);
+        }
+        if (e == cudaSuccess)
+            e = cudaEventRecord(e1, b->s);
+        if (e == cudaSuccess)
+            e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess)
+            e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess)
+            r = fail(PDMTS_ERR_CUDA, "batch autotune: %s", cudaGetErrorString(e));
+        else if (t == 0 || ms < best_ms) {
+            best = t;
+            best_ms = ms;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (r != PDMTS_OK)
+        return r;
+    for (pdmts_ctx *c : b->members)
+        PDMTS_TRY(c->arl->pd->zero_link_state(b->s, true));
+    PDMTS_CUDA_TRY(cudaStreamSynchronize(b->s));
+    b->tile = best;
+    return PDMTS_OK;
+}
+
+static int batch_round(pdmts_batch *b)
+{
+    const size_t nm = b->members.size();
+    const size_t K = b->fe_streams.size();
+    // the previous round must have ended: staging reuse and rebuild flags
+    if (b->pending) {
+        PDMTS_CUDA_TRY(cudaEventSynchronize(b->ev_end));
+        b->pending = false;
+    }
+    std::vector<int64_t> launches(nm, 0);
+    for (size_t i = 0; i < nm; ++i) {
+        pdmts_arl *A = b->members[i]->arl;
+        if (A->pd->lattice_tile < 0)
+            A->pd->lattice_tile = b->tile;  // the members' own substeps use the batch's tile (no solo tuning)
+        PDMTS_TRY(step_prepare(A, b->s));
+    }
+    for (size_t i = 0; i < nm; ++i)
+        PDMTS_TRY(step_free_begin(b->members[i]->arl, b->s, &launches[i]));
+    for (size_t i = 0; i < nm; ++i)
+        PDMTS_TRY(step_fe_free(b->members[i]->arl, b->fe_streams[i % K], true, &launches[i]));
+    PDMTS_TRY(batch_phase(b, false));
+    for (size_t i = 0; i < nm; ++i)
+        PDMTS_TRY(step_interface(b->members[i]->arl, b->s, b->fe_streams[i % K], true, &launches[i]));
+    for (size_t i = 0; i < nm; ++i)
+        PDMTS_TRY(step_link_begin(b->members[i]->arl, b->members[i]->arl->d_lam.p, b->s, &launches[i]));
+    PDMTS_TRY(batch_phase(b, true));
+    for (size_t i = 0; i < nm; ++i) {
+        PDMTS_TRY(step_finish(b->members[i]->arl, b->s, &launches[i]));
+        b->members[i]->stats.kernel_launches += launches[i];
+    }
+    PDMTS_CUDA_TRY(cudaEventRecord(b->ev_end, b->s));
+    b->pending = true;
+    b->rounds += 1;
+    PDMTS_CUDA_TRY(cudaGetLastError());
+    return PDMTS_OK;
+}
+
+extern "C" int mts_batch_create(int n_members, pdmts_ctx *const *members, pdmts_batch **out)
+{
+    clear_error();
+    if (!members || !out || n_members <= 0)
+        return fail(PDMTS_ERR_ARG, "mts_batch_create: NULL argument or no members");
+    *out = nullptr;
+    for (int i = 0; i < n_members; ++i) {
+        pdmts_ctx *c = members[i];
+        if (!c || !c->arl)
+            return fail(PDMTS_ERR_STATE, "mts_batch_create: member %d has no Arlequin coupling", i);
+        if (!c->time_set)
+            return fail(PDMTS_ERR_STATE, "mts_batch_create: member %d: call mts_set_time first", i);
+        pdmts_pd *pd = c->arl->pd;
+        if (pd->precision != PDMTS_FP32_BULK || pd->layout != pdmts_pd::LAYOUT_LATTICE2D)
+            return fail(PDMTS_ERR_UNSUPPORTED,
+                        "mts_batch_create: member %d: batching needs an FP32-bulk PD subdomain on a 2D lattice", i);
+        if (c->device != members[0]->device)
+            return fail(PDMTS_ERR_ARG, "mts_batch_create: members on different devices");
+        if (pd->force_kind != members[0]->arl->pd->force_kind)
+            return fail(PDMTS_ERR_ARG, "mts_batch_create: members with different force laws");
+        for (int k = 0; k < i; ++k)
+            if (members[k] == c)
+                return fail(PDMTS_ERR_ARG, "mts_batch_create: member %d appears twice", i);
+    }
+    PDMTS_CUDA_TRY(cudaSetDevice(members[0]->device));
+    auto *b = new (std::nothrow) pdmts_batch();
+    if (!b)
+        return fail(PDMTS_ERR_NOMEM, "mts_batch_create: out of host memory");
+    b->device = members[0]->device;
+    b->members.assign(members, members + n_members);
+    int lo = 0, hi = 0;
+    bool ok = cudaStreamCreateWithFlags(&b->s, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaDeviceGetStreamPriorityRange(&lo, &hi) == cudaSuccess &&
+              cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&b->ev_end, cudaEventDisableTiming) == cudaSuccess;
+    const int K = std::min(n_members, 8);
+    for (int k = 0; k < K && ok; ++k) {
+        cudaStream_t fs = nullptr;
+        ok = cudaStreamCreateWithPriority(&fs, cudaStreamNonBlocking, hi) == cudaSuccess;
+        if (ok)
+            b->fe_streams.push_back(fs);
+    }
+    if (!ok) {
+        mts_batch_destroy(b);
+        return fail(PDMTS_ERR_CUDA, "mts_batch_create: stream/event creation failed");
+    }
+    *out = b;
+    return PDMTS_OK;
+}
+
+extern "C" int mts_batch_advance(pdmts_batch *b, int64_t n_rounds)
+{
+    clear_error();
+    if (!b)
+        return fail(PDMTS_ERR_ARG, "mts_batch_advance: batch is NULL");
+    if (n_rounds < 0)
+        return fail(PDMTS_ERR_ARG, "mts_batch_advance: n_rounds < 0");
+    PDMTS_CUDA_TRY(cudaSetDevice(b->device));
+    // order the batch after everything queued for its members
+    for (pdmts_ctx *c : b->members) {
+        PDMTS_TRY(c->begin());
+        PDMTS_CUDA_TRY(cudaEventRecord(b->ev_in, c->stream));
+        PDMTS_CUDA_TRY(cudaStreamWaitEvent(b->s, b->ev_in, 0));
+    }
+    PDMTS_TRY(batch_tune(b));
+    for (int64_t k = 0; k < n_rounds; ++k)
+        PDMTS_TRY(batch_round(b));
+    // members' own streams (and through them their users' streams) follow the batch
+    PDMTS_CUDA_TRY(cudaEventRecord(b->ev_in, b->s));
+    for (pdmts_ctx *c : b->members) {
+        PDMTS_CUDA_TRY(cudaStreamWaitEvent(c->stream, b->ev_in, 0));
+        PDMTS_TRY(c->end());
+    }
+    return PDMTS_OK;
+}
+
+extern "C" int mts_batch_info(const pdmts_batch *b, pdmts_batch_info *info)
+{
+    clear_error();
+    if (!b || !info)
+        return fail(PDMTS_ERR_ARG, "mts_batch_info: NULL argument");
+    info->n_members = (int32_t)b->members.size();
+    info->lattice_tile = b->tile;
+    info->rounds = b->rounds;
+    info->work_items = b->work_items;
+    info->batched_launches = b->batched_launches;
+    return PDMTS_OK;
+}
+
+extern "C" int mts_batch_destroy(pdmts_batch *b)
+{
+    if (!b)
+        return PDMTS_OK;
+    cudaSetDevice(b->device);
+    if (b->s)
+        cudaStreamSynchronize(b->s);
+    for (cudaStream_t fs : b->fe_streams) {
+        cudaStreamSynchronize(fs);
+        cudaStreamDestroy(fs);
+    }
+    batch_free_buffers(b);
+    if (b->s) cudaStreamDestroy(b->s);
+    if (b->ev_in) cudaEventDestroy(b->ev_in);
+    if (b->ev_end) cudaEventDestroy(b->ev_end);
+    delete b;
+    return PDMTS_OK;
 }
 
 extern "C" int arlequin_read_lambda(pdmts_arl *A, double *lam, int64_t *n_lambda)

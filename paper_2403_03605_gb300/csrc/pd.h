@@ -114,6 +114,8 @@ struct pdmts_pd {
     int upload_weights_and_loads();  // (re)build mass, wb, g device arrays
     int step(bool init, double theta, cudaStream_t s, bool link = false);  // one substep
     pdmts::Lat2DArgs lattice_args(const pdmts::F32NodeArgs &N, uint32_t *mask, bool link) const;
+    pdmts::F32NodeArgs f32_node_args(bool init, double theta, bool link) const;
+    void substep_done(bool init, bool link);  // parity and counters after an enqueued substep
     int tune_lattice(cudaStream_t s);        // pick the lattice tile configuration (once)
     int alloc_link_state();                  // link-problem arrays (MTS coupling)
     int zero_link_state(cudaStream_t s, bool all = false);  // W_0 = 0 before a link run

@@ -91,6 +91,10 @@ SIGNATURES = [
     ("arlequin_read_lambda", _I, [_V, _V, C.POINTER(_I64)]),
     ("arlequin_constraint_residual", _I, [_V, C.POINTER(_D), C.POINTER(_D)]),
     ("arlequin_info", _I, [_V, _V]),
+    ("mts_batch_create", _I, [_I, C.POINTER(_V), C.POINTER(_V)]),
+    ("mts_batch_advance", _I, [_V, _I64]),
+    ("mts_batch_info", _I, [_V, _V]),
+    ("mts_batch_destroy", _I, [_V]),
     ("pdmts_set_timing", _I, [_V, _I]),
     ("pdmts_get_timing", _I, [_V, C.POINTER(_D), C.POINTER(_I64)]),
     ("mts_get_phase_timing", _I, [_V, C.POINTER(_D), C.POINTER(_I64)]),
@@ -407,6 +411,33 @@ def arlequin_info(arl):
     s = ArlInfo()
     _check(load().arlequin_info(arl, C.byref(s)), "arlequin_info")
     return {k: getattr(s, k) for k, _ in ArlInfo._fields_}
+
+
+class BatchInfo(C.Structure):
+    _fields_ = [("n_members", C.c_int32), ("lattice_tile", C.c_int32), ("rounds", C.c_int64),
+                ("work_items", C.c_int64), ("batched_launches", C.c_int64)]
+
+
+def mts_batch_create(members):
+    """A batch over the contexts `members` (each with a coupled problem bound)."""
+    arr = (_V * len(members))(*members)
+    out = _V()
+    _check(load().mts_batch_create(len(members), arr, C.byref(out)), "mts_batch_create")
+    return out
+
+
+def mts_batch_advance(batch, n_rounds):
+    _check(load().mts_batch_advance(batch, int(n_rounds)), "mts_batch_advance")
+
+
+def mts_batch_info(batch):
+    s = BatchInfo()
+    _check(load().mts_batch_info(batch, C.byref(s)), "mts_batch_info")
+    return {k: getattr(s, k) for k, _ in BatchInfo._fields_}
+
+
+def mts_batch_destroy(batch):
+    _check(load().mts_batch_destroy(batch), "mts_batch_destroy")
 
 
 def arlequin_read_lambda(arl):

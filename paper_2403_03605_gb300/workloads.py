@@ -328,3 +328,40 @@ def small_coupled(m=4, n_coarse=20, weight_kind=1, crack=True, traction=12e6, dx
     return coupled_plate(0.02, 0.01, (0.003, 0.007), dx, 1e-3, 1e-3,
                          crack=(0.005, 0.0, 0.008) if crack else None, traction=traction, dt=20e-9, m=m,
                          n_coarse=n_coarse, weight_kind=weight_kind, name="coupled_small")
+
+
+# Stable PD step of the coupled plates scales with the lattice spacing: the
+# 0.25 mm plate's bound is 51.7 ns (a statement of the benchmark, used only to
+# choose a step below it).
+DT_CRIT_PER_M = 51.7e-9 / 0.25e-3
+
+
+def batch_member(N: int, crack_len: float, traction: float, m: int, *, n_coarse=200, name="batch") -> CoupledProblem:
+    """One specimen of the batched benchmark: the 0.1 x 0.04 m plate with a 16 mm
+    PD strip at dx = sqrt(0.1 * 0.016 / N) (about N nodes), Q4 1 mm, 2 mm overlap,
+    an edge crack of length crack_len at mid-height, dt_PD = 0.4 of the bound."""
+    dx = math.sqrt(0.1 * 0.016 / N)
+    dt = 0.4 * DT_CRIT_PER_M * dx
+    return coupled_plate(0.1, 0.04, (0.012, 0.028), dx, 1e-3, 2e-3, crack=(0.020, 0.0, crack_len),
+                         traction=traction, dt=dt, m=m, n_coarse=n_coarse, name=name)
+
+
+def config4_draws(seed: int = 3605, n: int = 64):
+    """(N_PD, crack length, traction, m) of the batched benchmark's specimens,
+    drawn per specimen in this order: N ~ U[20k, 400k] (integer), crack ~
+    U[20, 60] mm, traction ~ U[6, 15] MPa, m ~ choice{5, 10, 20}."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        N = int(rng.integers(20_000, 400_001))
+        crack = float(rng.uniform(0.020, 0.060))
+        T = float(rng.uniform(6e6, 15e6))
+        m = int(rng.choice([5, 10, 20]))
+        out.append((N, crack, T, m))
+    return out
+
+
+def config4(seed: int = 3605, n: int = 64, n_coarse: int = 200) -> list[CoupledProblem]:
+    """Batched: n independent coupled plates of uneven size, crack, load and m."""
+    return [batch_member(N, c, T, m, n_coarse=n_coarse, name=f"batch_plate_{k}")
+            for k, (N, c, T, m) in enumerate(config4_draws(seed, n))]

@@ -115,3 +115,46 @@ def test_coupled_lattice_tiles_bit_identical(fresh):
             continue
         for a, b in zip(got, ref):
             assert np.array_equal(a, b)
+
+
+def _batch_members():
+    return [W.small_coupled(m=2, n_coarse=4, dx=0.25e-3),
+            W.small_coupled(m=3, n_coarse=4, dx=0.2e-3, traction=20e6),
+            W.small_coupled(m=5, n_coarse=4, dx=0.25e-3, crack=False)]
+
+
+def test_batch_equals_each_member_alone(fresh):
+    """A batch of coupled plates of different sizes, loads and m advanced with one
+    launch per substep slot gives every member the bits of its own solo run."""
+    cps = _batch_members()
+    rounds = 4
+    solo = [GpuMTS(fresh(), cp, P.PDMTS_FP32_BULK).run(rounds) for cp in cps]
+    members = [GpuMTS(fresh(), cp, P.PDMTS_FP32_BULK) for cp in cps]
+    b = P.mts_batch_create([g.ctx for g in members])
+    try:
+        P.mts_batch_advance(b, 2)
+        P.mts_batch_advance(b, rounds - 2)
+        info = P.mts_batch_info(b)
+    finally:
+        P.mts_batch_destroy(b)
+    assert info["rounds"] == rounds and info["n_members"] == 3 and info["lattice_tile"] in (0, 1)
+    # one batched launch per slot: max(m) slots in each of the free and link phases
+    assert info["batched_launches"] == rounds * 2 * max(cp.m for cp in cps)
+    for g, s_ in zip(members, solo):
+        for a, b_ in [(g.u(), s_.u()), (g.v(), s_.v()), (g.uf(), s_.uf()), (g.vf(), s_.vf()),
+                      (g.lam(), s_.lam()), (g.mu(), s_.mu())]:
+            assert np.array_equal(a, b_)
+        assert g.residual() <= 1e-5
+        st = P.pdmts_get_stats(g.ctx)
+        assert st["coarse_steps"] == rounds
+
+
+def test_batch_rejects_unsupported_members(fresh):
+    cp = W.small_coupled(m=2, n_coarse=2)
+    g64 = GpuMTS(fresh(), cp, P.PDMTS_FP64)
+    with pytest.raises(P.PdmtsError) as e:
+        P.mts_batch_create([g64.ctx])
+    assert e.value.code == -8  # PDMTS_ERR_UNSUPPORTED
+    g = GpuMTS(fresh(), cp, P.PDMTS_FP32_BULK)
+    with pytest.raises(P.PdmtsError):
+        P.mts_batch_create([g.ctx, g.ctx])
