@@ -309,6 +309,8 @@ def run_batch(args, rank, world, local_rank):
                    (i1["batched_launches"] - i0["batched_launches"]) // max(args.steps, 1),
                    "work_items_per_round": (i1["work_items"] - i0["work_items"]) // max(args.steps, 1),
                    "setup_s": round(t_setup, 2), "l2": "flushed between timed rounds (256 MB write)",
+                   "last_round_phase_ms": dict(zip(["lambda0_forces", "free_substeps", "lambda_m", "link_substeps",
+                                                    "corrections"], [round(x, 3) for x in i1["last_round_ms"]])),
                    "per_instance_loop_value": solo_value, "batch_over_loop": value / solo_value},
         "coarse_steps_per_s": d["coarse_steps"] / (batch_ms * 1e-3),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,

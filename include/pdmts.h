@@ -303,6 +303,10 @@ typedef struct {
     int64_t rounds;            /* rounds advanced                            */
     int64_t work_items;        /* (member, tile) items launched              */
     int64_t batched_launches;  /* batched substep launches                   */
+    /* phases of the last round on the batch stream (ms; blocks until it ends):
+     * [0] interface forces of lambda_0, [1] free PD substeps, [2] lambda_m and
+     * link-problem start, [3] link PD substeps, [4] corrections and flags */
+    double last_round_ms[5];
 } pdmts_batch_info;
 int mts_batch_info(const pdmts_batch *batch, pdmts_batch_info *info);
 int mts_batch_destroy(pdmts_batch *batch);

@@ -662,8 +662,10 @@ static int fe_assemble(pdmts_fem *fe, const std::vector<BandDesc> &bands, int ki
             rs += std::fabs(kv.second);
             ++e;
         }
+        // padding (zero values) repeats the node's x dof in both of its rows, so
+        // the x and y rows of a node keep one column list
         for (; e < fe->W; ++e)
-            fe->col[(size_t)i * fe->W + e] = (int32_t)i;
+            fe->col[(size_t)i * fe->W + e] = (int32_t)(i < n ? i : i - n);
         gersh = std::max(gersh, rs / fe->mass[(size_t)i]);
     }
     fe->paired_rows = true;
@@ -1561,8 +1563,8 @@ int mts_time_changed(pdmts_ctx *ctx)
 //   step_free_begin  s: fork mark, interface force of lambda_0 (Eq. 48a);
 //   (m free PD substeps with factor 1 - j/m)
 //   step_fe_free     fs: FE free step (Eq. 47a);
-//   step_interface   s: join, lambda_m = (-H)^-1 (G_FE v_FE - G_PD v_PD) (Eq. 49),
-//                    then the FE correction on fs (Eq. 47b);
+//   step_lambda      s: join, lambda_m = (-H)^-1 (G_FE v_FE - G_PD v_PD) (Eq. 49);
+//   step_fe_link     fs: the FE correction (Eq. 47b);
 //   step_link_begin  s: interface force of lambda_m, W_0 = 0 (Eq. 48b);
 //   (m link PD substeps with factor j/m)
 //   step_finish      s: U += W, rebuild flag, lambda_0 <- lambda_m, join fs.
@@ -1630,13 +1632,11 @@ static int step_fe_free(pdmts_arl *A, cudaStream_t fs, bool graphs, int64_t *lau
     return PDMTS_OK;
 }
 
-static int step_interface(pdmts_arl *A, cudaStream_t s, cudaStream_t fs, bool graphs, int64_t *launches)
+static int step_lambda(pdmts_arl *A, cudaStream_t s, int64_t *launches)
 {
-    pdmts_ctx *ctx = A->ctx;
     pdmts_pd *pd = A->pd;
     pdmts_fem *fe = A->fe;
     const bool f64 = pd->precision == PDMTS_FP64;
-    const double dtf = ctx->m_ratio * ctx->dt_pd;
     PDMTS_CUDA_TRY(cudaStreamWaitEvent(s, A->ev_join, 0));
     const float4 *v4 = f64 ? nullptr : pd->f_v4.p;
     const float2 *v2 = f64 ? nullptr : pd->f_v2.p;
@@ -1648,7 +1648,14 @@ static int step_interface(pdmts_arl *A, cudaStream_t s, cudaStream_t fs, bool gr
     // the multiplier solve stays FP64 in every precision
     k_gemv_rows<<<blocks(A->nlam * 32), 256, 0, s>>>(A->nlam, A->d_Hneg_inv.p, A->d_y.p, 1.0, A->d_lam.p);
     *launches += 2;
-    // FE correction U = V + Y lambda_m on the FE stream
+    return PDMTS_OK;
+}
+
+// FE correction U = V + Y lambda_m on the FE stream, after lambda_m on s.
+static int step_fe_link(pdmts_arl *A, cudaStream_t s, cudaStream_t fs, bool graphs, int64_t *launches)
+{
+    pdmts_ctx *ctx = A->ctx;
+    const double dtf = ctx->m_ratio * ctx->dt_pd;
     PDMTS_CUDA_TRY(cudaEventRecord(A->ev_fork, s));
     PDMTS_CUDA_TRY(cudaStreamWaitEvent(fs, A->ev_fork, 0));
     if (graphs)
@@ -1747,8 +1754,9 @@ static int coarse_step(pdmts_arl *A)
     PDMTS_TRY(step_fe_free(A, A->fe_stream, true, &launches));
     PDMTS_CUDA_TRY(cudaStreamWaitEvent(s, A->ev_join, 0));
     PDMTS_TRY(ctx->mark(&ph[1]));
-    PDMTS_TRY(step_interface(A, s, A->fe_stream, true, &launches));
+    PDMTS_TRY(step_lambda(A, s, &launches));
     PDMTS_TRY(ctx->mark(&ph[2]));
+    PDMTS_TRY(step_fe_link(A, s, A->fe_stream, true, &launches));
     PDMTS_TRY(step_link_begin(A, A->d_lam.p, s, &launches));
     PDMTS_TRY(pd_run_chain(pd, m, 2, A->theta_link.data(), s, true));
     PDMTS_TRY(ctx->mark(&ph[3]));
@@ -1781,8 +1789,10 @@ struct pdmts_batch {
     int device = 0;
     std::vector<pdmts_ctx *> members;
     cudaStream_t s = nullptr;               // batched substeps and per-member interface work
-    std::vector<cudaStream_t> fe_streams;   // FE steps, members round-robin
-    cudaEvent_t ev_in = nullptr, ev_end = nullptr;
+    std::vector<cudaStream_t> fe_streams;   // per-member work, members round-robin
+    std::vector<cudaEvent_t> ev_lane;       // one per member stream: its part of a phase is done
+    cudaEvent_t ev_in = nullptr, ev_end = nullptr, ev_phase = nullptr;
+    cudaEvent_t ev_t[6] = {};               // marks of the last round (phase times)
     int tile = -1;                          // batched lattice tile configuration (-1: tune)
     // argument blocks and work lists of one phase's slots: host staging (pinned) and device copies
     Lat2DArgs *h_args = nullptr;
@@ -1792,6 +1802,22 @@ struct pdmts_batch {
     int64_t cap_args = 0, cap_work = 0;
     int64_t rounds = 0, work_items = 0, batched_launches = 0;
     bool pending = false;                   // a round is in flight (staging in use)
+    // the argument blocks and work lists of a phase depend only on what the key
+    // records (buffer parities, schedules, windows, pointers): built once, kept
+    struct Plan {
+        std::vector<uint64_t> key;
+        Lat2DArgs *d_args = nullptr;
+        int2 *d_work = nullptr;
+        std::vector<int64_t> arg_off, work_off;
+    };
+    std::vector<Plan> plans;
+    struct RoundGraph {
+        std::vector<uint64_t> key;
+        cudaGraphExec_t exec = nullptr;
+        std::vector<struct MemberSnap> after, delta;
+        int64_t work_items = 0, batched_launches = 0;
+    };
+    std::vector<RoundGraph> graphs;
 };
 
 static void batch_free_buffers(pdmts_batch *b)
@@ -1823,56 +1849,126 @@ static int batch_reserve(pdmts_batch *b, int64_t nargs, int64_t nwork)
     return PDMTS_OK;
 }
 
-// Build the argument blocks and work lists of the slots of one phase (free or
-// link) of the current round, advancing each member's buffer parity as its
-// substeps are planned; upload them and launch the slots on b->s.
+static std::vector<uint64_t> batch_plan_key(const pdmts_batch *b, bool link)
+{
+    std::vector<uint64_t> k{(uint64_t)link, (uint64_t)b->tile};
+    for (pdmts_ctx *c : b->members) {
+        const pdmts_pd *pd = c->arl->pd;
+        double dt = c->dt_pd;
+        uint64_t dtb;
+        std::memcpy(&dtb, &dt, sizeof dtb);
+        k.insert(k.end(), {(uint64_t)(link ? pd->lk_cur : pd->cur), (uint64_t)c->m_ratio, dtb,
+                           (uint64_t)pd->link_win_lo[0], (uint64_t)pd->link_win_n[0], (uint64_t)pd->link_win_lo[1],
+                           (uint64_t)pd->link_win_n[1], (uint64_t)pd->has_g, (uint64_t)pd->breaking,
+                           (uint64_t)(uintptr_t)pd->f_u4[0].p, (uint64_t)(uintptr_t)pd->f_u4[1].p,
+                           (uint64_t)(uintptr_t)pd->lk_u4[0].p, (uint64_t)(uintptr_t)pd->f_wb.p});
+    }
+    return k;
+}
+
+static void batch_free_plans(pdmts_batch *b)
+{
+    for (auto &p : b->plans) {
+        if (p.d_args) cudaFree(p.d_args);
+        if (p.d_work) cudaFree(p.d_work);
+    }
+    b->plans.clear();
+}
+
+// The slots of one phase (free or link) of the current round: one batched
+// launch per slot over the members whose chain has that substep, with the
+// arguments each member's own substep would take. Each member's buffer parity
+// and counters advance as if it had run the substeps itself.
+static int batch_plan(pdmts_batch *b, bool link, pdmts_batch::Plan **out)
+{
+    const int nm = (int)b->members.size();
+    int M = 0;
+    for (pdmts_ctx *c : b->members)
+        M = std::max(M, c->m_ratio);
+    const std::vector<uint64_t> key = batch_plan_key(b, link);
+    pdmts_batch::Plan *plan = nullptr;
+    for (auto &p : b->plans)
+        if (p.key == key)
+            plan = &p;
+    if (!plan) {
+        if (b->plans.size() >= 8)
+            batch_free_plans(b);
+        // simulate the parities on copies of the members' counters, then put them back
+        std::vector<int> cur0((size_t)nm);
+        for (int i = 0; i < nm; ++i) {
+            const pdmts_pd *pd = b->members[(size_t)i]->arl->pd;
+            cur0[(size_t)i] = link ? pd->lk_cur : pd->cur;
+        }
+        pdmts_batch::Plan p;
+        p.key = key;
+        p.arg_off.assign((size_t)M + 1, 0);
+        p.work_off.assign((size_t)M + 1, 0);
+        std::vector<Lat2DArgs> args;
+        std::vector<int2> work;
+        for (int j = 0; j < M; ++j) {
+            const int64_t a0 = (int64_t)args.size();
+            for (int i = 0; i < nm; ++i) {
+                pdmts_ctx *c = b->members[(size_t)i];
+                if (j >= c->m_ratio)
+                    continue;
+                pdmts_arl *A = c->arl;
+                pdmts_pd *pd = A->pd;
+                int &cur = link ? pd->lk_cur : pd->cur;
+                cur = (cur0[(size_t)i] + j) & 1;
+                const double theta = link ? A->theta_link[(size_t)j] : A->theta_free[(size_t)j];
+                const F32NodeArgs N = pd->f32_node_args(false, theta, link);
+                Lat2DArgs L = pd->lattice_args(N, link ? pd->d_mask_link.p : pd->d_mask.p, link);
+                L.tile = b->tile;
+                const int ntiles = lattice2d_batch_prepare(L, b->tile);
+                if (ntiles < 0)
+                    return fail(PDMTS_ERR_UNSUPPORTED, "batch: tile configuration %d cannot be batched", b->tile);
+                const int slot_index = (int)((int64_t)args.size() - a0);
+                for (int t = 0; t < ntiles; ++t)
+                    work.push_back(make_int2(slot_index, t));
+                args.push_back(L);
+            }
+            p.arg_off[(size_t)j + 1] = (int64_t)args.size();
+            p.work_off[(size_t)j + 1] = (int64_t)work.size();
+        }
+        for (int i = 0; i < nm; ++i) {
+            pdmts_pd *pd = b->members[(size_t)i]->arl->pd;
+            (link ? pd->lk_cur : pd->cur) = cur0[(size_t)i];
+        }
+        if (cudaMalloc(&p.d_args, sizeof(Lat2DArgs) * std::max<size_t>(args.size(), 1)) != cudaSuccess ||
+            cudaMalloc(&p.d_work, sizeof(int2) * std::max<size_t>(work.size(), 1)) != cudaSuccess) {
+            if (p.d_args) cudaFree(p.d_args);
+            if (p.d_work) cudaFree(p.d_work);
+            return fail(PDMTS_ERR_NOMEM, "batch: plan of %zu work items", work.size());
+        }
+        PDMTS_CUDA_TRY(cudaMemcpy(p.d_args, args.data(), sizeof(Lat2DArgs) * args.size(), cudaMemcpyHostToDevice));
+        PDMTS_CUDA_TRY(cudaMemcpy(p.d_work, work.data(), sizeof(int2) * work.size(), cudaMemcpyHostToDevice));
+        b->plans.push_back(std::move(p));
+        plan = &b->plans.back();
+    }
+    *out = plan;
+    return PDMTS_OK;
+}
+
 static int batch_phase(pdmts_batch *b, bool link)
 {
     const int nm = (int)b->members.size();
     int M = 0;
     for (pdmts_ctx *c : b->members)
         M = std::max(M, c->m_ratio);
-    // count first: one argument block per (slot, active member), its tiles
-    std::vector<int64_t> arg_off((size_t)M + 1, 0), work_off((size_t)M + 1, 0);
-    std::vector<Lat2DArgs> args;
-    std::vector<int2> work;
+    pdmts_batch::Plan *plan = nullptr;
+    PDMTS_TRY(batch_plan(b, link, &plan));
+    const bool pmb = b->members[0]->arl->pd->force_kind == PDMTS_FORCE_PMB;
     for (int j = 0; j < M; ++j) {
-        for (int i = 0; i < nm; ++i) {
-            pdmts_ctx *c = b->members[(size_t)i];
-            if (j >= c->m_ratio)
-                continue;
-            pdmts_arl *A = c->arl;
-            pdmts_pd *pd = A->pd;
-            const double theta = link ? A->theta_link[(size_t)j] : A->theta_free[(size_t)j];
-            const F32NodeArgs N = pd->f32_node_args(false, theta, link);
-            Lat2DArgs L = pd->lattice_args(N, link ? pd->d_mask_link.p : pd->d_mask.p, link);
-            L.tile = b->tile;
-            const int ntiles = lattice2d_batch_prepare(L, b->tile);
-            if (ntiles < 0)
-                return fail(PDMTS_ERR_UNSUPPORTED, "batch: tile configuration %d cannot be batched", b->tile);
-            const int slot_index = (int)(args.size() - (size_t)arg_off[(size_t)j]);
-            for (int t = 0; t < ntiles; ++t)
-                work.push_back(make_int2(slot_index, t));
-            args.push_back(L);
-            pd->substep_done(false, link);
-        }
-        arg_off[(size_t)j + 1] = (int64_t)args.size();
-        work_off[(size_t)j + 1] = (int64_t)work.size();
-    }
-    PDMTS_TRY(batch_reserve(b, (int64_t)args.size(), (int64_t)work.size()));
-    std::memcpy(b->h_args, args.data(), sizeof(Lat2DArgs) * args.size());
-    std::memcpy(b->h_work, work.data(), sizeof(int2) * work.size());
-    PDMTS_CUDA_TRY(cudaMemcpyAsync(b->d_args, b->h_args, sizeof(Lat2DArgs) * args.size(), cudaMemcpyHostToDevice, b->s));
-    PDMTS_CUDA_TRY(cudaMemcpyAsync(b->d_work, b->h_work, sizeof(int2) * work.size(), cudaMemcpyHostToDevice, b->s));
-    const bool pmb = b->members[0]->pd->force_kind == PDMTS_FORCE_PMB;
-    for (int j = 0; j < M; ++j) {
-        const int nwork = (int)(work_off[(size_t)j + 1] - work_off[(size_t)j]);
-        cudaError_t e = launch_lattice2d_batch(b->d_args + arg_off[(size_t)j], b->d_work + work_off[(size_t)j], nwork,
-                                               b->tile, pmb, b->s);
+        const int nwork = (int)(plan->work_off[(size_t)j + 1] - plan->work_off[(size_t)j]);
+        cudaError_t e = launch_lattice2d_batch(plan->d_args + plan->arg_off[(size_t)j],
+                                               plan->d_work + plan->work_off[(size_t)j], nwork, b->tile, pmb, b->s);
         if (e != cudaSuccess)
             return fail(PDMTS_ERR_CUDA, "batched substep: %s", cudaGetErrorString(e));
         b->batched_launches += 1;
         b->work_items += nwork;
+        for (int i = 0; i < nm; ++i)
+            if (j < b->members[(size_t)i]->m_ratio)
+                b->members[(size_t)i]->arl->pd->substep_done(false, link);
     }
     return PDMTS_OK;
 }
@@ -1942,36 +2038,216 @@ static int batch_tune(pdmts_batch *b)
     return PDMTS_OK;
 }
 
-static int batch_round(pdmts_batch *b)
+// Member streams wait for the batch stream (ev_phase just recorded on b->s),
+// or the batch stream for every member stream.
+static int batch_fan_out(pdmts_batch *b)
+{
+    PDMTS_CUDA_TRY(cudaEventRecord(b->ev_phase, b->s));
+    for (cudaStream_t f : b->fe_streams)
+        PDMTS_CUDA_TRY(cudaStreamWaitEvent(f, b->ev_phase, 0));
+    return PDMTS_OK;
+}
+static int batch_fan_in(pdmts_batch *b)
+{
+    for (size_t k = 0; k < b->fe_streams.size(); ++k) {
+        PDMTS_CUDA_TRY(cudaEventRecord(b->ev_lane[k], b->fe_streams[k]));
+        PDMTS_CUDA_TRY(cudaStreamWaitEvent(b->s, b->ev_lane[k], 0));
+    }
+    return PDMTS_OK;
+}
+
+// One round: per member on its stream (members round-robin over the member
+// streams) the small coupling kernels, and on the batch stream the batched
+// substep slots; the FE solves run beside the PD slots.
+// The round's work; enqueued only while b->s is captured (the phase marks
+// are external event nodes, so the events can be read after a replay).
+static int batch_enqueue_round(pdmts_batch *b, bool graphs)
 {
     const size_t nm = b->members.size();
     const size_t K = b->fe_streams.size();
-    // the previous round must have ended: staging reuse and rebuild flags
-    if (b->pending) {
-        PDMTS_CUDA_TRY(cudaEventSynchronize(b->ev_end));
-        b->pending = false;
-    }
     std::vector<int64_t> launches(nm, 0);
+    auto lane = [&](size_t i) { return b->fe_streams[i % K]; };
+    PDMTS_CUDA_TRY(cudaEventRecordWithFlags(b->ev_t[0], b->s, cudaEventRecordExternal));
+    // interface forces of lambda_0, then the FE free steps (these do not hold up the PD slots)
+    PDMTS_TRY(batch_fan_out(b));
+    for (size_t i = 0; i < nm; ++i)
+        PDMTS_TRY(step_free_begin(b->members[i]->arl, lane(i), &launches[i]));
+    PDMTS_TRY(batch_fan_in(b));
+    PDMTS_CUDA_TRY(cudaEventRecordWithFlags(b->ev_t[1], b->s, cudaEventRecordExternal));
+    for (size_t i = 0; i < nm; ++i)
+        PDMTS_TRY(step_fe_free(b->members[i]->arl, lane(i), graphs, &launches[i]));
+    PDMTS_TRY(batch_phase(b, false));
+    PDMTS_CUDA_TRY(cudaEventRecordWithFlags(b->ev_t[2], b->s, cudaEventRecordExternal));
+    // lambda_m and the link-problem start, then the FE corrections
+    PDMTS_TRY(batch_fan_out(b));
+    for (size_t i = 0; i < nm; ++i) {
+        pdmts_arl *A = b->members[i]->arl;
+        PDMTS_TRY(step_lambda(A, lane(i), &launches[i]));
+        PDMTS_TRY(step_link_begin(A, A->d_lam.p, lane(i), &launches[i]));
+    }
+    PDMTS_TRY(batch_fan_in(b));
+    PDMTS_CUDA_TRY(cudaEventRecordWithFlags(b->ev_t[3], b->s, cudaEventRecordExternal));
+    for (size_t i = 0; i < nm; ++i)
+        PDMTS_TRY(step_fe_link(b->members[i]->arl, lane(i), lane(i), graphs, &launches[i]));
+    PDMTS_TRY(batch_phase(b, true));
+    PDMTS_CUDA_TRY(cudaEventRecordWithFlags(b->ev_t[4], b->s, cudaEventRecordExternal));
+    // corrections and rebuild flags
+    PDMTS_TRY(batch_fan_out(b));
+    for (size_t i = 0; i < nm; ++i) {
+        PDMTS_TRY(step_finish(b->members[i]->arl, lane(i), &launches[i]));
+        b->members[i]->stats.kernel_launches += launches[i];
+    }
+    PDMTS_TRY(batch_fan_in(b));
+    PDMTS_CUDA_TRY(cudaEventRecordWithFlags(b->ev_t[5], b->s, cudaEventRecordExternal));
+    return PDMTS_OK;
+}
+
+// Host-side state a round changes: buffer parities, counters, flags.
+struct MemberSnap {
+    int cur = 0, lk_cur = 0;
+    int64_t steps_done = 0;
+    pdmts_stats stats{};
+    bool flag_pending = false;
+};
+static MemberSnap member_snap(const pdmts_ctx *c)
+{
+    MemberSnap m;
+    m.cur = c->arl->pd->cur;
+    m.lk_cur = c->arl->pd->lk_cur;
+    m.steps_done = c->arl->pd->steps_done;
+    m.stats = c->stats;
+    m.flag_pending = c->arl->flag_pending;
+    return m;
+}
+
+static std::vector<uint64_t> batch_round_key(const pdmts_batch *b)
+{
+    std::vector<uint64_t> k = batch_plan_key(b, false);
+    for (pdmts_ctx *c : b->members)
+        k.push_back((uint64_t)c->arl->fe->keff_version);
+    return k;
+}
+
+// One round: per member on its stream (members round-robin over the member
+// streams) the small coupling kernels, and on the batch stream the batched
+// substep slots; the FE solves run beside the PD slots. The whole round is
+// captured once per key (buffer parities, schedules) as a CUDA graph and
+// replayed; the host applies the round's bookkeeping to the members.
+// Wait for the last round and take its rebuild flags (the flag copies ran
+// inside the round; its end event covers them).
+static int batch_settle(pdmts_batch *b)
+{
+    if (!b->pending)
+        return PDMTS_OK;
+    PDMTS_CUDA_TRY(cudaEventSynchronize(b->ev_end));
+    b->pending = false;
+    for (pdmts_ctx *c : b->members) {
+        pdmts_arl *A = c->arl;
+        if (A->flag_pending && *A->h_changed)
+            A->H_valid = false;
+        A->flag_pending = false;
+    }
+    return PDMTS_OK;
+}
+
+static int batch_round(pdmts_batch *b)
+{
+    const size_t nm = b->members.size();
+    PDMTS_TRY(batch_settle(b));
     for (size_t i = 0; i < nm; ++i) {
         pdmts_arl *A = b->members[i]->arl;
         if (A->pd->lattice_tile < 0)
             A->pd->lattice_tile = b->tile;  // the members' own substeps use the batch's tile (no solo tuning)
         PDMTS_TRY(step_prepare(A, b->s));
     }
-    for (size_t i = 0; i < nm; ++i)
-        PDMTS_TRY(step_free_begin(b->members[i]->arl, b->s, &launches[i]));
-    for (size_t i = 0; i < nm; ++i)
-        PDMTS_TRY(step_fe_free(b->members[i]->arl, b->fe_streams[i % K], true, &launches[i]));
-    PDMTS_TRY(batch_phase(b, false));
-    for (size_t i = 0; i < nm; ++i)
-        PDMTS_TRY(step_interface(b->members[i]->arl, b->s, b->fe_streams[i % K], true, &launches[i]));
-    for (size_t i = 0; i < nm; ++i)
-        PDMTS_TRY(step_link_begin(b->members[i]->arl, b->members[i]->arl->d_lam.p, b->s, &launches[i]));
-    PDMTS_TRY(batch_phase(b, true));
-    for (size_t i = 0; i < nm; ++i) {
-        PDMTS_TRY(step_finish(b->members[i]->arl, b->s, &launches[i]));
-        b->members[i]->stats.kernel_launches += launches[i];
+    // both phases' plans exist before any capture (the link phase starts at parity 0)
+    pdmts_batch::Plan *plan = nullptr;
+    PDMTS_TRY(batch_plan(b, false, &plan));
+    {
+        std::vector<int> lk(nm);
+        for (size_t i = 0; i < nm; ++i) {
+            lk[i] = b->members[i]->arl->pd->lk_cur;
+            b->members[i]->arl->pd->lk_cur = 0;
+        }
+        const int r = batch_plan(b, true, &plan);
+        for (size_t i = 0; i < nm; ++i)
+            b->members[i]->arl->pd->lk_cur = lk[i];
+        PDMTS_TRY(r);
     }
+    const std::vector<uint64_t> key = batch_round_key(b);
+    pdmts_batch::RoundGraph *g = nullptr;
+    for (auto &rg : b->graphs)
+        if (rg.key == key)
+            g = &rg;
+    if (!g) {
+        if (b->graphs.size() >= 4) {
+            for (auto &rg : b->graphs)
+                cudaGraphExecDestroy(rg.exec);
+            b->graphs.clear();
+        }
+        std::vector<MemberSnap> s0(nm);
+        for (size_t i = 0; i < nm; ++i)
+            s0[i] = member_snap(b->members[i]);
+        const int64_t wi0 = b->work_items, bl0 = b->batched_launches;
+        cudaGraph_t graph = nullptr;
+        PDMTS_CUDA_TRY(cudaStreamBeginCapture(b->s, cudaStreamCaptureModeThreadLocal));
+        const int r = batch_enqueue_round(b, false);
+        const cudaError_t ce = cudaStreamEndCapture(b->s, &graph);
+        pdmts_batch::RoundGraph rg;
+        rg.key = key;
+        rg.work_items = b->work_items - wi0;
+        rg.batched_launches = b->batched_launches - bl0;
+        b->work_items = wi0;
+        b->batched_launches = bl0;
+        for (size_t i = 0; i < nm; ++i) {
+            pdmts_ctx *c = b->members[i];
+            const MemberSnap s1 = member_snap(c);
+            rg.after.push_back(s1);
+            MemberSnap d = s1;
+            d.steps_done -= s0[i].steps_done;
+            d.stats.pd_substeps -= s0[i].stats.pd_substeps;
+            d.stats.bond_updates -= s0[i].stats.bond_updates;
+            d.stats.coarse_steps -= s0[i].stats.coarse_steps;
+            d.stats.bonds_broken -= s0[i].stats.bonds_broken;
+            d.stats.kernel_launches -= s0[i].stats.kernel_launches;
+            d.stats.graph_launches -= s0[i].stats.graph_launches;
+            rg.delta.push_back(d);
+            c->arl->pd->cur = s0[i].cur;
+            c->arl->pd->lk_cur = s0[i].lk_cur;
+            c->arl->pd->steps_done = s0[i].steps_done;
+            c->stats = s0[i].stats;
+            c->arl->flag_pending = s0[i].flag_pending;
+        }
+        if (r != PDMTS_OK) {
+            if (graph)
+                cudaGraphDestroy(graph);
+            return r;
+        }
+        if (ce != cudaSuccess)
+            return fail(PDMTS_ERR_CUDA, "batch round capture: %s", cudaGetErrorString(ce));
+        const cudaError_t ie = cudaGraphInstantiate(&rg.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ie != cudaSuccess)
+            return fail(PDMTS_ERR_CUDA, "batch round graph: %s", cudaGetErrorString(ie));
+        b->graphs.push_back(std::move(rg));
+        g = &b->graphs.back();
+    }
+    PDMTS_CUDA_TRY(cudaGraphLaunch(g->exec, b->s));
+    for (size_t i = 0; i < nm; ++i) {
+        pdmts_ctx *c = b->members[i];
+        const MemberSnap &a = g->after[i], &d = g->delta[i];
+        c->arl->pd->cur = a.cur;
+        c->arl->pd->lk_cur = a.lk_cur;
+        c->arl->pd->steps_done += d.steps_done;
+        c->stats.pd_substeps += d.stats.pd_substeps;
+        c->stats.bond_updates += d.stats.bond_updates;
+        c->stats.coarse_steps += d.stats.coarse_steps;
+        c->stats.kernel_launches += d.stats.kernel_launches;
+        c->stats.graph_launches += d.stats.graph_launches;
+        c->arl->flag_pending = a.flag_pending;
+    }
+    b->work_items += g->work_items;
+    b->batched_launches += g->batched_launches;
     PDMTS_CUDA_TRY(cudaEventRecord(b->ev_end, b->s));
     b->pending = true;
     b->rounds += 1;
@@ -2013,13 +2289,20 @@ extern "C" int mts_batch_create(int n_members, pdmts_ctx *const *members, pdmts_
     bool ok = cudaStreamCreateWithFlags(&b->s, cudaStreamNonBlocking) == cudaSuccess &&
               cudaDeviceGetStreamPriorityRange(&lo, &hi) == cudaSuccess &&
               cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) == cudaSuccess &&
-              cudaEventCreateWithFlags(&b->ev_end, cudaEventDisableTiming) == cudaSuccess;
+              cudaEventCreateWithFlags(&b->ev_end, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&b->ev_phase, cudaEventDisableTiming) == cudaSuccess;
+    for (int k = 0; k < 6 && ok; ++k)
+        ok = cudaEventCreate(&b->ev_t[k]) == cudaSuccess;
     const int K = std::min(n_members, 8);
     for (int k = 0; k < K && ok; ++k) {
         cudaStream_t fs = nullptr;
+        cudaEvent_t ev = nullptr;
         ok = cudaStreamCreateWithPriority(&fs, cudaStreamNonBlocking, hi) == cudaSuccess;
         if (ok)
             b->fe_streams.push_back(fs);
+        ok = ok && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess;
+        if (ok)
+            b->ev_lane.push_back(ev);
     }
     if (!ok) {
         mts_batch_destroy(b);
@@ -2044,8 +2327,10 @@ extern "C" int mts_batch_advance(pdmts_batch *b, int64_t n_rounds)
         PDMTS_CUDA_TRY(cudaStreamWaitEvent(b->s, b->ev_in, 0));
     }
     PDMTS_TRY(batch_tune(b));
+    PDMTS_TRY(batch_settle(b));
     for (int64_t k = 0; k < n_rounds; ++k)
         PDMTS_TRY(batch_round(b));
+    PDMTS_TRY(batch_settle(b));
     // members' own streams (and through them their users' streams) follow the batch
     PDMTS_CUDA_TRY(cudaEventRecord(b->ev_in, b->s));
     for (pdmts_ctx *c : b->members) {
@@ -2065,6 +2350,17 @@ extern "C" int mts_batch_info(const pdmts_batch *b, pdmts_batch_info *info)
     info->rounds = b->rounds;
     info->work_items = b->work_items;
     info->batched_launches = b->batched_launches;
+    for (int k = 0; k < 5; ++k)
+        info->last_round_ms[k] = 0.0;
+    if (b->rounds > 0) {
+        PDMTS_CUDA_TRY(cudaSetDevice(b->device));
+        PDMTS_CUDA_TRY(cudaEventSynchronize(b->ev_t[5]));
+        for (int k = 0; k < 5; ++k) {
+            float ms = 0.f;
+            PDMTS_CUDA_TRY(cudaEventElapsedTime(&ms, b->ev_t[k], b->ev_t[k + 1]));
+            info->last_round_ms[k] = ms;
+        }
+    }
     return PDMTS_OK;
 }
 
@@ -2080,9 +2376,19 @@ extern "C" int mts_batch_destroy(pdmts_batch *b)
         cudaStreamDestroy(fs);
     }
     batch_free_buffers(b);
+    batch_free_plans(b);
+    for (auto &rg : b->graphs)
+        if (rg.exec)
+            cudaGraphExecDestroy(rg.exec);
     if (b->s) cudaStreamDestroy(b->s);
     if (b->ev_in) cudaEventDestroy(b->ev_in);
     if (b->ev_end) cudaEventDestroy(b->ev_end);
+    if (b->ev_phase) cudaEventDestroy(b->ev_phase);
+    for (cudaEvent_t e : b->ev_t)
+        if (e)
+            cudaEventDestroy(e);
+    for (cudaEvent_t e : b->ev_lane)
+        cudaEventDestroy(e);
     delete b;
     return PDMTS_OK;
 }

@@ -415,7 +415,7 @@ def arlequin_info(arl):
 
 class BatchInfo(C.Structure):
     _fields_ = [("n_members", C.c_int32), ("lattice_tile", C.c_int32), ("rounds", C.c_int64),
-                ("work_items", C.c_int64), ("batched_launches", C.c_int64)]
+                ("work_items", C.c_int64), ("batched_launches", C.c_int64), ("last_round_ms", C.c_double * 5)]
 
 
 def mts_batch_create(members):
@@ -433,7 +433,9 @@ def mts_batch_advance(batch, n_rounds):
 def mts_batch_info(batch):
     s = BatchInfo()
     _check(load().mts_batch_info(batch, C.byref(s)), "mts_batch_info")
-    return {k: getattr(s, k) for k, _ in BatchInfo._fields_}
+    d = {k: getattr(s, k) for k, _ in BatchInfo._fields_}
+    d["last_round_ms"] = list(d["last_round_ms"])
+    return d
 
 
 def mts_batch_destroy(batch):
