@@ -284,9 +284,11 @@ int arlequin_info(pdmts_arl *arl, pdmts_arl_info *info);
 /* A batch of n_members coupled problems advanced together. Every member is a
  * context with a PD subdomain in PDMTS_FP32_BULK on a 2D lattice, an FE
  * subdomain, an Arlequin coupling and mts_set_time called; all on one device
- * and with one force law; no context twice. The members keep their own sizes,
- * loads, cracks and ratios m. The batch does not own them: destroy the batch
- * before its members. PDMTS_ERR_STATE / _UNSUPPORTED / _ARG otherwise. */
+ * and with one force law; no context twice; none already in a batch. The
+ * members keep their own sizes, loads, cracks and ratios m and may still be
+ * advanced or read alone between batch calls. The batch does not own them; a
+ * member destroyed first leaves the batch. PDMTS_ERR_STATE / _UNSUPPORTED /
+ * _ARG otherwise. */
 int mts_batch_create(int n_members, pdmts_ctx *const *members, pdmts_batch **batch);
 /* Advance every member by n_rounds of its own coarse steps (Algorithm 1,
  * m_i PD substeps each in the free and in the link problem). The PD substeps
@@ -303,9 +305,14 @@ typedef struct {
     int64_t rounds;            /* rounds advanced                            */
     int64_t work_items;        /* (member, tile) items launched              */
     int64_t batched_launches;  /* batched substep launches                   */
+    int64_t kernel_launches;   /* all kernels the batch launched (batched PD
+                                  substeps, batched FE solves, per-member
+                                  coupling kernels)                          */
     /* phases of the last round on the batch stream (ms; blocks until it ends):
-     * [0] interface forces of lambda_0, [1] free PD substeps, [2] lambda_m and
-     * link-problem start, [3] link PD substeps, [4] corrections and flags */
+     * [0] interface forces of lambda_0, [1] free PD substeps (the FE free
+     * steps run beside them), [2] lambda_m and link-problem start, [3] link
+     * PD substeps (the FE corrections beside them), [4] corrections, flags
+     * and the end of the FE corrections */
     double last_round_ms[5];
 } pdmts_batch_info;
 int mts_batch_info(const pdmts_batch *batch, pdmts_batch_info *info);

@@ -72,7 +72,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
     objs = [os.path.join(OBJ, os.path.basename(s) + ".o") for s in sources()]
     if force or jobs or not os.path.exists(LIB):
         tmp = LIB + f".tmp{os.getpid()}"
-        r = subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
+        libdir = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc))), "lib64")
+        r = subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-L", libdir, "-lcusolver",
+                            "-Xlinker", "-rpath=" + libdir], capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")
         os.replace(tmp, LIB)

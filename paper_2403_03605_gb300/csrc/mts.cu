@@ -21,6 +21,8 @@
 #include <array>
 #include <cmath>
 #include <cstring>
+
+#include <cusolverDn.h>
 #include <map>
 #include <new>
 
@@ -114,6 +116,7 @@ struct pdmts_fem {
     // Chebyshev schedule for K_eff (depends on dt_FE); version counts changes
     double keff_dt = -1, cheb_theta = 0, cheb_delta = 0;
     std::vector<double> cheb_c1, cheb_c2;
+    DevArr<double> d_cheb;            // the schedule on the device: c1[it], then c2[it]
     int64_t keff_version = 0;
     bool paired_rows = false;         // x and y rows of every node share one column list
     GraphSlot g_free, g_link;         // captured free step and link correction
@@ -145,7 +148,7 @@ struct pdmts_fem {
         g_link.reset();
         release(d_col); release(d_K); release(d_Keff); release(d_Minv); release(d_P);
         release(d_u); release(d_v); release(d_a); release(d_ut); release(d_vt); release(d_b); release(d_r);
-        release(d_d[0]); release(d_d[1]); release(d_aw); release(d_bw);
+        release(d_d[0]); release(d_d[1]); release(d_cheb); release(d_aw); release(d_bw);
     }
 };
 
@@ -198,10 +201,9 @@ struct pdmts_arl {
     std::vector<int64_t> gfeT_ptr;
     std::vector<int32_t> gfeT_k;
     std::vector<double> gfeT_val;
-    DevArr<int32_t> d_gfe_col, d_gpd_col, d_ov_node, d_ov_k, d_owner, d_gfeT_k;
+    DevArr<int32_t> d_gfe_col, d_gpd_col, d_ov_node, d_ov_k, d_gfeT_k;
     DevArr<int64_t> d_gfeT_ptr;
-    DevArr<double> d_gfe_val, d_gpd_val, d_ov_N, d_gfeT_val, d_Hfe, d_Hneg_inv, d_colbuf, d_lam0, d_lam, d_y,
-        d_unit;
+    DevArr<double> d_gfe_val, d_gpd_val, d_ov_N, d_gfeT_val, d_Hfe, d_Hneg_inv, d_colbuf, d_lam0, d_lam, d_y;
     DevArr<double> d_B[4];          // block Chebyshev work (x, r, d0, d1)
     DevArr<int64_t> d_gpd_ptr;
     DevArr<uint8_t> d_near;         // bond words of nodes within (m + 1) delta of a band
@@ -210,6 +212,15 @@ struct pdmts_arl {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_flag = nullptr;
     cudaStream_t fe_stream = nullptr;
     bool H_valid = false, Hfe_valid = false, flag_pending = false;
+    struct pdmts_batch *batch = nullptr;  // the batch this coupling belongs to, if any
+    cusolverDnHandle_t solver = nullptr;  // dense Cholesky (or LU) for (-H)^-1
+    int64_t lu_inverses = 0;              // inverses that needed LU (-H not numerically definite)
+    // colouring of the multiplier columns for the link runs of build_H (per m):
+    // colour c's unit multipliers and, per constraint row, the column it measures
+    int colors_m = 0;
+    std::vector<std::vector<int64_t>> color_cols;
+    DevArr<double> d_units;           // colours x nlam
+    DevArr<int32_t> d_owners;         // colours x nlam
     int64_t rebuilds = 0, colors = 0;
     int built_m = 0;
     std::vector<double> theta_free, theta_link;
@@ -237,10 +248,11 @@ struct pdmts_arl {
     }
     void release_all()
     {
-        release(d_gfe_col); release(d_gpd_col); release(d_ov_node); release(d_ov_k); release(d_owner);
+        release(d_gfe_col); release(d_gpd_col); release(d_ov_node); release(d_ov_k);
         release(d_gfeT_k); release(d_gfeT_ptr); release(d_gfeT_val); release(d_Hfe);
+        release(d_units); release(d_owners);
         release(d_gfe_val); release(d_gpd_val); release(d_ov_N); release(d_Hneg_inv);
-        release(d_colbuf); release(d_lam0); release(d_lam); release(d_y); release(d_unit);
+        release(d_colbuf); release(d_lam0); release(d_lam); release(d_y);
         for (auto &b : d_B)
             release(b);
         release(d_gpd_ptr); release(d_near); release(d_changed);
@@ -271,6 +283,79 @@ static int h2d_ell_t(T *dst, const std::vector<T> &src, int64_t rows, int W, cud
 }
 
 // ------------------------------------------------------------ FE kernels --
+// Per-dof operations, shared by the FE kernels of one subdomain and their
+// batched forms (so both give the same bits).
+__device__ __forceinline__ void fe_predict_dof(const int64_t i, const double *__restrict__ u,
+                                               const double *__restrict__ v, const double *__restrict__ a,
+                                               const double dt, const double beta, const double gamma,
+                                               double *__restrict__ ut, double *__restrict__ vt)
+{
+    ut[i] = u[i] + dt * v[i] + (0.5 - beta) * dt * dt * a[i];
+    vt[i] = v[i] + (1.0 - gamma) * dt * a[i];
+}
+// r = b - A x for row i of a transposed-ELL matrix (b may be null: r = -A x)
+__device__ __forceinline__ double fe_residual_dof(const int64_t ndof, const int64_t i, const int W,
+                                                  const int32_t *__restrict__ col, const double *__restrict__ val,
+                                                  const double *__restrict__ x, const double *__restrict__ b)
+{
+    double ax = 0.0;
+    for (int e = 0; e < W; ++e)
+        ax += val[e * ndof + i] * x[col[e * ndof + i]];
+    return (b ? b[i] : 0.0) - ax;
+}
+// One Chebyshev iteration for node ix (rows ix and nfe + ix share one column
+// list): x += d, r -= A d, dn = c1 d + c2 M^-1 r (dn null on the last).
+__device__ __forceinline__ void fe_cheb_node(const int64_t nfe, const int64_t ix, const int W,
+                                             const int32_t *__restrict__ col, const double *__restrict__ val,
+                                             const double *__restrict__ Minv, double *__restrict__ x,
+                                             double *__restrict__ r, const double *__restrict__ d,
+                                             double *__restrict__ dn, const double c1, const double c2)
+{
+    const int64_t ndof = 2 * nfe, iy = nfe + ix;
+    double adx = 0.0, ady = 0.0;
+    for (int e = 0; e < W; ++e) {
+        const double dv = d[col[e * ndof + ix]];
+        adx += val[e * ndof + ix] * dv;
+        ady += val[e * ndof + iy] * dv;
+    }
+    x[ix] += d[ix];
+    x[iy] += d[iy];
+    const double rx = r[ix] - adx, ry = r[iy] - ady;
+    r[ix] = rx;
+    r[iy] = ry;
+    if (dn) {
+        dn[ix] = c1 * d[ix] + c2 * Minv[ix] * rx;
+        dn[iy] = c1 * d[iy] + c2 * Minv[iy] * ry;
+    }
+}
+__device__ __forceinline__ void fe_correct_dof(const int64_t i, const double *__restrict__ ut,
+                                               const double *__restrict__ vt, const double *__restrict__ a,
+                                               const double dt, const double beta, const double gamma,
+                                               double *__restrict__ u, double *__restrict__ v)
+{
+    u[i] = ut[i] + beta * dt * dt * a[i];
+    v[i] = vt[i] + gamma * dt * a[i];
+}
+// b = -G_FE^T lambda at dof i (component c of FE node `node`)
+__device__ __forceinline__ double fe_gfe_lam_dof(const int c, const int64_t node, const int64_t nl,
+                                                 const int64_t *__restrict__ ptr, const int32_t *__restrict__ kk,
+                                                 const double *__restrict__ val, const double *__restrict__ lam)
+{
+    double s = 0.0;
+    for (int64_t j = ptr[node]; j < ptr[node + 1]; ++j)
+        s += val[j] * lam[(int64_t)c * nl + kk[j]];
+    return -s;
+}
+__device__ __forceinline__ void fe_apply_link_dof(const int64_t i, const double *__restrict__ aw, const double dt,
+                                                  const double beta, const double gamma, double *__restrict__ u,
+                                                  double *__restrict__ v, double *__restrict__ a)
+{
+    const double w = aw[i];
+    u[i] += beta * dt * dt * w;
+    v[i] += gamma * dt * w;
+    a[i] += w;
+}
+
 // Newmark predictor (Eq. 38 / Eq. 39): u~ = u + dt v + (1/2 - beta) dt^2 a,
 // v~ = v + (1 - gamma) dt a, and b = P - K u~ needs the full u~ (second kernel).
 __global__ void k_fe_predict(const int64_t ndof, const double *__restrict__ u, const double *__restrict__ v,
@@ -280,8 +365,7 @@ __global__ void k_fe_predict(const int64_t ndof, const double *__restrict__ u, c
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ndof)
         return;
-    ut[i] = u[i] + dt * v[i] + (0.5 - beta) * dt * dt * a[i];
-    vt[i] = v[i] + (1.0 - gamma) * dt * a[i];
+    fe_predict_dof(i, u, v, a, dt, beta, gamma, ut, vt);
 }
 
 // y = b - A x (ELL rows), optionally d = y / (theta M)
@@ -293,10 +377,7 @@ __global__ void k_fe_residual(const int64_t ndof, const int W, const int32_t *__
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ndof)
         return;
-    double ax = 0.0;
-    for (int e = 0; e < W; ++e)
-        ax += val[e * ndof + i] * x[col[e * ndof + i]];
-    const double ri = (b ? b[i] : 0.0) - ax;
+    const double ri = fe_residual_dof(ndof, i, W, col, val, x, b);
     r[i] = ri;
     if (d)
         d[i] = inv_theta * Minv[i] * ri;
@@ -332,8 +413,7 @@ __global__ void k_fe_correct_state(const int64_t ndof, const double *__restrict_
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ndof)
         return;
-    u[i] = ut[i] + beta * dt * dt * a[i];
-    v[i] = vt[i] + gamma * dt * a[i];
+    fe_correct_dof(i, ut, vt, a, dt, beta, gamma, u, v);
 }
 
 // b = -G_FE^T lambda on the FE dofs (gather over the transpose, so the sum
@@ -347,10 +427,7 @@ __global__ void k_gfe_lam(const int64_t nfe, const int dim, const int64_t nl, co
         return;
     const int c = (int)(i / nfe);
     const int64_t node = i - (int64_t)c * nfe;
-    double s = 0.0;
-    for (int64_t j = ptr[node]; j < ptr[node + 1]; ++j)
-        s += val[j] * lam[(int64_t)c * nl + kk[j]];
-    b[i] = -s;
+    b[i] = fe_gfe_lam_dof(c, node, nl, ptr, kk, val, lam);
 }
 
 // FE link correction (Eq. 47b with Newmark): u += beta dt^2 a_W,
@@ -362,10 +439,7 @@ __global__ void k_fe_apply_link(const int64_t ndof, const double *__restrict__ a
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ndof)
         return;
-    const double w = aw[i];
-    u[i] += beta * dt * dt * w;
-    v[i] += gamma * dt * w;
-    a[i] += w;
+    fe_apply_link_dof(i, aw, dt, beta, gamma, u, v, a);
 }
 
 // Right-hand sides G_FE^T e_q for a batch of multiplier columns q0..q0+nb-1.
@@ -427,38 +501,6 @@ __global__ void k_negate(const int64_t n, double *__restrict__ A)
         A[i] = -A[i];
 }
 
-// In-place Gauss-Jordan inversion of a symmetric positive definite matrix,
-// one pivot per launch triple (no pivoting needed for SPD).
-__global__ void k_gj_save_col(const int64_t n, const double *__restrict__ A, const int64_t p, double *__restrict__ cb)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n)
-        cb[i] = A[i * n + p];
-}
-__global__ void k_gj_scale_row(const int64_t n, double *__restrict__ A, const int64_t p,
-                               const double *__restrict__ cb)
-{
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n)
-        return;
-    const double piv = cb[p];
-    A[p * n + j] = (j == p) ? 1.0 / piv : A[p * n + j] / piv;
-}
-__global__ void k_gj_update(const int64_t n, double *__restrict__ A, const int64_t p, const double *__restrict__ cb)
-{
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n * n)
-        return;
-    const int64_t i = t / n, j = t - i * n;
-    if (i == p)
-        return;
-    const double f = cb[i];
-    if (j == p)
-        A[t] = -f * A[p * n + p];
-    else
-        A[t] -= f * A[p * n + j];
-}
-
 // y = A x for a row-major n x n matrix, one warp per row.
 __global__ void k_gemv_rows(const int64_t n, const double *__restrict__ A, const double *__restrict__ x,
                             const double scale, double *__restrict__ y)
@@ -489,27 +531,105 @@ __global__ void k_cheb_iter_node(const int64_t nfe, const int nrhs, const int W,
     if (t >= nfe * nrhs)
         return;
     const int64_t ndof = 2 * nfe;
-    const int64_t c = t / nfe, ix = t - c * nfe, iy = nfe + ix;
-    const double *dc = d + c * ndof;
-    double adx = 0.0, ady = 0.0;
-    for (int e = 0; e < W; ++e) {
-        const double dv = dc[col[e * ndof + ix]];
-        adx += val[e * ndof + ix] * dv;
-        ady += val[e * ndof + iy] * dv;
-    }
-    const int64_t qx = c * ndof + ix, qy = c * ndof + iy;
-    x[qx] += d[qx];
-    x[qy] += d[qy];
-    const double rx = r[qx] - adx, ry = r[qy] - ady;
-    r[qx] = rx;
-    r[qy] = ry;
-    if (dn) {
-        dn[qx] = c1 * d[qx] + c2 * Minv[ix] * rx;
-        dn[qy] = c1 * d[qy] + c2 * Minv[iy] * ry;
-    }
+    const int64_t c = t / nfe, ix = t - c * nfe;
+    fe_cheb_node(nfe, ix, W, col, val, Minv, x + c * ndof, r + c * ndof, d + c * ndof,
+                 dn ? dn + c * ndof : nullptr, c1, c2);
 }
 
 static inline unsigned blocks(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+// ------------------------------------------------------- batched FE solves --
+// The FE free step and FE correction of many subdomains at once: each CTA
+// takes 256 nodes of one subdomain (a block table {subdomain, first node}),
+// each thread both rows of a node, with the per-dof operations above.
+struct FeDev {
+    int64_t nfe, nl;
+    int W, it;
+    const int32_t *col;
+    const double *K, *Keff, *Minv, *P, *cheb;
+    double *u, *v, *a, *ut, *vt, *b, *r, *d0, *d1, *aw, *bw;
+    double inv_theta, dt, beta, gamma;
+    const int64_t *gT_ptr;
+    const int32_t *gT_k;
+    const double *gT_val, *lam;
+};
+
+__global__ void k_feb_predict(const FeDev *__restrict__ M, const int2 *__restrict__ blk)
+{
+    const int2 q = blk[blockIdx.x];
+    const FeDev &F = M[q.x];
+    const int64_t node = (int64_t)q.y + threadIdx.x;
+    if (node >= F.nfe)
+        return;
+    for (int c = 0; c < 2; ++c)
+        fe_predict_dof(c * F.nfe + node, F.u, F.v, F.a, F.dt, F.beta, F.gamma, F.ut, F.vt);
+}
+
+// b = P - K u~, then r = b - K_eff a (warm start) and d0 = M^-1 r / theta
+__global__ void k_feb_residual(const FeDev *__restrict__ M, const int2 *__restrict__ blk)
+{
+    const int2 q = blk[blockIdx.x];
+    const FeDev &F = M[q.x];
+    const int64_t node = (int64_t)q.y + threadIdx.x;
+    if (node >= F.nfe)
+        return;
+    const int64_t ndof = 2 * F.nfe;
+    for (int c = 0; c < 2; ++c) {
+        const int64_t i = c * F.nfe + node;
+        F.b[i] = fe_residual_dof(ndof, i, F.W, F.col, F.K, F.ut, F.P);
+        const double ri = fe_residual_dof(ndof, i, F.W, F.col, F.Keff, F.a, F.b);
+        F.r[i] = ri;
+        F.d0[i] = F.inv_theta * F.Minv[i] * ri;
+    }
+}
+
+// b = -G_FE^T lambda, x = a_W = 0, r = b (the residual at the zero start), d0
+__global__ void k_feb_link_init(const FeDev *__restrict__ M, const int2 *__restrict__ blk)
+{
+    const int2 q = blk[blockIdx.x];
+    const FeDev &F = M[q.x];
+    const int64_t node = (int64_t)q.y + threadIdx.x;
+    if (node >= F.nfe)
+        return;
+    for (int c = 0; c < 2; ++c) {
+        const int64_t i = c * F.nfe + node;
+        const double bi = fe_gfe_lam_dof(c, node, F.nl, F.gT_ptr, F.gT_k, F.gT_val, F.lam);
+        F.bw[i] = bi;
+        F.aw[i] = 0.0;
+        const double ri = bi - 0.0;  // K_eff times the zero start is +0 in every sum
+        F.r[i] = ri;
+        F.d0[i] = F.inv_theta * F.Minv[i] * ri;
+    }
+}
+
+__global__ void k_feb_cheb(const FeDev *__restrict__ M, const int2 *__restrict__ blk, const int k, const int link)
+{
+    const int2 q = blk[blockIdx.x];
+    const FeDev &F = M[q.x];
+    const int64_t node = (int64_t)q.y + threadIdx.x;
+    if (node >= F.nfe || k >= F.it)
+        return;
+    const double *d = (k & 1) ? F.d1 : F.d0;
+    double *dn = (k == F.it - 1) ? nullptr : ((k & 1) ? F.d0 : F.d1);
+    fe_cheb_node(F.nfe, node, F.W, F.col, F.Keff, F.Minv, link ? F.aw : F.a, F.r, d, dn, F.cheb[k],
+                 F.cheb[F.it + k]);
+}
+
+__global__ void k_feb_finish(const FeDev *__restrict__ M, const int2 *__restrict__ blk, const int link)
+{
+    const int2 q = blk[blockIdx.x];
+    const FeDev &F = M[q.x];
+    const int64_t node = (int64_t)q.y + threadIdx.x;
+    if (node >= F.nfe)
+        return;
+    for (int c = 0; c < 2; ++c) {
+        const int64_t i = c * F.nfe + node;
+        if (link)
+            fe_apply_link_dof(i, F.aw, F.dt, F.beta, F.gamma, F.u, F.v, F.a);
+        else
+            fe_correct_dof(i, F.ut, F.vt, F.a, F.dt, F.beta, F.gamma, F.u, F.v);
+    }
+}
 
 // ------------------------------------------------------- FE assembly ------
 // alpha-weighted Q4 plane-stress element stiffness and lumped mass with 2 x 2
@@ -762,6 +882,10 @@ static int fe_prepare_keff(pdmts_fem *fe, double dt, double beta)
         fe->cheb_c2[(size_t)k] = 2.0 * rn / std::max(fe->cheb_delta, 1e-300);
         rho = rn;
     }
+    std::vector<double> sched(fe->cheb_c1);
+    sched.insert(sched.end(), fe->cheb_c2.begin(), fe->cheb_c2.end());
+    PDMTS_TRY(fe->alloc(fe->d_cheb, 2 * (int64_t)it));
+    PDMTS_TRY(h2d(fe->d_cheb.p, sched, fe->ctx->stream));
     fe->keff_dt = dt;
     fe->keff_version += 1;
     PDMTS_CUDA_TRY(cudaStreamSynchronize(fe->ctx->stream));
@@ -1144,11 +1268,10 @@ static int build_constraint(pdmts_arl *A)
     PDMTS_TRY(h2d(A->d_ov_node.p, A->ov_node, s));
     PDMTS_TRY(h2d(A->d_ov_k.p, A->ov_k, s));
     PDMTS_TRY(h2d(A->d_ov_N.p, A->ov_N, s));
-    for (DevArr<double> *a : {&A->d_lam0, &A->d_lam, &A->d_y, &A->d_unit, &A->d_colbuf}) {
+    for (DevArr<double> *a : {&A->d_lam0, &A->d_lam, &A->d_y, &A->d_colbuf}) {
         PDMTS_TRY(A->alloc(*a, A->nlam));
         PDMTS_CUDA_TRY(cudaMemsetAsync(a->p, 0, sizeof(double) * A->nlam, s));
     }
-    PDMTS_TRY(A->alloc(A->d_owner, A->nlam));
     PDMTS_TRY(A->alloc(A->d_Hneg_inv, A->nlam * A->nlam));
     PDMTS_TRY(A->alloc(A->d_changed, 1));
     // bond words of PD nodes within (m + 1) delta of a band (rebuild rule)
@@ -1342,26 +1465,18 @@ static int pd_link_run(pdmts_arl *A, const double *dev_lam, int m, cudaStream_t 
     return PDMTS_OK;
 }
 
-// Interface operator H = G_FE Ydot_FE - G_PD Ydot_PD (Eq. 49) and its inverse.
-// Columns of H_PD come from link runs of several unit multipliers at once:
-// columns whose supports are more than 2R apart (R = 2 h_FE + m delta, the
-// reach of a link response over m substeps plus the shape-function supports)
-// cannot be seen by the same constraint row, so each row is attributed to the
-// one column of the run within R of it.
-static int build_H(pdmts_arl *A, int m)
+// Colouring of the multiplier columns for the link runs of build_H: columns
+// whose supports are more than 2R apart (R = 2 h_FE + m delta) share a colour,
+// and each constraint row is attributed to the one column of its colour
+// within R. Depends on the geometry and m only: computed once per m, with
+// every colour's unit vector and row owners uploaded together.
+static int build_colors(pdmts_arl *A, int m, cudaStream_t s)
 {
+    if (A->colors_m == m && !A->color_cols.empty())
+        return PDMTS_OK;
     pdmts_fem *fe = A->fe;
     pdmts_pd *pd = A->pd;
-    pdmts_ctx *ctx = A->ctx;
-    cudaStream_t s = ctx->stream;
     const int64_t nlam = A->nlam, nl = A->nl;
-    int64_t launches = 0;
-    const double dtf = m * ctx->dt_pd;
-    if (!A->Hfe_valid)
-        PDMTS_TRY(build_Hfe(A, dtf, &launches));
-    double *H = A->d_Hneg_inv.p;  // holds H while building, then (-H)^-1
-    PDMTS_CUDA_TRY(cudaMemcpyAsync(H, A->d_Hfe.p, sizeof(double) * nlam * nlam, cudaMemcpyDeviceToDevice, s));
-    // colouring of the multiplier columns
     double hmax = 0.0;
     for (int64_t e = 0; e < fe->ne; ++e) {
         const int32_t a = fe->conn[(size_t)e * 4], c = fe->conn[(size_t)e * 4 + 2];
@@ -1391,26 +1506,148 @@ static int build_H(pdmts_arl *A, int m)
         if (!placed)
             colors.push_back({q});
     }
-    A->colors = (int64_t)colors.size();
-    std::vector<double> unit((size_t)nlam);
-    std::vector<int32_t> owner((size_t)nlam);
-    const bool f64 = pd->precision == PDMTS_FP64;
-    for (auto &cl : colors) {
-        std::fill(unit.begin(), unit.end(), 0.0);
-        std::fill(owner.begin(), owner.end(), -1);
-        for (int64_t q : cl)
-            unit[(size_t)q] = 1.0;
+    const int64_t nc = (int64_t)colors.size();
+    std::vector<double> unit((size_t)(nc * nlam), 0.0);
+    std::vector<int32_t> owner((size_t)(nc * nlam), -1);
+    for (int64_t c = 0; c < nc; ++c) {
+        for (int64_t q : colors[(size_t)c])
+            unit[(size_t)(c * nlam + q)] = 1.0;
         for (int64_t r = 0; r < nlam; ++r)
-            for (int64_t q : cl) {
+            for (int64_t q : colors[(size_t)c]) {
                 const double dist = std::max(std::fabs(xk(q, 0) - xk(r, 0)), std::fabs(xk(q, 1) - xk(r, 1)));
                 if (dist <= R) {
-                    owner[(size_t)r] = (int32_t)q;
+                    owner[(size_t)(c * nlam + r)] = (int32_t)q;
                     break;
                 }
             }
-        PDMTS_TRY(h2d(A->d_unit.p, unit, s));
-        PDMTS_TRY(h2d(A->d_owner.p, owner, s));
-        PDMTS_TRY(pd_link_run(A, A->d_unit.p, m, s));
+    }
+    PDMTS_TRY(A->alloc(A->d_units, nc * nlam));
+    PDMTS_TRY(A->alloc(A->d_owners, nc * nlam));
+    PDMTS_TRY(h2d(A->d_units.p, unit, s));
+    PDMTS_TRY(h2d(A->d_owners.p, owner, s));
+    PDMTS_CUDA_TRY(cudaStreamSynchronize(s));
+    A->color_cols = std::move(colors);
+    A->colors = nc;
+    A->colors_m = m;
+    return PDMTS_OK;
+}
+
+// Row-major symmetric n x n: copy the upper triangle onto the lower.
+__global__ void k_mirror_upper(const int64_t n, double *__restrict__ M)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * n)
+        return;
+    const int64_t i = t / n, j = t - i * n;
+    if (i > j)
+        M[t] = M[j * n + i];
+}
+
+__global__ void k_identity(const int64_t n, double *__restrict__ M)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * n)
+        return;
+    const int64_t i = t / n, j = t - i * n;
+    M[t] = i == j ? 1.0 : 0.0;
+}
+
+// In-place inverse of the row-major n x n matrix M = -H (FP64, cuSOLVER).
+// -H is symmetric positive definite in exact arithmetic: Cholesky factorisation
+// and inversion from the factor (cuSOLVER's column-major lower triangle is
+// this row-major upper triangle; the lower one is mirrored afterwards). When
+// the measured operator is not (link runs in FP32 carry rounding into its
+// weakest directions), LU with partial pivoting of the full matrix: cuSOLVER
+// solves M^T X = I in its column-major view, and X read row-major is M^-1.
+static int invert_spd(pdmts_arl *A, double *M, int64_t n, cudaStream_t s, int64_t *launches)
+{
+    if (n > INT32_MAX)
+        return fail(PDMTS_ERR_UNSUPPORTED, "interface operator of %lld rows", (long long)n);
+    if (!A->solver && cusolverDnCreate(&A->solver) != CUSOLVER_STATUS_SUCCESS)
+        return fail(PDMTS_ERR_CUDA, "cusolverDnCreate failed");
+    if (cusolverDnSetStream(A->solver, s) != CUSOLVER_STATUS_SUCCESS)
+        return fail(PDMTS_ERR_CUDA, "cusolverDnSetStream failed");
+    const int ni = (int)n;
+    int l1 = 0, l2 = 0, l3 = 0;
+    if (cusolverDnDpotrf_bufferSize(A->solver, CUBLAS_FILL_MODE_LOWER, ni, M, ni, &l1) != CUSOLVER_STATUS_SUCCESS ||
+        cusolverDnDpotri_bufferSize(A->solver, CUBLAS_FILL_MODE_LOWER, ni, M, ni, &l2) != CUSOLVER_STATUS_SUCCESS ||
+        cusolverDnDgetrf_bufferSize(A->solver, ni, ni, M, ni, &l3) != CUSOLVER_STATUS_SUCCESS)
+        return fail(PDMTS_ERR_CUDA, "cuSOLVER workspace query failed");
+    const int lw = std::max({l1, l2, l3, 1});
+    DevArr<double> work, keep;
+    DevArr<int> info, piv;
+    int r = PDMTS_OK;
+    auto cleanup = [&]() {
+        A->release(work);
+        A->release(keep);
+        A->release(info);
+        A->release(piv);
+    };
+    if ((r = A->alloc(work, lw)) != PDMTS_OK || (r = A->alloc(keep, n * n)) != PDMTS_OK ||
+        (r = A->alloc(info, 2)) != PDMTS_OK || (r = A->alloc(piv, n)) != PDMTS_OK) {
+        cleanup();
+        return r;
+    }
+    int hinfo[2] = {0, 0};
+    cudaError_t e = cudaMemcpyAsync(keep.p, M, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(info.p, 0, 2 * sizeof(int), s);
+    if (e != cudaSuccess ||
+        cusolverDnDpotrf(A->solver, CUBLAS_FILL_MODE_LOWER, ni, M, ni, work.p, lw, info.p) != CUSOLVER_STATUS_SUCCESS ||
+        cusolverDnDpotri(A->solver, CUBLAS_FILL_MODE_LOWER, ni, M, ni, work.p, lw, info.p + 1) !=
+            CUSOLVER_STATUS_SUCCESS ||
+        cudaMemcpyAsync(hinfo, info.p, sizeof(hinfo), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cleanup();
+        return fail(PDMTS_ERR_CUDA, "Cholesky inverse failed: %s", cudaGetErrorString(cudaGetLastError()));
+    }
+    if (hinfo[0] == 0 && hinfo[1] == 0) {
+        k_mirror_upper<<<blocks(n * n), 256, 0, s>>>(n, M);
+        *launches += 1;
+    } else {
+        // LU with partial pivoting of the kept copy; the inverse lands in M
+        k_identity<<<blocks(n * n), 256, 0, s>>>(n, M);
+        *launches += 1;
+        hinfo[0] = hinfo[1] = 0;
+        if (cudaMemsetAsync(info.p, 0, 2 * sizeof(int), s) != cudaSuccess ||
+            cusolverDnDgetrf(A->solver, ni, ni, keep.p, ni, work.p, piv.p, info.p) != CUSOLVER_STATUS_SUCCESS ||
+            cusolverDnDgetrs(A->solver, CUBLAS_OP_N, ni, ni, keep.p, ni, piv.p, M, ni, info.p + 1) !=
+                CUSOLVER_STATUS_SUCCESS ||
+            cudaMemcpyAsync(hinfo, info.p, sizeof(hinfo), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            r = fail(PDMTS_ERR_CUDA, "LU inverse failed: %s", cudaGetErrorString(cudaGetLastError()));
+        else if (hinfo[0] != 0 || hinfo[1] != 0)
+            r = fail(PDMTS_ERR_STATE, "interface operator H is singular (cuSOLVER info %d, %d)", hinfo[0], hinfo[1]);
+        A->lu_inverses += 1;
+    }
+    PDMTS_CUDA_TRY(cudaStreamSynchronize(s));
+    cleanup();
+    return r;
+}
+
+// Interface operator H = G_FE Ydot_FE - G_PD Ydot_PD (Eq. 49) and its inverse.
+// Columns of H_PD come from link runs of several unit multipliers at once:
+// columns whose supports are more than 2R apart (R = 2 h_FE + m delta, the
+// reach of a link response over m substeps plus the shape-function supports)
+// cannot be seen by the same constraint row, so each row is attributed to the
+// one column of the run within R of it.
+static int build_H(pdmts_arl *A, int m)
+{
+    pdmts_fem *fe = A->fe;
+    pdmts_pd *pd = A->pd;
+    pdmts_ctx *ctx = A->ctx;
+    cudaStream_t s = ctx->stream;
+    const int64_t nlam = A->nlam, nl = A->nl;
+    int64_t launches = 0;
+    const double dtf = m * ctx->dt_pd;
+    if (!A->Hfe_valid)
+        PDMTS_TRY(build_Hfe(A, dtf, &launches));
+    double *H = A->d_Hneg_inv.p;  // holds H while building, then (-H)^-1
+    PDMTS_CUDA_TRY(cudaMemcpyAsync(H, A->d_Hfe.p, sizeof(double) * nlam * nlam, cudaMemcpyDeviceToDevice, s));
+    PDMTS_TRY(build_colors(A, m, s));
+    const bool f64 = pd->precision == PDMTS_FP64;
+    for (int64_t cidx = 0; cidx < A->colors; ++cidx) {
+        PDMTS_TRY(pd_link_run(A, A->d_units.p + cidx * nlam, m, s));
         // y = G_PD v_link
         cudaError_t e = launch_constraint(2, nl, A->d_gpd_ptr.p, A->d_gpd_col.p, A->d_gpd_val.p, pd->n,
                                           f64 ? pd->lk_v.p : nullptr, f64 ? nullptr : pd->lk_v4.p,
@@ -1418,20 +1655,14 @@ static int build_H(pdmts_arl *A, int m)
                                           0.0, A->d_y.p, s);
         if (e != cudaSuccess)
             return fail(PDMTS_ERR_CUDA, "constraint rows: %s", cudaGetErrorString(e));
-        k_scatter_color<<<blocks(nlam), 256, 0, s>>>(nlam, A->d_owner.p, A->d_y.p, -1.0, H);
+        k_scatter_color<<<blocks(nlam), 256, 0, s>>>(nlam, A->d_owners.p + cidx * nlam, A->d_y.p, -1.0, H);
         launches += 2;
-        // the host vectors are reused for the next colour
-        PDMTS_CUDA_TRY(cudaStreamSynchronize(s));
     }
-    // (-H)^-1 by Gauss-Jordan (-H is symmetric positive definite)
+    // (-H)^-1 (-H is symmetric positive definite)
     const int64_t n2 = nlam * nlam;
     k_negate<<<blocks(n2), 256, 0, s>>>(n2, H);
-    for (int64_t p = 0; p < nlam; ++p) {
-        k_gj_save_col<<<blocks(nlam), 256, 0, s>>>(nlam, H, p, A->d_colbuf.p);
-        k_gj_scale_row<<<blocks(nlam), 256, 0, s>>>(nlam, H, p, A->d_colbuf.p);
-        k_gj_update<<<blocks(n2), 256, 0, s>>>(nlam, H, p, A->d_colbuf.p);
-        launches += 3;
-    }
+    ++launches;
+    PDMTS_TRY(invert_spd(A, H, nlam, s, &launches));
     PDMTS_CUDA_TRY(cudaGetLastError());
     PDMTS_CUDA_TRY(cudaStreamSynchronize(s));
     ctx->stats.kernel_launches += launches;
@@ -1516,11 +1747,15 @@ extern "C" int arlequin_bind(pdmts_ctx *ctx, pdmts_pd *pd, pdmts_fem *fe, int we
     return PDMTS_OK;
 }
 
+static void batch_drop_member(pdmts_batch *b, pdmts_ctx *c);
+
 extern "C" int arlequin_destroy(pdmts_arl *A)
 {
     clear_error();
     if (!A)
         return PDMTS_OK;
+    if (A->batch)
+        batch_drop_member(A->batch, A->ctx);  // the batch goes on without this member
     cudaSetDevice(A->ctx->device);
     cudaStreamSynchronize(A->ctx->stream);
     if (A->fe_stream) {
@@ -1531,6 +1766,7 @@ extern "C" int arlequin_destroy(pdmts_arl *A)
     if (A->ev_join) cudaEventDestroy(A->ev_join);
     if (A->ev_flag) cudaEventDestroy(A->ev_flag);
     if (A->h_changed) cudaFreeHost(A->h_changed);
+    if (A->solver) cusolverDnDestroy(A->solver);
     if (A->ctx->arl == A)
         A->ctx->arl = nullptr;
     A->release_all();
@@ -1568,11 +1804,16 @@ int mts_time_changed(pdmts_ctx *ctx)
 //   step_link_begin  s: interface force of lambda_m, W_0 = 0 (Eq. 48b);
 //   (m link PD substeps with factor j/m)
 //   step_finish      s: U += W, rebuild flag, lambda_0 <- lambda_m, join fs.
+static int batch_settle(pdmts_batch *b);
+
 static int step_prepare(pdmts_arl *A, cudaStream_t s)
 {
     pdmts_ctx *ctx = A->ctx;
     pdmts_pd *pd = A->pd;
     const int m = ctx->m_ratio;
+    // a round of a batch this member belongs to may still be in flight
+    if (A->batch)
+        PDMTS_TRY(batch_settle(A->batch));
     // rebuild flag of the previous step (a bond near an overlap band broke)
     if (A->flag_pending) {
         PDMTS_CUDA_TRY(cudaEventSynchronize(A->ev_flag));
@@ -1632,12 +1873,15 @@ static int step_fe_free(pdmts_arl *A, cudaStream_t fs, bool graphs, int64_t *lau
     return PDMTS_OK;
 }
 
-static int step_lambda(pdmts_arl *A, cudaStream_t s, int64_t *launches)
+// fe_join: wait for the member's own FE free step (a batch orders its batched
+// FE solves itself)
+static int step_lambda(pdmts_arl *A, cudaStream_t s, int64_t *launches, bool fe_join = true)
 {
     pdmts_pd *pd = A->pd;
     pdmts_fem *fe = A->fe;
     const bool f64 = pd->precision == PDMTS_FP64;
-    PDMTS_CUDA_TRY(cudaStreamWaitEvent(s, A->ev_join, 0));
+    if (fe_join)
+        PDMTS_CUDA_TRY(cudaStreamWaitEvent(s, A->ev_join, 0));
     const float4 *v4 = f64 ? nullptr : pd->f_v4.p;
     const float2 *v2 = f64 ? nullptr : pd->f_v2.p;
     cudaError_t e = launch_constraint(2, A->nl, A->d_gpd_ptr.p, A->d_gpd_col.p, A->d_gpd_val.p, pd->n,
@@ -1680,7 +1924,7 @@ static int step_link_begin(pdmts_arl *A, const double *dev_lam, cudaStream_t s, 
     return PDMTS_OK;
 }
 
-static int step_finish(pdmts_arl *A, cudaStream_t s, int64_t *launches)
+static int step_finish(pdmts_arl *A, cudaStream_t s, int64_t *launches, bool fe_join = true)
 {
     pdmts_ctx *ctx = A->ctx;
     pdmts_pd *pd = A->pd;
@@ -1731,7 +1975,8 @@ static int step_finish(pdmts_arl *A, cudaStream_t s, int64_t *launches)
                                    cudaMemcpyDeviceToDevice, s));
     PDMTS_CUDA_TRY(cudaMemcpyAsync(A->d_lam0.p, A->d_lam.p, sizeof(double) * A->nlam, cudaMemcpyDeviceToDevice, s));
     // the step ends when the FE correction has also finished
-    PDMTS_CUDA_TRY(cudaStreamWaitEvent(s, A->ev_join, 0));
+    if (fe_join)
+        PDMTS_CUDA_TRY(cudaStreamWaitEvent(s, A->ev_join, 0));
     *launches += 2;
     ctx->stats.coarse_steps += 1;
     return PDMTS_OK;
@@ -1793,6 +2038,13 @@ struct pdmts_batch {
     std::vector<cudaEvent_t> ev_lane;       // one per member stream: its part of a phase is done
     cudaEvent_t ev_in = nullptr, ev_end = nullptr, ev_phase = nullptr;
     cudaEvent_t ev_t[6] = {};               // marks of the last round (phase times)
+    // batched FE solves: their stream, events, and the device table of the members' FE subdomains
+    cudaStream_t fs = nullptr;
+    cudaEvent_t ev_fe_free = nullptr, ev_fe_link = nullptr;
+    FeDev *d_fe = nullptr;
+    int2 *d_feblk = nullptr;
+    int nfeblk = 0, itmax = 0;
+    std::vector<uint64_t> fe_key;
     int tile = -1;                          // batched lattice tile configuration (-1: tune)
     // argument blocks and work lists of one phase's slots: host staging (pinned) and device copies
     Lat2DArgs *h_args = nullptr;
@@ -1800,7 +2052,7 @@ struct pdmts_batch {
     Lat2DArgs *d_args = nullptr;
     int2 *d_work = nullptr;
     int64_t cap_args = 0, cap_work = 0;
-    int64_t rounds = 0, work_items = 0, batched_launches = 0;
+    int64_t rounds = 0, work_items = 0, batched_launches = 0, kernel_launches = 0;
     bool pending = false;                   // a round is in flight (staging in use)
     // the argument blocks and work lists of a phase depend only on what the key
     // records (buffer parities, schedules, windows, pointers): built once, kept
@@ -1815,7 +2067,7 @@ struct pdmts_batch {
         std::vector<uint64_t> key;
         cudaGraphExec_t exec = nullptr;
         std::vector<struct MemberSnap> after, delta;
-        int64_t work_items = 0, batched_launches = 0;
+        int64_t work_items = 0, batched_launches = 0, kernel_launches = 0;
     };
     std::vector<RoundGraph> graphs;
 };
@@ -1965,6 +2217,7 @@ static int batch_phase(pdmts_batch *b, bool link)
         if (e != cudaSuccess)
             return fail(PDMTS_ERR_CUDA, "batched substep: %s", cudaGetErrorString(e));
         b->batched_launches += 1;
+        b->kernel_launches += 1;
         b->work_items += nwork;
         for (int i = 0; i < nm; ++i)
             if (j < b->members[(size_t)i]->m_ratio)
@@ -2059,45 +2312,140 @@ static int batch_fan_in(pdmts_batch *b)
 // One round: per member on its stream (members round-robin over the member
 // streams) the small coupling kernels, and on the batch stream the batched
 // substep slots; the FE solves run beside the PD slots.
+// Device table of the members' FE subdomains for the batched FE kernels
+// (rebuilt when a member's schedule or arrays change).
+static int batch_fe_table(pdmts_batch *b)
+{
+    std::vector<uint64_t> key;
+    for (pdmts_ctx *c : b->members) {
+        const pdmts_fem *fe = c->arl->fe;
+        key.insert(key.end(), {(uint64_t)fe->keff_version, (uint64_t)(uintptr_t)fe->d_cheb.p,
+                               (uint64_t)(uintptr_t)fe->d_u.p, (uint64_t)(uintptr_t)fe->d_Keff.p});
+    }
+    if (key == b->fe_key && b->d_fe)
+        return PDMTS_OK;
+    std::vector<FeDev> devs;
+    std::vector<int2> blk;
+    b->itmax = 0;
+    for (size_t i = 0; i < b->members.size(); ++i) {
+        pdmts_ctx *c = b->members[i];
+        pdmts_arl *A = c->arl;
+        pdmts_fem *fe = A->fe;
+        if (!fe->paired_rows)
+            return fail(PDMTS_ERR_UNSUPPORTED, "batch: member %zu: FE rows of a node do not share columns", i);
+        FeDev F{};
+        F.nfe = fe->n;
+        F.nl = A->nl;
+        F.W = fe->W;
+        F.it = (int)fe->cheb_c1.size();
+        F.col = fe->d_col.p;
+        F.K = fe->d_K.p;
+        F.Keff = fe->d_Keff.p;
+        F.Minv = fe->d_Minv.p;
+        F.P = fe->d_P.p;
+        F.cheb = fe->d_cheb.p;
+        F.u = fe->d_u.p; F.v = fe->d_v.p; F.a = fe->d_a.p; F.ut = fe->d_ut.p; F.vt = fe->d_vt.p;
+        F.b = fe->d_b.p; F.r = fe->d_r.p; F.d0 = fe->d_d[0].p; F.d1 = fe->d_d[1].p;
+        F.aw = fe->d_aw.p; F.bw = fe->d_bw.p;
+        F.inv_theta = 1.0 / fe->cheb_theta;
+        F.dt = c->m_ratio * c->dt_pd;
+        F.beta = c->beta_fe;
+        F.gamma = c->gamma_fe;
+        F.gT_ptr = A->d_gfeT_ptr.p;
+        F.gT_k = A->d_gfeT_k.p;
+        F.gT_val = A->d_gfeT_val.p;
+        F.lam = A->d_lam.p;
+        b->itmax = std::max(b->itmax, F.it);
+        for (int64_t n0 = 0; n0 < fe->n; n0 += 256)
+            blk.push_back(make_int2((int)i, (int)n0));
+        devs.push_back(F);
+    }
+    if (b->d_fe) cudaFree(b->d_fe);
+    if (b->d_feblk) cudaFree(b->d_feblk);
+    b->d_fe = nullptr;
+    b->d_feblk = nullptr;
+    if (cudaMalloc(&b->d_fe, sizeof(FeDev) * devs.size()) != cudaSuccess ||
+        cudaMalloc(&b->d_feblk, sizeof(int2) * std::max<size_t>(blk.size(), 1)) != cudaSuccess)
+        return fail(PDMTS_ERR_NOMEM, "batch: FE table");
+    PDMTS_CUDA_TRY(cudaMemcpy(b->d_fe, devs.data(), sizeof(FeDev) * devs.size(), cudaMemcpyHostToDevice));
+    PDMTS_CUDA_TRY(cudaMemcpy(b->d_feblk, blk.data(), sizeof(int2) * blk.size(), cudaMemcpyHostToDevice));
+    b->nfeblk = (int)blk.size();
+    b->fe_key = key;
+    return PDMTS_OK;
+}
+
+// The batched FE free step (link = false) or FE correction on b->fs.
+static int batch_fe(pdmts_batch *b, bool link)
+{
+    if (b->nfeblk == 0)
+        return PDMTS_OK;
+    if (link)
+        k_feb_link_init<<<b->nfeblk, 256, 0, b->fs>>>(b->d_fe, b->d_feblk);
+    else {
+        k_feb_predict<<<b->nfeblk, 256, 0, b->fs>>>(b->d_fe, b->d_feblk);
+        k_feb_residual<<<b->nfeblk, 256, 0, b->fs>>>(b->d_fe, b->d_feblk);
+    }
+    for (int k = 0; k < b->itmax; ++k)
+        k_feb_cheb<<<b->nfeblk, 256, 0, b->fs>>>(b->d_fe, b->d_feblk, k, link ? 1 : 0);
+    k_feb_finish<<<b->nfeblk, 256, 0, b->fs>>>(b->d_fe, b->d_feblk, link ? 1 : 0);
+    PDMTS_CUDA_TRY(cudaGetLastError());
+    return PDMTS_OK;
+}
+
 // The round's work; enqueued only while b->s is captured (the phase marks
 // are external event nodes, so the events can be read after a replay).
 static int batch_enqueue_round(pdmts_batch *b, bool graphs)
 {
+    (void)graphs;
     const size_t nm = b->members.size();
     const size_t K = b->fe_streams.size();
     std::vector<int64_t> launches(nm, 0);
     auto lane = [&](size_t i) { return b->fe_streams[i % K]; };
     PDMTS_CUDA_TRY(cudaEventRecordWithFlags(b->ev_t[0], b->s, cudaEventRecordExternal));
-    // interface forces of lambda_0, then the FE free steps (these do not hold up the PD slots)
+    // FE free steps of all members (batched) beside the PD free substeps
+    PDMTS_CUDA_TRY(cudaEventRecord(b->ev_phase, b->s));
+    PDMTS_CUDA_TRY(cudaStreamWaitEvent(b->fs, b->ev_phase, 0));
+    PDMTS_TRY(batch_fe(b, false));
+    PDMTS_CUDA_TRY(cudaEventRecord(b->ev_fe_free, b->fs));
+    // interface forces of lambda_0
     PDMTS_TRY(batch_fan_out(b));
     for (size_t i = 0; i < nm; ++i)
         PDMTS_TRY(step_free_begin(b->members[i]->arl, lane(i), &launches[i]));
     PDMTS_TRY(batch_fan_in(b));
     PDMTS_CUDA_TRY(cudaEventRecordWithFlags(b->ev_t[1], b->s, cudaEventRecordExternal));
-    for (size_t i = 0; i < nm; ++i)
-        PDMTS_TRY(step_fe_free(b->members[i]->arl, lane(i), graphs, &launches[i]));
     PDMTS_TRY(batch_phase(b, false));
     PDMTS_CUDA_TRY(cudaEventRecordWithFlags(b->ev_t[2], b->s, cudaEventRecordExternal));
-    // lambda_m and the link-problem start, then the FE corrections
+    // lambda_m and the link-problem start
     PDMTS_TRY(batch_fan_out(b));
+    for (cudaStream_t f : b->fe_streams)
+        PDMTS_CUDA_TRY(cudaStreamWaitEvent(f, b->ev_fe_free, 0));
     for (size_t i = 0; i < nm; ++i) {
         pdmts_arl *A = b->members[i]->arl;
-        PDMTS_TRY(step_lambda(A, lane(i), &launches[i]));
+        PDMTS_TRY(step_lambda(A, lane(i), &launches[i], false));
         PDMTS_TRY(step_link_begin(A, A->d_lam.p, lane(i), &launches[i]));
     }
     PDMTS_TRY(batch_fan_in(b));
     PDMTS_CUDA_TRY(cudaEventRecordWithFlags(b->ev_t[3], b->s, cudaEventRecordExternal));
-    for (size_t i = 0; i < nm; ++i)
-        PDMTS_TRY(step_fe_link(b->members[i]->arl, lane(i), lane(i), graphs, &launches[i]));
+    // FE corrections of all members (batched) beside the PD link substeps
+    PDMTS_CUDA_TRY(cudaEventRecord(b->ev_phase, b->s));
+    PDMTS_CUDA_TRY(cudaStreamWaitEvent(b->fs, b->ev_phase, 0));
+    PDMTS_TRY(batch_fe(b, true));
+    PDMTS_CUDA_TRY(cudaEventRecord(b->ev_fe_link, b->fs));
     PDMTS_TRY(batch_phase(b, true));
     PDMTS_CUDA_TRY(cudaEventRecordWithFlags(b->ev_t[4], b->s, cudaEventRecordExternal));
-    // corrections and rebuild flags
+    // corrections and rebuild flags; the round ends with the FE corrections
     PDMTS_TRY(batch_fan_out(b));
     for (size_t i = 0; i < nm; ++i) {
-        PDMTS_TRY(step_finish(b->members[i]->arl, lane(i), &launches[i]));
+        PDMTS_TRY(step_finish(b->members[i]->arl, lane(i), &launches[i], false));
+        b->kernel_launches += launches[i];
+        const pdmts_fem *fe = b->members[i]->arl->fe;
+        // the member's share of the batched FE kernels: as many as its own solves would launch
+        launches[i] += 2 * (int64_t)fe->cheb_c1.size() + 7;
         b->members[i]->stats.kernel_launches += launches[i];
     }
     PDMTS_TRY(batch_fan_in(b));
+    b->kernel_launches += (b->nfeblk > 0 ? 2 * (int64_t)b->itmax + 5 : 0);
+    PDMTS_CUDA_TRY(cudaStreamWaitEvent(b->s, b->ev_fe_link, 0));
     PDMTS_CUDA_TRY(cudaEventRecordWithFlags(b->ev_t[5], b->s, cudaEventRecordExternal));
     return PDMTS_OK;
 }
@@ -2158,7 +2506,10 @@ static int batch_round(pdmts_batch *b)
         pdmts_arl *A = b->members[i]->arl;
         if (A->pd->lattice_tile < 0)
             A->pd->lattice_tile = b->tile;  // the members' own substeps use the batch's tile (no solo tuning)
-        PDMTS_TRY(step_prepare(A, b->s));
+        A->batch = nullptr;                 // settled above
+        const int r = step_prepare(A, b->s);
+        A->batch = b;
+        PDMTS_TRY(r);
     }
     // both phases' plans exist before any capture (the link phase starts at parity 0)
     pdmts_batch::Plan *plan = nullptr;
@@ -2174,6 +2525,7 @@ static int batch_round(pdmts_batch *b)
             b->members[i]->arl->pd->lk_cur = lk[i];
         PDMTS_TRY(r);
     }
+    PDMTS_TRY(batch_fe_table(b));
     const std::vector<uint64_t> key = batch_round_key(b);
     pdmts_batch::RoundGraph *g = nullptr;
     for (auto &rg : b->graphs)
@@ -2188,7 +2540,7 @@ static int batch_round(pdmts_batch *b)
         std::vector<MemberSnap> s0(nm);
         for (size_t i = 0; i < nm; ++i)
             s0[i] = member_snap(b->members[i]);
-        const int64_t wi0 = b->work_items, bl0 = b->batched_launches;
+        const int64_t wi0 = b->work_items, bl0 = b->batched_launches, kl0 = b->kernel_launches;
         cudaGraph_t graph = nullptr;
         PDMTS_CUDA_TRY(cudaStreamBeginCapture(b->s, cudaStreamCaptureModeThreadLocal));
         const int r = batch_enqueue_round(b, false);
@@ -2197,8 +2549,10 @@ static int batch_round(pdmts_batch *b)
         rg.key = key;
         rg.work_items = b->work_items - wi0;
         rg.batched_launches = b->batched_launches - bl0;
+        rg.kernel_launches = b->kernel_launches - kl0;
         b->work_items = wi0;
         b->batched_launches = bl0;
+        b->kernel_launches = kl0;
         for (size_t i = 0; i < nm; ++i) {
             pdmts_ctx *c = b->members[i];
             const MemberSnap s1 = member_snap(c);
@@ -2248,11 +2602,29 @@ static int batch_round(pdmts_batch *b)
     }
     b->work_items += g->work_items;
     b->batched_launches += g->batched_launches;
+    b->kernel_launches += g->kernel_launches;
     PDMTS_CUDA_TRY(cudaEventRecord(b->ev_end, b->s));
     b->pending = true;
     b->rounds += 1;
     PDMTS_CUDA_TRY(cudaGetLastError());
     return PDMTS_OK;
+}
+
+// A member's coupling is being destroyed: wait for the batch, drop the member
+// and every cached plan, graph and table that refers to it.
+static void batch_drop_member(pdmts_batch *b, pdmts_ctx *c)
+{
+    cudaSetDevice(b->device);
+    cudaStreamSynchronize(b->s);
+    batch_settle(b);
+    b->members.erase(std::remove(b->members.begin(), b->members.end(), c), b->members.end());
+    c->arl->batch = nullptr;
+    batch_free_plans(b);
+    for (auto &rg : b->graphs)
+        if (rg.exec)
+            cudaGraphExecDestroy(rg.exec);
+    b->graphs.clear();
+    b->fe_key.clear();
 }
 
 extern "C" int mts_batch_create(int n_members, pdmts_ctx *const *members, pdmts_batch **out)
@@ -2278,6 +2650,8 @@ extern "C" int mts_batch_create(int n_members, pdmts_ctx *const *members, pdmts_
         for (int k = 0; k < i; ++k)
             if (members[k] == c)
                 return fail(PDMTS_ERR_ARG, "mts_batch_create: member %d appears twice", i);
+        if (c->arl->batch)
+            return fail(PDMTS_ERR_STATE, "mts_batch_create: member %d already belongs to a batch", i);
     }
     PDMTS_CUDA_TRY(cudaSetDevice(members[0]->device));
     auto *b = new (std::nothrow) pdmts_batch();
@@ -2293,6 +2667,9 @@ extern "C" int mts_batch_create(int n_members, pdmts_ctx *const *members, pdmts_
               cudaEventCreateWithFlags(&b->ev_phase, cudaEventDisableTiming) == cudaSuccess;
     for (int k = 0; k < 6 && ok; ++k)
         ok = cudaEventCreate(&b->ev_t[k]) == cudaSuccess;
+    ok = ok && cudaStreamCreateWithPriority(&b->fs, cudaStreamNonBlocking, hi) == cudaSuccess &&
+         cudaEventCreateWithFlags(&b->ev_fe_free, cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&b->ev_fe_link, cudaEventDisableTiming) == cudaSuccess;
     const int K = std::min(n_members, 8);
     for (int k = 0; k < K && ok; ++k) {
         cudaStream_t fs = nullptr;
@@ -2308,6 +2685,8 @@ extern "C" int mts_batch_create(int n_members, pdmts_ctx *const *members, pdmts_
         mts_batch_destroy(b);
         return fail(PDMTS_ERR_CUDA, "mts_batch_create: stream/event creation failed");
     }
+    for (pdmts_ctx *c : b->members)
+        c->arl->batch = b;
     *out = b;
     return PDMTS_OK;
 }
@@ -2320,23 +2699,27 @@ extern "C" int mts_batch_advance(pdmts_batch *b, int64_t n_rounds)
     if (n_rounds < 0)
         return fail(PDMTS_ERR_ARG, "mts_batch_advance: n_rounds < 0");
     PDMTS_CUDA_TRY(cudaSetDevice(b->device));
-    // order the batch after everything queued for its members
-    for (pdmts_ctx *c : b->members) {
-        PDMTS_TRY(c->begin());
-        PDMTS_CUDA_TRY(cudaEventRecord(b->ev_in, c->stream));
+    // order the batch after its members' user streams (a member's own stream
+    // is ordered into its user stream at the end of every call), once per
+    // distinct user stream
+    std::vector<cudaStream_t> users;
+    for (pdmts_ctx *c : b->members)
+        if (std::find(users.begin(), users.end(), c->user_stream) == users.end())
+            users.push_back(c->user_stream);
+    for (cudaStream_t u : users) {
+        PDMTS_CUDA_TRY(cudaEventRecord(b->ev_in, u));
         PDMTS_CUDA_TRY(cudaStreamWaitEvent(b->s, b->ev_in, 0));
     }
+    if (b->members.empty())
+        return PDMTS_OK;
     PDMTS_TRY(batch_tune(b));
-    PDMTS_TRY(batch_settle(b));
     for (int64_t k = 0; k < n_rounds; ++k)
         PDMTS_TRY(batch_round(b));
-    PDMTS_TRY(batch_settle(b));
-    // members' own streams (and through them their users' streams) follow the batch
+    // the users' streams follow the batch; a member's own stream follows its
+    // user stream when the member is next used alone
     PDMTS_CUDA_TRY(cudaEventRecord(b->ev_in, b->s));
-    for (pdmts_ctx *c : b->members) {
-        PDMTS_CUDA_TRY(cudaStreamWaitEvent(c->stream, b->ev_in, 0));
-        PDMTS_TRY(c->end());
-    }
+    for (cudaStream_t u : users)
+        PDMTS_CUDA_TRY(cudaStreamWaitEvent(u, b->ev_in, 0));
     return PDMTS_OK;
 }
 
@@ -2350,6 +2733,7 @@ extern "C" int mts_batch_info(const pdmts_batch *b, pdmts_batch_info *info)
     info->rounds = b->rounds;
     info->work_items = b->work_items;
     info->batched_launches = b->batched_launches;
+    info->kernel_launches = b->kernel_launches;
     for (int k = 0; k < 5; ++k)
         info->last_round_ms[k] = 0.0;
     if (b->rounds > 0) {
@@ -2371,6 +2755,10 @@ extern "C" int mts_batch_destroy(pdmts_batch *b)
     cudaSetDevice(b->device);
     if (b->s)
         cudaStreamSynchronize(b->s);
+    batch_settle(b);
+    for (pdmts_ctx *c : b->members)
+        if (c && c->arl && c->arl->batch == b)
+            c->arl->batch = nullptr;
     for (cudaStream_t fs : b->fe_streams) {
         cudaStreamSynchronize(fs);
         cudaStreamDestroy(fs);
@@ -2384,6 +2772,14 @@ extern "C" int mts_batch_destroy(pdmts_batch *b)
     if (b->ev_in) cudaEventDestroy(b->ev_in);
     if (b->ev_end) cudaEventDestroy(b->ev_end);
     if (b->ev_phase) cudaEventDestroy(b->ev_phase);
+    if (b->fs) {
+        cudaStreamSynchronize(b->fs);
+        cudaStreamDestroy(b->fs);
+    }
+    if (b->ev_fe_free) cudaEventDestroy(b->ev_fe_free);
+    if (b->ev_fe_link) cudaEventDestroy(b->ev_fe_link);
+    if (b->d_fe) cudaFree(b->d_fe);
+    if (b->d_feblk) cudaFree(b->d_feblk);
     for (cudaEvent_t e : b->ev_t)
         if (e)
             cudaEventDestroy(e);

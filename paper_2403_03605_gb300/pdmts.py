@@ -415,7 +415,8 @@ def arlequin_info(arl):
 
 class BatchInfo(C.Structure):
     _fields_ = [("n_members", C.c_int32), ("lattice_tile", C.c_int32), ("rounds", C.c_int64),
-                ("work_items", C.c_int64), ("batched_launches", C.c_int64), ("last_round_ms", C.c_double * 5)]
+                ("work_items", C.c_int64), ("batched_launches", C.c_int64), ("kernel_launches", C.c_int64),
+                ("last_round_ms", C.c_double * 5)]
 
 
 def mts_batch_create(members):

@@ -158,3 +158,25 @@ def test_batch_rejects_unsupported_members(fresh):
     g = GpuMTS(fresh(), cp, P.PDMTS_FP32_BULK)
     with pytest.raises(P.PdmtsError):
         P.mts_batch_create([g.ctx, g.ctx])
+
+
+def test_batch_members_alone_in_between_and_dropped(fresh):
+    """A member advanced alone between batch calls, and a member whose coupling is
+    destroyed while in the batch: the others still match their solo runs."""
+    cps = _batch_members()
+    solo = [GpuMTS(fresh(), cp, P.PDMTS_FP32_BULK) for cp in cps]
+    solo[0].run(2 + 1 + 2)
+    solo[1].run(2 + 2)
+    members = [GpuMTS(fresh(), cp, P.PDMTS_FP32_BULK) for cp in cps]
+    b = P.mts_batch_create([g.ctx for g in members])
+    try:
+        P.mts_batch_advance(b, 2)
+        members[0].run(1)                      # alone, between batch calls
+        P.arlequin_destroy(members[2].arl)     # the member leaves the batch
+        P.mts_batch_advance(b, 2)
+        assert P.mts_batch_info(b)["n_members"] == 2
+    finally:
+        P.mts_batch_destroy(b)
+    for g, s_ in zip(members[:2], solo[:2]):
+        assert np.array_equal(g.u(), s_.u()) and np.array_equal(g.uf(), s_.uf())
+        assert np.array_equal(g.lam(), s_.lam()) and np.array_equal(g.mu(), s_.mu())
