@@ -230,16 +230,21 @@ int mts_get_phase_timing(pdmts_ctx *ctx, double *phase_ms, int64_t *n_steps);
 /* ---- CCM subdomain and Arlequin coupling (Sec. 2.2-2.5, Eq. 33-49, Alg. 1) -- */
 
 /* Finite-element subdomain of `ctx` (one per context): linear elastic,
- * isotropic (Eq. 8-9), plane stress with thickness `thickness`. This build
- * takes dim = 2 with bilinear quadrilaterals (nodes_per_elem = 4, counter-
- * clockwise, axis-aligned rectangles). Xn: dim * n_nodes (SoA); conn:
- * n_elems * 4 int32 node ids. PDMTS_ERR_UNSUPPORTED for other element kinds. */
+ * isotropic (Eq. 8-9). dim = 2: bilinear quadrilaterals (nodes_per_elem = 4,
+ * counter-clockwise, axis-aligned rectangles), plane stress with thickness
+ * `thickness`. dim = 3: trilinear hexahedra (nodes_per_elem = 8, axis-aligned
+ * boxes; bottom face counter-clockwise seen from +z, then the top face in
+ * the same order), `thickness` unused. Xn: dim * n_nodes (SoA); conn:
+ * n_elems * nodes_per_elem int32 node ids. 2 x 2 (x 2) Gauss points.
+ * PDMTS_ERR_UNSUPPORTED for other element kinds. */
 int fem_create(pdmts_ctx *ctx, int dim, int64_t n_nodes, const double *Xn, int64_t n_elems,
                int nodes_per_elem, const int32_t *conn, double E, double nu, double rho,
                double thickness, pdmts_fem **fe);
-/* Uniform traction on boundary edges: face_nodes n_faces * 2 node ids,
- * traction n_faces * dim [Pa]; consistent nodal loads (Eq. 8). Call before
- * arlequin_bind. */
+/* Uniform traction on boundary faces: face_nodes n_faces * 2 node ids (2D
+ * edges) or n_faces * 4 (3D planar quadrilaterals, in order around the face),
+ * traction n_faces * dim [Pa]; the load of a face is shared equally by its
+ * nodes (the consistent load on these straight edges and parallelograms,
+ * Eq. 8). Call before arlequin_bind. */
 int fem_set_traction(pdmts_fem *fe, int64_t n_faces, const int32_t *face_nodes, const double *traction);
 int fem_destroy(pdmts_fem *fe);
 /* Initial FE displacement and velocity (dim * n_nodes each, NULL = zero); the
@@ -258,7 +263,8 @@ int fem_read_acceleration(pdmts_fem *fe, double *a);
  * weights (pd_set_weights), assembles the alpha-weighted FE stiffness, lumped
  * mass and loads (Eq. 34), and builds the constraint operators: the
  * multiplier lives on the FE nodes of the overlap, G_FE = int_O N_k N_I dV,
- * G_PD = N_k(x_p) V_p. Afterwards mts_advance runs Algorithm 1. */
+ * G_PD = N_k(x_p) V_p. Both subdomains have the same dim (2 or 3; axis <
+ * dim). Afterwards mts_advance runs Algorithm 1. */
 int arlequin_bind(pdmts_ctx *ctx, pdmts_pd *pd, pdmts_fem *fe, int weight_kind, int n_bands,
                   const double *bands, pdmts_arl **arl);
 int arlequin_destroy(pdmts_arl *arl);

@@ -1,9 +1,10 @@
 """FP64 CPU oracle of the multi-time-step Arlequin coupling (test infrastructure only).
 
 Follows arXiv 2403.03605 Sec. 2.2-2.5 step by step:
-  * finite elements (Eq. 24 ff.): bilinear Q4, plane stress D (Eq. 9), 2 x 2 Gauss
-    points, stiffness and lumped mass weighted by the Arlequin weight alpha and
-    loads by alpha (Eq. 34);
+  * finite elements (Eq. 24 ff.): bilinear Q4 with plane stress D (Eq. 9) and
+    2 x 2 Gauss points, or trilinear Hex8 with the 3D isotropic D and 2 x 2 x 2
+    Gauss points; stiffness and lumped mass weighted by the Arlequin weight
+    alpha and loads by alpha (Eq. 34);
   * PD subdomain weighted by 1 - alpha (Eq. 17, Eq. 34), stepped by the C oracle
     (velocity Verlet, Eq. 38 with gamma = 1/2, beta = 0);
   * velocity constraint G_FE v_FE - G_PD v_PD = 0 (Eq. 33, Eq. 41) with the
@@ -42,10 +43,13 @@ from . import (PD, damage, family, pd_forces, pd_run, precrack)
 
 GAUSS = np.array([-1.0, 1.0]) / np.sqrt(3.0)
 NAT = np.array([[-1.0, -1.0], [1.0, -1.0], [1.0, 1.0], [-1.0, 1.0]])  # Q4 node natural coordinates
+# Hex8 corners: bottom face (zeta = -1) counter-clockwise seen from +z, then the top face
+NAT3 = np.array([[-1.0, -1.0, -1.0], [1.0, -1.0, -1.0], [1.0, 1.0, -1.0], [-1.0, 1.0, -1.0],
+                 [-1.0, -1.0, 1.0], [1.0, -1.0, 1.0], [1.0, 1.0, 1.0], [-1.0, 1.0, 1.0]])
 
 
 def band_weight(x, bands, kind, outside):
-    """Arlequin weight alpha at points x (2, n) (Sec. 3.2)."""
+    """Arlequin weight alpha at points x (dim, n) (Sec. 3.2)."""
     x = np.asarray(x)
     a = np.full(x.shape[1], float(outside))
     for b in bands:
@@ -69,14 +73,39 @@ def q4_shape(xi, eta):
     return N, dxi, deta
 
 
+def hex8_shape(xi, eta, zeta):
+    """Trilinear shape functions and their natural derivatives (8,), (3, 8)."""
+    p = 1 + NAT3[:, 0] * xi
+    q = 1 + NAT3[:, 1] * eta
+    r = 1 + NAT3[:, 2] * zeta
+    N = p * q * r / 8
+    dN = np.stack([NAT3[:, 0] * q * r, NAT3[:, 1] * p * r, NAT3[:, 2] * p * q]) / 8
+    return N, dN
+
+
+def hex8_gauss(xe):
+    """Yield (N, physical derivatives (3, 8), detJ, point) at the 2 x 2 x 2 Gauss points of xe (3, 8)."""
+    for gx in GAUSS:
+        for gy in GAUSS:
+            for gz in GAUSS:
+                N, dN = hex8_shape(gx, gy, gz)
+                J = dN @ xe.T  # J[i, j] = d x_j / d xi_i
+                yield N, np.linalg.solve(J, dN), np.linalg.det(J), xe @ N
+
+
 class FE:
-    """Alpha-weighted Q4 plane-stress discretisation of the CCM subdomain (Eq. 24 ff., Eq. 34)."""
+    """Alpha-weighted discretisation of the CCM subdomain (Eq. 24 ff., Eq. 34):
+    Q4 plane stress in 2D, Hex8 isotropic linear elasticity in 3D."""
 
     def __init__(self, mesh, E, nu, rho, thick, bands, kind, faces, face_traction):
         self.X = np.asarray(mesh.X, dtype=np.float64)
         self.conn = np.asarray(mesh.conn, dtype=np.int64)
         n = self.X.shape[1]
         self.n = n
+        self.dim = self.X.shape[0]
+        if self.dim == 3:
+            self._init3d(E, nu, rho, bands, kind, faces, face_traction)
+            return
         D = E / (1 - nu * nu) * np.array([[1, nu, 0], [nu, 1, 0], [0, 0, (1 - nu) / 2]])
         rows, cols, vals = [], [], []
         mass = np.zeros(n)
@@ -114,6 +143,46 @@ class FE:
                 P[node + n] += al * t[1] * L * thick / 2
         self.P = P
 
+    def _init3d(self, E, nu, rho, bands, kind, faces, face_traction):
+        n = self.n
+        lam = E * nu / ((1 + nu) * (1 - 2 * nu))
+        mu = E / (2 * (1 + nu))
+        D = np.zeros((6, 6))
+        D[:3, :3] = lam
+        D[[0, 1, 2], [0, 1, 2]] = lam + 2 * mu
+        D[[3, 4, 5], [3, 4, 5]] = mu
+        rows, cols, vals = [], [], []
+        mass = np.zeros(n)
+        for nodes in self.conn:
+            xe = self.X[:, nodes]  # (3, 8)
+            ke = np.zeros((24, 24))
+            for N, dNx, detJ, xg in hex8_gauss(xe):
+                B = np.zeros((6, 24))  # strains xx, yy, zz, yz, xz, xy; local dof a * 3 + d
+                B[0, 0::3] = dNx[0]
+                B[1, 1::3] = dNx[1]
+                B[2, 2::3] = dNx[2]
+                B[3, 1::3] = dNx[2]; B[3, 2::3] = dNx[1]
+                B[4, 0::3] = dNx[2]; B[4, 2::3] = dNx[0]
+                B[5, 0::3] = dNx[1]; B[5, 1::3] = dNx[0]
+                al = band_weight(xg.reshape(3, 1), bands, kind, 1.0)[0]
+                ke += al * (B.T @ D @ B) * detJ
+                mass[nodes] += al * rho * N * detJ
+            dof = np.stack([nodes, nodes + n, nodes + 2 * n], axis=1).reshape(-1)
+            for a in range(24):
+                for b in range(24):
+                    rows.append(dof[a]); cols.append(dof[b]); vals.append(ke[a, b])
+        self.K = sp.csr_matrix((vals, (rows, cols)), shape=(3 * n, 3 * n))
+        self.M = np.concatenate([mass, mass, mass])
+        P = np.zeros(3 * n)
+        for fn, t in zip(np.asarray(faces), np.asarray(face_traction)):
+            xf = self.X[:, fn]  # (3, 4), corners in order around the face
+            area = 0.5 * np.linalg.norm(np.cross(xf[:, 2] - xf[:, 0], xf[:, 3] - xf[:, 1]))
+            al = band_weight(xf.mean(axis=1).reshape(3, 1), bands, kind, 1.0)[0]
+            for node in fn:
+                for d in range(3):
+                    P[node + d * n] += al * t[d] * area / 4
+        self.P = P
+
 
 class MTSOracle:
     """Algorithm 1 (MTS coupling of PD and CCM) in FP64 on the CPU."""
@@ -137,16 +206,17 @@ class MTSOracle:
         self.alpha = band_weight(pb.lat.X, cp.bands, cp.weight_kind, 0.0)
         npd = pb.n
         self.npd = npd
-        self.u = np.zeros((2, npd)); self.v = np.zeros_like(self.u); self.a = np.zeros_like(self.u)
+        self.dim = dim = pb.lat.dim
+        self.u = np.zeros((dim, npd)); self.v = np.zeros_like(self.u); self.a = np.zeros_like(self.u)
         self.pd_inited = False
         # --- FE subdomain ---
         self.fe = FE(cp.fe, mat.E, mat.nu, mat.rho, mat.thickness, cp.bands, cp.weight_kind, cp.faces,
                      cp.face_traction)
         nfe = self.fe.n
         self.nfe = nfe
-        self.uf = np.zeros(2 * nfe); self.vf = np.zeros_like(self.uf); self.af = np.zeros_like(self.uf)
+        self.uf = np.zeros(dim * nfe); self.vf = np.zeros_like(self.uf); self.af = np.zeros_like(self.uf)
         if v0 is not None:  # uniform initial velocity (patch tests)
-            self.v[:] = np.asarray(v0, dtype=np.float64).reshape(2, 1)
+            self.v[:] = np.asarray(v0, dtype=np.float64).reshape(dim, 1)
             self.vf[:] = np.repeat(np.asarray(v0, dtype=np.float64), nfe)
         Keff = sp.diags(self.fe.M) + self.beta * self.dt_fe ** 2 * self.fe.K
         self.Keff_lu = spla.splu(Keff.tocsc())
@@ -171,7 +241,8 @@ class MTSOracle:
     def _build_G(self):
         cp, fe = self.cp, self.fe
         X = fe.X
-        cen = X[:, fe.conn].mean(axis=2)  # (2, ne)
+        dim = self.dim
+        cen = X[:, fe.conn].mean(axis=2)  # (dim, ne)
         in_band = np.zeros(fe.conn.shape[0], bool)
         for b in cp.bands:
             c = cen[b.axis]
@@ -181,27 +252,32 @@ class MTSOracle:
         self.lam_nodes = lam_nodes
         nl = len(lam_nodes)
         self.nlam_nodes = nl
-        self.nlam = 2 * nl
+        self.nlam = dim * nl
         pos = {int(k): i for i, k in enumerate(lam_nodes)}
         nfe, npd = self.nfe, self.npd
         thick = cp.pd.mat.thickness
-        # G_FE[k, I] = int_O N_k N_I dV, per component (2 x 2 Gauss)
+        # G_FE[k, I] = int_O N_k N_I dV, per component (2 x 2 or 2 x 2 x 2 Gauss)
         rows, cols, vals = [], [], []
         for e in self.ov_elems:
             nodes = fe.conn[e]
             xe = X[:, nodes]
-            for gx in GAUSS:
-                for gy in GAUSS:
-                    N, dxi, deta = q4_shape(gx, gy)
-                    J = np.array([[dxi @ xe[0], dxi @ xe[1]], [deta @ xe[0], deta @ xe[1]]])
-                    w = np.linalg.det(J) * thick
-                    for a in range(4):
-                        for b in range(4):
-                            k = pos[int(nodes[a])]
-                            for c in range(2):
-                                rows.append(c * nl + k); cols.append(c * nfe + int(nodes[b]))
-                                vals.append(N[a] * N[b] * w)
-        self.Gfe = sp.csr_matrix((vals, (rows, cols)), shape=(2 * nl, 2 * nfe))
+            if dim == 2:
+                pts = []
+                for gx in GAUSS:
+                    for gy in GAUSS:
+                        N, dxi, deta = q4_shape(gx, gy)
+                        J = np.array([[dxi @ xe[0], dxi @ xe[1]], [deta @ xe[0], deta @ xe[1]]])
+                        pts.append((N, np.linalg.det(J) * thick))
+            else:
+                pts = [(N, detJ) for N, _, detJ, _ in hex8_gauss(xe)]
+            for N, w in pts:
+                for a in range(len(nodes)):
+                    for b in range(len(nodes)):
+                        k = pos[int(nodes[a])]
+                        for c in range(dim):
+                            rows.append(c * nl + k); cols.append(c * nfe + int(nodes[b]))
+                            vals.append(N[a] * N[b] * w)
+        self.Gfe = sp.csr_matrix((vals, (rows, cols)), shape=(dim * nl, dim * nfe))
         # G_PD[k, p] = N_k(x_p) V_p for PD nodes inside overlap elements
         Xp = cp.pd.lat.X
         rows, cols, vals = [], [], []
@@ -209,26 +285,30 @@ class MTSOracle:
             nodes = fe.conn[e]
             xe = X[:, nodes]
             lo, hi = xe.min(axis=1), xe.max(axis=1)
-            sel = np.nonzero((Xp[0] > lo[0]) & (Xp[0] < hi[0]) & (Xp[1] > lo[1]) & (Xp[1] < hi[1]))[0]
-            for p in sel:
-                xi = 2 * (Xp[0, p] - lo[0]) / (hi[0] - lo[0]) - 1
-                et = 2 * (Xp[1, p] - lo[1]) / (hi[1] - lo[1]) - 1
-                N, _, _ = q4_shape(xi, et)
-                for a in range(4):
+            inside = np.ones(npd, bool)
+            for d in range(dim):
+                inside &= (Xp[d] > lo[d]) & (Xp[d] < hi[d])
+            for p in np.nonzero(inside)[0]:
+                xi = 2 * (Xp[:, p] - lo) / (hi - lo) - 1
+                if dim == 2:
+                    N, _, _ = q4_shape(xi[0], xi[1])
+                else:
+                    N, _ = hex8_shape(xi[0], xi[1], xi[2])
+                for a in range(len(nodes)):
                     k = pos[int(nodes[a])]
-                    for c in range(2):
+                    for c in range(dim):
                         rows.append(c * nl + k); cols.append(c * npd + int(p)); vals.append(N[a] * cp.pd.vol)
-        self.Gpd = sp.csr_matrix((vals, (rows, cols)), shape=(2 * nl, 2 * npd))
+        self.Gpd = sp.csr_matrix((vals, (rows, cols)), shape=(dim * nl, dim * npd))
 
     def interface_force_density(self, lam):
-        """g = G_PD^T lambda / V per PD node (2, npd)."""
-        return (self.Gpd.T @ lam).reshape(2, self.npd) / self.cp.pd.vol
+        """g = G_PD^T lambda / V per PD node (dim, npd)."""
+        return (self.Gpd.T @ lam).reshape(self.dim, self.npd) / self.cp.pd.vol
 
     # ----------------------------------------------------------------------
     def pd_link(self, lam, mu):
         """Link problem (Eq. 48b): zero start, load (j/m) G_PD^T lambda, no breaking."""
         m = self.m
-        u = np.zeros((2, self.npd)); v = np.zeros_like(u); a = np.zeros_like(u)
+        u = np.zeros((self.dim, self.npd)); v = np.zeros_like(u); a = np.zeros_like(u)
         theta = np.arange(1, m + 1, dtype=np.float64) / m
         g = self.interface_force_density(lam)
         mu_c = mu.copy()

@@ -196,6 +196,7 @@ struct pdmts_arl {
     std::vector<int32_t> ov_node, ov_k;
     std::vector<double> ov_N;
     int64_t n_ov = 0;
+    int corners = 4;                 // FE element corners per overlap PD node (4 in 2D, 8 in 3D)
     // device
     // G_FE^T by FE node (CSR): multiplier node and weight of each entry
     std::vector<int64_t> gfeT_ptr;
@@ -695,41 +696,157 @@ static void q4_element(const pdmts_fem *fe, const std::vector<BandDesc> &bands, 
         }
 }
 
-// Largest eigenvalue of the symmetric 8 x 8 matrix a (cyclic Jacobi rotations;
-// a is overwritten).
-static double sym8_max_eig(double a[8][8])
+// Hex8 corners in natural coordinates: the bottom face (zeta = -1)
+// counter-clockwise seen from +z, then the top face in the same order.
+static const double kHexNat[8][3] = {{-1, -1, -1}, {1, -1, -1}, {1, 1, -1}, {-1, 1, -1},
+                                     {-1, -1, 1},  {1, -1, 1},  {1, 1, 1},  {-1, 1, 1}};
+
+// Trilinear shape functions and their natural derivatives at (xi, eta, zeta).
+static void hex8_shape(const double xi, const double et, const double ze, double N[8], double dN[8][3])
 {
+    for (int a = 0; a < 8; ++a) {
+        const double p = 1 + kHexNat[a][0] * xi, q = 1 + kHexNat[a][1] * et, r = 1 + kHexNat[a][2] * ze;
+        N[a] = 0.125 * p * q * r;
+        dN[a][0] = 0.125 * kHexNat[a][0] * q * r;
+        dN[a][1] = 0.125 * kHexNat[a][1] * p * r;
+        dN[a][2] = 0.125 * kHexNat[a][2] * p * q;
+    }
+}
+
+// Jacobian of the Hex8 map at a point, its determinant, the physical shape
+// derivatives and the physical position.
+static double hex8_map(const double xe[8][3], const double N[8], const double dN[8][3], double dNx[8][3],
+                       double xg[3])
+{
+    double J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    for (int d = 0; d < 3; ++d)
+        xg[d] = 0.0;
+    for (int a = 0; a < 8; ++a)
+        for (int i = 0; i < 3; ++i) {
+            for (int j = 0; j < 3; ++j)
+                J[i][j] += dN[a][i] * xe[a][j];  // J[i][j] = d x_j / d xi_i
+            xg[i] += N[a] * xe[a][i];
+        }
+    const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                       J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                       J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+    double Ji[3][3];  // inverse of J
+    Ji[0][0] = (J[1][1] * J[2][2] - J[1][2] * J[2][1]) / det;
+    Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
+    Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
+    Ji[1][0] = (J[1][2] * J[2][0] - J[1][0] * J[2][2]) / det;
+    Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
+    Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
+    Ji[2][0] = (J[1][0] * J[2][1] - J[1][1] * J[2][0]) / det;
+    Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
+    Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+    // d N / d x_j = sum_i (J^-1)[j][i] d N / d xi_i
+    for (int a = 0; a < 8; ++a)
+        for (int j = 0; j < 3; ++j)
+            dNx[a][j] = Ji[j][0] * dN[a][0] + Ji[j][1] * dN[a][1] + Ji[j][2] * dN[a][2];
+    return det;
+}
+
+// alpha-weighted Hex8 isotropic linear-elastic element stiffness and lumped
+// mass with 2 x 2 x 2 Gauss points (Eq. 24 ff. in 3D, Eq. 34). Local dof
+// order: node-major, a * 3 + component.
+static void hex8_element(const pdmts_fem *fe, const std::vector<BandDesc> &bands, int kind, int64_t e,
+                         double ke[24][24], double me[8])
+{
+    const double g = 1.0 / std::sqrt(3.0);
+    const double lam = fe->E * fe->nu / ((1.0 + fe->nu) * (1.0 - 2.0 * fe->nu));
+    const double mu = fe->E / (2.0 * (1.0 + fe->nu));
+    double D[6][6] = {};
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j)
+            D[i][j] = lam;
+        D[i][i] = lam + 2.0 * mu;
+        D[3 + i][3 + i] = mu;
+    }
+    double xe[8][3];
+    for (int a = 0; a < 8; ++a)
+        for (int d = 0; d < 3; ++d)
+            xe[a][d] = fe->X[(size_t)d * fe->n + fe->conn[(size_t)e * 8 + a]];
+    for (int a = 0; a < 24; ++a)
+        for (int b = 0; b < 24; ++b)
+            ke[a][b] = 0.0;
+    for (int a = 0; a < 8; ++a)
+        me[a] = 0.0;
+    for (int gi = 0; gi < 2; ++gi)
+        for (int gj = 0; gj < 2; ++gj)
+            for (int gk = 0; gk < 2; ++gk) {
+                double N[8], dN[8][3], dNx[8][3], xg[3];
+                hex8_shape(gi ? g : -g, gj ? g : -g, gk ? g : -g, N, dN);
+                const double detJ = hex8_map(xe, N, dN, dNx, xg);
+                // strains (xx, yy, zz, yz, xz, xy), engineering shears
+                double B[6][24] = {};
+                for (int a = 0; a < 8; ++a) {
+                    const double *d = dNx[a];
+                    B[0][3 * a] = d[0];
+                    B[1][3 * a + 1] = d[1];
+                    B[2][3 * a + 2] = d[2];
+                    B[3][3 * a + 1] = d[2]; B[3][3 * a + 2] = d[1];
+                    B[4][3 * a] = d[2];     B[4][3 * a + 2] = d[0];
+                    B[5][3 * a] = d[1];     B[5][3 * a + 1] = d[0];
+                }
+                const double al = arlequin_alpha(bands, kind, xg, 1.0);
+                const double w = al * detJ;
+                double DB[6][24];
+                for (int p = 0; p < 6; ++p)
+                    for (int b = 0; b < 24; ++b) {
+                        double t = 0.0;
+                        for (int q = 0; q < 6; ++q)
+                            t += D[p][q] * B[q][b];
+                        DB[p][b] = t;
+                    }
+                for (int a = 0; a < 24; ++a)
+                    for (int b = 0; b < 24; ++b) {
+                        double t = 0.0;
+                        for (int p = 0; p < 6; ++p)
+                            t += B[p][a] * DB[p][b];
+                        ke[a][b] += w * t;
+                    }
+                for (int a = 0; a < 8; ++a)
+                    me[a] += al * fe->rho * N[a] * detJ;
+            }
+}
+
+// Largest eigenvalue of the symmetric n x n matrix a (row-major, cyclic
+// Jacobi rotations; a is overwritten).
+static double sym_max_eig(std::vector<double> &A, const int n)
+{
+    auto a = [&](int i, int j) -> double & { return A[(size_t)i * n + j]; };
     for (int sweep = 0; sweep < 64; ++sweep) {
         double off = 0.0, diag = 0.0;
-        for (int i = 0; i < 8; ++i) {
-            diag += a[i][i] * a[i][i];
-            for (int j = i + 1; j < 8; ++j)
-                off += a[i][j] * a[i][j];
+        for (int i = 0; i < n; ++i) {
+            diag += a(i, i) * a(i, i);
+            for (int j = i + 1; j < n; ++j)
+                off += a(i, j) * a(i, j);
         }
         if (off <= 1e-30 * diag)
             break;
-        for (int p = 0; p < 8; ++p)
-            for (int q = p + 1; q < 8; ++q) {
-                if (a[p][q] == 0.0)
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                if (a(p, q) == 0.0)
                     continue;
-                const double th = 0.5 * (a[q][q] - a[p][p]) / a[p][q];
+                const double th = 0.5 * (a(q, q) - a(p, p)) / a(p, q);
                 const double t = (th >= 0 ? 1.0 : -1.0) / (std::fabs(th) + std::sqrt(th * th + 1.0));
                 const double c = 1.0 / std::sqrt(t * t + 1.0), sn = t * c;
-                for (int k = 0; k < 8; ++k) {  // columns p, q
-                    const double akp = a[k][p], akq = a[k][q];
-                    a[k][p] = c * akp - sn * akq;
-                    a[k][q] = sn * akp + c * akq;
+                for (int k = 0; k < n; ++k) {  // columns p, q
+                    const double akp = a(k, p), akq = a(k, q);
+                    a(k, p) = c * akp - sn * akq;
+                    a(k, q) = sn * akp + c * akq;
                 }
-                for (int k = 0; k < 8; ++k) {  // rows p, q
-                    const double apk = a[p][k], aqk = a[q][k];
-                    a[p][k] = c * apk - sn * aqk;
-                    a[q][k] = sn * apk + c * aqk;
+                for (int k = 0; k < n; ++k) {  // rows p, q
+                    const double apk = a(p, k), aqk = a(q, k);
+                    a(p, k) = c * apk - sn * aqk;
+                    a(q, k) = sn * apk + c * aqk;
                 }
             }
     }
-    double mx = a[0][0];
-    for (int i = 1; i < 8; ++i)
-        mx = std::max(mx, a[i][i]);
+    double mx = a(0, 0);
+    for (int i = 1; i < n; ++i)
+        mx = std::max(mx, a(i, i));
     return mx;
 }
 
@@ -742,27 +859,43 @@ static int fe_assemble(pdmts_fem *fe, const std::vector<BandDesc> &bands, int ki
     // M = sum M_e, x'Kx / x'Mx <= max_e of the largest eigenvalue of
     // M_e^-1/2 K_e M_e^-1/2 (every term is a ratio of non-negative sums)
     double elem_bound = 0.0;
+    const int dim = fe->dim, npe = fe->npe, nle = dim * npe;  // local dofs: node-major, a * dim + d
+    std::vector<double> K((size_t)nle * nle), sk((size_t)nle * nle);
+    double me[8];
     for (int64_t e = 0; e < fe->ne; ++e) {
-        double ke[8][8], me[4];
-        q4_element(fe, bands, kind, e, ke, me);
-        if (me[0] > 0 && me[1] > 0 && me[2] > 0 && me[3] > 0) {
-            double sk[8][8];
+        if (dim == 2) {
+            double ke[8][8];
+            q4_element(fe, bands, kind, e, ke, me);
             for (int a = 0; a < 8; ++a)
                 for (int b = 0; b < 8; ++b)
-                    sk[a][b] = ke[a][b] / std::sqrt(me[a / 2] * me[b / 2]);
-            elem_bound = std::max(elem_bound, sym8_max_eig(sk));
+                    K[(size_t)a * nle + b] = ke[a][b];
+        } else {
+            static thread_local double ke[24][24];
+            hex8_element(fe, bands, kind, e, ke, me);
+            for (int a = 0; a < 24; ++a)
+                for (int b = 0; b < 24; ++b)
+                    K[(size_t)a * nle + b] = ke[a][b];
         }
-        int64_t dof[8];
-        for (int a = 0; a < 4; ++a) {
-            const int64_t node = fe->conn[(size_t)e * 4 + a];
-            dof[2 * a] = node;
-            dof[2 * a + 1] = n + node;
-            fe->mass[(size_t)node] += me[a];
-            fe->mass[(size_t)(n + node)] += me[a];
+        bool massive = true;
+        for (int a = 0; a < npe; ++a)
+            massive = massive && me[a] > 0;
+        if (massive) {
+            for (int a = 0; a < nle; ++a)
+                for (int b = 0; b < nle; ++b)
+                    sk[(size_t)a * nle + b] = K[(size_t)a * nle + b] / std::sqrt(me[a / dim] * me[b / dim]);
+            elem_bound = std::max(elem_bound, sym_max_eig(sk, nle));
         }
-        for (int a = 0; a < 8; ++a)
-            for (int b = 0; b < 8; ++b)
-                rows[(size_t)dof[a]][(int32_t)dof[b]] += ke[a][b];
+        int64_t dof[24];
+        for (int a = 0; a < npe; ++a) {
+            const int64_t node = fe->conn[(size_t)e * npe + a];
+            for (int d = 0; d < dim; ++d) {
+                dof[dim * a + d] = d * n + node;
+                fe->mass[(size_t)(d * n + node)] += me[a];
+            }
+        }
+        for (int a = 0; a < nle; ++a)
+            for (int b = 0; b < nle; ++b)
+                rows[(size_t)dof[a]][(int32_t)dof[b]] += K[(size_t)a * nle + b];
     }
     int W = 0;
     for (auto &r : rows)
@@ -785,10 +918,10 @@ static int fe_assemble(pdmts_fem *fe, const std::vector<BandDesc> &bands, int ki
         // padding (zero values) repeats the node's x dof in both of its rows, so
         // the x and y rows of a node keep one column list
         for (; e < fe->W; ++e)
-            fe->col[(size_t)i * fe->W + e] = (int32_t)(i < n ? i : i - n);
+            fe->col[(size_t)i * fe->W + e] = (int32_t)(i % n);
         gersh = std::max(gersh, rs / fe->mass[(size_t)i]);
     }
-    fe->paired_rows = true;
+    fe->paired_rows = dim == 2;
     for (int64_t i = 0; i < n && fe->paired_rows; ++i)
         for (int e = 0; e < fe->W; ++e)
             if (fe->col[(size_t)i * fe->W + e] != fe->col[(size_t)(n + i) * fe->W + e]) {
@@ -798,9 +931,31 @@ static int fe_assemble(pdmts_fem *fe, const std::vector<BandDesc> &bands, int ki
     // both are upper bounds; the element bound is the tighter on Q4 meshes
     // (a relative margin covers the rounding of the rotations)
     fe->gersh = elem_bound > 0 ? std::min(gersh, elem_bound * (1.0 + 1e-9)) : gersh;
-    // consistent traction loads, weighted by alpha at the face midpoint (Eq. 34)
+    // consistent traction loads, weighted by alpha at the face midpoint (Eq. 34):
+    // 2D segments (2 nodes, length x thickness), 3D planar quads (4 nodes,
+    // area from the diagonals), the load shared equally by the face's nodes
     fe->load.assign((size_t)ndof, 0.0);
-    const int64_t nf = (int64_t)fe->faces.size() / 2;
+    if (dim == 3) {
+        const int64_t nf3 = (int64_t)fe->faces.size() / 4;
+        for (int64_t f = 0; f < nf3; ++f) {
+            const int32_t *fn = &fe->faces[(size_t)4 * f];
+            double d1[3], d2[3], xm[3] = {0, 0, 0};
+            for (int d = 0; d < 3; ++d) {
+                d1[d] = fe->X[(size_t)d * n + fn[2]] - fe->X[(size_t)d * n + fn[0]];
+                d2[d] = fe->X[(size_t)d * n + fn[3]] - fe->X[(size_t)d * n + fn[1]];
+                for (int a = 0; a < 4; ++a)
+                    xm[d] += 0.25 * fe->X[(size_t)d * n + fn[a]];
+            }
+            const double cx = d1[1] * d2[2] - d1[2] * d2[1], cy = d1[2] * d2[0] - d1[0] * d2[2],
+                         cz = d1[0] * d2[1] - d1[1] * d2[0];
+            const double area = 0.5 * std::sqrt(cx * cx + cy * cy + cz * cz);
+            const double al = arlequin_alpha(bands, kind, xm, 1.0);
+            for (int a = 0; a < 4; ++a)
+                for (int d = 0; d < 3; ++d)
+                    fe->load[(size_t)(d * n + fn[a])] += al * fe->face_tr[(size_t)f * 3 + d] * area / 4.0;
+        }
+    }
+    const int64_t nf = dim == 2 ? (int64_t)fe->faces.size() / 2 : 0;
     for (int64_t f = 0; f < nf; ++f) {
         const int64_t i = fe->faces[(size_t)2 * f], j = fe->faces[(size_t)2 * f + 1];
         const double dx = fe->X[(size_t)j] - fe->X[(size_t)i], dy = fe->X[(size_t)n + j] - fe->X[(size_t)n + i];
@@ -975,8 +1130,8 @@ extern "C" int fem_create(pdmts_ctx *ctx, int dim, int64_t n_nodes, const double
     *out = nullptr;
     if (ctx->fem)
         return fail(PDMTS_ERR_STATE, "fem_create: context already has a finite-element subdomain");
-    if (dim != 2 || nodes_per_elem != 4)
-        return fail(PDMTS_ERR_UNSUPPORTED, "fem_create: this build supports 2D Q4 elements (dim 2, 4 nodes)");
+    if (!((dim == 2 && nodes_per_elem == 4) || (dim == 3 && nodes_per_elem == 8)))
+        return fail(PDMTS_ERR_UNSUPPORTED, "fem_create: supported elements are Q4 (dim 2, 4 nodes) and Hex8 (dim 3, 8 nodes)");
     if (n_nodes <= 0 || n_elems <= 0 || n_nodes >= ((int64_t)1 << 30))
         return fail(PDMTS_ERR_ARG, "fem_create: bad sizes");
     if (!(E > 0) || !(rho > 0) || !(thickness > 0) || !(nu > -1.0 && nu < 0.5))
@@ -1020,8 +1175,9 @@ extern "C" int fem_set_traction(pdmts_fem *fe, int64_t n_faces, const int32_t *f
     clear_error();
     if (!fe || n_faces < 0 || (n_faces > 0 && (!face_nodes || !traction)))
         return fail(PDMTS_ERR_ARG, "fem_set_traction: bad arguments");
-    std::vector<int32_t> f((size_t)2 * n_faces);
-    std::vector<double> t((size_t)2 * n_faces);
+    const int npf = fe->dim == 2 ? 2 : 4;  // nodes per face
+    std::vector<int32_t> f((size_t)npf * n_faces);
+    std::vector<double> t((size_t)fe->dim * n_faces);
     if (n_faces > 0 &&
         (cudaMemcpy(f.data(), face_nodes, sizeof(int32_t) * f.size(), cudaMemcpyDefault) != cudaSuccess ||
          cudaMemcpy(t.data(), traction, sizeof(double) * t.size(), cudaMemcpyDefault) != cudaSuccess))
@@ -1111,19 +1267,20 @@ static int build_constraint(pdmts_arl *A)
     pdmts_fem *fe = A->fe;
     pdmts_pd *pd = A->pd;
     const int64_t nfe = fe->n, npd = pd->n;
+    const int dim = fe->dim, npe = fe->npe;
     // overlap elements: centroid strictly inside a band
     std::vector<int64_t> ov_el;
     std::vector<char> is_lam((size_t)nfe, 0);
     for (int64_t e = 0; e < fe->ne; ++e) {
-        double c[2] = {0, 0};
-        for (int a = 0; a < 4; ++a)
-            for (int d = 0; d < 2; ++d)
-                c[d] += 0.25 * fe->X[(size_t)d * nfe + fe->conn[(size_t)e * 4 + a]];
+        double c[3] = {0, 0, 0};
+        for (int a = 0; a < npe; ++a)
+            for (int d = 0; d < dim; ++d)
+                c[d] += fe->X[(size_t)d * nfe + fe->conn[(size_t)e * npe + a]] / npe;
         for (const BandDesc &b : A->bands)
             if (c[b.axis] > b.lo && c[b.axis] < b.hi) {
                 ov_el.push_back(e);
-                for (int a = 0; a < 4; ++a)
-                    is_lam[(size_t)fe->conn[(size_t)e * 4 + a]] = 1;
+                for (int a = 0; a < npe; ++a)
+                    is_lam[(size_t)fe->conn[(size_t)e * npe + a]] = 1;
                 break;
             }
     }
@@ -1137,36 +1294,54 @@ static int build_constraint(pdmts_arl *A)
             A->lam_node.push_back((int32_t)i);
         }
     A->nl = (int64_t)A->lam_node.size();
-    A->nlam = 2 * A->nl;
-    // G_FE[k, I] = int_O N_k N_I dV (2 x 2 Gauss), rows of width 9
+    A->nlam = dim * A->nl;
+    A->corners = npe;
+    // G_FE[k, I] = int_O N_k N_I dV (2 x 2 Gauss in 2D, 2 x 2 x 2 in 3D), rows of width 9 or 27
     std::vector<std::map<int32_t, double>> grow((size_t)A->nl);
     const double g = 1.0 / std::sqrt(3.0);
     const double nat[4][2] = {{-1, -1}, {1, -1}, {1, 1}, {-1, 1}};
     for (int64_t e : ov_el) {
-        double xe[4][2];
-        for (int a = 0; a < 4; ++a)
-            for (int d = 0; d < 2; ++d)
-                xe[a][d] = fe->X[(size_t)d * nfe + fe->conn[(size_t)e * 4 + a]];
-        for (int gi = 0; gi < 2; ++gi)
-            for (int gj = 0; gj < 2; ++gj) {
-                const double xi = gi ? g : -g, et = gj ? g : -g;
-                double N[4], dxi[4], det_[4];
-                for (int a = 0; a < 4; ++a) {
-                    N[a] = 0.25 * (1 + nat[a][0] * xi) * (1 + nat[a][1] * et);
-                    dxi[a] = 0.25 * nat[a][0] * (1 + nat[a][1] * et);
-                    det_[a] = 0.25 * nat[a][1] * (1 + nat[a][0] * xi);
+        const int32_t *cn = &fe->conn[(size_t)e * npe];
+        if (dim == 2) {
+            double xe[4][2];
+            for (int a = 0; a < 4; ++a)
+                for (int d = 0; d < 2; ++d)
+                    xe[a][d] = fe->X[(size_t)d * nfe + cn[a]];
+            for (int gi = 0; gi < 2; ++gi)
+                for (int gj = 0; gj < 2; ++gj) {
+                    const double xi = gi ? g : -g, et = gj ? g : -g;
+                    double N[4], dxi[4], det_[4];
+                    for (int a = 0; a < 4; ++a) {
+                        N[a] = 0.25 * (1 + nat[a][0] * xi) * (1 + nat[a][1] * et);
+                        dxi[a] = 0.25 * nat[a][0] * (1 + nat[a][1] * et);
+                        det_[a] = 0.25 * nat[a][1] * (1 + nat[a][0] * xi);
+                    }
+                    double J00 = 0, J01 = 0, J10 = 0, J11 = 0;
+                    for (int a = 0; a < 4; ++a) {
+                        J00 += dxi[a] * xe[a][0]; J01 += dxi[a] * xe[a][1];
+                        J10 += det_[a] * xe[a][0]; J11 += det_[a] * xe[a][1];
+                    }
+                    const double w = (J00 * J11 - J01 * J10) * fe->thick;
+                    for (int a = 0; a < 4; ++a)
+                        for (int b = 0; b < 4; ++b)
+                            grow[(size_t)pos[(size_t)cn[a]]][cn[b]] += N[a] * N[b] * w;
                 }
-                double J00 = 0, J01 = 0, J10 = 0, J11 = 0;
-                for (int a = 0; a < 4; ++a) {
-                    J00 += dxi[a] * xe[a][0]; J01 += dxi[a] * xe[a][1];
-                    J10 += det_[a] * xe[a][0]; J11 += det_[a] * xe[a][1];
-                }
-                const double w = (J00 * J11 - J01 * J10) * fe->thick;
-                for (int a = 0; a < 4; ++a)
-                    for (int b = 0; b < 4; ++b)
-                        grow[(size_t)pos[(size_t)fe->conn[(size_t)e * 4 + a]]][fe->conn[(size_t)e * 4 + b]] +=
-                            N[a] * N[b] * w;
-            }
+        } else {
+            double xe[8][3];
+            for (int a = 0; a < 8; ++a)
+                for (int d = 0; d < 3; ++d)
+                    xe[a][d] = fe->X[(size_t)d * nfe + cn[a]];
+            for (int gi = 0; gi < 2; ++gi)
+                for (int gj = 0; gj < 2; ++gj)
+                    for (int gk = 0; gk < 2; ++gk) {
+                        double N[8], dN[8][3], dNx[8][3], xg[3];
+                        hex8_shape(gi ? g : -g, gj ? g : -g, gk ? g : -g, N, dN);
+                        const double w = hex8_map(xe, N, dN, dNx, xg);
+                        for (int a = 0; a < 8; ++a)
+                            for (int b = 0; b < 8; ++b)
+                                grow[(size_t)pos[(size_t)cn[a]]][cn[b]] += N[a] * N[b] * w;
+                    }
+        }
     }
     A->gfe_w = 0;
     for (auto &r : grow)
@@ -1199,32 +1374,36 @@ static int build_constraint(pdmts_arl *A)
                 A->gfeT_val[(size_t)j] = kv.second;
             }
     }
-    // PD nodes inside overlap elements: G_PD[k, p] = N_k(x_p) V_p
+    // PD nodes inside overlap elements: G_PD[k, p] = N_k(x_p) V_p, N the
+    // bilinear (2D) or trilinear (3D) shape of the axis-aligned element
     std::vector<std::vector<std::pair<int32_t, double>>> prow((size_t)A->nl);
     A->ov_node.clear(); A->ov_k.clear(); A->ov_N.clear();
     for (int64_t e : ov_el) {
-        double lo[2] = {INFINITY, INFINITY}, hi[2] = {-INFINITY, -INFINITY};
-        int32_t cn[4];
-        for (int a = 0; a < 4; ++a) {
-            cn[a] = fe->conn[(size_t)e * 4 + a];
-            for (int d = 0; d < 2; ++d) {
+        double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        const int32_t *cn = &fe->conn[(size_t)e * npe];
+        for (int a = 0; a < npe; ++a)
+            for (int d = 0; d < dim; ++d) {
                 lo[d] = std::min(lo[d], fe->X[(size_t)d * nfe + cn[a]]);
                 hi[d] = std::max(hi[d], fe->X[(size_t)d * nfe + cn[a]]);
             }
-        }
-        // axis-aligned rectangle: node a at (lo|hi)
         for (int64_t p = 0; p < npd; ++p) {
-            const double x = pd->X[(size_t)p], y = pd->X[(size_t)npd + p];
-            if (!(x > lo[0] && x < hi[0] && y > lo[1] && y < hi[1]))
+            bool inside = true;
+            double xi[3] = {0, 0, 0};
+            for (int d = 0; d < dim && inside; ++d) {
+                const double x = pd->X[(size_t)d * npd + p];
+                inside = x > lo[d] && x < hi[d];
+                xi[d] = 2.0 * (x - lo[d]) / (hi[d] - lo[d]) - 1.0;
+            }
+            if (!inside)
                 continue;
-            const double xi = 2.0 * (x - lo[0]) / (hi[0] - lo[0]) - 1.0;
-            const double et = 2.0 * (y - lo[1]) / (hi[1] - lo[1]) - 1.0;
             A->ov_node.push_back((int32_t)p);
-            for (int a = 0; a < 4; ++a) {
+            for (int a = 0; a < npe; ++a) {
                 // natural coordinates of the corner from its position
-                const double ax = fe->X[(size_t)cn[a]] > 0.5 * (lo[0] + hi[0]) ? 1.0 : -1.0;
-                const double ay = fe->X[(size_t)nfe + cn[a]] > 0.5 * (lo[1] + hi[1]) ? 1.0 : -1.0;
-                const double Na = 0.25 * (1 + ax * xi) * (1 + ay * et);
+                double Na = dim == 2 ? 0.25 : 0.125;
+                for (int d = 0; d < dim; ++d) {
+                    const double ad = fe->X[(size_t)d * nfe + cn[a]] > 0.5 * (lo[d] + hi[d]) ? 1.0 : -1.0;
+                    Na *= 1 + ad * xi[d];
+                }
                 const int32_t k = pos[(size_t)cn[a]];
                 A->ov_k.push_back(k);
                 A->ov_N.push_back(Na);
@@ -1252,8 +1431,8 @@ static int build_constraint(pdmts_arl *A)
     PDMTS_TRY(A->alloc(A->d_gpd_col, std::max<int64_t>((int64_t)A->gpd_col.size(), 1)));
     PDMTS_TRY(A->alloc(A->d_gpd_val, std::max<int64_t>((int64_t)A->gpd_val.size(), 1)));
     PDMTS_TRY(A->alloc(A->d_ov_node, std::max<int64_t>(A->n_ov, 1)));
-    PDMTS_TRY(A->alloc(A->d_ov_k, std::max<int64_t>(4 * A->n_ov, 1)));
-    PDMTS_TRY(A->alloc(A->d_ov_N, std::max<int64_t>(4 * A->n_ov, 1)));
+    PDMTS_TRY(A->alloc(A->d_ov_k, std::max<int64_t>(npe * A->n_ov, 1)));
+    PDMTS_TRY(A->alloc(A->d_ov_N, std::max<int64_t>(npe * A->n_ov, 1)));
     PDMTS_TRY(A->alloc(A->d_gfeT_ptr, (int64_t)A->gfeT_ptr.size()));
     PDMTS_TRY(A->alloc(A->d_gfeT_k, std::max<int64_t>((int64_t)A->gfeT_k.size(), 1)));
     PDMTS_TRY(A->alloc(A->d_gfeT_val, std::max<int64_t>((int64_t)A->gfeT_val.size(), 1)));
@@ -1398,11 +1577,11 @@ static int build_Hfe(pdmts_arl *A, double dtf, int64_t *launches)
     for (int64_t q0 = 0; q0 < nlam; q0 += batch) {
         const int nb = (int)std::min<int64_t>(batch, nlam - q0);
         PDMTS_CUDA_TRY(cudaMemsetAsync(A->d_B[0].p, 0, sizeof(double) * ndof * nb, s));
-        k_gfe_rhs<<<blocks(nb), 256, 0, s>>>(fe->n, 2, A->nl, A->gfe_w, A->d_gfe_col.p, A->d_gfe_val.p, q0, nb,
+        k_gfe_rhs<<<blocks(nb), 256, 0, s>>>(fe->n, fe->dim, A->nl, A->gfe_w, A->d_gfe_col.p, A->d_gfe_val.p, q0, nb,
                                              A->d_B[0].p);
         PDMTS_CUDA_TRY(cudaMemsetAsync(xb.p, 0, sizeof(double) * ndof * nb, s));
         PDMTS_TRY(fe_cheb_solve(fe, nb, xb.p, A->d_B[0].p, A->d_B[1].p, A->d_B[2].p, A->d_B[3].p, s, launches));
-        k_hfe_cols<<<blocks(nlam * nb), 256, 0, s>>>(fe->n, 2, A->nl, A->gfe_w, A->d_gfe_col.p, A->d_gfe_val.p, q0,
+        k_hfe_cols<<<blocks(nlam * nb), 256, 0, s>>>(fe->n, fe->dim, A->nl, A->gfe_w, A->d_gfe_col.p, A->d_gfe_val.p, q0,
                                                      nb, xb.p, -A->ctx->gamma_fe * dtf, A->d_Hfe.p);
         *launches += 2;
     }
@@ -1421,7 +1600,7 @@ static int fe_link_enqueue(pdmts_arl *A, double dt, double beta, double gamma, c
 {
     pdmts_fem *fe = A->fe;
     const int64_t ndof = fe->ndof();
-    k_gfe_lam<<<blocks(ndof), 256, 0, s>>>(fe->n, 2, A->nl, A->d_gfeT_ptr.p, A->d_gfeT_k.p, A->d_gfeT_val.p,
+    k_gfe_lam<<<blocks(ndof), 256, 0, s>>>(fe->n, fe->dim, A->nl, A->d_gfeT_ptr.p, A->d_gfeT_k.p, A->d_gfeT_val.p,
                                            A->d_lam.p, fe->d_bw.p);
     PDMTS_CUDA_TRY(cudaMemsetAsync(fe->d_aw.p, 0, sizeof(double) * ndof, s));
     ++*launches;
@@ -1454,7 +1633,7 @@ static int pd_link_run(pdmts_arl *A, const double *dev_lam, int m, cudaStream_t 
 {
     pdmts_pd *pd = A->pd;
     const bool f64 = pd->precision == PDMTS_FP64;
-    cudaError_t e = launch_interface_force(pd->dim, pd->n, A->n_ov, A->d_ov_node.p, A->d_ov_k.p, A->d_ov_N.p, 4,
+    cudaError_t e = launch_interface_force(pd->dim, pd->n, A->n_ov, A->d_ov_node.p, A->d_ov_k.p, A->d_ov_N.p, A->corners,
                                            dev_lam, A->nl, f64 ? 0.0 : 1.0 / pd->h, f64 ? pd->lk_g.p : nullptr,
                                            f64 ? nullptr : pd->lk_gf.p, s);
     if (e != cudaSuccess)
@@ -1479,20 +1658,26 @@ static int build_colors(pdmts_arl *A, int m, cudaStream_t s)
     const int64_t nlam = A->nlam, nl = A->nl;
     double hmax = 0.0;
     for (int64_t e = 0; e < fe->ne; ++e) {
-        const int32_t a = fe->conn[(size_t)e * 4], c = fe->conn[(size_t)e * 4 + 2];
-        hmax = std::max({hmax, std::fabs(fe->X[(size_t)c] - fe->X[(size_t)a]),
-                         std::fabs(fe->X[(size_t)fe->n + c] - fe->X[(size_t)fe->n + a])});
+        // opposite corners of the (axis-aligned) element
+        const int32_t a = fe->conn[(size_t)e * fe->npe], c = fe->conn[(size_t)e * fe->npe + (fe->dim == 2 ? 2 : 6)];
+        for (int d = 0; d < fe->dim; ++d)
+            hmax = std::max(hmax, std::fabs(fe->X[(size_t)d * fe->n + c] - fe->X[(size_t)d * fe->n + a]));
     }
     const double R = 2.0 * hmax + m * pd->horizon;
     auto xk = [&](int64_t q, int d) { return fe->X[(size_t)d * fe->n + A->lam_node[(size_t)(q % nl)]]; };
+    auto dist_inf = [&](int64_t q, int64_t o) {
+        double dd = 0.0;
+        for (int d = 0; d < fe->dim; ++d)
+            dd = std::max(dd, std::fabs(xk(q, d) - xk(o, d)));
+        return dd;
+    };
     std::vector<std::vector<int64_t>> colors;
     for (int64_t q = 0; q < nlam; ++q) {
         bool placed = false;
         for (auto &cl : colors) {
             bool ok = true;
             for (int64_t o : cl) {
-                const double dist = std::max(std::fabs(xk(q, 0) - xk(o, 0)), std::fabs(xk(q, 1) - xk(o, 1)));
-                if (dist <= 2.0 * R) {
+                if (dist_inf(q, o) <= 2.0 * R) {
                     ok = false;
                     break;
                 }
@@ -1514,8 +1699,7 @@ static int build_colors(pdmts_arl *A, int m, cudaStream_t s)
             unit[(size_t)(c * nlam + q)] = 1.0;
         for (int64_t r = 0; r < nlam; ++r)
             for (int64_t q : colors[(size_t)c]) {
-                const double dist = std::max(std::fabs(xk(q, 0) - xk(r, 0)), std::fabs(xk(q, 1) - xk(r, 1)));
-                if (dist <= R) {
+                if (dist_inf(q, r) <= R) {
                     owner[(size_t)(c * nlam + r)] = (int32_t)q;
                     break;
                 }
@@ -1649,7 +1833,7 @@ static int build_H(pdmts_arl *A, int m)
     for (int64_t cidx = 0; cidx < A->colors; ++cidx) {
         PDMTS_TRY(pd_link_run(A, A->d_units.p + cidx * nlam, m, s));
         // y = G_PD v_link
-        cudaError_t e = launch_constraint(2, nl, A->d_gpd_ptr.p, A->d_gpd_col.p, A->d_gpd_val.p, pd->n,
+        cudaError_t e = launch_constraint(pd->dim, nl, A->d_gpd_ptr.p, A->d_gpd_col.p, A->d_gpd_val.p, pd->n,
                                           f64 ? pd->lk_v.p : nullptr, f64 ? nullptr : pd->lk_v4.p,
                                           f64 ? nullptr : pd->lk_v2.p, pd->h, nullptr, nullptr, 0, 0, nullptr, 1.0,
                                           0.0, A->d_y.p, s);
@@ -1684,8 +1868,8 @@ extern "C" int arlequin_bind(pdmts_ctx *ctx, pdmts_pd *pd, pdmts_fem *fe, int we
         return fail(PDMTS_ERR_STATE, "arlequin_bind: context already has a coupling");
     if (pd->ctx != ctx || fe->ctx != ctx)
         return fail(PDMTS_ERR_ARG, "arlequin_bind: subdomains belong to another context");
-    if (pd->dim != 2 || fe->dim != 2)
-        return fail(PDMTS_ERR_UNSUPPORTED, "arlequin_bind: this build couples 2D subdomains");
+    if (pd->dim != fe->dim)
+        return fail(PDMTS_ERR_ARG, "arlequin_bind: PD subdomain in %dD, FE subdomain in %dD", pd->dim, fe->dim);
     if (weight_kind < PDMTS_WEIGHT_CONSTANT || weight_kind > PDMTS_WEIGHT_CUBIC)
         return fail(PDMTS_ERR_ARG, "arlequin_bind: unknown weight kind %d", weight_kind);
     std::vector<double> bv((size_t)5 * n_bands);
@@ -1693,7 +1877,7 @@ extern "C" int arlequin_bind(pdmts_ctx *ctx, pdmts_pd *pd, pdmts_fem *fe, int we
     std::vector<BandDesc> bl;
     for (int k = 0; k < n_bands; ++k) {
         BandDesc b{(int)bv[(size_t)5 * k], bv[(size_t)5 * k + 1], bv[(size_t)5 * k + 2], (int)bv[(size_t)5 * k + 3]};
-        if ((b.axis != 0 && b.axis != 1) || !(b.hi > b.lo) || (b.fe_side != -1 && b.fe_side != 1))
+        if (b.axis < 0 || b.axis >= fe->dim || !(b.hi > b.lo) || (b.fe_side != -1 && b.fe_side != 1))
             return fail(PDMTS_ERR_ARG, "arlequin_bind: band %d is malformed", k);
         bl.push_back(b);
     }
@@ -1710,7 +1894,9 @@ extern "C" int arlequin_bind(pdmts_ctx *ctx, pdmts_pd *pd, pdmts_fem *fe, int we
     // PD weights alpha_i (0 outside the bands)
     std::vector<double> alpha((size_t)pd->n);
     for (int64_t p = 0; p < pd->n; ++p) {
-        const double x[2] = {pd->X[(size_t)p], pd->X[(size_t)pd->n + p]};
+        double x[3] = {0, 0, 0};
+        for (int d = 0; d < pd->dim; ++d)
+            x[d] = pd->X[(size_t)d * pd->n + p];
         alpha[(size_t)p] = arlequin_alpha(bl, weight_kind, x, 0.0);
     }
     r = pd_set_weights(pd, alpha.data());
@@ -1849,7 +2035,7 @@ static int step_free_begin(pdmts_arl *A, cudaStream_t s, int64_t *launches)
     const bool f64 = pd->precision == PDMTS_FP64;
     // the FE free step may start once the previous step has ended
     PDMTS_CUDA_TRY(cudaEventRecord(A->ev_fork, s));
-    cudaError_t e = launch_interface_force(pd->dim, pd->n, A->n_ov, A->d_ov_node.p, A->d_ov_k.p, A->d_ov_N.p, 4,
+    cudaError_t e = launch_interface_force(pd->dim, pd->n, A->n_ov, A->d_ov_node.p, A->d_ov_k.p, A->d_ov_N.p, A->corners,
                                            A->d_lam0.p, A->nl, f64 ? 0.0 : 1.0 / pd->h, f64 ? pd->d_g.p : nullptr,
                                            f64 ? nullptr : pd->f_g.p, s);
     if (e != cudaSuccess)
@@ -1884,7 +2070,7 @@ static int step_lambda(pdmts_arl *A, cudaStream_t s, int64_t *launches, bool fe_
         PDMTS_CUDA_TRY(cudaStreamWaitEvent(s, A->ev_join, 0));
     const float4 *v4 = f64 ? nullptr : pd->f_v4.p;
     const float2 *v2 = f64 ? nullptr : pd->f_v2.p;
-    cudaError_t e = launch_constraint(2, A->nl, A->d_gpd_ptr.p, A->d_gpd_col.p, A->d_gpd_val.p, pd->n,
+    cudaError_t e = launch_constraint(pd->dim, A->nl, A->d_gpd_ptr.p, A->d_gpd_col.p, A->d_gpd_val.p, pd->n,
                                       f64 ? pd->d_v.p : nullptr, v4, v2, pd->h, A->d_gfe_col.p, A->d_gfe_val.p,
                                       A->gfe_w, fe->n, fe->d_v.p, -1.0, 1.0, A->d_y.p, s);
     if (e != cudaSuccess)
@@ -1914,7 +2100,7 @@ static int step_link_begin(pdmts_arl *A, const double *dev_lam, cudaStream_t s, 
 {
     pdmts_pd *pd = A->pd;
     const bool f64 = pd->precision == PDMTS_FP64;
-    cudaError_t e = launch_interface_force(pd->dim, pd->n, A->n_ov, A->d_ov_node.p, A->d_ov_k.p, A->d_ov_N.p, 4,
+    cudaError_t e = launch_interface_force(pd->dim, pd->n, A->n_ov, A->d_ov_node.p, A->d_ov_k.p, A->d_ov_N.p, A->corners,
                                            dev_lam, A->nl, f64 ? 0.0 : 1.0 / pd->h, f64 ? pd->lk_g.p : nullptr,
                                            f64 ? nullptr : pd->lk_gf.p, s);
     if (e != cudaSuccess)
@@ -2818,7 +3004,7 @@ extern "C" int arlequin_constraint_residual(pdmts_arl *A, double *residual, doub
     const bool f64 = pd->precision == PDMTS_FP64;
     std::vector<double> y((size_t)A->nlam), yf((size_t)A->nlam);
     for (int pass = 0; pass < 2; ++pass) {
-        cudaError_t e = launch_constraint(2, A->nl, A->d_gpd_ptr.p, A->d_gpd_col.p, A->d_gpd_val.p, pd->n,
+        cudaError_t e = launch_constraint(pd->dim, A->nl, A->d_gpd_ptr.p, A->d_gpd_col.p, A->d_gpd_val.p, pd->n,
                                           f64 ? pd->d_v.p : nullptr, f64 ? nullptr : pd->f_v4.p,
                                           f64 ? nullptr : pd->f_v2.p, pd->h, A->d_gfe_col.p, A->d_gfe_val.p,
                                           A->gfe_w, fe->n, fe->d_v.p, pass == 0 ? -1.0 : 0.0, 1.0, A->d_y.p, s);

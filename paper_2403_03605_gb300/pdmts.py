@@ -351,7 +351,7 @@ class ArlInfo(C.Structure):
 
 
 def fem_create(ctx, X, conn, *, E, nu, rho, thickness):
-    """X: (2, n) node positions; conn: (ne, 4) int32 Q4 connectivity."""
+    """X: (dim, n) node positions; conn: (ne, 4) Q4 (2D) or (ne, 8) Hex8 (3D) int32 connectivity."""
     X = _f64(X)
     conn = np.ascontiguousarray(conn, dtype=np.int32)
     h = _V()

@@ -365,3 +365,81 @@ def config4(seed: int = 3605, n: int = 64, n_coarse: int = 200) -> list[CoupledP
     """Batched: n independent coupled plates of uneven size, crack, load and m."""
     return [batch_member(N, c, T, m, n_coarse=n_coarse, name=f"batch_plate_{k}")
             for k, (N, c, T, m) in enumerate(config4_draws(seed, n))]
+
+
+def hex8_block(x0, y0, z0, nex, ney, nez, h, node_offset=0):
+    """Structured Hex8 block (nodes x fastest, then y, then z); each element's
+    corners: the bottom face (z low) counter-clockwise seen from +z, then the
+    top face in the same order."""
+    xs = x0 + h * np.arange(nex + 1)
+    ys = y0 + h * np.arange(ney + 1)
+    zs = z0 + h * np.arange(nez + 1)
+    Z, Y, Xg = np.meshgrid(zs, ys, xs, indexing="ij")
+    X = np.stack([Xg.reshape(-1), Y.reshape(-1), Z.reshape(-1)])
+
+    def nid(i, j, k):
+        return (k * (ney + 1) + j) * (nex + 1) + i
+
+    conn = []
+    for k in range(nez):
+        for j in range(ney):
+            for i in range(nex):
+                conn.append([nid(i, j, k), nid(i + 1, j, k), nid(i + 1, j + 1, k), nid(i, j + 1, k),
+                             nid(i, j, k + 1), nid(i + 1, j, k + 1), nid(i + 1, j + 1, k + 1), nid(i, j + 1, k + 1)])
+    return X, np.asarray(conn, dtype=np.int32) + node_offset
+
+
+def coupled_plate3d(Lx, Ly, Lz, strip, dx, h_fe, overlap, *, crack=None, traction=12e6, dt=20e-9, m=10,
+                    n_coarse=300, weight_kind=1, mat: Material | None = None, name="coupled_plate3d") -> CoupledProblem:
+    """3D counterpart of coupled_plate: box [0, Lx] x [0, Ly] x [0, Lz]; PD strip
+    y in strip at spacing dx (through the thickness); Hex8 elements of size h_fe
+    on [0, y0 + overlap] and [y1 - overlap, Ly]; traction on the faces y = 0 and
+    y = Ly; crack = (y_level, x_lo, x_hi) through the thickness."""
+    mat = mat or Material(nu=0.25)
+    y0, y1 = strip
+    nx, ny, nz = int(round(Lx / dx)), int(round((y1 - y0) / dx)), int(round(Lz / dx))
+    lat = Lattice((nx, ny, nz), dx, (0.0, y0, 0.0))
+    delta = HORIZON_FACTOR * dx
+    c, s0 = pmb_constants(3, mat, delta)
+    cuts = [Cut(1, crack[0], 0, crack[1], crack[2])] if crack else []
+    pd = PDProblem(name + "_pd", lat, mat, delta, c, s0, dt, m * n_coarse, cuts, np.zeros((3, lat.n)), dx ** 3)
+    nex, nez = int(round(Lx / h_fe)), int(round(Lz / h_fe))
+    neb = int(round((y0 + overlap) / h_fe))
+    net = int(round((Ly - (y1 - overlap)) / h_fe))
+    Xb, cb = hex8_block(0.0, 0.0, 0.0, nex, neb, nez, h_fe)
+    Xt, ct = hex8_block(0.0, y1 - overlap, 0.0, nex, net, nez, h_fe, node_offset=Xb.shape[1])
+    fe = FEMesh(np.concatenate([Xb, Xt], axis=1), np.concatenate([cb, ct]), h_fe)
+    nb = Xb.shape[1]
+
+    def bot(i, k):  # node on the face y = 0 of the bottom block
+        return k * (neb + 1) * (nex + 1) + i
+
+    def top(i, k):  # node on the face y = Ly of the top block
+        return nb + (k * (net + 1) + net) * (nex + 1) + i
+
+    faces, tr = [], []
+    for k in range(nez):
+        for i in range(nex):
+            faces.append([bot(i, k), bot(i + 1, k), bot(i + 1, k + 1), bot(i, k + 1)])
+            tr.append([0.0, -traction, 0.0])
+            faces.append([top(i, k), top(i + 1, k), top(i + 1, k + 1), top(i, k + 1)])
+            tr.append([0.0, +traction, 0.0])
+    bands = [Band(1, y0, y0 + overlap, -1), Band(1, y1 - overlap, y1, +1)]
+    return CoupledProblem(name, pd, fe, np.asarray(faces, dtype=np.int32), np.asarray(tr), bands, weight_kind, m,
+                          n_coarse)
+
+
+def config3() -> CoupledProblem:
+    """3D coupled plate 0.1 x 0.04 x 0.002 m: PD strip 16 mm at 0.25 mm
+    (400 x 64 x 8 nodes), Hex8 1 mm elsewhere, 2 mm overlap, 50 mm edge crack
+    at mid-height, 12 MPa, dt_PD 20 ns, m = 10, 300 coarse steps, nu = 1/4."""
+    return coupled_plate3d(0.1, 0.04, 0.002, (0.012, 0.028), 0.25e-3, 1e-3, 2e-3, crack=(0.020, 0.0, 0.050),
+                           dt=20e-9, m=10, n_coarse=300, name="coupled_plate3d_100x40x2mm_pd400x64x8")
+
+
+def small_coupled3d(m=3, n_coarse=6, weight_kind=1, crack=True, traction=12e6, dx=0.5e-3) -> CoupledProblem:
+    """A small 3D coupled plate the oracle finishes in seconds (tests): 8 x 8 x 2 mm,
+    PD strip y in [2, 6] mm, Hex8 1 mm, 1 mm overlap bands."""
+    return coupled_plate3d(0.008, 0.008, 0.002, (0.002, 0.006), dx, 1e-3, 1e-3,
+                           crack=(0.004, 0.0, 0.003) if crack else None, traction=traction, dt=20e-9, m=m,
+                           n_coarse=n_coarse, weight_kind=weight_kind, name="coupled_small3d")

@@ -101,12 +101,13 @@ class GpuMTS:
         self.fe = P.fem_create(ctx, cp.fe.X, cp.fe.conn, E=mat.E, nu=mat.nu, rho=mat.rho, thickness=mat.thickness)
         P.fem_set_traction(self.fe, cp.faces, cp.face_traction)
         self.arl = P.arlequin_bind(ctx, self.pd, self.fe, cp.weight_kind, [b.as_array() for b in cp.bands])
+        dim = pb.lat.dim
         if v0 is not None:
             v0 = np.asarray(v0, dtype=np.float64)
-            P.pd_set_state(self.pd, None, np.repeat(v0.reshape(2, 1), pb.n, axis=1))
+            P.pd_set_state(self.pd, None, np.repeat(v0.reshape(dim, 1), pb.n, axis=1))
             P.fem_set_state(self.fe, None, np.repeat(v0, cp.fe.n))
         P.mts_set_time(ctx, cp.dt_pd, cp.m, cp.gamma_fe, cp.beta_fe)
-        self.ndof = 2 * cp.fe.n
+        self.ndof = dim * cp.fe.n
 
     def run(self, n):
         P.mts_advance(self.ctx, n)

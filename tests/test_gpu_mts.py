@@ -180,3 +180,40 @@ def test_batch_members_alone_in_between_and_dropped(fresh):
     for g, s_ in zip(members[:2], solo[:2]):
         assert np.array_equal(g.u(), s_.u()) and np.array_equal(g.uf(), s_.uf())
         assert np.array_equal(g.lam(), s_.lam()) and np.array_equal(g.mu(), s_.mu())
+
+
+CASES3D = [
+    dict(name="3d_linear_m3", cp=lambda: W.small_coupled3d(m=3, n_coarse=6)),
+    dict(name="3d_cubic_m2_breaking", cp=lambda: W.small_coupled3d(m=2, n_coarse=6, weight_kind=2, traction=40e6)),
+]
+
+
+@pytest.mark.parametrize("case", CASES3D, ids=[c["name"] for c in CASES3D])
+def test_mts3d_fp64_matches_oracle(fresh, case):
+    """3D coupling (bond-based PD through the thickness, Hex8 FE): FP64 parity
+    with the oracle's Algorithm 1."""
+    cp = case["cp"]()
+    o = MTSOracle(cp).advance(cp.n_coarse)
+    g = GpuMTS(fresh(), cp, P.PDMTS_FP64).run(cp.n_coarse)
+    _compare(g, o, FP64_TOL, 1e-8)
+    assert P.arlequin_info(g.arl)["rebuilds"] == o.n_rebuilds
+    assert g.residual() <= 1e-12
+
+
+def test_mts3d_fp32_bulk_within_tolerance(fresh):
+    cp = W.small_coupled3d(m=3, n_coarse=6)
+    o = MTSOracle(cp).advance(cp.n_coarse)
+    g = GpuMTS(fresh(), cp, P.PDMTS_FP32_BULK).run(cp.n_coarse)
+    mm = np.count_nonzero(g.mu() != o.mu) / len(o.mu)
+    print(f"MTS 3D fp32-bulk: rel-L2 u_pd {rel_l2(g.u(), o.u):.2e}, u_fe {rel_l2(g.uf(), o.uf):.2e}, mismatch {mm:.2e}")
+    assert rel_l2(g.u(), o.u) <= 1e-4 and rel_l2(g.uf(), o.uf) <= 1e-4
+    assert mm <= 1e-3
+    assert g.residual() <= 1e-5
+
+
+def test_mts3d_uniform_velocity_patch(fresh):
+    cp = W.small_coupled3d(m=2, n_coarse=3, crack=False, traction=0.0)
+    v0 = np.array([1.0, -2.0, 0.5])
+    g = GpuMTS(fresh(), cp, P.PDMTS_FP64, v0=v0).run(3)
+    assert np.abs(g.v() - v0.reshape(3, 1)).max() <= 1e-12 * 2.0
+    assert np.abs(g.vf() - np.repeat(v0, cp.fe.n)).max() <= 1e-12 * 2.0

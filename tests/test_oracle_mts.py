@@ -73,3 +73,35 @@ def test_rebuild_rule_matches_rebuilding_every_step():
     assert (b.mu != 1).sum() > (a.mu != 1).sum() - 1 and (a.mu == 0).sum() > 0
     assert np.array_equal(a.u, b.u) and np.array_equal(a.uf, b.uf) and np.array_equal(a.mu, b.mu)
     assert a.n_rebuilds < b.n_rebuilds
+
+
+def test_3d_coupling_constraint_operator_and_patch():
+    """3D (Hex8 FE, bond-based PD through the thickness): the velocity constraint
+    holds after every coarse step, the interface operator is symmetric negative
+    definite, and a uniform velocity field stays uniform with lambda = 0."""
+    cp = W.small_coupled3d(m=3, n_coarse=3)
+    o = MTSOracle(cp).advance(3)
+    assert max(o.residuals) <= 1e-12
+    H = o.H
+    assert np.abs(H - H.T).max() <= 1e-12 * np.abs(H).max()
+    assert np.linalg.eigvalsh(0.5 * (H + H.T)).max() < 0
+    v0 = np.array([1.0, -2.0, 0.5])
+    cp2 = W.small_coupled3d(m=2, n_coarse=2, crack=False, traction=0.0)
+    o2 = MTSOracle(cp2, v0=v0).advance(2)
+    assert np.abs(o2.v - v0.reshape(3, 1)).max() <= 1e-12 * 2.0
+    assert np.abs(o2.vf - np.repeat(v0, o2.nfe)).max() <= 1e-12 * 2.0
+    force_scale = cp2.pd.mat.rho * 2.0 / (cp2.m * cp2.dt_pd)
+    assert np.abs(o2.lam).max() <= 1e-9 * force_scale
+
+
+def test_hex8_stiffness_rigid_modes_and_volume():
+    """The Hex8 element stiffness has exactly the six rigid-body modes as its
+    null space, and the lumped mass sums to rho times the volume."""
+    from oracle.mts import FE
+    X, conn = W.hex8_block(0.0, 0.0, 0.0, 1, 1, 1, 2e-3)
+    mesh = W.FEMesh(X, conn, 2e-3)
+    fe = FE(mesh, 72e9, 0.25, 2440.0, 1.0, [], 1, np.zeros((0, 4), np.int32), np.zeros((0, 3)))
+    K = fe.K.toarray()
+    ev = np.linalg.eigvalsh(K)
+    assert np.sum(np.abs(ev) <= 1e-9 * ev.max()) == 6
+    assert abs(fe.M.sum() / 3 - 2440.0 * (2e-3) ** 3) <= 1e-12 * 2440.0 * (2e-3) ** 3
