@@ -37,6 +37,7 @@ import numpy as np  # noqa: E402
 WORKLOAD = dict(name="pd_strip_2000x400_dx0.05mm_m20_fp32bulk", nx=2000, ny=400, dx=0.05e-3, crack=0.05,
                 traction=12e6, dt=5e-9, m=20)
 COUPLED_NAME = "coupled_plate_100x40mm_pd2000x400_fe0.5mm_m20_fp32bulk"
+COUPLED3D_NAME = "coupled_plate3d_100x40x2mm_pd400x64x8_hex1mm_m10_fp32bulk"
 METRIC = "PD bond updates/s"
 UNIT = "bond updates/s"
 
@@ -115,6 +116,9 @@ def algorithmic_bytes(info, pb, with_body=True, coupled=False):
     per bond) is read once. Sliced-ELL layout: per directed bond a 4-byte
     family word and one status bit."""
     nb, n = info["n_bonds"], info["n"]
+    if info["dim"] == 3:  # u, v: 24 B pairs (hi xyz + lo xyz); a: 16 B; loads 12 B
+        per_node = 24 + 24 + 24 + 24 + 16 + 16 + 4 + (12 if with_body else 0) + (16 if coupled else 0)
+        return 4 * nb + nb / 8.0 + per_node * n, per_node
     per_node = 16 + 16 + 16 + 16 + 8 + 8 + 4 + (8 if with_body else 0) + (12 if coupled else 0)
     if info["layout"] == 1:
         return (per_node + 4) * n, per_node + 4
@@ -189,7 +193,7 @@ def setup_ours(P, ctx, workload):
         P.pd_set_body_force(pd, pb.b)
         P.mts_set_time(ctx, pb.dt, m)
         return pd, None, None, P.pd_info(pd), pb, m, None
-    cp = W.config2()
+    cp = W.config3() if workload == "coupled3d" else W.config2()
     pd, fe, arl = make_coupled(P, ctx, cp)
     return pd, fe, arl, P.pd_info(pd), cp.pd, cp.m, cp
 
@@ -199,10 +203,13 @@ def make_coupled(P, ctx, cp):
     pb = cp.pd
     mat = pb.mat
     pd = P.pd_create(ctx, pb.lat.X, horizon=pb.delta, c=pb.c, s0=pb.s0, rho=mat.rho, vol_uniform=pb.vol,
+                     micro_kind=pb.extra.get("micro", P.PDMTS_MICRO_POWER), l=pb.extra.get("l", 0.0),
                      precision=P.PDMTS_FP32_BULK)
     P.pd_set_precrack(pd, [c.as_array() for c in pb.cuts])
     fe = P.fem_create(ctx, cp.fe.X, cp.fe.conn, E=mat.E, nu=mat.nu, rho=mat.rho, thickness=mat.thickness)
     P.fem_set_traction(fe, cp.faces, cp.face_traction)
+    if cp.fixed is not None:
+        P.fem_set_fixed(fe, cp.fixed)
     arl = P.arlequin_bind(ctx, pd, fe, cp.weight_kind, [b.as_array() for b in cp.bands])
     P.mts_set_time(ctx, cp.dt_pd, cp.m, cp.gamma_fe, cp.beta_fe)
     return pd, fe, arl
@@ -339,7 +346,7 @@ def run_ours(args, rank, world, local_rank):
     B.build()
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    coupled = args.workload == "coupled"
+    coupled = args.workload in ("coupled", "coupled3d")
     stream = torch.cuda.current_stream(dev)
     ctx = P.pdmts_ctx_create(local_rank, stream.cuda_stream)
     t_setup = time.perf_counter()
@@ -394,7 +401,7 @@ def run_ours(args, rank, world, local_rank):
     # lattice kernel of each tile configuration, as listed at pd_set_lattice_tile
     lat_kernels = ["k_pd_step_lattice2d<false,2,3>", "k_pd_step_lattice2d<false,2,4>",
                    "k_pd_step_lattice2d_pipe<false,2,2>", "k_pd_step_lattice2d_pipe<false,1,4>"]
-    kname = lat_kernels[tile] if info["layout"] == 1 and tile >= 0 else "k_pd_step_f32<2>"
+    kname = lat_kernels[tile] if info["layout"] == 1 and tile >= 0 else f"k_pd_step_f32<{info['dim']}>"
     traffic = None
     tfile = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tfile):
@@ -413,7 +420,7 @@ def run_ours(args, rank, world, local_rank):
     b_np = np.zeros((pb.dim, pb.n)) if coupled else np.ascontiguousarray(pb.b)
     b_host = torch.from_numpy(b_np).pin_memory()
     u_host = torch.empty((pb.dim, pb.n), dtype=torch.float64).pin_memory()
-    nfe_dof = 2 * cp.fe.n if coupled else 0
+    nfe_dof = pb.dim * cp.fe.n if coupled else 0
     uf_host = torch.empty(max(nfe_dof, 1), dtype=torch.float64).pin_memory()
     P.pd_set_body_force(pd, b_host)  # first upload allocates the load arrays (outside the timing)
     e2e_steps = max(3, min(args.steps, 10))
@@ -434,14 +441,15 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- CPU baseline: the FP64 oracle on a bounded sample ----------------
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload != "coupled3d":
         nsub = 20
         rate, dt, _ = oracle_sample(make_problem(), nsub)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{nsub} FP64 oracle PD substeps of the same 800,000-node lattice ({dt:.1f} s)"}
 
     if rank == 0:
-        cfg = {"workload": COUPLED_NAME if coupled else WORKLOAD["name"], "pd_nodes": pb.n,
+        cfg = {"workload": (COUPLED3D_NAME if args.workload == "coupled3d" else COUPLED_NAME) if coupled
+               else WORKLOAD["name"], "pd_nodes": pb.n,
                "directed_bonds": info["n_bonds"], "m": m,
                "family_layout": "lattice bond words" if info["layout"] == 1 else "sliced ELL",
                "lattice_tile": tile,
@@ -490,7 +498,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["coupled", "pd", "batch"], default="coupled")
+    ap.add_argument("--workload", choices=["coupled", "pd", "batch", "coupled3d"], default="coupled")
     ap.add_argument("--batch-members", type=int, default=64, help="members of the batched workload")
     ap.add_argument("--lattice-tile", type=int, default=-1,
                     help="fix the lattice kernel tile configuration (default: autotune)")

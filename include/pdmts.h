@@ -246,9 +246,18 @@ int fem_create(pdmts_ctx *ctx, int dim, int64_t n_nodes, const double *Xn, int64
  * nodes (the consistent load on these straight edges and parallelograms,
  * Eq. 8). Call before arlequin_bind. */
 int fem_set_traction(pdmts_fem *fe, int64_t n_faces, const int32_t *face_nodes, const double *traction);
+/* Dirichlet boundary (Sec. 3.2: the beam's fixed end): dofs[n_fixed] are dof
+ * ids d * n_nodes + node (SoA, host or device memory) held at zero
+ * displacement, velocity and acceleration; n_fixed = 0 clears the set.
+ * Elimination keeps each fixed row and column only its diagonal, and the
+ * fixed dofs' loads are dropped. Call before arlequin_bind; arlequin_bind
+ * fails with PDMTS_ERR_ARG when a fixed dof belongs to an overlap element.
+ * PDMTS_ERR_ARG for an id out of range, PDMTS_ERR_STATE after binding. */
+int fem_set_fixed(pdmts_fem *fe, int64_t n_fixed, const int64_t *dofs);
 int fem_destroy(pdmts_fem *fe);
 /* Initial FE displacement and velocity (dim * n_nodes each, NULL = zero); the
- * acceleration follows from M a = P - K u. Call after arlequin_bind. */
+ * acceleration follows from M a = P - K u; entries at fixed dofs are taken
+ * as zero. Call after arlequin_bind. */
 int fem_set_state(pdmts_fem *fe, const double *u, const double *v);
 /* FE displacement, velocity, acceleration (dim * n_nodes doubles, SoA). */
 int fem_read_displacement(pdmts_fem *fe, double *u);

@@ -30,6 +30,8 @@ Readings (each listed in the design doc):
   * Weights (Sec. 3.2): with t = distance to the FE boundary / overlap width,
     alpha = t (linear), t^3 (cubic) or 1/2 (constant) inside a band; 1 on the
     FE-only side, 0 on the PD-only side.
+  * Dirichlet dofs (the beam's fixed end, Sec. 3.2) are eliminated: Newmark
+    solves for the free dofs only and the fixed ones stay zero.
 
 Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg may use it.
 """
@@ -39,7 +41,7 @@ import numpy as np
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
-from . import (PD, damage, family, pd_forces, pd_run, precrack)
+from . import (MICRO_POWER, PD, damage, family, pd_forces, pd_run, precrack)
 
 GAUSS = np.array([-1.0, 1.0]) / np.sqrt(3.0)
 NAT = np.array([[-1.0, -1.0], [1.0, -1.0], [1.0, 1.0], [-1.0, 1.0]])  # Q4 node natural coordinates
@@ -184,6 +186,55 @@ class FE:
         self.P = P
 
 
+class Newmark:
+    """K_eff = M + beta dt^2 K (Eq. 39) on the free dofs: solve() returns the
+    acceleration increment of a right-hand side with the fixed dofs at zero."""
+
+    def __init__(self, fe, dt, beta, fixed=None):
+        nd = fe.dim * fe.n
+        self.fixed = np.unique(np.asarray([] if fixed is None else fixed, dtype=np.int64))
+        free = np.ones(nd, bool)
+        free[self.fixed] = False
+        self.free = np.nonzero(free)[0]
+        self.nd = nd
+        self.fe = fe
+        Keff = (sp.diags(fe.M) + beta * dt ** 2 * fe.K).tocsr()[self.free][:, self.free]
+        self.lu = spla.splu(Keff.tocsc())
+
+    def solve(self, r):
+        x = np.zeros(self.nd)
+        x[self.free] = self.lu.solve(np.asarray(r)[self.free])
+        return x
+
+    def initial_acceleration(self, u):
+        a = (self.fe.P - self.fe.K @ u) / self.fe.M
+        a[self.fixed] = 0.0
+        return a
+
+
+def newmark_fe(fp, n_steps, record):
+    """Undecomposed finite-element reference (Table 1, cases 1 and 2): the
+    whole body as one FE subdomain (alpha = 1), Newmark with gamma, beta of
+    `fp` (beta = 0 with the lumped mass is the explicit scheme), fixed dofs
+    eliminated, starting at rest under the constant traction load. Returns
+    u at the dof ids `record` after each step, (n_steps, len(record))."""
+    mat = fp.mat
+    fe = FE(fp.mesh, mat.E, mat.nu, mat.rho, mat.thickness, [], 0, fp.faces, fp.face_traction)
+    dt, g_, b_ = fp.dt, fp.gamma, fp.beta
+    nw = Newmark(fe, dt, b_, fp.fixed)
+    u = np.zeros(fe.dim * fe.n)
+    v = np.zeros_like(u)
+    a = nw.initial_acceleration(u)
+    out = np.zeros((n_steps, len(record)))
+    for k in range(n_steps):
+        ut = u + dt * v + (0.5 - b_) * dt * dt * a
+        vt = v + (1 - g_) * dt * a
+        a = nw.solve(fe.P - fe.K @ ut)
+        u, v = ut + b_ * dt * dt * a, vt + g_ * dt * a
+        out[k] = u[record]
+    return out
+
+
 class MTSOracle:
     """Algorithm 1 (MTS coupling of PD and CCM) in FP64 on the CPU."""
 
@@ -197,7 +248,8 @@ class MTSOracle:
         self.gamma, self.beta = cp.gamma_fe, cp.beta_fe
         self.rebuild_mode = rebuild
         # --- PD subdomain (Eq. 1-5, weighted by 1 - alpha) ---
-        self.pd = PD(pb.lat.X, pb.vol, pb.delta, pb.c, pb.s0, mat.rho, cp.dt_pd, breaking=breaking)
+        self.pd = PD(pb.lat.X, pb.vol, pb.delta, pb.c, pb.s0, mat.rho, cp.dt_pd, breaking=breaking,
+                     micro=pb.extra.get("micro", MICRO_POWER), l=pb.extra.get("l", 0.0))
         self.rp, self.col = family(pb.lat.X, pb.delta)
         if pb.cuts:
             self.mu, _ = precrack(pb.lat.P, self.rp, self.col, [c.in_half_units(pb.lat) for c in pb.cuts])
@@ -218,10 +270,11 @@ class MTSOracle:
         if v0 is not None:  # uniform initial velocity (patch tests)
             self.v[:] = np.asarray(v0, dtype=np.float64).reshape(dim, 1)
             self.vf[:] = np.repeat(np.asarray(v0, dtype=np.float64), nfe)
-        Keff = sp.diags(self.fe.M) + self.beta * self.dt_fe ** 2 * self.fe.K
-        self.Keff_lu = spla.splu(Keff.tocsc())
+        self.solver = Newmark(self.fe, self.dt_fe, self.beta, getattr(cp, "fixed", None))
+        if v0 is not None:
+            self.vf[self.solver.fixed] = 0.0
         # initial acceleration from the equation of motion at t_0 with lambda_0 = 0
-        self.af = (self.fe.P - self.fe.K @ self.uf) / self.fe.M
+        self.af = self.solver.initial_acceleration(self.uf)
         # --- multiplier space and constraint matrices (Eq. 33, Eq. 41) ---
         self._build_G()
         self.lam = np.zeros(self.nlam)  # lambda_0 = 0 at t = 0
@@ -249,6 +302,8 @@ class MTSOracle:
             in_band |= (c > b.lo) & (c < b.hi)
         self.ov_elems = np.nonzero(in_band)[0]
         lam_nodes = np.unique(fe.conn[self.ov_elems].reshape(-1))
+        for d in range(dim):  # a fixed dof carries no multiplier force
+            assert not np.isin(d * self.nfe + lam_nodes, self.solver.fixed).any(), "fixed dof in the overlap"
         self.lam_nodes = lam_nodes
         nl = len(lam_nodes)
         self.nlam_nodes = nl
@@ -318,7 +373,7 @@ class MTSOracle:
 
     def fe_link(self, lam):
         """FE link response (Eq. 47b with Newmark): a = -K_eff^-1 G_FE^T lambda."""
-        aw = -self.Keff_lu.solve(self.Gfe.T @ lam)
+        aw = -self.solver.solve(self.Gfe.T @ lam)
         return self.beta * self.dt_fe ** 2 * aw, self.gamma * self.dt_fe * aw, aw
 
     def build_H(self):
@@ -343,7 +398,7 @@ class MTSOracle:
         # free FE problem (Eq. 47a with Newmark, Eq. 39)
         ut = self.uf + dtf * self.vf + (0.5 - b_) * dtf * dtf * self.af
         vt = self.vf + (1 - g_) * dtf * self.af
-        af = self.Keff_lu.solve(self.fe.P - self.fe.K @ ut)
+        af = self.solver.solve(self.fe.P - self.fe.K @ ut)
         Vu, Vv, Va = ut + b_ * dtf * dtf * af, vt + g_ * dtf * af, af
         # free PD problem (Eq. 48a): m substeps, multiplier (1 - j/m) lambda_0
         mu_start = self.mu.copy()

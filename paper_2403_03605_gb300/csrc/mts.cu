@@ -99,6 +99,7 @@ struct pdmts_fem {
     double E = 0, nu = 0, rho = 0, thick = 1;
     std::vector<int32_t> faces;       // nf * 2
     std::vector<double> face_tr;      // nf * dim
+    std::vector<char> fixed;          // ndof flags (empty: no Dirichlet dof)
     // assembled operators (host copies of the alpha-weighted matrices)
     int W = 18;                       // ELL width (2D Q4: 9 nodes x 2 components)
     std::vector<int32_t> col;         // ndof * W
@@ -897,6 +898,15 @@ static int fe_assemble(pdmts_fem *fe, const std::vector<BandDesc> &bands, int ki
             for (int b = 0; b < nle; ++b)
                 rows[(size_t)dof[a]][(int32_t)dof[b]] += K[(size_t)a * nle + b];
     }
+    // Dirichlet dofs (held at zero): their rows and columns keep only the
+    // diagonal, so K u, the residual and every iterate vanish there exactly and
+    // the free dofs see the reduced system; the entries stay in place (as
+    // zeros) so the x and y rows of a node keep one column list
+    if (!fe->fixed.empty())
+        for (int64_t i = 0; i < ndof; ++i)
+            for (auto &kv : rows[(size_t)i])
+                if (kv.first != i && (fe->fixed[(size_t)i] || fe->fixed[(size_t)kv.first]))
+                    kv.second = 0.0;
     int W = 0;
     for (auto &r : rows)
         W = std::max<int>(W, (int)r.size());
@@ -967,6 +977,10 @@ static int fe_assemble(pdmts_fem *fe, const std::vector<BandDesc> &bands, int ki
             for (int d = 0; d < 2; ++d)
                 fe->load[(size_t)(d * n + node)] += al * fe->face_tr[(size_t)f * 2 + d] * L * fe->thick / 2.0;
     }
+    if (!fe->fixed.empty())
+        for (int64_t i = 0; i < ndof; ++i)
+            if (fe->fixed[(size_t)i])
+                fe->load[(size_t)i] = 0.0;
     cudaStream_t s = fe->ctx->stream;
     PDMTS_TRY(fe->alloc(fe->d_col, ndof * fe->W));
     PDMTS_TRY(fe->alloc(fe->d_K, ndof * fe->W));
@@ -1195,6 +1209,28 @@ extern "C" int fem_set_traction(pdmts_fem *fe, int64_t n_faces, const int32_t *f
     return PDMTS_OK;
 }
 
+extern "C" int fem_set_fixed(pdmts_fem *fe, int64_t n_fixed, const int64_t *dofs)
+{
+    clear_error();
+    if (!fe || n_fixed < 0 || (n_fixed > 0 && !dofs))
+        return fail(PDMTS_ERR_ARG, "fem_set_fixed: bad arguments");
+    if (fe->assembled)
+        return fail(PDMTS_ERR_STATE, "fem_set_fixed: fix dofs before arlequin_bind");
+    std::vector<int64_t> d((size_t)n_fixed);
+    if (n_fixed > 0 && cudaMemcpy(d.data(), dofs, sizeof(int64_t) * d.size(), cudaMemcpyDefault) != cudaSuccess)
+        return fail(PDMTS_ERR_CUDA, "fem_set_fixed: copying inputs failed");
+    std::vector<char> f;
+    if (n_fixed > 0)
+        f.assign((size_t)fe->ndof(), 0);
+    for (int64_t k : d) {
+        if (k < 0 || k >= fe->ndof())
+            return fail(PDMTS_ERR_ARG, "fem_set_fixed: dof %lld out of range", (long long)k);
+        f[(size_t)k] = 1;
+    }
+    fe->fixed.swap(f);
+    return PDMTS_OK;
+}
+
 extern "C" int fem_destroy(pdmts_fem *fe)
 {
     clear_error();
@@ -1238,6 +1274,10 @@ extern "C" int fem_set_state(pdmts_fem *fe, const double *u, const double *v)
     for (int64_t i = 0; i < nd; ++i)
         if (!std::isfinite(hu[(size_t)i]) || !std::isfinite(hv[(size_t)i]))
             return fail(PDMTS_ERR_ARG, "fem_set_state: non-finite value");
+    if (!fe->fixed.empty())
+        for (int64_t i = 0; i < nd; ++i)
+            if (fe->fixed[(size_t)i])
+                hu[(size_t)i] = hv[(size_t)i] = 0.0;
     // acceleration from the equation of motion M a = P - K u (lambda = 0)
     std::vector<double> a((size_t)nd);
     for (int64_t i = 0; i < nd; ++i) {
@@ -1295,6 +1335,12 @@ static int build_constraint(pdmts_arl *A)
         }
     A->nl = (int64_t)A->lam_node.size();
     A->nlam = dim * A->nl;
+    // a Dirichlet dof carries no multiplier force: keep fixed dofs out of the overlap
+    if (!fe->fixed.empty())
+        for (int32_t k : A->lam_node)
+            for (int d = 0; d < dim; ++d)
+                if (fe->fixed[(size_t)(d * nfe + k)])
+                    return fail(PDMTS_ERR_ARG, "arlequin_bind: FE node %d is fixed and lies in an overlap element", k);
     A->corners = npe;
     // G_FE[k, I] = int_O N_k N_I dV (2 x 2 Gauss in 2D, 2 x 2 x 2 in 3D), rows of width 9 or 27
     std::vector<std::map<int32_t, double>> grow((size_t)A->nl);

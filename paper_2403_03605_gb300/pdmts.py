@@ -82,6 +82,7 @@ SIGNATURES = [
     ("fem_create", _I, [_V, _I, _I64, _V, _I64, _I, _V, _D, _D, _D, _D, C.POINTER(_V)]),
     ("fem_set_traction", _I, [_V, _I64, _V, _V]),
     ("fem_set_state", _I, [_V, _V, _V]),
+    ("fem_set_fixed", _I, [_V, _I64, _V]),
     ("fem_destroy", _I, [_V]),
     ("fem_read_displacement", _I, [_V, _V]),
     ("fem_read_velocity", _I, [_V, _V]),
@@ -365,6 +366,12 @@ def fem_set_traction(fe, faces, traction):
     faces = np.ascontiguousarray(faces, dtype=np.int32)
     traction = _f64(traction)
     _check(load().fem_set_traction(fe, int(faces.shape[0]), _ptr(faces), _ptr(traction)), "fem_set_traction")
+
+
+def fem_set_fixed(fe, dofs):
+    """dofs: FE dof ids d * n_nodes + node held at zero (Dirichlet)."""
+    d = np.ascontiguousarray(np.asarray(dofs, dtype=np.int64).reshape(-1))
+    _check(load().fem_set_fixed(fe, len(d), _ptr(d) if len(d) else None), "fem_set_fixed")
 
 
 def fem_set_state(fe, u=None, v=None):

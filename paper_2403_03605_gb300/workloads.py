@@ -227,7 +227,8 @@ class Band:
 
 @dataclass
 class FEMesh:
-    """Structured Q4 mesh: nodes (2, n) and counter-clockwise connectivity (ne, 4)."""
+    """Structured mesh: nodes (dim, n) and connectivity (ne, 4) Q4 counter-clockwise
+    or (ne, 8) Hex8."""
     X: np.ndarray
     conn: np.ndarray
     h: float  # element size
@@ -267,6 +268,7 @@ class CoupledProblem:
     n_coarse: int
     gamma_fe: float = 0.5
     beta_fe: float = 0.25
+    fixed: np.ndarray | None = None  # FE dof ids d * n + node held at zero (Dirichlet)
 
     @property
     def dt_pd(self):
@@ -443,3 +445,111 @@ def small_coupled3d(m=3, n_coarse=6, weight_kind=1, crack=True, traction=12e6, d
     return coupled_plate3d(0.008, 0.008, 0.002, (0.002, 0.006), dx, 1e-3, 1e-3,
                            crack=(0.004, 0.0, 0.003) if crack else None, traction=traction, dt=20e-9, m=m,
                            n_coarse=n_coarse, weight_kind=weight_kind, name="coupled_small3d")
+
+
+# ---------------------------------------------------------------------------
+# 3D beam of the coupling-accuracy study (Sec. 3.2, Table 1, Figs. 4-7)
+# ---------------------------------------------------------------------------
+BEAM_MATERIAL = Material(E=6.5e9, nu=0.25, rho=2235.0, G0=0.0, thickness=1.0)
+BEAM_HORIZON_FACTOR = 3.03   # delta = 3.03 dx
+BEAM_DT = 2.5e-5             # coarse (FE) step of Table 1
+BEAM_TRACTION = 4e6          # axial traction on the free end [Pa]
+
+
+def exp_micromodulus_c0(E: float, delta: float, ell: float) -> float:
+    """c0 of the 3D exponential micromodulus c(r) = c0 exp(-r / ell) (Sec. 3.2):
+    c0 = 3E / (pi int_0^delta r^6 exp(-r/ell) dr), the integral in closed form
+    ell^7 6! (1 - exp(-x) sum_{k<=6} x^k / k!) with x = delta / ell."""
+    x = delta / ell
+    tail = math.exp(-x) * sum(x ** k / math.factorial(k) for k in range(7))
+    return 3.0 * E / (math.pi * ell ** 7 * math.factorial(6) * (1.0 - tail))
+
+
+@dataclass
+class FEProblem:
+    """An undecomposed finite-element problem (the Table 1 reference)."""
+    name: str
+    mesh: FEMesh
+    faces: np.ndarray
+    face_traction: np.ndarray
+    fixed: np.ndarray
+    mat: Material
+    dt: float
+    n_steps: int
+    gamma: float = 0.5
+    beta: float = 0.25
+    record: dict = field(default_factory=dict)  # tracked points -> x dof id
+
+
+def _beam_block(x0, nex, ne_yz, h, node_offset=0):
+    """Hex8 block [x0, x0 + nex h] x [0, ne_yz h]^2 with its end-face helpers."""
+    X, conn = hex8_block(x0, 0.0, 0.0, nex, ne_yz, ne_yz, h, node_offset=node_offset)
+
+    def nid(i, j, k):
+        return node_offset + (k * (ne_yz + 1) + j) * (nex + 1) + i
+
+    def face(i):  # quads of the face x = x0 + i h, corners in order around each quad
+        return [[nid(i, j, k), nid(i, j + 1, k), nid(i, j + 1, k + 1), nid(i, j, k + 1)]
+                for k in range(ne_yz) for j in range(ne_yz)]
+
+    def face_nodes(i):
+        return [nid(i, j, k) for k in range(ne_yz + 1) for j in range(ne_yz + 1)]
+
+    return X, conn, nid, face, face_nodes
+
+
+def beam3d_fe(dx=0.1, n_steps=480, beta=0.25, length=10.0, width=1.0, mat: Material | None = None) -> FEProblem:
+    """Undecomposed Hex8 beam [0, length] x [0, width]^2 at element size dx,
+    fixed at x = 0 (all components), axial traction 4 MPa on x = length,
+    Newmark dt 2.5e-5 s; tracked points A (length, width/2, width/2) and, on
+    beams longer than 6, B (6, width/2, width/2) (Sec. 3.2, cases 1 and 2 of
+    Table 1)."""
+    nex, ne_yz = int(round(length / dx)), int(round(width / dx))
+    X, conn, nid, face, face_nodes = _beam_block(0.0, nex, ne_yz, dx)
+    n = X.shape[1]
+    faces = np.asarray(face(nex), dtype=np.int32)
+    tr = np.tile([BEAM_TRACTION, 0.0, 0.0], (len(faces), 1))
+    fixed = np.asarray([d * n + k for d in range(3) for k in face_nodes(0)], dtype=np.int64)
+    c = ne_yz // 2
+    ib = int(round(6.0 / dx))
+    record = {"A": nid(nex, c, c)}
+    if ib < nex:
+        record["B"] = nid(ib, c, c)
+    return FEProblem(f"beam3d_fe_dx{dx:g}", FEMesh(X, conn, dx), faces, tr, fixed, mat or BEAM_MATERIAL, BEAM_DT,
+                     n_steps, 0.5, beta, record=record)
+
+
+def beam3d(dx=0.1, overlap_cells=3, weight_kind=2, m=1, n_coarse=480, length=10.0, width=1.0,
+           pd_range=(4.0, 6.0)) -> CoupledProblem:
+    """The coupled beam of Table 1: PD on pd_range (exponential micromodulus,
+    ell = delta / 16, delta = 3.03 dx, nodes at cell centres, no breaking),
+    Hex8 elements of size dx on [0, x0 + l_O] and [x1 - l_O, length] with the
+    overlap width l_O = overlap_cells dx, overlap bands [x0, x0 + l_O] and
+    [x1 - l_O, x1], fixed end x = 0, traction on x = length, coarse step
+    2.5e-5 s and dt_PD = 2.5e-5 / m. extra["record"] holds the x dof ids of
+    the tracked points A and B on the right FE block."""
+    mat = BEAM_MATERIAL
+    x0, x1 = pd_range
+    lo = overlap_cells * dx
+    ne_yz = int(round(width / dx))
+    lat = Lattice((int(round((x1 - x0) / dx)), ne_yz, ne_yz), dx, (x0, 0.0, 0.0))
+    delta = BEAM_HORIZON_FACTOR * dx
+    ell = delta / 16.0
+    c0 = exp_micromodulus_c0(mat.E, delta, ell)
+    pd = PDProblem(f"beam3d_pd_dx{dx:g}", lat, mat, delta, c0, 1.0, BEAM_DT / m, m * n_coarse, [],
+                   np.zeros((3, lat.n)), dx ** 3, extra={"micro": 1, "l": ell})
+    nl_ = int(round((x0 + lo) / dx))
+    nr_ = int(round((length - (x1 - lo)) / dx))
+    Xl, cl, nidl, _, face_l = _beam_block(0.0, nl_, ne_yz, dx)
+    Xr, cr, nidr, face_r, _ = _beam_block(x1 - lo, nr_, ne_yz, dx, node_offset=Xl.shape[1])
+    X = np.concatenate([Xl, Xr], axis=1)
+    n = X.shape[1]
+    faces = np.asarray(face_r(nr_), dtype=np.int32)
+    tr = np.tile([BEAM_TRACTION, 0.0, 0.0], (len(faces), 1))
+    fixed = np.asarray([d * n + k for d in range(3) for k in face_l(0)], dtype=np.int64)
+    bands = [Band(0, x0, x0 + lo, -1), Band(0, x1 - lo, x1, +1)]
+    c = ne_yz // 2
+    pd.extra["record"] = {"A": nidr(nr_, c, c), "B": nidr(int(round((x1 - (x1 - lo)) / dx)), c, c)}
+    return CoupledProblem(f"beam3d_dx{dx:g}_lo{overlap_cells}_w{weight_kind}_m{m}", pd,
+                          FEMesh(X, np.concatenate([cl, cr]), dx), faces, tr, bands, weight_kind, m, n_coarse,
+                          fixed=fixed)

@@ -95,11 +95,14 @@ class GpuMTS:
         pb = cp.pd
         mat = pb.mat
         self.pd = P.pd_create(ctx, pb.lat.X, horizon=pb.delta, c=pb.c, s0=pb.s0, rho=mat.rho, vol_uniform=pb.vol,
+                              micro_kind=pb.extra.get("micro", P.PDMTS_MICRO_POWER), l=pb.extra.get("l", 0.0),
                               precision=precision)
         if pb.cuts:
             P.pd_set_precrack(self.pd, [c.as_array() for c in pb.cuts])
         self.fe = P.fem_create(ctx, cp.fe.X, cp.fe.conn, E=mat.E, nu=mat.nu, rho=mat.rho, thickness=mat.thickness)
         P.fem_set_traction(self.fe, cp.faces, cp.face_traction)
+        if cp.fixed is not None:
+            P.fem_set_fixed(self.fe, cp.fixed)
         self.arl = P.arlequin_bind(ctx, self.pd, self.fe, cp.weight_kind, [b.as_array() for b in cp.bands])
         dim = pb.lat.dim
         if v0 is not None:

@@ -1,0 +1,107 @@
+"""The 3D beam of the coupling-accuracy study (Sec. 3.2, Table 1): Dirichlet
+dofs on the GPU, FP64 parity of the coupled beam with the oracle, and the
+error of the coupled solution at the tracked point A against the
+undecomposed finite-element beam."""
+import numpy as np
+import pytest
+
+from gpu_common import GpuMTS, rel_l2
+from oracle.mts import MTSOracle, newmark_fe
+from paper_2403_03605_gb300 import pdmts as P
+from paper_2403_03605_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-10
+
+
+@pytest.fixture
+def fresh():
+    from paper_2403_03605_gb300 import build
+    build.build()
+    made = []
+
+    def mk():
+        c = P.pdmts_ctx_create(0)
+        made.append(c)
+        return c
+    yield mk
+    for c in made:
+        P.pdmts_ctx_destroy(c)
+
+
+def test_beam_fp64_matches_oracle(fresh):
+    """Fixed end, exponential micromodulus, cubic weights, m = 2: FP64 parity
+    with the oracle's Algorithm 1 after the reflected wave has crossed the
+    PD subdomain; the fixed dofs stay exactly zero."""
+    cp = W.beam3d(dx=0.25, overlap_cells=3, weight_kind=2, m=2, n_coarse=240)
+    o = MTSOracle(cp).advance(cp.n_coarse)
+    g = GpuMTS(fresh(), cp, P.PDMTS_FP64).run(cp.n_coarse)
+    for a, b in [(g.u(), o.u), (g.v(), o.v), (g.uf(), o.uf), (g.vf(), o.vf)]:
+        assert rel_l2(a, b) <= FP64_TOL
+    assert rel_l2(g.lam(), o.lam) <= 1e-8
+    assert np.all(g.uf()[cp.fixed] == 0.0) and np.all(g.vf()[cp.fixed] == 0.0)
+    assert g.residual() <= 1e-12
+
+
+def test_fixed_dofs_validation(fresh):
+    cp = W.beam3d(dx=0.25, overlap_cells=1, m=1, n_coarse=1)
+    ctx = fresh()
+    fe = P.fem_create(ctx, cp.fe.X, cp.fe.conn, E=1e9, nu=0.25, rho=1e3, thickness=1.0)
+    with pytest.raises(P.PdmtsError):
+        P.fem_set_fixed(fe, [3 * cp.fe.n])  # id out of range
+    # a node of an overlap element may not be fixed
+    ov = int(np.argmin(np.abs(cp.fe.X[0] - 4.0) + np.abs(cp.fe.X[1]) + np.abs(cp.fe.X[2])))
+    P.fem_set_fixed(fe, [ov])
+    pb = cp.pd
+    pd = P.pd_create(ctx, pb.lat.X, horizon=pb.delta, c=pb.c, s0=pb.s0, rho=pb.mat.rho, vol_uniform=pb.vol,
+                     micro_kind=P.PDMTS_MICRO_EXP, l=pb.extra["l"])
+    with pytest.raises(P.PdmtsError):
+        P.arlequin_bind(ctx, pd, fe, cp.weight_kind, [b.as_array() for b in cp.bands])
+
+
+# --- Table 1: u_x error at point A against the undecomposed FE beam --------
+DX, N_STEPS = 0.1, 480
+# (weight kind, overlap width in dx, m): cases 3-11 (m = 1) and the MTS
+# cases with cubic weights over 3 dx (m = 2, 5, 10)
+STUDY = [(k, c, 1) for k in (0, 1, 2) for c in (1, 3, 5)] + [(2, 3, 2), (2, 3, 5), (2, 3, 10)]
+PAPER = {(0, 1, 1): 1.74, (0, 3, 1): 1.72, (0, 5, 1): 1.68, (1, 1, 1): 1.74, (1, 3, 1): 1.09, (1, 5, 1): 0.92,
+         (2, 1, 1): 1.51, (2, 3, 1): 0.86, (2, 5, 1): 0.73, (2, 3, 2): 0.96, (2, 3, 5): 0.96, (2, 3, 10): 0.97}
+
+
+@pytest.fixture(scope="module")
+def beam_reference():
+    fp = W.beam3d_fe(dx=DX, n_steps=N_STEPS)
+    return newmark_fe(fp, N_STEPS, np.array([fp.record["A"]]))[:, 0]
+
+
+def _coupled_history(ctx, cp):
+    g = GpuMTS(ctx, cp, P.PDMTS_FP32_BULK)
+    ia = cp.pd.extra["record"]["A"]
+    out = np.zeros(cp.n_coarse)
+    for k in range(cp.n_coarse):
+        g.run(1)
+        out[k] = g.uf()[ia]
+    assert np.all(g.uf()[cp.fixed] == 0.0)
+    return out
+
+
+def test_beam_accuracy_study(fresh, beam_reference):
+    """Global error of u_x at A over all coarse steps (the error measure of
+    Sec. 3.2) for the weight types and overlap widths of Table 1 and for
+    m = 2, 5, 10: every case within a few percent, cubic over 3 dx better
+    than constant over dx, and the MTS cases as accurate as m = 1."""
+    ref = beam_reference
+    errs = {}
+    for kind, cells, m in STUDY:
+        cp = W.beam3d(dx=DX, overlap_cells=cells, weight_kind=kind, m=m, n_coarse=N_STEPS)
+        got = _coupled_history(fresh(), cp)
+        errs[(kind, cells, m)] = 100.0 * np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    names = {0: "constant", 1: "linear", 2: "cubic"}
+    print("\nweight    l_O  m  u_x err at A (%)  paper (%)")
+    for key, e in errs.items():
+        print(f"{names[key[0]]:9s} {key[1]}dx {key[2]:2d}  {e:8.3f}          {PAPER[key]:.2f}")
+    assert max(errs.values()) < 5.0
+    assert errs[(2, 3, 1)] < errs[(0, 1, 1)]
+    for m in (2, 5, 10):
+        assert abs(errs[(2, 3, m)] - errs[(2, 3, 1)]) < 0.5

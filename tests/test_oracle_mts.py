@@ -105,3 +105,101 @@ def test_hex8_stiffness_rigid_modes_and_volume():
     ev = np.linalg.eigvalsh(K)
     assert np.sum(np.abs(ev) <= 1e-9 * ev.max()) == 6
     assert abs(fe.M.sum() / 3 - 2440.0 * (2e-3) ** 3) <= 1e-12 * 2440.0 * (2e-3) ** 3
+
+
+# ---------------------------------------------------------------------------
+# Dirichlet elimination and the undecomposed FE reference (Sec. 3.2, Table 1)
+# ---------------------------------------------------------------------------
+def _modal_newmark(fp, n_steps):
+    """Closed-form Newmark response of the fixed-end beam started at rest
+    under a constant load, mode by mode: with mass-normalised modes of
+    (K_ff, M_ff), each modal coordinate is q_s (1 - cos(n theta)) with
+    q_s = phi' P / omega^2 and tan(theta / 2) = omega dt / 2 for the average
+    acceleration scheme (beta = 1/4, gamma = 1/2), cos(theta) = 1 - (omega
+    dt)^2 / 2 for the explicit one (beta = 0, lumped mass)."""
+    import scipy.linalg as sla
+    from oracle.mts import FE
+    mat = fp.mat
+    fe = FE(fp.mesh, mat.E, mat.nu, mat.rho, mat.thickness, [], 0, fp.faces, fp.face_traction)
+    nd = 3 * fe.n
+    free = np.setdiff1d(np.arange(nd), fp.fixed)
+    K = fe.K.toarray()[np.ix_(free, free)]
+    w2, phi = sla.eigh(K, np.diag(fe.M[free]))
+    om = np.sqrt(w2)
+    qs = phi.T @ fe.P[free] / w2
+    if fp.beta == 0.25:
+        th = 2.0 * np.arctan(om * fp.dt / 2.0)
+    else:
+        assert fp.beta == 0.0 and np.all(om * fp.dt < 2.0)
+        th = np.arccos(1.0 - (om * fp.dt) ** 2 / 2.0)
+    n = np.arange(1, n_steps + 1)[:, None]
+    out = np.zeros((n_steps, nd))
+    out[:, free] = (qs * (1.0 - np.cos(n * th))) @ phi.T
+    return out
+
+
+@pytest.mark.parametrize("beta", [0.25, 0.0])
+def test_fixed_end_newmark_matches_modal_closed_form(beta):
+    from oracle.mts import newmark_fe
+    fp = W.beam3d_fe(dx=0.25, n_steps=60, beta=beta, length=1.5, width=0.5)
+    nd = 3 * fp.mesh.n
+    got = newmark_fe(fp, fp.n_steps, np.arange(nd))
+    ref = _modal_newmark(fp, fp.n_steps)
+    assert np.all(got[:, fp.fixed] == 0.0)
+    assert np.abs(got - ref).max() <= 1e-9 * np.abs(ref).max()
+    # the tip moves: a dropped load or a wrongly fixed face would not
+    assert np.abs(got[:, fp.record["A"]]).max() > 1e-4
+
+
+def test_fixed_end_static_bar_is_exact_for_zero_poisson():
+    """With nu = 0 the clamped end exerts no lateral constraint and the static
+    solution of the fixed-end bar under an end traction is u_x = P x / E,
+    which trilinear elements reproduce exactly."""
+    from oracle.mts import FE
+    mat = W.Material(E=6.5e9, nu=0.0, rho=2235.0, G0=0.0, thickness=1.0)
+    fp = W.beam3d_fe(dx=0.25, length=1.5, width=0.5, mat=mat)
+    fe = FE(fp.mesh, mat.E, mat.nu, mat.rho, mat.thickness, [], 0, fp.faces, fp.face_traction)
+    nd = 3 * fe.n
+    free = np.setdiff1d(np.arange(nd), fp.fixed)
+    u = np.zeros(nd)
+    u[free] = np.linalg.solve(fe.K.toarray()[np.ix_(free, free)], fe.P[free])
+    x = fp.mesh.X[0]
+    np.testing.assert_allclose(u[:fe.n], W.BEAM_TRACTION * x / mat.E, rtol=0, atol=1e-12 * W.BEAM_TRACTION / mat.E)
+    assert np.abs(u[fe.n:]).max() <= 1e-12 * W.BEAM_TRACTION / mat.E
+    # total load = traction x end area
+    assert abs(fe.P[:fe.n].sum() - W.BEAM_TRACTION * 0.25) < 1e-6
+
+
+def test_exp_micromodulus_constant_matches_quadrature():
+    """c0 of the exponential micromodulus against a numerical quadrature of
+    its defining integral (Sec. 3.2)."""
+    from scipy.integrate import quad
+    delta = 3.03 * 0.1
+    ell = delta / 16
+    integral, _ = quad(lambda r: r ** 6 * np.exp(-r / ell), 0.0, delta, epsabs=0, epsrel=1e-13, limit=200)
+    c0 = W.exp_micromodulus_c0(6.5e9, delta, ell)
+    assert abs(c0 - 3 * 6.5e9 / (np.pi * integral)) <= 1e-10 * c0
+
+
+def test_coupled_beam_oracle_tracks_the_fe_reference():
+    """The coupled beam follows the undecomposed FE beam at point A within a
+    few percent over one round trip of the axial wave (480 coarse steps, a
+    coarse 0.25 m mesh, m = 2), and cubic weights over 3 dx beat constant
+    weights over dx, the ordering of Table 1."""
+    from oracle.mts import newmark_fe
+    n = 480
+    fp = W.beam3d_fe(dx=0.25, n_steps=n)
+    ref = newmark_fe(fp, n, np.array([fp.record["A"]]))[:, 0]
+    errs = {}
+    for kind, cells in [(0, 1), (2, 3)]:
+        cp = W.beam3d(dx=0.25, overlap_cells=cells, weight_kind=kind, m=2, n_coarse=n)
+        orc = MTSOracle(cp, breaking=False)
+        ia = cp.pd.extra["record"]["A"]
+        got = np.zeros(n)
+        for k in range(n):
+            orc.coarse_step()
+            got[k] = orc.uf[ia]
+        assert np.all(orc.uf[cp.fixed] == 0.0)
+        errs[kind] = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert max(errs.values()) < 0.05, errs
+    assert errs[2] < errs[0], errs
