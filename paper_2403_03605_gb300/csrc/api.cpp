@@ -1066,6 +1066,7 @@ int pdmts_pd::step(bool init, double theta, cudaStream_t s, bool link)
         const F32NodeArgs N = f32_node_args(init, theta, link);
         if (layout == LAYOUT_LATTICE2D) {
             Lat2DArgs A = lattice_args(N, mask, link);
+            A.pdl = chain_follow ? 1 : 0;
             e = launch_pd_step_lattice2d(A, init, s);
         } else {
             F32StepArgs A{};

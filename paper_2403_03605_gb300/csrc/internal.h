@@ -145,6 +145,7 @@ struct Lat2DArgs {
     int tile;                   // tile configuration, 0 .. kLatTiles - 1
     int num_sms;                // SMs of the device (persistent grids)
     int win_lo[2], win_n[2];    // optional windows in units of TY node rows (win_n[0] == 0: whole lattice)
+    int pdl;                    // launch as a programmatic dependent of the previous substep kernel
     F32NodeArgs nd;
 };
 

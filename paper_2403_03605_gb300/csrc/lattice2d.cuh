@@ -5,6 +5,7 @@
 #pragma once
 
 #include <algorithm>
+#include <utility>
 #include <type_traits>
 
 #include "f32_device.cuh"
@@ -398,6 +399,16 @@ __device__ __forceinline__ int lattice_trow(const Lat2DArgs &A, const int by)
     return A.win_n[0] > 0 ? (by < A.win_n[0] ? A.win_lo[0] + by : A.win_lo[1] + by - A.win_n[0]) : by;
 }
 
+// Programmatic dependent launch inside a substep chain: the CTAs of substep
+// k + 1 may be scheduled while substep k drains; every global access (the
+// ping-pong u buffers, v, a and the bond words are all read and written)
+// waits for substep k to complete. Outside such a launch both are no-ops.
+__device__ __forceinline__ void lattice_chain_entry()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // One CTA per tile (grid: tile columns x tile rows).
 template <bool PMB, int KR, int MINB>
 __global__ void __launch_bounds__(256, MINB) k_pd_step_lattice2d(const Lat2DArgs A, const int init)
@@ -405,6 +416,7 @@ __global__ void __launch_bounds__(256, MINB) k_pd_step_lattice2d(const Lat2DArgs
     extern __shared__ __align__(16) unsigned char lat_smem[];
     LatStage<KR> &S = *reinterpret_cast<LatStage<KR> *>(lat_smem);
     const int x0 = blockIdx.x * lat2d::TX, y0 = lattice_trow(A, (int)blockIdx.y) * LatStage<KR>::TYK;
+    lattice_chain_entry();
     lattice_issue_a<KR>(S, A, x0, y0);
     cp_async_commit();
     lattice_issue_b<KR>(S, A, x0, y0);
@@ -438,6 +450,7 @@ __global__ void __launch_bounds__(256, MINB) k_pd_step_lattice2d_pipe(const Lat2
             cp_async_commit();
         }
     };
+    lattice_chain_entry();
     issue(stages[0], blockIdx.x);
     issue(stages[1], blockIdx.x + G);
     unsigned nbroken = 0;
@@ -537,6 +550,25 @@ cudaError_t lattice_prepare(K kern, size_t smem, int &ctas)
     return cudaSuccess;
 }
 
+// Launch with 256 threads; `pdl` adds the programmatic-serialisation
+// attribute (the kernel begins with lattice_chain_entry).
+template <typename... P, typename... Q>
+cudaError_t lattice_launch(void (*kern)(P...), const dim3 grid, const size_t smem, cudaStream_t s, const bool pdl,
+                           Q &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<Q>(args)...);
+}
+
 template <int KR, int MINB>
 cudaError_t launch_lattice_pipe(const Lat2DArgs &A0, bool init, cudaStream_t s)
 {
@@ -551,8 +583,7 @@ cudaError_t launch_lattice_pipe(const Lat2DArgs &A0, bool init, cudaStream_t s)
     const int rows = lattice_tile_rows<LatStage<KR>::TYK>(A, A0);
     const int ntiles = ((A.nx + lat2d::TX - 1) / lat2d::TX) * rows;
     const int grid = std::max(1, std::min(ntiles, A.num_sms * nb));
-    kern<<<grid, 256, smem, s>>>(A, init ? 1 : 0, ntiles);
-    return cudaGetLastError();
+    return lattice_launch(kern, dim3((unsigned)grid), smem, s, A.pdl != 0, A, init ? 1 : 0, ntiles);
 }
 
 template <int KR, int MINB>
@@ -567,8 +598,7 @@ cudaError_t launch_lattice_kr(const Lat2DArgs &A0, bool init, cudaStream_t s)
     Lat2DArgs A = A0;
     const unsigned rows = (unsigned)lattice_tile_rows<LatStage<KR>::TYK>(A, A0);
     const dim3 grid((unsigned)((A.nx + lat2d::TX - 1) / lat2d::TX), rows);
-    kern<<<grid, 256, smem, s>>>(A, init ? 1 : 0);
-    return cudaGetLastError();
+    return lattice_launch(kern, grid, smem, s, A.pdl != 0, A, init ? 1 : 0);
 }
 
 template <int KR, int MINB>

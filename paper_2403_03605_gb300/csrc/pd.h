@@ -99,6 +99,7 @@ struct pdmts_pd {
     };
     std::vector<GraphEntry> graphs;
     bool use_graphs = true;
+    bool chain_follow = false;  // the substep being launched follows another one in its chain
 
     int cur = 0;            // buffer holding u at the current time
     bool need_init = true;  // a must be recomputed from u before the next step

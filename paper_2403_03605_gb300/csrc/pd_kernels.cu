@@ -701,8 +701,12 @@ int pd_run_chain(pdmts_pd *pd, int len, int sched, const double *theta, cudaStre
         PDMTS_TRY(ctx->time_begin(&t0));
     int &cur = link ? pd->lk_cur : pd->cur;
     if (!pd->use_graphs || len < 2) {
-        for (int k = 0; k < len; ++k)
-            PDMTS_TRY(pd->step(false, theta ? theta[k] : 0.0, s, link));
+        for (int k = 0; k < len; ++k) {
+            pd->chain_follow = k > 0;
+            const int r = pd->step(false, theta ? theta[k] : 0.0, s, link);
+            pd->chain_follow = false;
+            PDMTS_TRY(r);
+        }
         return link ? PDMTS_OK : ctx->time_end(t0, len);
     }
     const int p = cur + (link ? 2 : 0);
@@ -717,8 +721,11 @@ int pd_run_chain(pdmts_pd *pd, int len, int sched, const double *theta, cudaStre
         cudaGraph_t g = nullptr;
         PDMTS_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
         int r = PDMTS_OK;
-        for (int k = 0; k < len && r == PDMTS_OK; ++k)
+        for (int k = 0; k < len && r == PDMTS_OK; ++k) {
+            pd->chain_follow = k > 0;
             r = pd->step(false, theta ? theta[k] : 0.0, s, link);
+        }
+        pd->chain_follow = false;
         cudaError_t e = cudaStreamEndCapture(s, &g);
         cur = cur0;
         pd->steps_done = steps0;
