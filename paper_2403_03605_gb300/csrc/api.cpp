@@ -898,9 +898,10 @@ pdmts::Lat2DArgs pdmts_pd::lattice_args(const pdmts::F32NodeArgs &N, uint32_t *m
     A.tile = lattice_tile >= 0 ? lattice_tile : 0;
     A.num_sms = ctx->num_sms;
     A.nd = N;
+    const bool grow = link && chain_k >= 0 && chain_k < (int)link_step_win.size();
     for (int w = 0; w < 2; ++w) {
-        A.win_lo[w] = link ? link_win_lo[w] : 0;
-        A.win_n[w] = link ? link_win_n[w] : 0;
+        A.win_lo[w] = !link ? 0 : grow ? link_step_win[(size_t)chain_k][2 * w] : link_win_lo[w];
+        A.win_n[w] = !link ? 0 : grow ? link_step_win[(size_t)chain_k][2 * w + 1] : link_win_n[w];
     }
     return A;
 }
@@ -1026,7 +1027,7 @@ void pdmts_pd::substep_done(bool init, bool link)
     if (!link)
         steps_done++;
     ctx->stats.pd_substeps++;
-    ctx->stats.bond_updates += (link && link_bonds >= 0) ? link_bonds : (int64_t)row_ptr[(size_t)n];
+    ctx->stats.bond_updates += substep_bonds(link, chain_k);
 }
 
 int pdmts_pd::step(bool init, double theta, cudaStream_t s, bool link)

@@ -50,6 +50,44 @@ __device__ __forceinline__ void static_for(F &&f)
     }
 }
 
+// f(E - 1), f(E - 2), ..., f(B)
+template <int B, int E, class F>
+__device__ __forceinline__ void static_for_desc(F &&f)
+{
+    if constexpr (B < E) {
+        f(std::integral_constant<int, E - 1>{});
+        static_for_desc<B, E - 1>(f);
+    }
+}
+
+// Canonical bond order of a node. Every path (pair, warp fast path, masked)
+// sums a node's bond forces in this order, so every path and every tile
+// configuration gives the same bits: first the 14 bonds d of the half stencil
+// H+ = {dx > 0} + {dx = 0, dy > 0}, by column dx = 0..3 and dy ascending
+// (PDX/PDY below); then the 14 bonds -d, d in H+, in the same order of d.
+namespace lat2d {
+constexpr int NP = 14;
+__host__ __device__ constexpr int PDX(int k)
+{
+    constexpr int t[NP] = {0, 0, 0, 1, 1, 1, 1, 1, 2, 2, 2, 2, 2, 3};
+    return t[k];
+}
+__host__ __device__ constexpr int PDY(int k)
+{
+    constexpr int t[NP] = {1, 2, 3, -2, -1, 0, 1, 2, -2, -1, 0, 1, 2, 0};
+    return t[k];
+}
+__host__ __device__ constexpr int KP(int dx, int dy)
+{
+    for (int k = 0; k < NP; ++k)
+        if (PDX(k) == dx && PDY(k) == dy)
+            return k;
+    return -1;
+}
+// rows of column dx that hold H+ bonds: dy in [PLO(dx), RY(dx)]
+__host__ __device__ constexpr int PLO(int dx) { return dx == 0 ? 1 : -RY(dx); }
+}  // namespace lat2d
+
 // Bond word of a node with all 28 bonds present and intact.
 constexpr uint32_t kFullWord = (1u << lat2d::NS) - 1u;
 
@@ -65,10 +103,12 @@ __device__ __forceinline__ void lattice_acc(float &acc, const float s)
         acc = __fmaf_rn(s, (float)D, acc);
 }
 
+// One bond of the node with state nu = -u_i (and weight ai); accumulates its
+// force into f and returns the scalar s of the linear law's f = s d.
 template <int DX, int DY, bool ALPHA, bool PMB, bool MASKED>
-__device__ __forceinline__ void lattice_bond(const float4 uj, const float aj, const float4 nu, const float ai,
-                                             const Lat2DArgs &A, const uint32_t m0, uint32_t &m, float2 &f,
-                                             float &qmax)
+__device__ __forceinline__ float lattice_bond(const float4 uj, const float aj, const float4 nu, const float ai,
+                                              const Lat2DArgs &A, const uint32_t m0, uint32_t &m, float2 &f,
+                                              float &qmax)
 {
     constexpr int r2 = DX * DX + DY * DY;
     constexpr int K = lat2d::KOF(DX, DY);
@@ -119,10 +159,14 @@ __device__ __forceinline__ void lattice_bond(const float4 uj, const float aj, co
     } else {
         f = __ffma2_rn(make_float2(s, s), dir, f);
     }
+    return s;
 }
 
-// All 28 bonds of the KR nodes of one strip, stencil column by column, with
-// every bond taken as intact (fast path); qmax collects the largest q.
+// All 28 bonds of the KR nodes of one strip with every bond taken as intact
+// (fast path), in the canonical order: the H+ columns dx = 0..3 with rows
+// ascending, then the H- columns dx = 0, -1, -2, -3 with rows descending. A
+// thread reads each halo value of a column once and applies it to every node
+// of its strip within reach; qmax collects the largest q.
 template <int KR, bool ALPHA, bool PMB>
 __device__ __forceinline__ void lattice_strip(const float4 (*su)[lat2d::HX], const float (*sal)[lat2d::HX],
                                               const int hy0, const int hx0, const Lat2DArgs &A,
@@ -131,20 +175,36 @@ __device__ __forceinline__ void lattice_strip(const float4 (*su)[lat2d::HX], con
                                               float (&qmax)[KR])
 {
     using namespace lat2d;
-    static_for<-R, R + 1>([&](auto dxc) {
+    static_for<0, R + 1>([&](auto dxc) {
         constexpr int dx = decltype(dxc)::value;
-        constexpr int ry = RY(dx);
+        constexpr int ry = RY(dx), lo = PLO(dx);
         // keep the shared-memory reads of one column together: bounds how far
         // the scheduler hoists loads, and with it the live registers
         asm volatile("" ::: "memory");
-        static_for<-ry, KR + ry>([&](auto jc) {
+        static_for<lo, KR + ry>([&](auto jc) {
             constexpr int j = decltype(jc)::value;
             const float4 uj = su[hy0 + j][hx0 + dx];
             const float aj = ALPHA ? sal[hy0 + j][hx0 + dx] : 0.f;
             static_for<0, KR>([&](auto rc) {
                 constexpr int r = decltype(rc)::value;
                 constexpr int dy = j - r;
-                if constexpr (dy >= -ry && dy <= ry && (dx != 0 || dy != 0))
+                if constexpr (dy >= lo && dy <= ry)
+                    lattice_bond<dx, dy, ALPHA, PMB, false>(uj, aj, nu[r], ai[r], A, m0[r], m[r], f[r], qmax[r]);
+            });
+        });
+    });
+    static_for<0, R + 1>([&](auto c) {
+        constexpr int dx = -decltype(c)::value;
+        constexpr int ry = RY(dx), hi = -PLO(-dx);  // H- rows of column dx: dy in [-ry, hi]
+        asm volatile("" ::: "memory");
+        static_for_desc<-ry, KR + hi>([&](auto jc) {
+            constexpr int j = decltype(jc)::value;
+            const float4 uj = su[hy0 + j][hx0 + dx];
+            const float aj = ALPHA ? sal[hy0 + j][hx0 + dx] : 0.f;
+            static_for<0, KR>([&](auto rc) {
+                constexpr int r = decltype(rc)::value;
+                constexpr int dy = j - r;
+                if constexpr (dy >= -ry && dy <= hi)
                     lattice_bond<dx, dy, ALPHA, PMB, false>(uj, aj, nu[r], ai[r], A, m0[r], m[r], f[r], qmax[r]);
             });
         });
@@ -152,25 +212,23 @@ __device__ __forceinline__ void lattice_strip(const float4 (*su)[lat2d::HX], con
 }
 
 // The 28 bonds of one node with its bond bits: exact breaking, absent bonds
-// skipped. The bonds come in the order lattice_strip gives them to a node, so
-// a warp that takes this path without a break gets the fast path's bits.
+// skipped, in the canonical order (H+ by offset index, then -d for d in H+),
+// so a warp that takes this path without a break gets the fast path's bits.
 template <bool ALPHA, bool PMB>
 __device__ __forceinline__ void lattice_node_masked(const float4 (*su)[lat2d::HX], const float (*sal)[lat2d::HX],
                                                     const int hy, const int hx, const Lat2DArgs &A, const float4 nu,
                                                     const float ai, const uint32_t m0, uint32_t &m, float2 &f)
 {
     using namespace lat2d;
-    static_for<-R, R + 1>([&](auto dxc) {
-        constexpr int dx = decltype(dxc)::value;
-        constexpr int ry = RY(dx);
-        static_for<-ry, ry + 1>([&](auto dyc) {
-            constexpr int dy = decltype(dyc)::value;
-            if constexpr (dx != 0 || dy != 0) {
-                const float4 uj = su[hy + dy][hx + dx];
-                const float aj = ALPHA ? sal[hy + dy][hx + dx] : 0.f;
-                float qunused = 0.f;
-                lattice_bond<dx, dy, ALPHA, PMB, true>(uj, aj, nu, ai, A, m0, m, f, qunused);
-            }
+    static_for<0, 2>([&](auto sc) {
+        constexpr int sg = decltype(sc)::value ? -1 : 1;
+        static_for<0, NP>([&](auto kc) {
+            constexpr int k = decltype(kc)::value;
+            constexpr int dx = sg * PDX(k), dy = sg * PDY(k);
+            const float4 uj = su[hy + dy][hx + dx];
+            const float aj = ALPHA ? sal[hy + dy][hx + dx] : 0.f;
+            float qunused = 0.f;
+            lattice_bond<dx, dy, ALPHA, PMB, true>(uj, aj, nu, ai, A, m0, m, f, qunused);
         });
     });
 }

@@ -1572,6 +1572,53 @@ static int update_near_flags(pdmts_arl *A, int m)
             pd->link_bonds = bonds;
         }
     }
+    // A link run starts from rest and is loaded on the overlap nodes only, so
+    // after substep k (0-based) its state is nonzero only within k delta of a
+    // band: substep k evaluates the tile rows within (k + 2) delta (the rows
+    // left out hold exact zeros and would compute exact zeros). The windows
+    // grow to the fixed ones above at k = m - 1.
+    pd->link_step_win.clear();
+    pd->link_step_bonds.clear();
+    if (pd->link_win_n[0] > 0) {
+        const int ny = pd->lat_dims[1], nx = pd->lat_dims[0];
+        const int ntr = (ny + lat2d::TY - 1) / lat2d::TY;
+        for (int k = 0; k < m; ++k) {
+            const double reach = (k + 2) * pd->horizon;
+            std::vector<char> need((size_t)ntr, 0);
+            for (int y = 0; y < ny; ++y) {
+                const double c = pd->X[(size_t)npd + (size_t)y * nx];
+                for (const BandDesc &b : A->bands)
+                    if (c >= b.lo - reach && c <= b.hi + reach)
+                        need[(size_t)(y / lat2d::TY)] = 1;
+            }
+            std::array<int, 4> w = {0, 0, 0, 0};
+            int nw = 0;
+            bool ok = true;
+            for (int t = 0; t < ntr && ok; ++t) {
+                if (!need[(size_t)t])
+                    continue;
+                if (nw > 0 && w[2 * (nw - 1)] + w[2 * (nw - 1) + 1] == t)
+                    w[2 * (nw - 1) + 1]++;
+                else if (nw < 2)
+                    w[2 * nw] = t, w[2 * nw + 1] = 1, ++nw;
+                else
+                    ok = false;
+            }
+            if (!ok || nw == 0) {  // keep the fixed windows for every substep
+                pd->link_step_win.clear();
+                pd->link_step_bonds.clear();
+                break;
+            }
+            int64_t bonds = 0;
+            for (int q = 0; q < 2; ++q) {
+                const int64_t r0 = std::min<int64_t>((int64_t)w[2 * q] * lat2d::TY, ny);
+                const int64_t r1 = std::min<int64_t>((int64_t)(w[2 * q] + w[2 * q + 1]) * lat2d::TY, ny);
+                bonds += pd->row_ptr[(size_t)(r1 * nx)] - pd->row_ptr[(size_t)(r0 * nx)];
+            }
+            pd->link_step_win.push_back(w);
+            pd->link_step_bonds.push_back(bonds);
+        }
+    }
     // node ranges a link run may write: the windows widened to 32 rows
     pd->link_seg_lo[0] = pd->link_seg_lo[1] = 0;
     pd->link_seg_n[0] = pd->n;

@@ -89,6 +89,19 @@ struct pdmts_pd {
     int64_t link_seg_lo[2] = {0, 0}, link_seg_n[2] = {0, 0};
     int lattice_tile = -1;                                // lattice tile configuration (-1: tune)
     int64_t link_bonds = -1;  // directed bonds evaluated per link substep (-1: all)
+    // growing windows of the link chain: substep k (0-based) of a link run
+    // evaluates step_win[k] = {lo0, n0, lo1, n1} (TY-row units), holding every
+    // node within (k + 2) delta of a band; empty: link_win for every substep
+    std::vector<std::array<int, 4>> link_step_win;
+    std::vector<int64_t> link_step_bonds;
+    int chain_k = 0;  // index of the substep being launched within its chain
+    // directed bonds a substep evaluates (substep k of a link chain: its window)
+    int64_t substep_bonds(bool link, int k) const
+    {
+        if (link && k >= 0 && k < (int)link_step_bonds.size())
+            return link_step_bonds[(size_t)k];
+        return (link && link_bonds >= 0) ? link_bonds : (int64_t)row_ptr[(size_t)n];
+    }
     // interface force density of the free problem (G_PD^T lambda_0 / V): FP64 d_g or FP32 f_g
     bool has_g = false;
 

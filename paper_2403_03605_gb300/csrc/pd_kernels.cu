@@ -703,8 +703,10 @@ int pd_run_chain(pdmts_pd *pd, int len, int sched, const double *theta, cudaStre
     if (!pd->use_graphs || len < 2) {
         for (int k = 0; k < len; ++k) {
             pd->chain_follow = k > 0;
+            pd->chain_k = k;
             const int r = pd->step(false, theta ? theta[k] : 0.0, s, link);
             pd->chain_follow = false;
+            pd->chain_k = 0;
             PDMTS_TRY(r);
         }
         return link ? PDMTS_OK : ctx->time_end(t0, len);
@@ -723,9 +725,11 @@ int pd_run_chain(pdmts_pd *pd, int len, int sched, const double *theta, cudaStre
         int r = PDMTS_OK;
         for (int k = 0; k < len && r == PDMTS_OK; ++k) {
             pd->chain_follow = k > 0;
+            pd->chain_k = k;
             r = pd->step(false, theta ? theta[k] : 0.0, s, link);
         }
         pd->chain_follow = false;
+        pd->chain_k = 0;
         cudaError_t e = cudaStreamEndCapture(s, &g);
         cur = cur0;
         pd->steps_done = steps0;
@@ -747,8 +751,8 @@ int pd_run_chain(pdmts_pd *pd, int len, int sched, const double *theta, cudaStre
     ctx->stats.graph_launches++;
     ctx->stats.kernel_launches += len;
     ctx->stats.pd_substeps += len;
-    ctx->stats.bond_updates +=
-        (int64_t)len * ((link && pd->link_bonds >= 0) ? pd->link_bonds : pd->row_ptr[(size_t)pd->n]);
+    for (int k = 0; k < len; ++k)
+        ctx->stats.bond_updates += pd->substep_bonds(link, k);
     if (!link)
         pd->steps_done += len;
     if (len & 1)
