@@ -146,10 +146,15 @@ int pd_set_force_law(pdmts_pd *pd, int kind);
  * fastest. Configurations: 0: one CTA per 32 x 16 tile, strips of 2 nodes
  * per thread, registers for 3 CTAs per SM; 1: the same for 4 CTAs per SM;
  * 2: a persistent grid that stages each CTA's next tile while it computes
- * the current one, 2 nodes per thread; 3: the same with 1 node per thread.
+ * the current one, 2 nodes per thread; 3: the same with 1 node per thread;
+ * 4: configuration 0 where a tile whose nodes all hold
+ * their bonds evaluates each bond once (f_ji = -f_ij) and exchanges the
+ * reactions through shared memory (linear force law; PMB as configuration 0);
+ * 5 and 6: configurations 1 and 0 with every input of a tile staged by
+ * tensor copies (lattices with nx % 4 != 0 take configurations 1 and 0).
  * Other layouts and precisions ignore the setting. PDMTS_ERR_ARG if out of
  * range. */
-#define PDMTS_LATTICE_TILES 4
+#define PDMTS_LATTICE_TILES 7
 #define PDMTS_LATTICE_TILE_AUTO (-1)
 int pd_set_lattice_tile(pdmts_pd *pd, int tile);
 

@@ -291,9 +291,11 @@ extern "C" int pdmts_get_stats(pdmts_ctx *ctx, pdmts_stats *stats)
         return fail(PDMTS_ERR_ARG, "pdmts_get_stats: NULL argument");
     PDMTS_CUDA_TRY(cudaSetDevice(ctx->device));
     PDMTS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
-    unsigned long long broken = 0;
-    PDMTS_CUDA_TRY(cudaMemcpy(&broken, ctx->d_counter, sizeof(broken), cudaMemcpyDeviceToHost));
-    ctx->stats.bonds_broken = (int64_t)broken;
+    unsigned long long word[3] = {0, 0, 0};
+    PDMTS_CUDA_TRY(cudaMemcpy(word, ctx->d_counter, sizeof(word), cudaMemcpyDeviceToHost));
+    if (word[2])
+        return fail(PDMTS_ERR_CUDA, "pdmts_get_stats: a tensor-copy wait of the lattice kernel gave up");
+    ctx->stats.bonds_broken = (int64_t)word[0];
     *stats = ctx->stats;
     return PDMTS_OK;
 }

@@ -1,6 +1,7 @@
 // internal.h -- shared internal declarations of the pdmts library (host + device).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <array>
@@ -149,24 +150,37 @@ struct Lat2DArgs {
     F32NodeArgs nd;
 };
 
+// Tensor maps of the lattice kernel's inputs for the tensor-copy staging
+// (tile configurations with `tma`): u halo, weight halo, bond words, v, a,
+// 1/m and the two planes of the loads wb and g. Built per launch from the
+// pointers of a Lat2DArgs; needs nx % 4 == 0 (16-byte row pitch of the FP32
+// planes).
+struct LatMaps {
+    CUtensorMap u, al, mk, v, a, im, wb, g;
+};
+
 // Launchers (pd_kernels.cu). `init` computes a_0 from u_0 and predicts u_1
 // without touching v.
 cudaError_t launch_pd_step_f64(int dim, const F64StepArgs &A, bool init, cudaStream_t s);
 cudaError_t launch_pd_step_f32(int dim, const F32StepArgs &A, bool init, cudaStream_t s);
 cudaError_t launch_pd_step_lattice2d(const Lat2DArgs &A, bool init, cudaStream_t s);
 // Lattice tile configurations: strip height KR (nodes per thread, CTA tile
-// 32 x 8 KR), the resident CTAs per SM the registers are limited for, and
+// 32 x 8 KR), the resident CTAs per SM the registers are limited for,
 // whether the persistent pipelined kernel (asynchronous staging of the next
-// tiles) is used.
+// tiles) is used, and whether clean tiles evaluate each bond once (pair).
 struct LatTile {
-    int kr, min_blocks, pipelined;
+    int kr, min_blocks, pipelined, pair, tma;
 };
-constexpr int kLatTiles = 4;
-constexpr LatTile kLatTile[kLatTiles] = {{2, 3, 0}, {2, 4, 0}, {2, 2, 1}, {1, 4, 1}};
+constexpr int kLatTiles = 7;
+constexpr LatTile kLatTile[kLatTiles] = {{2, 3, 0, 0, 0}, {2, 4, 0, 0, 0}, {2, 2, 1, 0, 0}, {1, 4, 1, 0, 0},
+                                         {2, 3, 0, 1, 0}, {2, 4, 0, 0, 1}, {2, 3, 0, 0, 1}};
 cudaError_t launch_lattice2d_t0(const Lat2DArgs &A, bool init, cudaStream_t s);
 cudaError_t launch_lattice2d_t1(const Lat2DArgs &A, bool init, cudaStream_t s);
 cudaError_t launch_lattice2d_t2(const Lat2DArgs &A, bool init, cudaStream_t s);
 cudaError_t launch_lattice2d_t3(const Lat2DArgs &A, bool init, cudaStream_t s);
+cudaError_t launch_lattice2d_t4(const Lat2DArgs &A, bool init, cudaStream_t s);
+cudaError_t launch_lattice2d_t5(const Lat2DArgs &A, bool init, cudaStream_t s);
+cudaError_t launch_lattice2d_t6(const Lat2DArgs &A, bool init, cudaStream_t s);
 // Batched substeps (tile configurations 0 and 1): lattice2d_batch_prepare
 // converts A's windows to the configuration's tile rows and returns the
 // instance's tile count (-1 for another configuration); the launch runs one
@@ -251,7 +265,8 @@ struct pdmts_ctx {
     double gamma_fe = 0.5, beta_fe = 0.25;
     bool time_set = false;
     pdmts_stats stats{};
-    unsigned long long *d_counter = nullptr;  // [0] broken bonds, [1] non-finite input flag
+    unsigned long long *d_counter = nullptr;  // [0] broken bonds, [1] non-finite input flag,
+                                              // [2] a tensor-copy wait of the lattice kernel gave up
     int64_t device_bytes = 0;
     // substep-chain timing
     bool timing = false;

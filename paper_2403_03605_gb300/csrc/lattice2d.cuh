@@ -30,6 +30,9 @@ namespace pdmts {
 // directions of a bond reach the same decision and opposite forces.
 namespace lat2d {
 constexpr int HX = TX + 2 * R;
+// the weight halo is staged from column x0 - R - 1 (16-byte aligned for the
+// tensor copy), so its rows are HX + 2 wide and column hx sits at hx + 1
+constexpr int HXA = HX + 2;
 // reach of stencil column dx: |dy| <= RY(dx) with dx^2 + dy^2 <= 9
 __host__ __device__ constexpr int RY(int dx) { return dx == 0 ? 3 : (dx >= -2 && dx <= 2) ? 2 : 0; }
 __host__ __device__ constexpr int KOF(int dx, int dy)
@@ -168,7 +171,7 @@ __device__ __forceinline__ float lattice_bond(const float4 uj, const float aj, c
 // thread reads each halo value of a column once and applies it to every node
 // of its strip within reach; qmax collects the largest q.
 template <int KR, bool ALPHA, bool PMB>
-__device__ __forceinline__ void lattice_strip(const float4 (*su)[lat2d::HX], const float (*sal)[lat2d::HX],
+__device__ __forceinline__ void lattice_strip(const float4 (*su)[lat2d::HX], const float (*sal)[lat2d::HXA],
                                               const int hy0, const int hx0, const Lat2DArgs &A,
                                               const float4 (&nu)[KR], const float (&ai)[KR],
                                               const uint32_t (&m0)[KR], uint32_t (&m)[KR], float2 (&f)[KR],
@@ -215,7 +218,7 @@ __device__ __forceinline__ void lattice_strip(const float4 (*su)[lat2d::HX], con
 // skipped, in the canonical order (H+ by offset index, then -d for d in H+),
 // so a warp that takes this path without a break gets the fast path's bits.
 template <bool ALPHA, bool PMB>
-__device__ __forceinline__ void lattice_node_masked(const float4 (*su)[lat2d::HX], const float (*sal)[lat2d::HX],
+__device__ __forceinline__ void lattice_node_masked(const float4 (*su)[lat2d::HX], const float (*sal)[lat2d::HXA],
                                                     const int hy, const int hx, const Lat2DArgs &A, const float4 nu,
                                                     const float ai, const uint32_t m0, uint32_t &m, float2 &f)
 {
@@ -236,7 +239,7 @@ __device__ __forceinline__ void lattice_node_masked(const float4 (*su)[lat2d::HX
 // The masked path over a strip: a rolled loop over its nodes (the rare path
 // near cracks and edges; one copy of the bond code, one node's state live).
 template <int KR, bool ALPHA, bool PMB>
-__device__ __forceinline__ void lattice_strip_masked(const float4 (*su)[lat2d::HX], const float (*sal)[lat2d::HX],
+__device__ __forceinline__ void lattice_strip_masked(const float4 (*su)[lat2d::HX], const float (*sal)[lat2d::HXA],
                                                      const int hy0, const int hx0, const Lat2DArgs &A,
                                                      const float4 (&nu)[KR], const float (&ai)[KR],
                                                      const uint32_t (&m0)[KR], uint32_t (&m)[KR], float2 (&f)[KR])
@@ -296,18 +299,81 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
+// ---------------------------------------------------- tensor-copy staging ----
+// The same two groups as tensor copies (cp.async.bulk.tensor) issued by one
+// thread, each completing on an mbarrier. Out-of-lattice parts of a box read
+// as zeros, like the predicated copies above. Every wait is bounded: after
+// kTmaPolls polls (each suspends for at most ~1 us) it gives up; the CTA then
+// raises counter word [2] (reported by the host as an error), waits once more
+// (bounded) for its copies and returns without touching global memory.
+constexpr unsigned kTmaPolls = 1u << 21;
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t *bar, const unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, const unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, const unsigned parity)
+{
+    for (unsigned k = 0; k < kTmaPolls; ++k) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+            " selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(smem_addr(bar)), "r"(parity), "r"(1000u)
+            : "memory");
+        if (done)
+            return true;
+    }
+    return false;
+}
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, const int c0, const int c1,
+                                            uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_addr(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_addr(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, const int c0, const int c1,
+                                            const int c2, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}],"
+        " [%5];" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tma_gave_up(const Lat2DArgs &A)
+{
+    if (threadIdx.x == 0 && A.nd.broken)
+        atomicOr(A.nd.broken + 2, 1ull);
+}
+
 // Inputs of one tile in shared memory.
 template <int KR>
 struct LatStage {
     static constexpr int TYK = lat2d::TY * KR, HY = TYK + 2 * lat2d::R;
-    alignas(16) float4 u[HY][lat2d::HX];
-    alignas(16) float4 v[TYK][lat2d::TX];
-    alignas(16) float2 a[TYK][lat2d::TX];
-    alignas(16) float al[HY][lat2d::HX];
-    alignas(16) float im[TYK][lat2d::TX];
-    alignas(16) uint32_t mk[TYK][lat2d::TX];
-    alignas(16) float wb[2][TYK][lat2d::TX];
-    alignas(16) float g[2][TYK][lat2d::TX];
+    alignas(128) float4 u[HY][lat2d::HX];
+    alignas(128) float4 v[TYK][lat2d::TX];
+    alignas(128) float2 a[TYK][lat2d::TX];
+    alignas(128) float al[HY][lat2d::HXA];
+    alignas(128) float im[TYK][lat2d::TX];
+    alignas(128) uint32_t mk[TYK][lat2d::TX];
+    alignas(128) float wb[2][TYK][lat2d::TX];
+    alignas(128) float g[2][TYK][lat2d::TX];
+    alignas(8) uint64_t bar[2];  // tensor-copy barriers of groups A and B
+    // the weight halo indexed like u: alh()[hy][hx]
+    __device__ const float (*alh() const)[lat2d::HXA]
+    {
+        return reinterpret_cast<const float(*)[lat2d::HXA]>(&al[0][1]);
+    }
 };
 
 template <int KR>
@@ -326,7 +392,7 @@ __device__ __forceinline__ void lattice_issue_a(LatStage<KR> &S, const Lat2DArgs
             const int64_t gi = in ? (int64_t)gy * nx + gx : 0;
             cp_async16(&S.u[hy][hx], A.nd.u4_in + gi, in);
             if (A.alpha)
-                cp_async4(&S.al[hy][hx], A.alpha + gi, in);
+                cp_async4(&S.al[hy][hx + 1], A.alpha + gi, in);
         }
     }
     const int x = x0 + lane;
@@ -366,12 +432,174 @@ __device__ __forceinline__ void lattice_issue_b(LatStage<KR> &S, const Lat2DArgs
     }
 }
 
+// Both groups of a tile as tensor copies (thread 0 only); box bytes equal
+// the stage arrays' sizes, so each barrier completes when its group landed.
+template <int KR>
+__device__ __forceinline__ void lattice_tma_issue(LatStage<KR> &S, const LatMaps &M, const Lat2DArgs &A,
+                                                  const int x0, const int y0)
+{
+    using namespace lat2d;
+    const bool al = A.alpha != nullptr, wb = A.nd.wb != nullptr, g = A.nd.g != nullptr;
+    mbar_expect_tx(&S.bar[0], (unsigned)(sizeof(S.u) + (al ? sizeof(S.al) : 0) + sizeof(S.mk)));
+    tma_load_3d(&S.u[0][0], &M.u, 0, x0 - R, y0 - R, &S.bar[0]);
+    if (al)
+        tma_load_2d(&S.al[0][0], &M.al, x0 - R - 1, y0 - R, &S.bar[0]);
+    tma_load_2d(&S.mk[0][0], &M.mk, x0, y0, &S.bar[0]);
+    mbar_expect_tx(&S.bar[1], (unsigned)(sizeof(S.v) + sizeof(S.a) + sizeof(S.im) + (wb ? sizeof(S.wb) : 0) +
+                                         (g ? sizeof(S.g) : 0)));
+    tma_load_3d(&S.v[0][0], &M.v, 0, x0, y0, &S.bar[1]);
+    tma_load_2d(&S.a[0][0], &M.a, x0, y0, &S.bar[1]);
+    tma_load_2d(&S.im[0][0], &M.im, x0, y0, &S.bar[1]);
+    if (wb)
+        tma_load_3d(&S.wb[0][0][0], &M.wb, x0, y0, 0, &S.bar[1]);
+    if (g)
+        tma_load_3d(&S.g[0][0][0], &M.g, x0, y0, 0, &S.bar[1]);
+}
+
+// ------------------------------------------------- pair-symmetric tiles ----
+// Newton's third law (f_ji = -f_ij, Eq. 2 and Eq. 34's symmetric weights): a
+// CTA whose nodes all hold their 28 bonds evaluates each bond once. Every
+// source node i of a bond into the tile (the tile itself, 3 columns to its
+// left, 3 rows above, 2 below) evaluates its H+ bonds i -> i + d and stores
+// the scalar s of f = s d at the target, s[k][target] for d = d_k; after one
+// barrier each tile node adds its own H+ forces (already in registers) and
+// gathers -s d of its 14 H- bonds, in the canonical order. Halo sources are
+// split into warp-uniform tasks. A CTA in which any bond reached the critical
+// stretch (or any node misses a bond) takes the per-warp paths instead.
+template <int KR>
+struct LatPair {
+    alignas(16) float s[lat2d::NP][lat2d::TY * KR][lat2d::TX];
+};
+
+// Halo tasks: kind 0 = rows y = p < 0 above the tile (lanes along x), 1 = rows
+// y = TYK + p below it, 2 = columns x = p < 0 left of it (lanes along y,
+// y = lane - 3); dxs >= 0 restricts a task to the bonds of column dx = dxs.
+struct PairTask {
+    int kind, p, dxs, warp;
+};
+__host__ __device__ constexpr bool pair_sel(const PairTask t, const int dx, const int dy)
+{
+    const bool col = t.dxs < 0 || dx == t.dxs;
+    return col && (t.kind == 0 ? dy >= -t.p : t.kind == 1 ? dy <= -1 - t.p : dx >= -t.p);
+}
+// 36 bonds per lane over 8 warps, at most 5 each (tiles of 16 rows)
+constexpr int kPairTasks = 13;
+__host__ __device__ constexpr PairTask pair_task(const int i)
+{
+    constexpr PairTask t[kPairTasks] = {{2, -1, 1, 0}, {2, -1, 2, 1}, {2, -2, 2, 2}, {0, -2, -1, 3},
+                                        {0, -3, -1, 3}, {1, 0, -1, 4},  {2, -1, 3, 4}, {0, -1, 0, 5},
+                                        {1, 1, -1, 5},  {0, -1, 1, 6},  {0, -1, 2, 6}, {2, -2, 3, 6},
+                                        {2, -3, 3, 7}};
+    return t[i];
+}
+
+template <int KR, bool ALPHA, int TI>
+__device__ __forceinline__ void pair_halo_task(const LatStage<KR> &S, LatPair<KR> &P, const Lat2DArgs &A,
+                                               const int lane, float &qm)
+{
+    using namespace lat2d;
+    constexpr PairTask t = pair_task(TI);
+    constexpr int TYK = LatStage<KR>::TYK, HY = LatStage<KR>::HY;
+    static_assert(TYK + 5 <= 32, "left-column tasks put the rows on the lanes");
+    const int x = t.kind == 2 ? t.p : lane;
+    const int y = t.kind == 0 ? t.p : t.kind == 1 ? TYK + t.p : lane - R;
+    if (t.kind == 2 && lane >= TYK + 5)
+        return;
+    const float4 ui = S.u[y + R][x + R];
+    const float4 nu = make_float4(-ui.x, -ui.y, -ui.z, -ui.w);
+    const float ai = ALPHA ? S.alh()[y + R][x + R] : 0.f;
+    static_for<0, NP>([&](auto kc) {
+        constexpr int k = decltype(kc)::value;
+        constexpr int dx = PDX(k), dy = PDY(k);
+        if constexpr (pair_sel(pair_task(TI), dx, dy)) {
+            // left-column sources reach rows outside the halo only for targets
+            // outside the tile, whose s is never read: clamp the row
+            const int hy = t.kind == 2 ? min(max(y + dy + R, 0), HY - 1) : y + dy + R;
+            const float4 uj = S.u[hy][x + dx + R];
+            const float aj = ALPHA ? S.alh()[hy][x + dx + R] : 0.f;
+            float2 fd = make_float2(0.f, 0.f);
+            uint32_t md = 0u;
+            float q = -INFINITY;
+            const float sb = lattice_bond<dx, dy, ALPHA, false, false>(uj, aj, nu, ai, A, 0u, md, fd, q);
+            const bool tgt = x + dx >= 0 && x + dx < TX && y + dy >= 0 && y + dy < TYK;
+            if (tgt) {
+                P.s[k][y + dy][x + dx] = sb;
+                qm = fmaxf(qm, q);
+            }
+        }
+    });
+}
+
+// Pair evaluation of a clean tile: this thread's strip bonds of H+ (forces
+// into f, s into P) and its warp's halo tasks; qm collects the largest q.
+template <int KR, bool ALPHA>
+__device__ __forceinline__ void pair_compute(const LatStage<KR> &S, LatPair<KR> &P, const Lat2DArgs &A,
+                                             const float4 (&nu)[KR], const float (&ai)[KR], float2 (&f)[KR],
+                                             float &qm)
+{
+    using namespace lat2d;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int hx0 = tx + R, hy0 = ty * KR + R;
+    float qmax[KR];
+#pragma unroll
+    for (int r = 0; r < KR; ++r)
+        qmax[r] = -INFINITY;
+    static_for<0, R + 1>([&](auto dxc) {
+        constexpr int dx = decltype(dxc)::value;
+        constexpr int ry = RY(dx), lo = PLO(dx);
+        asm volatile("" ::: "memory");
+        static_for<lo, KR + ry>([&](auto jc) {
+            constexpr int j = decltype(jc)::value;
+            const float4 uj = S.u[hy0 + j][hx0 + dx];
+            const float aj = ALPHA ? S.alh()[hy0 + j][hx0 + dx] : 0.f;
+            static_for<0, KR>([&](auto rc) {
+                constexpr int r = decltype(rc)::value;
+                constexpr int dy = j - r;
+                if constexpr (dy >= lo && dy <= ry) {
+                    uint32_t md = 0u;
+                    const float sb =
+                        lattice_bond<dx, dy, ALPHA, false, false>(uj, aj, nu[r], ai[r], A, 0u, md, f[r], qmax[r]);
+                    const int yt = ty * KR + r + dy;  // the target, if in the tile
+                    if (tx + dx < TX && yt >= 0 && yt < KR * TY)
+                        P.s[KP(dx, dy)][yt][tx + dx] = sb;
+                }
+            });
+        });
+    });
+#pragma unroll
+    for (int r = 0; r < KR; ++r)
+        qm = fmaxf(qm, qmax[r]);
+    static_for<0, kPairTasks>([&](auto tc) {
+        constexpr int ti = decltype(tc)::value;
+        if (pair_task(ti).warp == ty)
+            pair_halo_task<KR, ALPHA, ti>(S, P, A, tx, qm);
+    });
+}
+
+// The 14 H- forces of this thread's strip nodes from their sources' s.
+template <int KR>
+__device__ __forceinline__ void pair_gather(const LatPair<KR> &P, float2 (&f)[KR])
+{
+    using namespace lat2d;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    static_for<0, KR>([&](auto rc) {
+        constexpr int r = decltype(rc)::value;
+        static_for<0, NP>([&](auto kc) {
+            constexpr int k = decltype(kc)::value;
+            constexpr int dx = PDX(k), dy = PDY(k);
+            const float s = P.s[k][ty * KR + r][tx];
+            lattice_acc<-dx>(f[r].x, s);
+            lattice_acc<-dy>(f[r].y, s);
+        });
+    });
+}
+
 // The substep of the tile at (x0, y0) from its staged inputs. On entry this
 // thread's group A has landed; group B is awaited with cp.async.wait_group
 // WAIT_B before the per-node update. Returns the bonds this thread broke.
-template <bool PMB, int KR, int WAIT_B>
+template <bool PMB, int KR, int WAIT_B, bool PAIR = false>
 __device__ __forceinline__ unsigned lattice_tile(LatStage<KR> &S, const Lat2DArgs &A, const int x0, const int y0,
-                                                 const int init)
+                                                 const int init, LatPair<KR> *P = nullptr)
 {
     using namespace lat2d;
     constexpr int HY = LatStage<KR>::HY;
@@ -380,7 +608,7 @@ __device__ __forceinline__ unsigned lattice_tile(LatStage<KR> &S, const Lat2DArg
     bool any_alpha = false;
     if (A.alpha)
         for (int q = threadIdx.x; q < HY * HX; q += blockDim.x)
-            any_alpha |= (&S.al[0][0])[q] != 0.f;
+            any_alpha |= S.alh()[q / HX][q % HX] != 0.f;
     // a tile whose halo carries no Arlequin weight evaluates every bond with
     // weight 1 exactly, so it can skip the weights (the barrier also makes
     // every thread's group A visible)
@@ -403,19 +631,40 @@ __device__ __forceinline__ unsigned lattice_tile(LatStage<KR> &S, const Lat2DArg
         full = full && (m0[r] == kFullWord || !valid);
         const float4 u = S.u[hy0 + r][hx0];
         nu[r] = make_float4(-u.x, -u.y, -u.z, -u.w);
-        ai[r] = has_alpha ? S.al[hy0 + r][hx0] : 0.f;
+        ai[r] = has_alpha ? S.alh()[hy0 + r][hx0] : 0.f;
         f[r] = make_float2(0.f, 0.f);
         qmax[r] = -INFINITY;
+    }
+    bool done = false;
+    if constexpr (PAIR && !PMB) {
+        // every node of the tile in the lattice with all its bonds intact
+        const bool clean = __syncthreads_and(full && vbits == (1u << KR) - 1u) != 0;
+        if (clean) {
+            float qm = -INFINITY;
+            if (has_alpha)
+                pair_compute<KR, true>(S, *P, A, nu, ai, f, qm);
+            else
+                pair_compute<KR, false>(S, *P, A, nu, ai, f, qm);
+            // the barrier also publishes every s
+            if (__syncthreads_or(N.breaking && qm >= A.qthr) == 0) {
+                pair_gather<KR>(*P, f);
+                done = true;
+            } else {
+#pragma unroll
+                for (int r = 0; r < KR; ++r)
+                    f[r] = make_float2(0.f, 0.f);
+            }
+        }
     }
     // Fast path: every node of the warp has all bonds intact; evaluate all
     // bonds without per-bond control flow and only note the largest q. If a
     // bond reached the critical stretch (rare), redo the warp bond by bond.
-    bool fast = __all_sync(0xffffffffu, full);
+    bool fast = !done && __all_sync(0xffffffffu, full);
     if (fast) {
         if (has_alpha)
-            lattice_strip<KR, true, PMB>(S.u, S.al, hy0, hx0, A, nu, ai, m0, m, f, qmax);
+            lattice_strip<KR, true, PMB>(S.u, S.alh(), hy0, hx0, A, nu, ai, m0, m, f, qmax);
         else
-            lattice_strip<KR, false, PMB>(S.u, S.al, hy0, hx0, A, nu, ai, m0, m, f, qmax);
+            lattice_strip<KR, false, PMB>(S.u, S.alh(), hy0, hx0, A, nu, ai, m0, m, f, qmax);
         bool hit = false;
 #pragma unroll
         for (int r = 0; r < KR; ++r)
@@ -423,13 +672,22 @@ __device__ __forceinline__ unsigned lattice_tile(LatStage<KR> &S, const Lat2DArg
         if (N.breaking && __any_sync(0xffffffffu, hit))
             fast = false;
     }
-    if (!fast) {
+    if (!fast && !done) {
         if (has_alpha)
-            lattice_strip_masked<KR, true, PMB>(S.u, S.al, hy0, hx0, A, nu, ai, m0, m, f);
+            lattice_strip_masked<KR, true, PMB>(S.u, S.alh(), hy0, hx0, A, nu, ai, m0, m, f);
         else
-            lattice_strip_masked<KR, false, PMB>(S.u, S.al, hy0, hx0, A, nu, ai, m0, m, f);
+            lattice_strip_masked<KR, false, PMB>(S.u, S.alh(), hy0, hx0, A, nu, ai, m0, m, f);
     }
-    cp_async_wait<WAIT_B>();  // this thread's group B (its own strip) has landed
+    if constexpr (WAIT_B >= 0) {
+        cp_async_wait<WAIT_B>();  // this thread's group B (its own strip) has landed
+    } else {
+        const bool ok = mbar_wait(&S.bar[1], 0);  // the tile's group B (tensor copies)
+        if (__syncthreads_or(!ok)) {
+            tma_gave_up(A);
+            mbar_wait(&S.bar[1], 0);
+            return 0;
+        }
+    }
     unsigned nbroken = 0;
 #pragma unroll
     for (int r = 0; r < KR; ++r) {
@@ -467,12 +725,14 @@ __device__ __forceinline__ void lattice_chain_entry()
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
-// One CTA per tile (grid: tile columns x tile rows).
-template <bool PMB, int KR, int MINB>
+// One CTA per tile (grid: tile columns x tile rows); PAIR adds the
+// pair-symmetric path (its s table after the stage in shared memory).
+template <bool PMB, int KR, int MINB, bool PAIR = false>
 __global__ void __launch_bounds__(256, MINB) k_pd_step_lattice2d(const Lat2DArgs A, const int init)
 {
     extern __shared__ __align__(16) unsigned char lat_smem[];
     LatStage<KR> &S = *reinterpret_cast<LatStage<KR> *>(lat_smem);
+    LatPair<KR> *P = PAIR ? reinterpret_cast<LatPair<KR> *>(lat_smem + sizeof(LatStage<KR>)) : nullptr;
     const int x0 = blockIdx.x * lat2d::TX, y0 = lattice_trow(A, (int)blockIdx.y) * LatStage<KR>::TYK;
     lattice_chain_entry();
     lattice_issue_a<KR>(S, A, x0, y0);
@@ -480,7 +740,38 @@ __global__ void __launch_bounds__(256, MINB) k_pd_step_lattice2d(const Lat2DArgs
     lattice_issue_b<KR>(S, A, x0, y0);
     cp_async_commit();
     cp_async_wait<1>();
-    const unsigned nbroken = lattice_tile<PMB, KR, 0>(S, A, x0, y0, init);
+    const unsigned nbroken = lattice_tile<PMB, KR, 0, PAIR>(S, A, x0, y0, init, P);
+    count_broken(A.nd.broken, nbroken);
+}
+
+// One CTA per tile with the inputs staged by tensor copies. The dynamic
+// shared memory is realigned to 128 bytes for the copy destinations.
+template <bool PMB, int KR, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_pd_step_lattice2d_tma(const Lat2DArgs A,
+                                                                      const __grid_constant__ LatMaps M,
+                                                                      const int init)
+{
+    extern __shared__ __align__(16) unsigned char lat_smem[];
+    const unsigned off = (128u - (smem_addr(lat_smem) & 127u)) & 127u;
+    LatStage<KR> &S = *reinterpret_cast<LatStage<KR> *>(lat_smem + off);
+    const int x0 = blockIdx.x * lat2d::TX, y0 = lattice_trow(A, (int)blockIdx.y) * LatStage<KR>::TYK;
+    if (threadIdx.x == 0) {
+        mbar_init(&S.bar[0], 1);
+        mbar_init(&S.bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    lattice_chain_entry();
+    if (threadIdx.x == 0)
+        lattice_tma_issue<KR>(S, M, A, x0, y0);
+    const bool ok = mbar_wait(&S.bar[0], 0);
+    if (__syncthreads_or(!ok)) {
+        tma_gave_up(A);
+        mbar_wait(&S.bar[0], 0);
+        mbar_wait(&S.bar[1], 0);
+        return;
+    }
+    const unsigned nbroken = lattice_tile<PMB, KR, -1>(S, A, x0, y0, init);
     count_broken(A.nd.broken, nbroken);
 }
 
@@ -644,12 +935,14 @@ cudaError_t launch_lattice_pipe(const Lat2DArgs &A0, bool init, cudaStream_t s)
     return lattice_launch(kern, dim3((unsigned)grid), smem, s, A.pdl != 0, A, init ? 1 : 0, ntiles);
 }
 
-template <int KR, int MINB>
+template <int KR, int MINB, bool PAIR = false>
 cudaError_t launch_lattice_kr(const Lat2DArgs &A0, bool init, cudaStream_t s)
 {
-    constexpr size_t smem = sizeof(LatStage<KR>);
+    // the pair path serves the linear law; PMB tiles take the per-warp paths
+    const size_t smem = sizeof(LatStage<KR>) + (PAIR && !A0.nd.pmb ? sizeof(LatPair<KR>) : 0);
     static int ctas[2] = {0, 0};
-    const auto kern = A0.nd.pmb ? k_pd_step_lattice2d<true, KR, MINB> : k_pd_step_lattice2d<false, KR, MINB>;
+    const auto kern =
+        A0.nd.pmb ? k_pd_step_lattice2d<true, KR, MINB, false> : k_pd_step_lattice2d<false, KR, MINB, PAIR>;
     cudaError_t e = lattice_prepare(kern, smem, ctas[A0.nd.pmb ? 1 : 0]);
     if (e != cudaSuccess)
         return e;
@@ -657,6 +950,30 @@ cudaError_t launch_lattice_kr(const Lat2DArgs &A0, bool init, cudaStream_t s)
     const unsigned rows = (unsigned)lattice_tile_rows<LatStage<KR>::TYK>(A, A0);
     const dim3 grid((unsigned)((A.nx + lat2d::TX - 1) / lat2d::TX), rows);
     return lattice_launch(kern, grid, smem, s, A.pdl != 0, A, init ? 1 : 0);
+}
+
+// Tensor maps of the inputs of one launch (lattice2d_tma.cu); false when the
+// lattice does not meet the copies' alignment (nx % 4 != 0) or encoding failed.
+bool lattice_make_maps(const Lat2DArgs &A, int tyk, LatMaps &M);
+
+// Tile configuration with tensor-copy staging; lattices that the copies cannot
+// address take the asynchronous-copy kernel of the same shape (same bits).
+template <int KR, int MINB>
+cudaError_t launch_lattice_tma(const Lat2DArgs &A0, bool init, cudaStream_t s)
+{
+    LatMaps M;
+    if (!lattice_make_maps(A0, LatStage<KR>::TYK, M))
+        return launch_lattice_kr<KR, MINB>(A0, init, s);
+    constexpr size_t smem = sizeof(LatStage<KR>) + 128;
+    static int ctas[2] = {0, 0};
+    const auto kern = A0.nd.pmb ? k_pd_step_lattice2d_tma<true, KR, MINB> : k_pd_step_lattice2d_tma<false, KR, MINB>;
+    cudaError_t e = lattice_prepare(kern, smem, ctas[A0.nd.pmb ? 1 : 0]);
+    if (e != cudaSuccess)
+        return e;
+    Lat2DArgs A = A0;
+    const unsigned rows = (unsigned)lattice_tile_rows<LatStage<KR>::TYK>(A, A0);
+    const dim3 grid((unsigned)((A.nx + lat2d::TX - 1) / lat2d::TX), rows);
+    return lattice_launch(kern, grid, smem, s, A.pdl != 0, A, M, init ? 1 : 0);
 }
 
 template <int KR, int MINB>

@@ -586,6 +586,9 @@ cudaError_t launch_pd_step_lattice2d(const Lat2DArgs &A, bool init, cudaStream_t
     case 1: return launch_lattice2d_t1(A, init, s);
     case 2: return launch_lattice2d_t2(A, init, s);
     case 3: return launch_lattice2d_t3(A, init, s);
+    case 4: return launch_lattice2d_t4(A, init, s);
+    case 5: return launch_lattice2d_t5(A, init, s);
+    case 6: return launch_lattice2d_t6(A, init, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -127,6 +127,7 @@ def test_graph_chain_equals_single_steps(fresh):
 LATTICE_CASES = [
     dict(name="config0", pb=lambda: W.config0(), steps=500),
     dict(name="weights", pb=lambda: W.small_plate(70, 45, nsteps=150), alpha=True, steps=150),
+    dict(name="weights_nx72", pb=lambda: W.small_plate(72, 45, nsteps=150), alpha=True, steps=150),
     dict(name="pmb", pb=lambda: W.small_plate(66, 41, nsteps=150), force=True, steps=150),
     dict(name="tiny", pb=lambda: W.plate2d(5, 3, 0.5e-3, traction=60e6), steps=40),
 ]
