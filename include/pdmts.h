@@ -151,10 +151,12 @@ int pd_set_force_law(pdmts_pd *pd, int kind);
  * their bonds evaluates each bond once (f_ji = -f_ij) and exchanges the
  * reactions through shared memory (linear force law; PMB as configuration 0);
  * 5 and 6: configurations 1 and 0 with every input of a tile staged by
- * tensor copies (lattices with nx % 4 != 0 take configurations 1 and 0).
+ * tensor copies; 7 and 8: persistent grids with two tensor-copy stages (the
+ * next tiles in flight while the CTA computes), 2 and 1 nodes per thread.
+ * Lattices with nx % 4 != 0 take configurations 1, 0, 0 and 1 for 5 to 8.
  * Other layouts and precisions ignore the setting. PDMTS_ERR_ARG if out of
  * range. */
-#define PDMTS_LATTICE_TILES 7
+#define PDMTS_LATTICE_TILES 9
 #define PDMTS_LATTICE_TILE_AUTO (-1)
 int pd_set_lattice_tile(pdmts_pd *pd, int tile);
 

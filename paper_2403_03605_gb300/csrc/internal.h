@@ -171,9 +171,10 @@ cudaError_t launch_pd_step_lattice2d(const Lat2DArgs &A, bool init, cudaStream_t
 struct LatTile {
     int kr, min_blocks, pipelined, pair, tma;
 };
-constexpr int kLatTiles = 7;
+constexpr int kLatTiles = 9;
 constexpr LatTile kLatTile[kLatTiles] = {{2, 3, 0, 0, 0}, {2, 4, 0, 0, 0}, {2, 2, 1, 0, 0}, {1, 4, 1, 0, 0},
-                                         {2, 3, 0, 1, 0}, {2, 4, 0, 0, 1}, {2, 3, 0, 0, 1}};
+                                         {2, 3, 0, 1, 0}, {2, 4, 0, 0, 1}, {2, 3, 0, 0, 1}, {2, 2, 1, 0, 1},
+                                         {1, 4, 1, 0, 1}};
 cudaError_t launch_lattice2d_t0(const Lat2DArgs &A, bool init, cudaStream_t s);
 cudaError_t launch_lattice2d_t1(const Lat2DArgs &A, bool init, cudaStream_t s);
 cudaError_t launch_lattice2d_t2(const Lat2DArgs &A, bool init, cudaStream_t s);
@@ -181,6 +182,8 @@ cudaError_t launch_lattice2d_t3(const Lat2DArgs &A, bool init, cudaStream_t s);
 cudaError_t launch_lattice2d_t4(const Lat2DArgs &A, bool init, cudaStream_t s);
 cudaError_t launch_lattice2d_t5(const Lat2DArgs &A, bool init, cudaStream_t s);
 cudaError_t launch_lattice2d_t6(const Lat2DArgs &A, bool init, cudaStream_t s);
+cudaError_t launch_lattice2d_t7(const Lat2DArgs &A, bool init, cudaStream_t s);
+cudaError_t launch_lattice2d_t8(const Lat2DArgs &A, bool init, cudaStream_t s);
 // Batched substeps (tile configurations 0 and 1): lattice2d_batch_prepare
 // converts A's windows to the configuration's tile rows and returns the
 // instance's tile count (-1 for another configuration); the launch runs one

@@ -597,9 +597,12 @@ __device__ __forceinline__ void pair_gather(const LatPair<KR> &P, float2 (&f)[KR
 // The substep of the tile at (x0, y0) from its staged inputs. On entry this
 // thread's group A has landed; group B is awaited with cp.async.wait_group
 // WAIT_B before the per-node update. Returns the bonds this thread broke.
+// WAIT_B < 0: group B came by tensor copies completing phase parity parB of
+// S.bar[1]; if that wait gives up the CTA returns kTileGaveUp at once.
+constexpr unsigned kTileGaveUp = ~0u;
 template <bool PMB, int KR, int WAIT_B, bool PAIR = false>
 __device__ __forceinline__ unsigned lattice_tile(LatStage<KR> &S, const Lat2DArgs &A, const int x0, const int y0,
-                                                 const int init, LatPair<KR> *P = nullptr)
+                                                 const int init, LatPair<KR> *P = nullptr, const unsigned parB = 0)
 {
     using namespace lat2d;
     constexpr int HY = LatStage<KR>::HY;
@@ -681,11 +684,11 @@ __device__ __forceinline__ unsigned lattice_tile(LatStage<KR> &S, const Lat2DArg
     if constexpr (WAIT_B >= 0) {
         cp_async_wait<WAIT_B>();  // this thread's group B (its own strip) has landed
     } else {
-        const bool ok = mbar_wait(&S.bar[1], 0);  // the tile's group B (tensor copies)
+        const bool ok = mbar_wait(&S.bar[1], parB);  // the tile's group B (tensor copies)
         if (__syncthreads_or(!ok)) {
             tma_gave_up(A);
-            mbar_wait(&S.bar[1], 0);
-            return 0;
+            mbar_wait(&S.bar[1], parB);
+            return kTileGaveUp;
         }
     }
     unsigned nbroken = 0;
@@ -772,6 +775,73 @@ __global__ void __launch_bounds__(256, MINB) k_pd_step_lattice2d_tma(const Lat2D
         return;
     }
     const unsigned nbroken = lattice_tile<PMB, KR, -1>(S, A, x0, y0, init);
+    if (nbroken != kTileGaveUp)
+        count_broken(A.nd.broken, nbroken);
+}
+
+// Persistent variant with tensor-copy staging: a grid of (SMs x resident
+// CTAs) walks the tile list; one thread keeps the next tile of each of the
+// two stages in flight while the CTA computes the current one. Stage s is
+// used for the CTA's tiles k = s, s + 2, ...: its barriers complete phase
+// parity (k / 2) & 1. The same per-tile code, so the same bits.
+template <bool PMB, int KR, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_pd_step_lattice2d_tpipe(const Lat2DArgs A,
+                                                                        const __grid_constant__ LatMaps M,
+                                                                        const int init, const int ntiles)
+{
+    constexpr int TYK = LatStage<KR>::TYK;
+    extern __shared__ __align__(16) unsigned char lat_smem[];
+    const unsigned off = (128u - (smem_addr(lat_smem) & 127u)) & 127u;
+    LatStage<KR> *stages = reinterpret_cast<LatStage<KR> *>(lat_smem + off);
+    const int ntx = (A.nx + lat2d::TX - 1) / lat2d::TX;
+    const int G = gridDim.x;
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < 2; ++q) {
+            mbar_init(&stages[q].bar[0], 1);
+            mbar_init(&stages[q].bar[1], 1);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    lattice_chain_entry();
+    auto issue = [&](LatStage<KR> &S, const int t) {
+        if (t < ntiles)
+            lattice_tma_issue<KR>(S, M, A, (t % ntx) * lat2d::TX, lattice_trow(A, t / ntx) * TYK);
+    };
+    if (threadIdx.x == 0) {
+        issue(stages[0], blockIdx.x);
+        issue(stages[1], blockIdx.x + G);
+    }
+    unsigned nbroken = 0;
+    int k = 0;
+    for (int t = blockIdx.x; t < ntiles; t += G, ++k) {
+        LatStage<KR> &S = stages[k & 1];
+        const unsigned par = (unsigned)(k >> 1) & 1u;
+        const bool ok = mbar_wait(&S.bar[0], par);
+        if (__syncthreads_or(!ok)) {  // give up: let this tile's and the other stage's copies land first
+            tma_gave_up(A);
+            mbar_wait(&S.bar[0], par);
+            mbar_wait(&S.bar[1], par);
+            if (t + G < ntiles) {
+                mbar_wait(&stages[(k + 1) & 1].bar[0], (unsigned)((k + 1) >> 1) & 1u);
+                mbar_wait(&stages[(k + 1) & 1].bar[1], (unsigned)((k + 1) >> 1) & 1u);
+            }
+            return;
+        }
+        const int x0 = (t % ntx) * lat2d::TX, y0 = lattice_trow(A, t / ntx) * TYK;
+        const unsigned r = lattice_tile<PMB, KR, -1>(S, A, x0, y0, init, nullptr, par);
+        if (r == kTileGaveUp) {
+            if (t + G < ntiles) {
+                mbar_wait(&stages[(k + 1) & 1].bar[0], (unsigned)((k + 1) >> 1) & 1u);
+                mbar_wait(&stages[(k + 1) & 1].bar[1], (unsigned)((k + 1) >> 1) & 1u);
+            }
+            return;
+        }
+        nbroken += r;
+        __syncthreads();  // every thread is done with S
+        if (threadIdx.x == 0)
+            issue(S, t + 2 * G);
+    }
     count_broken(A.nd.broken, nbroken);
 }
 
@@ -974,6 +1044,28 @@ cudaError_t launch_lattice_tma(const Lat2DArgs &A0, bool init, cudaStream_t s)
     const unsigned rows = (unsigned)lattice_tile_rows<LatStage<KR>::TYK>(A, A0);
     const dim3 grid((unsigned)((A.nx + lat2d::TX - 1) / lat2d::TX), rows);
     return lattice_launch(kern, grid, smem, s, A.pdl != 0, A, M, init ? 1 : 0);
+}
+
+// Persistent tensor-copy configuration (falls back like launch_lattice_tma).
+template <int KR, int MINB>
+cudaError_t launch_lattice_tpipe(const Lat2DArgs &A0, bool init, cudaStream_t s)
+{
+    LatMaps M;
+    if (!lattice_make_maps(A0, LatStage<KR>::TYK, M))
+        return launch_lattice_kr<KR, MINB>(A0, init, s);
+    constexpr size_t smem = 2 * sizeof(LatStage<KR>) + 128;
+    static int ctas[2] = {0, 0};
+    const auto kern =
+        A0.nd.pmb ? k_pd_step_lattice2d_tpipe<true, KR, MINB> : k_pd_step_lattice2d_tpipe<false, KR, MINB>;
+    int &nb = ctas[A0.nd.pmb ? 1 : 0];
+    cudaError_t e = lattice_prepare(kern, smem, nb);
+    if (e != cudaSuccess)
+        return e;
+    Lat2DArgs A = A0;
+    const int rows = lattice_tile_rows<LatStage<KR>::TYK>(A, A0);
+    const int ntiles = ((A.nx + lat2d::TX - 1) / lat2d::TX) * rows;
+    const int grid = std::max(1, std::min(ntiles, A.num_sms * nb));
+    return lattice_launch(kern, dim3((unsigned)grid), smem, s, A.pdl != 0, A, M, init ? 1 : 0, ntiles);
 }
 
 template <int KR, int MINB>

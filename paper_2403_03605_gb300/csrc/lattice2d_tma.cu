@@ -1,5 +1,5 @@
 // lattice2d_tma.cu -- tensor maps of the lattice kernel's inputs for the
-// tensor-copy staging (tile configurations 5 and 6), and their launchers.
+// tensor-copy staging (tile configurations 5 to 8), and their launchers.
 #include <cudaTypedefs.h>
 
 #include "lattice2d.cuh"
@@ -83,6 +83,16 @@ cudaError_t launch_lattice2d_t5(const Lat2DArgs &A, bool init, cudaStream_t s)
 cudaError_t launch_lattice2d_t6(const Lat2DArgs &A, bool init, cudaStream_t s)
 {
     return launch_lattice_tma<2, 3>(A, init, s);
+}
+
+cudaError_t launch_lattice2d_t7(const Lat2DArgs &A, bool init, cudaStream_t s)
+{
+    return launch_lattice_tpipe<2, 2>(A, init, s);
+}
+
+cudaError_t launch_lattice2d_t8(const Lat2DArgs &A, bool init, cudaStream_t s)
+{
+    return launch_lattice_tpipe<1, 4>(A, init, s);
 }
 
 }  // namespace pdmts

@@ -589,6 +589,8 @@ cudaError_t launch_pd_step_lattice2d(const Lat2DArgs &A, bool init, cudaStream_t
     case 4: return launch_lattice2d_t4(A, init, s);
     case 5: return launch_lattice2d_t5(A, init, s);
     case 6: return launch_lattice2d_t6(A, init, s);
+    case 7: return launch_lattice2d_t7(A, init, s);
+    case 8: return launch_lattice2d_t8(A, init, s);
     default: return cudaErrorInvalidValue;
     }
 }
