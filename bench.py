@@ -107,7 +107,9 @@ class ClockSampler:
 
 
 def algorithmic_bytes(info, pb, with_body=True, coupled=False):
-    """Bytes one FP32-bulk 2D substep must move with the family layout in use.
+    """Bytes one FP32-bulk substep must move with the family layout in use.
+    (3D: u and v 24 + 24 B each, a 16 + 16 B, loads 12 B, weight and
+    interface force 16 B; the 3D lattice reads four bond words, 16 B.)
 
     Per node: u (16 in, 16 out), v (16 in, 16 out), a (8 in, 8 out), 1/m (4),
     plus the weighted body force (8) in the pure-PD plate, or the Arlequin
@@ -118,6 +120,8 @@ def algorithmic_bytes(info, pb, with_body=True, coupled=False):
     nb, n = info["n_bonds"], info["n"]
     if info["dim"] == 3:  # u, v: 24 B pairs (hi xyz + lo xyz); a: 16 B; loads 12 B
         per_node = 24 + 24 + 24 + 24 + 16 + 16 + 4 + (12 if with_body else 0) + (16 if coupled else 0)
+        if info["layout"] == 2:  # 3D lattice: four bond words per node, no family list
+            return (per_node + 16) * n, per_node + 16
         return 4 * nb + nb / 8.0 + per_node * n, per_node
     per_node = 16 + 16 + 16 + 16 + 8 + 8 + 4 + (8 if with_body else 0) + (12 if coupled else 0)
     if info["layout"] == 1:
@@ -404,7 +408,8 @@ def run_ours(args, rank, world, local_rank):
                    "k_pd_step_lattice2d<false,2,3,true>", "k_pd_step_lattice2d_tma<false,2,4>",
                    "k_pd_step_lattice2d_tma<false,2,3>", "k_pd_step_lattice2d_tpipe<false,2,2>",
                    "k_pd_step_lattice2d_tpipe<false,1,4>"]
-    kname = lat_kernels[tile] if info["layout"] == 1 and tile >= 0 else f"k_pd_step_f32<{info['dim']}>"
+    kname = (lat_kernels[tile] if info["layout"] == 1 and tile >= 0 else
+             "k_pd_step_lattice3d<false,false>" if info["layout"] == 2 else f"k_pd_step_f32<{info['dim']}>")
     traffic = None
     tfile = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tfile):
@@ -454,7 +459,7 @@ def run_ours(args, rank, world, local_rank):
         cfg = {"workload": (COUPLED3D_NAME if args.workload == "coupled3d" else COUPLED_NAME) if coupled
                else WORKLOAD["name"], "pd_nodes": pb.n,
                "directed_bonds": info["n_bonds"], "m": m,
-               "family_layout": "lattice bond words" if info["layout"] == 1 else "sliced ELL",
+               "family_layout": {0: "sliced ELL", 1: "lattice bond words", 2: "3D lattice bond words"}[info["layout"]],
                "lattice_tile": tile,
                "graph": "one captured graph per PD substep chain",
                "parallelism": f"replicas x{world}" if world > 1 else "single GPU",

@@ -168,7 +168,8 @@ typedef struct {
     int64_t n_slots;       /* stored slots of the sliced-ELL layout        */
     int32_t max_degree;    /* largest family                               */
     int32_t on_lattice;    /* 1 if the nodes lie on a regular lattice      */
-    int32_t layout;        /* 0: sliced-ELL list; 1: 2D lattice bond words */
+    int32_t layout;        /* 0: sliced-ELL list; 1: 2D lattice bond words;
+                              2: 3D lattice bond words (4 per node)        */
     int32_t lattice_nx;    /* lattice layout: nodes along x                */
     int32_t lattice_ny;    /* lattice layout: nodes along y                */
     int32_t lattice_tile;  /* lattice kernel tile configuration in use,
@@ -176,6 +177,7 @@ typedef struct {
     double lattice_h;      /* lattice spacing (0 if not on a lattice)      */
     int64_t steps_done;    /* PD substeps advanced since creation          */
     int64_t device_bytes;  /* device memory held by this subdomain         */
+    int32_t lattice_nz;    /* 3D lattice layout: nodes along z (else 0)    */
 } pdmts_pd_info;
 int pd_info(const pdmts_pd *pd, pdmts_pd_info *info);
 

@@ -588,6 +588,10 @@ static inline void bond_bit(const pdmts_pd *pd, int64_t i, int32_t k, int64_t &w
     if (pd->layout == pdmts_pd::LAYOUT_LATTICE2D) {
         word = i;
         bit = pd->slot_of_csr[(size_t)(pd->row_ptr[(size_t)i] + k)];
+    } else if (pd->layout == pdmts_pd::LAYOUT_LATTICE3D) {
+        const int slot = pd->slot_of_csr[(size_t)(pd->row_ptr[(size_t)i] + k)];
+        word = (int64_t)(slot / 32) * pd->n + i;
+        bit = slot % 32;
     } else {
         word = pd->mask_ptr[(size_t)(i / 32)] + 32 * (k / 32) + (i % 32);
         bit = k % 32;
@@ -651,6 +655,72 @@ static bool try_lattice2d(pdmts_pd *pd)
     return true;
 }
 
+// The 3D lattice layout: the nodes are exactly the nx * ny * nz box numbered
+// x + nx (y + ny z) and every family is the 122-offset stencil |d|^2 <= 9
+// clipped to the box. Builds the four bond words of every node on success.
+static bool try_lattice3d(pdmts_pd *pd)
+{
+    if (pd->dim != 3 || !pd->on_lattice)
+        return false;
+    const int64_t n = pd->n;
+    int32_t nx = 0, ny = 0, nz = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        nx = std::max(nx, pd->lk[(size_t)i] + 1);
+        ny = std::max(ny, pd->lk[(size_t)n + i] + 1);
+        nz = std::max(nz, pd->lk[(size_t)2 * n + i] + 1);
+    }
+    if ((int64_t)nx * ny * nz != n || nx < 7 || ny < 7)
+        return false;
+    for (int64_t i = 0; i < n; ++i)
+        if (pd->lk[(size_t)i] + (int64_t)nx * (pd->lk[(size_t)n + i] + (int64_t)ny * pd->lk[(size_t)2 * n + i]) != i)
+            return false;
+    int slot_of[7][7][7];
+    int k = 0;
+    for (int dz = -3; dz <= 3; ++dz)
+        for (int dy = -3; dy <= 3; ++dy)
+            for (int dx = -3; dx <= 3; ++dx) {
+                const int r2 = dx * dx + dy * dy + dz * dz;
+                slot_of[dz + 3][dy + 3][dx + 3] = (r2 == 0 || r2 > 9) ? -1 : k++;
+            }
+    if (k != lat3d::NS)
+        return false;
+    std::vector<int8_t> slot((size_t)pd->row_ptr[(size_t)n]);
+    std::vector<uint32_t> words((size_t)lat3d::W * n, 0u);
+    for (int64_t i = 0; i < n; ++i) {
+        const int xi = pd->lk[(size_t)i], yi = pd->lk[(size_t)n + i], zi = pd->lk[(size_t)2 * n + i];
+        for (int64_t q = pd->row_ptr[(size_t)i]; q < pd->row_ptr[(size_t)i + 1]; ++q) {
+            const int64_t j = pd->col[(size_t)q];
+            const int ox = pd->lk[(size_t)j] - xi, oy = pd->lk[(size_t)n + j] - yi, oz = pd->lk[(size_t)2 * n + j] - zi;
+            if (ox < -3 || ox > 3 || oy < -3 || oy > 3 || oz < -3 || oz > 3 || slot_of[oz + 3][oy + 3][ox + 3] < 0)
+                return false;
+            const int sl = slot_of[oz + 3][oy + 3][ox + 3];
+            slot[(size_t)q] = (int8_t)sl;
+            words[(size_t)(sl / 32) * n + i] |= 1u << (sl % 32);
+        }
+        int expect = 0;
+        for (int dz = -3; dz <= 3; ++dz)
+            for (int dy = -3; dy <= 3; ++dy)
+                for (int dx = -3; dx <= 3; ++dx)
+                    if (slot_of[dz + 3][dy + 3][dx + 3] >= 0) {
+                        const int x = xi + dx, y = yi + dy, z = zi + dz;
+                        expect += x >= 0 && x < nx && y >= 0 && y < ny && z >= 0 && z < nz;
+                    }
+        if (expect != pd->row_ptr[(size_t)i + 1] - pd->row_ptr[(size_t)i])
+            return false;
+    }
+    pd->layout = pdmts_pd::LAYOUT_LATTICE3D;
+    pd->lat_dims[0] = nx;
+    pd->lat_dims[1] = ny;
+    pd->lat_dims[2] = nz;
+    pd->slot_of_csr.swap(slot);
+    pd->mask_host.swap(words);
+    pd->n_mask_words = (int64_t)lat3d::W * n;
+    pd->max_deg = 0;
+    for (int64_t i = 0; i < n; ++i)
+        pd->max_deg = std::max<int32_t>(pd->max_deg, (int32_t)(pd->row_ptr[(size_t)i + 1] - pd->row_ptr[(size_t)i]));
+    return true;
+}
+
 static double micromodulus_host(const pdmts_pd *pd, double xi2)
 {
     double r = std::sqrt(xi2);
@@ -667,13 +737,14 @@ static int upload_family_and_state(pdmts_pd *pd)
     cudaStream_t s = pd->ctx->stream;
     const int dim = pd->dim;
     const int64_t n = pd->n;
-    if (pd->layout == pdmts_pd::LAYOUT_LATTICE2D) {
-        PDMTS_TRY(pd->alloc(pd->d_mask, n));
-        PDMTS_TRY(pd->alloc(pd->d_exists, n));
+    if (pd->layout == pdmts_pd::LAYOUT_LATTICE2D || pd->layout == pdmts_pd::LAYOUT_LATTICE3D) {
+        const int64_t nw = pd->n_mask_words;
+        PDMTS_TRY(pd->alloc(pd->d_mask, nw));
+        PDMTS_TRY(pd->alloc(pd->d_exists, nw));
         PDMTS_TRY(pd->alloc(pd->d_V, n));
         PDMTS_TRY(pd->alloc(pd->d_out, (int64_t)dim * n));
-        PDMTS_TRY(upload(pd->d_mask, pd->mask_host.data(), n, s));
-        PDMTS_TRY(upload(pd->d_exists, pd->mask_host.data(), n, s));
+        PDMTS_TRY(upload(pd->d_mask, pd->mask_host.data(), nw, s));
+        PDMTS_TRY(upload(pd->d_exists, pd->mask_host.data(), nw, s));
         PDMTS_TRY(upload(pd->d_V, pd->V.data(), n, s));
         return alloc_f32_state(pd);
     }
@@ -908,6 +979,27 @@ pdmts::Lat2DArgs pdmts_pd::lattice_args(const pdmts::F32NodeArgs &N, uint32_t *m
     return A;
 }
 
+// Arguments of one 3D lattice substep: the per-|d|^2 constants are the ones
+// the sliced-ELL stencil table holds (same expressions, same rounding).
+pdmts::Lat3DArgs pdmts_pd::lattice3d_args(const pdmts::F32NodeArgs &N, uint32_t *mask) const
+{
+    Lat3DArgs A{};
+    A.nx = lat_dims[0];
+    A.ny = lat_dims[1];
+    A.nz = lat_dims[2];
+    A.mask = mask;
+    A.alpha = f_alpha.p;
+    for (int r2 = 1; r2 < 10; ++r2) {
+        const double xi2 = r2 * h * h;
+        A.coef[r2] = (float)(micromodulus_host(this, xi2) * h * h * V[0]);
+        A.thr[r2] = (float)(s0 * (2.0 + s0) * r2);
+        A.rd[r2] = (float)std::sqrt((double)r2);
+        A.r2[r2] = (float)r2;
+    }
+    A.nd = N;
+    return A;
+}
+
 // Lattice tile autotuner: times every tile configuration on scratch copies of
 // the FP32 state (the simulation state and counters are not touched) and keeps
 // the fastest. Runs once, before the first substep chain is captured.
@@ -1071,6 +1163,10 @@ int pdmts_pd::step(bool init, double theta, cudaStream_t s, bool link)
             Lat2DArgs A = lattice_args(N, mask, link);
             A.pdl = chain_follow ? 1 : 0;
             e = launch_pd_step_lattice2d(A, init, s);
+        } else if (layout == LAYOUT_LATTICE3D) {
+            Lat3DArgs A = lattice3d_args(N, mask);
+            A.pdl = chain_follow ? 1 : 0;
+            e = launch_pd_step_lattice3d(A, init, s);
         } else {
             F32StepArgs A{};
             A.fam = fam;
@@ -1173,7 +1269,7 @@ extern "C" int pd_create(pdmts_ctx *ctx, int dim, int64_t n, const double *X, co
         }
     }
     if (r == PDMTS_OK) {
-        if (precision == PDMTS_FP64 || force_sell || !try_lattice2d(pd))
+        if (precision == PDMTS_FP64 || force_sell || (!try_lattice2d(pd) && !try_lattice3d(pd)))
             build_sell(pd);
         r = upload_family_and_state(pd);
     }
@@ -1505,6 +1601,7 @@ extern "C" int pd_info(const pdmts_pd *pd, pdmts_pd_info *info)
     info->lattice_h = pd->on_lattice ? pd->h : 0.0;
     info->steps_done = pd->steps_done;
     info->device_bytes = pd->device_bytes;
+    info->lattice_nz = pd->layout == pdmts_pd::LAYOUT_LATTICE3D ? pd->lat_dims[2] : 0;
     return PDMTS_OK;
 }
 
@@ -1561,8 +1658,9 @@ extern "C" int pd_read_damage(pdmts_pd *pd, double *phi)
     cudaStream_t s = pd->ctx->stream;
     SellView fam{pd->d_tile_ptr.p, pd->d_tile_k.p, pd->d_mask_ptr.p, pd->d_col.p, pd->d_mask.p, pd->d_deg.p,
                  pd->n, pd->ntiles};
-    cudaError_t e = pd->layout == pdmts_pd::LAYOUT_LATTICE2D
-                        ? launch_damage_lattice(pd->n, pd->d_mask.p, pd->d_exists.p, 1, pd->d_out.p, s)
+    cudaError_t e = pd->layout != pdmts_pd::LAYOUT_SELL
+                        ? launch_damage_lattice(pd->n, pd->d_mask.p, pd->d_exists.p,
+                                                pd->layout == pdmts_pd::LAYOUT_LATTICE3D ? lat3d::W : 1, pd->d_out.p, s)
                         : launch_damage(fam, pd->precision == PDMTS_FP32_BULK, pd->d_V.p, pd->d_out.p, s);
     if (e != cudaSuccess)
         return fail(PDMTS_ERR_CUDA, "damage kernel failed: %s", cudaGetErrorString(e));

@@ -150,6 +150,25 @@ struct Lat2DArgs {
     F32NodeArgs nd;
 };
 
+// 3D lattice kernel: nodes form a full nx * ny * nz box numbered
+// i = x + nx (y + ny z); the family is the 122-offset stencil |d|^2 <= 9
+// (lattice units) clipped to the box, offsets in ascending neighbour-index
+// order, (dz, dy, dx) lexicographic. Bond bits: word w of node i at
+// mask[w * n + i], offset k at bit k % 32 of word k / 32. Per |d|^2 (0..9):
+// coef = c(|xi|) h^2 V, thr = s0 (2 + s0) |d|^2, rd = |d|, r2 = |d|^2.
+namespace lat3d {
+constexpr int NS = 122, W = 4;
+}
+struct Lat3DArgs {
+    int nx, ny, nz;
+    uint32_t *mask;
+    const float *alpha;         // n (null when no weights)
+    float coef[10], thr[10], rd[10], r2[10];
+    int pdl;                    // launch as a programmatic dependent of the previous substep kernel
+    F32NodeArgs nd;
+};
+cudaError_t launch_pd_step_lattice3d(const Lat3DArgs &A, bool init, cudaStream_t s);
+
 // Tensor maps of the lattice kernel's inputs for the tensor-copy staging
 // (tile configurations with `tma`): u halo, weight halo, bond words, v, a,
 // 1/m and the two planes of the loads wb and g. Built per launch from the

@@ -1517,9 +1517,10 @@ static int update_near_flags(pdmts_arl *A, int m)
                 near_node[(size_t)p] = 1;
         }
     std::vector<uint8_t> wflag((size_t)std::max<int64_t>(pd->n_mask_words, 1), 0);
-    if (pd->layout == pdmts_pd::LAYOUT_LATTICE2D) {
-        for (int64_t p = 0; p < npd; ++p)
-            wflag[(size_t)p] = near_node[(size_t)p];
+    if (pd->layout == pdmts_pd::LAYOUT_LATTICE2D || pd->layout == pdmts_pd::LAYOUT_LATTICE3D) {
+        for (int64_t w = 0; w < pd->n_mask_words / npd; ++w)
+            for (int64_t p = 0; p < npd; ++p)
+                wflag[(size_t)(w * npd + p)] = near_node[(size_t)p];
     } else {
         for (int64_t p = 0; p < npd; ++p) {
             const int64_t t = p / 32, lane = p % 32;

@@ -36,7 +36,7 @@ struct pdmts_pd {
     std::vector<int32_t> lk;  // dim * n integer lattice coordinates
 
     // family layout: sliced ELL (general) or the 2D lattice stencil
-    enum { LAYOUT_SELL = 0, LAYOUT_LATTICE2D = 1 };
+    enum { LAYOUT_SELL = 0, LAYOUT_LATTICE2D = 1, LAYOUT_LATTICE3D = 2 };
     int layout = LAYOUT_SELL;
     int32_t lat_dims[3] = {0, 0, 0};      // nodes per axis (lattice layout)
     std::vector<int8_t> slot_of_csr;      // lattice layout: stencil slot of each CSR bond
@@ -128,6 +128,7 @@ struct pdmts_pd {
     int upload_weights_and_loads();  // (re)build mass, wb, g device arrays
     int step(bool init, double theta, cudaStream_t s, bool link = false);  // one substep
     pdmts::Lat2DArgs lattice_args(const pdmts::F32NodeArgs &N, uint32_t *mask, bool link) const;
+    pdmts::Lat3DArgs lattice3d_args(const pdmts::F32NodeArgs &N, uint32_t *mask) const;
     pdmts::F32NodeArgs f32_node_args(bool init, double theta, bool link) const;
     void substep_done(bool init, bool link);  // parity and counters after an enqueued substep
     int tune_lattice(cudaStream_t s);        // pick the lattice tile configuration (once)

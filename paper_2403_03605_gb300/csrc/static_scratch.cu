@@ -69,8 +69,9 @@ extern "C" int pd_read_damage_static(pdmts_pd *pd, double *phi)
     // an earlier call needs clearing.
     SellView fam{pd->d_tile_ptr.p, pd->d_tile_k.p, pd->d_mask_ptr.p, pd->d_col.p, pd->d_mask.p, pd->d_deg.p,
                  pd->n, pd->ntiles};
-    cudaError_t e = pd->layout == pdmts_pd::LAYOUT_LATTICE2D
-                        ? launch_damage_lattice(pd->n, pd->d_mask.p, pd->d_exists.p, 1, scratch, s)
+    cudaError_t e = pd->layout != pdmts_pd::LAYOUT_SELL
+                        ? launch_damage_lattice(pd->n, pd->d_mask.p, pd->d_exists.p,
+                                                pd->layout == pdmts_pd::LAYOUT_LATTICE3D ? lat3d::W : 1, scratch, s)
                         : launch_damage(fam, pd->precision == PDMTS_FP32_BULK, pd->d_V.p, scratch, s);
     if (e != cudaSuccess)
         return fail(PDMTS_ERR_CUDA, "pd_read_damage_static: damage kernel failed: %s", cudaGetErrorString(e));

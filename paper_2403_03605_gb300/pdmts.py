@@ -38,7 +38,8 @@ class PDInfo(C.Structure):
     _fields_ = [("dim", C.c_int32), ("precision", C.c_int32), ("n", C.c_int64), ("n_bonds", C.c_int64),
                 ("n_slots", C.c_int64), ("max_degree", C.c_int32), ("on_lattice", C.c_int32),
                 ("layout", C.c_int32), ("lattice_nx", C.c_int32), ("lattice_ny", C.c_int32),
-                ("lattice_tile", C.c_int32), ("lattice_h", C.c_double), ("steps_done", C.c_int64), ("device_bytes", C.c_int64)]
+                ("lattice_tile", C.c_int32), ("lattice_h", C.c_double), ("steps_done", C.c_int64), ("device_bytes", C.c_int64),
+                ("lattice_nz", C.c_int32)]
 
 
 class Stats(C.Structure):

@@ -196,6 +196,42 @@ def test_config0_fp32_bulk_within_tolerance(fresh):
     assert mm <= FP32_MISMATCH, mm
 
 
+LATTICE3D_CASES = [
+    dict(name="breaking", pb=lambda: W.plate3d(15, 11, 8, 0.5e-3, cuts_mm=[(1, 2.75e-3, 0, 0.0, 3e-3)],
+                                               traction=40e6, nsteps=60)),
+    dict(name="weights_pmb", pb=lambda: W.plate3d(13, 10, 7, 0.5e-3, traction=40e6, nsteps=50), alpha=True,
+         force=True),
+    dict(name="exp_state", pb=lambda: W.plate3d(12, 9, 10, 0.5e-3, traction=20e6, nsteps=40), micro=True, state=True),
+]
+
+
+@pytest.mark.parametrize("case", LATTICE3D_CASES, ids=[c["name"] for c in LATTICE3D_CASES])
+def test_fp32_lattice3d_kernel_bit_identical_to_sliced_ell(fresh, case):
+    """The 3D lattice kernel (implicit 122-offset family, four bond words per
+    node) takes the sliced-ELL kernel's operations in the same order: the
+    same bits, breaks included."""
+    pb = case["pb"]()
+    rng = np.random.default_rng(23)
+    alpha = rng.uniform(0.0, 0.8, pb.n) if case.get("alpha") else None
+    force = P.PDMTS_FORCE_PMB if case.get("force") else P.PDMTS_FORCE_LINEAR
+    micro, l, c = P.PDMTS_MICRO_POWER, 0.0, None
+    if case.get("micro"):
+        micro, l, c = P.PDMTS_MICRO_EXP, pb.delta / 10.0, pb.c / pb.delta ** 3 * 500.0
+    u0 = rng.standard_normal((3, pb.n)) * pb.s0 * pb.lat.dx * 0.3 if case.get("state") else None
+    runs = []
+    for prec in (P.PDMTS_FP32_BULK, P.PDMTS_FP32_BULK_SELL):
+        g = GpuRun(fresh(), pb, prec, alpha=alpha, force=force, micro=micro, l=l, c=c, u0=u0)
+        runs.append((P.pd_info(g.pd)["layout"], g.run(pb.nsteps)))
+    (la, a), (ls, b) = runs
+    assert la == 2 and ls == 0
+    assert np.array_equal(a.u(), b.u()) and np.array_equal(a.v(), b.v())
+    assert np.array_equal(a.mu(), b.mu())
+    # damage from bond counts (lattice) or volume sums (sliced ELL, uniform V): equal up to FP64 rounding
+    np.testing.assert_allclose(a.damage(), b.damage(), rtol=0, atol=1e-14)
+    if case["name"] == "breaking":
+        assert (a.mu() == 0).sum() > 0
+
+
 @pytest.mark.parametrize("dim", [2, 3])
 def test_fp32_bulk_elastic_accuracy(fresh, dim):
     """Without breaking, FP32-bulk tracks the FP64 oracle closely (random initial state)."""
