@@ -493,7 +493,7 @@ def kernel_version():
     reported while the kernel it was measured on is unchanged."""
     import hashlib
     h = hashlib.sha256()
-    for name in ("lattice2d.cuh", "f32_device.cuh"):
+    for name in ("lattice2d.cuh", "f32_device.cuh", "lattice2d_tma.cu", "lattice3d.cu"):
         with open(os.path.join(ROOT, "paper_2403_03605_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]

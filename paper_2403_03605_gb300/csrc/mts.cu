@@ -385,26 +385,67 @@ __global__ void k_fe_residual(const int64_t ndof, const int W, const int32_t *__
         d[i] = inv_theta * Minv[i] * ri;
 }
 
-// One Chebyshev iteration for K_eff x = b preconditioned by the lumped mass,
-// on nrhs column-major vectors: x += d; r -= K_eff d; d' = c1 d + c2 M^-1 r.
-__global__ void k_cheb_iter(const int64_t ndof, const int nrhs, const int W, const int32_t *__restrict__ col,
-                            const double *__restrict__ val, const double *__restrict__ Minv, double *__restrict__ x,
-                            double *__restrict__ r, const double *__restrict__ d, double *__restrict__ dn,
-                            const double c1, const double c2)
+// Rows of wide ELL matrices (Hex8: 81 entries) with G threads per row: lane
+// `sub` of a row sums entries sub, sub + G, ...; the partial sums meet in a
+// butterfly, whose pairwise sums are commutative, so every lane of the group
+// holds the same bits. Used when the rows of a node do not share one column
+// list (3D), where one thread per row leaves the SMs waiting on a chain of 81
+// dependent FP64 products.
+constexpr int kRowGroup = 8;
+__device__ __forceinline__ double row_dot_group(const int64_t ndof, const int64_t i, const int W, const int sub,
+                                                const int32_t *__restrict__ col, const double *__restrict__ val,
+                                                const double *__restrict__ x, const bool act)
+{
+    double s = 0.0;
+    if (act)
+        for (int e = sub; e < W; e += kRowGroup)
+            s += val[e * ndof + i] * x[col[e * ndof + i]];
+#pragma unroll
+    for (int o = kRowGroup / 2; o > 0; o >>= 1)
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
+// r = b - A x (and d = M^-1 r / theta) with kRowGroup threads per row.
+__global__ void k_fe_residual_group(const int64_t ndof, const int W, const int32_t *__restrict__ col,
+                                    const double *__restrict__ val, const double *__restrict__ x,
+                                    const double *__restrict__ b, double *__restrict__ r,
+                                    const double *__restrict__ Minv, const double inv_theta, double *__restrict__ d)
 {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= ndof * nrhs)
+    const int64_t i = t / kRowGroup;
+    const int sub = (int)(t % kRowGroup);
+    const bool act = i < ndof;
+    const double ax = row_dot_group(ndof, act ? i : 0, W, sub, col, val, x, act);
+    if (!act || sub != 0)
         return;
-    const int64_t c = t / ndof, i = t - c * ndof;
-    const double *dc = d + c * ndof;
-    double ad = 0.0;
-    for (int e = 0; e < W; ++e)
-        ad += val[e * ndof + i] * dc[col[e * ndof + i]];
-    x[t] += d[t];
-    const double rn = r[t] - ad;
-    r[t] = rn;
+    const double ri = (b ? b[i] : 0.0) - ax;
+    r[i] = ri;
+    if (d)
+        d[i] = inv_theta * Minv[i] * ri;
+}
+
+// One Chebyshev iteration for K_eff x = b preconditioned by the lumped mass,
+// on nrhs column-major vectors (x += d; r -= K_eff d; d' = c1 d + c2 M^-1 r),
+// with kRowGroup threads per row.
+__global__ void k_cheb_iter_group(const int64_t ndof, const int nrhs, const int W, const int32_t *__restrict__ col,
+                                  const double *__restrict__ val, const double *__restrict__ Minv,
+                                  double *__restrict__ x, double *__restrict__ r, const double *__restrict__ d,
+                                  double *__restrict__ dn, const double c1, const double c2)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t row = t / kRowGroup;
+    const int sub = (int)(t % kRowGroup);
+    const bool act = row < ndof * nrhs;
+    const int64_t c = act ? row / ndof : 0, i = act ? row - c * ndof : 0;
+    const double ad = row_dot_group(ndof, i, W, sub, col, val, d + c * ndof, act);
+    if (!act || sub != 0)
+        return;
+    x[row] += d[row];
+    const double rn = r[row] - ad;
+    r[row] = rn;
     if (dn)
-        dn[t] = c1 * d[t] + c2 * Minv[i] * rn;
+        dn[row] = c1 * d[row] + c2 * Minv[i] * rn;
 }
 
 // Newmark corrector: u = u~ + beta dt^2 a, v = v~ + gamma dt a.
@@ -1069,9 +1110,14 @@ static int fe_cheb_solve(pdmts_fem *fe, int nrhs, double *x, const double *b, do
     const int64_t ndof = fe->ndof();
     const int64_t tot = ndof * nrhs;
     for (int c = 0; c < nrhs; ++c) {
-        k_fe_residual<<<blocks(ndof), 256, 0, s>>>(ndof, fe->W, fe->d_col.p, fe->d_Keff.p, x + c * ndof,
-                                                  b + c * ndof, r + c * ndof, fe->d_Minv.p, 1.0 / fe->cheb_theta,
-                                                  d0 + c * ndof);
+        if (fe->paired_rows)
+            k_fe_residual<<<blocks(ndof), 256, 0, s>>>(ndof, fe->W, fe->d_col.p, fe->d_Keff.p, x + c * ndof,
+                                                      b + c * ndof, r + c * ndof, fe->d_Minv.p, 1.0 / fe->cheb_theta,
+                                                      d0 + c * ndof);
+        else
+            k_fe_residual_group<<<blocks(ndof * kRowGroup), 256, 0, s>>>(
+                ndof, fe->W, fe->d_col.p, fe->d_Keff.p, x + c * ndof, b + c * ndof, r + c * ndof, fe->d_Minv.p,
+                1.0 / fe->cheb_theta, d0 + c * ndof);
         ++*launches;
     }
     double *d = d0, *dn = d1;
@@ -1083,9 +1129,9 @@ static int fe_cheb_solve(pdmts_fem *fe, int nrhs, double *x, const double *b, do
                                                                   fe->d_Minv.p, x, r, d, last ? nullptr : dn,
                                                                   fe->cheb_c1[(size_t)k], fe->cheb_c2[(size_t)k]);
         else
-            k_cheb_iter<<<blocks(tot), 256, 0, s>>>(ndof, nrhs, fe->W, fe->d_col.p, fe->d_Keff.p, fe->d_Minv.p, x, r,
-                                                    d, last ? nullptr : dn, fe->cheb_c1[(size_t)k],
-                                                    fe->cheb_c2[(size_t)k]);
+            k_cheb_iter_group<<<blocks(tot * kRowGroup), 256, 0, s>>>(
+                ndof, nrhs, fe->W, fe->d_col.p, fe->d_Keff.p, fe->d_Minv.p, x, r, d, last ? nullptr : dn,
+                fe->cheb_c1[(size_t)k], fe->cheb_c2[(size_t)k]);
         ++*launches;
         std::swap(d, dn);
     }
@@ -1099,8 +1145,12 @@ static int fe_free_enqueue(pdmts_fem *fe, double dt, double beta, double gamma, 
     const int64_t ndof = fe->ndof();
     k_fe_predict<<<blocks(ndof), 256, 0, s>>>(ndof, fe->d_u.p, fe->d_v.p, fe->d_a.p, dt, beta, gamma, fe->d_ut.p,
                                               fe->d_vt.p);
-    k_fe_residual<<<blocks(ndof), 256, 0, s>>>(ndof, fe->W, fe->d_col.p, fe->d_K.p, fe->d_ut.p, fe->d_P.p, fe->d_b.p,
-                                               nullptr, 0.0, nullptr);
+    if (fe->paired_rows)
+        k_fe_residual<<<blocks(ndof), 256, 0, s>>>(ndof, fe->W, fe->d_col.p, fe->d_K.p, fe->d_ut.p, fe->d_P.p,
+                                                   fe->d_b.p, nullptr, 0.0, nullptr);
+    else
+        k_fe_residual_group<<<blocks(ndof * kRowGroup), 256, 0, s>>>(ndof, fe->W, fe->d_col.p, fe->d_K.p, fe->d_ut.p,
+                                                                     fe->d_P.p, fe->d_b.p, nullptr, 0.0, nullptr);
     *launches += 2;
     // warm start from the previous acceleration (kept in d_a)
     PDMTS_TRY(fe_cheb_solve(fe, 1, fe->d_a.p, fe->d_b.p, fe->d_r.p, fe->d_d[0].p, fe->d_d[1].p, s, launches));
