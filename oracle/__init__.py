@@ -214,3 +214,30 @@ def kinetic_energy(pd: PD, v, alpha=None) -> float:
     alpha = _f64(alpha)
     p = pd.params()
     return lib().orc_kinetic_energy(C.byref(p), _ptr(pd.V), _ptr(alpha), _ptr(v))
+
+
+def crack_tip(X, phi, normal: int, level: float, along: int, band: float, threshold: float = 0.35):
+    """Extreme crack-tip positions of a damage field (damage as in Eq. 5).
+
+    The paper does not define a crack tip; the reading taken here: among the
+    nodes whose damage is at least `threshold` and whose distance to the crack
+    plane x[normal] = level is at most `band`, the smallest and the largest
+    coordinate along axis `along`. Returns (lo, hi), or (nan, nan) when no node
+    qualifies. The default threshold sits below 11/28 (2D) and 47/122 (3D),
+    the damage of a node next to a fully separated lattice plane at
+    delta = 3.015 dx, and above 6/28, that of the second row. A plain loop
+    over the nodes: for the small cases of the tests.
+    """
+    X = np.asarray(X, dtype=np.float64)
+    phi = np.asarray(phi, dtype=np.float64)
+    lo, hi = float("inf"), float("-inf")
+    for i in range(X.shape[1]):
+        if phi[i] >= threshold and abs(X[normal, i] - level) <= band:
+            x = float(X[along, i])
+            if x < lo:
+                lo = x
+            if x > hi:
+                hi = x
+    if hi == float("-inf"):
+        return float("nan"), float("nan")
+    return lo, hi
