@@ -202,13 +202,13 @@ def setup_ours(P, ctx, workload):
     return pd, fe, arl, P.pd_info(pd), cp.pd, cp.m, cp
 
 
-def make_coupled(P, ctx, cp):
-    """Bind one coupled plate (FP32-bulk PD, Q4 FE, Arlequin bands) in ctx."""
+def make_coupled(P, ctx, cp, precision=None):
+    """Bind one coupled plate (FP32-bulk PD unless stated, Q4/Hex8 FE, Arlequin bands) in ctx."""
     pb = cp.pd
     mat = pb.mat
     pd = P.pd_create(ctx, pb.lat.X, horizon=pb.delta, c=pb.c, s0=pb.s0, rho=mat.rho, vol_uniform=pb.vol,
                      micro_kind=pb.extra.get("micro", P.PDMTS_MICRO_POWER), l=pb.extra.get("l", 0.0),
-                     precision=P.PDMTS_FP32_BULK)
+                     precision=P.PDMTS_FP32_BULK if precision is None else precision)
     P.pd_set_precrack(pd, [c.as_array() for c in pb.cuts])
     fe = P.fem_create(ctx, cp.fe.X, cp.fe.conn, E=mat.E, nu=mat.nu, rho=mat.rho, thickness=mat.thickness)
     P.fem_set_traction(fe, cp.faces, cp.face_traction)
@@ -447,6 +447,12 @@ def run_ours(args, rank, world, local_rank):
     e2e_value = e2e_units * world / e2e_s
     assert np.isfinite(u_host.numpy()).all()
 
+    # ---- stated error of FP32-bulk and the plain FP64 form's rate ---------
+    accuracy, fp64_form = (None, None)
+    if args.accuracy_steps != 0:
+        accuracy, fp64_form = run_accuracy(P, dev, stream, args.workload, args.accuracy_steps,
+                                           args.accuracy_budget_s)
+
     # ---- CPU baseline: the FP64 oracle on a bounded sample ----------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload != "coupled3d":
@@ -461,6 +467,7 @@ def run_ours(args, rank, world, local_rank):
                "directed_bonds": info["n_bonds"], "m": m,
                "family_layout": {0: "sliced ELL", 1: "lattice bond words", 2: "3D lattice bond words"}[info["layout"]],
                "lattice_tile": tile,
+               "link_tile": P.pd_info(pd)["link_tile"] if coupled else None,
                "graph": "one captured graph per PD substep chain",
                "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                "l2": "flushed between timed steps (256 MB write)"}
@@ -479,6 +486,8 @@ def run_ours(args, rank, world, local_rank):
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind, "kernel": kname,
                          "algorithmic_bytes_per_launch": abytes, "launch_us": launch_ms * 1e3},
             "cpu_baseline": cpu,
+            "accuracy": accuracy,
+            "fp64_form": fp64_form,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(b_host.numel() * 8),
                     "d2h_bytes_per_step": int(u_host.numel() * 8 + nfe_dof * 8)},
             "gpu_launches": int(launches),
@@ -486,6 +495,89 @@ def run_ours(args, rank, world, local_rank):
         }
         print(json.dumps(line), flush=True)
     P.pdmts_ctx_destroy(ctx)
+
+
+# crack plane (normal axis, level, along axis) and the half-width of the band
+# searched for the crack tip: up to the inner edges of the overlap bands
+# (coupled plates) or a quarter of the strip's height (pure-PD strip)
+ACCURACY_CRACK = {"coupled": ((1, 0.020, 0), 8e-3), "coupled3d": ((1, 0.020, 0), 6e-3),
+                  "pd": ((1, 0.010, 0), 5e-3)}
+
+
+def run_accuracy(P, dev, stream, workload, n_steps, budget_s):
+    """The stated error of the FP32-bulk path and the rate of the plain FP64
+    form: the same workload advanced from rest by a fresh FP64 context and a
+    fresh FP32-bulk context (the FP64 path is bit-identical to the FP64 oracle
+    in the parity tests), coarse step by coarse step (pure PD: chains of m
+    substeps). The FP64 run stops after n_steps or once it has used budget_s
+    seconds of wall time, and the FP32-bulk run takes the same number of
+    steps. Reports displacement rel-L2, bond-status mismatch and crack-tip
+    error of FP32-bulk against FP64 at the end, and both forms' bond
+    updates/s over steps 2.. (device time, CUDA events on the caller's
+    stream; the first step also builds the interface operator)."""
+    import torch
+    from paper_2403_03605_gb300 import diagnostics as D
+    from paper_2403_03605_gb300 import workloads as W
+    coupled = workload in ("coupled", "coupled3d")
+    cp = (W.config3() if workload == "coupled3d" else W.config2()) if coupled else None
+    if n_steps < 0:
+        n_steps = {"coupled": 60, "coupled3d": 30, "pd": 100}[workload]
+    n_steps = max(n_steps, 2)
+    res = {}
+    for name, prec in (("fp64", P.PDMTS_FP64), ("fp32_bulk", P.PDMTS_FP32_BULK)):
+        ctx = P.pdmts_ctx_create(dev.index, stream.cuda_stream)
+        try:
+            if coupled:
+                pd, fe, arl = make_coupled(P, ctx, cp, precision=prec)
+                pb = cp.pd
+            else:
+                pb = make_problem()
+                pd = P.pd_create(ctx, pb.lat.X, horizon=pb.delta, c=pb.c, s0=pb.s0, rho=pb.mat.rho,
+                                 vol_uniform=pb.vol, precision=prec)
+                P.pd_set_precrack(pd, [c.as_array() for c in pb.cuts])
+                P.pd_set_body_force(pd, pb.b)
+                P.mts_set_time(ctx, pb.dt, WORKLOAD["m"])
+            t0 = time.perf_counter()
+            P.mts_advance(ctx, 1)  # the first coarse step also builds the interface operator
+            torch.cuda.synchronize(dev)
+            st0 = P.pdmts_get_stats(ctx)
+            ms, done = 0.0, 1
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            while done < n_steps:
+                e0.record(stream)
+                P.mts_advance(ctx, 1)
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                ms += e0.elapsed_time(e1)
+                done += 1
+                if name == "fp64" and time.perf_counter() - t0 > budget_s:
+                    n_steps = done  # the FP32-bulk run takes as many steps
+            st1 = P.pdmts_get_stats(ctx)
+            out = {"u": P.pd_read_displacement(pd), "mu": P.pd_read_bond_status(pd)[0],
+                   "phi": P.pd_read_damage(pd), "ms": ms, "steps": done,
+                   "value": (st1["bond_updates"] - st0["bond_updates"]) / (ms * 1e-3)}
+            if coupled:
+                out["uf"] = P.fem_read_displacement(fe, pb.dim * cp.fe.n)
+                out["rebuilds"] = P.arlequin_info(arl)["rebuilds"]
+            res[name] = out
+        finally:
+            P.pdmts_ctx_destroy(ctx)
+    crack, band = ACCURACY_CRACK[workload]
+    acc = D.compare(res["fp32_bulk"], res["fp64"], pb.lat.X, crack, band)
+    acc = {k: (round(v, 12) if isinstance(v, float) else v) for k, v in acc.items()}
+    steps = res["fp64"]["steps"]
+    acc.update({"vs": "FP64 GPU path (bit-identical to the FP64 oracle in the parity tests)",
+                "coarse_steps" if coupled else "chains": steps,
+                "physical_time_s": steps * (cp.m * cp.dt_pd if coupled else WORKLOAD["m"] * WORKLOAD["dt"]),
+                "crack_tip_rule": f"extreme x of nodes with damage >= 0.35 within {band * 1e3:g} mm of the crack plane",
+                "tolerance": {"u_pd_rel_l2": 1e-4, "broken_mismatch_frac": 1e-3}})
+    if coupled:
+        acc["interface_builds"] = {k: res[k]["rebuilds"] for k in res}
+    fp64 = {"value": res["fp64"]["value"], "unit": UNIT, "ms_per_step": res["fp64"]["ms"] / (steps - 1),
+            "fp32_bulk_value_same_steps": res["fp32_bulk"]["value"],
+            "fp32_bulk_over_fp64": res["fp32_bulk"]["value"] / res["fp64"]["value"],
+            "steps_timed": steps - 1}
+    return acc, fp64
 
 
 def kernel_version():
@@ -508,6 +600,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=["coupled", "pd", "batch", "coupled3d"], default="coupled")
     ap.add_argument("--batch-members", type=int, default=64, help="members of the batched workload")
+    ap.add_argument("--accuracy-steps", type=int, default=-1,
+                    help="coarse steps (pure PD: chains) of the FP32-bulk vs FP64 accuracy run; "
+                         "-1: 60 (coupled), 30 (coupled3d), 100 (pd); 0: skip")
+    ap.add_argument("--accuracy-budget-s", type=float, default=60.0,
+                    help="wall-time budget of the FP64 accuracy run (it stops early past it)")
     ap.add_argument("--lattice-tile", type=int, default=-1,
                     help="fix the lattice kernel tile configuration (default: autotune)")
     args = ap.parse_args()

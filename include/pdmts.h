@@ -140,10 +140,12 @@ int pd_set_force_law(pdmts_pd *pd, int kind);
 
 /* Tile configuration of the FP32-bulk 2D lattice kernel (a performance
  * setting; results do not depend on it: every configuration evaluates each
- * node's bonds in the same order). 0 .. PDMTS_LATTICE_TILES - 1 fixes one;
- * PDMTS_LATTICE_TILE_AUTO (the default) times every configuration once, on
- * scratch copies of the state, before the next substep chain and keeps the
- * fastest. Configurations: 0: one CTA per 32 x 16 tile, strips of 2 nodes
+ * node's bonds in the same order). 0 .. PDMTS_LATTICE_TILES - 1 fixes one
+ * for every chain; PDMTS_LATTICE_TILE_AUTO (the default) times every
+ * configuration once, on scratch copies of the state, before the next
+ * substep chain and keeps the fastest, and for a coupled subdomain also
+ * times one chain of the link run's growing windows (a few hundred tiles per
+ * launch) and keeps the fastest configuration for link chains separately. Configurations: 0: one CTA per 32 x 16 tile, strips of 2 nodes
  * per thread, registers for 3 CTAs per SM; 1: the same for 4 CTAs per SM;
  * 2: a persistent grid that stages each CTA's next tile while it computes
  * the current one, 2 nodes per thread; 3: the same with 1 node per thread;
@@ -178,6 +180,8 @@ typedef struct {
     int64_t steps_done;    /* PD substeps advanced since creation          */
     int64_t device_bytes;  /* device memory held by this subdomain         */
     int32_t lattice_nz;    /* 3D lattice layout: nodes along z (else 0)    */
+    int32_t link_tile;     /* tile configuration of the link chains (the
+                              coupled subdomain's link runs, Eq. 48b)      */
 } pdmts_pd_info;
 int pd_info(const pdmts_pd *pd, pdmts_pd_info *info);
 

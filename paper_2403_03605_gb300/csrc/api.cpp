@@ -968,7 +968,7 @@ pdmts::Lat2DArgs pdmts_pd::lattice_args(const pdmts::F32NodeArgs &N, uint32_t *m
         A.cpmb[r2] = (float)(coef * r2 * r2);
     }
     A.qthr = (float)(s0 * (2.0 + s0));
-    A.tile = lattice_tile >= 0 ? lattice_tile : 0;
+    A.tile = link && link_tile >= 0 ? link_tile : lattice_tile >= 0 ? lattice_tile : 0;
     A.num_sms = ctx->num_sms;
     A.nd = N;
     const bool grow = link && chain_k >= 0 && chain_k < (int)link_step_win.size();
@@ -1073,10 +1073,48 @@ int pdmts_pd::tune_lattice(cudaStream_t s)
             best_ms = ms;
         }
     }
+    // link chains (coupled subdomains): the launches of a link run cover only
+    // the growing windows around the overlap bands, a few hundred tiles each,
+    // where a CTA's latency rather than the work decides; time every
+    // configuration over one chain of those windows (second of two passes)
+    int best_link = -1;
+    float best_link_ms = 0.f;
+    const int nwin = (int)link_step_win.size();
+    for (int t = 0; t < kLatTiles && nwin > 0 && e == cudaSuccess; ++t) {
+        Lat2DArgs A = lattice_args(N, sm.p, false);
+        A.tile = t;
+        int c = 0;
+        for (int pass = 0; pass < 2 && e == cudaSuccess; ++pass) {
+            if (pass == 1)
+                e = cudaEventRecord(e0, s);
+            for (int k = 0; k < nwin && e == cudaSuccess; ++k) {
+                for (int w = 0; w < 2; ++w) {
+                    A.win_lo[w] = link_step_win[(size_t)k][2 * w];
+                    A.win_n[w] = link_step_win[(size_t)k][2 * w + 1];
+                }
+                A.nd.u4_in = su[c].p;
+                A.nd.u4_out = su[1 - c].p;
+                e = launch_pd_step_lattice2d(A, false, s);
+                c = 1 - c;
+            }
+        }
+        if (e == cudaSuccess)
+            e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess)
+            e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess)
+            e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && (best_link < 0 || ms < best_link_ms)) {
+            best_link = t;
+            best_link_ms = ms;
+        }
+    }
     release_all();
     if (e != cudaSuccess)
         return fail(PDMTS_ERR_CUDA, "lattice autotune: %s", cudaGetErrorString(e));
     lattice_tile = best;
+    link_tile = best_link;
     pd_invalidate_graphs(this);
     return PDMTS_OK;
 }
@@ -1578,6 +1616,7 @@ extern "C" int pd_set_lattice_tile(pdmts_pd *pd, int tile)
         return fail(PDMTS_ERR_ARG, "pd_set_lattice_tile: tile %d outside [0, %d) and not AUTO", tile, kLatTiles);
     static_assert(kLatTiles == PDMTS_LATTICE_TILES, "tile table and ABI disagree");
     pd->lattice_tile = tile;
+    pd->link_tile = -1;  // a fixed configuration serves the link chains too; AUTO tunes both
     pd_invalidate_graphs(pd);
     return PDMTS_OK;
 }
@@ -1602,6 +1641,7 @@ extern "C" int pd_info(const pdmts_pd *pd, pdmts_pd_info *info)
     info->steps_done = pd->steps_done;
     info->device_bytes = pd->device_bytes;
     info->lattice_nz = pd->layout == pdmts_pd::LAYOUT_LATTICE3D ? pd->lat_dims[2] : 0;
+    info->link_tile = pd->link_tile >= 0 ? pd->link_tile : pd->lattice_tile;
     return PDMTS_OK;
 }
 

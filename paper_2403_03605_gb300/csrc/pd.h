@@ -88,6 +88,7 @@ struct pdmts_pd {
     // to 32 rows, a multiple of every lattice tile height); {0, n} without windows
     int64_t link_seg_lo[2] = {0, 0}, link_seg_n[2] = {0, 0};
     int lattice_tile = -1;                                // lattice tile configuration (-1: tune)
+    int link_tile = -1;   // configuration of link chains, tuned on their windows (-1: lattice_tile)
     int64_t link_bonds = -1;  // directed bonds evaluated per link substep (-1: all)
     // growing windows of the link chain: substep k (0-based) of a link run
     // evaluates step_win[k] = {lo0, n0, lo1, n1} (TY-row units), holding every

@@ -39,7 +39,7 @@ class PDInfo(C.Structure):
                 ("n_slots", C.c_int64), ("max_degree", C.c_int32), ("on_lattice", C.c_int32),
                 ("layout", C.c_int32), ("lattice_nx", C.c_int32), ("lattice_ny", C.c_int32),
                 ("lattice_tile", C.c_int32), ("lattice_h", C.c_double), ("steps_done", C.c_int64), ("device_bytes", C.c_int64),
-                ("lattice_nz", C.c_int32)]
+                ("lattice_nz", C.c_int32), ("link_tile", C.c_int32)]
 
 
 class Stats(C.Structure):

@@ -101,14 +101,21 @@ def test_config1_full_size_properties(fresh, prec):
 def test_coupled_lattice_tiles_bit_identical(fresh):
     """Coupled FP32-bulk steps on the 100 x 40 mm plate with every lattice tile
     configuration (the link substeps run on windows of tile rows converted per
-    tile height): identical PD, FE and multiplier states."""
+    tile height), and with the tuned pair of configurations (free chains, link
+    chains): identical PD, FE and multiplier states."""
     cp = W.config1()
     ref = None
-    for tile in range(P.PDMTS_LATTICE_TILES):
+    for tile in [*range(P.PDMTS_LATTICE_TILES), P.PDMTS_LATTICE_TILE_AUTO]:
         g = GpuMTS(fresh(), cp, P.PDMTS_FP32_BULK)
         P.pd_set_lattice_tile(g.pd, tile)
         g.run(4)
-        assert P.pd_info(g.pd)["lattice_tile"] == tile
+        info = P.pd_info(g.pd)
+        if tile >= 0:
+            assert info["lattice_tile"] == tile and info["link_tile"] == tile
+        else:  # tuned separately for the free and the link chains
+            assert 0 <= info["lattice_tile"] < P.PDMTS_LATTICE_TILES
+            assert 0 <= info["link_tile"] < P.PDMTS_LATTICE_TILES
+            print("config1 tuned tiles: free", info["lattice_tile"], "link", info["link_tile"])
         got = (g.u(), g.v(), g.uf(), g.lam(), g.mu())
         if ref is None:
             ref = got

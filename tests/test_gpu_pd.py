@@ -11,6 +11,7 @@ import pytest
 
 import oracle
 from gpu_common import GpuRun, OracleRun, rel_l2
+from paper_2403_03605_gb300 import diagnostics as D
 from paper_2403_03605_gb300 import pdmts as P
 from paper_2403_03605_gb300 import workloads as W
 
@@ -19,6 +20,9 @@ pytestmark = pytest.mark.gpu
 FP64_TOL = 1e-10
 FP32_TOL = 1e-4
 FP32_MISMATCH = 1e-3
+# crack plane of config 0 (normal y, level 25 mm, along x) and the band searched
+# for the crack tip (5 mm: the loading layers at the faces stay outside)
+CONFIG0_CRACK = (1, 0.025, 0, 5e-3)
 
 
 @pytest.fixture(scope="module")
@@ -75,6 +79,12 @@ def test_config0_fp64_bit_identical(fresh):
     assert o.broken > 1000  # the run breaks bonds beyond the pre-crack
     g = GpuRun(fresh(), pb, P.PDMTS_FP64).run(pb.nsteps)
     _assert_fp64_identical(g, o)
+    # crack tips of the two runs (oracle rule on the oracle's damage, the
+    # library's host-side rule on the GPU damage): identical
+    tip_o = oracle.crack_tip(pb.lat.X, o.damage(), *CONFIG0_CRACK)
+    tip_g = D.crack_tip(pb.lat.X, g.damage(), *CONFIG0_CRACK)
+    print(f"config0 crack tips: oracle {tip_o}, GPU FP64 {tip_g}")
+    assert tip_o == tip_g and not np.isnan(tip_o[0])
 
 
 VARIANTS = [
@@ -191,9 +201,12 @@ def test_config0_fp32_bulk_within_tolerance(fresh):
     g32 = GpuRun(fresh(), pb, P.PDMTS_FP32_BULK).run(pb.nsteps)
     err = rel_l2(g32.u(), g64.u())
     mm = _mismatch(g32.mu(), g64.mu())
-    print(f"config0 fp32-bulk vs fp64: rel-L2 u {err:.2e}, broken mismatch {mm:.2e}")
+    tip_err = D.tip_error(D.crack_tip(pb.lat.X, g32.damage(), *CONFIG0_CRACK),
+                          D.crack_tip(pb.lat.X, g64.damage(), *CONFIG0_CRACK))
+    print(f"config0 fp32-bulk vs fp64: rel-L2 u {err:.2e}, broken mismatch {mm:.2e}, crack-tip error {tip_err:.2e} m")
     assert err <= FP32_TOL, err
     assert mm <= FP32_MISMATCH, mm
+    assert tip_err <= pb.delta, tip_err  # reported; within one horizon
 
 
 LATTICE3D_CASES = [
