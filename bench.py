@@ -541,6 +541,8 @@ def run_accuracy(P, dev, stream, workload, n_steps, budget_s):
             P.mts_advance(ctx, 1)  # the first coarse step also builds the interface operator
             torch.cuda.synchronize(dev)
             st0 = P.pdmts_get_stats(ctx)
+            P.pdmts_get_timing(ctx)
+            P.pdmts_set_timing(ctx, True)
             ms, done = 0.0, 1
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             while done < n_steps:
@@ -552,10 +554,13 @@ def run_accuracy(P, dev, stream, workload, n_steps, budget_s):
                 done += 1
                 if name == "fp64" and time.perf_counter() - t0 > budget_s:
                     n_steps = done  # the FP32-bulk run takes as many steps
+            P.pdmts_set_timing(ctx, False)
+            chain_ms, chain_sub = P.pdmts_get_timing(ctx)
             st1 = P.pdmts_get_stats(ctx)
+            units = st1["bond_updates"] - st0["bond_updates"]
             out = {"u": P.pd_read_displacement(pd), "mu": P.pd_read_bond_status(pd)[0],
-                   "phi": P.pd_read_damage(pd), "ms": ms, "steps": done,
-                   "value": (st1["bond_updates"] - st0["bond_updates"]) / (ms * 1e-3)}
+                   "phi": P.pd_read_damage(pd), "ms": ms, "steps": done, "value": units / (ms * 1e-3),
+                   "chain_ms": chain_ms, "chain_sub": chain_sub, "units": units}
             if coupled:
                 out["uf"] = P.fem_read_displacement(fe, pb.dim * cp.fe.n)
                 out["rebuilds"] = P.arlequin_info(arl)["rebuilds"]
@@ -573,10 +578,30 @@ def run_accuracy(P, dev, stream, workload, n_steps, budget_s):
                 "tolerance": {"u_pd_rel_l2": 1e-4, "broken_mismatch_frac": 1e-3}})
     if coupled:
         acc["interface_builds"] = {k: res[k]["rebuilds"] for k in res}
-    fp64 = {"value": res["fp64"]["value"], "unit": UNIT, "ms_per_step": res["fp64"]["ms"] / (steps - 1),
+    r64 = res["fp64"]
+    # the FP64 parity kernel evaluates each intact bond with 26 FP64 adds,
+    # multiplies and compares in 2D (30 with Arlequin weights; 3D: 37 and 41),
+    # each taking one FMA slot of the FP64 pipe: peak = the nominal 1.25
+    # TFLOP/s (152 SMs x 2 FP64 FMA per clock x 2.07 GHz x 2 flops) / 2
+    # the timed chains are the free chains (every substep evaluates every
+    # intact bond of the subdomain; link chains are not timed)
+    ops = {2: 26, 3: 37}[pb.dim] + (4 if coupled else 0)
+    chain_s = r64["chain_ms"] * 1e-3
+    intact = int(np.count_nonzero(r64["mu"]))
+    achieved = ops * intact * r64["chain_sub"] / chain_s / 1e9 if chain_s > 0 else None
+    peak = 1250.0 / 2
+    fp64 = {"value": r64["value"], "unit": UNIT, "ms_per_step": r64["ms"] / (steps - 1),
             "fp32_bulk_value_same_steps": res["fp32_bulk"]["value"],
-            "fp32_bulk_over_fp64": res["fp32_bulk"]["value"] / res["fp64"]["value"],
-            "steps_timed": steps - 1}
+            "fp32_bulk_over_fp64": res["fp32_bulk"]["value"] / r64["value"],
+            "steps_timed": steps - 1,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G FP64 ops/s",
+                         "frac": achieved / peak if achieved else None, "traffic": None,
+                         "peak_kind": "nominal FP64 rate 1.25 TFLOP/s (FMA = 2 flops) / 2: each non-fused op "
+                                      "takes one FMA slot",
+                         "kernel": f"k_pd_step_f64<{pb.dim}>", "ops_per_bond": ops,
+                         "launch_us": 1e3 * r64["chain_ms"] / max(r64["chain_sub"], 1),
+                         "time_basis": "free substep chains (CUDA events around each chain) x the bonds "
+                                       "intact at the end of the run"}}
     return acc, fp64
 
 
