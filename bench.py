@@ -470,7 +470,8 @@ def run_ours(args, rank, world, local_rank):
                "link_tile": P.pd_info(pd)["link_tile"] if coupled else None,
                "graph": "one captured graph per PD substep chain",
                "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-               "l2": "flushed between timed steps (256 MB write)"}
+               "l2": "flushed between timed steps (256 MB write)",
+               "l2_bytes": getattr(torch.cuda.get_device_properties(dev), "L2_cache_size", None)}
         if coupled:
             ai = P.arlequin_info(arl)
             cfg.update({"phase_us_per_step": {k: round(v * 1e3 / max(nph, 1), 1) for k, v in phases.items()}})

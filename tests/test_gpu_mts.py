@@ -4,6 +4,7 @@ import pytest
 
 from gpu_common import GpuMTS, rel_l2
 from oracle.mts import MTSOracle
+from paper_2403_03605_gb300 import diagnostics as D
 from paper_2403_03605_gb300 import pdmts as P
 from paper_2403_03605_gb300 import workloads as W
 
@@ -96,6 +97,39 @@ def test_config1_full_size_properties(fresh, prec):
     info = P.arlequin_info(g.arl)
     print("config1 coupling:", info)
     assert info["n_lambda"] == 2 * 606
+
+
+FULL_SIZE = [dict(name="config2_800k", cp=W.config2, steps=20, n_lambda=4020),
+             dict(name="config3_3d_205k", cp=W.config3, steps=6, n_lambda=5454)]
+
+
+@pytest.mark.parametrize("case", FULL_SIZE, ids=[c["name"] for c in FULL_SIZE])
+def test_full_size_coupled_fp32_bulk_against_fp64(fresh, case):
+    """The benchmark plates at full size, as bench.py runs them (FP32-bulk PD,
+    autotuned lattice tiles): after every coarse step the velocity constraint
+    holds, and at the end FP32-bulk agrees with the FP64 path (bit-identical
+    to the oracle on the parity cases) within the stated tolerances: PD and
+    FE displacement rel-L2 <= 1e-4, broken-bond mismatch <= 0.1 %, crack tip
+    within one horizon."""
+    cp = case["cp"]()
+    runs = {}
+    for prec in (P.PDMTS_FP64, P.PDMTS_FP32_BULK):
+        g = GpuMTS(fresh(), cp, prec)
+        for _ in range(case["steps"]):
+            g.run(1)
+            res = g.residual()
+            assert res <= (1e-11 if prec == P.PDMTS_FP64 else 1e-5), (prec, res)
+        assert P.arlequin_info(g.arl)["n_lambda"] == case["n_lambda"]
+        runs[prec] = dict(u=g.u(), uf=g.uf(), mu=g.mu(), phi=P.pd_read_damage(g.pd))
+    a, b = runs[P.PDMTS_FP32_BULK], runs[P.PDMTS_FP64]
+    assert np.isfinite(a["u"]).all() and np.isfinite(a["uf"]).all()
+    eu, ef = rel_l2(a["u"], b["u"]), rel_l2(a["uf"], b["uf"])
+    mm = float(np.count_nonzero(a["mu"] != b["mu"])) / len(b["mu"])
+    X = cp.pd.lat.X
+    tip = D.tip_error(D.crack_tip(X, a["phi"], 1, 0.020, 0, 6e-3), D.crack_tip(X, b["phi"], 1, 0.020, 0, 6e-3))
+    print(f"{case['name']}: rel-L2 u_pd {eu:.2e} u_fe {ef:.2e}, mismatch {mm:.2e}, crack-tip error {tip:.2e} m")
+    assert eu <= 1e-4 and ef <= 1e-4 and mm <= 1e-3
+    assert tip <= cp.pd.delta
 
 
 def test_coupled_lattice_tiles_bit_identical(fresh):
