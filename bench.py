@@ -16,7 +16,7 @@ body force on its faces), 20 substeps per step.
 
 Inputs are seeded synthetic data resident in HBM before the timed region; L2
 is flushed between timed steps. --impl reference times the FP64 CPU oracle
-(the reference of this build) on the host cores, on bounded samples of the
+(the FP64 reference implementation) on the host cores, on bounded samples of the
 same lattice. One JSON line is printed by rank 0.
 """
 from __future__ import annotations

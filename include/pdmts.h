@@ -40,7 +40,7 @@ extern "C" {
 #define PDMTS_ERR_TIMEOUT (-5)     /* a bounded device-side wait gave up                    */
 #define PDMTS_ERR_STATE (-6)       /* call out of order (e.g. advance before set-up)        */
 #define PDMTS_ERR_NOMEM (-7)       /* host or device allocation failed                      */
-#define PDMTS_ERR_UNSUPPORTED (-8) /* valid request this build does not implement            */
+#define PDMTS_ERR_UNSUPPORTED (-8) /* valid request this library does not implement          */
 
 /* ---- enumerations -------------------------------------------------------- */
 #define PDMTS_FP64 0      /* all PD arithmetic in IEEE FP64, fixed summation order, no FMA  */

@@ -15,7 +15,7 @@ Follows arXiv 2403.03605 Sec. 2.2-2.5 step by step:
     problem for lambda_m (Eq. 49), correction U = V + Y lambda_m and
     Algorithm 1's loop.
 
-Readings (each listed in the design doc):
+Readings of points the paper leaves open or garbles:
   * Signs are taken from Eq. 33: the FE equation carries +G_FE^T lambda, the PD
     equation -G_PD^T lambda, the constraint G_FE v_FE - G_PD v_PD = 0. Eq. 43-49
     are then derived from these (their printed signs disagree with Eq. 33).

@@ -20,7 +20,7 @@
  *   time        Newmark gamma = 1/2, beta = 0 (velocity Verlet)     (Eq. 38)
  * plus the Arlequin weighting of the PD energy by (1 - alpha)        (Eq. 17, Eq. 34)
  *
- * Readings of points the paper leaves open (each is listed in the design doc):
+ * Readings of points the paper leaves open or garbles:
  *  - The breaking test s >= s_crit is evaluated as |xi+eta|^2 >= (1+s0)^2 |xi|^2,
  *    which is the same inequality squared (both sides are non-negative).
  *    orc_stretch_literal() evaluates Eq. 3 literally so a test can check that

@@ -46,7 +46,7 @@ class OracleRun:
         return oracle.damage(self.pd, self.rp, self.col, self.mu)
 
 
-class GpuRun:
+class GpuPDRun:
     """The same PD problem advanced by libpdmts.so through the C ABI."""
 
     def __init__(self, ctx, pb: W.PDProblem, precision, *, micro=P.PDMTS_MICRO_POWER, l=0.0, c=None,

@@ -84,7 +84,7 @@ def _table1():
 
 
 def _paper(key):
-    """The printed error of the case matching this build's explicit PD
+    """The printed error of the case matching this library's explicit PD
     (beta_PD = 0) where Table 1 has one, else the beta_PD = 1/4 case."""
     rows = _table1()[key]
     explicit = [r for r in rows if r[1] == 0.0]

@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_common import GpuRun, OracleRun, rel_l2
+from gpu_common import GpuPDRun, OracleRun, rel_l2
 from paper_2403_03605_gb300 import diagnostics as D
 from paper_2403_03605_gb300 import pdmts as P
 from paper_2403_03605_gb300 import workloads as W
@@ -48,7 +48,7 @@ def fresh(ctx):
         P.pdmts_ctx_destroy(c)
 
 
-def _assert_fp64_identical(g: GpuRun, o: OracleRun):
+def _assert_fp64_identical(g: GpuPDRun, o: OracleRun):
     u, v, a = g.u(), g.v(), g.a()
     assert rel_l2(u, o.u) <= FP64_TOL
     assert rel_l2(v, o.v) <= FP64_TOL
@@ -62,7 +62,7 @@ def _assert_fp64_identical(g: GpuRun, o: OracleRun):
 def test_family_and_precrack_match_oracle(fresh):
     for pb in (W.config0(), W.plate3d(11, 9, 8, 0.5e-3, cuts_mm=[(1, 2.25e-3, 0, 0.0, 2.5e-3)])):
         ctx = fresh()
-        g = GpuRun(ctx, pb, P.PDMTS_FP64)
+        g = GpuPDRun(ctx, pb, P.PDMTS_FP64)
         o = OracleRun(pb)
         rp, col = P.pd_read_family(g.pd)
         assert np.array_equal(rp, o.rp) and np.array_equal(col, o.col)
@@ -77,7 +77,7 @@ def test_config0_fp64_bit_identical(fresh):
     pb = W.config0()
     o = OracleRun(pb).run(pb.nsteps)
     assert o.broken > 1000  # the run breaks bonds beyond the pre-crack
-    g = GpuRun(fresh(), pb, P.PDMTS_FP64).run(pb.nsteps)
+    g = GpuPDRun(fresh(), pb, P.PDMTS_FP64).run(pb.nsteps)
     _assert_fp64_identical(g, o)
     # crack tips of the two runs (oracle rule on the oracle's damage, the
     # library's host-side rule on the GPU damage): identical
@@ -116,7 +116,7 @@ def test_fp64_parity_variants(fresh, case):
         u0 = rng.standard_normal((pb.dim, pb.n)) * pb.s0 * pb.lat.dx * 0.4
         v0 = rng.standard_normal((pb.dim, pb.n)) * 0.05
     o = OracleRun(pb, alpha=alpha, micro=micro_o, l=l, c=c, force=force_o, u0=u0, v0=v0).run(pb.nsteps)
-    g = GpuRun(fresh(), pb, P.PDMTS_FP64, micro=micro_g, l=l, c=c, force=force_g, u0=u0, v0=v0,
+    g = GpuPDRun(fresh(), pb, P.PDMTS_FP64, micro=micro_g, l=l, c=c, force=force_g, u0=u0, v0=v0,
                alpha=alpha).run(pb.nsteps)
     assert pb.n % 32 != 0 or case["name"] == "random_state_2d"
     _assert_fp64_identical(g, o)
@@ -125,8 +125,8 @@ def test_fp64_parity_variants(fresh, case):
 def test_graph_chain_equals_single_steps(fresh):
     """Substeps replayed from a captured CUDA graph equal substeps launched one by one."""
     pb = W.small_plate(45, 30, nsteps=0)
-    g1 = GpuRun(fresh(), pb, P.PDMTS_FP64).run(97)
-    g2 = GpuRun(fresh(), pb, P.PDMTS_FP64)
+    g1 = GpuPDRun(fresh(), pb, P.PDMTS_FP64).run(97)
+    g2 = GpuPDRun(fresh(), pb, P.PDMTS_FP64)
     for _ in range(97):
         g2.run(1)
     assert np.array_equal(g1.u(), g2.u()) and np.array_equal(g1.mu(), g2.mu())
@@ -159,8 +159,8 @@ def test_fp32_lattice_kernel_agrees_with_sliced_ell_kernel(fresh, case):
     kernel in its scaled form (q = lhs / |d|^2) and in stencil-column order:
     they agree to FP32 rounding, with the FP32 bar on the broken set."""
     pb, alpha, force, u0 = _lattice_pair(fresh, case)
-    gl = GpuRun(fresh(), pb, P.PDMTS_FP32_BULK, alpha=alpha, force=force, u0=u0)
-    gs = GpuRun(fresh(), pb, P.PDMTS_FP32_BULK_SELL, alpha=alpha, force=force, u0=u0)
+    gl = GpuPDRun(fresh(), pb, P.PDMTS_FP32_BULK, alpha=alpha, force=force, u0=u0)
+    gs = GpuPDRun(fresh(), pb, P.PDMTS_FP32_BULK_SELL, alpha=alpha, force=force, u0=u0)
     assert P.pd_info(gl.pd)["layout"] == 1 and P.pd_info(gs.pd)["layout"] == 0
     gl.run(case["steps"])
     gs.run(case["steps"])
@@ -180,7 +180,7 @@ def test_lattice_tile_configurations_bit_identical(fresh, case):
     pb, alpha, force, u0 = _lattice_pair(fresh, case)
     runs = []
     for tile in [*range(P.PDMTS_LATTICE_TILES), P.PDMTS_LATTICE_TILE_AUTO]:
-        g = GpuRun(fresh(), pb, P.PDMTS_FP32_BULK, alpha=alpha, force=force, u0=u0)
+        g = GpuPDRun(fresh(), pb, P.PDMTS_FP32_BULK, alpha=alpha, force=force, u0=u0)
         P.pd_set_lattice_tile(g.pd, tile)
         g.run(case["steps"])
         got = P.pd_info(g.pd)["lattice_tile"]
@@ -197,8 +197,8 @@ def _mismatch(mu_a, mu_b):
 
 def test_config0_fp32_bulk_within_tolerance(fresh):
     pb = W.config0()
-    g64 = GpuRun(fresh(), pb, P.PDMTS_FP64).run(pb.nsteps)
-    g32 = GpuRun(fresh(), pb, P.PDMTS_FP32_BULK).run(pb.nsteps)
+    g64 = GpuPDRun(fresh(), pb, P.PDMTS_FP64).run(pb.nsteps)
+    g32 = GpuPDRun(fresh(), pb, P.PDMTS_FP32_BULK).run(pb.nsteps)
     err = rel_l2(g32.u(), g64.u())
     mm = _mismatch(g32.mu(), g64.mu())
     tip_err = D.tip_error(D.crack_tip(pb.lat.X, g32.damage(), *CONFIG0_CRACK),
@@ -233,7 +233,7 @@ def test_fp32_lattice3d_kernel_bit_identical_to_sliced_ell(fresh, case):
     u0 = rng.standard_normal((3, pb.n)) * pb.s0 * pb.lat.dx * 0.3 if case.get("state") else None
     runs = []
     for prec in (P.PDMTS_FP32_BULK, P.PDMTS_FP32_BULK_SELL):
-        g = GpuRun(fresh(), pb, prec, alpha=alpha, force=force, micro=micro, l=l, c=c, u0=u0)
+        g = GpuPDRun(fresh(), pb, prec, alpha=alpha, force=force, micro=micro, l=l, c=c, u0=u0)
         runs.append((P.pd_info(g.pd)["layout"], g.run(pb.nsteps)))
     (la, a), (ls, b) = runs
     assert la == 2 and ls == 0
@@ -255,7 +255,7 @@ def test_fp32_bulk_elastic_accuracy(fresh, dim):
     rng = np.random.default_rng(5)
     u0 = rng.standard_normal((pb.dim, pb.n)) * 1e-9
     o = OracleRun(pb, breaking=False, u0=u0).run(pb.nsteps)
-    g = GpuRun(fresh(), pb, P.PDMTS_FP32_BULK, breaking=False, u0=u0).run(pb.nsteps)
+    g = GpuPDRun(fresh(), pb, P.PDMTS_FP32_BULK, breaking=False, u0=u0).run(pb.nsteps)
     eu, ev = rel_l2(g.u(), o.u), rel_l2(g.v(), o.v)
     print(f"fp32 elastic dim={dim}: rel-L2 u {eu:.2e} v {ev:.2e}")
     assert eu <= 1e-5, eu
@@ -280,7 +280,7 @@ def test_edge_cases(fresh):
     # every bond pre-broken: nodes fly freely, damage 1 everywhere
     pb = W.plate2d(8, 8, 1e-3, traction=0.0)
     ctx = fresh()
-    g = GpuRun(ctx, pb, P.PDMTS_FP64)
+    g = GpuPDRun(ctx, pb, P.PDMTS_FP64)
     P.pd_set_precrack(g.pd, [(1, (k + 1) * 1e-3, 0, -1.0, 1.0) for k in range(7)] +
                       [(0, (k + 1) * 1e-3, 1, -1.0, 1.0) for k in range(7)])
     mu = g.mu()
@@ -309,7 +309,7 @@ def test_newtons_third_law_full_size(fresh):
     rng = np.random.default_rng(3)
     u0 = rng.standard_normal((2, pb.n)) * 1e-9
     ctx = fresh()
-    g = GpuRun(ctx, pb, P.PDMTS_FP64, u0=u0, body=False, breaking=False)
+    g = GpuPDRun(ctx, pb, P.PDMTS_FP64, u0=u0, body=False, breaking=False)
     a = g.a()
     m = pb.mat.rho * pb.vol
     assert np.abs((m * a).sum(1)).max() <= 1e-12 * np.abs(m * a).sum()
@@ -324,8 +324,8 @@ def test_full_size_strip_fp64_and_fp32_against_oracle(fresh):
     u0 = rng.standard_normal((2, pb.n)) * pb.s0 * pb.lat.dx * 0.3
     nst = 12
     o = OracleRun(pb, u0=u0).run(nst)
-    g64 = GpuRun(fresh(), pb, P.PDMTS_FP64, u0=u0).run(nst)
+    g64 = GpuPDRun(fresh(), pb, P.PDMTS_FP64, u0=u0).run(nst)
     _assert_fp64_identical(g64, o)
-    g32 = GpuRun(fresh(), pb, P.PDMTS_FP32_BULK, u0=u0).run(nst)
+    g32 = GpuPDRun(fresh(), pb, P.PDMTS_FP32_BULK, u0=u0).run(nst)
     assert rel_l2(g32.u(), o.u) <= FP32_TOL
     assert _mismatch(g32.mu(), o.mu) <= FP32_MISMATCH
