@@ -136,7 +136,7 @@ def oracle_sample(pb, nsub, setup=None):
         rp, col = oracle.family(pb.lat.X, pb.delta)
         mu, _ = oracle.precrack(pb.lat.P, rp, col, [c.in_half_units(pb.lat) for c in pb.cuts])
         opd = oracle.PD(pb.lat.X, pb.vol, pb.delta, pb.c, pb.s0, pb.mat.rho, pb.dt)
-        u = np.zeros((2, pb.n)); v = np.zeros_like(u); a = np.zeros_like(u)
+        u = np.zeros((pb.dim, pb.n)); v = np.zeros_like(u); a = np.zeros_like(u)
         oracle.pd_run(opd, rp, col, mu, u, v, a, 0, b=pb.b, init=True)
         setup = (rp, col, mu, opd, u, v, a)
     rp, col, mu, opd, u, v, a = setup
@@ -146,10 +146,26 @@ def oracle_sample(pb, nsub, setup=None):
     return len(col) * nsub / dt, dt, setup
 
 
+def reference_problem(workload):
+    """(workload name, PD problem) whose PD substeps the oracle samples for a
+    workload: the coupled plates' own PD lattices (their loads come through
+    the interface, so the sampled substeps start from rest), the pure-PD
+    strip for the pd and batch workloads (a batch member is a smaller plate
+    of the same kind)."""
+    from paper_2403_03605_gb300 import workloads as W
+    if workload == "coupled":
+        return COUPLED_NAME, W.config2().pd
+    if workload == "coupled3d":
+        return COUPLED3D_NAME, W.config3().pd
+    if workload == "batch":
+        return BATCH_NAME.format(n=64), make_problem()
+    return WORKLOAD["name"], make_problem()
+
+
 def run_reference(args, rank, world):
-    pb = make_problem()
     if rank != 0:
         return
+    name, pb = reference_problem(args.workload)
     nsub = 2
     setup = None
     for _ in range(args.warmup):
@@ -160,12 +176,12 @@ def run_reference(args, rank, world):
         total_t += dt
         total_u += len(setup[1]) * nsub
     value = total_u / total_t
-    sample = f"{nsub} FP64 oracle substeps of the {pb.n}-node lattice per step"
+    sample = (f"{nsub} FP64 oracle PD substeps per step of the workload's {pb.n}-node PD lattice "
+              f"(the PD substeps only: no FE step or interface solve)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD["name"], "nodes": pb.n,
-                                            "bonds": len(setup[1]), "m": WORKLOAD["m"]},
+            "data": "synthetic", "config": {"workload": name, "pd_nodes": pb.n, "directed_bonds": len(setup[1])},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -308,6 +324,14 @@ def run_batch(args, rank, world, local_rank):
         P.pdmts_ctx_destroy(c)
     if rank != 0:
         return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        nsub = 20
+        _, rpb = reference_problem("batch")
+        rate, dt, _ = oracle_sample(rpb, nsub)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{nsub} FP64 oracle PD substeps of an {rpb.n}-node plate of the same kind ({dt:.1f} s; "
+                         f"the PD substeps only)"}
     nodes = sum(cp.pd.n for cp in cps)
     ms_mix = sorted({cp.m for cp in cps})
     # algorithmic bytes of the PD substeps of the timed rounds (100 B per node and substep,
@@ -333,7 +357,7 @@ def run_batch(args, rank, world, local_rank):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": None, "peak_kind": peak_kind, "kernel": "k_pd_step_lattice2d_batch (whole round)",
                      "algorithmic_bytes_per_step": sub_bytes / args.steps},
-        "cpu_baseline": None,
+        "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
@@ -455,11 +479,13 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- CPU baseline: the FP64 oracle on a bounded sample ----------------
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload != "coupled3d":
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         nsub = 20
-        rate, dt, _ = oracle_sample(make_problem(), nsub)
+        _, rpb = reference_problem(args.workload)
+        rate, dt, _ = oracle_sample(rpb, nsub)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{nsub} FP64 oracle PD substeps of the same 800,000-node lattice ({dt:.1f} s)"}
+               "sample": f"{nsub} FP64 oracle PD substeps of the workload's {rpb.n}-node PD lattice ({dt:.1f} s; "
+                         f"the PD substeps only)"}
 
     if rank == 0:
         cfg = {"workload": (COUPLED3D_NAME if args.workload == "coupled3d" else COUPLED_NAME) if coupled
