@@ -357,6 +357,23 @@ typedef struct {
 } pdmts_stats;
 int pdmts_get_stats(pdmts_ctx *ctx, pdmts_stats *stats);
 
+/* Checkpoint / resume (the paper has no counterpart; a long run can be
+ * stopped and continued). mts_state_size gives the size in bytes of the
+ * context's time-stepping state; mts_state_save copies it into `image` (host
+ * or device memory, caller-owned, exactly that many bytes); mts_state_load
+ * restores an image into a context set up by the same calls (same subdomains,
+ * precision, coupling and time settings; the PD step counter comes from the
+ * image, the context's statistics do not). The image holds the PD state in its working precision and layout
+ * (both displacement buffers, velocity, acceleration), the bond words, the FE
+ * state and the last multiplier; continuing after a load gives the same bits
+ * as continuing the saved context. A load makes the next coarse step rebuild
+ * the interface operator. Blocking (waits for the context's work, and for a
+ * batch round it takes part in). PDMTS_ERR_ARG for a wrong size or an image
+ * from another set-up, PDMTS_ERR_STATE without a PD subdomain. */
+int mts_state_size(pdmts_ctx *ctx, int64_t *bytes);
+int mts_state_save(pdmts_ctx *ctx, void *image, int64_t bytes);
+int mts_state_load(pdmts_ctx *ctx, const void *image, int64_t bytes);
+
 #ifdef __cplusplus
 }
 #endif

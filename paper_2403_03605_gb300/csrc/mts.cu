@@ -3183,3 +3183,167 @@ extern "C" int arlequin_info(pdmts_arl *A, pdmts_arl_info *info)
     info->device_bytes = A->device_bytes + A->fe->device_bytes;
     return PDMTS_OK;
 }
+
+// ------------------------------------------------- checkpoint / resume --
+// The time-stepping state of a context as one opaque image: a header that
+// identifies the set-up, then the raw device arrays that carry state from one
+// coarse step to the next, in a fixed order. Everything else (operators,
+// loads, the interface operator, tuned tiles, captured graphs) follows from
+// the set-up calls; the interface operator is rebuilt after a load, from the
+// bond words near the overlap bands, which by the rebuild rule are the ones
+// it was last built from.
+namespace {
+struct StateHeader {
+    char magic[8];
+    int32_t version, precision, layout, dim;
+    int64_t n, n_mask_words, fe_ndof, nlam;
+    int32_t cur, need_init, lk_cur, has_link;
+    int64_t steps_done, n_segments, payload_bytes;
+};
+constexpr char kStateMagic[8] = {'P', 'D', 'M', 'T', 'S', 'S', 'T', '1'};
+
+template <typename T>
+static void add_seg(std::vector<std::pair<void *, size_t>> &segs, DevArr<T> &a)
+{
+    if (a.p)
+        segs.emplace_back((void *)a.p, sizeof(T) * (size_t)std::max<int64_t>(a.count, 1));
+}
+
+static int state_layout(pdmts_ctx *ctx, StateHeader &h, std::vector<std::pair<void *, size_t>> &segs)
+{
+    pdmts_pd *pd = ctx->pd;
+    if (!pd)
+        return fail(PDMTS_ERR_STATE, "checkpoint: the context has no PD subdomain");
+    std::memset(&h, 0, sizeof h);
+    std::memcpy(h.magic, kStateMagic, sizeof h.magic);
+    h.version = 1;
+    h.precision = pd->precision;
+    h.layout = pd->layout;
+    h.dim = pd->dim;
+    h.n = pd->n;
+    h.n_mask_words = pd->n_mask_words;
+    h.cur = pd->cur;
+    h.need_init = pd->need_init ? 1 : 0;
+    h.lk_cur = pd->lk_cur;
+    h.has_link = pd->has_link && pd->d_mask_link.p ? 1 : 0;
+    h.steps_done = pd->steps_done;
+    segs.clear();
+    if (pd->precision == PDMTS_FP64) {
+        add_seg(segs, pd->d_u[0]);
+        add_seg(segs, pd->d_u[1]);
+        add_seg(segs, pd->d_v);
+        add_seg(segs, pd->d_a);
+    } else {
+        add_seg(segs, pd->f_u4[0]);
+        add_seg(segs, pd->f_u4[1]);
+        add_seg(segs, pd->f_u2[0]);
+        add_seg(segs, pd->f_u2[1]);
+        add_seg(segs, pd->f_v4);
+        add_seg(segs, pd->f_v2);
+        add_seg(segs, pd->f_a);
+    }
+    add_seg(segs, pd->d_mask);
+    if (h.has_link)
+        add_seg(segs, pd->d_mask_link);
+    if (ctx->fem && ctx->fem->assembled) {
+        h.fe_ndof = ctx->fem->ndof();
+        add_seg(segs, ctx->fem->d_u);
+        add_seg(segs, ctx->fem->d_v);
+        add_seg(segs, ctx->fem->d_a);
+    }
+    if (ctx->arl) {
+        h.nlam = ctx->arl->nlam;
+        add_seg(segs, ctx->arl->d_lam0);
+        add_seg(segs, ctx->arl->d_lam);
+    }
+    h.n_segments = (int64_t)segs.size();
+    for (auto &sg : segs)
+        h.payload_bytes += (int64_t)sg.second;
+    return PDMTS_OK;
+}
+
+// Wait for the context's work, including a batch round it takes part in and
+// its FE stream.
+static int state_quiesce(pdmts_ctx *ctx)
+{
+    PDMTS_CUDA_TRY(cudaSetDevice(ctx->device));
+    if (ctx->arl && ctx->arl->batch)
+        PDMTS_TRY(batch_settle(ctx->arl->batch));
+    PDMTS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    if (ctx->arl && ctx->arl->fe_stream)
+        PDMTS_CUDA_TRY(cudaStreamSynchronize(ctx->arl->fe_stream));
+    return PDMTS_OK;
+}
+}  // namespace
+
+extern "C" int mts_state_size(pdmts_ctx *ctx, int64_t *bytes)
+{
+    clear_error();
+    if (!ctx || !bytes)
+        return fail(PDMTS_ERR_ARG, "mts_state_size: NULL argument");
+    StateHeader h;
+    std::vector<std::pair<void *, size_t>> segs;
+    PDMTS_TRY(state_layout(ctx, h, segs));
+    *bytes = (int64_t)sizeof(StateHeader) + h.payload_bytes;
+    return PDMTS_OK;
+}
+
+extern "C" int mts_state_save(pdmts_ctx *ctx, void *image, int64_t bytes)
+{
+    clear_error();
+    if (!ctx || !image)
+        return fail(PDMTS_ERR_ARG, "mts_state_save: NULL argument");
+    StateHeader h;
+    std::vector<std::pair<void *, size_t>> segs;
+    PDMTS_TRY(state_layout(ctx, h, segs));
+    if (bytes != (int64_t)sizeof(StateHeader) + h.payload_bytes)
+        return fail(PDMTS_ERR_ARG, "mts_state_save: image of %lld bytes, the state needs %lld", (long long)bytes,
+                    (long long)(sizeof(StateHeader) + h.payload_bytes));
+    PDMTS_TRY(state_quiesce(ctx));
+    char *dst = static_cast<char *>(image);
+    PDMTS_CUDA_TRY(cudaMemcpy(dst, &h, sizeof h, cudaMemcpyDefault));
+    dst += sizeof h;
+    for (auto &sg : segs) {
+        PDMTS_CUDA_TRY(cudaMemcpy(dst, sg.first, sg.second, cudaMemcpyDefault));
+        dst += sg.second;
+    }
+    return PDMTS_OK;
+}
+
+extern "C" int mts_state_load(pdmts_ctx *ctx, const void *image, int64_t bytes)
+{
+    clear_error();
+    if (!ctx || !image)
+        return fail(PDMTS_ERR_ARG, "mts_state_load: NULL argument");
+    StateHeader mine, h;
+    std::vector<std::pair<void *, size_t>> segs;
+    PDMTS_TRY(state_layout(ctx, mine, segs));
+    if (bytes != (int64_t)sizeof(StateHeader) + mine.payload_bytes)
+        return fail(PDMTS_ERR_ARG, "mts_state_load: image of %lld bytes, this context's state has %lld",
+                    (long long)bytes, (long long)(sizeof(StateHeader) + mine.payload_bytes));
+    PDMTS_TRY(state_quiesce(ctx));
+    PDMTS_CUDA_TRY(cudaMemcpy(&h, image, sizeof h, cudaMemcpyDefault));
+    if (std::memcmp(h.magic, kStateMagic, sizeof h.magic) != 0 || h.version != mine.version ||
+        h.precision != mine.precision || h.layout != mine.layout || h.dim != mine.dim || h.n != mine.n ||
+        h.n_mask_words != mine.n_mask_words || h.fe_ndof != mine.fe_ndof || h.nlam != mine.nlam ||
+        h.has_link != mine.has_link || h.n_segments != mine.n_segments || h.payload_bytes != mine.payload_bytes)
+        return fail(PDMTS_ERR_ARG, "mts_state_load: the image was saved from a different set-up");
+    if (h.cur < 0 || h.cur > 1 || h.lk_cur < 0 || h.lk_cur > 1 || h.steps_done < 0)
+        return fail(PDMTS_ERR_ARG, "mts_state_load: corrupt image header");
+    const char *src = static_cast<const char *>(image) + sizeof h;
+    for (auto &sg : segs) {
+        PDMTS_CUDA_TRY(cudaMemcpy(sg.first, src, sg.second, cudaMemcpyDefault));
+        src += sg.second;
+    }
+    pdmts_pd *pd = ctx->pd;
+    pd->cur = h.cur;
+    pd->need_init = h.need_init != 0;
+    pd->lk_cur = h.lk_cur;
+    pd->steps_done = h.steps_done;
+    pd_invalidate_graphs(pd);
+    if (ctx->arl) {
+        ctx->arl->H_valid = false;  // rebuilt from the loaded bond words at the next step
+        ctx->arl->flag_pending = false;
+    }
+    return PDMTS_OK;
+}

@@ -101,6 +101,9 @@ SIGNATURES = [
     ("pdmts_get_timing", _I, [_V, C.POINTER(_D), C.POINTER(_I64)]),
     ("mts_get_phase_timing", _I, [_V, C.POINTER(_D), C.POINTER(_I64)]),
     ("pdmts_get_stats", _I, [_V, C.POINTER(Stats)]),
+    ("mts_state_size", _I, [_V, C.POINTER(_I64)]),
+    ("mts_state_save", _I, [_V, _V, _I64]),
+    ("mts_state_load", _I, [_V, _V, _I64]),
 ]
 
 
@@ -463,3 +466,19 @@ def arlequin_constraint_residual(arl):
     r, f = _D(), _D()
     _check(load().arlequin_constraint_residual(arl, C.byref(r), C.byref(f)), "arlequin_constraint_residual")
     return r.value, f.value
+
+
+# ------------------------------------------------------ checkpoint / resume
+def mts_state_save(ctx):
+    """The context's time-stepping state as a uint8 image (host memory)."""
+    n = _I64()
+    _check(load().mts_state_size(ctx, C.byref(n)), "mts_state_size")
+    img = np.empty(n.value, dtype=np.uint8)
+    _check(load().mts_state_save(ctx, _ptr(img), n.value), "mts_state_save")
+    return img
+
+
+def mts_state_load(ctx, image):
+    """Restore an image from mts_state_save into a context with the same set-up."""
+    img = np.ascontiguousarray(image, dtype=np.uint8)
+    _check(load().mts_state_load(ctx, _ptr(img), img.size), "mts_state_load")
