@@ -1,0 +1,96 @@
+"""Failures made on the host come back as status codes and leave the library
+usable (no GPU fault is provoked): a device allocator that refuses, NaN/Inf
+inputs, and a body force rejected between steps without touching the state."""
+import numpy as np
+import pytest
+
+from gpu_common import GpuPDRun
+from paper_2403_03605_gb300 import pdmts as P
+from paper_2403_03605_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+PDMTS_ERR_ARG, PDMTS_ERR_NOMEM = -1, -7
+_KEEP = []  # allocator callbacks must outlive the contexts that call them
+
+
+class BudgetAllocator:
+    """Device memory from PyTorch's caching allocator until `left` runs out,
+    then NULL (an out-of-memory condition made on the host)."""
+
+    def __init__(self, left, stream):
+        import torch
+        self.torch = torch
+        self.left = left
+        self.stream = stream
+        self.alloc = P.ALLOC_FN(self._alloc)
+        self.free = P.FREE_FN(self._free)
+
+    def _alloc(self, size, user):
+        if self.left <= 0:
+            return None
+        self.left -= 1
+        return self.torch.cuda.caching_allocator_alloc(int(size), 0, self.stream)
+
+    def _free(self, ptr, user):
+        self.torch.cuda.caching_allocator_delete(ptr)
+
+
+@pytest.fixture
+def fresh():
+    from paper_2403_03605_gb300 import build
+    build.build()
+    made = []
+
+    def mk(**kw):
+        c = P.pdmts_ctx_create(0, **kw)
+        made.append(c)
+        return c
+    yield mk
+    for c in made:
+        P.pdmts_ctx_destroy(c)
+
+
+def test_allocation_failure_is_reported_and_recoverable(fresh):
+    import torch
+    stream = torch.cuda.current_stream(0).cuda_stream
+    ctx = fresh(torch_allocator=False)
+    al = BudgetAllocator(2, stream)
+    _KEEP.append(al)
+    assert P.load().pdmts_set_allocator(ctx, al.alloc, al.free, None) == 0
+    pb = W.small_plate(40, 24, nsteps=20)
+    with pytest.raises(P.PdmtsError) as e:
+        P.pd_create(ctx, pb.lat.X, horizon=pb.delta, c=pb.c, s0=pb.s0, rho=pb.mat.rho, vol_uniform=pb.vol)
+    assert e.value.code == PDMTS_ERR_NOMEM
+    # with memory available again the same context sets the problem up and runs
+    al.left = 10 ** 9
+    pd = P.pd_create(ctx, pb.lat.X, horizon=pb.delta, c=pb.c, s0=pb.s0, rho=pb.mat.rho, vol_uniform=pb.vol)
+    P.pd_set_precrack(pd, [c.as_array() for c in pb.cuts])
+    P.pd_set_body_force(pd, pb.b)
+    P.mts_set_time(ctx, pb.dt, 1)
+    P.mts_advance(ctx, 20)
+    ref = GpuPDRun(fresh(), pb, P.PDMTS_FP64).run(20)  # the default allocator
+    assert np.array_equal(P.pd_read_displacement(pd), ref.u())
+
+
+def test_non_finite_inputs_are_rejected_and_leave_the_state(fresh):
+    pb = W.small_plate(40, 24, nsteps=40)
+    X = pb.lat.X.copy()
+    X[0, 5] = np.nan
+    with pytest.raises(P.PdmtsError) as e:
+        P.pd_create(fresh(), X, horizon=pb.delta, c=pb.c, s0=pb.s0, rho=pb.mat.rho, vol_uniform=pb.vol)
+    assert e.value.code == PDMTS_ERR_ARG
+    for prec in (P.PDMTS_FP64, P.PDMTS_FP32_BULK):
+        a = GpuPDRun(fresh(), pb, prec).run(20)
+        b = GpuPDRun(fresh(), pb, prec).run(20)
+        bad = pb.b.copy()
+        bad[1, 7] = np.inf
+        with pytest.raises(P.PdmtsError) as e:
+            P.pd_set_body_force(b.pd, bad)
+        assert e.value.code == PDMTS_ERR_ARG
+        bad[1, 7] = np.nan
+        with pytest.raises(P.PdmtsError):
+            P.pd_set_body_force(b.pd, bad)
+        a.run(20)
+        b.run(20)  # the rejected loads left the previous ones in place
+        assert np.array_equal(a.u(), b.u()) and np.array_equal(a.mu(), b.mu())
