@@ -203,3 +203,39 @@ def test_coupled_beam_oracle_tracks_the_fe_reference():
         errs[kind] = np.linalg.norm(got - ref) / np.linalg.norm(ref)
     assert max(errs.values()) < 0.05, errs
     assert errs[2] < errs[0], errs
+
+
+def test_free_and_link_runs_superpose_to_the_interpolated_multiplier():
+    """With breaking off the PD and FE subdomains are linear, so the split of
+    a coarse step into a free run and a link run (Eq. 47-48, U = V + Y lambda_m)
+    must equal one direct run under the full interface load: on the PD side m
+    substeps whose multiplier is interpolated linearly between lambda_0 and
+    lambda_m (Eq. 42, the free run's (1 - j/m) lambda_0 plus the link run's
+    (j/m) lambda_m); on the FE side one Newmark step under -G_FE^T lambda_m.
+    For m > 1 this pins the free run's lambda_0 term, which vanishes at
+    m = 1 and so escapes the monolithic m = 1 pin."""
+    from oracle import pd_run
+    cp = W.small_coupled(m=4, n_coarse=6)
+    o = MTSOracle(cp, breaking=False)
+    o.advance(3)  # a state with lambda_0 != 0
+    u, v, a = o.u.copy(), o.v.copy(), o.a.copy()
+    uf, vf, af = o.uf.copy(), o.vf.copy(), o.af.copy()
+    lam0 = o.lam.copy()
+    lam_m = o.coarse_step()
+    assert np.linalg.norm(lam0) > 0 and np.linalg.norm(lam_m) > 0
+    m = cp.m
+    g0, gm = o.interface_force_density(lam0), o.interface_force_density(lam_m)
+    mu = o.mu.copy()
+    for j in range(1, m + 1):
+        gj = (1.0 - j / m) * g0 + (j / m) * gm
+        pd_run(o.pd, o.rp, o.col, mu, u, v, a, 1, alpha=o.alpha, b=None, g=np.ascontiguousarray(gj),
+               theta=np.ones(1), breaking=False)
+    for x, y in [(u, o.u), (v, o.v), (a, o.a)]:
+        assert np.linalg.norm(x - y) <= 1e-11 * np.linalg.norm(y)
+    # FE: one implicit Newmark step with the load P - G_FE^T lambda_m
+    dtf, be, ga = o.dt_fe, o.beta, o.gamma
+    ut = uf + dtf * vf + (0.5 - be) * dtf * dtf * af
+    vt = vf + (1 - ga) * dtf * af
+    an = o.solver.solve(o.fe.P - o.Gfe.T @ lam_m - o.fe.K @ ut)
+    for x, y in [(ut + be * dtf * dtf * an, o.uf), (vt + ga * dtf * an, o.vf), (an, o.af)]:
+        assert np.linalg.norm(x - y) <= 1e-11 * np.linalg.norm(y)
