@@ -332,6 +332,44 @@ def test_breaking_test_matches_literal_stretch_and_is_irreversible():
         prev = mu.copy()
 
 
+@pytest.mark.parametrize("break_step", [1, 2])
+def test_bond_breaks_before_it_carries_force(break_step):
+    """Eq. 4 includes t' = t: a bond that reaches the critical stretch at a
+    step carries no force at that step. Two nodes separating along their bond
+    from rest positions: the Verlet recurrence with the bond force until the
+    breaking step and none from it on is written out step by step; the bond
+    (both directions) is cut exactly at that step."""
+    L, ang, s0 = 7e-4, 0.37, 1e-3
+    pd, rp, col, e = _two_nodes(L, ang, c=6e22)
+    pd.s0, pd.breaking = s0, True
+    cL = pd.c / L ** 3
+    w2 = 2.0 * cL * L * L * pd.V[0] / pd.rho  # relative (stretch) mode
+    dt = 0.2 / math.sqrt(w2)
+    pd.dt = dt
+    # relative speed: the stretch q / L first reaches s0 at step break_step
+    q_at = (lambda v0: [dt * v0, dt * v0 + dt * (v0 - 0.5 * dt * w2 * dt * v0) - 0.5 * dt * dt * w2 * dt * v0])
+    v0 = 1.5 * s0 * L / dt if break_step == 1 else 0.7 * s0 * L / dt
+    q1, q2 = q_at(v0)
+    assert (q1 / L >= s0) == (break_step == 1) and q2 / L >= s0
+    u = np.zeros((2, 2)); v = np.zeros_like(u); a = np.zeros_like(u)
+    v[:, 0], v[:, 1] = -0.5 * v0 * e, 0.5 * v0 * e
+    mu = np.ones(len(col), np.uint8)
+    oracle.pd_run(pd, rp, col, mu, u, v, a, 0, init=True)  # a_0 = 0 (no stretch yet)
+    assert np.all(a == 0.0)
+    # written-out recurrence of the relative coordinate q and speed w
+    q, w, acc = 0.0, v0, 0.0
+    for n in range(1, 4):
+        oracle.pd_run(pd, rp, col, mu, u, v, a, 1)
+        q_new = q + dt * w + 0.5 * dt * dt * acc
+        acc_new = -w2 * q_new if n < break_step else 0.0
+        w = w + 0.5 * dt * (acc + acc_new)
+        q, acc = q_new, acc_new
+        rel_q = float((u[:, 1] - u[:, 0]) @ e)
+        rel_w = float((v[:, 1] - v[:, 0]) @ e)
+        assert abs(rel_q - q) <= 1e-12 * abs(q) and abs(rel_w - w) <= 1e-12 * abs(v0)
+        assert int(mu.sum()) == (2 if n < break_step else 0)
+
+
 def test_damage_definition():
     """Eq. 5 on a hand-made family: phi = 1 - intact volume / family volume."""
     X = np.array([[0.0, 1.0, 2.0, 3.0], [0.0, 0.0, 0.0, 0.0]])
