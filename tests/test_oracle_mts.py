@@ -239,3 +239,59 @@ def test_free_and_link_runs_superpose_to_the_interpolated_multiplier():
     an = o.solver.solve(o.fe.P - o.Gfe.T @ lam_m - o.fe.K @ ut)
     for x, y in [(ut + be * dtf * dtf * an, o.uf), (vt + ga * dtf * an, o.vf), (an, o.af)]:
         assert np.linalg.norm(x - y) <= 1e-11 * np.linalg.norm(y)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_fe_patch_affine_field_energy_and_interior_balance(dim):
+    """Patch test of the Q4 (plane stress) and Hex8 elements on a block of
+    rectangular (non-square) elements: an affine displacement u = F x leaves
+    every interior node in equilibrium (K u = 0 there), and the strain energy
+    (1/2) u' K u equals the continuum energy of the uniform strain times the
+    volume, written with Lame constants: mu e:e + (lam'/2) (tr e)^2, where
+    lam' = 2 lam mu / (lam + 2 mu) in plane stress and lam' = lam in 3D. The
+    lumped mass sums to rho times the volume."""
+    from oracle.mts import FE
+    E, nu, rho, t = 72e9, 0.3, 2440.0, 1e-3
+    rng = np.random.default_rng(5)
+    if dim == 2:
+        X0, c0 = W.q4_block(0.0, 0.0, 4, 3, 1e-3)
+        X = X0 * np.array([[1.0], [1.7]])  # rectangles 1 x 1.7 mm
+        ne, vol = 4 * 3, 4e-3 * 3 * 1.7e-3 * t
+        fe = FE(W.FEMesh(X, c0, 1e-3), E, nu, rho, t, [], 1, np.zeros((0, 2), np.int32), np.zeros((0, 2)))
+    else:
+        X0, c0 = W.hex8_block(0.0, 0.0, 0.0, 3, 3, 3, 1e-3)
+        X = X0 * np.array([[1.0], [1.4], [0.8]])
+        vol = 3e-3 * 3 * 1.4e-3 * 3 * 0.8e-3
+        fe = FE(W.FEMesh(X, c0, 1e-3), E, nu, rho, 1.0, [], 1, np.zeros((0, 4), np.int32), np.zeros((0, 3)))
+    F = rng.standard_normal((dim, dim)) * 1e-4
+    u = (F @ X).reshape(-1)  # SoA: all x, then all y (, all z)
+    K = fe.K.toarray()
+    f = K @ u
+    n = X.shape[1]
+    lo, hi = X.min(axis=1, keepdims=True), X.max(axis=1, keepdims=True)
+    interior = np.all((X > lo + 1e-12) & (X < hi - 1e-12), axis=0)
+    assert interior.sum() > 0
+    scale = np.abs(f).max()
+    for d in range(dim):
+        assert np.abs(f[d * n:(d + 1) * n][interior]).max() <= 1e-9 * scale
+    eps = 0.5 * (F + F.T)
+    mu = E / (2 * (1 + nu))
+    lam = E * nu / ((1 + nu) * (1 - 2 * nu))
+    if dim == 2:
+        lam = 2 * lam * mu / (lam + 2 * mu)
+    w = mu * np.sum(eps * eps) + 0.5 * lam * np.trace(eps) ** 2
+    energy = 0.5 * u @ f
+    assert abs(energy - w * vol) <= 1e-11 * w * vol
+    assert abs(fe.M.sum() / dim - rho * vol) <= 1e-12 * rho * vol
+    # one element: exactly the rigid-body modes in the null space (3 in 2D,
+    # 6 in 3D; under-integration would add hourglass modes)
+    if dim == 2:
+        X1, c1 = W.q4_block(0.0, 0.0, 1, 1, 1e-3)
+        one = FE(W.FEMesh(X1 * np.array([[1.0], [1.7]]), c1, 1e-3), E, nu, rho, t, [], 1,
+                 np.zeros((0, 2), np.int32), np.zeros((0, 2)))
+    else:
+        X1, c1 = W.hex8_block(0.0, 0.0, 0.0, 1, 1, 1, 1e-3)
+        one = FE(W.FEMesh(X1 * np.array([[1.0], [1.4], [0.8]]), c1, 1e-3), E, nu, rho, 1.0, [], 1,
+                 np.zeros((0, 4), np.int32), np.zeros((0, 3)))
+    ev = np.linalg.eigvalsh(one.K.toarray())
+    assert np.sum(np.abs(ev) <= 1e-9 * ev.max()) == (3 if dim == 2 else 6)
