@@ -154,9 +154,9 @@ def reference_problem(workload):
     of the same kind)."""
     from paper_2403_03605_gb300 import workloads as W
     if workload == "coupled":
-        return COUPLED_NAME, W.config2().pd
+        return COUPLED_NAME, W.coupled_plate_2000x400().pd
     if workload == "coupled3d":
-        return COUPLED3D_NAME, W.config3().pd
+        return COUPLED3D_NAME, W.coupled_plate3d_400x64x8().pd
     if workload == "batch":
         return BATCH_NAME.format(n=64), make_problem()
     return WORKLOAD["name"], make_problem()
@@ -213,7 +213,7 @@ def setup_ours(P, ctx, workload):
         P.pd_set_body_force(pd, pb.b)
         P.mts_set_time(ctx, pb.dt, m)
         return pd, None, None, P.pd_info(pd), pb, m, None
-    cp = W.config3() if workload == "coupled3d" else W.config2()
+    cp = W.coupled_plate3d_400x64x8() if workload == "coupled3d" else W.coupled_plate_2000x400()
     pd, fe, arl = make_coupled(P, ctx, cp)
     return pd, fe, arl, P.pd_info(pd), cp.pd, cp.m, cp
 
@@ -253,7 +253,7 @@ def run_batch(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream(dev)
     t_setup = time.perf_counter()
-    cps = W.config4(n=args.batch_members)
+    cps = W.batch_plates(n=args.batch_members)
     ctxs, handles = [], []
     for cp in cps:
         ctx = P.pdmts_ctx_create(local_rank, stream.cuda_stream)
@@ -546,7 +546,7 @@ def run_accuracy(P, dev, stream, workload, n_steps, budget_s):
     from paper_2403_03605_gb300 import diagnostics as D
     from paper_2403_03605_gb300 import workloads as W
     coupled = workload in ("coupled", "coupled3d")
-    cp = (W.config3() if workload == "coupled3d" else W.config2()) if coupled else None
+    cp = (W.coupled_plate3d_400x64x8() if workload == "coupled3d" else W.coupled_plate_2000x400()) if coupled else None
     if n_steps < 0:
         n_steps = {"coupled": 60, "coupled3d": 30, "pd": 100}[workload]
     n_steps = max(n_steps, 2)

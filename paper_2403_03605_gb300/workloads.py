@@ -180,7 +180,7 @@ def plate3d(nx: int, ny: int, nz: int, dx: float, *, cuts_mm=(), traction=12e6, 
     return PDProblem(name, lat, mat, delta, c, s0, dt, nsteps, cuts, b, dx ** 3)
 
 
-def config0() -> PDProblem:
+def plate_100x100() -> PDProblem:
     """Pure FP64 2D plate: 0.05 x 0.05 m, dx 0.5 mm (100 x 100 nodes), centred 10 mm
     pre-crack at mid-height, 12 MPa on top/bottom edges, dt 25 ns, 500 steps."""
     return plate2d(100, 100, 0.5e-3, cuts_mm=[(1, 0.025, 0, 0.020, 0.030)], traction=12e6,
@@ -309,7 +309,7 @@ def coupled_plate(Lx, Ly, strip, dx, h_fe, overlap, *, crack=None, traction=12e6
     return CoupledProblem(name, pd, fe, faces, tr, bands, weight_kind, m, n_coarse)
 
 
-def config1() -> CoupledProblem:
+def coupled_plate_400x64() -> CoupledProblem:
     """Coupled 2D plate 0.1 x 0.04 m, 50 mm edge pre-crack at mid-height; PD strip
     16 mm (400 x 64 nodes at 0.25 mm), Q4 elements of 1 mm elsewhere, 2 mm overlap
     bands with linear weights; 12 MPa; dt_PD 20 ns, m = 10, 200 coarse steps."""
@@ -317,7 +317,7 @@ def config1() -> CoupledProblem:
                          dt=20e-9, m=10, n_coarse=200, name="coupled_plate_100x40mm_pd400x64")
 
 
-def config2() -> CoupledProblem:
+def coupled_plate_2000x400() -> CoupledProblem:
     """Fine coupled plate: PD strip 20 mm at 0.05 mm (2000 x 400 = 800k nodes), Q4
     0.5 mm, 2 mm overlap, 50 mm edge crack at mid-height; dt_PD 5 ns, m = 20, 500 coarse."""
     return coupled_plate(0.1, 0.04, (0.010, 0.030), 0.05e-3, 0.5e-3, 2e-3, crack=(0.020, 0.0, 0.050),
@@ -348,7 +348,7 @@ def batch_member(N: int, crack_len: float, traction: float, m: int, *, n_coarse=
                          traction=traction, dt=dt, m=m, n_coarse=n_coarse, name=name)
 
 
-def config4_draws(seed: int = 3605, n: int = 64):
+def batch_plates_draws(seed: int = 3605, n: int = 64):
     """(N_PD, crack length, traction, m) of the batched benchmark's specimens,
     drawn per specimen in this order: N ~ U[20k, 400k] (integer), crack ~
     U[20, 60] mm, traction ~ U[6, 15] MPa, m ~ choice{5, 10, 20}."""
@@ -363,10 +363,10 @@ def config4_draws(seed: int = 3605, n: int = 64):
     return out
 
 
-def config4(seed: int = 3605, n: int = 64, n_coarse: int = 200) -> list[CoupledProblem]:
+def batch_plates(seed: int = 3605, n: int = 64, n_coarse: int = 200) -> list[CoupledProblem]:
     """Batched: n independent coupled plates of uneven size, crack, load and m."""
     return [batch_member(N, c, T, m, n_coarse=n_coarse, name=f"batch_plate_{k}")
-            for k, (N, c, T, m) in enumerate(config4_draws(seed, n))]
+            for k, (N, c, T, m) in enumerate(batch_plates_draws(seed, n))]
 
 
 def hex8_block(x0, y0, z0, nex, ney, nez, h, node_offset=0):
@@ -431,7 +431,7 @@ def coupled_plate3d(Lx, Ly, Lz, strip, dx, h_fe, overlap, *, crack=None, tractio
                           n_coarse)
 
 
-def config3() -> CoupledProblem:
+def coupled_plate3d_400x64x8() -> CoupledProblem:
     """3D coupled plate 0.1 x 0.04 x 0.002 m: PD strip 16 mm at 0.25 mm
     (400 x 64 x 8 nodes), Hex8 1 mm elsewhere, 2 mm overlap, 50 mm edge crack
     at mid-height, 12 MPa, dt_PD 20 ns, m = 10, 300 coarse steps, nu = 1/4."""

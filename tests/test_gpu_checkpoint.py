@@ -33,7 +33,7 @@ def _coupled_state(g):
 
 COUPLED = [dict(name="fp64_breaking_rebuilds", cp=lambda: W.small_coupled(m=4, n_coarse=12, traction=30e6),
                 prec=P.PDMTS_FP64, before=5, after=6),
-           dict(name="fp32_bulk_plate_25600", cp=W.config1, prec=P.PDMTS_FP32_BULK, before=3, after=4)]
+           dict(name="fp32_bulk_plate_25600", cp=W.coupled_plate_400x64, prec=P.PDMTS_FP32_BULK, before=3, after=4)]
 
 
 @pytest.mark.parametrize("case", COUPLED, ids=[c["name"] for c in COUPLED])

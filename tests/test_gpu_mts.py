@@ -84,10 +84,10 @@ def test_mts_uniform_velocity_patch(fresh):
 
 
 @pytest.mark.parametrize("prec", [P.PDMTS_FP64, P.PDMTS_FP32_BULK])
-def test_config1_full_size_properties(fresh, prec):
+def test_coupled_400x64_full_size_properties(fresh, prec):
     """The 100 x 40 mm coupled plate (25,600 PD nodes, 3,030 FE nodes): the
     velocity constraint holds after every coarse step and the state stays finite."""
-    cp = W.config1()
+    cp = W.coupled_plate_400x64()
     g = GpuMTS(fresh(), cp, prec)
     for _ in range(3):
         g.run(5)
@@ -95,12 +95,12 @@ def test_config1_full_size_properties(fresh, prec):
         assert res <= (1e-11 if prec == P.PDMTS_FP64 else 1e-5), res
     assert np.isfinite(g.u()).all() and np.isfinite(g.uf()).all()
     info = P.arlequin_info(g.arl)
-    print("config1 coupling:", info)
+    print("400x64 coupling:", info)
     assert info["n_lambda"] == 2 * 606
 
 
-FULL_SIZE = [dict(name="config2_800k", cp=W.config2, steps=20, n_lambda=4020),
-             dict(name="config3_3d_205k", cp=W.config3, steps=6, n_lambda=5454)]
+FULL_SIZE = [dict(name="coupled_2000x400", cp=W.coupled_plate_2000x400, steps=20, n_lambda=4020),
+             dict(name="coupled3d_400x64x8", cp=W.coupled_plate3d_400x64x8, steps=6, n_lambda=5454)]
 
 
 @pytest.mark.parametrize("case", FULL_SIZE, ids=[c["name"] for c in FULL_SIZE])
@@ -137,7 +137,7 @@ def test_coupled_lattice_tiles_bit_identical(fresh):
     configuration (the link substeps run on windows of tile rows converted per
     tile height), and with the tuned pair of configurations (free chains, link
     chains): identical PD, FE and multiplier states."""
-    cp = W.config1()
+    cp = W.coupled_plate_400x64()
     ref = None
     for tile in [*range(P.PDMTS_LATTICE_TILES), P.PDMTS_LATTICE_TILE_AUTO]:
         g = GpuMTS(fresh(), cp, P.PDMTS_FP32_BULK)
@@ -149,7 +149,7 @@ def test_coupled_lattice_tiles_bit_identical(fresh):
         else:  # tuned separately for the free and the link chains
             assert 0 <= info["lattice_tile"] < P.PDMTS_LATTICE_TILES
             assert 0 <= info["link_tile"] < P.PDMTS_LATTICE_TILES
-            print("config1 tuned tiles: free", info["lattice_tile"], "link", info["link_tile"])
+            print("400x64 tuned tiles: free", info["lattice_tile"], "link", info["link_tile"])
         got = (g.u(), g.v(), g.uf(), g.lam(), g.mu())
         if ref is None:
             ref = got

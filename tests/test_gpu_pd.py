@@ -20,9 +20,9 @@ pytestmark = pytest.mark.gpu
 FP64_TOL = 1e-10
 FP32_TOL = 1e-4
 FP32_MISMATCH = 1e-3
-# crack plane of config 0 (normal y, level 25 mm, along x) and the band searched
+# crack plane of the 100 x 100 plate (normal y, level 25 mm, along x) and the band searched
 # for the crack tip (5 mm: the loading layers at the faces stay outside)
-CONFIG0_CRACK = (1, 0.025, 0, 5e-3)
+PLATE100_CRACK = (1, 0.025, 0, 5e-3)
 
 
 @pytest.fixture(scope="module")
@@ -60,7 +60,7 @@ def _assert_fp64_identical(g: GpuPDRun, o: OracleRun):
 
 
 def test_family_and_precrack_match_oracle(fresh):
-    for pb in (W.config0(), W.plate3d(11, 9, 8, 0.5e-3, cuts_mm=[(1, 2.25e-3, 0, 0.0, 2.5e-3)])):
+    for pb in (W.plate_100x100(), W.plate3d(11, 9, 8, 0.5e-3, cuts_mm=[(1, 2.25e-3, 0, 0.0, 2.5e-3)])):
         ctx = fresh()
         g = GpuPDRun(ctx, pb, P.PDMTS_FP64)
         o = OracleRun(pb)
@@ -71,19 +71,19 @@ def test_family_and_precrack_match_oracle(fresh):
         assert int((mu == 0).sum()) == o.ncut > 0
 
 
-def test_config0_fp64_bit_identical(fresh):
+def test_plate_100x100_fp64_bit_identical(fresh):
     """100 x 100 plate, centred crack, 12 MPa, dt 25 ns, 500 steps: identical
     displacements and an identical broken-bond set, with breaking under way."""
-    pb = W.config0()
+    pb = W.plate_100x100()
     o = OracleRun(pb).run(pb.nsteps)
     assert o.broken > 1000  # the run breaks bonds beyond the pre-crack
     g = GpuPDRun(fresh(), pb, P.PDMTS_FP64).run(pb.nsteps)
     _assert_fp64_identical(g, o)
     # crack tips of the two runs (oracle rule on the oracle's damage, the
     # library's host-side rule on the GPU damage): identical
-    tip_o = oracle.crack_tip(pb.lat.X, o.damage(), *CONFIG0_CRACK)
-    tip_g = D.crack_tip(pb.lat.X, g.damage(), *CONFIG0_CRACK)
-    print(f"config0 crack tips: oracle {tip_o}, GPU FP64 {tip_g}")
+    tip_o = oracle.crack_tip(pb.lat.X, o.damage(), *PLATE100_CRACK)
+    tip_g = D.crack_tip(pb.lat.X, g.damage(), *PLATE100_CRACK)
+    print(f"100x100 plate crack tips: oracle {tip_o}, GPU FP64 {tip_g}")
     assert tip_o == tip_g and not np.isnan(tip_o[0])
 
 
@@ -135,7 +135,7 @@ def test_graph_chain_equals_single_steps(fresh):
 
 
 LATTICE_CASES = [
-    dict(name="config0", pb=lambda: W.config0(), steps=500),
+    dict(name="plate_100x100", pb=lambda: W.plate_100x100(), steps=500),
     dict(name="weights", pb=lambda: W.small_plate(70, 45, nsteps=150), alpha=True, steps=150),
     dict(name="weights_nx72", pb=lambda: W.small_plate(72, 45, nsteps=150), alpha=True, steps=150),
     dict(name="pmb", pb=lambda: W.small_plate(66, 41, nsteps=150), force=True, steps=150),
@@ -195,15 +195,15 @@ def _mismatch(mu_a, mu_b):
     return float(np.count_nonzero(mu_a != mu_b)) / len(mu_a)
 
 
-def test_config0_fp32_bulk_within_tolerance(fresh):
-    pb = W.config0()
+def test_plate_100x100_fp32_bulk_within_tolerance(fresh):
+    pb = W.plate_100x100()
     g64 = GpuPDRun(fresh(), pb, P.PDMTS_FP64).run(pb.nsteps)
     g32 = GpuPDRun(fresh(), pb, P.PDMTS_FP32_BULK).run(pb.nsteps)
     err = rel_l2(g32.u(), g64.u())
     mm = _mismatch(g32.mu(), g64.mu())
-    tip_err = D.tip_error(D.crack_tip(pb.lat.X, g32.damage(), *CONFIG0_CRACK),
-                          D.crack_tip(pb.lat.X, g64.damage(), *CONFIG0_CRACK))
-    print(f"config0 fp32-bulk vs fp64: rel-L2 u {err:.2e}, broken mismatch {mm:.2e}, crack-tip error {tip_err:.2e} m")
+    tip_err = D.tip_error(D.crack_tip(pb.lat.X, g32.damage(), *PLATE100_CRACK),
+                          D.crack_tip(pb.lat.X, g64.damage(), *PLATE100_CRACK))
+    print(f"100x100 plate fp32-bulk vs fp64: rel-L2 u {err:.2e}, broken mismatch {mm:.2e}, crack-tip error {tip_err:.2e} m")
     assert err <= FP32_TOL, err
     assert mm <= FP32_MISMATCH, mm
     assert tip_err <= pb.delta, tip_err  # reported; within one horizon

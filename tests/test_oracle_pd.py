@@ -41,10 +41,10 @@ def test_interior_family_sizes():
     assert np.diff(rp3).max() == 122 and np.diff(rp3)[4 + 9 * (4 + 9 * 4)] == 122
 
 
-def test_family_total_config0_by_offset_counting():
+def test_family_total_100x100_by_offset_counting():
     """Directed-bond total of the 100 x 100 plate equals sum over stencil offsets of
     (nx - |di|)(ny - |dj|), an integer count independent of the float search."""
-    pb = W.config0()
+    pb = W.plate_100x100()
     rp, col = oracle.family(pb.lat.X, pb.delta)
     nx, ny = pb.lat.shape
     total = sum((nx - abs(a)) * (ny - abs(b)) for a, b in _lattice_offsets(2, W.HORIZON_FACTOR))
@@ -93,9 +93,9 @@ def test_precrack_matches_exact_rational_brute_force():
     assert cnt == ref > 0
 
 
-def test_precrack_count_config0():
+def test_precrack_count_100x100():
     """Centred 10 mm crack of the 100 x 100 plate cuts 720 directed bonds."""
-    pb = W.config0()
+    pb = W.plate_100x100()
     rp, col = oracle.family(pb.lat.X, pb.delta)
     mu, cnt = oracle.precrack(pb.lat.P, rp, col, [c.in_half_units(pb.lat) for c in pb.cuts])
     assert cnt == 720

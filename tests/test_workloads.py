@@ -4,8 +4,8 @@ import numpy as np
 from paper_2403_03605_gb300 import workloads as W
 
 
-def test_config4_draws_follow_the_stated_distributions():
-    d = W.config4_draws()
+def test_batch_draws_follow_the_stated_distributions():
+    d = W.batch_plates_draws()
     assert len(d) == 64
     N = np.array([x[0] for x in d])
     crack = np.array([x[1] for x in d])
@@ -15,7 +15,7 @@ def test_config4_draws_follow_the_stated_distributions():
     assert crack.min() >= 0.020 and crack.max() <= 0.060
     assert T.min() >= 6e6 and T.max() <= 15e6
     assert set(m.tolist()) <= {5, 10, 20} and len(set(m.tolist())) == 3
-    assert W.config4_draws() == d  # seeded
+    assert W.batch_plates_draws() == d  # seeded
     # about 13.6 million PD nodes in total
     assert 12e6 < N.sum() < 15e6
 
