@@ -109,6 +109,8 @@ int pdmts_ctx_synchronize(pdmts_ctx *ctx);
 int pd_create(pdmts_ctx *ctx, int dim, int64_t n, const double *X, const double *vol,
               double vol_uniform, double horizon, int micro_kind, double c, double l,
               double s0, double rho, int precision, pdmts_pd **pd);
+/* Release the subdomain and its device memory (waits for the context's
+ * work). A coupling bound to it must be destroyed first. NULL is a no-op. */
 int pd_destroy(pdmts_pd *pd);
 
 /* Pre-crack: each cut is 5 doubles {normal axis, level, along axis, lo, hi}:
@@ -344,6 +346,8 @@ typedef struct {
     double last_round_ms[5];
 } pdmts_batch_info;
 int mts_batch_info(const pdmts_batch *batch, pdmts_batch_info *info);
+/* Release the batch (waits for its last round); the members stay usable
+ * alone. NULL is a no-op. */
 int mts_batch_destroy(pdmts_batch *batch);
 
 /* Counters since context creation. */
