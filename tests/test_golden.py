@@ -22,3 +22,23 @@ def test_table1_fixture():
     assert all(r[5] in (1, 2, 5, 10) and 0.7 <= r[6] <= 1.8 for r in rows)
     explicit_mts = {r[0]: (r[1], r[2], r[5]) for r in rows if r[4] == 0 and r[5] > 1 and r[3] == 0.25}
     assert explicit_mts == {13: ("cubic", 3, 2), 17: ("cubic", 3, 5), 18: ("cubic", 3, 10)}
+
+
+def test_oracle_plate_run_matches_its_recorded_summary():
+    """The oracle's 500-step run of the 100 x 100 pre-cracked plate reproduces
+    the summary tests/golden/make_oracle_goldens.py recorded from it (counts
+    exactly, the state bit for bit): an unintended change of the oracle's
+    arithmetic fails here. The counts are cross-checked by integer arithmetic:
+    intact = family - pre-cut - broken."""
+    import importlib.util
+    import json
+    spec = importlib.util.spec_from_file_location("make_oracle_goldens",
+                                                  os.path.join(GOLDEN, "make_oracle_goldens.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    with open(os.path.join(GOLDEN, "oracle_plate_100x100.json")) as f:
+        rec = json.load(f)
+    got = mod.run()
+    assert got == rec
+    assert rec["intact_at_end"] == rec["directed_bonds"] - rec["precut"] - rec["broken_by_dynamics"]
+    assert rec["directed_bonds"] == 272836 and rec["precut"] == 720
