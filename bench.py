@@ -238,12 +238,21 @@ def make_coupled(P, ctx, cp, precision=None):
 BATCH_NAME = "batch_{n}_coupled_plates_seed3605_pd20k-400k_m5-10-20_fp32bulk"
 
 
+def shard(n, rank, world):
+    """Indices of the independent members rank `rank` of `world` advances
+    (round robin over the seeded member list; the shards partition it)."""
+    return list(range(rank, n, world))
+
+
 def run_batch(args, rank, world, local_rank):
     """Batched workload: independent coupled plates of uneven size, crack, load
     and m (seeded), advanced one round (one coarse step of each) at a time by
     mts_batch_advance; the per-instance loop over the same rounds is timed
-    beside it."""
+    beside it. With N ranks the members are sharded over them (no collective
+    on the data path; the job's rate is the summed units over the slowest
+    rank's time)."""
     import torch
+    import torch.distributed as dist
     from paper_2403_03605_gb300 import build as B
     from paper_2403_03605_gb300 import pdmts as P
     from paper_2403_03605_gb300 import workloads as W
@@ -253,7 +262,8 @@ def run_batch(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream(dev)
     t_setup = time.perf_counter()
-    cps = W.batch_plates(n=args.batch_members)
+    all_cps = W.batch_plates(n=args.batch_members)
+    cps = [all_cps[i] for i in shard(len(all_cps), rank, world)]
     ctxs, handles = [], []
     for cp in cps:
         ctx = P.pdmts_ctx_create(local_rank, stream.cuda_stream)
@@ -290,14 +300,21 @@ def run_batch(args, rank, world, local_rank):
 
     i0 = P.mts_batch_info(batch)
     r0 = rebuilds()
+    if world > 1:
+        dist.barrier()
     with ClockSampler(local_rank) as clk:
         time.sleep(0.3)
         torch.cuda.nvtx.range_push("timed_steps")
         batch_ms, d = timed(lambda: P.mts_batch_advance(batch, 1))
         torch.cuda.nvtx.range_pop()
+    if world > 1:
+        dist.barrier()
     i1 = P.mts_batch_info(batch)
     timed_rebuilds = rebuilds() - r0
-    value = d["bond_updates"] / (batch_ms * 1e-3)
+    own_ms = batch_ms  # this rank's members
+    own_value = d["bond_updates"] / (own_ms * 1e-3)
+    batch_ms, _, value = reduce_job(own_ms, d["bond_updates"], world, device=dev)  # the job
+    _, coarse_total, _ = reduce_job(own_ms, d["coarse_steps"], world, device=dev)
     launches = i1["kernel_launches"] - i0["kernel_launches"]
     solo_ms, ds = timed(lambda: [P.mts_advance(c, 1) for c in ctxs])
     solo_value = ds["bond_updates"] / (solo_ms * 1e-3)
@@ -316,7 +333,7 @@ def run_batch(args, rank, world, local_rank):
             P.fem_read_displacement(fe, uf.shape[0], uf.numpy())
     torch.cuda.synchronize(dev)
     e2e_s = time.perf_counter() - t0
-    e2e_value = (stats_sum()["bond_updates"] - s0["bond_updates"]) / e2e_s
+    _, _, e2e_value = reduce_job(1e3 * e2e_s, stats_sum()["bond_updates"] - s0["bond_updates"], world, device=dev)
     d2h = sum(u.numel() * 8 + uf.numel() * 8 for u, uf in outs)
     info = P.mts_batch_info(batch)
     P.mts_batch_destroy(batch)
@@ -332,18 +349,20 @@ def run_batch(args, rank, world, local_rank):
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{nsub} FP64 oracle PD substeps of an {rpb.n}-node plate of the same kind ({dt:.1f} s; "
                          f"the PD substeps only)"}
-    nodes = sum(cp.pd.n for cp in cps)
-    ms_mix = sorted({cp.m for cp in cps})
-    # algorithmic bytes of the PD substeps of the timed rounds (100 B per node and substep,
-    # FP32-bulk coupled), over the whole round time: a lower bound on the substeps' own rate
+    nodes = sum(cp.pd.n for cp in all_cps)
+    ms_mix = sorted({cp.m for cp in all_cps})
+    # algorithmic bytes of rank 0's PD substeps of the timed rounds (100 B per node and
+    # substep, FP32-bulk coupled), over its whole round time: a lower bound on the
+    # substeps' own rate
     sub_bytes = 100.0 * sum(2 * cp.m * cp.pd.n for cp in cps) * args.steps
-    achieved = sub_bytes / (batch_ms * 1e-3) / 1e9
+    achieved = sub_bytes / (own_ms * 1e-3) / 1e9
     peak, peak_kind = peaks()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": batch_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": BATCH_NAME.format(n=len(cps)), "members": len(cps), "pd_nodes_total": nodes,
+        "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": BATCH_NAME.format(n=len(all_cps)), "members": len(all_cps),
+                   "members_per_rank": "round robin" if world > 1 else len(cps), "pd_nodes_total": nodes,
                    "m_values": ms_mix, "step": "one round = one coarse step of every member",
                    "lattice_tile": info["lattice_tile"], "batched_launches_per_round":
                    (i1["batched_launches"] - i0["batched_launches"]) // max(args.steps, 1),
@@ -352,8 +371,8 @@ def run_batch(args, rank, world, local_rank):
                    "last_round_phase_ms": dict(zip(["lambda0_forces", "free_substeps", "lambda_m", "link_substeps",
                                                     "corrections"], [round(x, 3) for x in i1["last_round_ms"]])),
                    "interface_rebuilds_in_timed_rounds": timed_rebuilds,
-                   "per_instance_loop_value": solo_value, "batch_over_loop": value / solo_value},
-        "coarse_steps_per_s": d["coarse_steps"] / (batch_ms * 1e-3),
+                   "per_instance_loop_value": solo_value, "batch_over_loop": own_value / solo_value},
+        "coarse_steps_per_s": coarse_total / (batch_ms * 1e-3),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": None, "peak_kind": peak_kind, "kernel": "k_pd_step_lattice2d_batch (whole round)",
                      "algorithmic_bytes_per_step": sub_bytes / args.steps},

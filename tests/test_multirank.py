@@ -50,3 +50,15 @@ def test_reference_arm_other_ranks_do_no_work(monkeypatch):
         steps, warmup, gpus = 2, 1, 2
     bench.run_reference(A(), rank=1, world=2)
     assert not called
+
+
+@pytest.mark.parametrize("world", [1, 2, 3, 4, 8])
+def test_batch_shards_partition_the_members(world):
+    """The independent plates of the batched workload are sharded over the
+    ranks: every member on exactly one rank, shard sizes within one."""
+    import bench
+    n = 64
+    shards = [bench.shard(n, r, world) for r in range(world)]
+    flat = sorted(i for s in shards for i in s)
+    assert flat == list(range(n))
+    assert max(map(len, shards)) - min(map(len, shards)) <= 1
