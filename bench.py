@@ -1,6 +1,7 @@
 """Benchmark of the MTS-coupled PD hot path (bond updates/s, HBM roofline).
 
-python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload coupled|pd]
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                [--workload coupled|pd|coupled3d|batch] [--accuracy-steps S] [--lattice-tile T]
 
 Default workload (coupled): the fine coupled plate, 0.1 x 0.04 m with a 50 mm
 edge pre-crack, a 20 mm PD strip at 0.05 mm (2000 x 400 = 800,000 PD nodes,
@@ -12,7 +13,14 @@ substeps. `value` counts every PD bond update (free and link substeps) per
 second of device time; coarse steps/s is reported beside it.
 
 --workload pd: the same 800,000-node lattice as a pure PD plate (traction as a
-body force on its faces), 20 substeps per step.
+body force on its faces), 20 substeps per step. --workload coupled3d: the 3D
+coupled plate (400 x 64 x 8 PD nodes, Hex8 FE, m = 10). --workload batch: 64
+seeded coupled plates of uneven size and m, one round per step.
+
+Beside the timed figures the line reports the stated error of FP32-bulk
+against the FP64 path on the same workload (displacement rel-L2, bond-status
+mismatch, crack-tip error) and the FP64 form's rate with its FP64-ALU
+roofline.
 
 Inputs are seeded synthetic data resident in HBM before the timed region; L2
 is flushed between timed steps. --impl reference times the FP64 CPU oracle
