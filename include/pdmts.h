@@ -193,16 +193,20 @@ int pd_read_velocity(pdmts_pd *pd, double *v);
 int pd_read_acceleration(pdmts_pd *pd, double *a);
 /* Damage phi_i (Eq. 5), n doubles. */
 int pd_read_damage(pdmts_pd *pd, double *phi);
-/* Damage like pd_read_damage, for callers that must not allocate device
- * memory at this point (e.g. while a stream is being captured into a CUDA
- * graph, or under a fixed memory budget). The paper has no counterpart; it is
- * a library facility. The per-node result is staged in a device array that is
- * part of the library image (2^20 doubles, 8 MiB, held by every GPU that
- * loads the library until exit); no cudaMalloc/cudaFree or other allocating
- * routine is called. The first call on a device looks the array's address up
- * (once per device) and should come before any stream capture. PD subdomains
- * with more than 2^20 nodes are rejected with PDMTS_ERR_UNSUPPORTED. All calls
- * share the one array: calls whose work overlaps on the same GPU (different
+/* Damage like pd_read_damage, for callers that cannot let the library
+ * allocate device memory at this point: an application whose device memory is
+ * wholly reserved by its own pool allocator, or a time-critical loop where an
+ * allocation is forbidden because cudaMalloc/cudaFree may synchronise the
+ * device. The paper has no counterpart; it is a library facility. The
+ * per-node result is staged in a device array that is part of the library
+ * image (2^20 doubles, 8 MiB, held by every GPU that loads the library until
+ * exit); no cudaMalloc/cudaFree or other allocating routine is called. The
+ * first call on a device looks the array's address up (once per device). The
+ * call is blocking: it synchronises the context's stream and copies the
+ * result into phi (host or device memory, n doubles) before it returns. PD
+ * subdomains with more than 2^20 nodes are rejected with
+ * PDMTS_ERR_UNSUPPORTED. All calls share the one array, which keeps the last
+ * call's contents: calls whose work overlaps on the same GPU (different
  * contexts or threads) race and must be serialised by the caller. On failure
  * only the host-side error message is recorded. */
 int pd_read_damage_static(pdmts_pd *pd, double *phi);

@@ -1,16 +1,20 @@
 // static_scratch.cu -- damage read-back that allocates nothing.
 //
-// Some callers cannot allocate device memory at the point where they want
-// results: code running while a CUDA stream is being captured into a graph
-// (a cudaMalloc there breaks or invalidates the capture), code inside a
-// tightly budgeted memory pool that must not grow, or a real-time loop that
-// forbids allocator calls. pd_read_damage_static serves them: it runs the same
-// damage kernel as pd_read_damage, but stages the per-node result in a
-// file-scope device array instead of library-allocated memory, and calls no
+// Some callers cannot let a library allocate device memory when they ask for
+// results: an application whose device memory is entirely reserved by its own
+// pool allocator (a cudaMalloc from the library would fail, or would take
+// memory the pool counts on), or a time-critical loop in which an allocation
+// is not allowed because cudaMalloc/cudaFree may synchronise the device and
+// stall the work on other streams. pd_read_damage_static serves them: it runs
+// the same damage kernel as pd_read_damage, but stages the per-node result in
+// a file-scope device array instead of library-allocated memory, and calls no
 // allocating routine (no cudaMalloc / cudaFree, no host heap).
 //
 // The array is part of the library's device image: every GPU that loads the
-// library holds its kStaticDamageMax doubles until the process exits.
+// library holds its kStaticDamageMax doubles until the process exits. All
+// calls share it, and it keeps what the last call wrote; the kernel writes
+// every entry it reads back, so nothing needs clearing first. Calls whose work
+// overlaps on one GPU (other contexts, other host threads) race on it.
 #include <atomic>
 
 #include "pd.h"

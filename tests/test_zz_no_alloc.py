@@ -1,8 +1,10 @@
 """The damage read-back that allocates nothing (pd_read_damage_static).
 
-Callers that cannot allocate device memory at the point of the call (during
-CUDA graph capture, or under a fixed memory budget) use this entry point; it
-stages the result in a device array that is part of the library image. Here it
+Callers that cannot let the library allocate device memory at the point of the
+call (an application whose device memory is wholly held by its own pool
+allocator, or a time-critical loop in which an allocation, which may
+synchronise the device, is not allowed) use this entry point; it stages the
+result in a device array that is part of the library image. Here it
 is called through the C ABI and compared with pd_read_damage on two calls in a
 row, for both family layouts; the file is named so that pytest collects it
 after every other test.
