@@ -137,10 +137,13 @@ def algorithmic_bytes(info, pb, with_body=True, coupled=False):
     return 4 * nb + nb / 8.0 + per_node * n, per_node
 
 
-def oracle_sample(pb, nsub, setup=None):
-    """Time `nsub` oracle substeps on this workload (FP64, plain C, one core)."""
+def oracle_sample(pb, nsub, setup=None, threads=1):
+    """Time `nsub` oracle substeps on this workload (FP64, plain C) on `threads`
+    host threads (0: every core; the same bits for any count). Returns (rate,
+    seconds, setup, threads used)."""
     import oracle
     if setup is None:
+        oracle.set_threads(1)
         rp, col = oracle.family(pb.lat.X, pb.delta)
         mu, _ = oracle.precrack(pb.lat.P, rp, col, [c.in_half_units(pb.lat) for c in pb.cuts])
         opd = oracle.PD(pb.lat.X, pb.vol, pb.delta, pb.c, pb.s0, pb.mat.rho, pb.dt)
@@ -148,10 +151,29 @@ def oracle_sample(pb, nsub, setup=None):
         oracle.pd_run(opd, rp, col, mu, u, v, a, 0, b=pb.b, init=True)
         setup = (rp, col, mu, opd, u, v, a)
     rp, col, mu, opd, u, v, a = setup
+    used = oracle.set_threads(threads)
     t0 = time.perf_counter()
     oracle.pd_run(opd, rp, col, mu, u, v, a, nsub, b=pb.b)
     dt = time.perf_counter() - t0
-    return len(col) * nsub / dt, dt, setup
+    oracle.set_threads(1)
+    return len(col) * nsub / dt, dt, setup, used
+
+
+def cpu_baseline(workload, what):
+    """The FP64 oracle timed on this host on a bounded sample of the workload's
+    PD lattice: 20 substeps on one core, then on every core (OpenMP over nodes,
+    identical bits) as many substeps as take about as long. The line's value
+    is the all-core rate; the one-core rate is kept beside it."""
+    _, rpb = reference_problem(workload)
+    r1, dt1, setup, _ = oracle_sample(rpb, 20)
+    probe, tp, setup, cores = oracle_sample(rpb, 2, setup, threads=0)
+    nsub = max(2, min(400, int(round(2 * dt1 / max(tp, 1e-6)))))
+    rn, dtn, setup, cores = oracle_sample(rpb, nsub, setup, threads=0)
+    return {"value": rn, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{nsub} FP64 oracle PD substeps of {what} ({rpb.n} nodes) on {cores} host threads "
+                      f"({dtn:.1f} s; the PD substeps only)",
+            "single_core": {"value": r1, "unit": UNIT, "cores": 1,
+                            "sample": f"20 substeps of the same lattice on one thread ({dt1:.1f} s)"}}
 
 
 def reference_problem(workload):
@@ -177,20 +199,20 @@ def run_reference(args, rank, world):
     nsub = 2
     setup = None
     for _ in range(args.warmup):
-        _, _, setup = oracle_sample(pb, nsub, setup)
+        _, _, setup, cores = oracle_sample(pb, nsub, setup, threads=0)
     total_t, total_u = 0.0, 0
     for _ in range(args.steps):
-        rate, dt, setup = oracle_sample(pb, nsub, setup)
+        rate, dt, setup, cores = oracle_sample(pb, nsub, setup, threads=0)
         total_t += dt
         total_u += len(setup[1]) * nsub
     value = total_u / total_t
-    sample = (f"{nsub} FP64 oracle PD substeps per step of the workload's {pb.n}-node PD lattice "
-              f"(the PD substeps only: no FE step or interface solve)")
+    sample = (f"{nsub} FP64 oracle PD substeps per step of the workload's {pb.n}-node PD lattice on {cores} "
+              f"host threads (the PD substeps only: no FE step or interface solve)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": name, "pd_nodes": pb.n, "directed_bonds": len(setup[1])},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -246,10 +268,25 @@ def make_coupled(P, ctx, cp, precision=None):
 BATCH_NAME = "batch_{n}_coupled_plates_seed3605_pd20k-400k_m5-10-20_fp32bulk"
 
 
-def shard(n, rank, world):
-    """Indices of the independent members rank `rank` of `world` advances
-    (round robin over the seeded member list; the shards partition it)."""
-    return list(range(rank, n, world))
+def shard(work, rank, world):
+    """Indices of the independent members rank `rank` of `world` advances.
+    `work` holds each member's work per round (PD nodes x m). Largest first,
+    each member goes to the rank with the least work so far (lowest rank on a
+    tie), so the shards partition the members with balanced work; the job's
+    time is the slowest rank's."""
+    load = [0.0] * world
+    mine = []
+    for i in sorted(range(len(work)), key=lambda k: (-work[k], k)):
+        r = min(range(world), key=lambda q: (load[q], q))
+        load[r] += work[i]
+        if r == rank:
+            mine.append(i)
+    return sorted(mine)
+
+
+def member_work(cp):
+    """PD node updates of one member per round (its m free and m link substeps)."""
+    return float(cp.pd.n) * 2 * cp.m
 
 
 def run_batch(args, rank, world, local_rank):
@@ -271,7 +308,7 @@ def run_batch(args, rank, world, local_rank):
     stream = torch.cuda.current_stream(dev)
     t_setup = time.perf_counter()
     all_cps = W.batch_plates(n=args.batch_members)
-    cps = [all_cps[i] for i in shard(len(all_cps), rank, world)]
+    cps = [all_cps[i] for i in shard([member_work(cp) for cp in all_cps], rank, world)]
     ctxs, handles = [], []
     for cp in cps:
         ctx = P.pdmts_ctx_create(local_rank, stream.cuda_stream)
@@ -351,12 +388,7 @@ def run_batch(args, rank, world, local_rank):
         return
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        nsub = 20
-        _, rpb = reference_problem("batch")
-        rate, dt, _ = oracle_sample(rpb, nsub)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{nsub} FP64 oracle PD substeps of an {rpb.n}-node plate of the same kind ({dt:.1f} s; "
-                         f"the PD substeps only)"}
+        cpu = cpu_baseline("batch", "a plate of the same kind")
     nodes = sum(cp.pd.n for cp in all_cps)
     ms_mix = sorted({cp.m for cp in all_cps})
     # algorithmic bytes of rank 0's PD substeps of the timed rounds (100 B per node and
@@ -370,7 +402,7 @@ def run_batch(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": batch_ms / args.steps, "higher_is_better": True,
         "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": BATCH_NAME.format(n=len(all_cps)), "members": len(all_cps),
-                   "members_per_rank": "round robin" if world > 1 else len(cps), "pd_nodes_total": nodes,
+                   "members_per_rank": "balanced by PD nodes x m" if world > 1 else len(cps), "pd_nodes_total": nodes,
                    "m_values": ms_mix, "step": "one round = one coarse step of every member",
                    "lattice_tile": info["lattice_tile"], "batched_launches_per_round":
                    (i1["batched_launches"] - i0["batched_launches"]) // max(args.steps, 1),
@@ -507,12 +539,7 @@ def run_ours(args, rank, world, local_rank):
     # ---- CPU baseline: the FP64 oracle on a bounded sample ----------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        nsub = 20
-        _, rpb = reference_problem(args.workload)
-        rate, dt, _ = oracle_sample(rpb, nsub)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{nsub} FP64 oracle PD substeps of the workload's {rpb.n}-node PD lattice ({dt:.1f} s; "
-                         f"the PD substeps only)"}
+        cpu = cpu_baseline(args.workload, "the workload's PD lattice")
 
     if rank == 0:
         cfg = {"workload": (COUPLED3D_NAME if args.workload == "coupled3d" else COUPLED_NAME) if coupled

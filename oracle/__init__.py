@@ -20,7 +20,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liborc.so")
-_SOURCES = ["pd_oracle.c", "mts_oracle.c"]
+_SOURCES = ["pd_oracle.c"]
 _lock = threading.Lock()
 _lib = None
 
@@ -37,9 +37,12 @@ def build(force: bool = False) -> str:
         if os.path.getmtime(_LIB) >= newest:
             return _LIB
     tmp = _LIB + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-           "-o", tmp, *srcs, "-lm"]
-    subprocess.run(cmd, check=True, cwd=_HERE)
+    base = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-o", tmp]
+    # OpenMP spreads the node loops over host threads (same bits for any count);
+    # without it the oracle runs on one thread
+    r = subprocess.run([*base, "-fopenmp", *srcs, "-lm"], cwd=_HERE, capture_output=True, text=True)
+    if r.returncode != 0:
+        subprocess.run([*base, *srcs, "-lm"], check=True, cwd=_HERE)
     os.replace(tmp, _LIB)
     return _LIB
 
@@ -80,9 +83,15 @@ def _declare(L):
     L.orc_strain_energy.restype = C.c_double
     L.orc_kinetic_energy.argtypes = [C.POINTER(PDParams), _P, _P, _P]
     L.orc_kinetic_energy.restype = C.c_double
-    if hasattr(L, "orc_mts_declare_marker"):
-        from . import mts as _mts  # noqa: F401  (declares the MTS entry points)
-        _mts._declare(L)
+    L.orc_set_threads.argtypes = [C.c_int]
+    L.orc_set_threads.restype = C.c_int
+    L.orc_set_threads(1)
+
+
+def set_threads(n: int) -> int:
+    """Host threads of the oracle's node loops (n <= 0: every core). The result
+    does not depend on it. Returns the count in effect (1 without OpenMP)."""
+    return int(lib().orc_set_threads(int(n)))
 
 
 def _ptr(a):

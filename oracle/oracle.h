@@ -25,6 +25,7 @@ typedef struct {
     double dt;          /* time step */
 } orc_pd_params;
 
+int orc_set_threads(int n);  /* host threads of the node loops (n <= 0: all); returns the count */
 int orc_family(int dim, int64_t n, const double *X, double delta, int64_t *row_ptr, int32_t *col);
 int64_t orc_precrack(int dim, int64_t n, const int64_t *P, const int64_t *row_ptr,
                      const int32_t *col, int ncut, const int64_t *cut, uint8_t *mu);

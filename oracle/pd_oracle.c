@@ -49,6 +49,29 @@
 
 #include "oracle.h"
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ------------------------------------------------------------------------ */
+/* Host threads.  The node loops below may run on several threads: node i    */
+/* reads u, X, V and alpha and writes only its own row of mu and its own      */
+/* force, so the result does not depend on the thread count.  The default is  */
+/* one thread; the benchmark's CPU baseline asks for every core.             */
+/* ------------------------------------------------------------------------ */
+static int g_threads = 1;
+
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    g_threads = n > 0 ? n : omp_get_num_procs();
+#else
+    (void)n;
+    g_threads = 1;
+#endif
+    return g_threads;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Micromodulus c(|xi|) (Eq. 2 with the readings above).                     */
 /* ------------------------------------------------------------------------ */
@@ -222,6 +245,7 @@ int64_t orc_pd_forces(const orc_pd_params *p, const double *X, const double *V,
     const int64_t n = p->n;
     const double s0p2 = (1.0 + p->s0) * (1.0 + p->s0);
     int64_t newly = 0;
+#pragma omp parallel for schedule(static) reduction(+ : newly) num_threads(g_threads)
     for (int64_t i = 0; i < n; ++i) {
         double fi[3] = {0.0, 0.0, 0.0};
         double ai = alpha ? alpha[i] : 0.0;

@@ -55,10 +55,15 @@ def test_reference_arm_other_ranks_do_no_work(monkeypatch):
 @pytest.mark.parametrize("world", [1, 2, 3, 4, 8])
 def test_batch_shards_partition_the_members(world):
     """The independent plates of the batched workload are sharded over the
-    ranks: every member on exactly one rank, shard sizes within one."""
+    ranks: every member on exactly one rank, and the work (PD nodes x m per
+    round) balanced so that the slowest rank, which sets the job's time,
+    carries little more than its share."""
     import bench
-    n = 64
-    shards = [bench.shard(n, r, world) for r in range(world)]
+    from paper_2403_03605_gb300 import workloads as W
+    work = [float(N) * 2 * m for N, _, _, m in W.batch_plates_draws(3605, 64)]
+    shards = [bench.shard(work, r, world) for r in range(world)]
     flat = sorted(i for s in shards for i in s)
-    assert flat == list(range(n))
-    assert max(map(len, shards)) - min(map(len, shards)) <= 1
+    assert flat == list(range(64))
+    loads = [sum(work[i] for i in s) for s in shards]
+    assert max(loads) <= 1.02 * sum(work) / world
+    assert max(loads) / min(loads) <= 1.04

@@ -381,3 +381,25 @@ def test_damage_definition():
     mu = np.array([1, 0, 1, 1, 0, 0, 1, 1, 1, 1], np.uint8)
     phi = oracle.damage(pd, rp, col, mu)
     np.testing.assert_allclose(phi, [1 - 2 / 5, 1 - 4 / 8, 1 - 6 / 7, 0.0], rtol=0, atol=1e-15)
+
+
+def test_host_threads_give_the_same_bits():
+    """The oracle's node loops on several host threads (each node writes only its
+    own bond row and force) reproduce the one-thread run bit for bit, breaking
+    included: the all-core CPU baseline times the same computation."""
+    pb = W.small_plate(48, 30, nsteps=150)
+    rp, col = oracle.family(pb.lat.X, pb.delta)
+    cut = [c.in_half_units(pb.lat) for c in pb.cuts]
+    runs = []
+    for threads in (1, 4):
+        assert oracle.set_threads(threads) in (1, threads)
+        mu, _ = oracle.precrack(pb.lat.P, rp, col, cut)
+        opd = oracle.PD(pb.lat.X, pb.vol, pb.delta, pb.c, pb.s0, MAT.rho, pb.dt)
+        u = np.zeros((2, pb.n)); v = np.zeros_like(u); a = np.zeros_like(u)
+        nb = oracle.pd_run(opd, rp, col, mu, u, v, a, pb.nsteps, b=pb.b, init=True)
+        runs.append((u, v, a, mu, nb))
+    oracle.set_threads(1)
+    (u1, v1, a1, m1, n1), (u4, v4, a4, m4, n4) = runs
+    assert n1 == n4 and n1 > 0
+    for x, y in ((u1, u4), (v1, v4), (a1, a4), (m1, m4)):
+        assert np.array_equal(x, y)
