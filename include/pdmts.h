@@ -354,6 +354,20 @@ int mts_batch_info(const pdmts_batch *batch, pdmts_batch_info *info);
  * alone. NULL is a no-op. */
 int mts_batch_destroy(pdmts_batch *batch);
 
+/* Test facility for the failure path of the bounded device-side waits. The
+ * lattice kernels that stage a tile's inputs by tensor copies wait on
+ * mbarriers with a poll limit (2^21 polls of at most ~1 us each); a wait that
+ * gives up makes its tile skip all writes and raises a device flag. This call
+ * sets the limit of each tile's first wait to `polls` (0: give up at once;
+ * negative: restore the default); the waits that drain the tile's copies
+ * before it returns keep the full limit, so no copy is in flight when a tile
+ * ends. After a give-up the substep's result is undefined: mts_advance,
+ * mts_batch_advance, the read-backs, pdmts_get_stats and mts_state_save of
+ * that context return PDMTS_ERR_TIMEOUT (the advance once the flag has
+ * reached the host, at the latest after the next blocking call) until
+ * mts_state_load loads a checkpoint image. Not part of the method; for tests. */
+int pdmts_set_debug_poll_limit(pdmts_ctx *ctx, int64_t polls);
+
 /* Counters since context creation. */
 typedef struct {
     int64_t pd_substeps;      /* PD substeps (free + link)                */

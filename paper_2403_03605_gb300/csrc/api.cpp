@@ -93,6 +93,31 @@ int pdmts_ctx::end()
     return PDMTS_OK;
 }
 
+int pdmts_ctx::watch_enqueue(cudaStream_t s)
+{
+    PDMTS_CUDA_TRY(cudaMemcpyAsync(h_watch, d_counter + 2, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    return PDMTS_OK;
+}
+
+int pdmts_ctx::watch_check(const char *who)
+{
+    if (!gave_up && __atomic_load_n(h_watch, __ATOMIC_ACQUIRE) != 0)
+        gave_up = true;
+    if (gave_up)
+        return fail(PDMTS_ERR_TIMEOUT,
+                    "%s: a bounded tensor-copy wait of the lattice kernel gave up; the state is undefined "
+                    "(load a checkpoint image with mts_state_load to continue)",
+                    who);
+    return PDMTS_OK;
+}
+
+int pdmts_ctx::sync_checked(const char *who)
+{
+    PDMTS_TRY(watch_enqueue(stream));
+    PDMTS_CUDA_TRY(cudaStreamSynchronize(stream));
+    return watch_check(who);
+}
+
 int pdmts_ctx::pool_event(cudaEvent_t *e)
 {
     if (ev_pool.empty()) {
@@ -140,6 +165,22 @@ extern "C" int pdmts_set_timing(pdmts_ctx *ctx, int enabled)
     if (!ctx)
         return fail(PDMTS_ERR_ARG, "pdmts_set_timing: ctx is NULL");
     ctx->timing = enabled != 0;
+    return PDMTS_OK;
+}
+
+extern int pd_invalidate_graphs(pdmts_pd *pd);  // pd_kernels.cu
+
+extern "C" int pdmts_set_debug_poll_limit(pdmts_ctx *ctx, int64_t polls)
+{
+    clear_error();
+    if (!ctx)
+        return fail(PDMTS_ERR_ARG, "pdmts_set_debug_poll_limit: ctx is NULL");
+    const unsigned lim = polls < 0 ? kWaitPolls : (unsigned)std::min<int64_t>(polls, kWaitPolls);
+    if (lim != ctx->first_wait_polls) {
+        ctx->first_wait_polls = lim;
+        if (ctx->pd)
+            pd_invalidate_graphs(ctx->pd);  // captured chains hold the launch arguments
+    }
     return PDMTS_OK;
 }
 
@@ -215,11 +256,13 @@ extern "C" int pdmts_ctx_create(pdmts_ctx **ctx, int device, void *cuda_stream)
     if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming) != cudaSuccess ||
-        cudaMalloc(&c->d_counter, 64) != cudaSuccess) {
+        cudaMalloc(&c->d_counter, 64) != cudaSuccess ||
+        cudaMallocHost(&c->h_watch, 64) != cudaSuccess) {
         cudaGetLastError();
         pdmts_ctx_destroy(c);
         return fail(PDMTS_ERR_CUDA, "pdmts_ctx_create: stream/event/counter creation failed");
     }
+    std::memset(c->h_watch, 0, 64);
     if (cudaMemset(c->d_counter, 0, 64) != cudaSuccess) {
         pdmts_ctx_destroy(c);
         return fail(PDMTS_ERR_CUDA, "pdmts_ctx_create: memset failed");
@@ -243,6 +286,8 @@ extern "C" int pdmts_ctx_destroy(pdmts_ctx *ctx)
         pd_destroy(ctx->pd);
     if (ctx->d_counter)
         cudaFree(ctx->d_counter);
+    if (ctx->h_watch)
+        cudaFreeHost(ctx->h_watch);
     for (auto &m : ctx->ev_marks) {
         ctx->ev_pool.push_back(m.first);
         ctx->ev_pool.push_back(m.second);
@@ -294,7 +339,8 @@ extern "C" int pdmts_get_stats(pdmts_ctx *ctx, pdmts_stats *stats)
     unsigned long long word[3] = {0, 0, 0};
     PDMTS_CUDA_TRY(cudaMemcpy(word, ctx->d_counter, sizeof(word), cudaMemcpyDeviceToHost));
     if (word[2])
-        return fail(PDMTS_ERR_CUDA, "pdmts_get_stats: a tensor-copy wait of the lattice kernel gave up");
+        ctx->gave_up = true;
+    PDMTS_TRY(ctx->watch_check("pdmts_get_stats"));
     ctx->stats.bonds_broken = (int64_t)word[0];
     *stats = ctx->stats;
     return PDMTS_OK;
@@ -970,6 +1016,7 @@ pdmts::Lat2DArgs pdmts_pd::lattice_args(const pdmts::F32NodeArgs &N, uint32_t *m
     A.qthr = (float)(s0 * (2.0 + s0));
     A.tile = link && link_tile >= 0 ? link_tile : lattice_tile >= 0 ? lattice_tile : 0;
     A.num_sms = ctx->num_sms;
+    A.first_polls = ctx->first_wait_polls;
     A.nd = N;
     const bool grow = link && chain_k >= 0 && chain_k < (int)link_step_win.size();
     for (int w = 0; w < 2; ++w) {
@@ -1668,7 +1715,7 @@ static int read_field(pdmts_pd *pd, int which, double *out)
         src = pd->d_out.p;
     }
     PDMTS_CUDA_TRY(cudaMemcpyAsync(out, src, sizeof(double) * m, cudaMemcpyDefault, s));
-    PDMTS_CUDA_TRY(cudaStreamSynchronize(s));
+    PDMTS_TRY(pd->ctx->sync_checked("pd_read"));
     return pd->ctx->end();
 }
 
@@ -1706,7 +1753,7 @@ extern "C" int pd_read_damage(pdmts_pd *pd, double *phi)
         return fail(PDMTS_ERR_CUDA, "damage kernel failed: %s", cudaGetErrorString(e));
     pd->ctx->stats.kernel_launches++;
     PDMTS_CUDA_TRY(cudaMemcpyAsync(phi, pd->d_out.p, sizeof(double) * pd->n, cudaMemcpyDefault, s));
-    PDMTS_CUDA_TRY(cudaStreamSynchronize(s));
+    PDMTS_TRY(pd->ctx->sync_checked("pd_read_damage"));
     return pd->ctx->end();
 }
 
@@ -1720,7 +1767,7 @@ extern "C" int pd_read_bond_status(pdmts_pd *pd, uint8_t *mu, int64_t *n_intact)
     cudaStream_t s = pd->ctx->stream;
     PDMTS_CUDA_TRY(cudaMemcpyAsync(pd->mask_host.data(), pd->d_mask.p, sizeof(uint32_t) * pd->n_mask_words,
                                    cudaMemcpyDeviceToHost, s));
-    PDMTS_CUDA_TRY(cudaStreamSynchronize(s));
+    PDMTS_TRY(pd->ctx->sync_checked("pd_read_bond_status"));
     std::vector<uint8_t> st((size_t)pd->row_ptr[(size_t)pd->n]);
     int64_t intact = 0;
     for (int64_t i = 0; i < pd->n; ++i) {
@@ -1818,8 +1865,11 @@ extern "C" int mts_advance(pdmts_ctx *ctx, int64_t n_coarse)
         return fail(PDMTS_ERR_STATE, "mts_advance: no PD subdomain");
     if (!ctx->time_set)
         return fail(PDMTS_ERR_STATE, "mts_advance: call mts_set_time first");
-    if (ctx->arl)
-        return mts_advance_coupled(ctx, n_coarse);
+    PDMTS_TRY(ctx->watch_check("mts_advance"));
+    if (ctx->arl) {
+        PDMTS_TRY(mts_advance_coupled(ctx, n_coarse));
+        return ctx->watch_enqueue(ctx->stream);
+    }
     PDMTS_CUDA_TRY(cudaSetDevice(ctx->device));
     PDMTS_TRY(ctx->begin());
     pdmts_pd *pd = ctx->pd;
@@ -1831,5 +1881,6 @@ extern "C" int mts_advance(pdmts_ctx *ctx, int64_t n_coarse)
     const int chunk = ctx->m_ratio >= 2 ? ctx->m_ratio : 16;
     PDMTS_TRY(pd_run_steps_graph(pd, nsteps, chunk, s));
     ctx->stats.coarse_steps += n_coarse;
+    PDMTS_TRY(ctx->watch_enqueue(s));
     return ctx->end();
 }

@@ -14,6 +14,10 @@
 
 namespace pdmts {
 
+// Poll limit of a bounded device-side wait on an mbarrier (each poll suspends
+// for at most ~1 us): 2^21 polls, about two seconds.
+constexpr unsigned kWaitPolls = 1u << 21;
+
 // ---------------------------------------------------------------- errors ---
 int fail(int code, const char *fmt, ...);  // records a thread-local message, returns code
 void clear_error();
@@ -147,6 +151,7 @@ struct Lat2DArgs {
     int num_sms;                // SMs of the device (persistent grids)
     int win_lo[2], win_n[2];    // optional windows in units of TY node rows (win_n[0] == 0: whole lattice)
     int pdl;                    // launch as a programmatic dependent of the previous substep kernel
+    unsigned first_polls = kWaitPolls;  // poll limit of each tile's first tensor-copy wait (tests lower it)
     F32NodeArgs nd;
 };
 
@@ -289,6 +294,16 @@ struct pdmts_ctx {
     pdmts_stats stats{};
     unsigned long long *d_counter = nullptr;  // [0] broken bonds, [1] non-finite input flag,
                                               // [2] a tensor-copy wait of the lattice kernel gave up
+    // Give-up watch: h_watch (pinned host) receives d_counter[2] by a copy
+    // queued behind each advance and before each read-back's synchronisation;
+    // once a give-up is seen the state is undefined and `gave_up` latches
+    // until a checkpoint image is loaded.
+    unsigned long long *h_watch = nullptr;
+    bool gave_up = false;
+    unsigned first_wait_polls = pdmts::kWaitPolls;  // pdmts_set_debug_poll_limit
+    int watch_enqueue(cudaStream_t s);   // queue the copy of d_counter[2] to h_watch on s
+    int watch_check(const char *who);    // PDMTS_ERR_TIMEOUT once a give-up has been seen
+    int sync_checked(const char *who);   // watch_enqueue + synchronise `stream` + watch_check
     int64_t device_bytes = 0;
     // substep-chain timing
     bool timing = false;

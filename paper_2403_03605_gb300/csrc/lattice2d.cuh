@@ -303,10 +303,13 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // The same two groups as tensor copies (cp.async.bulk.tensor) issued by one
 // thread, each completing on an mbarrier. Out-of-lattice parts of a box read
 // as zeros, like the predicated copies above. Every wait is bounded: after
-// kTmaPolls polls (each suspends for at most ~1 us) it gives up; the CTA then
-// raises counter word [2] (reported by the host as an error), waits once more
-// (bounded) for its copies and returns without touching global memory.
-constexpr unsigned kTmaPolls = 1u << 21;
+// kTmaPolls polls (each suspends for at most ~1 us; a tile's first wait takes
+// its limit from Lat2DArgs::first_polls, which only tests lower) it gives up;
+// the CTA then raises counter word [2] (reported by the host as
+// PDMTS_ERR_TIMEOUT), waits once more with the full limit for its copies and
+// returns without touching global memory. The substep's result is then
+// undefined.
+constexpr unsigned kTmaPolls = kWaitPolls;
 
 __device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void mbar_init(uint64_t *bar, const unsigned count)
@@ -318,9 +321,9 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, const unsigned byt
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
                  : "memory");
 }
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, const unsigned parity)
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, const unsigned parity, const unsigned polls = kTmaPolls)
 {
-    for (unsigned k = 0; k < kTmaPolls; ++k) {
+    for (unsigned k = 0; k < polls; ++k) {
         unsigned done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
@@ -767,7 +770,7 @@ __global__ void __launch_bounds__(256, MINB) k_pd_step_lattice2d_tma(const Lat2D
     lattice_chain_entry();
     if (threadIdx.x == 0)
         lattice_tma_issue<KR>(S, M, A, x0, y0);
-    const bool ok = mbar_wait(&S.bar[0], 0);
+    const bool ok = mbar_wait(&S.bar[0], 0, A.first_polls);
     if (__syncthreads_or(!ok)) {
         tma_gave_up(A);
         mbar_wait(&S.bar[0], 0);
@@ -817,7 +820,7 @@ __global__ void __launch_bounds__(256, MINB) k_pd_step_lattice2d_tpipe(const Lat
     for (int t = blockIdx.x; t < ntiles; t += G, ++k) {
         LatStage<KR> &S = stages[k & 1];
         const unsigned par = (unsigned)(k >> 1) & 1u;
-        const bool ok = mbar_wait(&S.bar[0], par);
+        const bool ok = mbar_wait(&S.bar[0], par, A.first_polls);
         if (__syncthreads_or(!ok)) {  // give up: let this tile's and the other stage's copies land first
             tma_gave_up(A);
             mbar_wait(&S.bar[0], par);

@@ -1305,7 +1305,7 @@ static int fem_read(pdmts_fem *fe, int which, double *out)
     PDMTS_TRY(fe->ctx->begin());
     const double *src = which == 0 ? fe->d_u.p : which == 1 ? fe->d_v.p : fe->d_a.p;
     PDMTS_CUDA_TRY(cudaMemcpyAsync(out, src, sizeof(double) * fe->ndof(), cudaMemcpyDefault, fe->ctx->stream));
-    PDMTS_CUDA_TRY(cudaStreamSynchronize(fe->ctx->stream));
+    PDMTS_TRY(fe->ctx->sync_checked("fem_read"));
     return fe->ctx->end();
 }
 extern "C" int fem_set_state(pdmts_fem *fe, const double *u, const double *v)
@@ -3042,9 +3042,13 @@ extern "C" int mts_batch_advance(pdmts_batch *b, int64_t n_rounds)
     }
     if (b->members.empty())
         return PDMTS_OK;
+    for (pdmts_ctx *c : b->members)
+        PDMTS_TRY(c->watch_check("mts_batch_advance"));
     PDMTS_TRY(batch_tune(b));
     for (int64_t k = 0; k < n_rounds; ++k)
         PDMTS_TRY(batch_round(b));
+    for (pdmts_ctx *c : b->members)
+        PDMTS_TRY(c->watch_enqueue(b->s));
     // the users' streams follow the batch; a member's own stream follows its
     // user stream when the member is next used alone
     PDMTS_CUDA_TRY(cudaEventRecord(b->ev_in, b->s));
@@ -3127,7 +3131,7 @@ extern "C" int arlequin_read_lambda(pdmts_arl *A, double *lam, int64_t *n_lambda
     PDMTS_CUDA_TRY(cudaSetDevice(A->ctx->device));
     PDMTS_TRY(A->ctx->begin());
     PDMTS_CUDA_TRY(cudaMemcpyAsync(lam, A->d_lam0.p, sizeof(double) * A->nlam, cudaMemcpyDefault, A->ctx->stream));
-    PDMTS_CUDA_TRY(cudaStreamSynchronize(A->ctx->stream));
+    PDMTS_TRY(A->ctx->sync_checked("arlequin_read_lambda"));
     if (n_lambda)
         *n_lambda = A->nlam;
     return A->ctx->end();
@@ -3157,7 +3161,7 @@ extern "C" int arlequin_constraint_residual(pdmts_arl *A, double *residual, doub
         PDMTS_CUDA_TRY(cudaMemcpyAsync(pass == 0 ? y.data() : yf.data(), A->d_y.p, sizeof(double) * A->nlam,
                                        cudaMemcpyDeviceToHost, s));
     }
-    PDMTS_CUDA_TRY(cudaStreamSynchronize(s));
+    PDMTS_TRY(A->ctx->sync_checked("arlequin_constraint_residual"));
     double r2 = 0, f2 = 0;
     for (int64_t k = 0; k < A->nlam; ++k) {
         r2 += y[(size_t)k] * y[(size_t)k];
@@ -3300,6 +3304,7 @@ extern "C" int mts_state_save(pdmts_ctx *ctx, void *image, int64_t bytes)
         return fail(PDMTS_ERR_ARG, "mts_state_save: image of %lld bytes, the state needs %lld", (long long)bytes,
                     (long long)(sizeof(StateHeader) + h.payload_bytes));
     PDMTS_TRY(state_quiesce(ctx));
+    PDMTS_TRY(ctx->sync_checked("mts_state_save"));
     char *dst = static_cast<char *>(image);
     PDMTS_CUDA_TRY(cudaMemcpy(dst, &h, sizeof h, cudaMemcpyDefault));
     dst += sizeof h;
@@ -3345,5 +3350,10 @@ extern "C" int mts_state_load(pdmts_ctx *ctx, const void *image, int64_t bytes)
         ctx->arl->H_valid = false;  // rebuilt from the loaded bond words at the next step
         ctx->arl->flag_pending = false;
     }
+    // the loaded image replaces a state a give-up left undefined
+    PDMTS_CUDA_TRY(cudaMemsetAsync(ctx->d_counter + 2, 0, sizeof(unsigned long long), ctx->stream));
+    PDMTS_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    __atomic_store_n(ctx->h_watch, 0ull, __ATOMIC_RELEASE);
+    ctx->gave_up = false;
     return PDMTS_OK;
 }

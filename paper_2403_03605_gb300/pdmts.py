@@ -98,6 +98,7 @@ SIGNATURES = [
     ("mts_batch_info", _I, [_V, _V]),
     ("mts_batch_destroy", _I, [_V]),
     ("pdmts_set_timing", _I, [_V, _I]),
+    ("pdmts_set_debug_poll_limit", _I, [_V, _I64]),
     ("pdmts_get_timing", _I, [_V, C.POINTER(_D), C.POINTER(_I64)]),
     ("mts_get_phase_timing", _I, [_V, C.POINTER(_D), C.POINTER(_I64)]),
     ("pdmts_get_stats", _I, [_V, C.POINTER(Stats)]),
@@ -212,6 +213,12 @@ def pdmts_get_stats(ctx):
 
 def pdmts_set_timing(ctx, enabled):
     _check(load().pdmts_set_timing(ctx, int(bool(enabled))), "pdmts_set_timing")
+
+
+def pdmts_set_debug_poll_limit(ctx, polls):
+    """Poll limit of each lattice tile's first tensor-copy wait (tests of the
+    give-up path; negative restores the default)."""
+    _check(load().pdmts_set_debug_poll_limit(ctx, int(polls)), "pdmts_set_debug_poll_limit")
 
 
 def pdmts_get_timing(ctx):

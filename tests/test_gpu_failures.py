@@ -94,3 +94,42 @@ def test_non_finite_inputs_are_rejected_and_leave_the_state(fresh):
         a.run(20)
         b.run(20)  # the rejected loads left the previous ones in place
         assert np.array_equal(a.u(), b.u()) and np.array_equal(a.mu(), b.mu())
+
+
+PDMTS_ERR_TIMEOUT = -5
+
+
+def test_bounded_tensor_copy_wait_gives_up_and_recovers(fresh):
+    """A bounded wait that runs out, made without a fault: the first tensor-copy
+    wait of every lattice tile gets a poll limit of 0 (a wait that nothing can
+    satisfy in time), so each tile gives up, drains its copies with the full
+    limit and returns without writing. The next blocking call reports
+    PDMTS_ERR_TIMEOUT; advancing, the statistics and saving a checkpoint are
+    refused while the state is undefined; loading the image saved before the
+    give-up makes the context usable again, and it continues with the bits of
+    an uninterrupted run."""
+    pb = W.small_plate(48, 30, nsteps=40)  # nx % 4 == 0: the tensor-copy tile configuration applies
+    ref = GpuPDRun(fresh(), pb, P.PDMTS_FP32_BULK)
+    P.pd_set_lattice_tile(ref.pd, 5)
+    ref.run(30)
+    g = GpuPDRun(fresh(), pb, P.PDMTS_FP32_BULK)
+    P.pd_set_lattice_tile(g.pd, 5)
+    g.run(20)
+    image = P.mts_state_save(g.ctx)
+    P.pdmts_set_debug_poll_limit(g.ctx, 0)
+    P.mts_advance(g.ctx, 1)  # queued; its tiles give up on the device
+    with pytest.raises(P.PdmtsError) as e:
+        g.u()
+    assert e.value.code == PDMTS_ERR_TIMEOUT and "gave up" in str(e.value)
+    for call in (lambda: P.mts_advance(g.ctx, 1), lambda: P.pdmts_get_stats(g.ctx),
+                 lambda: P.mts_state_save(g.ctx), lambda: P.pd_read_damage(g.pd)):
+        with pytest.raises(P.PdmtsError) as e:
+            call()
+        assert e.value.code == PDMTS_ERR_TIMEOUT
+    P.pdmts_set_debug_poll_limit(g.ctx, -1)
+    P.mts_state_load(g.ctx, image)
+    g.run(10)
+    assert np.array_equal(g.u(), ref.u()) and np.array_equal(g.v(), ref.v())
+    assert np.array_equal(g.mu(), ref.mu())
+    assert P.pd_info(g.pd)["lattice_tile"] == 5
+    P.pdmts_get_stats(g.ctx)  # usable again

@@ -190,6 +190,49 @@ def test_batch_equals_each_member_alone(fresh):
         assert st["coarse_steps"] == rounds
 
 
+def _oracle_batch_members():
+    return [W.small_coupled(m=2, n_coarse=6, dx=0.25e-3),
+            W.small_coupled(m=3, n_coarse=6, dx=0.2e-3, traction=20e6),
+            W.small_coupled(m=5, n_coarse=6, dx=0.25e-3, crack=False),
+            # m = 20; its interface operator is rebuilt inside the batch (rounds 5 and 6)
+            W.small_coupled(m=20, n_coarse=6, dx=0.25e-3, traction=6e6),
+            # 70 x 14 lattice: rows not a multiple of 16 bytes of FP32 (nx % 4 != 0)
+            W.small_coupled(m=3, n_coarse=6, dx=0.02 / 70)]
+
+
+def test_batch_members_match_the_oracle(fresh):
+    """Every member of a batch of coupled plates (m = 2, 3, 5, 20; lattices of
+    80 x 16, 100 x 20 and 70 x 14 nodes; with and without a crack; one member
+    whose interface operator is rebuilt inside the batch) advanced by
+    mts_batch_advance in FP32-bulk agrees with its own FP64 oracle run of
+    Algorithm 1 within the stated FP32-bulk tolerances: PD and FE displacement
+    rel-L2 <= 1e-4, broken-bond mismatch <= 0.1 %, velocity-constraint residual
+    <= 1e-5."""
+    cps = _oracle_batch_members()
+    rounds = cps[0].n_coarse
+    oracles = [MTSOracle(cp).advance(rounds) for cp in cps]
+    members = [GpuMTS(fresh(), cp, P.PDMTS_FP32_BULK) for cp in cps]
+    assert members[4].cp.pd.lat.shape[0] % 4 != 0
+    b = P.mts_batch_create([g.ctx for g in members])
+    try:
+        P.mts_batch_advance(b, 2)
+        P.mts_batch_advance(b, rounds - 2)
+        info = P.mts_batch_info(b)
+    finally:
+        P.mts_batch_destroy(b)
+    assert info["rounds"] == rounds
+    assert oracles[3].n_rebuilds > 1 and P.arlequin_info(members[3].arl)["rebuilds"] > 1
+    for g, o in zip(members, oracles):
+        eu, ef = rel_l2(g.u(), o.u), rel_l2(g.uf(), o.uf)
+        ev, el = rel_l2(g.v(), o.v), rel_l2(g.lam(), o.lam)
+        mm = np.count_nonzero(g.mu() != o.mu) / len(o.mu)
+        print(f"batch member {g.cp.pd.lat.shape} m={g.cp.m}: rel-L2 u_pd {eu:.2e} v_pd {ev:.2e} u_fe {ef:.2e} "
+              f"lambda {el:.2e}, mismatch {mm:.2e}, broken {(o.mu == 0).sum()}")
+        assert eu <= 1e-4 and ef <= 1e-4 and ev <= 1e-3
+        assert mm <= 1e-3
+        assert g.residual() <= 1e-5
+
+
 def test_batch_rejects_unsupported_members(fresh):
     cp = W.small_coupled(m=2, n_coarse=2)
     g64 = GpuMTS(fresh(), cp, P.PDMTS_FP64)
