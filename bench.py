@@ -490,7 +490,7 @@ def run_ours(args, rank, world, local_rank):
                    "k_pd_step_lattice2d_pipe<false,2,2>", "k_pd_step_lattice2d_pipe<false,1,4>",
                    "k_pd_step_lattice2d<false,2,3,true>", "k_pd_step_lattice2d_tma<false,2,4>",
                    "k_pd_step_lattice2d_tma<false,2,3>", "k_pd_step_lattice2d_tpipe<false,2,2>",
-                   "k_pd_step_lattice2d_tpipe<false,1,4>"]
+                   "k_pd_step_lattice2d_tpipe<false,1,4>", "k_pd_step_lattice2d_tma<false,4,2>"]
     kname = (lat_kernels[tile] if info["layout"] == 1 and tile >= 0 else
              "k_pd_step_lattice3d<false,false>" if info["layout"] == 2 else f"k_pd_step_f32<{info['dim']}>")
     traffic = None

@@ -156,11 +156,15 @@ int pd_set_force_law(pdmts_pd *pd, int kind);
  * reactions through shared memory (linear force law; PMB as configuration 0);
  * 5 and 6: configurations 1 and 0 with every input of a tile staged by
  * tensor copies; 7 and 8: persistent grids with two tensor-copy stages (the
- * next tiles in flight while the CTA computes), 2 and 1 nodes per thread.
- * Lattices with nx % 4 != 0 take configurations 1, 0, 0 and 1 for 5 to 8.
- * Other layouts and precisions ignore the setting. PDMTS_ERR_ARG if out of
- * range. */
-#define PDMTS_LATTICE_TILES 9
+ * next tiles in flight while the CTA computes), 2 and 1 nodes per thread;
+ * 9: tensor copies, one CTA per 32 x 32 tile, strips of 4 nodes per thread,
+ * registers for 2 CTAs per SM. Lattices with nx % 4 != 0 take the
+ * asynchronous-copy kernel of the same shape for 5 to 9 (1, 0, 0, 1 and
+ * 4-node strips). The 3D lattice layout has three configurations of its own
+ * (0, 1: blocks of 32 x 4 and 32 x 8 nodes of one z plane; AUTO times them the
+ * same way). Other layouts and precisions ignore the setting. PDMTS_ERR_ARG
+ * if out of range. */
+#define PDMTS_LATTICE_TILES 10
 #define PDMTS_LATTICE_TILE_AUTO (-1)
 int pd_set_lattice_tile(pdmts_pd *pd, int tile);
 

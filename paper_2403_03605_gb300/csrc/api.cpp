@@ -380,7 +380,7 @@ void pdmts_pd::release_all()
     release(d_mask); release(d_V); release(d_out); release(d_b); release(d_exists);
     release(d_X); release(d_cb); release(d_alpha); release(d_mass); release(d_wb); release(d_g);
     release(d_v); release(d_a); release(d_u[0]); release(d_u[1]);
-    release(d_stencil); release(f_alpha); release(f_invm); release(f_wb); release(f_g);
+    release(d_stencil); release(f_alpha); release(f_invm); release(f_wb); release(f_g); release(f_rowalpha);
     release(f_v4); release(f_v2); release(f_a);
     release(f_u4[0]); release(f_u4[1]); release(f_u2[0]); release(f_u2[1]);
     release(lk_u[0]); release(lk_u[1]); release(lk_v); release(lk_a); release(lk_g);
@@ -972,12 +972,23 @@ int pdmts_pd::upload_weights_and_loads()
             invm[(size_t)i] = (float)(1.0 / ((1.0 - (has_alpha ? alpha[(size_t)i] : 0.0)) * rho));
         PDMTS_TRY(alloc(f_invm, n));
         PDMTS_TRY(upload(f_invm, invm.data(), n, s));
+        std::vector<uint8_t> rowa;
         if (has_alpha) {
             std::vector<float> af(alpha.begin(), alpha.end());
             PDMTS_TRY(alloc(f_alpha, n));
             PDMTS_TRY(upload(f_alpha, af.data(), n, s));
+            if (layout == LAYOUT_LATTICE3D) {
+                const int64_t nx = lat_dims[0], ny = lat_dims[1];
+                rowa.assign((size_t)ny, 0);
+                for (int64_t i = 0; i < n; ++i)
+                    if (af[(size_t)i] != 0.f)
+                        rowa[(size_t)((i / nx) % ny)] = 1;
+                PDMTS_TRY(alloc(f_rowalpha, ny));
+                PDMTS_TRY(upload(f_rowalpha, rowa.data(), ny, s));
+            }
         } else {
             release(f_alpha);
+            release(f_rowalpha);
         }
         if (has_b) {
             if (!f_wb.p)
@@ -1014,6 +1025,7 @@ pdmts::Lat2DArgs pdmts_pd::lattice_args(const pdmts::F32NodeArgs &N, uint32_t *m
         A.cpmb[r2] = (float)(coef * r2 * r2);
     }
     A.qthr = (float)(s0 * (2.0 + s0));
+    A.qfast = (float)(s0 * (2.0 + s0) * (1.0 - 1.0 / 4096.0));
     A.tile = link && link_tile >= 0 ? link_tile : lattice_tile >= 0 ? lattice_tile : 0;
     A.num_sms = ctx->num_sms;
     A.first_polls = ctx->first_wait_polls;
@@ -1028,21 +1040,26 @@ pdmts::Lat2DArgs pdmts_pd::lattice_args(const pdmts::F32NodeArgs &N, uint32_t *m
 
 // Arguments of one 3D lattice substep: the per-|d|^2 constants are the ones
 // the sliced-ELL stencil table holds (same expressions, same rounding).
-pdmts::Lat3DArgs pdmts_pd::lattice3d_args(const pdmts::F32NodeArgs &N, uint32_t *mask) const
+pdmts::Lat3DArgs pdmts_pd::lattice3d_args(const pdmts::F32NodeArgs &N, uint32_t *mask, bool link) const
 {
     Lat3DArgs A{};
     A.nx = lat_dims[0];
     A.ny = lat_dims[1];
     A.nz = lat_dims[2];
     A.mask = mask;
+    A.exists = d_exists.p;
     A.alpha = f_alpha.p;
+    A.row_alpha = f_alpha.p ? f_rowalpha.p : nullptr;
     for (int r2 = 1; r2 < 10; ++r2) {
         const double xi2 = r2 * h * h;
         A.coef[r2] = (float)(micromodulus_host(this, xi2) * h * h * V[0]);
         A.thr[r2] = (float)(s0 * (2.0 + s0) * r2);
         A.rd[r2] = (float)std::sqrt((double)r2);
         A.r2[r2] = (float)r2;
+        A.ir2[r2] = (float)(1.0 / r2);
     }
+    A.qfast = (float)(s0 * (2.0 + s0) * (1.0 - 1.0 / 65536.0));
+    A.tile = link && link_tile >= 0 ? link_tile : lattice_tile >= 0 ? lattice_tile : 0;
     A.nd = N;
     return A;
 }
@@ -1052,6 +1069,8 @@ pdmts::Lat3DArgs pdmts_pd::lattice3d_args(const pdmts::F32NodeArgs &N, uint32_t 
 // the fastest. Runs once, before the first substep chain is captured.
 int pdmts_pd::tune_lattice(cudaStream_t s)
 {
+    if (layout == LAYOUT_LATTICE3D)
+        return tune_lattice3d(s);
     if (lattice_tile >= 0 || layout != LAYOUT_LATTICE2D || precision == PDMTS_FP64)
         return PDMTS_OK;
     DevArr<float4> su[2], sv;
@@ -1166,6 +1185,98 @@ int pdmts_pd::tune_lattice(cudaStream_t s)
     return PDMTS_OK;
 }
 
+// The 3D lattice tile configurations (blocks of 32 x 4 and 32 x 8 nodes) timed
+// the same way on scratch copies of the state; all give the same bits. The
+// link chains of a coupled subdomain run on the whole box and take the same
+// configuration.
+int pdmts_pd::tune_lattice3d(cudaStream_t s)
+{
+    if (lattice_tile >= 0 || precision == PDMTS_FP64)
+        return PDMTS_OK;
+    DevArr<float4> su4[2], sv4, sa;
+    DevArr<float2> su2[2], sv2;
+    DevArr<uint32_t> sm;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int best = 0;
+    float best_ms = 0.f;
+    int r = PDMTS_OK;
+    auto release_all = [&]() {
+        release(su4[0]); release(su4[1]); release(sv4); release(sa); release(su2[0]); release(su2[1]);
+        release(sv2); release(sm);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    };
+    if ((r = alloc(su4[0], n)) != PDMTS_OK || (r = alloc(su4[1], n)) != PDMTS_OK ||
+        (r = alloc(su2[0], n)) != PDMTS_OK || (r = alloc(su2[1], n)) != PDMTS_OK || (r = alloc(sv4, n)) != PDMTS_OK ||
+        (r = alloc(sv2, n)) != PDMTS_OK || (r = alloc(sa, n)) != PDMTS_OK || (r = alloc(sm, n_mask_words)) != PDMTS_OK) {
+        release_all();
+        return r;
+    }
+    cudaError_t e = cudaMemcpyAsync(su4[0].p, f_u4[cur].p, sizeof(float4) * n, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(su2[0].p, f_u2[cur].p, sizeof(float2) * n, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(sv4.p, f_v4.p, sizeof(float4) * n, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(sv2.p, f_v2.p, sizeof(float2) * n, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(sa.p, f_a.p, sizeof(float4) * n, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(sm.p, d_mask.p, sizeof(uint32_t) * n_mask_words, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaEventCreate(&e0);
+    if (e == cudaSuccess)
+        e = cudaEventCreate(&e1);
+    F32NodeArgs N{};
+    N.n = n;
+    N.inv_m = f_invm.p;
+    N.wb = f_wb.p;
+    N.g = has_g ? f_g.p : nullptr;
+    N.v4 = sv4.p;
+    N.v2 = sv2.p;
+    N.a = reinterpret_cast<float *>(sa.p);
+    N.dt = (float)ctx->dt_pd;
+    N.hdt = (float)(0.5 * ctx->dt_pd);
+    N.hdt2 = (float)(0.5 * ctx->dt_pd * ctx->dt_pd);
+    N.breaking = breaking ? 1 : 0;
+    N.pmb = force_kind == PDMTS_FORCE_PMB;
+    N.broken = nullptr;
+    for (int t = 0; t < kLat3DTiles && e == cudaSuccess; ++t) {
+        Lat3DArgs A = lattice3d_args(N, sm.p, false);
+        A.tile = t;
+        int c = 0;
+        for (int k = 0; k < 12 && e == cudaSuccess; ++k) {
+            if (k == 2)
+                e = cudaEventRecord(e0, s);
+            A.nd.u4_in = su4[c].p;
+            A.nd.u2_in = su2[c].p;
+            A.nd.u4_out = su4[1 - c].p;
+            A.nd.u2_out = su2[1 - c].p;
+            if (e == cudaSuccess)
+                e = launch_pd_step_lattice3d(A, false, s);
+            c = 1 - c;
+        }
+        if (e == cudaSuccess)
+            e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess)
+            e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess)
+            e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && (t == 0 || ms < best_ms)) {
+            best = t;
+            best_ms = ms;
+        }
+    }
+    release_all();
+    if (e != cudaSuccess)
+        return fail(PDMTS_ERR_CUDA, "3D lattice autotune: %s", cudaGetErrorString(e));
+    lattice_tile = best;
+    link_tile = -1;
+    pd_invalidate_graphs(this);
+    return PDMTS_OK;
+}
+
 // Per-node arguments of one FP32-bulk substep at the current buffer parity.
 F32NodeArgs pdmts_pd::f32_node_args(bool init, double theta, bool link) const
 {
@@ -1249,7 +1360,7 @@ int pdmts_pd::step(bool init, double theta, cudaStream_t s, bool link)
             A.pdl = chain_follow ? 1 : 0;
             e = launch_pd_step_lattice2d(A, init, s);
         } else if (layout == LAYOUT_LATTICE3D) {
-            Lat3DArgs A = lattice3d_args(N, mask);
+            Lat3DArgs A = lattice3d_args(N, mask, link);
             A.pdl = chain_follow ? 1 : 0;
             e = launch_pd_step_lattice3d(A, init, s);
         } else {
@@ -1659,8 +1770,9 @@ extern "C" int pd_set_lattice_tile(pdmts_pd *pd, int tile)
     clear_error();
     if (!pd)
         return fail(PDMTS_ERR_ARG, "pd_set_lattice_tile: pd is NULL");
-    if (tile != PDMTS_LATTICE_TILE_AUTO && (tile < 0 || tile >= kLatTiles))
-        return fail(PDMTS_ERR_ARG, "pd_set_lattice_tile: tile %d outside [0, %d) and not AUTO", tile, kLatTiles);
+    const int ntiles = pd->layout == pdmts_pd::LAYOUT_LATTICE3D ? kLat3DTiles : kLatTiles;
+    if (tile != PDMTS_LATTICE_TILE_AUTO && (tile < 0 || tile >= ntiles))
+        return fail(PDMTS_ERR_ARG, "pd_set_lattice_tile: tile %d outside [0, %d) and not AUTO", tile, ntiles);
     static_assert(kLatTiles == PDMTS_LATTICE_TILES, "tile table and ABI disagree");
     pd->lattice_tile = tile;
     pd->link_tile = -1;  // a fixed configuration serves the link chains too; AUTO tunes both

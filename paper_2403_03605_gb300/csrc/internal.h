@@ -147,6 +147,7 @@ struct Lat2DArgs {
     float clin[10];             // linear law: c(|xi|) h^2 V |d|^2 / 2
     float cpmb[10];             // PMB: c(|xi|) h^2 V |d|^4
     float qthr;                 // s0 (2 + s0)
+    float qfast;                // qthr (1 - 2^-12): threshold of the fast path's conservative break watch
     int tile;                   // tile configuration, 0 .. kLatTiles - 1
     int num_sms;                // SMs of the device (persistent grids)
     int win_lo[2], win_n[2];    // optional windows in units of TY node rows (win_n[0] == 0: whole lattice)
@@ -158,20 +159,27 @@ struct Lat2DArgs {
 // 3D lattice kernel: nodes form a full nx * ny * nz box numbered
 // i = x + nx (y + ny z); the family is the 122-offset stencil |d|^2 <= 9
 // (lattice units) clipped to the box, offsets in ascending neighbour-index
-// order, (dz, dy, dx) lexicographic. Bond bits: word w of node i at
-// mask[w * n + i], offset k at bit k % 32 of word k / 32. Per |d|^2 (0..9):
-// coef = c(|xi|) h^2 V, thr = s0 (2 + s0) |d|^2, rd = |d|, r2 = |d|^2.
+// order, (dz, dy, dx) lexicographic; a node's bond forces are summed in that
+// order. Bond bits: word w of node i at mask[w * n + i], offset k at bit k % 32
+// of word k / 32. Per |d|^2 (0..9): coef = c(|xi|) h^2 V, thr = s0 (2 + s0)
+// |d|^2, rd = |d|, r2 = |d|^2, ir2 = 1 / |d|^2.
 namespace lat3d {
 constexpr int NS = 122, W = 4;
 }
 struct Lat3DArgs {
     int nx, ny, nz;
     uint32_t *mask;
+    const uint32_t *exists;     // bond words of the bonds that exist (all intact)
     const float *alpha;         // n (null when no weights)
-    float coef[10], thr[10], rd[10], r2[10];
+    const uint8_t *row_alpha;   // ny: 1 if a node of row y carries a weight (null when no weights)
+    // indexed by |d|^2 up to 18 = 9 + 3^2 (a row's dy^2 + dz^2 plus dx^2); 0 past 9
+    float coef[19], thr[10], rd[19], r2[19], ir2[19];
+    float qfast;                // s0 (2 + s0) (1 - 2^-16): a bond at or past the critical stretch exceeds it
+    int tile;                   // 3D tile configuration: blocks of 32 x (4 << tile) nodes in x, y
     int pdl;                    // launch as a programmatic dependent of the previous substep kernel
     F32NodeArgs nd;
 };
+constexpr int kLat3DTiles = 2;
 cudaError_t launch_pd_step_lattice3d(const Lat3DArgs &A, bool init, cudaStream_t s);
 
 // Tensor maps of the lattice kernel's inputs for the tensor-copy staging
@@ -195,10 +203,10 @@ cudaError_t launch_pd_step_lattice2d(const Lat2DArgs &A, bool init, cudaStream_t
 struct LatTile {
     int kr, min_blocks, pipelined, pair, tma;
 };
-constexpr int kLatTiles = 9;
+constexpr int kLatTiles = 10;
 constexpr LatTile kLatTile[kLatTiles] = {{2, 3, 0, 0, 0}, {2, 4, 0, 0, 0}, {2, 2, 1, 0, 0}, {1, 4, 1, 0, 0},
                                          {2, 3, 0, 1, 0}, {2, 4, 0, 0, 1}, {2, 3, 0, 0, 1}, {2, 2, 1, 0, 1},
-                                         {1, 4, 1, 0, 1}};
+                                         {1, 4, 1, 0, 1}, {4, 2, 0, 0, 1}};
 cudaError_t launch_lattice2d_t0(const Lat2DArgs &A, bool init, cudaStream_t s);
 cudaError_t launch_lattice2d_t1(const Lat2DArgs &A, bool init, cudaStream_t s);
 cudaError_t launch_lattice2d_t2(const Lat2DArgs &A, bool init, cudaStream_t s);
@@ -208,6 +216,7 @@ cudaError_t launch_lattice2d_t5(const Lat2DArgs &A, bool init, cudaStream_t s);
 cudaError_t launch_lattice2d_t6(const Lat2DArgs &A, bool init, cudaStream_t s);
 cudaError_t launch_lattice2d_t7(const Lat2DArgs &A, bool init, cudaStream_t s);
 cudaError_t launch_lattice2d_t8(const Lat2DArgs &A, bool init, cudaStream_t s);
+cudaError_t launch_lattice2d_t9(const Lat2DArgs &A, bool init, cudaStream_t s);
 // Batched substeps (tile configurations 0 and 1): lattice2d_batch_prepare
 // converts A's windows to the configuration's tile rows and returns the
 // instance's tile count (-1 for another configuration); the launch runs one

@@ -106,12 +106,22 @@ __device__ __forceinline__ void lattice_acc(float &acc, const float s)
         acc = __fmaf_rn(s, (float)D, acc);
 }
 
+// Watch of the fast path for bonds at or past the critical stretch: w.x is
+// the largest p (linear law) or q (PMB) of the bonds seen, w.y the largest
+// |eta| component (linear law; 0 for PMB). Every bond has
+// q = p + |eta|^2 / |d|^2 <= p + 2 max(|eta_x|, |eta_y|)^2, so when the bound
+// w.x + 2 w.y^2 of a strip stays below qfast = qthr (1 - 2^-12) none of its
+// bonds reached qthr (the margin covers the rounding of q and of the bound)
+// and the masked path, which decides each bond exactly, would break nothing.
+__device__ __forceinline__ float watch_bound(const float2 w) { return __fmaf_rn(2.f * w.y, w.y, w.x); }
+constexpr float2 kWatch0 = {-INFINITY, 0.f};
+
 // One bond of the node with state nu = -u_i (and weight ai); accumulates its
 // force into f and returns the scalar s of the linear law's f = s d.
 template <int DX, int DY, bool ALPHA, bool PMB, bool MASKED>
 __device__ __forceinline__ float lattice_bond(const float4 uj, const float aj, const float4 nu, const float ai,
                                               const Lat2DArgs &A, const uint32_t m0, uint32_t &m, float2 &f,
-                                              float &qmax)
+                                              float2 &watch)
 {
     constexpr int r2 = DX * DX + DY * DY;
     constexpr int K = lat2d::KOF(DX, DY);
@@ -146,7 +156,12 @@ __device__ __forceinline__ float lattice_bond(const float4 uj, const float aj, c
     }
     float s = sc;
     if constexpr (!MASKED) {
-        qmax = fmaxf(qmax, q);
+        if constexpr (PMB) {
+            watch.x = fmaxf(watch.x, q);
+        } else {
+            watch.x = fmaxf(watch.x, p);
+            watch.y = fmaxf(watch.y, fmaxf(fabsf(eta.x), fabsf(eta.y)));
+        }
     } else {
         const bool on = (m0 >> K) & 1u;
         const bool brk = on && A.nd.breaking && q >= A.qthr;
@@ -169,13 +184,13 @@ __device__ __forceinline__ float lattice_bond(const float4 uj, const float aj, c
 // (fast path), in the canonical order: the H+ columns dx = 0..3 with rows
 // ascending, then the H- columns dx = 0, -1, -2, -3 with rows descending. A
 // thread reads each halo value of a column once and applies it to every node
-// of its strip within reach; qmax collects the largest q.
+// of its strip within reach; watch collects the break watch of each node.
 template <int KR, bool ALPHA, bool PMB>
 __device__ __forceinline__ void lattice_strip(const float4 (*su)[lat2d::HX], const float (*sal)[lat2d::HXA],
                                               const int hy0, const int hx0, const Lat2DArgs &A,
                                               const float4 (&nu)[KR], const float (&ai)[KR],
                                               const uint32_t (&m0)[KR], uint32_t (&m)[KR], float2 (&f)[KR],
-                                              float (&qmax)[KR])
+                                              float2 (&watch)[KR])
 {
     using namespace lat2d;
     static_for<0, R + 1>([&](auto dxc) {
@@ -192,7 +207,7 @@ __device__ __forceinline__ void lattice_strip(const float4 (*su)[lat2d::HX], con
                 constexpr int r = decltype(rc)::value;
                 constexpr int dy = j - r;
                 if constexpr (dy >= lo && dy <= ry)
-                    lattice_bond<dx, dy, ALPHA, PMB, false>(uj, aj, nu[r], ai[r], A, m0[r], m[r], f[r], qmax[r]);
+                    lattice_bond<dx, dy, ALPHA, PMB, false>(uj, aj, nu[r], ai[r], A, m0[r], m[r], f[r], watch[r]);
             });
         });
     });
@@ -208,7 +223,7 @@ __device__ __forceinline__ void lattice_strip(const float4 (*su)[lat2d::HX], con
                 constexpr int r = decltype(rc)::value;
                 constexpr int dy = j - r;
                 if constexpr (dy >= -ry && dy <= hi)
-                    lattice_bond<dx, dy, ALPHA, PMB, false>(uj, aj, nu[r], ai[r], A, m0[r], m[r], f[r], qmax[r]);
+                    lattice_bond<dx, dy, ALPHA, PMB, false>(uj, aj, nu[r], ai[r], A, m0[r], m[r], f[r], watch[r]);
             });
         });
     });
@@ -230,8 +245,8 @@ __device__ __forceinline__ void lattice_node_masked(const float4 (*su)[lat2d::HX
             constexpr int dx = sg * PDX(k), dy = sg * PDY(k);
             const float4 uj = su[hy + dy][hx + dx];
             const float aj = ALPHA ? sal[hy + dy][hx + dx] : 0.f;
-            float qunused = 0.f;
-            lattice_bond<dx, dy, ALPHA, PMB, true>(uj, aj, nu, ai, A, m0, m, f, qunused);
+            float2 wunused = kWatch0;
+            lattice_bond<dx, dy, ALPHA, PMB, true>(uj, aj, nu, ai, A, m0, m, f, wunused);
         });
     });
 }
@@ -498,7 +513,7 @@ __host__ __device__ constexpr PairTask pair_task(const int i)
 
 template <int KR, bool ALPHA, int TI>
 __device__ __forceinline__ void pair_halo_task(const LatStage<KR> &S, LatPair<KR> &P, const Lat2DArgs &A,
-                                               const int lane, float &qm)
+                                               const int lane, float2 &wm)
 {
     using namespace lat2d;
     constexpr PairTask t = pair_task(TI);
@@ -522,31 +537,32 @@ __device__ __forceinline__ void pair_halo_task(const LatStage<KR> &S, LatPair<KR
             const float aj = ALPHA ? S.alh()[hy][x + dx + R] : 0.f;
             float2 fd = make_float2(0.f, 0.f);
             uint32_t md = 0u;
-            float q = -INFINITY;
-            const float sb = lattice_bond<dx, dy, ALPHA, false, false>(uj, aj, nu, ai, A, 0u, md, fd, q);
+            float2 w = kWatch0;
+            const float sb = lattice_bond<dx, dy, ALPHA, false, false>(uj, aj, nu, ai, A, 0u, md, fd, w);
             const bool tgt = x + dx >= 0 && x + dx < TX && y + dy >= 0 && y + dy < TYK;
             if (tgt) {
                 P.s[k][y + dy][x + dx] = sb;
-                qm = fmaxf(qm, q);
+                wm.x = fmaxf(wm.x, w.x);
+                wm.y = fmaxf(wm.y, w.y);
             }
         }
     });
 }
 
 // Pair evaluation of a clean tile: this thread's strip bonds of H+ (forces
-// into f, s into P) and its warp's halo tasks; qm collects the largest q.
+// into f, s into P) and its warp's halo tasks; wm collects the break watch.
 template <int KR, bool ALPHA>
 __device__ __forceinline__ void pair_compute(const LatStage<KR> &S, LatPair<KR> &P, const Lat2DArgs &A,
                                              const float4 (&nu)[KR], const float (&ai)[KR], float2 (&f)[KR],
-                                             float &qm)
+                                             float2 &wm)
 {
     using namespace lat2d;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int hx0 = tx + R, hy0 = ty * KR + R;
-    float qmax[KR];
+    float2 watch[KR];
 #pragma unroll
     for (int r = 0; r < KR; ++r)
-        qmax[r] = -INFINITY;
+        watch[r] = kWatch0;
     static_for<0, R + 1>([&](auto dxc) {
         constexpr int dx = decltype(dxc)::value;
         constexpr int ry = RY(dx), lo = PLO(dx);
@@ -561,7 +577,7 @@ __device__ __forceinline__ void pair_compute(const LatStage<KR> &S, LatPair<KR> 
                 if constexpr (dy >= lo && dy <= ry) {
                     uint32_t md = 0u;
                     const float sb =
-                        lattice_bond<dx, dy, ALPHA, false, false>(uj, aj, nu[r], ai[r], A, 0u, md, f[r], qmax[r]);
+                        lattice_bond<dx, dy, ALPHA, false, false>(uj, aj, nu[r], ai[r], A, 0u, md, f[r], watch[r]);
                     const int yt = ty * KR + r + dy;  // the target, if in the tile
                     if (tx + dx < TX && yt >= 0 && yt < KR * TY)
                         P.s[KP(dx, dy)][yt][tx + dx] = sb;
@@ -570,12 +586,14 @@ __device__ __forceinline__ void pair_compute(const LatStage<KR> &S, LatPair<KR> 
         });
     });
 #pragma unroll
-    for (int r = 0; r < KR; ++r)
-        qm = fmaxf(qm, qmax[r]);
+    for (int r = 0; r < KR; ++r) {
+        wm.x = fmaxf(wm.x, watch[r].x);
+        wm.y = fmaxf(wm.y, watch[r].y);
+    }
     static_for<0, kPairTasks>([&](auto tc) {
         constexpr int ti = decltype(tc)::value;
         if (pair_task(ti).warp == ty)
-            pair_halo_task<KR, ALPHA, ti>(S, P, A, tx, qm);
+            pair_halo_task<KR, ALPHA, ti>(S, P, A, tx, wm);
     });
 }
 
@@ -623,7 +641,8 @@ __device__ __forceinline__ unsigned lattice_tile(LatStage<KR> &S, const Lat2DArg
     const int hx0 = tx + R, hy0 = ty * KR + R;
     const int x = x0 + tx, ys = y0 + ty * KR;  // the strip: nodes (x, ys + r), r < KR
     float4 nu[KR];
-    float ai[KR], qmax[KR];
+    float ai[KR];
+    float2 watch[KR];
     uint32_t m0[KR], m[KR];
     float2 f[KR];
     unsigned vbits = 0;  // bit r: node r of the strip lies in the lattice
@@ -639,20 +658,20 @@ __device__ __forceinline__ unsigned lattice_tile(LatStage<KR> &S, const Lat2DArg
         nu[r] = make_float4(-u.x, -u.y, -u.z, -u.w);
         ai[r] = has_alpha ? S.alh()[hy0 + r][hx0] : 0.f;
         f[r] = make_float2(0.f, 0.f);
-        qmax[r] = -INFINITY;
+        watch[r] = kWatch0;
     }
     bool done = false;
     if constexpr (PAIR && !PMB) {
         // every node of the tile in the lattice with all its bonds intact
         const bool clean = __syncthreads_and(full && vbits == (1u << KR) - 1u) != 0;
         if (clean) {
-            float qm = -INFINITY;
+            float2 wm = kWatch0;
             if (has_alpha)
-                pair_compute<KR, true>(S, *P, A, nu, ai, f, qm);
+                pair_compute<KR, true>(S, *P, A, nu, ai, f, wm);
             else
-                pair_compute<KR, false>(S, *P, A, nu, ai, f, qm);
+                pair_compute<KR, false>(S, *P, A, nu, ai, f, wm);
             // the barrier also publishes every s
-            if (__syncthreads_or(N.breaking && qm >= A.qthr) == 0) {
+            if (__syncthreads_or(N.breaking && watch_bound(wm) >= A.qfast) == 0) {
                 pair_gather<KR>(*P, f);
                 done = true;
             } else {
@@ -663,18 +682,19 @@ __device__ __forceinline__ unsigned lattice_tile(LatStage<KR> &S, const Lat2DArg
         }
     }
     // Fast path: every node of the warp has all bonds intact; evaluate all
-    // bonds without per-bond control flow and only note the largest q. If a
-    // bond reached the critical stretch (rare), redo the warp bond by bond.
+    // bonds without per-bond control flow and only keep the break watch. If a
+    // bond may have reached the critical stretch (rare), redo the warp bond by
+    // bond.
     bool fast = !done && __all_sync(0xffffffffu, full);
     if (fast) {
         if (has_alpha)
-            lattice_strip<KR, true, PMB>(S.u, S.alh(), hy0, hx0, A, nu, ai, m0, m, f, qmax);
+            lattice_strip<KR, true, PMB>(S.u, S.alh(), hy0, hx0, A, nu, ai, m0, m, f, watch);
         else
-            lattice_strip<KR, false, PMB>(S.u, S.alh(), hy0, hx0, A, nu, ai, m0, m, f, qmax);
+            lattice_strip<KR, false, PMB>(S.u, S.alh(), hy0, hx0, A, nu, ai, m0, m, f, watch);
         bool hit = false;
 #pragma unroll
         for (int r = 0; r < KR; ++r)
-            hit = hit || (((vbits >> r) & 1u) && qmax[r] >= A.qthr);
+            hit = hit || (((vbits >> r) & 1u) && watch_bound(watch[r]) >= A.qfast);
         if (N.breaking && __any_sync(0xffffffffu, hit))
             fast = false;
     }

@@ -95,4 +95,9 @@ cudaError_t launch_lattice2d_t8(const Lat2DArgs &A, bool init, cudaStream_t s)
     return launch_lattice_tpipe<1, 4>(A, init, s);
 }
 
+cudaError_t launch_lattice2d_t9(const Lat2DArgs &A, bool init, cudaStream_t s)
+{
+    return launch_lattice_tma<4, 2>(A, init, s);
+}
+
 }  // namespace pdmts

@@ -1,19 +1,36 @@
 // lattice3d.cu -- the FP32-bulk PD substep on a regular 3D lattice (arXiv
 // 2403.03605, Eq. 1-4 with the Arlequin bond weights of Sec. 3.2 and the
 // per-node update of Eq. 38). The family is implicit: a node's neighbours are
-// the 122 stencil offsets, visited in ascending neighbour-index order, and
-// only its four bond words are read. One thread per node; the neighbours'
-// displacements come through the read-only cache. Every operation and its
-// order follow the sliced-ELL FP32 kernel, so the two give the same bits.
+// the 122 stencil offsets |d|^2 <= 9 and only its four bond words are read.
+//
+// One thread per node; a block holds 32 consecutive x of 4 or 8 rows y of one
+// plane z, so a warp shares (y, z) and its neighbour loads are coalesced.
+// A node's bonds are summed in ascending neighbour-index order, (dz, dy, dx)
+// lexicographic, with the sliced-ELL kernel's operations: both give the same
+// bits. The stencil is walked row by row ((dz, dy), 29 rows, rolled loops)
+// into one of four compile-time row bodies by the row's reach in dx (0..3),
+// so the code stays small; each row loads through one base pointer with the
+// dx offsets as immediates.
+//
+// Fast path: a warp whose nodes hold every bond that exists evaluates its
+// bonds without bit tests. Planes and rows outside the box are skipped by
+// warp-uniform tests. A warp with a lane near the x faces of the box takes a
+// variant in which a lane whose x + dx leaves the box reads its own column and
+// multiplies that bond's coefficient and stretch by 0 (an exact zero
+// contribution). Only the largest reduced stretch (|d + eta|^2 - |d|^2) / |d|^2
+// is kept; if it may have reached the critical stretch, or a node of the warp
+// misses a bond, the warp evaluates its nodes bond by bond with the bits
+// (masked path, the same order and operations, so the same bits when nothing
+// breaks).
 #include "f32_device.cuh"
 #include "lattice2d.cuh"
 
 namespace pdmts {
 namespace lat3d {
+// offset k of the stencil, in (dz, dy, dx) lexicographic order
 struct Off {
     int dx, dy, dz;
 };
-// offset k of the stencil: (dz, dy, dx) lexicographic, 0 < |d|^2 <= 9
 __host__ __device__ constexpr Off off(const int k)
 {
     int c = 0;
@@ -30,105 +47,346 @@ __host__ __device__ constexpr Off off(const int k)
     return Off{0, 0, 0};
 }
 static_assert(off(NS - 1).dz == 3 && off(NS).dz == 0, "122 offsets");
+struct OffTable {
+    signed char dx[NS], dy[NS], dz[NS];
+};
+__host__ __device__ constexpr OffTable make_off_table()
+{
+    OffTable t{};
+    for (int k = 0; k < NS; ++k) {
+        t.dx[k] = (signed char)off(k).dx;
+        t.dy[k] = (signed char)off(k).dy;
+        t.dz[k] = (signed char)off(k).dz;
+    }
+    return t;
+}
+__constant__ OffTable kOff = make_off_table();
+// reach of a plane |dz| = a in dy: dy^2 <= 9 - a^2
+__host__ __device__ constexpr int reach_y(const int a) { return a == 0 ? 3 : a == 3 ? 0 : 2; }
+// reach of row dy of plane |dz| = a in dx: floor(sqrt(9 - a^2 - dy^2))
+__host__ __device__ constexpr int reach_x(const int a, const int dy)
+{
+    const int rem = 9 - a * a - dy * dy;
+    return rem < 0 ? -1 : rem >= 9 ? 3 : rem >= 4 ? 2 : rem >= 1 ? 1 : 0;
+}
+constexpr int stencil_bonds()
+{
+    int c = 0;
+    for (int dz = -3; dz <= 3; ++dz)
+        for (int dy = -reach_y(dz < 0 ? -dz : dz); dy <= reach_y(dz < 0 ? -dz : dz); ++dy)
+            c += 2 * reach_x(dz < 0 ? -dz : dz, dy) + 1;
+    return c - 1;
+}
+static_assert(stencil_bonds() == NS, "row bodies cover the stencil");
 }  // namespace lat3d
 
-// f += s d for a compile-time component d (skipped when 0: f + 0 s == f)
-template <int D>
-__device__ __forceinline__ void acc3(float &f, const float s)
+// eta = u_j - u_i from compensated pairs, d . eta (a zero x term of d is left
+// out: it changes at most the sign of a zero dot, which no result depends on)
+// and lhs = |d + eta|^2 - |d|^2 = 2 d . eta + |eta|^2, for d = (DX, fdy, fdz).
+struct Bond3D {
+    float e0, e1, e2, dot, lhs;
+};
+template <int DX>
+__device__ __forceinline__ Bond3D bond3d_eval(const float4 s4, const float2 s2, const float4 nu4, const float2 nu2,
+                                              const float fdy, const float fdz)
 {
-    if constexpr (D != 0)
-        f = __fmaf_rn(s, (float)D, f);
+    // (dhx, dhy), (dhz, dlx), (dly, dlz): eta = (u_j - u_i)_hi + (u_j - u_i)_lo
+    const float2 pa = __fadd2_rn(make_float2(s4.x, s4.y), make_float2(nu4.x, nu4.y));
+    const float2 pb = __fadd2_rn(make_float2(s4.z, s4.w), make_float2(nu4.z, nu4.w));
+    const float2 pc = __fadd2_rn(s2, nu2);
+    Bond3D b;
+    b.e0 = __fadd_rn(pa.x, pb.y);
+    b.e1 = __fadd_rn(pa.y, pc.x);
+    b.e2 = __fadd_rn(pb.x, pc.y);
+    float dot;
+    if constexpr (DX != 0)
+        dot = __fmaf_rn(fdy, b.e1, __fmul_rn((float)DX, b.e0));
+    else
+        dot = __fmul_rn(fdy, b.e1);
+    dot = __fmaf_rn(fdz, b.e2, dot);
+    float q = __fmul_rn(b.e0, b.e0);
+    q = __fmaf_rn(b.e1, b.e1, q);
+    q = __fmaf_rn(b.e2, b.e2, q);
+    b.dot = dot;
+    b.lhs = __fmaf_rn(2.f, dot, q);
+    return b;
 }
 
-template <bool ALPHA, bool PMB>
-__global__ void __launch_bounds__(256) k_pd_step_lattice3d(const Lat3DArgs A, const int init)
+// Row constants: per |dx| = 0..3 the coefficient c(|xi|) h^2 V and 1/|d|^2
+// of the bond (dx, dy, dz), for the row's dy^2 + dz^2 = rb.
+struct Row3D {
+    float coef[4], ir2[4], rr[4], rd[4];
+};
+
+// The bonds of one row (dy, dz) of a node, dx = -RX..RX ascending, loaded
+// through one base pointer; RX = 3 is only the centre row (dy = dz = 0),
+// which skips dx = 0. XE: a lane of the warp lies within 3 columns of an x
+// face (xm[dx + 3] = 0 where x + dx leaves the box: the lane reads its own
+// column and the bond contributes an exact zero).
+template <int RX, bool ALPHA, bool PMB, bool XE>
+__device__ __forceinline__ void row3d(const Lat3DArgs &A, const int row, const float fdy, const float fdz,
+                                      const Row3D &R, const float4 nu4, const float2 nu2, const float ai,
+                                      const float (&xm)[7], float (&f)[3], float &qmax)
 {
     const F32NodeArgs &N = A.nd;
-    const int x = blockIdx.x * 32 + (threadIdx.x & 31), y = blockIdx.y * 8 + (threadIdx.x >> 5), z = blockIdx.z;
-    const bool valid = x < A.nx && y < A.ny;
-    const int sy = A.nx, sz = A.nx * A.ny;  // n < 2^24 on this path
-    const int i = valid ? x + sy * y + sz * z : 0;
+    const float4 *p4 = N.u4_in + row;
+    const float2 *p2 = N.u2_in + row;
+    const float *pa = ALPHA ? A.alpha + row : nullptr;
+    static_for<-RX, RX + 1>([&](auto dxc) {
+        constexpr int dx = decltype(dxc)::value;
+        constexpr int adx = dx < 0 ? -dx : dx;
+        if constexpr (!(RX == 3 && dx == 0)) {
+            const bool in = !XE || xm[dx + 3] != 0.f;
+            const float4 s4 = __ldg(in ? p4 + dx : p4);
+            const float2 s2 = __ldg(in ? p2 + dx : p2);
+            const Bond3D b = bond3d_eval<dx>(s4, s2, nu4, nu2, fdy, fdz);
+            float coef = R.coef[adx];
+            if constexpr (XE) {
+                qmax = fmaxf(qmax, __fmul_rn(__fmul_rn(b.lhs, R.ir2[adx]), xm[dx + 3]));
+                coef = __fmul_rn(coef, xm[dx + 3]);
+            } else {
+                qmax = fmaxf(qmax, __fmul_rn(b.lhs, R.ir2[adx]));
+            }
+            if constexpr (ALPHA)
+                coef = __fmul_rn(coef, bond_weight(ai, __ldg(in ? pa + dx : pa)));
+            if constexpr (PMB) {
+                const float rr = R.rr[adx];
+                const float ry = __fsqrt_rn(__fadd_rn(rr, fmaxf(b.lhs, -rr)));
+                const float sc =
+                    __fdiv_rn(__fmul_rn(__fmul_rn(coef, rr), b.lhs), __fmul_rn(__fadd_rn(ry, R.rd[adx]), ry));
+                f[0] = __fmaf_rn(sc, __fadd_rn((float)dx, b.e0), f[0]);
+                f[1] = __fmaf_rn(sc, __fadd_rn(fdy, b.e1), f[1]);
+                f[2] = __fmaf_rn(sc, __fadd_rn(fdz, b.e2), f[2]);
+            } else {
+                const float sc = __fmul_rn(coef, b.dot);
+                if constexpr (dx != 0)
+                    f[0] = __fmaf_rn(sc, (float)dx, f[0]);
+                f[1] = __fmaf_rn(sc, fdy, f[1]);
+                f[2] = __fmaf_rn(sc, fdz, f[2]);
+            }
+        }
+    });
+}
+
+// Fast path of one node: planes dz ascending, rows dy ascending (rolled
+// loops; absent planes and rows skipped warp-uniformly), each row's bonds in
+// one of four compile-time bodies.
+template <bool ALPHA, bool PMB, bool XE>
+__device__ __forceinline__ void node_fast(const Lat3DArgs &A, const int i, const int x, const int y, const int z,
+                                          const float4 nu4, const float2 nu2, const float ai, float (&f)[3],
+                                          float &qmax)
+{
+    const int sy = A.nx, sz = A.nx * A.ny;
+    float xm[7];
+#pragma unroll
+    for (int d = 0; d < 7; ++d)
+        xm[d] = (x + d - 3 >= 0 && x + d - 3 < A.nx) ? 1.f : 0.f;
+#pragma unroll 1
+    for (int dz = -3; dz <= 3; ++dz) {
+        if (z + dz < 0 || z + dz >= A.nz)  // warp-uniform: a warp shares z
+            continue;
+        const int ry = lat3d::reach_y(dz < 0 ? -dz : dz);
+#pragma unroll 1
+        for (int dy = -ry; dy <= ry; ++dy) {
+            if (y + dy < 0 || y + dy >= A.ny)  // warp-uniform: a warp shares y
+                continue;
+            const int rb = dy * dy + dz * dz;
+            const int rx = rb == 0 ? 3 : rb <= 5 ? 2 : rb == 8 ? 1 : 0;  // floor(sqrt(9 - rb)), rb in {0,1,2,4,5,8,9}
+            Row3D R;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const int r2 = rb + a * a;  // <= 18: the tables hold zeros past 9
+                R.coef[a] = A.coef[r2];
+                R.ir2[a] = A.ir2[r2];
+                if constexpr (PMB) {
+                    R.rr[a] = A.r2[r2];
+                    R.rd[a] = A.rd[r2];
+                }
+            }
+            const int row = i + dz * sz + dy * sy;
+            const float fdy = (float)dy, fdz = (float)dz;
+            switch (rx) {
+            case 3:
+                row3d<3, ALPHA, PMB, XE>(A, row, fdy, fdz, R, nu4, nu2, ai, xm, f, qmax);
+                break;
+            case 2:
+                row3d<2, ALPHA, PMB, XE>(A, row, fdy, fdz, R, nu4, nu2, ai, xm, f, qmax);
+                break;
+            case 1:
+                row3d<1, ALPHA, PMB, XE>(A, row, fdy, fdz, R, nu4, nu2, ai, xm, f, qmax);
+                break;
+            default:
+                row3d<0, ALPHA, PMB, XE>(A, row, fdy, fdz, R, nu4, nu2, ai, xm, f, qmax);
+                break;
+            }
+        }
+    }
+}
+
+// Masked path of one node: its bonds in order with their bits; a bond at or
+// past the critical stretch is cleared and carries no force. The operations
+// of the fast path, with every term of d . eta present (offsets from a table).
+template <bool ALPHA, bool PMB>
+__device__ __forceinline__ void node_masked(const Lat3DArgs &A, const int i, const float4 nu4, const float2 nu2,
+                                            const float ai, const uint32_t (&m0)[lat3d::W], uint32_t (&m)[lat3d::W],
+                                            float (&f)[3])
+{
+    const F32NodeArgs &N = A.nd;
+    const int sy = A.nx, sz = A.nx * A.ny;
+#pragma unroll
+    for (int w = 0; w < lat3d::W; ++w) {
+        const uint32_t word = m0[w];
+        uint32_t mw = word;
+#pragma unroll 1
+        for (int b = 0; b < 32; ++b) {
+            const int k = 32 * w + b;
+            if (k >= lat3d::NS || !((word >> b) & 1u))
+                continue;
+            const int dx = lat3d::kOff.dx[k], dy = lat3d::kOff.dy[k], dz = lat3d::kOff.dz[k];
+            const int j = i + dx + dy * sy + dz * sz;  // the bond exists: inside the box
+            const float4 s4 = __ldg(N.u4_in + j);
+            const float2 s2 = __ldg(N.u2_in + j);
+            const float fdx = (float)dx, fdy = (float)dy, fdz = (float)dz;
+            const float2 pa = __fadd2_rn(make_float2(s4.x, s4.y), make_float2(nu4.x, nu4.y));
+            const float2 pb = __fadd2_rn(make_float2(s4.z, s4.w), make_float2(nu4.z, nu4.w));
+            const float2 pc = __fadd2_rn(s2, nu2);
+            const float e0 = __fadd_rn(pa.x, pb.y), e1 = __fadd_rn(pa.y, pc.x), e2 = __fadd_rn(pb.x, pc.y);
+            float dot = __fmul_rn(fdx, e0);
+            dot = __fmaf_rn(fdy, e1, dot);
+            dot = __fmaf_rn(fdz, e2, dot);
+            float q = __fmul_rn(e0, e0);
+            q = __fmaf_rn(e1, e1, q);
+            q = __fmaf_rn(e2, e2, q);
+            const float lhs = __fmaf_rn(2.f, dot, q);
+            const int r2 = dx * dx + dy * dy + dz * dz;
+            if (N.breaking && lhs >= A.thr[r2]) {
+                mw &= ~(1u << b);
+                continue;
+            }
+            float coef = A.coef[r2];
+            if constexpr (ALPHA)
+                coef = __fmul_rn(coef, bond_weight(ai, __ldg(A.alpha + j)));
+            if constexpr (PMB) {
+                const float rr = A.r2[r2];
+                const float ry = __fsqrt_rn(__fadd_rn(rr, fmaxf(lhs, -rr)));
+                const float sc = __fdiv_rn(__fmul_rn(__fmul_rn(coef, rr), lhs), __fmul_rn(__fadd_rn(ry, A.rd[r2]), ry));
+                f[0] = __fmaf_rn(sc, __fadd_rn(fdx, e0), f[0]);
+                f[1] = __fmaf_rn(sc, __fadd_rn(fdy, e1), f[1]);
+                f[2] = __fmaf_rn(sc, __fadd_rn(fdz, e2), f[2]);
+            } else {
+                const float sc = __fmul_rn(coef, dot);
+                f[0] = __fmaf_rn(sc, fdx, f[0]);
+                f[1] = __fmaf_rn(sc, fdy, f[1]);
+                f[2] = __fmaf_rn(sc, fdz, f[2]);
+            }
+        }
+        m[w] = mw;
+    }
+}
+
+// One thread per node; blocks of 32 x BY nodes (x, y) of one plane z.
+template <int BY, bool ALPHA, bool PMB>
+__global__ void __launch_bounds__(32 * BY, 32 / BY) k_pd_step_lattice3d(const Lat3DArgs A, const int init)
+{
+    const F32NodeArgs &N = A.nd;
+    const int lane = threadIdx.x & 31;
+    const int x = blockIdx.x * 32 + lane, y = blockIdx.y * BY + (threadIdx.x >> 5), z = blockIdx.z;
     lattice_chain_entry();
+    if (y >= A.ny)  // the whole warp
+        return;
+    const int nx = A.nx;
+    const int64_t n = N.n;
+    const bool xin = x < nx;
+    // a lane past the box edge mirrors the last column and writes nothing
+    const int i = (xin ? x : nx - 1) + nx * (y + A.ny * z);
     const float4 u4 = N.u4_in[i];
     const float2 u2 = N.u2_in[i];
     const float4 nu4 = make_float4(-u4.x, -u4.y, -u4.z, -u4.w);
     const float2 nu2 = make_float2(-u2.x, -u2.y);
     const float ai = ALPHA ? A.alpha[i] : 0.f;
     uint32_t m0[lat3d::W], m[lat3d::W];
+    bool full = true;
 #pragma unroll
     for (int w = 0; w < lat3d::W; ++w) {
-        m0[w] = valid ? A.mask[(int64_t)w * N.n + i] : 0u;
+        m0[w] = A.mask[(int64_t)w * n + i];
         m[w] = m0[w];
+        full = full && m0[w] == A.exists[(int64_t)w * n + i];
+    }
+    // a warp whose 7-row neighbourhood carries no weight evaluates every bond
+    // with weight 1 exactly and skips the weights
+    bool has_alpha = false;
+    if (ALPHA) {
+        const int yy = y - 3 + lane;
+        has_alpha = __any_sync(0xffffffffu, lane < 7 && yy >= 0 && yy < A.ny && A.row_alpha[yy] != 0);
     }
     float f[3] = {0.f, 0.f, 0.f};
-    static_for<0, lat3d::NS>([&](auto kc) {
-        constexpr int k = decltype(kc)::value;
-        constexpr lat3d::Off o = lat3d::off(k);
-        constexpr int w = k >> 5, b = k & 31, r2 = o.dx * o.dx + o.dy * o.dy + o.dz * o.dz;
-        if ((m0[w] >> b) & 1u) {
-            const int j = i + o.dx + o.dy * sy + o.dz * sz;
-            const float4 j4 = __ldg(N.u4_in + j);
-            const float2 j2 = __ldg(N.u2_in + j);
-            // (dhx, dhy), (dhz, dlx), (dly, dlz): eta = (u_j - u_i)_hi + (u_j - u_i)_lo
-            const float2 pa = __fadd2_rn(make_float2(j4.x, j4.y), make_float2(nu4.x, nu4.y));
-            const float2 pb = __fadd2_rn(make_float2(j4.z, j4.w), make_float2(nu4.z, nu4.w));
-            const float2 pc = __fadd2_rn(j2, nu2);
-            const float eta[3] = {__fadd_rn(pa.x, pb.y), __fadd_rn(pa.y, pc.x), __fadd_rn(pb.x, pc.y)};
-            // d . eta and |eta|^2 in the sliced-ELL kernel's order
-            float dot = __fmul_rn((float)o.dx, eta[0]);
-            dot = __fmaf_rn((float)o.dy, eta[1], dot);
-            dot = __fmaf_rn((float)o.dz, eta[2], dot);
-            float e2 = __fmul_rn(eta[0], eta[0]);
-            e2 = __fmaf_rn(eta[1], eta[1], e2);
-            e2 = __fmaf_rn(eta[2], eta[2], e2);
-            const float lhs = __fmaf_rn(2.f, dot, e2);
-            if (N.breaking && lhs >= A.thr[r2]) {
-                m[w] &= ~(1u << b);
-            } else {
-                float coef = A.coef[r2];
-                if constexpr (ALPHA)
-                    coef = __fmul_rn(coef, bond_weight(ai, __ldg(A.alpha + j)));
-                if constexpr (PMB) {
-                    const float rr = A.r2[r2];
-                    const float ry = __fsqrt_rn(__fadd_rn(rr, fmaxf(lhs, -rr)));
-                    const float sc = __fdiv_rn(__fmul_rn(__fmul_rn(coef, rr), lhs), __fmul_rn(__fadd_rn(ry, A.rd[r2]), ry));
-                    f[0] = __fmaf_rn(sc, __fadd_rn((float)o.dx, eta[0]), f[0]);
-                    f[1] = __fmaf_rn(sc, __fadd_rn((float)o.dy, eta[1]), f[1]);
-                    f[2] = __fmaf_rn(sc, __fadd_rn((float)o.dz, eta[2]), f[2]);
-                } else {
-                    const float sc = __fmul_rn(coef, dot);
-                    acc3<o.dx>(f[0], sc);
-                    acc3<o.dy>(f[1], sc);
-                    acc3<o.dz>(f[2], sc);
-                }
-            }
+    bool fast = __all_sync(0xffffffffu, full);
+    if (fast) {
+        float qmax = -INFINITY;
+        const bool xe = __any_sync(0xffffffffu, x < 3 || x > nx - 4);
+        if (has_alpha) {
+            if (xe)
+                node_fast<true, PMB, true>(A, i, x, y, z, nu4, nu2, ai, f, qmax);
+            else
+                node_fast<true, PMB, false>(A, i, x, y, z, nu4, nu2, ai, f, qmax);
+        } else {
+            if (xe)
+                node_fast<false, PMB, true>(A, i, x, y, z, nu4, nu2, ai, f, qmax);
+            else
+                node_fast<false, PMB, false>(A, i, x, y, z, nu4, nu2, ai, f, qmax);
         }
-    });
+        if (N.breaking && __any_sync(0xffffffffu, xin && qmax >= A.qfast))
+            fast = false;
+    }
+    if (!fast) {
+        f[0] = f[1] = f[2] = 0.f;
+        if (has_alpha)
+            node_masked<true, PMB>(A, i, nu4, nu2, ai, m0, m, f);
+        else
+            node_masked<false, PMB>(A, i, nu4, nu2, ai, m0, m, f);
+    }
     unsigned nbroken = 0;
+    if (xin) {
 #pragma unroll
-    for (int w = 0; w < lat3d::W; ++w)
-        if (m[w] != m0[w]) {
-            A.mask[(int64_t)w * N.n + i] = m[w];
-            nbroken += __popc(m0[w] ^ m[w]);
-        }
+        for (int w = 0; w < lat3d::W; ++w)
+            if (m[w] != m0[w]) {
+                A.mask[(int64_t)w * n + i] = m[w];
+                nbroken += __popc(m0[w] ^ m[w]);
+            }
+    }
     count_broken(N.broken, nbroken);
-    if (!valid)
+    if (!xin)
         return;
     float uh[3] = {u4.x, u4.y, u4.z}, ul[3] = {u4.w, u2.x, u2.y};
     finish_node_f32<3>(N, i, f, uh, ul, init);
+}
+
+template <int BY>
+static cudaError_t launch_lattice3d_by(const Lat3DArgs &A, bool init, cudaStream_t s)
+{
+    const dim3 grid((unsigned)((A.nx + 31) / 32), (unsigned)((A.ny + BY - 1) / BY), (unsigned)A.nz);
+    const bool al = A.alpha != nullptr;
+    const auto kern = al ? (A.nd.pmb ? k_pd_step_lattice3d<BY, true, true> : k_pd_step_lattice3d<BY, true, false>)
+                         : (A.nd.pmb ? k_pd_step_lattice3d<BY, false, true> : k_pd_step_lattice3d<BY, false, false>);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(32 * BY);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = A.pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, A, init ? 1 : 0);
 }
 
 cudaError_t launch_pd_step_lattice3d(const Lat3DArgs &A, bool init, cudaStream_t s)
 {
     if (A.nx <= 0 || A.ny <= 0 || A.nz <= 0)
         return cudaSuccess;
-    if (A.nz > 65535 || (A.ny + 7) / 8 > 65535)
+    if ((A.ny + 3) / 4 > 65535 || A.nz > 65535)
         return cudaErrorInvalidConfiguration;
-    const dim3 grid((unsigned)((A.nx + 31) / 32), (unsigned)((A.ny + 7) / 8), (unsigned)A.nz);
-    const bool al = A.alpha != nullptr;
-    const auto kern = al ? (A.nd.pmb ? k_pd_step_lattice3d<true, true> : k_pd_step_lattice3d<true, false>)
-                         : (A.nd.pmb ? k_pd_step_lattice3d<false, true> : k_pd_step_lattice3d<false, false>);
-    return lattice_launch(kern, grid, 0, s, A.pdl != 0, A, init ? 1 : 0);
+    return A.tile == 1 ? launch_lattice3d_by<8>(A, init, s) : launch_lattice3d_by<4>(A, init, s);
 }
 
 }  // namespace pdmts

@@ -67,6 +67,7 @@ struct pdmts_pd {
     DevArr<pdmts::StencilEntry> d_stencil;
     int n_stencil = 0;
     DevArr<float> f_alpha, f_invm, f_wb, f_g;
+    DevArr<uint8_t> f_rowalpha;  // 3D lattice: per row y, 1 if a node of the row carries a weight
     // state in lattice units, compensated pairs, per-node packed:
     // 2D: u4 = {hx, hy, lx, ly}; 3D: u4 = {hx, hy, hz, lx}, u2 = {ly, lz}
     DevArr<float4> f_u4[2], f_v4;
@@ -129,10 +130,11 @@ struct pdmts_pd {
     int upload_weights_and_loads();  // (re)build mass, wb, g device arrays
     int step(bool init, double theta, cudaStream_t s, bool link = false);  // one substep
     pdmts::Lat2DArgs lattice_args(const pdmts::F32NodeArgs &N, uint32_t *mask, bool link) const;
-    pdmts::Lat3DArgs lattice3d_args(const pdmts::F32NodeArgs &N, uint32_t *mask) const;
+    pdmts::Lat3DArgs lattice3d_args(const pdmts::F32NodeArgs &N, uint32_t *mask, bool link) const;
     pdmts::F32NodeArgs f32_node_args(bool init, double theta, bool link) const;
     void substep_done(bool init, bool link);  // parity and counters after an enqueued substep
     int tune_lattice(cudaStream_t s);        // pick the lattice tile configuration (once)
+    int tune_lattice3d(cudaStream_t s);      // the same for the 3D lattice layout
     int alloc_link_state();                  // link-problem arrays (MTS coupling)
     int zero_link_state(cudaStream_t s, bool all = false);  // W_0 = 0 before a link run
     int ensure_init(cudaStream_t s);

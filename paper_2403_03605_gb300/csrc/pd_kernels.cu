@@ -591,6 +591,7 @@ cudaError_t launch_pd_step_lattice2d(const Lat2DArgs &A, bool init, cudaStream_t
     case 6: return launch_lattice2d_t6(A, init, s);
     case 7: return launch_lattice2d_t7(A, init, s);
     case 8: return launch_lattice2d_t8(A, init, s);
+    case 9: return launch_lattice2d_t9(A, init, s);
     default: return cudaErrorInvalidValue;
     }
 }

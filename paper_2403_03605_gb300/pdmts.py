@@ -25,7 +25,7 @@ PDMTS_FP64, PDMTS_FP32_BULK, PDMTS_FP32_BULK_SELL = 0, 1, 2
 PDMTS_MICRO_POWER, PDMTS_MICRO_EXP = 0, 1
 PDMTS_FORCE_LINEAR, PDMTS_FORCE_PMB = 0, 1
 PDMTS_WEIGHT_CONSTANT, PDMTS_WEIGHT_LINEAR, PDMTS_WEIGHT_CUBIC = 0, 1, 2
-PDMTS_LATTICE_TILES, PDMTS_LATTICE_TILE_AUTO = 9, -1
+PDMTS_LATTICE_TILES, PDMTS_LATTICE_TILE_AUTO = 10, -1
 
 
 class PdmtsError(RuntimeError):

@@ -215,34 +215,46 @@ LATTICE3D_CASES = [
     dict(name="weights_pmb", pb=lambda: W.plate3d(13, 10, 7, 0.5e-3, traction=40e6, nsteps=50), alpha=True,
          force=True),
     dict(name="exp_state", pb=lambda: W.plate3d(12, 9, 10, 0.5e-3, traction=20e6, nsteps=40), micro=True, state=True),
+    # weights only on the rows y >= 10: warps near them take the weighted code, the others skip the weights
+    dict(name="wide_weights", pb=lambda: W.plate3d(75, 14, 9, 0.5e-3, cuts_mm=[(1, 3.5e-3, 0, 0.0, 8e-3)],
+                                                   traction=40e6, nsteps=40), alpha="rows"),
 ]
 
 
 @pytest.mark.parametrize("case", LATTICE3D_CASES, ids=[c["name"] for c in LATTICE3D_CASES])
 def test_fp32_lattice3d_kernel_bit_identical_to_sliced_ell(fresh, case):
     """The 3D lattice kernel (implicit 122-offset family, four bond words per
-    node) takes the sliced-ELL kernel's operations in the same order: the
-    same bits, breaks included."""
+    node; blocks of 32 x 4 or 32 x 8 nodes of one plane) takes the sliced-ELL
+    kernel's operations in the same order: the same bits, breaks included, for
+    both tile configurations (lattices of 12 to 75 nodes along x, so that
+    warps run past the box, touch its x faces or lie inside, and 7 to 10
+    along z)."""
     pb = case["pb"]()
     rng = np.random.default_rng(23)
     alpha = rng.uniform(0.0, 0.8, pb.n) if case.get("alpha") else None
+    if case.get("alpha") == "rows":
+        alpha[pb.lat.idx[1] < 10] = 0.0
     force = P.PDMTS_FORCE_PMB if case.get("force") else P.PDMTS_FORCE_LINEAR
     micro, l, c = P.PDMTS_MICRO_POWER, 0.0, None
     if case.get("micro"):
         micro, l, c = P.PDMTS_MICRO_EXP, pb.delta / 10.0, pb.c / pb.delta ** 3 * 500.0
     u0 = rng.standard_normal((3, pb.n)) * pb.s0 * pb.lat.dx * 0.3 if case.get("state") else None
-    runs = []
-    for prec in (P.PDMTS_FP32_BULK, P.PDMTS_FP32_BULK_SELL):
-        g = GpuPDRun(fresh(), pb, prec, alpha=alpha, force=force, micro=micro, l=l, c=c, u0=u0)
-        runs.append((P.pd_info(g.pd)["layout"], g.run(pb.nsteps)))
-    (la, a), (ls, b) = runs
-    assert la == 2 and ls == 0
-    assert np.array_equal(a.u(), b.u()) and np.array_equal(a.v(), b.v())
-    assert np.array_equal(a.mu(), b.mu())
-    # damage from bond counts (lattice) or volume sums (sliced ELL, uniform V): equal up to FP64 rounding
-    np.testing.assert_allclose(a.damage(), b.damage(), rtol=0, atol=1e-14)
-    if case["name"] == "breaking":
-        assert (a.mu() == 0).sum() > 0
+    b = GpuPDRun(fresh(), pb, P.PDMTS_FP32_BULK_SELL, alpha=alpha, force=force, micro=micro, l=l, c=c, u0=u0)
+    assert P.pd_info(b.pd)["layout"] == 0
+    b.run(pb.nsteps)
+    for tile in range(2):
+        a = GpuPDRun(fresh(), pb, P.PDMTS_FP32_BULK, alpha=alpha, force=force, micro=micro, l=l, c=c, u0=u0)
+        assert P.pd_info(a.pd)["layout"] == 2
+        P.pd_set_lattice_tile(a.pd, tile)
+        a.run(pb.nsteps)
+        assert np.array_equal(a.u(), b.u()) and np.array_equal(a.v(), b.v()), tile
+        assert np.array_equal(a.mu(), b.mu()), tile
+        # damage from bond counts (lattice) or volume sums (sliced ELL, uniform V): equal up to FP64 rounding
+        np.testing.assert_allclose(a.damage(), b.damage(), rtol=0, atol=1e-14)
+    if case["name"] in ("breaking", "wide_weights"):
+        assert (b.mu() == 0).sum() > 0
+    with pytest.raises(P.PdmtsError):
+        P.pd_set_lattice_tile(a.pd, 2)  # 3D lattices have two configurations
 
 
 @pytest.mark.parametrize("dim", [2, 3])
