@@ -972,19 +972,22 @@ int pdmts_pd::upload_weights_and_loads()
             invm[(size_t)i] = (float)(1.0 / ((1.0 - (has_alpha ? alpha[(size_t)i] : 0.0)) * rho));
         PDMTS_TRY(alloc(f_invm, n));
         PDMTS_TRY(upload(f_invm, invm.data(), n, s));
-        std::vector<uint8_t> rowa;
+        std::vector<int32_t> rowa;
         if (has_alpha) {
             std::vector<float> af(alpha.begin(), alpha.end());
             PDMTS_TRY(alloc(f_alpha, n));
             PDMTS_TRY(upload(f_alpha, af.data(), n, s));
-            if (layout == LAYOUT_LATTICE3D) {
+            if (layout == LAYOUT_LATTICE2D || layout == LAYOUT_LATTICE3D) {
                 const int64_t nx = lat_dims[0], ny = lat_dims[1];
-                rowa.assign((size_t)ny, 0);
+                std::vector<uint8_t> flag((size_t)ny, 0);
                 for (int64_t i = 0; i < n; ++i)
                     if (af[(size_t)i] != 0.f)
-                        rowa[(size_t)((i / nx) % ny)] = 1;
-                PDMTS_TRY(alloc(f_rowalpha, ny));
-                PDMTS_TRY(upload(f_rowalpha, rowa.data(), ny, s));
+                        flag[(size_t)((i / nx) % ny)] = 1;
+                rowa.assign((size_t)ny + 1, 0);
+                for (int64_t y = 0; y < ny; ++y)
+                    rowa[(size_t)y + 1] = rowa[(size_t)y] + flag[(size_t)y];
+                PDMTS_TRY(alloc(f_rowalpha, ny + 1));
+                PDMTS_TRY(upload(f_rowalpha, rowa.data(), ny + 1, s));
             }
         } else {
             release(f_alpha);
@@ -1019,6 +1022,7 @@ pdmts::Lat2DArgs pdmts_pd::lattice_args(const pdmts::F32NodeArgs &N, uint32_t *m
     A.ny = lat_dims[1];
     A.mask = mask;
     A.alpha = f_alpha.p;
+    A.alpha_rows = f_alpha.p ? f_rowalpha.p : nullptr;
     for (int r2 = 0; r2 < 10; ++r2) {
         const double coef = r2 > 0 ? micromodulus_host(this, r2 * h * h) * h * h * V[0] : 0.0;
         A.clin[r2] = (float)(coef * r2 / 2.0);
@@ -1049,7 +1053,7 @@ pdmts::Lat3DArgs pdmts_pd::lattice3d_args(const pdmts::F32NodeArgs &N, uint32_t 
     A.mask = mask;
     A.exists = d_exists.p;
     A.alpha = f_alpha.p;
-    A.row_alpha = f_alpha.p ? f_rowalpha.p : nullptr;
+    A.alpha_rows = f_alpha.p ? f_rowalpha.p : nullptr;
     for (int r2 = 1; r2 < 10; ++r2) {
         const double xi2 = r2 * h * h;
         A.coef[r2] = (float)(micromodulus_host(this, xi2) * h * h * V[0]);

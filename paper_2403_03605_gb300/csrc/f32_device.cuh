@@ -91,36 +91,53 @@ __device__ __forceinline__ void finish_node_f32(const F32NodeArgs &N, const int6
     store_pair<DIM>(N.u4_out, N.u2_out, i, uh, ul);
 }
 
+// Packed FP32x2 forms: one instruction for both components, each rounded
+// exactly like the scalar operation (a - b as fma(b, -1, a), rounded once).
+__device__ __forceinline__ float2 fsub2(const float2 a, const float2 b)
+{
+    return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
+__device__ __forceinline__ float2 splat2(const float x) { return make_float2(x, x); }
+
+// df_add on both components at once: the same operations as df_add.
+__device__ __forceinline__ void df_add2(float2 &hi, float2 &lo, const float2 x)
+{
+    const float2 s = __fadd2_rn(hi, x);
+    const float2 bp = fsub2(s, hi);
+    float2 e = __fadd2_rn(fsub2(hi, fsub2(s, bp)), fsub2(x, bp));
+    e = __fadd2_rn(e, lo);
+    const float2 h2 = __fadd2_rn(s, e);
+    lo = fsub2(e, fsub2(h2, s));
+    hi = h2;
+}
+
 // finish_node_f32<2> with the node's inputs already at hand (staged in shared
-// memory): the same operations in the same order, so the same bits.
+// memory), both components in packed FP32x2: the same operations in the same
+// order per component, so the same bits.
 __device__ __forceinline__ void finish_node_2d_vals(const F32NodeArgs &N, const int64_t i, const float (&f)[2],
                                                     float (&uh)[2], float (&ul)[2], const float2 ao,
                                                     const float4 vv, const float im, const float2 wb,
                                                     const float2 g, const int init)
 {
-    const float aov[2] = {ao.x, ao.y}, wbv[2] = {wb.x, wb.y}, gv[2] = {g.x, g.y};
-    float an[2];
-#pragma unroll
-    for (int d = 0; d < 2; ++d) {
-        float t = f[d];
-        if (N.wb)
-            t = __fadd_rn(t, wbv[d]);
-        if (N.g)
-            t = __fmaf_rn(N.theta, gv[d], t);
-        an[d] = __fmul_rn(t, im);
-    }
-    float vh[2] = {vv.x, vv.y}, vl[2] = {vv.z, vv.w};
+    float2 t = make_float2(f[0], f[1]);
+    if (N.wb)
+        t = __fadd2_rn(t, wb);
+    if (N.g)
+        t = __ffma2_rn(splat2(N.theta), g, t);
+    const float2 an = __fmul2_rn(t, splat2(im));
+    float2 vh = make_float2(vv.x, vv.y), vl = make_float2(vv.z, vv.w);
     if (!init) {
-#pragma unroll
-        for (int d = 0; d < 2; ++d)
-            df_add(vh[d], vl[d], __fmul_rn(N.hdt, __fadd_rn(aov[d], an[d])));
-        N.v4[i] = make_float4(vh[0], vh[1], vl[0], vl[1]);
+        df_add2(vh, vl, __fmul2_rn(splat2(N.hdt), __fadd2_rn(ao, an)));
+        N.v4[i] = make_float4(vh.x, vh.y, vl.x, vl.y);
     }
-    reinterpret_cast<float2 *>(N.a)[i] = make_float2(an[0], an[1]);
-#pragma unroll
-    for (int d = 0; d < 2; ++d)
-        df_add(uh[d], ul[d], __fmaf_rn(N.dt, vh[d], __fmaf_rn(N.dt, vl[d], __fmul_rn(N.hdt2, an[d]))));
-    N.u4_out[i] = make_float4(uh[0], uh[1], ul[0], ul[1]);
+    reinterpret_cast<float2 *>(N.a)[i] = an;
+    float2 h = make_float2(uh[0], uh[1]), l = make_float2(ul[0], ul[1]);
+    df_add2(h, l, __ffma2_rn(splat2(N.dt), vh, __ffma2_rn(splat2(N.dt), vl, __fmul2_rn(splat2(N.hdt2), an))));
+    N.u4_out[i] = make_float4(h.x, h.y, l.x, l.y);
+    uh[0] = h.x;
+    uh[1] = h.y;
+    ul[0] = l.x;
+    ul[1] = l.y;
 }
 
 __device__ __forceinline__ void count_broken(unsigned long long *counter, unsigned nbroken)

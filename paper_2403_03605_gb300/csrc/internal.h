@@ -144,6 +144,7 @@ struct Lat2DArgs {
     int nx, ny;
     uint32_t *mask;
     const float *alpha;         // n (null when no weights)
+    const int32_t *alpha_rows;  // ny + 1: rows y' < y with a weighted node (null when no weights)
     float clin[10];             // linear law: c(|xi|) h^2 V |d|^2 / 2
     float cpmb[10];             // PMB: c(|xi|) h^2 V |d|^4
     float qthr;                 // s0 (2 + s0)
@@ -171,7 +172,7 @@ struct Lat3DArgs {
     uint32_t *mask;
     const uint32_t *exists;     // bond words of the bonds that exist (all intact)
     const float *alpha;         // n (null when no weights)
-    const uint8_t *row_alpha;   // ny: 1 if a node of row y carries a weight (null when no weights)
+    const int32_t *alpha_rows;  // ny + 1: rows y' < y with a weighted node (null when no weights)
     // indexed by |d|^2 up to 18 = 9 + 3^2 (a row's dy^2 + dz^2 plus dx^2); 0 past 9
     float coef[19], thr[10], rd[19], r2[19], ir2[19];
     float qfast;                // s0 (2 + s0) (1 - 2^-16): a bond at or past the critical stretch exceeds it

@@ -629,14 +629,12 @@ __device__ __forceinline__ unsigned lattice_tile(LatStage<KR> &S, const Lat2DArg
     constexpr int HY = LatStage<KR>::HY;
     const F32NodeArgs &N = A.nd;
     const int nx = A.nx, ny = A.ny;
-    bool any_alpha = false;
-    if (A.alpha)
-        for (int q = threadIdx.x; q < HY * HX; q += blockDim.x)
-            any_alpha |= S.alh()[q / HX][q % HX] != 0.f;
-    // a tile whose halo carries no Arlequin weight evaluates every bond with
-    // weight 1 exactly, so it can skip the weights (the barrier also makes
-    // every thread's group A visible)
-    const bool has_alpha = __syncthreads_or(any_alpha) != 0;
+    // a tile whose halo rows carry no Arlequin weight evaluates every bond
+    // with weight 1 exactly, so it can skip the weights
+    const bool has_alpha =
+        A.alpha && A.alpha_rows[min(ny, y0 + HY - R)] - A.alpha_rows[max(0, y0 - R)] > 0;
+    if constexpr (WAIT_B >= 0)
+        __syncthreads();  // every thread's asynchronous copies of group A are visible
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int hx0 = tx + R, hy0 = ty * KR + R;
     const int x = x0 + tx, ys = y0 + ty * KR;  // the strip: nodes (x, ys + r), r < KR
@@ -919,13 +917,15 @@ __global__ void __launch_bounds__(256, MINB) k_pd_step_lattice2d_batch(const Lat
                                                                         const int2 *__restrict__ work,
                                                                         const int init)
 {
-    __shared__ __align__(16) Lat2DArgs sA;
+    // raw storage: the argument block is copied in as words (no initialiser runs)
+    __shared__ __align__(16) unsigned char sA_raw[sizeof(Lat2DArgs)];
+    Lat2DArgs &sA = *reinterpret_cast<Lat2DArgs *>(sA_raw);
     extern __shared__ __align__(16) unsigned char lat_smem[];
     LatStage<KR> &S = *reinterpret_cast<LatStage<KR> *>(lat_smem);
     const int2 w = work[blockIdx.x];
     static_assert(sizeof(Lat2DArgs) % 4 == 0, "argument block copied as words");
     const int *src = reinterpret_cast<const int *>(args + w.x);
-    int *dst = reinterpret_cast<int *>(&sA);
+    int *dst = reinterpret_cast<int *>(sA_raw);
     for (int q = threadIdx.x; q < (int)(sizeof(Lat2DArgs) / 4); q += blockDim.x)
         dst[q] = src[q];
     __syncthreads();

@@ -314,11 +314,7 @@ __global__ void __launch_bounds__(32 * BY, 32 / BY) k_pd_step_lattice3d(const La
     }
     // a warp whose 7-row neighbourhood carries no weight evaluates every bond
     // with weight 1 exactly and skips the weights
-    bool has_alpha = false;
-    if (ALPHA) {
-        const int yy = y - 3 + lane;
-        has_alpha = __any_sync(0xffffffffu, lane < 7 && yy >= 0 && yy < A.ny && A.row_alpha[yy] != 0);
-    }
+    const bool has_alpha = ALPHA && A.alpha_rows[min(A.ny, y + 4)] - A.alpha_rows[max(0, y - 3)] > 0;
     float f[3] = {0.f, 0.f, 0.f};
     bool fast = __all_sync(0xffffffffu, full);
     if (fast) {
