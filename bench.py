@@ -386,6 +386,10 @@ def run_batch(args, rank, world, local_rank):
         P.pdmts_ctx_destroy(c)
     if rank != 0:
         return
+    accuracy = None
+    if args.accuracy_steps != 0 and world == 1:
+        accuracy = run_batch_accuracy(P, dev, stream, all_cps, 20 if args.accuracy_steps < 0 else args.accuracy_steps,
+                                      args.batch_accuracy_members, args.accuracy_budget_s)
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline("batch", "a plate of the same kind")
@@ -417,6 +421,7 @@ def run_batch(args, rank, world, local_rank):
                      "traffic": None, "peak_kind": peak_kind, "kernel": "k_pd_step_lattice2d_batch (whole round)",
                      "algorithmic_bytes_per_step": sub_bytes / args.steps},
         "cpu_baseline": cpu,
+        "accuracy": accuracy,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
@@ -535,6 +540,10 @@ def run_ours(args, rank, world, local_rank):
     if args.accuracy_steps != 0:
         accuracy, fp64_form = run_accuracy(P, dev, stream, args.workload, args.accuracy_steps,
                                            args.accuracy_budget_s)
+        if args.workload == "coupled":
+            from paper_2403_03605_gb300 import workloads as W
+            accuracy["full_length"] = run_accuracy_full_length(P, dev, stream, W.coupled_plate_400x64(),
+                                                               args.accuracy_budget_s)
 
     # ---- CPU baseline: the FP64 oracle on a bounded sample ----------------
     cpu = None
@@ -667,9 +676,14 @@ def run_accuracy(P, dev, stream, workload, n_steps, budget_s):
     # the timed chains are the free chains (every substep evaluates every
     # intact bond of the subdomain; link chains are not timed)
     ops = {2: 26, 3: 37}[pb.dim] + (4 if coupled else 0)
+    # the method's own minimum per bond (no per-bond micromodulus: 2 sub xi,
+    # 2 sub eta, 2 xi.eta, 4 |xi+eta|^2, 2 |xi|^2, 2 compare/scale, 4 force
+    # and accumulate in 2D; 26 in 3D)
+    ops_min = {2: 18, 3: 26}[pb.dim]
     chain_s = r64["chain_ms"] * 1e-3
     intact = int(np.count_nonzero(r64["mu"]))
     achieved = ops * intact * r64["chain_sub"] / chain_s / 1e9 if chain_s > 0 else None
+    achieved_min = ops_min * intact * r64["chain_sub"] / chain_s / 1e9 if chain_s > 0 else None
     peak = 1250.0 / 2
     fp64 = {"value": r64["value"], "unit": UNIT, "ms_per_step": r64["ms"] / (steps - 1),
             "fp32_bulk_value_same_steps": res["fp32_bulk"]["value"],
@@ -680,10 +694,114 @@ def run_accuracy(P, dev, stream, workload, n_steps, budget_s):
                          "peak_kind": "nominal FP64 rate 1.25 TFLOP/s (FMA = 2 flops) / 2: each non-fused op "
                                       "takes one FMA slot",
                          "kernel": f"k_pd_step_f64<{pb.dim}>", "ops_per_bond": ops,
+                         "ops_per_bond_method_minimum": ops_min,
+                         "frac_at_method_minimum": achieved_min / peak if achieved_min else None,
                          "launch_us": 1e3 * r64["chain_ms"] / max(r64["chain_sub"], 1),
                          "time_basis": "free substep chains (CUDA events around each chain) x the bonds "
                                        "intact at the end of the run"}}
     return acc, fp64
+
+
+def run_accuracy_full_length(P, dev, stream, cp, budget_s):
+    """FP32-bulk against FP64 over a coupled configuration's whole length
+    (cp.n_coarse coarse steps) on the 100 x 40 mm plate at dx = 0.25 mm (25,600
+    PD nodes, m = 10, 200 coarse steps), where the FP64 run and its interface
+    rebuilds fit a bench; the FP64 run stops early only past budget_s."""
+    from paper_2403_03605_gb300 import diagnostics as D
+    res = {}
+    n_steps = cp.n_coarse
+    for name, prec in (("fp64", P.PDMTS_FP64), ("fp32_bulk", P.PDMTS_FP32_BULK)):
+        ctx = P.pdmts_ctx_create(dev.index, stream.cuda_stream)
+        try:
+            pd, fe, arl = make_coupled(P, ctx, cp, precision=prec)
+            t0, done = time.perf_counter(), 0
+            while done < n_steps:
+                P.mts_advance(ctx, 1)
+                done += 1
+                if name == "fp64" and done % 10 == 0:
+                    P.pdmts_get_stats(ctx)  # synchronises: the budget counts device time
+                    if time.perf_counter() - t0 > budget_s:
+                        n_steps = done
+            res[name] = {"u": P.pd_read_displacement(pd), "mu": P.pd_read_bond_status(pd)[0],
+                         "phi": P.pd_read_damage(pd), "uf": P.fem_read_displacement(fe, cp.pd.dim * cp.fe.n),
+                         "steps": done, "rebuilds": P.arlequin_info(arl)["rebuilds"],
+                         "wall_s": time.perf_counter() - t0}
+        finally:
+            P.pdmts_ctx_destroy(ctx)
+    crack, band = ACCURACY_CRACK["coupled"]
+    acc = D.compare(res["fp32_bulk"], res["fp64"], cp.pd.lat.X, crack, band)
+    acc = {k: (round(v, 12) if isinstance(v, float) else v) for k, v in acc.items()}
+    acc.update({"workload": "coupled_plate_100x40mm_pd400x64_fe1mm_m10", "coarse_steps": res["fp64"]["steps"],
+                "configuration_length": cp.n_coarse, "physical_time_s": res["fp64"]["steps"] * cp.m * cp.dt_pd,
+                "interface_builds": {k: res[k]["rebuilds"] for k in res},
+                "wall_s": {k: round(res[k]["wall_s"], 1) for k in res},
+                "tolerance": {"u_pd_rel_l2": 1e-4, "broken_mismatch_frac": 1e-3}})
+    return acc
+
+
+def run_batch_accuracy(P, dev, stream, all_cps, n_rounds, n_members, budget_s):
+    """The stated error of the batched FP32-bulk path: a spread of members of
+    the batched workload (every len/n-th, so sizes and m vary) advanced as one
+    FP32-bulk batch from rest for n_rounds rounds, each compared with its own
+    FP64 solo run of the same coarse steps (the FP64 path is bit-identical to
+    the FP64 oracle in the parity tests). Members are added while the FP64
+    runs stay within budget_s of wall time. Reports the worst member and each
+    member's figures."""
+    import torch
+    from paper_2403_03605_gb300 import diagnostics as D
+    n_rounds = max(n_rounds, 1)
+    stride = max(1, len(all_cps) // max(n_members, 1))
+    pick = list(range(0, len(all_cps), stride))[:n_members]
+    t0 = time.perf_counter()
+    ref = {}
+    for k in pick:  # FP64 solo runs, within the budget
+        if ref and time.perf_counter() - t0 > budget_s:
+            break
+        cp = all_cps[k]
+        ctx = P.pdmts_ctx_create(dev.index, stream.cuda_stream)
+        try:
+            pd, fe, arl = make_coupled(P, ctx, cp, precision=P.PDMTS_FP64)
+            P.mts_advance(ctx, n_rounds)
+            ref[k] = {"u": P.pd_read_displacement(pd), "mu": P.pd_read_bond_status(pd)[0],
+                      "phi": P.pd_read_damage(pd), "uf": P.fem_read_displacement(fe, cp.pd.dim * cp.fe.n),
+                      "rebuilds": P.arlequin_info(arl)["rebuilds"]}
+        finally:
+            P.pdmts_ctx_destroy(ctx)
+    fp64_s = time.perf_counter() - t0
+    members = sorted(ref)
+    ctxs, handles = [], []
+    for k in members:
+        ctx = P.pdmts_ctx_create(dev.index, stream.cuda_stream)
+        ctxs.append(ctx)
+        handles.append(make_coupled(P, ctx, all_cps[k]))
+    batch = P.mts_batch_create(ctxs)
+    rows = []
+    try:
+        P.mts_batch_advance(batch, n_rounds)
+        torch.cuda.synchronize(dev)
+        crack, band = ACCURACY_CRACK["coupled"]
+        for k, (pd, fe, arl) in zip(members, handles):
+            cp = all_cps[k]
+            got = {"u": P.pd_read_displacement(pd), "mu": P.pd_read_bond_status(pd)[0],
+                   "phi": P.pd_read_damage(pd), "uf": P.fem_read_displacement(fe, cp.pd.dim * cp.fe.n)}
+            acc = D.compare(got, ref[k], cp.pd.lat.X, crack, band)
+            rows.append({"member": k, "pd_nodes": cp.pd.n, "m": cp.m, "u_pd_rel_l2": acc["u_pd_rel_l2"],
+                         "u_fe_rel_l2": acc.get("u_fe_rel_l2"), "broken_mismatch_frac": acc["broken_mismatch_frac"],
+                         "n_broken_ref": acc["n_broken_ref"], "crack_tip_error_m": acc["crack_tip_error_m"],
+                         "interface_builds": {"fp64": ref[k]["rebuilds"], "fp32_bulk": P.arlequin_info(arl)["rebuilds"]}})
+    finally:
+        P.mts_batch_destroy(batch)
+        for c in ctxs:
+            P.pdmts_ctx_destroy(c)
+    def worst(key):
+        vals = [r[key] for r in rows if r.get(key) is not None and not (isinstance(r[key], float) and np.isnan(r[key]))]
+        return max(vals) if vals else None
+    return {"vs": "each member's FP64 solo GPU run (bit-identical to the FP64 oracle in the parity tests)",
+            "members_compared": len(rows), "members_in_batch": len(all_cps), "coarse_steps": n_rounds,
+            "u_pd_rel_l2": worst("u_pd_rel_l2"), "u_fe_rel_l2": worst("u_fe_rel_l2"),
+            "broken_mismatch_frac": worst("broken_mismatch_frac"), "crack_tip_error_m": worst("crack_tip_error_m"),
+            "tolerance": {"u_pd_rel_l2": 1e-4, "broken_mismatch_frac": 1e-3},
+            "fp64_wall_s": round(fp64_s, 1), "per_member": rows}
 
 
 def kernel_version():
@@ -706,6 +824,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=["coupled", "pd", "batch", "coupled3d"], default="coupled")
     ap.add_argument("--batch-members", type=int, default=64, help="members of the batched workload")
+    ap.add_argument("--batch-accuracy-members", type=int, default=8,
+                    help="batch members compared with their FP64 solo runs (a spread over the list)")
     ap.add_argument("--accuracy-steps", type=int, default=-1,
                     help="coarse steps (pure PD: chains) of the FP32-bulk vs FP64 accuracy run; "
                          "-1: 60 (coupled), 30 (coupled3d), 100 (pd); 0: skip")

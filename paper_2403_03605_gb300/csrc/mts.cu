@@ -2499,7 +2499,11 @@ static int batch_plan(pdmts_batch *b, bool link, pdmts_batch::Plan **out)
                 cur = (cur0[(size_t)i] + j) & 1;
                 const double theta = link ? A->theta_link[(size_t)j] : A->theta_free[(size_t)j];
                 const F32NodeArgs N = pd->f32_node_args(false, theta, link);
+                // substep j of a link run evaluates that substep's window, as
+                // the member's own link chain does
+                pd->chain_k = j;
                 Lat2DArgs L = pd->lattice_args(N, link ? pd->d_mask_link.p : pd->d_mask.p, link);
+                pd->chain_k = 0;
                 L.tile = b->tile;
                 const int ntiles = lattice2d_batch_prepare(L, b->tile);
                 if (ntiles < 0)
@@ -2550,8 +2554,12 @@ static int batch_phase(pdmts_batch *b, bool link)
         b->kernel_launches += 1;
         b->work_items += nwork;
         for (int i = 0; i < nm; ++i)
-            if (j < b->members[(size_t)i]->m_ratio)
-                b->members[(size_t)i]->arl->pd->substep_done(false, link);
+            if (j < b->members[(size_t)i]->m_ratio) {
+                pdmts_pd *pd = b->members[(size_t)i]->arl->pd;
+                pd->chain_k = j;  // the bonds substep j evaluates
+                pd->substep_done(false, link);
+                pd->chain_k = 0;
+            }
     }
     return PDMTS_OK;
 }

@@ -233,6 +233,27 @@ def test_batch_members_match_the_oracle(fresh):
         assert g.residual() <= 1e-5
 
 
+def test_batch_equals_solo_with_growing_link_windows(fresh):
+    """Members of the batched workload's kind (the 100 x 40 mm plate, 16 mm PD
+    strip at dx = 0.28 and 0.23 mm, m = 5 and 10): a link run's early
+    substeps reach only the rows near the overlap bands, so each substep
+    evaluates its own window of rows. Batched, every member gets the bits of
+    its solo run, and counts the same bond updates."""
+    cps = [W.batch_member(20_000, 0.030, 1.0e7, 5, n_coarse=3), W.batch_member(30_000, 0.045, 1.2e7, 10, n_coarse=3)]
+    rounds = 3
+    solo = [GpuMTS(fresh(), cp, P.PDMTS_FP32_BULK).run(rounds) for cp in cps]
+    members = [GpuMTS(fresh(), cp, P.PDMTS_FP32_BULK) for cp in cps]
+    b = P.mts_batch_create([g.ctx for g in members])
+    try:
+        P.mts_batch_advance(b, rounds)
+    finally:
+        P.mts_batch_destroy(b)
+    for g, s_ in zip(members, solo):
+        for a, b_ in [(g.u(), s_.u()), (g.v(), s_.v()), (g.uf(), s_.uf()), (g.lam(), s_.lam()), (g.mu(), s_.mu())]:
+            assert np.array_equal(a, b_)
+        assert P.pdmts_get_stats(g.ctx)["bond_updates"] == P.pdmts_get_stats(s_.ctx)["bond_updates"]
+
+
 def test_batch_rejects_unsupported_members(fresh):
     cp = W.small_coupled(m=2, n_coarse=2)
     g64 = GpuMTS(fresh(), cp, P.PDMTS_FP64)
