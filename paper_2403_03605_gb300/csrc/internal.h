@@ -258,6 +258,11 @@ cudaError_t launch_constraint(int dim, int64_t nl, const int64_t *gpd_ptr, const
                               const float2 *v2, double h, const int32_t *gfe_col, const double *gfe_val, int gfe_w,
                               int64_t nfe, const double *vfe, double sign_pd, double sign_fe, double *y,
                               cudaStream_t s);
+// The PD part of launch_constraint (2D, sign_pd, no FE term) for nv FP32
+// velocity fields v4 + j v4_stride at once, into y + j y_stride.
+cudaError_t launch_constraint_pd_many(int64_t nl, const int64_t *gpd_ptr, const int32_t *gpd_col,
+                                      const double *gpd_val, int64_t npd, const float4 *v4, int64_t v4_stride,
+                                      int nv, double h, double sign_pd, double *y, int64_t y_stride, cudaStream_t s);
 // U_PD += W (u, v, a of the link state), then the prediction for the next
 // substep u + dt v + dt^2/2 a.
 struct PDAddLink {

@@ -216,7 +216,7 @@ struct pdmts_arl {
     bool H_valid = false, Hfe_valid = false, flag_pending = false;
     struct pdmts_batch *batch = nullptr;  // the batch this coupling belongs to, if any
     cusolverDnHandle_t solver = nullptr;  // dense Cholesky (or LU) for (-H)^-1
-    int64_t lu_inverses = 0;              // inverses that needed LU (-H not numerically definite)
+    int64_t lu_inverses = 0;              // inverses by LU
     // colouring of the multiplier columns for the link runs of build_H (per m):
     // colour c's unit multipliers and, per constraint row, the column it measures
     int colors_m = 0;
@@ -529,6 +529,9 @@ __global__ void k_hfe_cols(const int64_t nfe, const int dim, const int64_t nl, c
 __global__ void k_scatter_color(const int64_t nlam, const int32_t *__restrict__ owner, const double *__restrict__ y,
                                 const double sign, double *__restrict__ H)
 {
+    // blockIdx.y: one of several colours (owner rows and y of colour y at y nlam)
+    owner += (int64_t)blockIdx.y * nlam;
+    y += (int64_t)blockIdx.y * nlam;
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= nlam)
         return;
@@ -1883,10 +1886,12 @@ __global__ void k_identity(const int64_t n, double *__restrict__ M)
 // In-place inverse of the row-major n x n matrix M = -H (FP64, cuSOLVER).
 // -H is symmetric positive definite in exact arithmetic: Cholesky factorisation
 // and inversion from the factor (cuSOLVER's column-major lower triangle is
-// this row-major upper triangle; the lower one is mirrored afterwards). When
-// the measured operator is not (link runs in FP32 carry rounding into its
-// weakest directions), LU with partial pivoting of the full matrix: cuSOLVER
-// solves M^T X = I in its column-major view, and X read row-major is M^-1.
+// this row-major upper triangle; the lower one is mirrored afterwards). An
+// operator measured by FP32 link runs (FP32-bulk) carries their rounding in
+// its weakest directions and need not be numerically definite, and one that
+// fails Cholesky is not either: LU with partial pivoting of the full matrix,
+// where cuSOLVER solves M^T X = I in its column-major view, and X read
+// row-major is M^-1.
 static int invert_spd(pdmts_arl *A, double *M, int64_t n, cudaStream_t s, int64_t *launches)
 {
     if (n > INT32_MAX)
@@ -1920,12 +1925,17 @@ static int invert_spd(pdmts_arl *A, double *M, int64_t n, cudaStream_t s, int64_
     cudaError_t e = cudaMemcpyAsync(keep.p, M, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess)
         e = cudaMemsetAsync(info.p, 0, 2 * sizeof(int), s);
-    if (e != cudaSuccess ||
-        cusolverDnDpotrf(A->solver, CUBLAS_FILL_MODE_LOWER, ni, M, ni, work.p, lw, info.p) != CUSOLVER_STATUS_SUCCESS ||
-        cusolverDnDpotri(A->solver, CUBLAS_FILL_MODE_LOWER, ni, M, ni, work.p, lw, info.p + 1) !=
-            CUSOLVER_STATUS_SUCCESS ||
-        cudaMemcpyAsync(hinfo, info.p, sizeof(hinfo), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess) {
+    // an operator measured by FP32 link runs carries their rounding in its
+    // weakest directions and need not be numerically definite: LU at once
+    if (A->pd->precision != PDMTS_FP64) {
+        hinfo[0] = 1;
+    } else if (e != cudaSuccess ||
+               cusolverDnDpotrf(A->solver, CUBLAS_FILL_MODE_LOWER, ni, M, ni, work.p, lw, info.p) !=
+                   CUSOLVER_STATUS_SUCCESS ||
+               cusolverDnDpotri(A->solver, CUBLAS_FILL_MODE_LOWER, ni, M, ni, work.p, lw, info.p + 1) !=
+                   CUSOLVER_STATUS_SUCCESS ||
+               cudaMemcpyAsync(hinfo, info.p, sizeof(hinfo), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+               cudaStreamSynchronize(s) != cudaSuccess) {
         cleanup();
         return fail(PDMTS_ERR_CUDA, "Cholesky inverse failed: %s", cudaGetErrorString(cudaGetLastError()));
     }
@@ -1953,6 +1963,126 @@ static int invert_spd(pdmts_arl *A, double *M, int64_t n, cudaStream_t s, int64_
     return r;
 }
 
+// The PD columns of H for an FP32-bulk 2D lattice, up to kLinkGroup colours
+// at a time: every colour of a group gets its own link state (a slot of one
+// pool), the m substeps of all the group's link runs are one batched launch
+// each over the (colour, tile) work items of that substep's window, and each
+// colour's constraint rows are then scattered into H. The batched launch runs
+// the single-lattice tile code, so every column has the bits of its own link
+// run. Returns PDMTS_ERR_UNSUPPORTED (nothing enqueued) for other set-ups.
+constexpr int kLinkGroup = 32;
+static int build_H_pd_grouped(pdmts_arl *A, int m, double *H, cudaStream_t s, int64_t *launches)
+{
+    pdmts_pd *pd = A->pd;
+    const int64_t n = pd->n, nlam = A->nlam;
+    if (pd->precision == PDMTS_FP64 || pd->layout != pdmts_pd::LAYOUT_LATTICE2D || pd->dim != 2 || A->colors < 2)
+        return PDMTS_ERR_UNSUPPORTED;
+    // slots of 16 n floats (64 B per node): u4 x 2, v4, a (float2), g (2 planes)
+    const int64_t slot_floats = 16 * n;
+    const int64_t budget = (int64_t)1 << 31;
+    const int G = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)kLinkGroup, A->colors,
+                                                                budget / (int64_t)(sizeof(float) * slot_floats)}));
+    if (G < 2)
+        return PDMTS_ERR_UNSUPPORTED;
+    constexpr int tile = 1;  // a batchable tile configuration (all give the same bits)
+    DevArr<float> pool;
+    DevArr<Lat2DArgs> d_args;
+    DevArr<int2> d_work;
+    DevArr<double> d_ys;
+    int r = A->alloc(pool, (int64_t)G * slot_floats);
+    if (r == PDMTS_OK)
+        r = A->alloc(d_ys, (int64_t)G * nlam);
+    auto cleanup = [&]() {
+        A->release(pool);
+        A->release(d_args);
+        A->release(d_work);
+        A->release(d_ys);
+    };
+    if (r != PDMTS_OK) {
+        cleanup();
+        return r;
+    }
+    auto slot = [&](int g) { return pool.p + (int64_t)g * slot_floats; };
+    // launch arguments and work items of every substep for G slots; the first
+    // q slots' items are a prefix of each substep's list
+    std::vector<Lat2DArgs> args((size_t)m * G);
+    std::vector<int2> work;
+    std::vector<int64_t> work_off((size_t)m * (G + 1));
+    for (int j = 0; j < m; ++j) {
+        for (int g = 0; g < G; ++g) {
+            float *b = slot(g);
+            F32NodeArgs N = pd->f32_node_args(false, A->theta_link[(size_t)j], true);
+            // substep j of a run started from W_0 = 0 (both buffers zero, a_0 = 0)
+            // reads buffer (j + 1) & 1 and writes buffer j & 1
+            float4 *u4[2] = {reinterpret_cast<float4 *>(b), reinterpret_cast<float4 *>(b + 4 * n)};
+            N.u4_in = u4[(j + 1) & 1];
+            N.u4_out = u4[j & 1];
+            N.v4 = reinterpret_cast<float4 *>(b + 8 * n);
+            N.a = b + 12 * n;
+            N.g = b + 14 * n;
+            N.u2_in = nullptr;
+            N.u2_out = nullptr;
+            N.v2 = nullptr;
+            pd->chain_k = j;
+            Lat2DArgs L = pd->lattice_args(N, pd->d_mask_link.p, true);
+            pd->chain_k = 0;
+            L.tile = tile;
+            const int nt = lattice2d_batch_prepare(L, tile);
+            if (nt < 0) {
+                cleanup();
+                return PDMTS_ERR_UNSUPPORTED;
+            }
+            work_off[(size_t)j * (G + 1) + g] = (int64_t)work.size();
+            for (int t = 0; t < nt; ++t)
+                work.push_back(make_int2(g, t));
+            args[(size_t)j * G + g] = L;
+        }
+        work_off[(size_t)j * (G + 1) + G] = (int64_t)work.size();
+    }
+    if ((r = A->alloc(d_args, (int64_t)args.size())) != PDMTS_OK ||
+        (r = A->alloc(d_work, (int64_t)std::max<size_t>(work.size(), 1))) != PDMTS_OK ||
+        (r = h2d(d_args.p, args, s)) != PDMTS_OK || (r = h2d(d_work.p, work, s)) != PDMTS_OK) {
+        cleanup();
+        return r;
+    }
+    const bool pmb = pd->force_kind == PDMTS_FORCE_PMB;
+    cudaError_t e = cudaSuccess;
+    int64_t bonds_per_run = 0;
+    for (int j = 0; j < m; ++j)
+        bonds_per_run += pd->substep_bonds(true, j);
+    for (int64_t c0 = 0; c0 < A->colors && e == cudaSuccess; c0 += G) {
+        const int q = (int)std::min<int64_t>(G, A->colors - c0);
+        e = cudaMemsetAsync(pool.p, 0, sizeof(float) * slot_floats * q, s);
+        for (int g = 0; g < q && e == cudaSuccess; ++g)
+            e = launch_interface_force(pd->dim, n, A->n_ov, A->d_ov_node.p, A->d_ov_k.p, A->d_ov_N.p, A->corners,
+                                       A->d_units.p + (c0 + g) * nlam, A->nl, 1.0 / pd->h, nullptr, slot(g) + 14 * n,
+                                       s);
+        for (int j = 0; j < m && e == cudaSuccess; ++j) {
+            const int64_t w0 = work_off[(size_t)j * (G + 1)], w1 = work_off[(size_t)j * (G + 1) + q];
+            e = launch_lattice2d_batch(d_args.p + (int64_t)j * G, d_work.p + w0, (int)(w1 - w0), tile, pmb, s);
+        }
+        // y = G_PD v_link of every colour of the group, scattered into H
+        if (e == cudaSuccess)
+            e = launch_constraint_pd_many(A->nl, A->d_gpd_ptr.p, A->d_gpd_col.p, A->d_gpd_val.p, n,
+                                          reinterpret_cast<const float4 *>(slot(0) + 8 * n), slot_floats / 4, q,
+                                          pd->h, 1.0, d_ys.p, nlam, s);
+        if (e == cudaSuccess) {
+            k_scatter_color<<<dim3(blocks(nlam), (unsigned)q), 256, 0, s>>>(nlam, A->d_owners.p + c0 * nlam, d_ys.p,
+                                                                           -1.0, H);
+            e = cudaGetLastError();
+        }
+        *launches += 3 + (int64_t)q + m;
+        pd->ctx->stats.pd_substeps += (int64_t)q * m;
+        pd->ctx->stats.bond_updates += (int64_t)q * bonds_per_run;
+    }
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(s);  // the pool and the work lists are released below
+    cleanup();
+    if (e != cudaSuccess)
+        return fail(PDMTS_ERR_CUDA, "grouped link runs: %s", cudaGetErrorString(e));
+    return PDMTS_OK;
+}
+
 // Interface operator H = G_FE Ydot_FE - G_PD Ydot_PD (Eq. 49) and its inverse.
 // Columns of H_PD come from link runs of several unit multipliers at once:
 // columns whose supports are more than 2R apart (R = 2 h_FE + m delta, the
@@ -1974,7 +2104,10 @@ static int build_H(pdmts_arl *A, int m)
     PDMTS_CUDA_TRY(cudaMemcpyAsync(H, A->d_Hfe.p, sizeof(double) * nlam * nlam, cudaMemcpyDeviceToDevice, s));
     PDMTS_TRY(build_colors(A, m, s));
     const bool f64 = pd->precision == PDMTS_FP64;
-    for (int64_t cidx = 0; cidx < A->colors; ++cidx) {
+    const int gr = build_H_pd_grouped(A, m, H, s, &launches);
+    if (gr != PDMTS_OK && gr != PDMTS_ERR_UNSUPPORTED)
+        return gr;
+    for (int64_t cidx = 0; gr == PDMTS_ERR_UNSUPPORTED && cidx < A->colors; ++cidx) {
         PDMTS_TRY(pd_link_run(A, A->d_units.p + cidx * nlam, m, s));
         // y = G_PD v_link
         cudaError_t e = launch_constraint(pd->dim, nl, A->d_gpd_ptr.p, A->d_gpd_col.p, A->d_gpd_val.p, pd->n,

@@ -428,10 +428,14 @@ __global__ void k_constraint(const int dim, const int64_t nl, const int64_t *__r
                              const float2 *__restrict__ v2, const double h, const int32_t *__restrict__ gfe_col,
                              const double *__restrict__ gfe_val, const int gfe_w, const int64_t nfe,
                              const double *__restrict__ vfe, const double sign_pd, const double sign_fe,
-                             double *__restrict__ y)
+                             double *__restrict__ y, const int64_t v4_stride, const int64_t y_stride)
 {
     // one warp per multiplier node k, all components (rows c nl + k): the PD
-    // velocities of the node's support are gathered once for every component
+    // velocities of the node's support are gathered once for every component;
+    // blockIdx.y picks one of several FP32 velocity fields (v4 + y v4_stride)
+    // and its output rows (y + y y_stride)
+    v4 += (int64_t)blockIdx.y * v4_stride;
+    y += (int64_t)blockIdx.y * y_stride;
     const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (k >= nl)
@@ -647,7 +651,21 @@ cudaError_t launch_constraint(int dim, int64_t nl, const int64_t *gpd_ptr, const
         return cudaErrorInvalidValue;
     k_constraint<<<(unsigned)((nl * 32 + 255) / 256), 256, 0, s>>>(dim, nl, gpd_ptr, gpd_col, gpd_val, npd, v64, v4,
                                                                       v2, h, gfe_col, gfe_val, gfe_w, nfe, vfe,
-                                                                      sign_pd, sign_fe, y);
+                                                                      sign_pd, sign_fe, y, 0, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_constraint_pd_many(int64_t nl, const int64_t *gpd_ptr, const int32_t *gpd_col,
+                                      const double *gpd_val, int64_t npd, const float4 *v4, int64_t v4_stride,
+                                      int nv, double h, double sign_pd, double *y, int64_t y_stride, cudaStream_t s)
+{
+    if (nl == 0 || nv <= 0)
+        return cudaSuccess;
+    if (nv > 65535)
+        return cudaErrorInvalidValue;
+    const dim3 grid((unsigned)((nl * 32 + 255) / 256), (unsigned)nv);
+    k_constraint<<<grid, 256, 0, s>>>(2, nl, gpd_ptr, gpd_col, gpd_val, npd, nullptr, v4, nullptr, h, nullptr, nullptr,
+                                      0, 0, nullptr, sign_pd, 0.0, y, v4_stride, y_stride);
     return cudaGetLastError();
 }
 
