@@ -621,18 +621,26 @@ __device__ __forceinline__ void pair_gather(const LatPair<KR> &P, float2 (&f)[KR
 // WAIT_B < 0: group B came by tensor copies completing phase parity parB of
 // S.bar[1]; if that wait gives up the CTA returns kTileGaveUp at once.
 constexpr unsigned kTileGaveUp = ~0u;
+
+// Whether the halo rows of the tile at row y0 carry an Arlequin weight. A
+// tile whose halo carries none evaluates every bond with weight 1 exactly, so
+// it can skip the weights. Read before the tile's inputs are awaited, so that
+// the two loads' latency hides behind the staging.
+template <int KR>
+__device__ __forceinline__ bool tile_has_alpha(const Lat2DArgs &A, const int y0)
+{
+    constexpr int HY = LatStage<KR>::HY;
+    return A.alpha && A.alpha_rows[min(A.ny, y0 + HY - lat2d::R)] - A.alpha_rows[max(0, y0 - lat2d::R)] > 0;
+}
+
 template <bool PMB, int KR, int WAIT_B, bool PAIR = false>
 __device__ __forceinline__ unsigned lattice_tile(LatStage<KR> &S, const Lat2DArgs &A, const int x0, const int y0,
-                                                 const int init, LatPair<KR> *P = nullptr, const unsigned parB = 0)
+                                                 const int init, const bool has_alpha, LatPair<KR> *P = nullptr,
+                                                 const unsigned parB = 0)
 {
     using namespace lat2d;
-    constexpr int HY = LatStage<KR>::HY;
     const F32NodeArgs &N = A.nd;
     const int nx = A.nx, ny = A.ny;
-    // a tile whose halo rows carry no Arlequin weight evaluates every bond
-    // with weight 1 exactly, so it can skip the weights
-    const bool has_alpha =
-        A.alpha && A.alpha_rows[min(ny, y0 + HY - R)] - A.alpha_rows[max(0, y0 - R)] > 0;
     if constexpr (WAIT_B >= 0)
         __syncthreads();  // every thread's asynchronous copies of group A are visible
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
@@ -759,12 +767,13 @@ __global__ void __launch_bounds__(256, MINB) k_pd_step_lattice2d(const Lat2DArgs
     LatPair<KR> *P = PAIR ? reinterpret_cast<LatPair<KR> *>(lat_smem + sizeof(LatStage<KR>)) : nullptr;
     const int x0 = blockIdx.x * lat2d::TX, y0 = lattice_trow(A, (int)blockIdx.y) * LatStage<KR>::TYK;
     lattice_chain_entry();
+    const bool ha = tile_has_alpha<KR>(A, y0);
     lattice_issue_a<KR>(S, A, x0, y0);
     cp_async_commit();
     lattice_issue_b<KR>(S, A, x0, y0);
     cp_async_commit();
     cp_async_wait<1>();
-    const unsigned nbroken = lattice_tile<PMB, KR, 0, PAIR>(S, A, x0, y0, init, P);
+    const unsigned nbroken = lattice_tile<PMB, KR, 0, PAIR>(S, A, x0, y0, init, ha, P);
     count_broken(A.nd.broken, nbroken);
 }
 
@@ -788,6 +797,7 @@ __global__ void __launch_bounds__(256, MINB) k_pd_step_lattice2d_tma(const Lat2D
     lattice_chain_entry();
     if (threadIdx.x == 0)
         lattice_tma_issue<KR>(S, M, A, x0, y0);
+    const bool ha = tile_has_alpha<KR>(A, y0);
     const bool ok = mbar_wait(&S.bar[0], 0, A.first_polls);
     if (__syncthreads_or(!ok)) {
         tma_gave_up(A);
@@ -795,7 +805,7 @@ __global__ void __launch_bounds__(256, MINB) k_pd_step_lattice2d_tma(const Lat2D
         mbar_wait(&S.bar[1], 0);
         return;
     }
-    const unsigned nbroken = lattice_tile<PMB, KR, -1>(S, A, x0, y0, init);
+    const unsigned nbroken = lattice_tile<PMB, KR, -1>(S, A, x0, y0, init, ha);
     if (nbroken != kTileGaveUp)
         count_broken(A.nd.broken, nbroken);
 }
@@ -838,6 +848,8 @@ __global__ void __launch_bounds__(256, MINB) k_pd_step_lattice2d_tpipe(const Lat
     for (int t = blockIdx.x; t < ntiles; t += G, ++k) {
         LatStage<KR> &S = stages[k & 1];
         const unsigned par = (unsigned)(k >> 1) & 1u;
+        const int x0 = (t % ntx) * lat2d::TX, y0 = lattice_trow(A, t / ntx) * TYK;
+        const bool ha = tile_has_alpha<KR>(A, y0);
         const bool ok = mbar_wait(&S.bar[0], par, A.first_polls);
         if (__syncthreads_or(!ok)) {  // give up: let this tile's and the other stage's copies land first
             tma_gave_up(A);
@@ -849,8 +861,7 @@ __global__ void __launch_bounds__(256, MINB) k_pd_step_lattice2d_tpipe(const Lat
             }
             return;
         }
-        const int x0 = (t % ntx) * lat2d::TX, y0 = lattice_trow(A, t / ntx) * TYK;
-        const unsigned r = lattice_tile<PMB, KR, -1>(S, A, x0, y0, init, nullptr, par);
+        const unsigned r = lattice_tile<PMB, KR, -1>(S, A, x0, y0, init, ha, nullptr, par);
         if (r == kTileGaveUp) {
             if (t + G < ntiles) {
                 mbar_wait(&stages[(k + 1) & 1].bar[0], (unsigned)((k + 1) >> 1) & 1u);
@@ -897,10 +908,11 @@ __global__ void __launch_bounds__(256, MINB) k_pd_step_lattice2d_pipe(const Lat2
     int k = 0;
     for (int t = blockIdx.x; t < ntiles; t += G, ++k) {
         LatStage<KR> &S = stages[k & 1];
+        const int x0 = (t % ntx) * lat2d::TX, y0 = lattice_trow(A, t / ntx) * TYK;
+        const bool ha = tile_has_alpha<KR>(A, y0);
         // pending, newest first: B(t+G), A(t+G), B(t); A(t) has landed
         cp_async_wait<3>();
-        const int x0 = (t % ntx) * lat2d::TX, y0 = lattice_trow(A, t / ntx) * TYK;
-        nbroken += lattice_tile<PMB, KR, 2>(S, A, x0, y0, init);
+        nbroken += lattice_tile<PMB, KR, 2>(S, A, x0, y0, init, ha);
         __syncthreads();  // every thread is done with S
         issue(S, t + 2 * G);
     }
@@ -932,12 +944,13 @@ __global__ void __launch_bounds__(256, MINB) k_pd_step_lattice2d_batch(const Lat
     const Lat2DArgs &A = sA;
     const int ntx = (A.nx + lat2d::TX - 1) / lat2d::TX;
     const int x0 = (w.y % ntx) * lat2d::TX, y0 = lattice_trow(A, w.y / ntx) * LatStage<KR>::TYK;
+    const bool ha = tile_has_alpha<KR>(A, y0);
     lattice_issue_a<KR>(S, A, x0, y0);
     cp_async_commit();
     lattice_issue_b<KR>(S, A, x0, y0);
     cp_async_commit();
     cp_async_wait<1>();
-    const unsigned nbroken = lattice_tile<PMB, KR, 0>(S, A, x0, y0, init);
+    const unsigned nbroken = lattice_tile<PMB, KR, 0>(S, A, x0, y0, init, ha);
     count_broken(A.nd.broken, nbroken);
 }
 
