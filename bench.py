@@ -66,6 +66,46 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def stored_counters(workload, tile):
+    """Per-launch ncu figures of the lattice kernel (DRAM bytes, warp
+    instructions, SM-side L2 bytes) stored in profiles/traffic.json, or {} when
+    absent or measured on other kernel source; and the L2 sector bandwidth
+    ncu reports as the peak of this GPU."""
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(tfile) as f:
+            tj = json.load(f)
+        ent = tj.get(workload, {}).get(str(tile), {})
+        return (ent if ent.get("kernel_version") == kernel_version(workload) else {}), tj.get("l2_peak_gbs")
+    except Exception:
+        return {}, None
+
+
+def issue_and_l2(ent, launch_ms, clocks, n_sm, l2_peak):
+    """Instruction-issue and L2 lines for a kernel whose chain stays in L2:
+    warp instructions per launch against the issue peak (one warp instruction
+    per cycle on each of the four schedulers of every SM, at the median SM
+    clock sampled in the timed region), and the SM-side L2 bytes per launch
+    against ncu's nominal L2 sector rate. Per-launch counts are ncu's; the
+    launch time is the live CUDA-event figure. A plain device copy between two
+    L2-resident 32 MB buffers reaches about 8.2 TB/s on this GPU, so the L2
+    fraction reads against a nominal ceiling, not a measured one."""
+    mhz = clocks.get("sm_mhz") or 2070.0
+    ipeak = n_sm * 4 * mhz * 1e6
+    winst = ent.get("warp_instructions_per_launch")
+    iach = winst / (launch_ms * 1e-3) if winst else None
+    issue = {"warp_instructions_per_launch": winst, "achieved": iach, "peak": ipeak,
+             "unit": "warp instructions/s", "frac": iach / ipeak if iach else None,
+             "peak_kind": f"{n_sm} SMs x 4 schedulers x {mhz:.0f} MHz (sampled)"}
+    lb = ent.get("l2_bytes_per_launch")
+    lach = lb / (launch_ms * 1e-3) / 1e9 if lb else None
+    l2 = {"bytes_per_launch": lb, "achieved": lach, "peak": l2_peak, "unit": "GB/s",
+          "frac": lach / l2_peak if lach and l2_peak else None,
+          "peak_kind": "nominal: ncu's peak L2 sector rate on this GPU (188 slices x 3 sectors x 32 B per L2 cycle)",
+          "source": "ncu lts__t_sectors_srcunit_tex.sum x 32 B"}
+    return issue, l2
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
@@ -497,18 +537,12 @@ def run_ours(args, rank, world, local_rank):
                    "k_pd_step_lattice2d_tma<false,2,3>", "k_pd_step_lattice2d_tpipe<false,2,2>",
                    "k_pd_step_lattice2d_tpipe<false,1,4>", "k_pd_step_lattice2d_tma<false,4,2>"]
     kname = (lat_kernels[tile] if info["layout"] == 1 and tile >= 0 else
-             "k_pd_step_lattice3d<false,false>" if info["layout"] == 2 else f"k_pd_step_f32<{info['dim']}>")
-    traffic = None
-    tfile = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tfile):
-        try:
-            with open(tfile) as f:
-                tj = json.load(f)
-            ent = tj.get(args.workload, {}).get(str(tile), {})
-            if ent.get("kernel_version") == kernel_version():
-                traffic = ent["dram_bytes_per_launch"]
-        except Exception:
-            traffic = None
+             f"k_pd_step_lattice3d<{8 if tile == 1 else 4},{int(coupled)},0>" if info["layout"] == 2
+             else f"k_pd_step_f32<{info['dim']}>")
+    ent, l2_peak = stored_counters(args.workload, tile)
+    traffic = ent.get("dram_bytes_per_launch")
+    issue, l2 = issue_and_l2(ent, launch_ms, clk.summary(),
+                             torch.cuda.get_device_properties(dev).multi_processor_count, l2_peak)
 
     # ---- end to end through the C ABI with host buffers ------------------
     # each step: upload a PD body-force field from pinned host memory, advance
@@ -575,6 +609,8 @@ def run_ours(args, rank, world, local_rank):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind, "kernel": kname,
                          "algorithmic_bytes_per_launch": abytes, "launch_us": launch_ms * 1e3},
+            "issue_rate": issue,
+            "l2_bandwidth": l2,
             "cpu_baseline": cpu,
             "accuracy": accuracy,
             "fp64_form": fp64_form,
@@ -804,12 +840,15 @@ def run_batch_accuracy(P, dev, stream, all_cps, n_rounds, n_members, budget_s):
             "fp64_wall_s": round(fp64_s, 1), "per_member": rows}
 
 
-def kernel_version():
-    """Hash of the hot-path kernel source: a stored DRAM-traffic figure is only
-    reported while the kernel it was measured on is unchanged."""
+def kernel_version(workload="coupled"):
+    """Hash of the source of the lattice kernel a workload runs (2D: the 2D
+    kernel files; 3D: the 3D kernel and the headers it includes): a stored
+    ncu figure is only reported while that kernel is unchanged."""
     import hashlib
+    names = (("lattice3d.cu", "lattice2d.cuh", "f32_device.cuh") if workload == "coupled3d"
+             else ("lattice2d.cuh", "f32_device.cuh", "lattice2d_tma.cu"))
     h = hashlib.sha256()
-    for name in ("lattice2d.cuh", "f32_device.cuh", "lattice2d_tma.cu", "lattice3d.cu"):
+    for name in names:
         with open(os.path.join(ROOT, "paper_2403_03605_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]

@@ -380,7 +380,7 @@ void pdmts_pd::release_all()
     release(d_mask); release(d_V); release(d_out); release(d_b); release(d_exists);
     release(d_X); release(d_cb); release(d_alpha); release(d_mass); release(d_wb); release(d_g);
     release(d_v); release(d_a); release(d_u[0]); release(d_u[1]);
-    release(d_stencil); release(f_alpha); release(f_invm); release(f_wb); release(f_g); release(f_rowalpha);
+    release(d_stencil); release(f_alpha); release(f_invm); release(f_wb); release(f_g); release(f_rowalpha); release(d_rowtab);
     release(f_v4); release(f_v2); release(f_a);
     release(f_u4[0]); release(f_u4[1]); release(f_u2[0]); release(f_u2[1]);
     release(lk_u[0]); release(lk_u[1]); release(lk_v); release(lk_a); release(lk_g);
@@ -778,6 +778,45 @@ static double micromodulus_host(const pdmts_pd *pd, double xi2)
 // Device arrays of the family and the state.
 static int alloc_f32_state(pdmts_pd *pd);
 
+// The 3D lattice kernel's row table: per stencil row (dz, dy) the per-|d|^2
+// constants of its bonds (the expressions and rounding of the sliced-ELL
+// stencil table), its node offset and its reach in dx.
+static int upload_row_table(pdmts_pd *pd)
+{
+    const lat3d::RowTab t = lat3d::make_row_tab();
+    const double h = pd->h;
+    const int64_t nx = pd->lat_dims[0], ny = pd->lat_dims[1];
+    if (3 * nx * ny > (int64_t)INT32_MAX)
+        return fail(PDMTS_ERR_UNSUPPORTED, "pd_create: 3D lattice planes of %lld nodes too large",
+                    (long long)(nx * ny));
+    std::vector<Row3DEnt> rows(lat3d::NR);
+    for (int r = 0; r < lat3d::NR; ++r) {
+        const int dy = t.dy[r], dz = t.dz[r];
+        float c[4] = {0.f, 0.f, 0.f, 0.f}, q[4] = {0.f, 0.f, 0.f, 0.f}, rr[4] = {0.f, 0.f, 0.f, 0.f},
+              rd[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int a = 0; a < 4; ++a) {
+            const int r2 = dy * dy + dz * dz + a * a;
+            if (r2 > 9)
+                continue;
+            c[a] = (float)(micromodulus_host(pd, r2 * h * h) * h * h * pd->V[0]);
+            q[a] = (float)(1.0 / r2);
+            rr[a] = (float)r2;
+            rd[a] = (float)std::sqrt((double)r2);
+        }
+        Row3DEnt &E = rows[(size_t)r];
+        E.coef = make_float4(c[0], c[1], c[2], c[3]);
+        E.ir2 = make_float4(q[0], q[1], q[2], q[3]);
+        E.rr = make_float4(rr[0], rr[1], rr[2], rr[3]);
+        E.rd = make_float4(rd[0], rd[1], rd[2], rd[3]);
+        E.off = (int)(dz * nx * ny + dy * nx);
+        E.fdy = (float)dy;
+        E.fdz = (float)dz;
+        E.rx = t.rx[r];
+    }
+    PDMTS_TRY(pd->alloc(pd->d_rowtab, lat3d::NR));
+    return upload(pd->d_rowtab, rows.data(), lat3d::NR, pd->ctx->stream);
+}
+
 static int upload_family_and_state(pdmts_pd *pd)
 {
     cudaStream_t s = pd->ctx->stream;
@@ -792,6 +831,8 @@ static int upload_family_and_state(pdmts_pd *pd)
         PDMTS_TRY(upload(pd->d_mask, pd->mask_host.data(), nw, s));
         PDMTS_TRY(upload(pd->d_exists, pd->mask_host.data(), nw, s));
         PDMTS_TRY(upload(pd->d_V, pd->V.data(), n, s));
+        if (pd->layout == pdmts_pd::LAYOUT_LATTICE3D)
+            PDMTS_TRY(upload_row_table(pd));
         return alloc_f32_state(pd);
     }
     PDMTS_TRY(pd->alloc(pd->d_tile_ptr, pd->ntiles + 1));
@@ -1054,6 +1095,7 @@ pdmts::Lat3DArgs pdmts_pd::lattice3d_args(const pdmts::F32NodeArgs &N, uint32_t 
     A.exists = d_exists.p;
     A.alpha = f_alpha.p;
     A.alpha_rows = f_alpha.p ? f_rowalpha.p : nullptr;
+    A.rows = d_rowtab.p;
     for (int r2 = 1; r2 < 10; ++r2) {
         const double xi2 = r2 * h * h;
         A.coef[r2] = (float)(micromodulus_host(this, xi2) * h * h * V[0]);

@@ -166,13 +166,53 @@ struct Lat2DArgs {
 // |d|^2, rd = |d|, r2 = |d|^2, ir2 = 1 / |d|^2.
 namespace lat3d {
 constexpr int NS = 122, W = 4;
+// reach of a plane |dz| = a in dy: dy^2 <= 9 - a^2
+__host__ __device__ constexpr int reach_y(const int a) { return a == 0 ? 3 : a == 3 ? 0 : 2; }
+// reach of row dy of plane |dz| = a in dx: floor(sqrt(9 - a^2 - dy^2))
+__host__ __device__ constexpr int reach_x(const int a, const int dy)
+{
+    const int rem = 9 - a * a - dy * dy;
+    return rem < 0 ? -1 : rem >= 9 ? 3 : rem >= 4 ? 2 : rem >= 1 ? 1 : 0;
 }
+// The 29 stencil rows (dz, dy) in lexicographic order and their reach in dx.
+constexpr int NR = 29;
+struct RowTab {
+    signed char dy[NR], dz[NR], rx[NR];
+};
+__host__ __device__ constexpr RowTab make_row_tab()
+{
+    RowTab t{};
+    int r = 0;
+    for (int dz = -3; dz <= 3; ++dz) {
+        const int a = dz < 0 ? -dz : dz;
+        for (int dy = -reach_y(a); dy <= reach_y(a); ++dy) {
+            t.dy[r] = (signed char)dy;
+            t.dz[r] = (signed char)dz;
+            t.rx[r] = (signed char)reach_x(a, dy);
+            ++r;
+        }
+    }
+    return t;
+}
+}  // namespace lat3d
+// One stencil row of the 3D lattice kernel (a table of NR rows in device
+// memory, built once per PD body): per |dx| = 0..3 the coefficient
+// c(|xi|) h^2 V, 1/|d|^2, |d|^2 and |d| of the bond (dx, dy, dz) (zeros past
+// |d|^2 = 9), the row's offset dz nx ny + dy nx in the node numbering, dy and
+// dz as floats and its reach in dx.
+struct alignas(16) Row3DEnt {
+    float4 coef, ir2, rr, rd;
+    int off;
+    float fdy, fdz;
+    int rx;
+};
 struct Lat3DArgs {
     int nx, ny, nz;
     uint32_t *mask;
     const uint32_t *exists;     // bond words of the bonds that exist (all intact)
     const float *alpha;         // n (null when no weights)
     const int32_t *alpha_rows;  // ny + 1: rows y' < y with a weighted node (null when no weights)
+    const Row3DEnt *rows;       // the NR stencil rows (device)
     // indexed by |d|^2 up to 18 = 9 + 3^2 (a row's dy^2 + dz^2 plus dx^2); 0 past 9
     float coef[19], thr[10], rd[19], r2[19], ir2[19];
     float qfast;                // s0 (2 + s0) (1 - 2^-16): a bond at or past the critical stretch exceeds it

@@ -67,6 +67,7 @@ struct pdmts_pd {
     DevArr<pdmts::StencilEntry> d_stencil;
     int n_stencil = 0;
     DevArr<float> f_alpha, f_invm, f_wb, f_g;
+    DevArr<pdmts::Row3DEnt> d_rowtab;  // 3D lattice layout: the stencil rows' constants and offsets
     DevArr<int32_t> f_rowalpha;  // lattice layouts: ny + 1 prefix counts of the rows with a weighted node
     // state in lattice units, compensated pairs, per-node packed:
     // 2D: u4 = {hx, hy, lx, ly}; 3D: u4 = {hx, hy, hz, lx}, u2 = {ly, lz}
