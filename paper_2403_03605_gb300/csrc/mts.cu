@@ -573,6 +573,11 @@ __global__ void k_cheb_iter_node(const int64_t nfe, const int nrhs, const int W,
                                  double *__restrict__ x, double *__restrict__ r, const double *__restrict__ d,
                                  double *__restrict__ dn, const double c1, const double c2)
 {
+    // launched as a programmatic dependent of the previous kernel of the
+    // solve: wait for its results, then let the next iteration's CTAs take
+    // SM slots as they free up (no-ops when launched plainly)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nfe * nrhs)
         return;
@@ -650,6 +655,10 @@ __global__ void k_feb_link_init(const FeDev *__restrict__ M, const int2 *__restr
 
 __global__ void k_feb_cheb(const FeDev *__restrict__ M, const int2 *__restrict__ blk, const int k, const int link)
 {
+    // a programmatic dependent of the previous kernel of the solve (see
+    // k_cheb_iter_node)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int2 q = blk[blockIdx.x];
     const FeDev &F = M[q.x];
     const int64_t node = (int64_t)q.y + threadIdx.x;
@@ -1127,11 +1136,22 @@ static int fe_cheb_solve(pdmts_fem *fe, int nrhs, double *x, const double *b, do
     const int it = (int)fe->cheb_c1.size();
     for (int k = 0; k < it; ++k) {
         const bool last = k == it - 1;
-        if (fe->paired_rows)
-            k_cheb_iter_node<<<blocks(fe->n * nrhs), 256, 0, s>>>(fe->n, nrhs, fe->W, fe->d_col.p, fe->d_Keff.p,
-                                                                  fe->d_Minv.p, x, r, d, last ? nullptr : dn,
-                                                                  fe->cheb_c1[(size_t)k], fe->cheb_c2[(size_t)k]);
-        else
+        if (fe->paired_rows) {
+            // each iteration a programmatic dependent of the kernel before it
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(blocks(fe->n * nrhs));
+            cfg.blockDim = dim3(256);
+            cfg.stream = s;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+            at[0].val.programmaticStreamSerializationAllowed = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            PDMTS_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_cheb_iter_node, (int64_t)fe->n, nrhs, fe->W,
+                                              (const int32_t *)fe->d_col.p, (const double *)fe->d_Keff.p,
+                                              (const double *)fe->d_Minv.p, x, r, (const double *)d,
+                                              last ? nullptr : dn, fe->cheb_c1[(size_t)k], fe->cheb_c2[(size_t)k]));
+        } else
             k_cheb_iter_group<<<blocks(tot * kRowGroup), 256, 0, s>>>(
                 ndof, nrhs, fe->W, fe->d_col.p, fe->d_Keff.p, fe->d_Minv.p, x, r, d, last ? nullptr : dn,
                 fe->cheb_c1[(size_t)k], fe->cheb_c2[(size_t)k]);
@@ -2856,8 +2876,20 @@ static int batch_fe(pdmts_batch *b, bool link)
         k_feb_predict<<<b->nfeblk, 256, 0, b->fs>>>(b->d_fe, b->d_feblk);
         k_feb_residual<<<b->nfeblk, 256, 0, b->fs>>>(b->d_fe, b->d_feblk);
     }
-    for (int k = 0; k < b->itmax; ++k)
-        k_feb_cheb<<<b->nfeblk, 256, 0, b->fs>>>(b->d_fe, b->d_feblk, k, link ? 1 : 0);
+    for (int k = 0; k < b->itmax; ++k) {
+        // each iteration a programmatic dependent of the kernel before it
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)b->nfeblk);
+        cfg.blockDim = dim3(256);
+        cfg.stream = b->fs;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        PDMTS_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_feb_cheb, (const FeDev *)b->d_fe, (const int2 *)b->d_feblk, k,
+                                          link ? 1 : 0));
+    }
     k_feb_finish<<<b->nfeblk, 256, 0, b->fs>>>(b->d_fe, b->d_feblk, link ? 1 : 0);
     PDMTS_CUDA_TRY(cudaGetLastError());
     return PDMTS_OK;
