@@ -547,7 +547,12 @@ __global__ void k_negate(const int64_t n, double *__restrict__ A)
         A[i] = -A[i];
 }
 
-// y = A x for a row-major n x n matrix, one warp per row.
+// y = scale A x for a row-major n x n matrix, one warp per row. The matrix
+// is read once per call from DRAM (it does not fit in L2 beside the PD
+// state), so each lane keeps four independent 16-byte loads in flight: a
+// warp streams 2 KB at a time and the ~26 warps an SM holds cover the memory
+// latency. Even n (rows 16-byte aligned) takes the paired loads; odd n the
+// plain loop.
 __global__ void k_gemv_rows(const int64_t n, const double *__restrict__ A, const double *__restrict__ x,
                             const double scale, double *__restrict__ y)
 {
@@ -556,8 +561,33 @@ __global__ void k_gemv_rows(const int64_t n, const double *__restrict__ A, const
     if (row >= n)
         return;
     double s = 0.0;
-    for (int64_t j = lane; j < n; j += 32)
-        s += A[row * n + j] * x[j];
+    if ((n & 1) == 0) {
+        const double2 *a2 = reinterpret_cast<const double2 *>(A + row * n);
+        const double2 *x2 = reinterpret_cast<const double2 *>(x);
+        const int64_t n2 = n / 2;
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        int64_t j = lane;
+        for (; j + 96 < n2; j += 128) {
+            double2 p[4], q[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                p[u] = __ldcs(a2 + j + 32 * u);
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                q[u] = __ldg(x2 + j + 32 * u);
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                acc[u] = fma(p[u].y, q[u].y, fma(p[u].x, q[u].x, acc[u]));
+        }
+        for (; j < n2; j += 32) {
+            const double2 p = __ldcs(a2 + j), q = __ldg(x2 + j);
+            acc[0] = fma(p.y, q.y, fma(p.x, q.x, acc[0]));
+        }
+        s = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+    } else {
+        for (int64_t j = lane; j < n; j += 32)
+            s += A[row * n + j] * x[j];
+    }
     for (int o = 16; o > 0; o >>= 1)
         s += __shfl_down_sync(0xffffffffu, s, o);
     if (lane == 0)
@@ -1136,8 +1166,10 @@ static int fe_cheb_solve(pdmts_fem *fe, int nrhs, double *x, const double *b, do
     const int it = (int)fe->cheb_c1.size();
     for (int k = 0; k < it; ++k) {
         const bool last = k == it - 1;
+        const double c1 = fe->cheb_c1[(size_t)k], c2 = fe->cheb_c2[(size_t)k];
         if (fe->paired_rows) {
             // each iteration a programmatic dependent of the kernel before it
+            // (2D: the small solve no longer trails the PD chain beside it)
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3(blocks(fe->n * nrhs));
             cfg.blockDim = dim3(256);
@@ -1150,11 +1182,13 @@ static int fe_cheb_solve(pdmts_fem *fe, int nrhs, double *x, const double *b, do
             PDMTS_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_cheb_iter_node, (int64_t)fe->n, nrhs, fe->W,
                                               (const int32_t *)fe->d_col.p, (const double *)fe->d_Keff.p,
                                               (const double *)fe->d_Minv.p, x, r, (const double *)d,
-                                              last ? nullptr : dn, fe->cheb_c1[(size_t)k], fe->cheb_c2[(size_t)k]));
-        } else
+                                              last ? nullptr : dn, c1, c2));
+        } else {
+            // plain launches: the 3D solve, placed as eagerly, took SM slots
+            // from the PD chain on the step's critical path (1.41 -> 1.57 ms)
             k_cheb_iter_group<<<blocks(tot * kRowGroup), 256, 0, s>>>(
-                ndof, nrhs, fe->W, fe->d_col.p, fe->d_Keff.p, fe->d_Minv.p, x, r, d, last ? nullptr : dn,
-                fe->cheb_c1[(size_t)k], fe->cheb_c2[(size_t)k]);
+                ndof, nrhs, fe->W, fe->d_col.p, fe->d_Keff.p, fe->d_Minv.p, x, r, d, last ? nullptr : dn, c1, c2);
+        }
         ++*launches;
         std::swap(d, dn);
     }
