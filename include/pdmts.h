@@ -305,6 +305,17 @@ int arlequin_destroy(pdmts_arl *arl);
 int arlequin_read_lambda(pdmts_arl *arl, double *lambda, int64_t *n_lambda);
 /* |G_FE v_FE - G_PD v_PD| (Eq. 41) at the current time and |G_FE v_FE|. */
 int arlequin_constraint_residual(pdmts_arl *arl, double *residual, double *reference);
+/* How lambda_m = (-H)^-1 y (Eq. 49) is multiplied out each coarse step. AUTO:
+ * in the FP64 precision an FP64 product; in FP32-bulk (even n_lambda) the
+ * inverse kept as FP32 pairs (hi + lo, scaled by a power of two) and
+ * multiplied with error-free FP32 products and compensated sums: FP64-level
+ * accuracy (about 2^-40 of sum |a_j y_j|) at the FP32 rate, since GB300 runs
+ * FP64 FMAs at a small fraction of its FP32 rate. FP64: the FP64 product in
+ * every precision. Takes effect at the next coarse step; PDMTS_ERR_ARG for an
+ * unknown kind. */
+#define PDMTS_PRODUCT_AUTO 0
+#define PDMTS_PRODUCT_FP64 1
+int arlequin_set_multiplier_product(pdmts_arl *arl, int kind);
 
 typedef struct {
     int64_t n_lambda;        /* multiplier components                     */

@@ -292,12 +292,13 @@ cudaError_t launch_interface_force(int dim, int64_t n, int64_t n_ov, const int32
 // y[c * nl + k] = sign * sum_p G_PD[k, p] v_p[c] over CSR rows (row k, per
 // component) plus, if gfe_col != null, sum_I G_FE[k, I] vfe[c * nfe + I]
 // (ELL rows of width gfe_w). v is the PD velocity (FP64 v64, or the FP32
-// packed pairs v4/v2 scaled by h).
+// packed pairs v4/v2 scaled by h). yf, if not null, also receives each y as
+// an FP32 pair (hi = y rounded to FP32, lo = the rest rounded to FP32).
 cudaError_t launch_constraint(int dim, int64_t nl, const int64_t *gpd_ptr, const int32_t *gpd_col,
                               const double *gpd_val, int64_t npd, const double *v64, const float4 *v4,
                               const float2 *v2, double h, const int32_t *gfe_col, const double *gfe_val, int gfe_w,
                               int64_t nfe, const double *vfe, double sign_pd, double sign_fe, double *y,
-                              cudaStream_t s);
+                              cudaStream_t s, float2 *yf = nullptr);
 // The PD part of launch_constraint (2D, sign_pd, no FE term) for nv FP32
 // velocity fields v4 + j v4_stride at once, into y + j y_stride.
 cudaError_t launch_constraint_pd_many(int64_t nl, const int64_t *gpd_ptr, const int32_t *gpd_col,

@@ -207,6 +207,12 @@ struct pdmts_arl {
     DevArr<int64_t> d_gfeT_ptr;
     DevArr<double> d_gfe_val, d_gpd_val, d_ov_N, d_gfeT_val, d_Hfe, d_Hneg_inv, d_colbuf, d_lam0, d_lam, d_y;
     DevArr<double> d_B[4];          // block Chebyshev work (x, r, d0, d1)
+    // FP32-bulk precision, even n_lambda: (-H)^-1 scaled by 2^-e (e = exponent
+    // of its largest entry) as FP32 pairs, 2^e, and y as FP32 pairs
+    int product_kind = PDMTS_PRODUCT_AUTO;
+    DevArr<float2> d_Hinv_df, d_ydf;
+    DevArr<double> d_df_scale;
+    DevArr<unsigned long long> d_absmax;
     DevArr<int64_t> d_gpd_ptr;
     DevArr<uint8_t> d_near;         // bond words of nodes within (m + 1) delta of a band
     DevArr<unsigned long long> d_changed;
@@ -258,6 +264,7 @@ struct pdmts_arl {
         for (auto &b : d_B)
             release(b);
         release(d_gpd_ptr); release(d_near); release(d_changed);
+        release(d_Hinv_df); release(d_ydf); release(d_df_scale); release(d_absmax);
     }
 };
 
@@ -545,6 +552,105 @@ __global__ void k_negate(const int64_t n, double *__restrict__ A)
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n)
         A[i] = -A[i];
+}
+
+// ---- the multiplier product in FP32 pairs (FP32-bulk precision) ----------
+// GB300 runs FP64 fused multiply-adds at 2 per SM per cycle, so the n^2 FP64
+// FMAs of lambda = (-H)^-1 y bound the FP64 product rather than its bytes.
+// With each entry split into an FP32 pair (hi + lo, the FP64 value to about
+// 2^-48 relative) the product takes error-free FP32 products and compensated
+// sums (Dekker's and Knuth's constructions): about 12 FP32 operations per
+// entry, the same 8 bytes per entry, FP64-level accuracy (about 2^-40 of
+// sum |a_j x_j|).
+
+// largest |A_i| as the bit pattern of a non-negative double (ordered like
+// the values)
+__global__ void k_absmax_bits(const int64_t n, const double *__restrict__ A, unsigned long long *__restrict__ m)
+{
+    unsigned long long v = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        v = max(v, (unsigned long long)__double_as_longlong(fabs(A[i])));
+    for (int o = 16; o > 0; o >>= 1)
+        v = max(v, (unsigned long long)__shfl_down_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0 && v)
+        atomicMax(m, v);
+}
+
+// out_i = A_i 2^-e as an FP32 pair (the scaled value is exact in FP64, so hi
+// and lo are its nearest FP32 value and the nearest FP32 value of the rest);
+// e is the exponent of the largest |A_i|, and inv_scale = 2^e
+__global__ void k_df_split(const int64_t n, const double *__restrict__ A, const unsigned long long *__restrict__ m,
+                           float2 *__restrict__ out, double *__restrict__ inv_scale)
+{
+    const double mx = __longlong_as_double((long long)*m);
+    const int e = mx > 0.0 ? ilogb(mx) : 0;
+    const double sc = ldexp(1.0, -e);
+    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i0 == 0)
+        *inv_scale = ldexp(1.0, e);
+    for (int64_t i = i0; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = A[i] * sc;
+        const float hi = __double2float_rn(v);
+        out[i] = make_float2(hi, __double2float_rn(v - (double)hi));
+    }
+}
+
+// (sh, sl) += (ah + al)(xh + xl): the product ah xh exactly as p + e (one
+// FMA), the cross terms rounded once (al xl is below 2^-48 of the product),
+// p added to sh by two-sum, the error terms gathered in sl
+__device__ __forceinline__ void df_mac(float &sh, float &sl, const float ah, const float al, const float xh,
+                                       const float xl)
+{
+    const float p = __fmul_rn(ah, xh);
+    const float e = __fmaf_rn(ah, xh, -p);
+    const float c = __fmaf_rn(ah, xl, __fmaf_rn(al, xh, e));
+    const float t = __fadd_rn(sh, p);
+    const float bp = __fsub_rn(t, sh);
+    const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+    sh = t;
+    sl = __fadd_rn(sl, __fadd_rn(err, c));
+}
+
+// y = inv_scale (A x) for a row-major n x n matrix of FP32 pairs (n even:
+// rows start 16-byte aligned and two entries load as one float4), one warp per
+// row, four 16-byte loads of A in flight per lane, two independent pair
+// accumulators per lane, the lanes' sums added in FP64.
+__global__ void k_gemv_df(const int64_t n, const float2 *__restrict__ A, const float2 *__restrict__ x,
+                          const double *__restrict__ inv_scale, double *__restrict__ y)
+{
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= n)
+        return;
+    const float4 *a4 = reinterpret_cast<const float4 *>(A + row * n);
+    const float4 *x4 = reinterpret_cast<const float4 *>(x);
+    const int64_t n2 = n / 2;
+    float sh[2] = {0.f, 0.f}, sl[2] = {0.f, 0.f};
+    int64_t j = lane;
+    for (; j + 96 < n2; j += 128) {
+        float4 a[4], v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            a[u] = __ldcs(a4 + j + 32 * u);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            v[u] = __ldg(x4 + j + 32 * u);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            df_mac(sh[u & 1], sl[u & 1], a[u].x, a[u].y, v[u].x, v[u].y);
+            df_mac(sh[u & 1], sl[u & 1], a[u].z, a[u].w, v[u].z, v[u].w);
+        }
+    }
+    for (; j < n2; j += 32) {
+        const float4 a = __ldcs(a4 + j), v = __ldg(x4 + j);
+        df_mac(sh[0], sl[0], a.x, a.y, v.x, v.y);
+        df_mac(sh[0], sl[0], a.z, a.w, v.z, v.w);
+    }
+    double s = ((double)sh[0] + (double)sl[0]) + ((double)sh[1] + (double)sl[1]);
+    for (int o = 16; o > 0; o >>= 1)
+        s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0)
+        y[row] = s * *inv_scale;
 }
 
 // y = scale A x for a row-major n x n matrix, one warp per row. The matrix
@@ -2178,6 +2284,20 @@ static int build_H(pdmts_arl *A, int m)
     k_negate<<<blocks(n2), 256, 0, s>>>(n2, H);
     ++launches;
     PDMTS_TRY(invert_spd(A, H, nlam, s, &launches));
+    if (!f64 && nlam % 2 == 0) {
+        // the FP32-pair copy the FP32-bulk steps multiply with
+        if (A->d_Hinv_df.count != n2) {
+            PDMTS_TRY(A->alloc(A->d_Hinv_df, n2));
+            PDMTS_TRY(A->alloc(A->d_ydf, nlam));
+            PDMTS_TRY(A->alloc(A->d_df_scale, 1));
+            PDMTS_TRY(A->alloc(A->d_absmax, 1));
+        }
+        PDMTS_CUDA_TRY(cudaMemsetAsync(A->d_absmax.p, 0, sizeof(unsigned long long), s));
+        const unsigned g = (unsigned)std::min<int64_t>(blocks(n2), 4096);
+        k_absmax_bits<<<g, 256, 0, s>>>(n2, H, A->d_absmax.p);
+        k_df_split<<<g, 256, 0, s>>>(n2, H, A->d_absmax.p, A->d_Hinv_df.p, A->d_df_scale.p);
+        launches += 2;
+    }
     PDMTS_CUDA_TRY(cudaGetLastError());
     PDMTS_CUDA_TRY(cudaStreamSynchronize(s));
     ctx->stats.kernel_launches += launches;
@@ -2401,13 +2521,20 @@ static int step_lambda(pdmts_arl *A, cudaStream_t s, int64_t *launches, bool fe_
         PDMTS_CUDA_TRY(cudaStreamWaitEvent(s, A->ev_join, 0));
     const float4 *v4 = f64 ? nullptr : pd->f_v4.p;
     const float2 *v2 = f64 ? nullptr : pd->f_v2.p;
+    // FP32-bulk: the product in FP32 pairs (FP64-level accuracy at the FP32
+    // rate); FP64: the FP64 product
+    const bool df = !f64 && A->product_kind == PDMTS_PRODUCT_AUTO && A->d_Hinv_df.p &&
+                    A->d_Hinv_df.count == A->nlam * A->nlam;
     cudaError_t e = launch_constraint(pd->dim, A->nl, A->d_gpd_ptr.p, A->d_gpd_col.p, A->d_gpd_val.p, pd->n,
                                       f64 ? pd->d_v.p : nullptr, v4, v2, pd->h, A->d_gfe_col.p, A->d_gfe_val.p,
-                                      A->gfe_w, fe->n, fe->d_v.p, -1.0, 1.0, A->d_y.p, s);
+                                      A->gfe_w, fe->n, fe->d_v.p, -1.0, 1.0, A->d_y.p, s, df ? A->d_ydf.p : nullptr);
     if (e != cudaSuccess)
         return fail(PDMTS_ERR_CUDA, "interface residual: %s", cudaGetErrorString(e));
-    // the multiplier solve stays FP64 in every precision
-    k_gemv_rows<<<blocks(A->nlam * 32), 256, 0, s>>>(A->nlam, A->d_Hneg_inv.p, A->d_y.p, 1.0, A->d_lam.p);
+    if (df)
+        k_gemv_df<<<blocks(A->nlam * 32), 256, 0, s>>>(A->nlam, A->d_Hinv_df.p, A->d_ydf.p, A->d_df_scale.p,
+                                                        A->d_lam.p);
+    else
+        k_gemv_rows<<<blocks(A->nlam * 32), 256, 0, s>>>(A->nlam, A->d_Hneg_inv.p, A->d_y.p, 1.0, A->d_lam.p);
     *launches += 2;
     return PDMTS_OK;
 }
@@ -3342,6 +3469,17 @@ extern "C" int arlequin_read_lambda(pdmts_arl *A, double *lam, int64_t *n_lambda
     if (n_lambda)
         *n_lambda = A->nlam;
     return A->ctx->end();
+}
+
+extern "C" int arlequin_set_multiplier_product(pdmts_arl *A, int kind)
+{
+    clear_error();
+    if (!A)
+        return fail(PDMTS_ERR_ARG, "arlequin_set_multiplier_product: arl is NULL");
+    if (kind != PDMTS_PRODUCT_AUTO && kind != PDMTS_PRODUCT_FP64)
+        return fail(PDMTS_ERR_ARG, "arlequin_set_multiplier_product: unknown kind %d", kind);
+    A->product_kind = kind;
+    return PDMTS_OK;
 }
 
 extern "C" int arlequin_constraint_residual(pdmts_arl *A, double *residual, double *reference)

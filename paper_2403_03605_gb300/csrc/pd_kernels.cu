@@ -428,7 +428,8 @@ __global__ void k_constraint(const int dim, const int64_t nl, const int64_t *__r
                              const float2 *__restrict__ v2, const double h, const int32_t *__restrict__ gfe_col,
                              const double *__restrict__ gfe_val, const int gfe_w, const int64_t nfe,
                              const double *__restrict__ vfe, const double sign_pd, const double sign_fe,
-                             double *__restrict__ y, const int64_t v4_stride, const int64_t y_stride)
+                             double *__restrict__ y, const int64_t v4_stride, const int64_t y_stride,
+                             float2 *__restrict__ yf)
 {
     // one warp per multiplier node k, all components (rows c nl + k): the PD
     // velocities of the node's support are gathered once for every component;
@@ -472,8 +473,13 @@ __global__ void k_constraint(const int dim, const int64_t nl, const int64_t *__r
         double t = sign_pd * sp[c] + sign_fe * sf;
         for (int o = 16; o > 0; o >>= 1)
             t += __shfl_down_sync(0xffffffffu, t, o);
-        if (lane == 0)
+        if (lane == 0) {
             y[(int64_t)c * nl + k] = t;
+            if (yf) {
+                const float hi = __double2float_rn(t);
+                yf[(int64_t)c * nl + k] = make_float2(hi, __double2float_rn(t - (double)hi));
+            }
+        }
     }
 }
 
@@ -642,7 +648,7 @@ cudaError_t launch_constraint(int dim, int64_t nl, const int64_t *gpd_ptr, const
                               const double *gpd_val, int64_t npd, const double *v64, const float4 *v4,
                               const float2 *v2, double h, const int32_t *gfe_col, const double *gfe_val, int gfe_w,
                               int64_t nfe, const double *vfe, double sign_pd, double sign_fe, double *y,
-                              cudaStream_t s)
+                              cudaStream_t s, float2 *yf)
 {
     const int64_t rows = (int64_t)dim * nl;
     if (rows == 0)
@@ -651,7 +657,7 @@ cudaError_t launch_constraint(int dim, int64_t nl, const int64_t *gpd_ptr, const
         return cudaErrorInvalidValue;
     k_constraint<<<(unsigned)((nl * 32 + 255) / 256), 256, 0, s>>>(dim, nl, gpd_ptr, gpd_col, gpd_val, npd, v64, v4,
                                                                       v2, h, gfe_col, gfe_val, gfe_w, nfe, vfe,
-                                                                      sign_pd, sign_fe, y, 0, 0);
+                                                                      sign_pd, sign_fe, y, 0, 0, yf);
     return cudaGetLastError();
 }
 
@@ -665,7 +671,7 @@ cudaError_t launch_constraint_pd_many(int64_t nl, const int64_t *gpd_ptr, const 
         return cudaErrorInvalidValue;
     const dim3 grid((unsigned)((nl * 32 + 255) / 256), (unsigned)nv);
     k_constraint<<<grid, 256, 0, s>>>(2, nl, gpd_ptr, gpd_col, gpd_val, npd, nullptr, v4, nullptr, h, nullptr, nullptr,
-                                      0, 0, nullptr, sign_pd, 0.0, y, v4_stride, y_stride);
+                                      0, 0, nullptr, sign_pd, 0.0, y, v4_stride, y_stride, nullptr);
     return cudaGetLastError();
 }
 

@@ -26,6 +26,7 @@ PDMTS_MICRO_POWER, PDMTS_MICRO_EXP = 0, 1
 PDMTS_FORCE_LINEAR, PDMTS_FORCE_PMB = 0, 1
 PDMTS_WEIGHT_CONSTANT, PDMTS_WEIGHT_LINEAR, PDMTS_WEIGHT_CUBIC = 0, 1, 2
 PDMTS_LATTICE_TILES, PDMTS_LATTICE_TILE_AUTO = 10, -1
+PDMTS_PRODUCT_AUTO, PDMTS_PRODUCT_FP64 = 0, 1
 
 
 class PdmtsError(RuntimeError):
@@ -93,6 +94,7 @@ SIGNATURES = [
     ("arlequin_read_lambda", _I, [_V, _V, C.POINTER(_I64)]),
     ("arlequin_constraint_residual", _I, [_V, C.POINTER(_D), C.POINTER(_D)]),
     ("arlequin_info", _I, [_V, _V]),
+    ("arlequin_set_multiplier_product", _I, [_V, _I]),
     ("mts_batch_create", _I, [_I, C.POINTER(_V), C.POINTER(_V)]),
     ("mts_batch_advance", _I, [_V, _I64]),
     ("mts_batch_info", _I, [_V, _V]),
@@ -459,6 +461,11 @@ def mts_batch_info(batch):
 
 def mts_batch_destroy(batch):
     _check(load().mts_batch_destroy(batch), "mts_batch_destroy")
+
+
+def arlequin_set_multiplier_product(arl, kind):
+    """AUTO: FP32-pair product of lambda_m = (-H)^-1 y in FP32-bulk, FP64 in FP64; FP64: always FP64."""
+    _check(load().arlequin_set_multiplier_product(arl, int(kind)), "arlequin_set_multiplier_product")
 
 
 def arlequin_read_lambda(arl):

@@ -73,6 +73,29 @@ def test_mts_fp32_bulk_within_tolerance(fresh):
     assert g.residual() <= 1e-5
 
 
+def test_fp32_pair_multiplier_product_matches_fp64_product(fresh):
+    """FP32-bulk multiplies lambda_m = (-H)^-1 y out with the inverse kept as
+    FP32 pairs (error-free FP32 products, compensated sums). On the first
+    coarse step everything before the product is the same in a run that takes
+    the FP64 product instead, so the two lambda_m differ only by the
+    product's rounding: within 1e-10 of the largest |lambda| (an FP32-only
+    product, without the low parts, would miss by about 1e-7)."""
+    cp = W.small_coupled(m=4, n_coarse=4)
+    a = GpuMTS(fresh(), cp, P.PDMTS_FP32_BULK)
+    b = GpuMTS(fresh(), cp, P.PDMTS_FP32_BULK)
+    P.arlequin_set_multiplier_product(b.arl, P.PDMTS_PRODUCT_FP64)
+    assert P.arlequin_info(a.arl)["n_lambda"] % 2 == 0
+    a.run(1)
+    b.run(1)
+    la, lb = a.lam(), b.lam()
+    scale = np.abs(lb).max()
+    print(f"pair product vs FP64 product: max diff {np.abs(la - lb).max() / scale:.2e} of max |lambda|")
+    assert scale > 0
+    assert np.abs(la - lb).max() <= 1e-10 * scale
+    with pytest.raises(P.PdmtsError):
+        P.arlequin_set_multiplier_product(a.arl, 7)
+
+
 def test_mts_uniform_velocity_patch(fresh):
     cp = W.small_coupled(m=5, n_coarse=4, crack=False, traction=0.0)
     v0 = np.array([3.0, -1.5])
