@@ -47,3 +47,36 @@ def test_reference_arm_names_the_arm_workload():
     assert bench.reference_problem("batch")[0] == bench.BATCH_NAME.format(n=64)
     # the coupled plate's PD lattice is the 800,000-node strip the arm advances
     assert bench.reference_problem("coupled")[1].n == 2000 * 400
+
+
+def test_issue_and_l2_lines():
+    """The issue-rate line puts ncu's warp instructions per launch over the
+    live launch time against 152 SMs x 4 schedulers x the sampled clock; the
+    L2 line puts the SMs' L2 bytes per launch against the stored nominal rate.
+    Without stored counts both lines carry the peak and no fraction."""
+    ent = {"warp_instructions_per_launch": 12_000_000, "l2_bytes_per_launch": 120_000_000}
+    issue, l2 = bench.issue_and_l2(ent, 0.02, {"sm_mhz": 2000.0}, 152, 36000.0)
+    assert issue["peak"] == 152 * 4 * 2000e6
+    assert issue["achieved"] == pytest.approx(12e6 / 20e-6)
+    assert issue["frac"] == pytest.approx(6e11 / 1.216e12)
+    assert l2["achieved"] == pytest.approx(120e6 / 20e-6 / 1e9)
+    assert l2["frac"] == pytest.approx(6000.0 / 36000.0)
+    issue, l2 = bench.issue_and_l2({}, 0.02, {"sm_mhz": None}, 152, None)
+    assert issue["peak"] == 152 * 4 * 2070e6 and issue["frac"] is None and l2["frac"] is None
+
+
+def test_stored_counters_follow_the_kernel_source():
+    """profiles/traffic.json's figures are reported only under the hash of the
+    kernel source they were measured on (2D and 3D hashed separately)."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(bench.__file__), "profiles", "traffic.json")) as f:
+        tj = json.load(f)
+    for wl, tiles in tj.items():
+        if not isinstance(tiles, dict):
+            continue
+        for tile, ent in tiles.items():
+            got, peak = bench.stored_counters(wl, tile)
+            assert peak == tj["l2_peak_gbs"]
+            assert (got == ent) == (ent["kernel_version"] == bench.kernel_version(wl))
+    assert bench.kernel_version("coupled") == bench.kernel_version("pd") != bench.kernel_version("coupled3d")
