@@ -4,7 +4,7 @@ FP64 build: identical arithmetic in the oracle's order, so displacements,
 velocities, accelerations, damage and the broken-bond set must agree exactly;
 the stated bar is rel-L2 <= 1e-10 and an identical broken set.
 FP32-bulk build: rel-L2 of u <= 1e-4 and broken-bond mismatch <= 0.1 % against
-the FP64 result (the benchmark spec's tolerances), written into each test.
+the FP64 result (the stated tolerances of the FP32-bulk path), written into each test.
 """
 import numpy as np
 import pytest
