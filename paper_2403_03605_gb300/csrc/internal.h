@@ -323,10 +323,12 @@ struct PDAddLink {
     const float *waf;
 };
 cudaError_t launch_pd_add_link(const PDAddLink &A, cudaStream_t s);
-// Count bond words of `flag`ged nodes that differ between two mask arrays
-// (lattice layout: words indexed by node; sliced ELL: per tile).
-cudaError_t launch_count_changed(int64_t nwords, const uint32_t *a, const uint32_t *b, const uint8_t *word_flag,
-                                 unsigned long long *count, cudaStream_t s);
+// End of a coarse step in one launch: count[0] += the changed bits of the
+// `flag`ged words of a against b (lattice layout: words indexed by node;
+// sliced ELL: per tile), b = a, lam0 = lam (nlam doubles), next_count[0] = 0.
+cudaError_t launch_finish_words(int64_t nwords, const uint32_t *a, uint32_t *b, const uint8_t *word_flag,
+                                unsigned long long *count, unsigned long long *next_count, int64_t nlam,
+                                const double *lam, double *lam0, cudaStream_t s);
 
 }  // namespace pdmts
 

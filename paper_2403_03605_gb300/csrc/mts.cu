@@ -215,7 +215,8 @@ struct pdmts_arl {
     DevArr<unsigned long long> d_absmax;
     DevArr<int64_t> d_gpd_ptr;
     DevArr<uint8_t> d_near;         // bond words of nodes within (m + 1) delta of a band
-    DevArr<unsigned long long> d_changed;
+    DevArr<unsigned long long> d_changed;     // two counters, used in turn by successive steps
+    int changed_slot = 0;                     // the counter the next step adds to
     unsigned long long *h_changed = nullptr;  // pinned
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_flag = nullptr;
     cudaStream_t fe_stream = nullptr;
@@ -1711,7 +1712,9 @@ static int build_constraint(pdmts_arl *A)
         PDMTS_CUDA_TRY(cudaMemsetAsync(a->p, 0, sizeof(double) * A->nlam, s));
     }
     PDMTS_TRY(A->alloc(A->d_Hneg_inv, A->nlam * A->nlam));
-    PDMTS_TRY(A->alloc(A->d_changed, 1));
+    PDMTS_TRY(A->alloc(A->d_changed, 2));
+    PDMTS_CUDA_TRY(cudaMemsetAsync(A->d_changed.p, 0, 2 * sizeof(unsigned long long), s));
+    A->changed_slot = 0;
     // bond words of PD nodes within (m + 1) delta of a band (rebuild rule)
     PDMTS_CUDA_TRY(cudaStreamSynchronize(s));
     return PDMTS_OK;
@@ -2608,16 +2611,18 @@ static int step_finish(pdmts_arl *A, cudaStream_t s, int64_t *launches, bool fe_
     if (e != cudaSuccess)
         return fail(PDMTS_ERR_CUDA, "PD correction: %s", cudaGetErrorString(e));
     // ---- rebuild flag: bonds near a band broken this step; new start mask ----
-    PDMTS_CUDA_TRY(cudaMemsetAsync(A->d_changed.p, 0, sizeof(unsigned long long), s));
-    e = launch_count_changed(pd->n_mask_words, pd->d_mask.p, pd->d_mask_link.p, A->d_near.p, A->d_changed.p, s);
+    // one launch: count the changed bits near a band into this step's
+    // counter, copy the bond words into the next step's start words and
+    // lambda_m into lambda_0, zero the other counter for the next step
+    unsigned long long *cnt = A->d_changed.p + A->changed_slot;
+    e = launch_finish_words(pd->n_mask_words, pd->d_mask.p, pd->d_mask_link.p, A->d_near.p, cnt,
+                            A->d_changed.p + (1 - A->changed_slot), A->nlam, A->d_lam.p, A->d_lam0.p, s);
     if (e != cudaSuccess)
         return fail(PDMTS_ERR_CUDA, "rebuild flag: %s", cudaGetErrorString(e));
-    PDMTS_CUDA_TRY(cudaMemcpyAsync(A->h_changed, A->d_changed.p, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    A->changed_slot = 1 - A->changed_slot;
+    PDMTS_CUDA_TRY(cudaMemcpyAsync(A->h_changed, cnt, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
     PDMTS_CUDA_TRY(cudaEventRecord(A->ev_flag, s));
     A->flag_pending = true;
-    PDMTS_CUDA_TRY(cudaMemcpyAsync(pd->d_mask_link.p, pd->d_mask.p, sizeof(uint32_t) * pd->n_mask_words,
-                                   cudaMemcpyDeviceToDevice, s));
-    PDMTS_CUDA_TRY(cudaMemcpyAsync(A->d_lam0.p, A->d_lam.p, sizeof(double) * A->nlam, cudaMemcpyDeviceToDevice, s));
     // the step ends when the FE correction has also finished
     if (fe_join)
         PDMTS_CUDA_TRY(cudaStreamWaitEvent(s, A->ev_join, 0));

@@ -548,13 +548,28 @@ __global__ void k_pd_add_link(const PDAddLink A)
     }
 }
 
-__global__ void k_count_changed(const int64_t nwords, const uint32_t *__restrict__ a, const uint32_t *__restrict__ b,
-                                const uint8_t *__restrict__ flag, unsigned long long *count)
+// End of a coarse step in one pass: count the bits that changed in flagged
+// words (a vs the step-start words b) into count[0], copy a into b (the next
+// step's start words), copy lam into lam0, and zero count[1] (the counter
+// the next step adds to; the two swap every step).
+__global__ void k_finish_words(const int64_t nwords, const uint32_t *__restrict__ a, uint32_t *__restrict__ b,
+                               const uint8_t *__restrict__ flag, unsigned long long *count,
+                               unsigned long long *next_count, const int64_t nlam, const double *__restrict__ lam,
+                               double *__restrict__ lam0)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     unsigned c = 0;
-    if (i < nwords && flag[i] && a[i] != b[i])
-        c = __popc(a[i] ^ b[i]);
+    if (i < nwords) {
+        const uint32_t ai = a[i], bi = b[i];
+        if (flag[i] && ai != bi)
+            c = __popc(ai ^ bi);
+        if (ai != bi)
+            b[i] = ai;
+    }
+    if (i < nlam)
+        lam0[i] = lam[i];
+    if (i == 0)
+        *next_count = 0ull;
     c = __reduce_add_sync(0xffffffffu, c);
     if ((threadIdx.x & 31) == 0 && c)
         atomicAdd(count, (unsigned long long)c);
@@ -684,12 +699,13 @@ cudaError_t launch_pd_add_link(const PDAddLink &A, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_count_changed(int64_t nwords, const uint32_t *a, const uint32_t *b, const uint8_t *word_flag,
-                                 unsigned long long *count, cudaStream_t s)
+cudaError_t launch_finish_words(int64_t nwords, const uint32_t *a, uint32_t *b, const uint8_t *word_flag,
+                                unsigned long long *count, unsigned long long *next_count, int64_t nlam,
+                                const double *lam, double *lam0, cudaStream_t s)
 {
-    if (nwords == 0)
-        return cudaSuccess;
-    k_count_changed<<<(unsigned)((nwords + 255) / 256), 256, 0, s>>>(nwords, a, b, word_flag, count);
+    const int64_t n = std::max<int64_t>(std::max<int64_t>(nwords, nlam), 1);
+    k_finish_words<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(nwords, a, b, word_flag, count, next_count, nlam, lam,
+                                                                lam0);
     return cudaGetLastError();
 }
 
