@@ -285,10 +285,12 @@ cudaError_t launch_weighted_load(int dim, int64_t n, const double *b, const doub
 // Interface force density of the PD overlap nodes, g_p = sum_a N_a(x_p)
 // lambda[k_a] per component (= (G_PD^T lambda)_p / V_p); nodes outside the
 // overlap are not written. g64 (FP64, dim * n) or g32 (FP32 lattice units,
-// scaled by inv_h); lam is dim * nl (component-major).
+// scaled by inv_h); lam is dim * nl (component-major). g64b / g32b, if not
+// null, receive the same values (a second force field from the same lam).
 cudaError_t launch_interface_force(int dim, int64_t n, int64_t n_ov, const int32_t *ov_node, const int32_t *ov_k,
                                    const double *ov_N, int corners, const double *lam, int64_t nl, double inv_h,
-                                   double *g64, float *g32, cudaStream_t s);
+                                   double *g64, float *g32, cudaStream_t s, double *g64b = nullptr,
+                                   float *g32b = nullptr);
 // y[c * nl + k] = sign * sum_p G_PD[k, p] v_p[c] over CSR rows (row k, per
 // component) plus, if gfe_col != null, sum_I G_FE[k, I] vfe[c * nfe + I]
 // (ELL rows of width gfe_w). v is the PD velocity (FP64 v64, or the FP32

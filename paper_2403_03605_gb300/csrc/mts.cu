@@ -217,6 +217,9 @@ struct pdmts_arl {
     DevArr<uint8_t> d_near;         // bond words of nodes within (m + 1) delta of a band
     DevArr<unsigned long long> d_changed;     // two counters, used in turn by successive steps
     int changed_slot = 0;                     // the counter the next step adds to
+    // the PD free-chain interface force already holds G_PD^T lambda_0 (written
+    // beside the link force of the lambda_m that becomes lambda_0)
+    bool g0_ready = false;
     unsigned long long *h_changed = nullptr;  // pinned
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_flag = nullptr;
     cudaStream_t fe_stream = nullptr;
@@ -2489,6 +2492,8 @@ static int step_free_begin(pdmts_arl *A, cudaStream_t s, int64_t *launches)
     const bool f64 = pd->precision == PDMTS_FP64;
     // the FE free step may start once the previous step has ended
     PDMTS_CUDA_TRY(cudaEventRecord(A->ev_fork, s));
+    if (A->g0_ready)  // written by the previous step's link force (same lambda)
+        return PDMTS_OK;
     cudaError_t e = launch_interface_force(pd->dim, pd->n, A->n_ov, A->d_ov_node.p, A->d_ov_k.p, A->d_ov_N.p, A->corners,
                                            A->d_lam0.p, A->nl, f64 ? 0.0 : 1.0 / pd->h, f64 ? pd->d_g.p : nullptr,
                                            f64 ? nullptr : pd->f_g.p, s);
@@ -2561,11 +2566,18 @@ static int step_link_begin(pdmts_arl *A, const double *dev_lam, cudaStream_t s, 
 {
     pdmts_pd *pd = A->pd;
     const bool f64 = pd->precision == PDMTS_FP64;
+    // lambda_m becomes the next step's lambda_0 (step_finish): its force is
+    // also the next free chain's, written now into the free-chain field (the
+    // free chain of this step has finished)
+    const bool next_g0 = dev_lam == A->d_lam.p;
     cudaError_t e = launch_interface_force(pd->dim, pd->n, A->n_ov, A->d_ov_node.p, A->d_ov_k.p, A->d_ov_N.p, A->corners,
                                            dev_lam, A->nl, f64 ? 0.0 : 1.0 / pd->h, f64 ? pd->lk_g.p : nullptr,
-                                           f64 ? nullptr : pd->lk_gf.p, s);
+                                           f64 ? nullptr : pd->lk_gf.p, s,
+                                           next_g0 && f64 ? pd->d_g.p : nullptr,
+                                           next_g0 && !f64 ? pd->f_g.p : nullptr);
     if (e != cudaSuccess)
         return fail(PDMTS_ERR_CUDA, "interface force: %s", cudaGetErrorString(e));
+    A->g0_ready = next_g0;
     ++*launches;
     PDMTS_TRY(pd->zero_link_state(s));
     return PDMTS_OK;
@@ -3698,6 +3710,7 @@ extern "C" int mts_state_load(pdmts_ctx *ctx, const void *image, int64_t bytes)
     pd_invalidate_graphs(pd);
     if (ctx->arl) {
         ctx->arl->H_valid = false;  // rebuilt from the loaded bond words at the next step
+        ctx->arl->g0_ready = false; // lambda_0 comes from the image
         ctx->arl->flag_pending = false;
     }
     // the loaded image replaces a state a give-up left undefined

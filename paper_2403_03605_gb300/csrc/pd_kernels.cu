@@ -405,7 +405,8 @@ __global__ void k_weighted_load(const int dim, const int64_t n, const double *__
 __global__ void k_interface_force(const int dim, const int64_t n, const int64_t n_ov, const int32_t *__restrict__ ov_node,
                                   const int32_t *__restrict__ ov_k, const double *__restrict__ ov_N, const int corners,
                                   const double *__restrict__ lam, const int64_t nl, const double inv_h,
-                                  double *__restrict__ g64, float *__restrict__ g32)
+                                  double *__restrict__ g64, float *__restrict__ g32, double *__restrict__ g64b,
+                                  float *__restrict__ g32b)
 {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= n_ov)
@@ -419,6 +420,10 @@ __global__ void k_interface_force(const int dim, const int64_t n, const int64_t 
             g64[d * n + p] = g;
         if (g32)
             g32[d * n + p] = (float)(g * inv_h);
+        if (g64b)
+            g64b[d * n + p] = g;
+        if (g32b)
+            g32b[d * n + p] = (float)(g * inv_h);
     }
 }
 
@@ -650,12 +655,12 @@ cudaError_t launch_weighted_load(int dim, int64_t n, const double *b, const doub
 
 cudaError_t launch_interface_force(int dim, int64_t n, int64_t n_ov, const int32_t *ov_node, const int32_t *ov_k,
                                    const double *ov_N, int corners, const double *lam, int64_t nl, double inv_h,
-                                   double *g64, float *g32, cudaStream_t s)
+                                   double *g64, float *g32, cudaStream_t s, double *g64b, float *g32b)
 {
     if (n_ov == 0)
         return cudaSuccess;
     k_interface_force<<<(unsigned)((n_ov + 255) / 256), 256, 0, s>>>(dim, n, n_ov, ov_node, ov_k, ov_N, corners, lam,
-                                                                      nl, inv_h, g64, g32);
+                                                                      nl, inv_h, g64, g32, g64b, g32b);
     return cudaGetLastError();
 }
 
