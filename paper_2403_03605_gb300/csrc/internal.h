@@ -324,13 +324,13 @@ struct PDAddLink {
     const float2 *wu2, *wv2;
     const float *waf;
 };
-cudaError_t launch_pd_add_link(const PDAddLink &A, cudaStream_t s);
-// End of a coarse step in one launch: count[0] += the changed bits of the
-// `flag`ged words of a against b (lattice layout: words indexed by node;
-// sliced ELL: per tile), b = a, lam0 = lam (nlam doubles), next_count[0] = 0.
-cudaError_t launch_finish_words(int64_t nwords, const uint32_t *a, uint32_t *b, const uint8_t *word_flag,
-                                unsigned long long *count, unsigned long long *next_count, int64_t nlam,
-                                const double *lam, double *lam0, cudaStream_t s);
+// End of a coarse step in one launch: U_PD += W on L's link segments,
+// count[0] += the changed bits of the `flag`ged words of a against b
+// (lattice layout: words indexed by node; sliced ELL: per tile), b = a,
+// lam0 = lam (nlam doubles).
+cudaError_t launch_finish_step(const PDAddLink &L, int64_t nwords, const uint32_t *a, uint32_t *b,
+                               const uint8_t *word_flag, unsigned long long *count, int64_t nlam,
+                               const double *lam, double *lam0, cudaStream_t s);
 
 }  // namespace pdmts
 

@@ -215,8 +215,7 @@ struct pdmts_arl {
     DevArr<unsigned long long> d_absmax;
     DevArr<int64_t> d_gpd_ptr;
     DevArr<uint8_t> d_near;         // bond words of nodes within (m + 1) delta of a band
-    DevArr<unsigned long long> d_changed;     // two counters, used in turn by successive steps
-    int changed_slot = 0;                     // the counter the next step adds to
+    DevArr<unsigned long long> d_changed;
     // the PD free-chain interface force already holds G_PD^T lambda_0 (written
     // beside the link force of the lambda_m that becomes lambda_0)
     bool g0_ready = false;
@@ -1715,9 +1714,7 @@ static int build_constraint(pdmts_arl *A)
         PDMTS_CUDA_TRY(cudaMemsetAsync(a->p, 0, sizeof(double) * A->nlam, s));
     }
     PDMTS_TRY(A->alloc(A->d_Hneg_inv, A->nlam * A->nlam));
-    PDMTS_TRY(A->alloc(A->d_changed, 2));
-    PDMTS_CUDA_TRY(cudaMemsetAsync(A->d_changed.p, 0, 2 * sizeof(unsigned long long), s));
-    A->changed_slot = 0;
+    PDMTS_TRY(A->alloc(A->d_changed, 1));
     // bond words of PD nodes within (m + 1) delta of a band (rebuild rule)
     PDMTS_CUDA_TRY(cudaStreamSynchronize(s));
     return PDMTS_OK;
@@ -2486,13 +2483,16 @@ static int step_prepare(pdmts_arl *A, cudaStream_t s)
     return PDMTS_OK;
 }
 
-static int step_free_begin(pdmts_arl *A, cudaStream_t s, int64_t *launches)
+// may_skip: the free-chain force may be taken from the previous step's
+// link-force launch (not in a captured round, whose replays must each
+// compute it)
+static int step_free_begin(pdmts_arl *A, cudaStream_t s, int64_t *launches, bool may_skip = false)
 {
     pdmts_pd *pd = A->pd;
     const bool f64 = pd->precision == PDMTS_FP64;
     // the FE free step may start once the previous step has ended
     PDMTS_CUDA_TRY(cudaEventRecord(A->ev_fork, s));
-    if (A->g0_ready)  // written by the previous step's link force (same lambda)
+    if (may_skip && A->g0_ready)  // written by the previous step's link force (same lambda)
         return PDMTS_OK;
     cudaError_t e = launch_interface_force(pd->dim, pd->n, A->n_ov, A->d_ov_node.p, A->d_ov_k.p, A->d_ov_N.p, A->corners,
                                            A->d_lam0.p, A->nl, f64 ? 0.0 : 1.0 / pd->h, f64 ? pd->d_g.p : nullptr,
@@ -2619,26 +2619,23 @@ static int step_finish(pdmts_arl *A, cudaStream_t s, int64_t *launches, bool fe_
         L.wv2 = pd->lk_v2.p;
         L.waf = pd->lk_af.p;
     }
-    cudaError_t e = launch_pd_add_link(L, s);
+    // one launch: U_PD += W; the rebuild flag (bonds near a band broken this
+    // step) counted; the bond words copied into the next step's start words
+    // and lambda_m into lambda_0 (the counter is cleared within the step, so
+    // a captured round replays correctly)
+    unsigned long long *cnt = A->d_changed.p;
+    PDMTS_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s));
+    cudaError_t e = launch_finish_step(L, pd->n_mask_words, pd->d_mask.p, pd->d_mask_link.p, A->d_near.p, cnt,
+                                       A->nlam, A->d_lam.p, A->d_lam0.p, s);
     if (e != cudaSuccess)
-        return fail(PDMTS_ERR_CUDA, "PD correction: %s", cudaGetErrorString(e));
-    // ---- rebuild flag: bonds near a band broken this step; new start mask ----
-    // one launch: count the changed bits near a band into this step's
-    // counter, copy the bond words into the next step's start words and
-    // lambda_m into lambda_0, zero the other counter for the next step
-    unsigned long long *cnt = A->d_changed.p + A->changed_slot;
-    e = launch_finish_words(pd->n_mask_words, pd->d_mask.p, pd->d_mask_link.p, A->d_near.p, cnt,
-                            A->d_changed.p + (1 - A->changed_slot), A->nlam, A->d_lam.p, A->d_lam0.p, s);
-    if (e != cudaSuccess)
-        return fail(PDMTS_ERR_CUDA, "rebuild flag: %s", cudaGetErrorString(e));
-    A->changed_slot = 1 - A->changed_slot;
+        return fail(PDMTS_ERR_CUDA, "PD correction and rebuild flag: %s", cudaGetErrorString(e));
     PDMTS_CUDA_TRY(cudaMemcpyAsync(A->h_changed, cnt, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
     PDMTS_CUDA_TRY(cudaEventRecord(A->ev_flag, s));
     A->flag_pending = true;
     // the step ends when the FE correction has also finished
     if (fe_join)
         PDMTS_CUDA_TRY(cudaStreamWaitEvent(s, A->ev_join, 0));
-    *launches += 2;
+    *launches += 1;
     ctx->stats.coarse_steps += 1;
     return PDMTS_OK;
 }
@@ -2655,7 +2652,7 @@ static int coarse_step(pdmts_arl *A)
     std::array<cudaEvent_t, 5> ph{};
     PDMTS_TRY(ctx->mark(&ph[0]));
     // the PD chain is enqueued before the FE step so that it starts without waiting for the host
-    PDMTS_TRY(step_free_begin(A, s, &launches));
+    PDMTS_TRY(step_free_begin(A, s, &launches, true));
     PDMTS_TRY(pd_run_chain(pd, m, 1, A->theta_free.data(), s, false));
     PDMTS_TRY(step_fe_free(A, A->fe_stream, true, &launches));
     PDMTS_CUDA_TRY(cudaStreamWaitEvent(s, A->ev_join, 0));

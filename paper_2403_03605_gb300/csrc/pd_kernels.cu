@@ -488,11 +488,9 @@ __global__ void k_constraint(const int dim, const int64_t nl, const int64_t *__r
     }
 }
 
-__global__ void k_pd_add_link(const PDAddLink A)
+// U_PD += W and the next prediction for link-segment entry t (< seg_n[0] + seg_n[1]).
+__device__ __forceinline__ void pd_add_link_node(const PDAddLink &A, const int64_t t)
 {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= A.seg_n[0] + A.seg_n[1])
-        return;
     const int64_t i = t < A.seg_n[0] ? A.seg_lo[0] + t : A.seg_lo[1] + (t - A.seg_n[0]);
     const int64_t n = A.n;
     if (A.u) {
@@ -553,16 +551,17 @@ __global__ void k_pd_add_link(const PDAddLink A)
     }
 }
 
-// End of a coarse step in one pass: count the bits that changed in flagged
-// words (a vs the step-start words b) into count[0], copy a into b (the next
-// step's start words), copy lam into lam0, and zero count[1] (the counter
-// the next step adds to; the two swap every step).
-__global__ void k_finish_words(const int64_t nwords, const uint32_t *__restrict__ a, uint32_t *__restrict__ b,
-                               const uint8_t *__restrict__ flag, unsigned long long *count,
-                               unsigned long long *next_count, const int64_t nlam, const double *__restrict__ lam,
-                               double *__restrict__ lam0)
+// End of a coarse step in one pass: U_PD += W on the link segments (L), count
+// the bits that changed in flagged words (a vs the step-start words b) into
+// count[0], copy a into b (the next step's start words), copy lam into lam0.
+__global__ void k_finish_step(const PDAddLink L, const int64_t nwords, const uint32_t *__restrict__ a,
+                              uint32_t *__restrict__ b, const uint8_t *__restrict__ flag,
+                              unsigned long long *count, const int64_t nlam, const double *__restrict__ lam,
+                              double *__restrict__ lam0)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < L.seg_n[0] + L.seg_n[1])
+        pd_add_link_node(L, i);
     unsigned c = 0;
     if (i < nwords) {
         const uint32_t ai = a[i], bi = b[i];
@@ -573,8 +572,6 @@ __global__ void k_finish_words(const int64_t nwords, const uint32_t *__restrict_
     }
     if (i < nlam)
         lam0[i] = lam[i];
-    if (i == 0)
-        *next_count = 0ull;
     c = __reduce_add_sync(0xffffffffu, c);
     if ((threadIdx.x & 31) == 0 && c)
         atomicAdd(count, (unsigned long long)c);
@@ -695,22 +692,14 @@ cudaError_t launch_constraint_pd_many(int64_t nl, const int64_t *gpd_ptr, const 
     return cudaGetLastError();
 }
 
-cudaError_t launch_pd_add_link(const PDAddLink &A, cudaStream_t s)
+cudaError_t launch_finish_step(const PDAddLink &L, int64_t nwords, const uint32_t *a, uint32_t *b,
+                               const uint8_t *word_flag, unsigned long long *count, int64_t nlam,
+                               const double *lam, double *lam0, cudaStream_t s)
 {
-    const int64_t cnt = A.seg_n[0] + A.seg_n[1];
-    if (cnt == 0)
-        return cudaSuccess;
-    k_pd_add_link<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(A);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_finish_words(int64_t nwords, const uint32_t *a, uint32_t *b, const uint8_t *word_flag,
-                                unsigned long long *count, unsigned long long *next_count, int64_t nlam,
-                                const double *lam, double *lam0, cudaStream_t s)
-{
-    const int64_t n = std::max<int64_t>(std::max<int64_t>(nwords, nlam), 1);
-    k_finish_words<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(nwords, a, b, word_flag, count, next_count, nlam, lam,
-                                                                lam0);
+    const int64_t n =
+        std::max<int64_t>(std::max<int64_t>(std::max<int64_t>(nwords, nlam), L.seg_n[0] + L.seg_n[1]), 1);
+    k_finish_step<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(L, nwords, a, b, word_flag, count, nlam, lam,
+                                                               lam0);
     return cudaGetLastError();
 }
 
