@@ -1278,10 +1278,13 @@ static int fe_cheb_solve(pdmts_fem *fe, int nrhs, double *x, const double *b, do
         const double c1 = fe->cheb_c1[(size_t)k], c2 = fe->cheb_c2[(size_t)k];
         if (fe->paired_rows) {
             // each iteration a programmatic dependent of the kernel before it
-            // (2D: the small solve no longer trails the PD chain beside it)
+            // (2D: the small solve no longer trails the PD chain beside it);
+            // CTAs of 512 threads (16K registers): a resident FE CTA takes the
+            // register share of one PD lattice CTA, like a 256-thread one, for
+            // twice the work
             cudaLaunchConfig_t cfg = {};
-            cfg.gridDim = dim3(blocks(fe->n * nrhs));
-            cfg.blockDim = dim3(256);
+            cfg.gridDim = dim3(blocks(fe->n * nrhs, 512));
+            cfg.blockDim = dim3(512);
             cfg.stream = s;
             cudaLaunchAttribute at[1];
             at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
