@@ -1262,7 +1262,7 @@ static int fe_cheb_solve(pdmts_fem *fe, int nrhs, double *x, const double *b, do
     const int64_t tot = ndof * nrhs;
     for (int c = 0; c < nrhs; ++c) {
         if (fe->paired_rows)
-            k_fe_residual<<<blocks(ndof), 256, 0, s>>>(ndof, fe->W, fe->d_col.p, fe->d_Keff.p, x + c * ndof,
+            k_fe_residual<<<blocks(ndof, 512), 512, 0, s>>>(ndof, fe->W, fe->d_col.p, fe->d_Keff.p, x + c * ndof,
                                                       b + c * ndof, r + c * ndof, fe->d_Minv.p, 1.0 / fe->cheb_theta,
                                                       d0 + c * ndof);
         else
@@ -1315,7 +1315,7 @@ static int fe_free_enqueue(pdmts_fem *fe, double dt, double beta, double gamma, 
     k_fe_predict<<<blocks(ndof), 256, 0, s>>>(ndof, fe->d_u.p, fe->d_v.p, fe->d_a.p, dt, beta, gamma, fe->d_ut.p,
                                               fe->d_vt.p);
     if (fe->paired_rows)
-        k_fe_residual<<<blocks(ndof), 256, 0, s>>>(ndof, fe->W, fe->d_col.p, fe->d_K.p, fe->d_ut.p, fe->d_P.p,
+        k_fe_residual<<<blocks(ndof, 512), 512, 0, s>>>(ndof, fe->W, fe->d_col.p, fe->d_K.p, fe->d_ut.p, fe->d_P.p,
                                                    fe->d_b.p, nullptr, 0.0, nullptr);
     else
         k_fe_residual_group<<<blocks(ndof * kRowGroup), 256, 0, s>>>(ndof, fe->W, fe->d_col.p, fe->d_K.p, fe->d_ut.p,
